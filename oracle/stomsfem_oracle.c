@@ -1,0 +1,450 @@
+/*
+ * Plain FP64 CPU oracle for the StoMsFEM local-upscaling hot path
+ * (Hou, Li, Zhang: "Exploring the locally low dimensional structure in
+ * solving random elliptic PDEs").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls,
+ * links or includes this file; only the test suite, the smoke check and
+ * the CPU-baseline leg of the benchmark load it.  It shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * Everything here is the textbook definition written out, slow and
+ * obviously correct, in IEEE double:
+ *   - coefficient sampling    a(x, xi) = exp(s * sum_i xi_i psi_i(x))
+ *                             (nonlinear transform, Sec. 2.1.3) or the
+ *                             bounded-exponent variant exp(L*sigmoid(g*z));
+ *   - fine Q1 finite elements (the fine mesh T_h of Sec. 2.2);
+ *   - the MsFEM cell problem  -div(a grad phi) = 0 in the patch,
+ *                             phi = bilinear nodal function on the patch
+ *                             boundary (Eq. MsFEB), solved on T_h;
+ *   - oversampling            (Remark on oversampling, Sec. 2.2): solve on
+ *                             the enlarged patch, recombine the patch
+ *                             solutions so the basis is nodal at the cell
+ *                             corners, restrict to the cell;
+ *   - upscaled stiffness/load (Eq. stiffness_local): S_ll' = int a grad
+ *                             phi_l . grad phi_l', b_l = int f phi_l;
+ *   - coarse assembly + solve (Eq. upscaleSUF) with zero Dirichlet data;
+ *   - fine-grid FEM           (the standard FEM the paper compares with).
+ *
+ * Linear systems use this file's own banded Cholesky.  Each of the four
+ * cell problems is solved separately (no partition-of-unity shortcut) so
+ * that sum_l phi_l == 1 remains a genuine check.
+ *
+ * Conventions: fine grid nf x nf elements on the unit square, h = 1/nf;
+ * node (i, j) at (i h, j h), i = x index; arrays are y-major
+ * (index j*(nf+1)+i for nodes, ey*nf+ex for elements).  Element corner
+ * order SW, SE, NE, NW.  Coarse cell (cx, cy) covers fine elements
+ * [cx*rho, (cx+1)*rho) x [cy*rho, (cy+1)*rho), rho = nf/nc.  K_e is
+ * packed as the upper triangle row-major: (0,0) (0,1) (0,2) (0,3) (1,1)
+ * (1,2) (1,3) (2,2) (2,3) (3,3).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Q1 element stiffness on a square for unit coefficient (independent of
+ * the element size in 2D), corners SW, SE, NE, NW. */
+static const double KREF[4][4] = {
+    {4.0 / 6.0, -1.0 / 6.0, -2.0 / 6.0, -1.0 / 6.0},
+    {-1.0 / 6.0, 4.0 / 6.0, -1.0 / 6.0, -2.0 / 6.0},
+    {-2.0 / 6.0, -1.0 / 6.0, 4.0 / 6.0, -1.0 / 6.0},
+    {-1.0 / 6.0, -2.0 / 6.0, -1.0 / 6.0, 4.0 / 6.0}};
+
+/* corner c of an element (ex, ey): x/y offsets */
+static const int CDX[4] = {0, 1, 1, 0};
+static const int CDY[4] = {0, 0, 1, 1};
+
+/* ---------------------------------------------------------------- */
+/* Coefficient sampling: a(x, xi) at fine-element centroids.          */
+/* kind 0: a = exp(scale * z);  kind 1: a = exp(L / (1 + exp(-g z))) */
+/* with z(x) = sum_i xi_i exp(-|x - c_i|^2 / w^2), c_i the lattice     */
+/* cell centres ((bx+1/2)/nbx, (by+1/2)/nby), i = by*nbx + bx.         */
+/* ---------------------------------------------------------------- */
+int orc_sample_coef(int nf, int kind, int nbx, int nby, double width,
+                    double scale, double contrast_log, double gain,
+                    const double* xi, int S, double* a, int nthreads) {
+  if (nf <= 0 || nbx <= 0 || nby <= 0 || S < 0 || width <= 0.0) return -1;
+  const int K = nbx * nby;
+  const double h = 1.0 / nf;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static) collapse(2)
+#endif
+  for (int s = 0; s < S; ++s) {
+    for (int ey = 0; ey < nf; ++ey) {
+      const double y = (ey + 0.5) * h;
+      for (int ex = 0; ex < nf; ++ex) {
+        const double x = (ex + 0.5) * h;
+        double z = 0.0;
+        for (int by = 0; by < nby; ++by) {
+          const double cy = (by + 0.5) / nby;
+          for (int bx = 0; bx < nbx; ++bx) {
+            const double cx = (bx + 0.5) / nbx;
+            const double r2 = (x - cx) * (x - cx) + (y - cy) * (y - cy);
+            z += xi[(size_t)s * K + by * nbx + bx] * exp(-r2 / (width * width));
+          }
+        }
+        double v;
+        if (kind == 0)
+          v = exp(scale * z);
+        else
+          v = exp(contrast_log / (1.0 + exp(-gain * z)));
+        a[((size_t)s * nf + ey) * nf + ex] = v;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------- */
+/* Banded symmetric positive definite matrices.                       */
+/* Storage: band[k*(bw+1) + d] = A[k][k-d], d = 0..bw (lower band).   */
+/* ---------------------------------------------------------------- */
+static inline double* band_at(double* band, int bw, int r, int c) {
+  /* r >= c, r - c <= bw */
+  return &band[(size_t)r * (bw + 1) + (r - c)];
+}
+
+/* In-place Cholesky A = L L^T, L stored in the same band. Returns 0 or
+ * the (1-based) index of the first non-positive pivot. */
+static int band_cholesky(double* band, int n, int bw) {
+  for (int j = 0; j < n; ++j) {
+    /* L[j][j] = sqrt(A[j][j] - sum_{p<j} L[j][p]^2) */
+    double s = *band_at(band, bw, j, j);
+    const int p0 = j - bw < 0 ? 0 : j - bw;
+    for (int p = p0; p < j; ++p) {
+      const double l = *band_at(band, bw, j, p);
+      s -= l * l;
+    }
+    if (!(s > 0.0)) return j + 1;
+    const double ljj = sqrt(s);
+    *band_at(band, bw, j, j) = ljj;
+    /* L[i][j] = (A[i][j] - sum_{p<j} L[i][p] L[j][p]) / L[j][j] */
+    const int i1 = j + bw < n - 1 ? j + bw : n - 1;
+    for (int i = j + 1; i <= i1; ++i) {
+      double t = *band_at(band, bw, i, j);
+      const int q0 = i - bw > p0 ? i - bw : p0;
+      for (int p = q0; p < j; ++p)
+        t -= *band_at(band, bw, i, p) * *band_at(band, bw, j, p);
+      *band_at(band, bw, i, j) = t / ljj;
+    }
+  }
+  return 0;
+}
+
+/* Solve L L^T x = b in place (b overwritten with x). */
+static void band_solve(double* band, int n, int bw, double* b) {
+  for (int i = 0; i < n; ++i) { /* L y = b */
+    double t = b[i];
+    const int p0 = i - bw < 0 ? 0 : i - bw;
+    for (int p = p0; p < i; ++p) t -= *band_at(band, bw, i, p) * b[p];
+    b[i] = t / *band_at(band, bw, i, i);
+  }
+  for (int i = n - 1; i >= 0; --i) { /* L^T x = y */
+    double t = b[i];
+    const int q1 = i + bw < n - 1 ? i + bw : n - 1;
+    for (int q = i + 1; q <= q1; ++q) t -= *band_at(band, bw, q, i) * b[q];
+    b[i] = t / *band_at(band, bw, i, i);
+  }
+}
+
+/* 4x4 inverse by Gauss-Jordan elimination with partial pivoting. */
+static int inv4(const double Ain[4][4], double Ainv[4][4]) {
+  double M[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? Ain[r][c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return -1;
+    if (piv != c)
+      for (int k = 0; k < 8; ++k) {
+        double t = M[c][k]; M[c][k] = M[piv][k]; M[piv][k] = t;
+      }
+    const double d = M[c][c];
+    for (int k = 0; k < 8; ++k) M[c][k] /= d;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+        for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) Ainv[r][c] = M[r][c + 4];
+  return 0;
+}
+
+/* ---------------------------------------------------------------- */
+/* One MsFEM unit: cell (cx, cy) of one sample, oversampling layer o. */
+/*   a      : [nf*nf] coefficient of this sample                       */
+/*   Ke[10] : packed upscaled stiffness, be[4] : upscaled load         */
+/*   phi    : optional [4][(rho+1)^2] basis on the cell nodes          */
+/*   psi    : optional [4][(Nx+1)(Ny+1)] patch solutions (before the   */
+/*            oversampling recombination); dims via patch_dims         */
+/* Returns 0, or -k for a failed Cholesky at pivot k.                  */
+/* ---------------------------------------------------------------- */
+void orc_patch_bounds(int nf, int nc, int cx, int cy, int o, int* x0, int* x1,
+                      int* y0, int* y1) {
+  const int rho = nf / nc;
+  *x0 = cx * rho - o < 0 ? 0 : cx * rho - o;
+  *x1 = (cx + 1) * rho + o > nf ? nf : (cx + 1) * rho + o;
+  *y0 = cy * rho - o < 0 ? 0 : cy * rho - o;
+  *y1 = (cy + 1) * rho + o > nf ? nf : (cy + 1) * rho + o;
+}
+
+int orc_cell(int nf, int nc, double f, const double* a, int cx, int cy, int o,
+             double* Ke, double* be, double* phi, double* psi) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || o < 0) return -1000;
+  const int rho = nf / nc;
+  int x0, x1, y0, y1;
+  orc_patch_bounds(nf, nc, cx, cy, o, &x0, &x1, &y0, &y1);
+  const int Nx = x1 - x0, Ny = y1 - y0;     /* patch elements per side */
+  const int mx = Nx - 1, my = Ny - 1;       /* interior nodes per side */
+  const int n = mx * my;
+  const int bw = mx + 1;                    /* 9-point stencil bandwidth */
+  const int PN = (Nx + 1) * (Ny + 1);       /* patch nodes */
+
+  double* band = (double*)calloc((size_t)(n > 0 ? n : 1) * (bw + 1), sizeof(double));
+  double* rhs = (double*)calloc((size_t)4 * (n > 0 ? n : 1), sizeof(double));
+  double* pv = (double*)malloc(sizeof(double) * 4 * PN); /* psi_l on patch nodes */
+  if (!band || !rhs || !pv) { free(band); free(rhs); free(pv); return -1001; }
+
+  /* Boundary data: the bilinear nodal functions of the patch rectangle,
+   * p_SW = (1-X)(1-Y), p_SE = X(1-Y), p_NE = X Y, p_NW = (1-X) Y, with
+   * X, Y in [0, 1] the patch's own normalised coordinates (Eq. MsFEB). */
+  for (int j = 0; j <= Ny; ++j)
+    for (int i = 0; i <= Nx; ++i) {
+      const double X = (double)i / Nx, Y = (double)j / Ny;
+      const int k = j * (Nx + 1) + i;
+      pv[0 * PN + k] = (1.0 - X) * (1.0 - Y);
+      pv[1 * PN + k] = X * (1.0 - Y);
+      pv[2 * PN + k] = X * Y;
+      pv[3 * PN + k] = (1.0 - X) * Y;
+    }
+
+  /* Element-by-element assembly of A_II and of -A_IB p_l. */
+  for (int ey = 0; ey < Ny; ++ey)
+    for (int ex = 0; ex < Nx; ++ex) {
+      const double ae = a[(size_t)(y0 + ey) * nf + (x0 + ex)];
+      for (int r = 0; r < 4; ++r) {
+        const int ri = ex + CDX[r], rj = ey + CDY[r];
+        const int r_int = ri > 0 && ri < Nx && rj > 0 && rj < Ny;
+        if (!r_int) continue;
+        const int rk = (rj - 1) * mx + (ri - 1);
+        for (int c = 0; c < 4; ++c) {
+          const int ci = ex + CDX[c], cj = ey + CDY[c];
+          const double v = ae * KREF[r][c];
+          const int c_int = ci > 0 && ci < Nx && cj > 0 && cj < Ny;
+          if (c_int) {
+            const int ck = (cj - 1) * mx + (ci - 1);
+            if (ck <= rk) *band_at(band, bw, rk, ck) += v;
+          } else {
+            const int pk = cj * (Nx + 1) + ci;
+            for (int l = 0; l < 4; ++l) rhs[l * n + rk] -= v * pv[l * PN + pk];
+          }
+        }
+      }
+    }
+
+  int rc = 0;
+  if (n > 0) {
+    rc = band_cholesky(band, n, bw);
+    if (rc != 0) { free(band); free(rhs); free(pv); return -rc; }
+    for (int l = 0; l < 4; ++l) band_solve(band, n, bw, rhs + (size_t)l * n);
+    for (int j = 1; j < Ny; ++j)
+      for (int i = 1; i < Nx; ++i)
+        for (int l = 0; l < 4; ++l)
+          pv[l * PN + j * (Nx + 1) + i] = rhs[l * n + (j - 1) * mx + (i - 1)];
+  }
+  if (psi) memcpy(psi, pv, sizeof(double) * 4 * PN);
+
+  /* Oversampling recombination: C[j][k] = psi_j(corner k of the cell);
+   * phi_i = sum_j Cinv[i][j]... with phi_i(corner k) = delta_ik, i.e.
+   * phi = D psi with D C = I, D = C^{-1}. */
+  const int ccx[4] = {cx * rho, (cx + 1) * rho, (cx + 1) * rho, cx * rho};
+  const int ccy[4] = {cy * rho, cy * rho, (cy + 1) * rho, (cy + 1) * rho};
+  double C[4][4], D[4][4];
+  for (int j = 0; j < 4; ++j)
+    for (int k = 0; k < 4; ++k)
+      C[j][k] = pv[j * PN + (ccy[k] - y0) * (Nx + 1) + (ccx[k] - x0)];
+  if (inv4(C, D) != 0) { free(band); free(rhs); free(pv); return -1002; }
+
+  /* phi on the cell nodes */
+  const int CN = (rho + 1) * (rho + 1);
+  double* ph = (double*)malloc(sizeof(double) * 4 * CN);
+  if (!ph) { free(band); free(rhs); free(pv); return -1001; }
+  for (int j = 0; j <= rho; ++j)
+    for (int i = 0; i <= rho; ++i) {
+      const int pk = (cy * rho + j - y0) * (Nx + 1) + (cx * rho + i - x0);
+      for (int l = 0; l < 4; ++l) {
+        double v = 0.0;
+        for (int q = 0; q < 4; ++q) v += D[l][q] * pv[q * PN + pk];
+        ph[l * CN + j * (rho + 1) + i] = v;
+      }
+    }
+
+  /* Eq. stiffness_local on the fine grid of the cell: exact integration of
+   * a piecewise-constant a against Q1 functions. */
+  double S[4][4] = {{0}};
+  double b[4] = {0};
+  const double h = 1.0 / nf;
+  for (int ey = 0; ey < rho; ++ey)
+    for (int ex = 0; ex < rho; ++ex) {
+      const double ae = a[(size_t)(cy * rho + ey) * nf + (cx * rho + ex)];
+      double loc[4][4];
+      for (int l = 0; l < 4; ++l)
+        for (int c = 0; c < 4; ++c)
+          loc[l][c] = ph[l * CN + (ey + CDY[c]) * (rho + 1) + (ex + CDX[c])];
+      for (int l = 0; l < 4; ++l)
+        for (int lp = 0; lp < 4; ++lp) {
+          double e = 0.0;
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) e += loc[l][r] * KREF[r][c] * loc[lp][c];
+          S[l][lp] += ae * e;
+        }
+      for (int l = 0; l < 4; ++l)
+        for (int c = 0; c < 4; ++c) b[l] += f * h * h / 4.0 * loc[l][c];
+    }
+  int q = 0;
+  for (int l = 0; l < 4; ++l)
+    for (int lp = l; lp < 4; ++lp) Ke[q++] = S[l][lp];
+  for (int l = 0; l < 4; ++l) be[l] = b[l];
+  if (phi) memcpy(phi, ph, sizeof(double) * 4 * CN);
+  free(ph); free(band); free(rhs); free(pv);
+  return 0;
+}
+
+/* All units of S samples.  oversample: [nc*nc] layer widths or NULL (0).
+ * Ke [S][nc*nc][10], be [S][nc*nc][4], phi optional
+ * [S][nc*nc][4][(rho+1)^2].  status [S*nc*nc] (0 ok). */
+int orc_upscale(int nf, int nc, double f, const double* a, const int8_t* oversample,
+                int S, double* Ke, double* be, double* phi, int32_t* status,
+                int nthreads) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0) return -1;
+  const int rho = nf / nc;
+  const int CN = (rho + 1) * (rho + 1);
+  const long units = (long)S * nc * nc;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+#endif
+  for (long u = 0; u < units; ++u) {
+    const int s = (int)(u / (nc * nc));
+    const int cell = (int)(u % (nc * nc));
+    const int cx = cell % nc, cy = cell / nc;
+    const int o = oversample ? oversample[cell] : 0;
+    const int rc = orc_cell(nf, nc, f, a + (size_t)s * nf * nf, cx, cy, o,
+                            Ke + (size_t)u * 10, be + (size_t)u * 4,
+                            phi ? phi + (size_t)u * 4 * CN : NULL, NULL);
+    if (status) status[u] = rc;
+    if (rc != 0) bad = 1;
+  }
+  return bad ? -2 : 0;
+}
+
+/* Eq. upscaleSUF: assemble the coarse system from the packed K_e and b_e
+ * over the (nc+1)^2 coarse nodes, keep the interior nodes (zero Dirichlet
+ * on the boundary), solve.  u [S][(nc+1)^2], boundary entries 0. */
+int orc_coarse_solve(int nc, const double* Ke, const double* be, int S, double* u) {
+  if (nc <= 0 || S < 0) return -1;
+  const int NN = nc + 1;
+  const int mi = nc - 1, n = mi * mi, bw = mi + 1;
+  for (int s = 0; s < S; ++s) {
+    double* band = (double*)calloc((size_t)(n > 0 ? n : 1) * (bw + 1), sizeof(double));
+    double* rhs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!band || !rhs) { free(band); free(rhs); return -3; }
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cx = 0; cx < nc; ++cx) {
+        const double* K = Ke + ((size_t)s * nc * nc + cy * nc + cx) * 10;
+        const double* B = be + ((size_t)s * nc * nc + cy * nc + cx) * 4;
+        double M[4][4];
+        int q = 0;
+        for (int l = 0; l < 4; ++l)
+          for (int lp = l; lp < 4; ++lp) { M[l][lp] = K[q]; M[lp][l] = K[q]; ++q; }
+        for (int r = 0; r < 4; ++r) {
+          const int ri = cx + CDX[r], rj = cy + CDY[r];
+          if (ri <= 0 || ri >= nc || rj <= 0 || rj >= nc) continue;
+          const int rk = (rj - 1) * mi + (ri - 1);
+          rhs[rk] += B[r];
+          for (int c = 0; c < 4; ++c) {
+            const int ci = cx + CDX[c], cj = cy + CDY[c];
+            if (ci <= 0 || ci >= nc || cj <= 0 || cj >= nc) continue;
+            const int ck = (cj - 1) * mi + (ci - 1);
+            if (ck <= rk) *band_at(band, bw, rk, ck) += M[r][c];
+          }
+        }
+      }
+    int rc = 0;
+    if (n > 0) {
+      rc = band_cholesky(band, n, bw);
+      if (rc == 0) band_solve(band, n, bw, rhs);
+    }
+    double* us = u + (size_t)s * NN * NN;
+    for (int k = 0; k < NN * NN; ++k) us[k] = 0.0;
+    if (rc == 0)
+      for (int j = 1; j < nc; ++j)
+        for (int i = 1; i < nc; ++i) us[j * NN + i] = rhs[(j - 1) * mi + (i - 1)];
+    free(band); free(rhs);
+    if (rc != 0) return -4;
+  }
+  return 0;
+}
+
+/* Standard Q1 FEM on the fine grid, zero Dirichlet data, load f:
+ * u [(nf+1)^2], boundary entries 0. */
+int orc_fine_fem(int nf, double f, const double* a, double* u) {
+  if (nf <= 0) return -1;
+  const int NN = nf + 1, mi = nf - 1, n = mi * mi, bw = mi + 1;
+  const double h = 1.0 / nf;
+  double* band = (double*)calloc((size_t)(n > 0 ? n : 1) * (bw + 1), sizeof(double));
+  double* rhs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!band || !rhs) { free(band); free(rhs); return -3; }
+  for (int ey = 0; ey < nf; ++ey)
+    for (int ex = 0; ex < nf; ++ex) {
+      const double ae = a[(size_t)ey * nf + ex];
+      for (int r = 0; r < 4; ++r) {
+        const int ri = ex + CDX[r], rj = ey + CDY[r];
+        if (ri <= 0 || ri >= nf || rj <= 0 || rj >= nf) continue;
+        const int rk = (rj - 1) * mi + (ri - 1);
+        rhs[rk] += f * h * h / 4.0;
+        for (int c = 0; c < 4; ++c) {
+          const int ci = ex + CDX[c], cj = ey + CDY[c];
+          if (ci <= 0 || ci >= nf || cj <= 0 || cj >= nf) continue;
+          const int ck = (cj - 1) * mi + (ci - 1);
+          if (ck <= rk) *band_at(band, bw, rk, ck) += ae * KREF[r][c];
+        }
+      }
+    }
+  int rc = 0;
+  if (n > 0) {
+    rc = band_cholesky(band, n, bw);
+    if (rc == 0) band_solve(band, n, bw, rhs);
+  }
+  for (int k = 0; k < NN * NN; ++k) u[k] = 0.0;
+  if (rc == 0)
+    for (int j = 1; j < nf; ++j)
+      for (int i = 1; i < nf; ++i) u[j * NN + i] = rhs[(j - 1) * mi + (i - 1)];
+  free(band); free(rhs);
+  return rc == 0 ? 0 : -4;
+}
+
+/* Solve a dense-in-band SPD system given as a full n x n row-major matrix
+ * through this file's banded Cholesky (bw = half bandwidth).  Exposed so
+ * that the factorisation itself can be checked against a library solve. */
+int orc_band_solve_dense(int n, int bw, const double* A, double* b) {
+  double* band = (double*)calloc((size_t)(n > 0 ? n : 1) * (bw + 1), sizeof(double));
+  if (!band) return -3;
+  for (int r = 0; r < n; ++r)
+    for (int c = r - bw < 0 ? 0 : r - bw; c <= r; ++c)
+      *band_at(band, bw, r, c) = A[(size_t)r * n + c];
+  int rc = band_cholesky(band, n, bw);
+  if (rc == 0) band_solve(band, n, bw, b);
+  free(band);
+  return rc == 0 ? 0 : -4;
+}
