@@ -1,0 +1,396 @@
+"""Throughput of the StoMsFEM local-upscaling hot path on GB300.
+
+One step = one batch of samples through the whole plain path:
+coefficient sampling (xi -> a), simultaneous local upscaling of every
+(sample, coarse cell) unit (a -> K_e, b_e), coarse assembly + solve and the
+running Monte Carlo moments (K_e, b_e -> u, mean, M2).  The metric is
+coarse elements (units) upscaled per second at H/h = 32 (the 1024^2 /
+32^2 workload with per-cell oversampling 0..4), for the chosen precision
+form, with the plain FP64 path measured in the same run for the speed-up
+and the coarse-solution error of the chosen form against it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun), every rank processes its own samples (weak scaling,
+no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1607_00693_gb300 import workloads as W  # noqa: E402
+
+FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
+DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def alu_peak_tflops(form):
+    """Non-tensor peak from unit counts and clock: 152 SMs x 128 FP32 lanes
+    x 2 flops x 2.07 GHz for FP32; FP64 at 2 FMA/clk/SM (1/64 of FP32), the
+    rate the FP64 FMA probe measured (1.20 TFLOP/s at 2.0 GHz)."""
+    clk = _peaks().get("sm_max_mhz", 2070.0) * 1e6
+    if form == "fp64":
+        return 152 * 2 * 2 * clk / 1e12
+    return 152 * 128 * 2 * clk / 1e12
+
+
+def unit_flops(nf, nc, ov, form, refine=2):
+    """Algorithmic flops of one sample (all cells): banded Cholesky of each
+    patch matrix, forward/back substitution of 3 right-hand sides, the
+    refinement sweeps, the K_e/b_e accumulation (about 70 flops per fine
+    element of the cell)."""
+    rho = nf // nc
+    tot = 0.0
+    for cell in range(nc * nc):
+        cx, cy = cell % nc, cell // nc
+        o = int(ov[cell]) if ov is not None else 0
+        x0, x1 = max(0, cx * rho - o), min(nf, (cx + 1) * rho + o)
+        y0, y1 = max(0, cy * rho - o), min(nf, (cy + 1) * rho + o)
+        mx, my = x1 - x0 - 1, y1 - y0 - 1
+        n, b = mx * my, mx + 1
+        k = np.arange(n)
+        t = np.minimum(b, n - 1 - k).astype(np.float64)
+        chol = float(np.sum(t * (t + 1) / 2))
+        solve = 3.0 * 2.0 * float(np.sum(t))
+        fl = 2.0 * (chol + solve)
+        if form == "fp32r":
+            fl += refine * (2.0 * 3 * 9 * n + 2.0 * solve)
+        fl += 70.0 * rho * rho
+        tot += fl
+    return tot
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_step(w, xi, ov, nthreads=0):
+    """The oracle on one batch: a from xi, per-unit MsFEM, coarse solve,
+    moments.  Returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    a = oracle.sample_coef(w["nf"], w["field"], xi, nthreads=nthreads)
+    Ke, be = oracle.upscale(w["nf"], w["nc"], w["f"], a, ov, nthreads=nthreads)
+    u = oracle.coarse_solve(w["nc"], Ke, be)
+    oracle.mc_moments(u)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, ov, samples=2):
+    import oracle
+    oracle.build()
+    xi = W.draw_xi(w["field"], samples, w["seed"], w["dist"])
+    dt = cpu_oracle_step(w, xi, ov)
+    units = samples * w["nc"] ** 2
+    return {"value": units / dt, "unit": "units/s", "cores": oracle.ncores(), "kind": "oracle",
+            "sample": "%d samples x %d cells of %s (FP64 oracle: a, cell problems, coarse solve), "
+                      "%.1f s" % (samples, w["nc"] ** 2, w["name"], dt)}
+
+
+def run_reference(args, w, ov):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    S = args.ref_samples
+    units = S * w["nc"] ** 2
+    for i in range(args.warmup):
+        cpu_oracle_step(w, W.draw_xi(w["field"], S, w["seed"], w["dist"], first=i * S), ov)
+    tt = 0.0
+    for i in range(args.steps):
+        tt += cpu_oracle_step(w, W.draw_xi(w["field"], S, w["seed"], w["dist"],
+                                           first=(args.warmup + i) * S), ov)
+    value = units * args.steps / tt
+    line = {"impl": "reference", "metric": "coarse elements upscaled/s at H/h=32",
+            "value": value, "unit": "units/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "nf": w["nf"], "nc": w["nc"],
+                       "samples_per_step": S, "oversample": "0..4 per cell"},
+            "cpu_baseline": {"value": value, "unit": "units/s", "cores": oracle.ncores(),
+                             "kind": "oracle",
+                             "sample": "%d samples x %d cells per step of %s" % (S, w["nc"] ** 2,
+                                                                                w["name"])},
+            "e2e": {"value": value, "unit": "units/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp32", choices=list(FORMS))
+    ap.add_argument("--workload", default="upscale_1024")
+    ap.add_argument("--batch", type=int, default=512, help="samples per step")
+    ap.add_argument("--fp64-batch", type=int, default=32, help="samples per step of the FP64 arm")
+    ap.add_argument("--ref-samples", type=int, default=1)
+    ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    w = W.workload(args.workload)
+    w["name"] = args.workload
+    ov = W.draw_oversample(w["nc"], w["oversample"])
+    if args.impl == "reference":
+        return run_reference(args, w, ov)
+
+    import torch
+    from paper_1607_00693_gb300 import api
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    nf, nc = w["nf"], w["nc"]
+    ncell = nc * nc
+    B = args.batch
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    K = W.n_vars(w["field"])
+    total = w["samples"]
+    # this rank's samples: a contiguous shard of the workload's stream
+    per_rank = max(B, total // ws)
+    xi_host = W.draw_xi(w["field"], per_rank, w["seed"], w["dist"], first=rank * per_rank)
+    xi = torch.from_numpy(xi_host).to(dev)
+    ov_t = torch.from_numpy(ov).to(dev) if ov is not None else None
+    mo = int(ov.max()) if ov is not None else 0
+    nn = (nc + 1) ** 2
+
+    def buffers(Bs, form):
+        a = torch.empty((Bs, nf, nf), dtype=torch.float64, device=dev)
+        Ke = torch.empty((Bs, ncell, 10), dtype=torch.float64, device=dev)
+        be = torch.empty((Bs, ncell, 4), dtype=torch.float64, device=dev)
+        u = torch.empty((Bs, nn), dtype=torch.float64, device=dev)
+        _, rb = api.stomsfem_upscale_workspace_size(g, mo, FORMS[form])
+        wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+        wsc = torch.empty(api.stomsfem_coarse_workspace_size(g, Bs), dtype=torch.uint8, device=dev)
+        mom = [torch.zeros(nn, dtype=torch.float64, device=dev) for _ in range(2)]
+        cnt = torch.zeros(1, dtype=torch.float64, device=dev)
+        return dict(a=a, Ke=Ke, be=be, u=u, wsu=wsu, wsc=wsc, mean=mom[0], m2=mom[1], cnt=cnt)
+
+    def step(bf, xs, form, ev=None):
+        api.stomsfem_sample_coef(g, fld, xs, bf["a"], stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        api.stomsfem_upscale(g, bf["a"], bf["Ke"], bf["be"], oversample=ov_t, max_oversample=mo,
+                             precision=FORMS[form], refine_iters=2, workspace=bf["wsu"], stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        api.stomsfem_coarse_solve(g, bf["Ke"], bf["be"], bf["u"], bf["mean"], bf["m2"], bf["cnt"],
+                                  workspace=bf["wsc"], stream=stream)
+
+    def xs_for(i, Bs):
+        s0 = (i * Bs) % max(1, per_rank - Bs + 1)
+        return xi[s0:s0 + Bs]
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(form, Bs, steps, warmup, clocks=None):
+        bf = buffers(Bs, form)
+        with torch.cuda.stream(stream):
+            for i in range(warmup):
+                step(bf, xs_for(i, Bs), form)
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if clocks:
+                clocks.start()
+            e0.record(stream)
+            for i in range(steps):
+                step(bf, xs_for(warmup + i, Bs), form, evs[i])
+            e1.record(stream)
+            stream.synchronize()
+            clk = clocks.stop() if clocks else None
+            barrier()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        up_ms = [a.elapsed_time(b) for a, b in evs]
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, up_ms, clk, bf
+
+    form = args.form
+    clocks = ClockSampler(local)
+    ms, up_ms, clk, bf = timed(form, B, args.steps, args.warmup, clocks)
+    units_step = B * ncell
+    value = units_step * ws * args.steps / (ms / 1e3)
+    fl = unit_flops(nf, nc, ov, form) * B
+    up_avg = sum(up_ms) / len(up_ms)
+    achieved = fl / (up_avg / 1e3) / 1e12
+    peak = alu_peak_tflops(form)
+
+    # the plain FP64 arm (same path, FP64 throughout), smaller batch
+    ms64, up64, _, bf64 = timed("fp64", args.fp64_batch, max(1, min(args.steps, 2)), 1)
+    value64 = args.fp64_batch * ncell * ws * max(1, min(args.steps, 2)) / (ms64 / 1e3)
+    # coarse-solution error of the chosen form vs the FP64 path on the same samples
+    Bc = min(args.fp64_batch, B)
+    bf_c = buffers(Bc, form)
+    with torch.cuda.stream(stream):
+        step(bf_c, xs_for(0, Bc), form)
+        step(bf64, xs_for(0, args.fp64_batch), "fp64")
+    stream.synchronize()
+    uf = bf_c["u"].double().cpu().numpy()
+    u64 = bf64["u"][:Bc].cpu().numpy()
+    err = float(np.max(np.linalg.norm(uf - u64, axis=1) / np.linalg.norm(u64, axis=1)))
+    del bf_c
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public calls: pinned host xi in, u out
+        steps_e = args.steps
+        xh = torch.from_numpy(xi_host[:B].copy()).pin_memory()
+        uh = torch.empty((B, nn), dtype=torch.float64).pin_memory()
+        xd = torch.empty((B, K), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            xd.copy_(xh, non_blocking=True)
+            step(bf, xd, form)
+            uh.copy_(bf["u"], non_blocking=True)
+            stream.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps_e):
+                xd.copy_(xh, non_blocking=True)
+                step(bf, xd, form)
+                uh.copy_(bf["u"], non_blocking=True)
+            e1.record(stream)
+            stream.synchronize()
+        mse = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([mse], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mse = float(t.item())
+        e2e = {"value": units_step * ws * steps_e / (mse / 1e3), "unit": "units/s",
+               "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, ov, args.cpu_samples)
+
+    if rank == 0:
+        line = {
+            "metric": "coarse elements upscaled/s at H/h=32",
+            "value": value, "unit": "units/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[form], "data": "synthetic",
+            "config": {"workload": args.workload, "nf": nf, "nc": nc, "H_over_h": nf // nc,
+                       "samples_per_step": B, "units_per_step": units_step,
+                       "oversample": "0..4 per cell (seeded)", "form": form,
+                       "l2": "inputs larger than L2 (a: %.1f GB per step)" % (B * nf * nf * 8 / 1e9),
+                       "parallelism": "replicas (sample shards)" if ws > 1 else "single GPU"},
+            "forms": {"chosen": form, "chosen_units_per_s": value, "fp64_units_per_s": value64,
+                      "speedup_vs_fp64": value / value64, "coarse_rel_l2_vs_fp64": err},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "upscale_kernel (%s)" % form,
+                         "peak_note": "derived: 152 SMs x %s x 2070 MHz" % (
+                             "2 FP64 FMA/clk" if form == "fp64" else "128 FP32 lanes x 2 flops")},
+            "e2e": e2e,
+            "gpu_launches": 5 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,147 @@
+/*
+ * stomsfem.h -- C ABI of the GB300 (sm_103a) StoMsFEM local-upscaling library.
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the
+ * stochastic multiscale finite element method of Hou, Li and Zhang
+ * ("Exploring the locally low dimensional structure in solving random
+ * elliptic PDEs"): for every (random sample, coarse cell) pair it builds
+ * the fine-grid Q1 stiffness of the sampled coefficient, solves the cell
+ * problems that give the multiscale basis, forms the upscaled stiffness
+ * and load, and then assembles and solves each sample's coarse system.
+ *
+ * Conventions shared by every call
+ *  - Unit square, zero Dirichlet data on its boundary, constant load f.
+ *    Fine grid nf x nf square elements (h = 1/nf); coarse grid nc x nc
+ *    cells (H = 1/nc); rho = nf/nc must be an integer.
+ *  - Arrays are row-major and y-major: coefficient a[s][ey][ex] (one value
+ *    per fine element, evaluated at its centroid); coarse nodal vectors
+ *    u[s][J*(nc+1)+I].  Cell index cell = cy*nc + cx.
+ *  - Quad corner order SW, SE, NE, NW.  K_e is packed as its upper triangle
+ *    row by row: (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3).
+ *  - Every pointer argument named as device memory must point to device
+ *    memory of the current CUDA device; the caller owns all arrays.  All
+ *    calls are asynchronous on `stream` (NULL = legacy default stream)
+ *    unless stated otherwise; arguments are validated on the host before
+ *    any launch and a failing call launches nothing.
+ *  - Return value: STOMSFEM_OK (0) or a negative STOMSFEM_E* code;
+ *    stomsfem_last_error() gives a one-line message for the calling thread.
+ */
+#ifndef STOMSFEM_H
+#define STOMSFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* stomsfem_stream_t; /* same object as cudaStream_t */
+
+enum {
+  STOMSFEM_OK = 0,
+  STOMSFEM_EINVAL = -1,   /* bad argument or descriptor */
+  STOMSFEM_ENOMEM = -2,   /* workspace too small / allocation failed */
+  STOMSFEM_ECUDA = -3,    /* a CUDA runtime call failed (message has details) */
+  STOMSFEM_ENOTSPD = -4,  /* Cholesky breakdown in at least one unit */
+  STOMSFEM_ETIMEOUT = -5, /* a bounded device wait expired */
+  STOMSFEM_EVERSION = -6  /* bad or incompatible serialized object */
+};
+
+enum { STOMSFEM_FP64 = 0, STOMSFEM_FP32_REFINED = 1, STOMSFEM_FP32 = 2 };
+enum { STOMSFEM_FIELD_EXP = 0, STOMSFEM_FIELD_EXP_SIGMOID = 1 };
+
+typedef struct {
+  int32_t nf; /* fine elements per side */
+  int32_t nc; /* coarse cells per side, nf % nc == 0 */
+  double f;   /* constant load */
+} stomsfem_grid;
+
+/* Coefficient model (the nonlinear transform of Sec. 2.1.3 applied to an
+ * affine expansion in localized bumps):
+ *   z(x)  = sum_i xi_i exp(-|x - c_i|^2 / width^2),
+ *           c_i = ((bx + 1/2)/nbx, (by + 1/2)/nby),  i = by*nbx + bx;
+ *   EXP:          a = exp(scale * z)
+ *   EXP_SIGMOID:  a = exp(contrast_log / (1 + exp(-gain * z)))           */
+typedef struct {
+  int32_t kind;
+  int32_t nbx, nby;
+  double width;
+  double scale;
+  double contrast_log;
+  double gain;
+} stomsfem_field;
+
+const char* stomsfem_version(void);
+const char* stomsfem_last_error(void);
+
+/* Coefficient sampling (Sec. 2.1.3, the parametrized coefficient of
+ * Eq. MsFEB2).  xi: device [S][nbx*nby] float64; a: device [S][nf][nf]
+ * float64, a value per fine element at its centroid ((ex+1/2)h, (ey+1/2)h).
+ * Errors: EINVAL for bad sizes. */
+int stomsfem_sample_coef(const stomsfem_grid* grid, const stomsfem_field* field,
+                         const double* xi, int32_t S, double* a, stomsfem_stream_t stream);
+
+/* Scratch needed by stomsfem_upscale for one resident warp ("slot") and the
+ * recommended total (one slot per resident warp of the whole GPU).  Each
+ * slot holds one unit's banded Cholesky factor and solution vectors. */
+int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_oversample,
+                                    int32_t precision, size_t* slot_bytes,
+                                    size_t* recommended_bytes);
+
+/* Simultaneous local upscaling of S samples: for every (sample, cell) unit
+ * solve the four cell problems of Eq. MsFEB on the fine mesh (bilinear
+ * boundary data on the patch = the cell enlarged by oversample[cell] fine
+ * elements on each side and clipped to the domain, Remark on oversampling),
+ * recombine the patch solutions into the basis that is nodal at the cell
+ * corners, and form the upscaled stiffness and load of Eq. stiffness_local
+ * on the cell.
+ *   a            device [S][nf][nf] float64 coefficient
+ *   oversample   device [nc*nc] int8 layer widths, or NULL for none; every
+ *                entry must lie in [0, max_oversample] (units with an
+ *                out-of-range entry get status EINVAL and NaN outputs)
+ *   precision    STOMSFEM_FP64: everything in FP64.
+ *                STOMSFEM_FP32_REFINED: FP32 factor and solves, FP64
+ *                  residuals (refine_iters steps of iterative refinement)
+ *                  and FP64 K_e/b_e accumulation.
+ *                STOMSFEM_FP32: FP32 throughout, results stored as FP64.
+ *   Ke           device [S][nc*nc][10] float64 (packed upper triangle)
+ *   be           device [S][nc*nc][4] float64
+ *   phi          device [S][nc*nc][4][(rho+1)^2] float64 basis on the cell
+ *                nodes, or NULL
+ *   unit_status  device [S][nc*nc] int32 or NULL: 0 on success; k+1 when
+ *                pivot k of the unit's patch matrix was not positive; -1
+ *                for an oversample entry outside [0, max_oversample];
+ *                STOMSFEM_ENOTSPD when the corner matrix of the
+ *                oversampling recombination is singular.  Failed units
+ *                get NaN outputs.
+ *   workspace    device scratch of workspace_bytes (>= one slot per warp
+ *                launched; more slots = more units in flight)
+ * Errors: EINVAL (sizes, pointers, precision, bandwidth > 64), ENOMEM
+ * (workspace below 4 slots), ECUDA. */
+int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                     int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
+                     double* Ke, double* be, double* phi, int32_t* unit_status, void* workspace,
+                     size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* Scratch needed by stomsfem_coarse_solve. */
+int stomsfem_coarse_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
+
+/* Coarse assembly and solve (Eq. upscaleSUF) with zero Dirichlet data on
+ * the boundary nodes, plus the running Monte Carlo moments of Eq.
+ * MCestimate.  Ke [S][nc*nc][10], be [S][nc*nc][4] device float64;
+ * u device [S][(nc+1)^2] float64 (boundary entries 0).  mean, m2 device
+ * [(nc+1)^2] float64 and count device [1] float64 are running accumulators
+ * (all zero before the first batch), merged with this batch's moments:
+ * mean = M[u], m2 = sum (u - mean)^2 over all samples so far, so the MC
+ * variance is m2/count.  mean/m2/count may all be NULL to skip the
+ * moments.  Errors: EINVAL, ENOMEM, ECUDA; a sample whose coarse matrix
+ * is not positive definite gets NaN in u. */
+int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const double* be,
+                          int32_t S, double* u, double* mean, double* m2, double* count,
+                          void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOMSFEM_H */

@@ -1,0 +1,72 @@
+"""ctypes view of libstomsfem.so (the C ABI declared in include/stomsfem.h).
+
+No fallback: if the library is missing, importing a binding that needs it
+raises; nothing in this package computes any step of the method in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTSPD, ETIMEOUT, EVERSION = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32_REFINED, FP32 = 0, 1, 2
+FIELD_EXP, FIELD_EXP_SIGMOID = 0, 1
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nf", ctypes.c_int32), ("nc", ctypes.c_int32), ("f", ctypes.c_double)]
+
+
+class Field(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32),
+                ("width", ctypes.c_double), ("scale", ctypes.c_double),
+                ("contrast_log", ctypes.c_double), ("gain", ctypes.c_double)]
+
+
+class StomsfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("stomsfem error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_SZ = ctypes.c_size_t
+_SIG = {
+    "stomsfem_version": (ctypes.c_char_p, []),
+    "stomsfem_last_error": (ctypes.c_char_p, []),
+    "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
+    "stomsfem_upscale_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I,
+                                                        ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "stomsfem_upscale": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _P, _P, _P, _P,
+                                        _P, _SZ, _P]),
+    "stomsfem_coarse_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_coarse_solve": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P,
+                                             _SZ, _P]),
+}
+
+
+def lib(path: str | None = None):
+    """Load (once) and return the library handle; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        p = path or LIB
+        if not os.path.exists(p):
+            raise RuntimeError("libstomsfem.so not built (%s); run __graft_entry__.build()" % p)
+        L = ctypes.CDLL(p)
+        for name, (res, args) in _SIG.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != OK:
+        raise StomsfemError(rc, lib().stomsfem_last_error().decode(errors="replace"))
+    return rc

@@ -1,0 +1,107 @@
+"""Python binding of the C ABI, one function per entry point, same names.
+
+Only argument marshalling happens here: shapes, dtypes and devices of the
+torch tensors are checked, raw device pointers and the current CUDA
+stream are passed to the library, and its status is turned into an
+exception.  Every step of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+from ._lib import FP32, FP32_REFINED, FP64, FIELD_EXP, FIELD_EXP_SIGMOID, Grid, Field  # noqa: F401
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def grid(nf, nc, f=1.0):
+    return Grid(int(nf), int(nc), float(f))
+
+
+def field(kind, nbx, nby, width, scale=1.0, contrast_log=0.0, gain=1.0):
+    return Field(int(kind), int(nbx), int(nby), float(width), float(scale), float(contrast_log),
+                 float(gain))
+
+
+def field_from_dict(d):
+    return field(d["kind"], d["nbx"], d["nby"], d["width"], d.get("scale", 1.0),
+                 d.get("contrast_log", 0.0), d.get("gain", 1.0))
+
+
+def stomsfem_version():
+    return L.lib().stomsfem_version().decode()
+
+
+def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
+    S = xi.shape[0]
+    L.check(L.lib().stomsfem_sample_coef(ctypes.byref(g), ctypes.byref(fld),
+                                         _dev(xi, torch.float64, (S, fld.nbx * fld.nby), "xi"), S,
+                                         _dev(a, torch.float64, (S, g.nf, g.nf), "a"), _stream(stream)))
+
+
+def stomsfem_upscale_workspace_size(g: Grid, max_oversample=0, precision=FP64):
+    sb, rb = ctypes.c_size_t(), ctypes.c_size_t()
+    L.check(L.lib().stomsfem_upscale_workspace_size(ctypes.byref(g), int(max_oversample),
+                                                    int(precision), ctypes.byref(sb), ctypes.byref(rb)))
+    return sb.value, rb.value
+
+
+def stomsfem_upscale(g: Grid, a, Ke, be, oversample=None, max_oversample=0, precision=FP64,
+                     refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None):
+    S = a.shape[0]
+    ncell = g.nc * g.nc
+    rho = g.nf // g.nc
+    if workspace is None:
+        _, rb = stomsfem_upscale_workspace_size(g, max_oversample if oversample is not None else 0,
+                                                precision)
+        workspace = torch.empty(rb, dtype=torch.uint8, device=a.device)
+    L.check(L.lib().stomsfem_upscale(
+        ctypes.byref(g), _dev(a, torch.float64, (S, g.nf, g.nf), "a"),
+        _dev(oversample, torch.int8, (ncell,), "oversample"), int(max_oversample), S, int(precision),
+        int(refine_iters), _dev(Ke, torch.float64, (S, ncell, 10), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
+        _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
+def stomsfem_coarse_workspace_size(g: Grid, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_coarse_workspace_size(ctypes.byref(g), int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_coarse_solve(g: Grid, Ke, be, u, mean=None, m2=None, count=None, workspace=None,
+                          stream=None):
+    S = Ke.shape[0]
+    ncell = g.nc * g.nc
+    nn = (g.nc + 1) ** 2
+    if workspace is None:
+        workspace = torch.empty(stomsfem_coarse_workspace_size(g, S), dtype=torch.uint8,
+                                device=Ke.device)
+    L.check(L.lib().stomsfem_coarse_solve(
+        ctypes.byref(g), _dev(Ke, torch.float64, (S, ncell, 10), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"), S, _dev(u, torch.float64, (S, nn), "u"),
+        _dev(mean, torch.float64, (nn,), "mean"), _dev(m2, torch.float64, (nn,), "m2"),
+        _dev(count, torch.float64, (1,), "count"), _dev(workspace, torch.uint8, None, "workspace"),
+        workspace.numel(), _stream(stream)))

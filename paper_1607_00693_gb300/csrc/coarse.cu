@@ -1,0 +1,156 @@
+// Coarse assembly and solve (Eq. upscaleSUF) and Monte Carlo moments
+// (Eq. MCestimate).  One warp per sample: the coarse matrix over the
+// (nc-1)^2 interior coarse nodes is again a 9-point-stencil SPD matrix,
+// assembled row by row from the K_e of the four cells around each node
+// and factorised with the same warp banded Cholesky as the cell problems.
+#include "band_warp.cuh"
+#include "common.cuh"
+
+namespace stomsfem {
+
+constexpr int kCoarseWarps = 4;
+
+__device__ __forceinline__ int kidx(int l, int lp) {
+  // packed upper-triangle index of the symmetric 4x4 entry (l, lp)
+  if (l > lp) { const int t = l; l = lp; lp = t; }
+  return l * 4 - (l * (l - 1)) / 2 + (lp - l);
+}
+
+struct CoarseGen {
+  const double* Ke;  // this sample [nc*nc][10]
+  const double* be;  // [nc*nc][4]
+  int nc, mi;
+  __device__ __forceinline__ double K(int cx, int cy, int l, int lp) const {
+    return Ke[(size_t)(cy * nc + cx) * 10 + kidx(l, lp)];
+  }
+  template <typename T>
+  __device__ __forceinline__ T coef(int r, int d) const {
+    if (d != 0 && d != 1 && d != mi - 1 && d != mi && d != mi + 1) return T(0);
+    const int J = r / mi + 1, I = r - (J - 1) * mi + 1;
+    double v = 0.0;
+    // cells around node (I, J): SW (I-1,J-1) node=NE(2); SE (I,J-1) node=NW(3);
+    // NE (I,J) node=SW(0); NW (I-1,J) node=SE(1)
+    if (d == 0) v += K(I - 1, J - 1, 2, 2) + K(I, J - 1, 3, 3) + K(I, J, 0, 0) + K(I - 1, J, 1, 1);
+    if (d == 1 && I > 1) v += K(I - 1, J - 1, 2, 3) + K(I - 1, J, 1, 0);
+    if (d == mi && J > 1) v += K(I - 1, J - 1, 2, 1) + K(I, J - 1, 3, 0);
+    if (d == mi + 1 && I > 1 && J > 1) v += K(I - 1, J - 1, 2, 0);
+    if (d == mi - 1 && I < mi && J > 1) v += K(I, J - 1, 3, 1);
+    return (T)v;
+  }
+  template <typename T>
+  __device__ __forceinline__ T rhs(int r, int) const {
+    const int J = r / mi + 1, I = r - (J - 1) * mi + 1;
+    return (T)(be[(size_t)((J - 1) * nc + I - 1) * 4 + 2] + be[(size_t)((J - 1) * nc + I) * 4 + 3] +
+               be[(size_t)(J * nc + I) * 4 + 0] + be[(size_t)(J * nc + I - 1) * 4 + 1]);
+  }
+};
+
+__global__ void __launch_bounds__(kCoarseWarps * 32)
+coarse_kernel(int nc, int S, const double* __restrict__ Ke, const double* __restrict__ be,
+              double* __restrict__ u, unsigned char* ws, size_t slot_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int mi = nc - 1, n = mi * mi, b = nc;
+  BandRing<double, 1> ring = make_ring<double, 1>(smem + wib * ring_bytes<double, 1>(b), b);
+  const int gw = blockIdx.x * kCoarseWarps + wib, nw = gridDim.x * kCoarseWarps;
+  unsigned char* slot = ws + (size_t)gw * slot_bytes;
+  double* Lg = reinterpret_cast<double*>(slot);
+  double* x = reinterpret_cast<double*>(slot + (((size_t)(n > 0 ? n : 1) * (b + 1) * 8 + 255) & ~size_t(255)));
+  const int NN = nc + 1;
+  for (int s = gw; s < S; s += nw) {
+    CoarseGen gen{Ke + (size_t)s * nc * nc * 10, be + (size_t)s * nc * nc * 4, nc, mi};
+    int fail = -1;
+    if (n > 0) {
+      fail = band_factor_forward<double, 1>(gen, n, b, ring, Lg, x, lane);
+      if (fail < 0) band_backward<double, 1>(n, b, ring.R, Lg, x, ring.rhs, lane);
+    }
+    __syncwarp();
+    double* us = u + (size_t)s * NN * NN;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    for (int q = lane; q < NN * NN; q += 32) {
+      const int I = q % NN, J = q / NN;
+      double v = 0.0;
+      if (I > 0 && J > 0 && I < nc && J < nc) v = fail < 0 ? x[(J - 1) * mi + (I - 1)] : nanv;
+      us[q] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// Merge this batch's moments into the running ones (pairwise update of
+// Chan, Golub and LeVeque): batch mean/M2 two-pass, then combine.
+__global__ void moments_kernel(int nn, int S, const double* __restrict__ u, double* mean, double* m2,
+                               const double* count) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  double mb = 0.0;
+  for (int s = 0; s < S; ++s) mb += u[(size_t)s * nn + q];
+  mb /= S;
+  double M2b = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const double d = u[(size_t)s * nn + q] - mb;
+    M2b += d * d;
+  }
+  const double na = count[0], nb = (double)S, nt = na + nb;
+  const double delta = mb - mean[q];
+  mean[q] = mean[q] + delta * (nb / nt);
+  m2[q] = m2[q] + M2b + delta * delta * (na * nb / nt);
+}
+
+__global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
+
+static size_t coarse_slot_bytes(int nc) {
+  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1, b = nc;
+  return (((size_t)n * (b + 1) * 8 + 255) & ~size_t(255)) + (((size_t)n * 8 + 255) & ~size_t(255));
+}
+
+}  // namespace stomsfem
+
+using namespace stomsfem;
+
+extern "C" int stomsfem_coarse_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes) {
+  if (!grid || grid->nc <= 0 || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  const int sms = device_sm_count();
+  long long slots = (long long)(sms > 0 ? sms : 152) * 8;
+  if (slots > S) slots = S;
+  if (slots < kCoarseWarps) slots = kCoarseWarps;
+  *bytes = coarse_slot_bytes(grid->nc) * (size_t)slots;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const double* be,
+                                     int32_t S, double* u, double* mean, double* m2, double* count,
+                                     void* workspace, size_t workspace_bytes,
+                                     stomsfem_stream_t stream) {
+  if (!grid || grid->nc <= 0) return set_error(STOMSFEM_EINVAL, "bad grid");
+  if (grid->nc > 64) return set_error(STOMSFEM_EINVAL, "nc %d > 64 (coarse bandwidth limit)", grid->nc);
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (S == 0) return STOMSFEM_OK;
+  if (!Ke || !be || !u || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  const bool mom = mean || m2 || count;
+  if (mom && !(mean && m2 && count))
+    return set_error(STOMSFEM_EINVAL, "mean, m2 and count must be given together");
+  const size_t sb = coarse_slot_bytes(grid->nc);
+  long long slots = (long long)(workspace_bytes / sb);
+  if (slots < kCoarseWarps)
+    return set_error(STOMSFEM_ENOMEM, "coarse workspace %zu < %d slots of %zu", workspace_bytes,
+                     kCoarseWarps, sb);
+  long long blocks = slots / kCoarseWarps;
+  const long long need = ((long long)S + kCoarseWarps - 1) / kCoarseWarps;
+  if (blocks > need) blocks = need;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = ring_bytes<double, 1>(grid->nc) * kCoarseWarps;
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+  coarse_kernel<<<(unsigned)blocks, kCoarseWarps * 32, smem, st>>>(
+      grid->nc, S, Ke, be, u, static_cast<unsigned char*>(workspace), sb);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  if (mom) {
+    const int nn = (grid->nc + 1) * (grid->nc + 1);
+    moments_kernel<<<(nn + 127) / 128, 128, 0, st>>>(nn, S, u, mean, m2, count);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+    count_kernel<<<1, 1, 0, st>>>(count, S);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+  }
+  return STOMSFEM_OK;
+}

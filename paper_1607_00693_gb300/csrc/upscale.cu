@@ -1,0 +1,484 @@
+// Simultaneous local upscaling: one warp per (sample, coarse cell) unit.
+//
+// Per unit (Eq. MsFEB, Remark on oversampling, Eq. stiffness_local):
+//   1. patch = cell enlarged by o fine elements per side, clipped to [0,1]^2;
+//   2. cell problems: psi_l = p_l + psi0_l with p_l the bilinear nodal
+//      function of the patch rectangle and psi0_l vanishing on the patch
+//      boundary, A_II psi0_l = -(A p_l)_I for l = SW, SE, NE (the NW one is
+//      1 - the others: the four p_l sum to 1 and A 1 = 0); the 9-point Q1
+//      matrix rows are generated from a on the fly as the banded Cholesky
+//      sweep needs them (band_warp.cuh);
+//   3. optional FP64 iterative refinement of the FP32 solution;
+//   4. M_jk = a_cell(psi_j, psi_k), m_j = int_cell f psi_j over the cell's
+//      fine elements; oversampling recombination phi = D psi with
+//      D = C^{-1}, C_jk = psi_j(cell corner k); K_e = D M D^T, b_e = D m.
+#include <cstdio>
+
+#include "band_warp.cuh"
+#include "common.cuh"
+
+namespace stomsfem {
+
+constexpr int kUpscaleWarps = 4;   // warps (units in flight) per block
+constexpr int kMaxBand = 64;       // half bandwidth limit (mx + 1)
+
+struct UnitGeom {
+  int x0, y0, Nx, Ny, mx, my, n, b;
+  int cx0, cy0;  // cell origin in patch-local node coordinates
+};
+
+__device__ inline UnitGeom unit_geom(int nf, int rho, int cx, int cy, int o) {
+  UnitGeom g;
+  const int x0 = max(0, cx * rho - o), x1 = min(nf, (cx + 1) * rho + o);
+  const int y0 = max(0, cy * rho - o), y1 = min(nf, (cy + 1) * rho + o);
+  g.x0 = x0;
+  g.y0 = y0;
+  g.Nx = x1 - x0;
+  g.Ny = y1 - y0;
+  g.mx = g.Nx - 1;
+  g.my = g.Ny - 1;
+  g.n = g.mx * g.my;
+  g.b = g.mx + 1;
+  g.cx0 = cx * rho - x0;
+  g.cy0 = cy * rho - y0;
+  return g;
+}
+
+// Row generator of the patch system: matrix rows from a, right-hand sides
+// -(A p_l) at interior nodes in closed form (differences of a only, so the
+// small right-hand sides keep their relative accuracy in FP32).
+struct PatchGen {
+  const double* a;  // this sample's coefficient [nf][nf]
+  int nf, x0, y0, Nx, Ny, mx;
+
+  __device__ __forceinline__ double ael(int ex, int ey) const {
+    return __ldg(a + (size_t)(y0 + ey) * nf + (x0 + ex));
+  }
+  __device__ __forceinline__ void node(int r, int& i, int& j) const {
+    j = r / mx + 1;
+    i = r - (j - 1) * mx + 1;
+  }
+  template <typename T>
+  __device__ __forceinline__ T coef(int r, int d) const {
+    if (d != 0 && d != 1 && d != mx - 1 && d != mx && d != mx + 1) return T(0);
+    int i, j;
+    node(r, i, j);
+    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
+    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
+    T v = T(0);
+    if (d == 0) v += (T(2) / T(3)) * (aSW + aSE + aNE + aNW);
+    if (d == 1 && i > 1) v -= (aSW + aNW) / T(6);                    // west
+    if (d == mx && j > 1) v -= (aSW + aSE) / T(6);                   // south
+    if (d == mx + 1 && i > 1 && j > 1) v -= aSW / T(3);              // south-west
+    if (d == mx - 1 && i < mx && j > 1) v -= aSE / T(3);             // south-east
+    return v;
+  }
+  // (A X), (A Y), (A XY) at interior node (i, j) for the patch coordinates
+  // X = i/Nx, Y = j/Ny; then -(A p_l) for p_SW = 1-X-Y+XY, p_SE = X-XY, p_NE = XY.
+  template <typename T>
+  __device__ __forceinline__ void ap(int i, int j, T& AX, T& AY, T& AXY) const {
+    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
+    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
+    AX = ((aSW + aNW) - (aSE + aNE)) / (T(2) * (T)Nx);
+    AY = ((aSW + aSE) - (aNW + aNE)) / (T(2) * (T)Ny);
+    const T Xc = (T)i / (T)Nx, Yc = (T)j / (T)Ny;
+    AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) / (T(3) * (T)Nx * (T)Ny);
+  }
+  template <typename T>
+  __device__ __forceinline__ T rhs(int r, int l) const {
+    int i, j;
+    node(r, i, j);
+    T AX, AY, AXY;
+    ap<T>(i, j, AX, AY, AXY);
+    if (l == 0) return AX + AY - AXY;
+    if (l == 1) return AXY - AX;
+    return -AXY;
+  }
+};
+
+// Right-hand side of a refinement step: the FP64 residual
+// -(A (p_l + psi0_l)) at interior nodes, psi0 = 0 on the patch boundary.
+struct ResidualGen {
+  PatchGen pg;
+  const double* psi0;  // [n][3]
+  __device__ __forceinline__ double psi(int i, int j, int l) const {
+    if (i <= 0 || j <= 0 || i > pg.mx || j > pg.Ny - 1) return 0.0;
+    return psi0[((size_t)(j - 1) * pg.mx + (i - 1)) * 3 + l];
+  }
+  template <typename T>
+  __device__ __forceinline__ T coef(int, int) const { return T(0); }
+  template <typename T>
+  __device__ __forceinline__ T rhs(int r, int l) const {
+    int i, j;
+    pg.node(r, i, j);
+    const double aSW = pg.ael(i - 1, j - 1), aSE = pg.ael(i, j - 1);
+    const double aNE = pg.ael(i, j), aNW = pg.ael(i - 1, j);
+    double AX, AY, AXY;
+    pg.ap<double>(i, j, AX, AY, AXY);
+    double r0 = (l == 0) ? AX + AY - AXY : (l == 1 ? AXY - AX : -AXY);
+    // subtract A psi0 with the full 9-point stencil
+    const double c = (2.0 / 3.0) * (aSW + aSE + aNE + aNW);
+    double s = c * psi(i, j, l);
+    s -= (aSW + aNW) / 6.0 * psi(i - 1, j, l);
+    s -= (aSE + aNE) / 6.0 * psi(i + 1, j, l);
+    s -= (aSW + aSE) / 6.0 * psi(i, j - 1, l);
+    s -= (aNE + aNW) / 6.0 * psi(i, j + 1, l);
+    s -= aSW / 3.0 * psi(i - 1, j - 1, l);
+    s -= aSE / 3.0 * psi(i + 1, j - 1, l);
+    s -= aNE / 3.0 * psi(i + 1, j + 1, l);
+    s -= aNW / 3.0 * psi(i - 1, j + 1, l);
+    return (T)(r0 - s);
+  }
+};
+
+// psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction).
+template <typename T>
+__device__ __forceinline__ void psi_at(const UnitGeom& g, const double* psi0, int i, int j, T out[3]) {
+  const T X = (T)i / (T)g.Nx, Y = (T)j / (T)g.Ny;
+  out[0] = (T(1) - X) * (T(1) - Y);
+  out[1] = X * (T(1) - Y);
+  out[2] = X * Y;
+  if (i > 0 && j > 0 && i < g.Nx && j < g.Ny) {
+    const double* p = psi0 + ((size_t)(j - 1) * g.mx + (i - 1)) * 3;
+    out[0] += (T)p[0];
+    out[1] += (T)p[1];
+    out[2] += (T)p[2];
+  }
+}
+
+// 4x4 inverse, Gauss-Jordan with partial pivoting (FP64).  Returns false if singular.
+__device__ inline bool inv4(double C[4][4], double D[4][4]) {
+  double M[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? C[r][c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < 8; ++k) {
+        const double t = M[c][k];
+        M[c][k] = M[piv][k];
+        M[piv][k] = t;
+      }
+    const double dinv = 1.0 / M[c][c];
+    for (int k = 0; k < 8; ++k) M[c][k] *= dinv;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+        for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) D[r][c] = M[r][c + 4];
+  return true;
+}
+
+struct UpscaleArgs {
+  const double* a;
+  const int8_t* oversample;
+  int nf, nc, rho, max_o, S;
+  double f;
+  int refine;
+  double* Ke;
+  double* be;
+  double* phi;
+  int32_t* status;
+  unsigned char* ws;
+  size_t slot_bytes;
+  int bmax, nmax;
+  long long units;
+};
+
+// TK: factor/solve type; TA: type of the K_e/b_e accumulation.
+template <typename TK, typename TA>
+__global__ void __launch_bounds__(kUpscaleWarps * 32)
+upscale_kernel(UpscaleArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const size_t ring_sz = ring_bytes<TK, 3>(A.bmax);
+  BandRing<TK, 3> ring = make_ring<TK, 3>(smem + wib * ring_sz, A.bmax);
+  const long long gw = (long long)blockIdx.x * kUpscaleWarps + wib;
+  const long long nw = (long long)gridDim.x * kUpscaleWarps;
+  unsigned char* slot = A.ws + (size_t)gw * A.slot_bytes;
+  TK* Lg = reinterpret_cast<TK*>(slot);
+  const size_t l_bytes = ((size_t)A.nmax * (A.bmax + 1) * sizeof(TK) + 255) & ~size_t(255);
+  double* psi0 = reinterpret_cast<double*>(slot + l_bytes);
+  double* corr = psi0 + (size_t)A.nmax * 3;
+  const int ncell = A.nc * A.nc;
+  const int CN = (A.rho + 1) * (A.rho + 1);
+
+  for (long long u = gw; u < A.units; u += nw) {
+    const int s = (int)(u / ncell);
+    const int cell = (int)(u % ncell);
+    const int cx = cell % A.nc, cy = cell / A.nc;
+    int o = A.oversample ? (int)A.oversample[cell] : 0;
+    double* Ke = A.Ke + (size_t)u * 10;
+    double* be = A.be + (size_t)u * 4;
+    if (o < 0 || o > A.max_o) {
+      if (lane < 10) Ke[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane < 4) be[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane == 0 && A.status) A.status[u] = -1;
+      continue;
+    }
+    const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
+    PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
+    int fail = -1;
+    if (g.n > 0) {
+      fail = band_factor_forward<TK, 3>(pg, g.n, g.b, ring, Lg, psi0, lane);
+      if (fail < 0) {
+        band_backward<TK, 3>(g.n, g.b, ring.R, Lg, psi0, ring.rhs, lane);
+        // FP64 iterative refinement with the FP32 factor
+        for (int it = 0; it < A.refine; ++it) {
+          __syncwarp();
+          ResidualGen rg{pg, psi0};
+          band_forward_stored<TK, 3>(rg, g.n, g.b, ring, Lg, corr, lane);
+          band_backward<TK, 3>(g.n, g.b, ring.R, Lg, corr, ring.rhs, lane);
+          __syncwarp();
+          for (int k = lane; k < g.n * 3; k += 32) psi0[k] += corr[k];
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    if (fail >= 0) {
+      if (lane < 10) Ke[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane < 4) be[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane == 0 && A.status) A.status[u] = fail + 1;
+      continue;
+    }
+    // M_jk = a_cell(psi_j, psi_k) (j, k < 3) by the edge/diagonal difference
+    // form of the Q1 element energy: (1/6)[sum_edges du dv + 2 sum_diags du dv];
+    // m_j = (h^2/4) f sum over element corners of psi_j.
+    TA M[6] = {0, 0, 0, 0, 0, 0};
+    TA m[3] = {0, 0, 0};
+    for (int e = lane; e < A.rho * A.rho; e += 32) {
+      const int ex = e % A.rho, ey = e / A.rho;
+      const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
+      TA c0[3], c1[3], c2[3], c3[3];
+      psi_at<TA>(g, psi0, i0, j0, c0);
+      psi_at<TA>(g, psi0, i0 + 1, j0, c1);
+      psi_at<TA>(g, psi0, i0 + 1, j0 + 1, c2);
+      psi_at<TA>(g, psi0, i0, j0 + 1, c3);
+      const TA ae = (TA)pg.ael(i0, j0);
+      TA dd[3][6];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        dd[l][0] = c0[l] - c1[l];
+        dd[l][1] = c1[l] - c2[l];
+        dd[l][2] = c2[l] - c3[l];
+        dd[l][3] = c3[l] - c0[l];
+        dd[l][4] = c0[l] - c2[l];
+        dd[l][5] = c1[l] - c3[l];
+        m[l] += (c0[l] + c1[l]) + (c2[l] + c3[l]);
+      }
+      int q = 0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int lp = l; lp < 3; ++lp) {
+          const TA v = dd[l][0] * dd[lp][0] + dd[l][1] * dd[lp][1] + dd[l][2] * dd[lp][2] +
+                       dd[l][3] * dd[lp][3] + TA(2) * (dd[l][4] * dd[lp][4] + dd[l][5] * dd[lp][5]);
+          M[q++] += ae * v;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M[q] = warp_sum(M[q]);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) m[l] = warp_sum(m[l]);
+
+    // recombination matrix D = C^{-1}, C_jk = psi_j(cell corner k)
+    double D[4][4];
+    const bool patch_is_cell = (g.cx0 == 0 && g.cy0 == 0 && g.Nx == A.rho && g.Ny == A.rho);
+    bool ok = true;
+    if (patch_is_cell) {
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) D[r][c] = (r == c) ? 1.0 : 0.0;
+    } else {
+      const int ci[4] = {g.cx0, g.cx0 + A.rho, g.cx0 + A.rho, g.cx0};
+      const int cj[4] = {g.cy0, g.cy0, g.cy0 + A.rho, g.cy0 + A.rho};
+      double C[4][4];
+      for (int k = 0; k < 4; ++k) {
+        double v[3];
+        psi_at<double>(g, psi0, ci[k], cj[k], v);
+        C[0][k] = v[0];
+        C[1][k] = v[1];
+        C[2][k] = v[2];
+        C[3][k] = 1.0 - v[0] - v[1] - v[2];
+      }
+      ok = inv4(C, D);
+    }
+    if (lane == 0) {
+      const double h = 1.0 / A.nf;
+      double MM[4][4];
+      const double M6[6] = {(double)M[0], (double)M[1], (double)M[2],
+                            (double)M[3], (double)M[4], (double)M[5]};
+      MM[0][0] = M6[0]; MM[0][1] = MM[1][0] = M6[1]; MM[0][2] = MM[2][0] = M6[2];
+      MM[1][1] = M6[3]; MM[1][2] = MM[2][1] = M6[4]; MM[2][2] = M6[5];
+      for (int r = 0; r < 3; ++r) {
+        MM[r][3] = MM[3][r] = -(MM[r][0] + MM[r][1] + MM[r][2]);
+      }
+      MM[3][3] = -(MM[0][3] + MM[1][3] + MM[2][3]);
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) MM[r][c] /= 6.0;
+      const double fq = A.f * h * h / 4.0;
+      double mv[4] = {fq * (double)m[0], fq * (double)m[1], fq * (double)m[2], 0.0};
+      const double H = (double)A.rho * h;
+      mv[3] = A.f * H * H - (mv[0] + mv[1] + mv[2]);
+      // K = D MM D^T, b = D mv
+      double T4[4][4];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+          double t = 0.0;
+          for (int k = 0; k < 4; ++k) t += D[r][k] * MM[k][c];
+          T4[r][c] = t;
+        }
+      int q = 0;
+      for (int r = 0; r < 4; ++r)
+        for (int c = r; c < 4; ++c) {
+          double t = 0.0;
+          for (int k = 0; k < 4; ++k) t += T4[r][k] * D[c][k];
+          Ke[q++] = ok ? t : __longlong_as_double(0x7ff8000000000000ll);
+        }
+      for (int r = 0; r < 4; ++r) {
+        double t = 0.0;
+        for (int k = 0; k < 4; ++k) t += D[r][k] * mv[k];
+        be[r] = ok ? t : __longlong_as_double(0x7ff8000000000000ll);
+      }
+      if (A.status) A.status[u] = ok ? 0 : STOMSFEM_ENOTSPD;
+    }
+    if (A.phi) {
+      double* ph = A.phi + (size_t)u * 4 * CN;
+      for (int q = lane; q < CN; q += 32) {
+        const int i = g.cx0 + q % (A.rho + 1), j = g.cy0 + q / (A.rho + 1);
+        double v[3];
+        psi_at<double>(g, psi0, i, j, v);
+        const double v4[4] = {v[0], v[1], v[2], 1.0 - v[0] - v[1] - v[2]};
+        for (int l = 0; l < 4; ++l) {
+          double t = 0.0;
+          for (int k = 0; k < 4; ++k) t += D[l][k] * v4[k];
+          ph[(size_t)l * CN + q] = t;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+static size_t slot_bytes_for(int nmax, int bmax, int precision) {
+  const size_t tk = precision == STOMSFEM_FP64 ? 8 : 4;
+  const size_t l_bytes = ((size_t)nmax * (bmax + 1) * tk + 255) & ~size_t(255);
+  return l_bytes + (((size_t)nmax * 3 * 8 * 2 + 255) & ~size_t(255));
+}
+
+static int validate_grid(const stomsfem_grid* g) {
+  if (!g) return set_error(STOMSFEM_EINVAL, "grid is NULL");
+  if (g->nf <= 0 || g->nc <= 0 || g->nf % g->nc != 0)
+    return set_error(STOMSFEM_EINVAL, "grid: need nf > 0, nc > 0, nf %% nc == 0 (nf=%d nc=%d)",
+                     g->nf, g->nc);
+  return STOMSFEM_OK;
+}
+
+static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax) {
+  const int rho = g->nf / g->nc;
+  const int side = rho + 2 * max_o < g->nf ? rho + 2 * max_o : g->nf;
+  const int m = side - 1;
+  *nmax = m * m > 1 ? m * m : 1;
+  *bmax = m + 1;
+}
+
+}  // namespace stomsfem
+
+using namespace stomsfem;
+
+extern "C" int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_oversample,
+                                               int32_t precision, size_t* slot_bytes,
+                                               size_t* recommended_bytes) {
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (max_oversample < 0 || precision < 0 || precision > 2)
+    return set_error(STOMSFEM_EINVAL, "bad max_oversample/precision");
+  int nmax, bmax;
+  patch_limits(grid, max_oversample, &nmax, &bmax);
+  const size_t sb = slot_bytes_for(nmax, bmax, precision);
+  if (slot_bytes) *slot_bytes = sb;
+  if (recommended_bytes) {
+    const int sms = device_sm_count();
+    *recommended_bytes = sb * (size_t)(sms > 0 ? sms : 152) * 16;
+  }
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
+                                const int8_t* oversample, int32_t max_oversample, int32_t S,
+                                int32_t precision, int32_t refine_iters, double* Ke, double* be,
+                                double* phi, int32_t* unit_status, void* workspace,
+                                size_t workspace_bytes, stomsfem_stream_t stream) {
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (precision < 0 || precision > 2) return set_error(STOMSFEM_EINVAL, "bad precision %d", precision);
+  if (max_oversample < 0) return set_error(STOMSFEM_EINVAL, "bad max_oversample");
+  if (refine_iters < 0 || refine_iters > 8)
+    return set_error(STOMSFEM_EINVAL, "refine_iters must be in [0, 8]");
+  if (S == 0) return STOMSFEM_OK;
+  if (!a || !Ke || !be || !workspace)
+    return set_error(STOMSFEM_EINVAL, "a, Ke, be and workspace must be device pointers");
+  const int mo = oversample ? max_oversample : 0;
+  int nmax, bmax;
+  patch_limits(grid, mo, &nmax, &bmax);
+  if (bmax > kMaxBand)
+    return set_error(STOMSFEM_EINVAL, "patch bandwidth %d exceeds %d (rho + 2*max_o too large)",
+                     bmax, kMaxBand);
+  const size_t sb = slot_bytes_for(nmax, bmax, precision);
+  const long long units = (long long)S * grid->nc * grid->nc;
+  long long slots = (long long)(workspace_bytes / sb);
+  if (slots < kUpscaleWarps)
+    return set_error(STOMSFEM_ENOMEM, "workspace %zu bytes < %d slots of %zu bytes", workspace_bytes,
+                     kUpscaleWarps, sb);
+  long long blocks = slots / kUpscaleWarps;
+  const long long need = (units + kUpscaleWarps - 1) / kUpscaleWarps;
+  if (blocks > need) blocks = need;
+  if (blocks > 1 << 20) blocks = 1 << 20;
+
+  UpscaleArgs A;
+  A.a = a;
+  A.oversample = oversample;
+  A.nf = grid->nf;
+  A.nc = grid->nc;
+  A.rho = grid->nf / grid->nc;
+  A.max_o = mo;
+  A.S = S;
+  A.f = grid->f;
+  A.refine = precision == STOMSFEM_FP32_REFINED ? refine_iters : 0;
+  A.Ke = Ke;
+  A.be = be;
+  A.phi = phi;
+  A.status = unit_status;
+  A.ws = static_cast<unsigned char*>(workspace);
+  A.slot_bytes = sb;
+  A.bmax = bmax;
+  A.nmax = nmax;
+  A.units = units;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == STOMSFEM_FP64) {
+    const size_t smem = ring_bytes<double, 3>(bmax) * kUpscaleWarps;
+    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<double, double>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    upscale_kernel<double, double><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
+  } else if (precision == STOMSFEM_FP32_REFINED) {
+    const size_t smem = ring_bytes<float, 3>(bmax) * kUpscaleWarps;
+    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<float, double>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    upscale_kernel<float, double><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
+  } else {
+    const size_t smem = ring_bytes<float, 3>(bmax) * kUpscaleWarps;
+    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<float, float>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    upscale_kernel<float, float><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
+  }
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
