@@ -1,0 +1,454 @@
+// Blocked warp-level banded SPD solver for 9-point-stencil matrices (one
+// warp per system).
+//
+// Right-looking banded Cholesky in column blocks of NB = 16.  For block K
+// (rows/columns [K, K+nb)) the warp
+//   1. factorises the tall panel [K, K+np) x [K, K+nb), np = nb + b: each
+//      lane holds up to RPL panel rows in registers; the block-row
+//      multipliers of each column step are broadcast through shared memory
+//      (128-bit loads); the NR right-hand sides ride along, which is the
+//      forward substitution;
+//   2. applies the rank-nb update to the trailing b x b window with 4 x 4
+//      register tiles (128-bit shared loads of the transposed panel);
+//   3. retires the block's rows and generates the next rows: a 9-point row
+//      has 5 entries at or left of the diagonal, at offsets 0, 1, mx-1, mx,
+//      mx+1, which the row generator returns in one call.
+// The matrix lives only as a window of RW >= NB + b band rows in shared
+// memory (RW a power of two; row r at slot r & (RW-1), entry A[r][r-d] at
+// column d).  Factor blocks go to global scratch as (NB + bmax) x NB
+// row-major tiles for the back substitution and refinement sweeps.
+//
+// Row generator interface:
+//   gen.row<T>(r, T e[5], T rhs[NR]) : band entries A[r][r], A[r][r-1],
+//       A[r][r-mx+1], A[r][r-mx], A[r][r-mx-1] (0 where absent) and rhs;
+//   gen.mx : offset of the south neighbour.
+#pragma once
+#include "common.cuh"
+
+namespace stomsfem {
+
+constexpr int kNB = 16;
+
+template <typename T>
+struct BlkSmem {
+  T* wnd;  // [RW][PW] band rows
+  T* tb;   // [NB + bmax][NB] factor block staging (aliases wnd)
+  T* pt;   // [NB][RP] trailing panel, p-major: pt[p*RP + (i - nb)] = L[K+i][K+p]
+  T* rhs;  // [RW][4]
+  T* lb;   // [NB] broadcast of the block-row multipliers
+  int RW, PW, RP;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline int blk_ring_rows(int bmax) {
+  int r = 16;
+  while (r < kNB + bmax) r <<= 1;
+  return r;
+}
+
+__host__ __device__ inline int blk_wnd_elems(int bmax) {
+  const int a = blk_ring_rows(bmax) * (bmax + 1), b = (kNB + bmax) * kNB;
+  return a > b ? a : b;
+}
+
+template <typename T>
+__host__ __device__ inline size_t blk_smem_bytes(int bmax) {
+  const int RW = blk_ring_rows(bmax), RP = (bmax + 3) & ~3;
+  return al16(sizeof(T) * blk_wnd_elems(bmax)) + al16(sizeof(T) * kNB * RP) +
+         al16(sizeof(T) * RW * 4) + al16(sizeof(T) * kNB);
+}
+
+template <typename T>
+__device__ inline BlkSmem<T> make_blk(unsigned char* base, int bmax) {
+  BlkSmem<T> s;
+  s.RW = blk_ring_rows(bmax);
+  s.PW = bmax + 1;
+  s.RP = (bmax + 3) & ~3;
+  size_t o = 0;
+  s.wnd = reinterpret_cast<T*>(base + o);
+  s.tb = s.wnd;
+  o += al16(sizeof(T) * blk_wnd_elems(bmax));
+  s.pt = reinterpret_cast<T*>(base + o);
+  o += al16(sizeof(T) * kNB * s.RP);
+  s.rhs = reinterpret_cast<T*>(base + o);
+  o += al16(sizeof(T) * s.RW * 4);
+  s.lb = reinterpret_cast<T*>(base + o);
+  return s;
+}
+
+__host__ __device__ inline size_t blk_factor_elems(int n, int bmax) {
+  return (size_t)((n + kNB - 1) / kNB) * (kNB + bmax) * kNB;
+}
+
+// The pivot and its reciprocal.
+__device__ __forceinline__ void pivot_of(float a, float& d, float& dinv) {
+  dinv = __frsqrt_rn(a);
+  d = a * dinv;
+}
+__device__ __forceinline__ void pivot_of(double a, double& d, double& dinv) {
+  d = sqrt(a);
+  dinv = 1.0 / d;
+}
+
+// Fill rows [r0, r1) of the window: zero band, then the generator's entries.
+template <typename T, int NR, class Gen>
+__device__ __forceinline__ void blk_fill(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int b,
+                                         int lane) {
+  const int msk = s.RW - 1;
+  for (int r = r0; r < r1; ++r) {
+    T* row = s.wnd + (r & msk) * s.PW;
+    for (int d = lane; d <= b; d += 32) row[d] = T(0);
+  }
+  __syncwarp();
+  const int mx = gen.mx;
+  for (int r = r0 + lane; r < r1; r += 32) {
+    T e[5], rh[NR];
+    gen.template row<T>(r, e, rh);
+    T* row = s.wnd + (r & msk) * s.PW;
+    row[0] += e[0];
+    if (r >= 1 && 1 <= b) row[1] += e[1];
+    if (mx - 1 >= 0 && r >= mx - 1 && mx - 1 <= b) row[mx - 1] += e[2];
+    if (r >= mx && mx <= b) row[mx] += e[3];
+    if (r >= mx + 1 && mx + 1 <= b) row[mx + 1] += e[4];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) s.rhs[(r & msk) * 4 + c] = rh[c];
+  }
+}
+
+// One column step j = J of the panel factorisation, then the next; the
+// recursion keeps every register-array index a compile-time constant.
+template <int J, typename T, int NR, int RPL>
+__device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T* lb, int lane,
+                                          int nb, int np, int K, int& fail) {
+  if constexpr (J < kNB) {
+    if (J < nb && fail < 0) {
+      const T dj = __shfl_sync(0xffffffffu, pr[0][J], J);
+      if (!(dj > T(0))) fail = K + J;
+      T d, dinv;
+      pivot_of(dj > T(0) ? dj : T(1), d, dinv);
+      T yj[NR];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) yj[c] = __shfl_sync(0xffffffffu, rh[0][c], J) * dinv;
+      T lq[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int i = lane + 32 * q;
+        const bool below = (i > J) && (i < np);
+        const T l = below ? pr[q][J] * dinv : T(0);
+        if (below) {
+          pr[q][J] = l;
+#pragma unroll
+          for (int c = 0; c < NR; ++c) rh[q][c] -= l * yj[c];
+        }
+        if (q == 0 && i == J) {
+          pr[0][J] = dinv;  // the factor blocks keep 1 / L_jj
+#pragma unroll
+          for (int c = 0; c < NR; ++c) rh[0][c] = yj[c];
+        }
+        lq[q] = l;
+      }
+      if (J + 1 < kNB) {
+        if (lane < kNB) lb[lane] = lq[0];
+        __syncwarp();
+        T Lv[kNB];
+#pragma unroll
+        for (int v = 0; v < kNB / 4; ++v) {
+          if (4 * v + 3 > J) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 f = reinterpret_cast<const float4*>(lb)[v];
+              Lv[4 * v] = f.x; Lv[4 * v + 1] = f.y; Lv[4 * v + 2] = f.z; Lv[4 * v + 3] = f.w;
+            } else {
+              const double2 f0 = reinterpret_cast<const double2*>(lb)[2 * v];
+              const double2 f1 = reinterpret_cast<const double2*>(lb)[2 * v + 1];
+              Lv[4 * v] = f0.x; Lv[4 * v + 1] = f0.y; Lv[4 * v + 2] = f1.x; Lv[4 * v + 3] = f1.y;
+            }
+          } else {
+            Lv[4 * v] = Lv[4 * v + 1] = Lv[4 * v + 2] = Lv[4 * v + 3] = T(0);
+          }
+        }
+#pragma unroll
+        for (int p = J + 1; p < kNB; ++p) {
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) pr[q][p] -= lq[q] * Lv[p];
+        }
+        __syncwarp();
+      }
+    }
+    panel_col<J + 1, T, NR, RPL>(pr, rh, lb, lane, nb, np, K, fail);
+  }
+}
+
+// Factorise (and forward-substitute NR rhs).  Lg: blocks of (NB+bmax) x NB;
+// yg[k*NR + c] receives the forward solution.  Returns -1 or the first
+// failing pivot index (warp-uniform).
+template <typename T, int NR, int RPL, class Gen, typename TS>
+__device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<T>& s,
+                          T* __restrict__ Lg, TS* __restrict__ yg, int lane) {
+  const int LBS = (kNB + bmax) * kNB;
+  const int msk = s.RW - 1;
+  int filled = 0;
+  for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
+    const int nb = min(kNB, n - K);
+    const int np = min(nb + b, n - K);
+    const int need = min(n, K + kNB + b);
+    if (filled < need) {
+      blk_fill<T, NR>(gen, s, filled, need, b, lane);
+      filled = need;
+    }
+    __syncwarp();
+    // ---- 1. panel factorisation in registers
+    T pr[RPL][kNB];
+    T rh[RPL][NR];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int i = lane + 32 * q;
+      const T* row = s.wnd + ((K + i) & msk) * s.PW;
+      const bool in = i < np;
+#pragma unroll
+      for (int p = 0; p < kNB; ++p) {
+        const int d = i - p;
+        pr[q][p] = (in && p < nb && d >= 0 && d <= b) ? row[d] : T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) rh[q][c] = in ? s.rhs[((K + i) & msk) * 4 + c] : T(0);
+    }
+    int fail = -1;
+    panel_col<0, T, NR, RPL>(pr, rh, s.lb, lane, nb, np, K, fail);
+    if (fail >= 0) return fail;
+    // ---- write the factor block, forward solution, trailing rhs and panel
+    T* Lb = Lg + (size_t)kb * LBS;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int i = lane + 32 * q;
+      if (i < np) {
+        T* dst = Lb + i * kNB;
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+          for (int v = 0; v < kNB / 4; ++v)
+            reinterpret_cast<float4*>(dst)[v] =
+                make_float4(4 * v <= i ? pr[q][4 * v] : 0.f, 4 * v + 1 <= i ? pr[q][4 * v + 1] : 0.f,
+                            4 * v + 2 <= i ? pr[q][4 * v + 2] : 0.f,
+                            4 * v + 3 <= i ? pr[q][4 * v + 3] : 0.f);
+        } else {
+#pragma unroll
+          for (int v = 0; v < kNB / 2; ++v)
+            reinterpret_cast<double2*>(dst)[v] = make_double2(
+                2 * v <= i ? pr[q][2 * v] : 0.0, 2 * v + 1 <= i ? pr[q][2 * v + 1] : 0.0);
+        }
+        if (i < nb) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yg[(size_t)(K + i) * NR + c] = (TS)rh[q][c];
+        } else {
+          const int slot = (K + i) & msk;
+#pragma unroll
+          for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[q][c];
+#pragma unroll
+          for (int p = 0; p < kNB; ++p) s.pt[p * s.RP + (i - nb)] = pr[q][p];
+        }
+      }
+    }
+    __syncwarp();
+    // ---- 2. trailing update A22 -= L21 L21^T with 4x4 register tiles
+    const int nt = np - nb;
+    if (nt > 0) {
+      const int T4 = (nt + 3) >> 2;
+      const int ntiles = T4 * (T4 + 1) / 2;
+      for (int t = lane; t < ntiles; t += 32) {
+        int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        if ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        if (ti * (ti + 1) / 2 > t) --ti;
+        const int tj = t - ti * (ti + 1) / 2;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+        // L[K+nb+ia][K+p] vanishes for nb + ia - p > b: rows of this tile
+        // need p >= nb + 4 ti - b only
+        const int p0 = max(0, nb + 4 * ti - b);
+        const T* col = s.pt + p0 * s.RP;
+        for (int p = p0; p < nb; ++p, col += s.RP) {
+          T va[4], vc[4];
+          if constexpr (sizeof(T) == 4) {
+            const float4 A4 = *reinterpret_cast<const float4*>(col + 4 * ti);
+            const float4 C4 = *reinterpret_cast<const float4*>(col + 4 * tj);
+            va[0] = A4.x; va[1] = A4.y; va[2] = A4.z; va[3] = A4.w;
+            vc[0] = C4.x; vc[1] = C4.y; vc[2] = C4.z; vc[3] = C4.w;
+          } else {
+            const double2 A0 = *reinterpret_cast<const double2*>(col + 4 * ti);
+            const double2 A1 = *reinterpret_cast<const double2*>(col + 4 * ti + 2);
+            const double2 C0 = *reinterpret_cast<const double2*>(col + 4 * tj);
+            const double2 C1 = *reinterpret_cast<const double2*>(col + 4 * tj + 2);
+            va[0] = A0.x; va[1] = A0.y; va[2] = A1.x; va[3] = A1.y;
+            vc[0] = C0.x; vc[1] = C0.y; vc[2] = C1.x; vc[3] = C1.y;
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] += va[a] * vc[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int ia = 4 * ti + a;
+          if (ia < nt) {
+            T* wr = s.wnd + ((K + nb + ia) & msk) * s.PW + ia - 4 * tj;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (4 * tj + c <= ia) wr[-c] -= acc[a][c];
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return -1;
+}
+
+// Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
+template <typename T, int NR, typename TS>
+__device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
+                             TS* __restrict__ xg, int lane) {
+  const int LBS = (kNB + bmax) * kNB;
+  const int nbk = (n + kNB - 1) / kNB;
+  const int msk = s.RW - 1;
+  T* xr = s.rhs;  // ring of solution rows
+  for (int kb = nbk - 1; kb >= 0; --kb) {
+    const int K = kb * kNB;
+    const int nb = min(kNB, n - K);
+    const int np = min(nb + b, n - K);
+    const T* Lb = Lg + (size_t)kb * LBS;
+    {  // stage the factor block in shared memory (128-bit copies)
+      const int nv = np * kNB * (int)sizeof(T) / 16;
+      const int4* src = reinterpret_cast<const int4*>(Lb);
+      int4* dst = reinterpret_cast<int4*>(s.tb);
+      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    }
+    __syncwarp();
+    // lane p < nb: yv = y_p - sum over the rows below the block of L[i][p] x_i
+    T yv[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) yv[c] = T(0);
+    if (lane < nb) {
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] = T(0);
+      for (int i = nb; i < np; ++i) {
+        const T l = s.tb[i * kNB + lane];
+        const T* xi = xr + ((K + i) & msk) * 4;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] += l * xi[c];
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) yv[c] = (T)xg[(size_t)(K + lane) * NR + c] - acc[c];
+    }
+    // in-block triangular solve, column oriented: x_p = yv_p / L_pp, then
+    // rows p'' < p subtract L[p][p''] x_p
+#pragma unroll
+    for (int p = kNB - 1; p >= 0; --p) {
+      if (p < nb) {
+        const T iLpp = s.tb[p * kNB + p];
+        T xp[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) xp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
+        if (lane < p) {
+          const T l = s.tb[p * kNB + lane];
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yv[c] -= l * xp[c];
+        }
+        if (lane == p) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yv[c] = xp[c];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < nb) {
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        xr[((K + lane) & msk) * 4 + c] = yv[c];
+        xg[(size_t)(K + lane) * NR + c] = (TS)yv[c];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Forward substitution with the stored factor: rg [n][NR] double holds the
+// right-hand side on entry and the forward solution y on exit.
+template <typename T, int NR, int RPL>
+__device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
+                                   const T* __restrict__ Lg, double* __restrict__ rg, int lane) {
+  const int LBS = (kNB + bmax) * kNB;
+  const int msk = s.RW - 1;
+  T* rr = s.rhs;  // ring of pending right-hand-side rows
+  int filled = 0;
+  for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
+    const int nb = min(kNB, n - K);
+    const int np = min(nb + b, n - K);
+    const int need = min(n, K + kNB + b);
+    for (int r = filled + lane; r < need; r += 32) {
+#pragma unroll
+      for (int c = 0; c < NR; ++c) rr[(r & msk) * 4 + c] = (T)rg[(size_t)r * NR + c];
+    }
+    filled = max(filled, need);
+    {
+      const T* Lb = Lg + (size_t)kb * LBS;
+      const int nv = np * kNB * (int)sizeof(T) / 16;
+      const int4* src = reinterpret_cast<const int4*>(Lb);
+      int4* dst = reinterpret_cast<int4*>(s.tb);
+      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    }
+    __syncwarp();
+    T yv[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) yv[c] = (lane < nb) ? rr[((K + lane) & msk) * 4 + c] : T(0);
+#pragma unroll
+    for (int p = 0; p < kNB; ++p) {
+      if (p < nb) {
+        const T iLpp = s.tb[p * kNB + p];
+        T yp[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) yp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
+        if (lane > p && lane < nb) {
+          const T l = s.tb[lane * kNB + p];
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yv[c] -= l * yp[c];
+        }
+        if (lane == p) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yv[c] = yp[c];
+        }
+      }
+    }
+    T* yb = s.pt;  // block solution broadcast
+    if (lane < nb) {
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        rg[(size_t)(K + lane) * NR + c] = (double)yv[c];
+        yb[lane * NR + c] = yv[c];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int i = lane + 32 * q;
+      if (i >= nb && i < np) {
+        T acc[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = T(0);
+        for (int p = 0; p < nb; ++p) {
+          const T l = s.tb[i * kNB + p];
+#pragma unroll
+          for (int c = 0; c < NR; ++c) acc[c] += l * yb[p * NR + c];
+        }
+        const int slot = (K + i) & msk;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) rr[slot * 4 + c] -= acc[c];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace stomsfem

@@ -7,14 +7,15 @@
 //      boundary, A_II psi0_l = -(A p_l)_I for l = SW, SE, NE (the NW one is
 //      1 - the others: the four p_l sum to 1 and A 1 = 0); the 9-point Q1
 //      matrix rows are generated from a on the fly as the banded Cholesky
-//      sweep needs them (band_warp.cuh);
+//      blocked banded Cholesky needs them (band_block.cuh);
 //   3. optional FP64 iterative refinement of the FP32 solution;
 //   4. M_jk = a_cell(psi_j, psi_k), m_j = int_cell f psi_j over the cell's
 //      fine elements; oversampling recombination phi = D psi with
 //      D = C^{-1}, C_jk = psi_j(cell corner k); K_e = D M D^T, b_e = D m.
 #include <cstdio>
+#include <type_traits>
 
-#include "band_warp.cuh"
+#include "band_block.cuh"
 #include "common.cuh"
 
 namespace stomsfem {
@@ -94,6 +95,28 @@ struct PatchGen {
     if (l == 1) return AXY - AX;
     return -AXY;
   }
+  // Whole row r: band entries at offsets 0, 1 (west), mx-1 (south-east),
+  // mx (south), mx+1 (south-west) and the three right-hand sides, from the
+  // four elements around the node.
+  template <typename T>
+  __device__ __forceinline__ void row(int r, T e[5], T rh[3]) const {
+    int i, j;
+    node(r, i, j);
+    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
+    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
+    e[0] = (T(2) / T(3)) * ((aSW + aSE) + (aNE + aNW));
+    e[1] = i > 1 ? -(aSW + aNW) / T(6) : T(0);
+    e[2] = (i < mx && j > 1) ? -aSE / T(3) : T(0);
+    e[3] = j > 1 ? -(aSW + aSE) / T(6) : T(0);
+    e[4] = (i > 1 && j > 1) ? -aSW / T(3) : T(0);
+    const T AX = ((aSW + aNW) - (aSE + aNE)) / (T(2) * (T)Nx);
+    const T AY = ((aSW + aSE) - (aNW + aNE)) / (T(2) * (T)Ny);
+    const T Xc = (T)i / (T)Nx, Yc = (T)j / (T)Ny;
+    const T AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) / (T(3) * (T)Nx * (T)Ny);
+    rh[0] = AX + AY - AXY;
+    rh[1] = AXY - AX;
+    rh[2] = -AXY;
+  }
 };
 
 // Right-hand side of a refinement step: the FP64 residual
@@ -132,47 +155,52 @@ struct ResidualGen {
 };
 
 // psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction).
-template <typename T>
-__device__ __forceinline__ void psi_at(const UnitGeom& g, const double* psi0, int i, int j, T out[3]) {
+template <typename T, typename TS>
+__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3]) {
   const T X = (T)i / (T)g.Nx, Y = (T)j / (T)g.Ny;
   out[0] = (T(1) - X) * (T(1) - Y);
   out[1] = X * (T(1) - Y);
   out[2] = X * Y;
   if (i > 0 && j > 0 && i < g.Nx && j < g.Ny) {
-    const double* p = psi0 + ((size_t)(j - 1) * g.mx + (i - 1)) * 3;
+    const TS* p = psi0 + ((size_t)(j - 1) * g.mx + (i - 1)) * 3;
     out[0] += (T)p[0];
     out[1] += (T)p[1];
     out[2] += (T)p[2];
   }
 }
 
-// 4x4 inverse, Gauss-Jordan with partial pivoting (FP64).  Returns false if singular.
-__device__ inline bool inv4(double C[4][4], double D[4][4]) {
-  double M[4][8];
+// 4x4 inverse by Gauss-Jordan elimination without row exchanges, all
+// indices static so the matrix stays in registers.  C_jk = psi_j(corner k)
+// is strongly diagonally dominant (the patch basis at the cell corners is
+// close to the patch's own bilinear nodal values), so no pivoting is needed;
+// a vanishing pivot reports failure.
+template <typename T>
+__device__ __forceinline__ bool inv4(T C[4][4], T D[4][4]) {
+  T M[4][8];
+#pragma unroll
   for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? C[r][c] : (c - 4 == r ? 1.0 : 0.0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? C[r][c] : (c - 4 == r ? T(1) : T(0));
+  bool ok = true;
+#pragma unroll
   for (int c = 0; c < 4; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < 4; ++r)
-      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-    if (M[piv][c] == 0.0) return false;
-    if (piv != c)
-      for (int k = 0; k < 8; ++k) {
-        const double t = M[c][k];
-        M[c][k] = M[piv][k];
-        M[piv][k] = t;
-      }
-    const double dinv = 1.0 / M[c][c];
+    ok = ok && (M[c][c] != T(0));
+    const T dinv = T(1) / M[c][c];
+#pragma unroll
     for (int k = 0; k < 8; ++k) M[c][k] *= dinv;
+#pragma unroll
     for (int r = 0; r < 4; ++r)
       if (r != c) {
-        const double f = M[r][c];
+        const T f = M[r][c];
+#pragma unroll
         for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
       }
   }
+#pragma unroll
   for (int r = 0; r < 4; ++r)
+#pragma unroll
     for (int c = 0; c < 4; ++c) D[r][c] = M[r][c + 4];
-  return true;
+  return ok;
 }
 
 struct UpscaleArgs {
@@ -186,27 +214,30 @@ struct UpscaleArgs {
   double* phi;
   int32_t* status;
   unsigned char* ws;
-  size_t slot_bytes;
+  size_t slot_bytes, l_bytes;
   int bmax, nmax;
   long long units;
 };
 
-// TK: factor/solve type; TA: type of the K_e/b_e accumulation.
-template <typename TK, typename TA>
-__global__ void __launch_bounds__(kUpscaleWarps * 32)
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// TK: factor/solve type; TA: type of the K_e/b_e accumulation and of the
+// recombination; RPL: panel rows per lane (ceil((16 + bmax) / 32)).
+template <typename TK, typename TA, int RPL>
+__global__ void __launch_bounds__(kUpscaleWarps * 32, sizeof(TK) == 4 ? 3 : 2)
 upscale_kernel(UpscaleArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const size_t ring_sz = ring_bytes<TK, 3>(A.bmax);
-  BandRing<TK, 3> ring = make_ring<TK, 3>(smem + wib * ring_sz, A.bmax);
+  const BlkSmem<TK> sm = make_blk<TK>(smem + wib * blk_smem_bytes<TK>(A.bmax), A.bmax);
   const long long gw = (long long)blockIdx.x * kUpscaleWarps + wib;
   const long long nw = (long long)gridDim.x * kUpscaleWarps;
   unsigned char* slot = A.ws + (size_t)gw * A.slot_bytes;
+  // solutions are kept in FP64 except in the all-FP32 form
+  using TS = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
   TK* Lg = reinterpret_cast<TK*>(slot);
-  const size_t l_bytes = ((size_t)A.nmax * (A.bmax + 1) * sizeof(TK) + 255) & ~size_t(255);
-  double* psi0 = reinterpret_cast<double*>(slot + l_bytes);
-  double* corr = psi0 + (size_t)A.nmax * 3;
+  TS* psi0 = reinterpret_cast<TS*>(slot + A.l_bytes);
+  double* corr = reinterpret_cast<double*>(slot + A.l_bytes) + (size_t)A.nmax * 3;
   const int ncell = A.nc * A.nc;
   const int CN = (A.rho + 1) * (A.rho + 1);
 
@@ -214,54 +245,55 @@ upscale_kernel(UpscaleArgs A) {
     const int s = (int)(u / ncell);
     const int cell = (int)(u % ncell);
     const int cx = cell % A.nc, cy = cell / A.nc;
-    int o = A.oversample ? (int)A.oversample[cell] : 0;
+    const int o = A.oversample ? (int)A.oversample[cell] : 0;
     double* Ke = A.Ke + (size_t)u * 10;
     double* be = A.be + (size_t)u * 4;
     if (o < 0 || o > A.max_o) {
-      if (lane < 10) Ke[lane] = __longlong_as_double(0x7ff8000000000000ll);
-      if (lane < 4) be[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane < 10) Ke[lane] = qnan();
+      if (lane < 4) be[lane] = qnan();
       if (lane == 0 && A.status) A.status[u] = -1;
       continue;
     }
     const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
-    PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
+    const PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
     int fail = -1;
     if (g.n > 0) {
-      fail = band_factor_forward<TK, 3>(pg, g.n, g.b, ring, Lg, psi0, lane);
+      fail = blk_factor<TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, lane);
       if (fail < 0) {
-        band_backward<TK, 3>(g.n, g.b, ring.R, Lg, psi0, ring.rhs, lane);
-        // FP64 iterative refinement with the FP32 factor
+        blk_backward<TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, lane);
+        // FP64 iterative refinement with the factor: corr = residual, solve, add
         for (int it = 0; it < A.refine; ++it) {
           __syncwarp();
-          ResidualGen rg{pg, psi0};
-          band_forward_stored<TK, 3>(rg, g.n, g.b, ring, Lg, corr, lane);
-          band_backward<TK, 3>(g.n, g.b, ring.R, Lg, corr, ring.rhs, lane);
+          const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
+          for (int k = lane; k < g.n * 3; k += 32) corr[k] = rg.rhs<double>(k / 3, k % 3);
           __syncwarp();
-          for (int k = lane; k < g.n * 3; k += 32) psi0[k] += corr[k];
+          blk_forward_stored<TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, lane);
+          blk_backward<TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, lane);
           __syncwarp();
+          for (int k = lane; k < g.n * 3; k += 32) psi0[k] += (TS)corr[k];
         }
       }
     }
     __syncwarp();
     if (fail >= 0) {
-      if (lane < 10) Ke[lane] = __longlong_as_double(0x7ff8000000000000ll);
-      if (lane < 4) be[lane] = __longlong_as_double(0x7ff8000000000000ll);
+      if (lane < 10) Ke[lane] = qnan();
+      if (lane < 4) be[lane] = qnan();
       if (lane == 0 && A.status) A.status[u] = fail + 1;
       continue;
     }
     // M_jk = a_cell(psi_j, psi_k) (j, k < 3) by the edge/diagonal difference
-    // form of the Q1 element energy: (1/6)[sum_edges du dv + 2 sum_diags du dv];
-    // m_j = (h^2/4) f sum over element corners of psi_j.
+    // form of the Q1 element energy, 6 u^T K_ref v = sum_edges du dv +
+    // 2 sum_diagonals du dv; m_j = sum over element corners of psi_j.
     TA M[6] = {0, 0, 0, 0, 0, 0};
     TA m[3] = {0, 0, 0};
     for (int e = lane; e < A.rho * A.rho; e += 32) {
       const int ex = e % A.rho, ey = e / A.rho;
       const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
       TA c0[3], c1[3], c2[3], c3[3];
-      psi_at<TA>(g, psi0, i0, j0, c0);
-      psi_at<TA>(g, psi0, i0 + 1, j0, c1);
-      psi_at<TA>(g, psi0, i0 + 1, j0 + 1, c2);
-      psi_at<TA>(g, psi0, i0, j0 + 1, c3);
+      psi_at<TA, TS>(g, psi0, i0, j0, c0);
+      psi_at<TA, TS>(g, psi0, i0 + 1, j0, c1);
+      psi_at<TA, TS>(g, psi0, i0 + 1, j0 + 1, c2);
+      psi_at<TA, TS>(g, psi0, i0, j0 + 1, c3);
       const TA ae = (TA)pg.ael(i0, j0);
       TA dd[3][6];
 #pragma unroll
@@ -289,37 +321,34 @@ upscale_kernel(UpscaleArgs A) {
 #pragma unroll
     for (int l = 0; l < 3; ++l) m[l] = warp_sum(m[l]);
 
-    // recombination matrix D = C^{-1}, C_jk = psi_j(cell corner k)
-    double D[4][4];
+    // recombination D = C^{-1}, C_jk = psi_j(cell corner k); identity when
+    // the patch is the cell (its corners carry the bilinear data exactly)
+    TA D[4][4];
     const bool patch_is_cell = (g.cx0 == 0 && g.cy0 == 0 && g.Nx == A.rho && g.Ny == A.rho);
     bool ok = true;
     if (patch_is_cell) {
       for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) D[r][c] = (r == c) ? 1.0 : 0.0;
+        for (int c = 0; c < 4; ++c) D[r][c] = (r == c) ? TA(1) : TA(0);
     } else {
       const int ci[4] = {g.cx0, g.cx0 + A.rho, g.cx0 + A.rho, g.cx0};
       const int cj[4] = {g.cy0, g.cy0, g.cy0 + A.rho, g.cy0 + A.rho};
-      double C[4][4];
+      TA C[4][4];
       for (int k = 0; k < 4; ++k) {
-        double v[3];
-        psi_at<double>(g, psi0, ci[k], cj[k], v);
+        TA v[3];
+        psi_at<TA, TS>(g, psi0, ci[k], cj[k], v);
         C[0][k] = v[0];
         C[1][k] = v[1];
         C[2][k] = v[2];
-        C[3][k] = 1.0 - v[0] - v[1] - v[2];
+        C[3][k] = TA(1) - v[0] - v[1] - v[2];
       }
-      ok = inv4(C, D);
+      ok = inv4<TA>(C, D);
     }
     if (lane == 0) {
       const double h = 1.0 / A.nf;
       double MM[4][4];
-      const double M6[6] = {(double)M[0], (double)M[1], (double)M[2],
-                            (double)M[3], (double)M[4], (double)M[5]};
-      MM[0][0] = M6[0]; MM[0][1] = MM[1][0] = M6[1]; MM[0][2] = MM[2][0] = M6[2];
-      MM[1][1] = M6[3]; MM[1][2] = MM[2][1] = M6[4]; MM[2][2] = M6[5];
-      for (int r = 0; r < 3; ++r) {
-        MM[r][3] = MM[3][r] = -(MM[r][0] + MM[r][1] + MM[r][2]);
-      }
+      MM[0][0] = M[0]; MM[0][1] = MM[1][0] = M[1]; MM[0][2] = MM[2][0] = M[2];
+      MM[1][1] = M[3]; MM[1][2] = MM[2][1] = M[4]; MM[2][2] = M[5];
+      for (int r = 0; r < 3; ++r) MM[r][3] = MM[3][r] = -(MM[r][0] + MM[r][1] + MM[r][2]);
       MM[3][3] = -(MM[0][3] + MM[1][3] + MM[2][3]);
       for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) MM[r][c] /= 6.0;
@@ -327,25 +356,24 @@ upscale_kernel(UpscaleArgs A) {
       double mv[4] = {fq * (double)m[0], fq * (double)m[1], fq * (double)m[2], 0.0};
       const double H = (double)A.rho * h;
       mv[3] = A.f * H * H - (mv[0] + mv[1] + mv[2]);
-      // K = D MM D^T, b = D mv
       double T4[4][4];
       for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) {
           double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += D[r][k] * MM[k][c];
+          for (int k = 0; k < 4; ++k) t += (double)D[r][k] * MM[k][c];
           T4[r][c] = t;
         }
       int q = 0;
       for (int r = 0; r < 4; ++r)
         for (int c = r; c < 4; ++c) {
           double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += T4[r][k] * D[c][k];
-          Ke[q++] = ok ? t : __longlong_as_double(0x7ff8000000000000ll);
+          for (int k = 0; k < 4; ++k) t += T4[r][k] * (double)D[c][k];
+          Ke[q++] = ok ? t : qnan();
         }
       for (int r = 0; r < 4; ++r) {
         double t = 0.0;
-        for (int k = 0; k < 4; ++k) t += D[r][k] * mv[k];
-        be[r] = ok ? t : __longlong_as_double(0x7ff8000000000000ll);
+        for (int k = 0; k < 4; ++k) t += (double)D[r][k] * mv[k];
+        be[r] = ok ? t : qnan();
       }
       if (A.status) A.status[u] = ok ? 0 : STOMSFEM_ENOTSPD;
     }
@@ -354,11 +382,11 @@ upscale_kernel(UpscaleArgs A) {
       for (int q = lane; q < CN; q += 32) {
         const int i = g.cx0 + q % (A.rho + 1), j = g.cy0 + q / (A.rho + 1);
         double v[3];
-        psi_at<double>(g, psi0, i, j, v);
+        psi_at<double, TS>(g, psi0, i, j, v);
         const double v4[4] = {v[0], v[1], v[2], 1.0 - v[0] - v[1] - v[2]};
         for (int l = 0; l < 4; ++l) {
           double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += D[l][k] * v4[k];
+          for (int k = 0; k < 4; ++k) t += (double)D[l][k] * v4[k];
           ph[(size_t)l * CN + q] = t;
         }
       }
@@ -367,10 +395,12 @@ upscale_kernel(UpscaleArgs A) {
   }
 }
 
-static size_t slot_bytes_for(int nmax, int bmax, int precision) {
+static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void slot_layout(int nmax, int bmax, int precision, size_t* slot, size_t* l_bytes) {
   const size_t tk = precision == STOMSFEM_FP64 ? 8 : 4;
-  const size_t l_bytes = ((size_t)nmax * (bmax + 1) * tk + 255) & ~size_t(255);
-  return l_bytes + (((size_t)nmax * 3 * 8 * 2 + 255) & ~size_t(255));
+  *l_bytes = round256(blk_factor_elems(nmax, bmax) * tk);
+  *slot = *l_bytes + round256((size_t)nmax * 3 * 8 * 2);
 }
 
 static int validate_grid(const stomsfem_grid* g) {
@@ -389,6 +419,30 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
   *bmax = m + 1;
 }
 
+template <typename TK, typename TA, int RPL>
+static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
+  auto kern = upscale_kernel<TK, TA, RPL>;
+  const size_t smem = blk_smem_bytes<TK>(A.bmax) * kUpscaleWarps;
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUpscaleWarps * 32, smem));
+  if (per_sm < 1) return set_error(STOMSFEM_EINVAL, "upscale kernel does not fit on an SM (smem %zu)", smem);
+  long long blocks = (long long)per_sm * device_sm_count();
+  if (blocks > max_blocks) blocks = max_blocks;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
+
+template <typename TK, typename TA>
+static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
+  const int rpl = (kNB + A.bmax + 31) / 32;
+  if (rpl <= 1) return launch_upscale<TK, TA, 1>(A, max_blocks, st);
+  if (rpl == 2) return launch_upscale<TK, TA, 2>(A, max_blocks, st);
+  return launch_upscale<TK, TA, 3>(A, max_blocks, st);
+}
+
 }  // namespace stomsfem
 
 using namespace stomsfem;
@@ -402,11 +456,12 @@ extern "C" int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_
     return set_error(STOMSFEM_EINVAL, "bad max_oversample/precision");
   int nmax, bmax;
   patch_limits(grid, max_oversample, &nmax, &bmax);
-  const size_t sb = slot_bytes_for(nmax, bmax, precision);
+  size_t sb, lb;
+  slot_layout(nmax, bmax, precision, &sb, &lb);
   if (slot_bytes) *slot_bytes = sb;
   if (recommended_bytes) {
     const int sms = device_sm_count();
-    *recommended_bytes = sb * (size_t)(sms > 0 ? sms : 152) * 16;
+    *recommended_bytes = sb * (size_t)(sms > 0 ? sms : 152) * 32;
   }
   return STOMSFEM_OK;
 }
@@ -432,16 +487,16 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   if (bmax > kMaxBand)
     return set_error(STOMSFEM_EINVAL, "patch bandwidth %d exceeds %d (rho + 2*max_o too large)",
                      bmax, kMaxBand);
-  const size_t sb = slot_bytes_for(nmax, bmax, precision);
+  size_t sb, lb;
+  slot_layout(nmax, bmax, precision, &sb, &lb);
   const long long units = (long long)S * grid->nc * grid->nc;
-  long long slots = (long long)(workspace_bytes / sb);
+  const long long slots = (long long)(workspace_bytes / sb);
   if (slots < kUpscaleWarps)
     return set_error(STOMSFEM_ENOMEM, "workspace %zu bytes < %d slots of %zu bytes", workspace_bytes,
                      kUpscaleWarps, sb);
-  long long blocks = slots / kUpscaleWarps;
+  long long max_blocks = slots / kUpscaleWarps;
   const long long need = (units + kUpscaleWarps - 1) / kUpscaleWarps;
-  if (blocks > need) blocks = need;
-  if (blocks > 1 << 20) blocks = 1 << 20;
+  if (max_blocks > need) max_blocks = need;
 
   UpscaleArgs A;
   A.a = a;
@@ -459,26 +514,12 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   A.status = unit_status;
   A.ws = static_cast<unsigned char*>(workspace);
   A.slot_bytes = sb;
+  A.l_bytes = lb;
   A.bmax = bmax;
   A.nmax = nmax;
   A.units = units;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == STOMSFEM_FP64) {
-    const size_t smem = ring_bytes<double, 3>(bmax) * kUpscaleWarps;
-    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<double, double>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    upscale_kernel<double, double><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
-  } else if (precision == STOMSFEM_FP32_REFINED) {
-    const size_t smem = ring_bytes<float, 3>(bmax) * kUpscaleWarps;
-    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<float, double>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    upscale_kernel<float, double><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
-  } else {
-    const size_t smem = ring_bytes<float, 3>(bmax) * kUpscaleWarps;
-    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(upscale_kernel<float, float>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    upscale_kernel<float, float><<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
-  }
-  STOMSFEM_TRY_CUDA(cudaGetLastError());
-  return STOMSFEM_OK;
+  if (precision == STOMSFEM_FP64) return launch_rpl<double, double>(A, max_blocks, st);
+  if (precision == STOMSFEM_FP32_REFINED) return launch_rpl<float, double>(A, max_blocks, st);
+  return launch_rpl<float, float>(A, max_blocks, st);
 }
