@@ -124,6 +124,35 @@ int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* o
                      double* Ke, double* be, double* phi, int32_t* unit_status, void* workspace,
                      size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* Allocation-free variant of stomsfem_upscale (the paper has no counterpart;
+ * this is a library convenience).  For callers that cannot allocate device
+ * memory where they upscale -- code running inside another framework's
+ * memory pool or a plugin that must not grow the device footprint, loops
+ * that must not take cudaMalloc's implicit synchronisation, programs that
+ * only receive device pointers -- the scratch is a fixed 64 MiB file-scope
+ * device array instead of a caller workspace; inputs and outputs are the
+ * caller's, with the same meaning and layout as in stomsfem_upscale.
+ *  - The array is reserved on a device when the library module holding it
+ *    is loaded there (by default, at the first call of this function on
+ *    that device) and is held until the process exits.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same array.  Nothing in it needs to start at zero
+ *    (each unit overwrites what it reads), but calls that can overlap on
+ *    the GPU (different streams, or different host threads) race on it and
+ *    must be serialised by the caller.
+ *  - Errors: EINVAL when 4 warp slots of the requested patch size do not fit
+ *    in the array (message gives the sizes), plus those of stomsfem_upscale.
+ *    Fewer slots than the workspace path may mean lower throughput. */
+int stomsfem_upscale_noalloc(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                             int32_t max_oversample, int32_t S, int32_t precision,
+                             int32_t refine_iters, double* Ke, double* be, double* phi,
+                             int32_t* unit_status, stomsfem_stream_t stream);
+
+/* Size in bytes of the static scratch array used by stomsfem_upscale_noalloc. */
+size_t stomsfem_upscale_static_scratch_bytes(void);
+
 /* Scratch needed by stomsfem_coarse_solve. */
 int stomsfem_coarse_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
 
