@@ -203,8 +203,8 @@ def main():
     ap.add_argument("--workload", default="upscale_1024")
     ap.add_argument("--batch", type=int, default=512, help="samples per step")
     ap.add_argument("--fp64-batch", type=int, default=32, help="samples per step of the FP64 arm")
-    ap.add_argument("--ref-samples", type=int, default=1)
-    ap.add_argument("--cpu-samples", type=int, default=2)
+    ap.add_argument("--ref-samples", type=int, default=8)
+    ap.add_argument("--cpu-samples", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
