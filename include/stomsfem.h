@@ -170,6 +170,54 @@ int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const dou
                           int32_t S, double* u, double* mean, double* m2, double* count,
                           void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Reduced-basis (POD) upscaling, Sec. 3.2 (Eq. KLphi, Eqs. localRB and
+ * localRBsystem, Algs. 3 and 4), for cells without oversampling.
+ * ------------------------------------------------------------------- */
+typedef struct stomsfem_pod stomsfem_pod; /* opaque, owned by the library */
+
+/* Offline stage (Alg. 3).  Inputs are training snapshots of the multiscale
+ * basis as produced by stomsfem_upscale (phi output, oversample NULL) and
+ * the training coefficients:
+ *   phi_snap  device [S_train][nc*nc][4][(rho+1)^2] float64
+ *   a_train   device [S_train][nf][nf] float64
+ * Per cell: phibar_l = training mean of phi_l; abar = training mean of a;
+ * KL expansion of the centred interior snapshots (the four l stacked, one
+ * basis per cell) in the energy inner product int abar grad u . grad v
+ * (footnote of Eq. KLphi); modes kept while sqrt(lambda_q/lambda_1) >= tol,
+ * at most max_rank; or, if ranks_in (host [nc*nc]) is not NULL, exactly
+ * ranks_in[cell] modes.  ranks_out (host [nc*nc], may be NULL) receives the
+ * ranks.  Limits: 2 <= rho <= 8, 1 <= max_rank <= 27.  Allocates the
+ * handle's device memory and synchronises `stream` before returning.
+ * Errors: EINVAL, ENOTSPD (training-mean energy matrix), ECUDA. */
+int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                       int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
+                       stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
+
+/* Frees the handle (synchronous). */
+int stomsfem_pod_destroy(stomsfem_pod* pod);
+
+/* Copies all KL eigenvalues, host [nc*nc][(rho-1)^2], descending per cell
+ * (synchronous). */
+int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host);
+
+/* Scratch of stomsfem_pod_upscale for S samples (BF16 copy of a by cell and
+ * the FP32 reduced matrices). */
+int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* bytes);
+
+/* Online stage (Alg. 4) for S samples a (device [S][nf][nf] float64):
+ * G = W^T A(omega) W for the extended basis W = [phibar, V] as one
+ * tensor-core GEMM per cell (BF16 operands, FP32 accumulation), the r x r
+ * Galerkin system (V^T A V) c_l = -V^T A phibar_l in FP32, then
+ * refine_iters FP64 refinement steps whose residual is formed with the fine
+ * 9-point stencil of A(omega) (0 = none: K_e and b_e from the FP32 reduced
+ * quantities).  Outputs as in stomsfem_upscale (Ke [S][nc*nc][10], be
+ * [S][nc*nc][4], unit_status [S][nc*nc] or NULL: 0, ENOTSPD, ETIMEOUT).
+ * Errors: EINVAL, ENOMEM (workspace), ECUDA. */
+int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t refine_iters,
+                         double* Ke, double* be, int32_t* unit_status, void* workspace,
+                         size_t workspace_bytes, stomsfem_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,7 @@ def _L():
         lib = ctypes.CDLL(_SO)
         d, i, p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
         lib.orc_sample_coef.argtypes = [i, i, i, i, d, d, d, d, p, i, p, i]
+        lib.orc_sample_coef_window.argtypes = [i, i, i, i, d, d, d, d, p, i, i, i, i, p]
         lib.orc_cell.argtypes = [i, i, d, p, i, i, i, p, p, p, p]
         lib.orc_upscale.argtypes = [i, i, d, p, p, i, p, p, p, p, i]
         lib.orc_coarse_solve.argtypes = [i, p, p, i, p]
@@ -95,6 +96,21 @@ def sample_coef(nf, field, xi, nthreads=0):
                               float(field.get("gain", 1.0)), _ptr(xi), S, _ptr(a), nthreads)
     if rc != 0:
         raise ValueError("orc_sample_coef failed: %d" % rc)
+    return a
+
+
+def sample_coef_window(nf, field, xi_row, ex0, ex1, ey0, ey1, out=None):
+    """The coefficient of one sample on the element window [ex0,ex1)x[ey0,ey1)
+    of an nf x nf array (other entries: ``out``'s, default NaN)."""
+    xi_row = np.ascontiguousarray(xi_row, dtype=np.float64)
+    a = np.full((nf, nf), np.nan) if out is None else out
+    rc = _L().orc_sample_coef_window(nf, int(field["kind"]), int(field["nbx"]), int(field["nby"]),
+                                     float(field["width"]), float(field.get("scale", 1.0)),
+                                     float(field.get("contrast_log", 0.0)),
+                                     float(field.get("gain", 1.0)), _ptr(xi_row), ex0, ex1, ey0,
+                                     ey1, _ptr(a))
+    if rc != 0:
+        raise ValueError("orc_sample_coef_window failed")
     return a
 
 

@@ -100,6 +100,34 @@ int orc_sample_coef(int nf, int kind, int nbx, int nby, double width,
   return 0;
 }
 
+/* The same coefficient for one sample, only on the element window
+ * [ex0, ex1) x [ey0, ey1); the rest of a[nf*nf] is left untouched. */
+int orc_sample_coef_window(int nf, int kind, int nbx, int nby, double width, double scale,
+                           double contrast_log, double gain, const double* xi, int ex0,
+                           int ex1, int ey0, int ey1, double* a) {
+  if (nf <= 0 || nbx <= 0 || nby <= 0 || width <= 0.0) return -1;
+  if (ex0 < 0 || ey0 < 0 || ex1 > nf || ey1 > nf) return -1;
+  const double h = 1.0 / nf;
+  for (int ey = ey0; ey < ey1; ++ey) {
+    const double y = (ey + 0.5) * h;
+    for (int ex = ex0; ex < ex1; ++ex) {
+      const double x = (ex + 0.5) * h;
+      double z = 0.0;
+      for (int by = 0; by < nby; ++by) {
+        const double cy = (by + 0.5) / nby;
+        for (int bx = 0; bx < nbx; ++bx) {
+          const double cx = (bx + 0.5) / nbx;
+          const double r2 = (x - cx) * (x - cx) + (y - cy) * (y - cy);
+          z += xi[by * nbx + bx] * exp(-r2 / (width * width));
+        }
+      }
+      a[(size_t)ey * nf + ex] =
+          kind == 0 ? exp(scale * z) : exp(contrast_log / (1.0 + exp(-gain * z)));
+    }
+  }
+  return 0;
+}
+
 /* ---------------------------------------------------------------- */
 /* Banded symmetric positive definite matrices.                       */
 /* Storage: band[k*(bw+1) + d] = A[k][k-d], d = 0..bw (lower band).   */

@@ -47,6 +47,15 @@ _SIG = {
     "stomsfem_coarse_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
     "stomsfem_coarse_solve": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P,
                                              _SZ, _P]),
+    "stomsfem_upscale_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _P, _P,
+                                                _P, _P, _P]),
+    "stomsfem_upscale_static_scratch_bytes": (ctypes.c_size_t, []),
+    "stomsfem_pod_build": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, ctypes.c_double, _I, _P,
+                                          ctypes.POINTER(_P), _P, _P]),
+    "stomsfem_pod_destroy": (ctypes.c_int, [_P]),
+    "stomsfem_pod_eigenvalues": (ctypes.c_int, [_P, _P]),
+    "stomsfem_pod_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_pod_upscale": (ctypes.c_int, [_P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 
 

@@ -105,3 +105,52 @@ def stomsfem_coarse_solve(g: Grid, Ke, be, u, mean=None, m2=None, count=None, wo
         _dev(mean, torch.float64, (nn,), "mean"), _dev(m2, torch.float64, (nn,), "m2"),
         _dev(count, torch.float64, (1,), "count"), _dev(workspace, torch.uint8, None, "workspace"),
         workspace.numel(), _stream(stream)))
+
+
+def stomsfem_pod_build(g: Grid, phi_snap, a_train, tol=1e-6, max_rank=27, ranks=None, stream=None):
+    """Returns (handle, ranks list)."""
+    S = a_train.shape[0]
+    ncell = g.nc * g.nc
+    rho = g.nf // g.nc
+    h = ctypes.c_void_p()
+    rk = (ctypes.c_int32 * ncell)()
+    rin = None
+    if ranks is not None:
+        rin = (ctypes.c_int32 * ncell)(*[int(x) for x in ranks])
+    L.check(L.lib().stomsfem_pod_build(
+        ctypes.byref(g), _dev(phi_snap, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi_snap"),
+        _dev(a_train, torch.float64, (S, g.nf, g.nf), "a_train"), S, float(tol), int(max_rank),
+        ctypes.cast(rin, ctypes.c_void_p) if rin is not None else None, ctypes.byref(h),
+        ctypes.cast(rk, ctypes.c_void_p), _stream(stream)))
+    return h, list(rk)
+
+
+def stomsfem_pod_destroy(h):
+    L.check(L.lib().stomsfem_pod_destroy(h))
+
+
+def stomsfem_pod_eigenvalues(h, g: Grid):
+    import numpy as np
+    rho = g.nf // g.nc
+    lam = np.empty((g.nc * g.nc, (rho - 1) ** 2))
+    L.check(L.lib().stomsfem_pod_eigenvalues(h, lam.ctypes.data_as(ctypes.c_void_p)))
+    return lam
+
+
+def stomsfem_pod_workspace_size(h, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_pod_workspace_size(h, int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_pod_upscale(h, g: Grid, a, Ke, be, refine_iters=0, unit_status=None, workspace=None,
+                         stream=None):
+    S = a.shape[0]
+    ncell = g.nc * g.nc
+    if workspace is None:
+        workspace = torch.empty(stomsfem_pod_workspace_size(h, S), dtype=torch.uint8, device=a.device)
+    L.check(L.lib().stomsfem_pod_upscale(
+        h, _dev(a, torch.float64, (S, g.nf, g.nf), "a"), S, int(refine_iters),
+        _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))

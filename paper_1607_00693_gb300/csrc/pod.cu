@@ -1,0 +1,863 @@
+// Reduced-basis (POD) upscaling, Sec. 3.2 of the paper.
+//
+// Offline (Alg. 3, Eq. KLphi), per coarse cell, FP64:
+//   phibar_l = training mean of the multiscale basis phi_l (l = 1..4),
+//   abar     = training mean of the coefficient on the cell,
+//   C        = covariance of the centred interior snapshots (all four l
+//              stacked, one shared basis per cell),
+//   KL in the energy inner product <u,v> = u^T Abar v (footnote of Eq.
+//   KLphi): Abar = R R^T, B = R^T C R = W Lambda W^T (parallel cyclic Jacobi),
+//   zeta_q = R^{-T} w_q, kept while sqrt(lambda_q / lambda_1) >= tol,
+//   element tensors T_e = W_e^T K_ref W_e of the extended basis
+//   Wfull = [phibar_1..4, zeta_1..r] in packed upper-triangle order.
+// Online (Alg. 4, Eqs. localRB and localRBsystem), per (sample, cell):
+//   G(omega) = Wfull^T A(omega) Wfull = sum_e a_e T_e  -> one GEMM per cell,
+//              [samples x elements] x [elements x packed entries], BF16
+//              operands, FP32 accumulation in tensor memory (tcgen05);
+//   (V^T A V) c_l = -V^T A phibar_l: r x r FP32 Cholesky in a warp;
+//   optional FP64 refinement: residual through the fine 9-point stencil;
+//   K_e = a(phibar + V c, phibar + V c), b_e = f int (phibar + V c).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace stomsfem {
+
+constexpr int kPodMaxRho = 8;      // elements per cell side (64 elements = one 128-byte K row)
+constexpr int kPodMaxN = 49;       // interior nodes, (rho - 1)^2
+constexpr int kPodMaxRank = 27;    // (4 + r)(5 + r)/2 <= 496 packed entries fit 512 TMEM columns
+constexpr int kPodK = 64;          // GEMM K (elements per cell, zero padded)
+constexpr int kPodTileM = 128;
+
+__device__ __forceinline__ int pidx(int a, int b, int P0) {
+  // packed upper-triangle index of (a, b), a <= b < P0
+  return a * P0 - (a * (a - 1)) / 2 + (b - a);
+}
+
+__device__ __constant__ double kKref[4][4] = {{4.0 / 6, -1.0 / 6, -2.0 / 6, -1.0 / 6},
+                                              {-1.0 / 6, 4.0 / 6, -1.0 / 6, -2.0 / 6},
+                                              {-2.0 / 6, -1.0 / 6, 4.0 / 6, -1.0 / 6},
+                                              {-1.0 / 6, -2.0 / 6, -1.0 / 6, 4.0 / 6}};
+
+struct PodDims {
+  int nf, nc, rho, N2, n, ne, P0, P, Ppad, ncell;
+  double f;
+};
+
+// ------------------------------------------------------------------ offline
+
+// phibar[cell][4][N2], abar[cell][ne]
+__global__ void pod_mean_kernel(PodDims d, const double* __restrict__ phi, const double* __restrict__ a,
+                                int Ns, double* __restrict__ phibar, double* __restrict__ abar) {
+  const int cell = blockIdx.x;
+  const int cx = cell % d.nc, cy = cell / d.nc;
+  for (int q = threadIdx.x; q < 4 * d.N2; q += blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < Ns; ++t) s += phi[((size_t)t * d.ncell + cell) * 4 * d.N2 + q];
+    phibar[(size_t)cell * 4 * d.N2 + q] = s / Ns;
+  }
+  for (int e = threadIdx.x; e < d.ne; e += blockDim.x) {
+    const int ex = e % d.rho, ey = e / d.rho;
+    double s = 0.0;
+    for (int t = 0; t < Ns; ++t) s += a[((size_t)t * d.nf + cy * d.rho + ey) * d.nf + cx * d.rho + ex];
+    abar[(size_t)cell * d.ne + e] = s / Ns;
+  }
+}
+
+// interior node q (0..n-1) -> cell node index
+__device__ __forceinline__ int inner_node(int q, int rho) {
+  const int m = rho - 1;
+  const int j = q / m + 1, i = q % m + 1;
+  return j * (rho + 1) + i;
+}
+
+// Covariance of the centred interior snapshots: cov[cell][n][n].
+__global__ void pod_cov_kernel(PodDims d, const double* __restrict__ phi, int Ns,
+                               const double* __restrict__ phibar, double* __restrict__ cov) {
+  const int cell = blockIdx.x;
+  const int n = d.n;
+  const double* pb = phibar + (size_t)cell * 4 * d.N2;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    if (j < i) continue;
+    const int vi = inner_node(i, d.rho), vj = inner_node(j, d.rho);
+    double s = 0.0;
+    for (int t = 0; t < Ns; ++t) {
+      const double* ph = phi + ((size_t)t * d.ncell + cell) * 4 * d.N2;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) s += (ph[l * d.N2 + vi] - pb[l * d.N2 + vi]) * (ph[l * d.N2 + vj] - pb[l * d.N2 + vj]);
+    }
+    s /= (4.0 * Ns);
+    cov[((size_t)cell * n + i) * n + j] = s;
+    cov[((size_t)cell * n + j) * n + i] = s;
+  }
+}
+
+// One CTA per cell: energy metric, KL eigenproblem, rank, basis.
+//   W [cell][N2][P0]: columns 0..3 = phibar_l, 4..4+r-1 = zeta_q (0 on the
+//   boundary), the rest 0.  lam [cell][n] eigenvalues, descending.
+__global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
+                               const double* __restrict__ phibar, const double* __restrict__ abar,
+                               double tol, int max_rank, const int32_t* __restrict__ ranks_in,
+                               double* __restrict__ W, double* __restrict__ lam_out,
+                               int32_t* __restrict__ ranks_out, int32_t* __restrict__ err) {
+  extern __shared__ double eig_smem[];  // three (kPodMaxN+1)^2 matrices
+  typedef double Mat[kPodMaxN + 1];
+  Mat* R = reinterpret_cast<Mat*>(eig_smem);
+  Mat* B = R + (kPodMaxN + 1);
+  Mat* Z = B + (kPodMaxN + 1);
+  __shared__ double cs[(kPodMaxN + 1) / 2][2];
+  __shared__ int pairs[(kPodMaxN + 1) / 2][2];
+  __shared__ int order[kPodMaxN + 1];
+  __shared__ double offn;
+  __shared__ int s_rank;
+  const int cell = blockIdx.x;
+  const int n = d.n, rho = d.rho, m = rho - 1;
+  const int ne2 = (n + 1) & ~1;  // even size for the round-robin ordering
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // --- Abar on the interior nodes (dense), into R
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) R[idx / ne2][idx % ne2] = 0.0;
+  __syncthreads();
+  if (tid == 0) {
+    for (int ey = 0; ey < rho; ++ey)
+      for (int ex = 0; ex < rho; ++ex) {
+        const double ae = abar[(size_t)cell * d.ne + ey * rho + ex];
+        const int ci[4] = {ex, ex + 1, ex + 1, ex}, cj[4] = {ey, ey, ey + 1, ey + 1};
+        for (int r = 0; r < 4; ++r) {
+          if (ci[r] <= 0 || ci[r] >= rho || cj[r] <= 0 || cj[r] >= rho) continue;
+          const int qr = (cj[r] - 1) * m + ci[r] - 1;
+          for (int c = 0; c < 4; ++c) {
+            if (ci[c] <= 0 || ci[c] >= rho || cj[c] <= 0 || cj[c] >= rho) continue;
+            R[qr][(cj[c] - 1) * m + ci[c] - 1] += ae * kKref[r][c];
+          }
+        }
+      }
+  }
+  __syncthreads();
+  // --- Cholesky Abar = R R^T (lower, in place)
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double v = R[k][k];
+      if (!(v > 0.0)) atomicOr(err, 1);
+      R[k][k] = sqrt(v > 0.0 ? v : 1.0);
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += nt) R[i][k] /= R[k][k];
+    __syncthreads();
+    for (int idx = tid; idx < (n - k - 1) * (n - k - 1); idx += nt) {
+      const int i = k + 1 + idx / (n - k - 1), j = k + 1 + idx % (n - k - 1);
+      if (j <= i) R[i][j] -= R[i][k] * R[j][k];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) {
+    const int i = idx / ne2, j = idx % ne2;
+    if (j > i || i >= n) R[i][j] = (i == j && i >= n) ? 1.0 : (j > i ? 0.0 : R[i][j]);
+  }
+  __syncthreads();
+  // --- B = R^T C R: Z = C R, then B = R^T Z
+  const double* C = cov + (size_t)cell * n * n;
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) {
+    const int i = idx / ne2, j = idx % ne2;
+    double s = 0.0;
+    if (i < n && j < n)
+      for (int k = j; k < n; ++k) s += C[i * n + k] * R[k][j];
+    Z[i][j] = s;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) {
+    const int i = idx / ne2, j = idx % ne2;
+    double s = 0.0;
+    for (int k = i; k < n; ++k) s += R[k][i] * Z[k][j];
+    B[i][j] = s;
+  }
+  __syncthreads();
+  // --- parallel cyclic Jacobi with round-robin pairs; Z accumulates vectors
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) Z[idx / ne2][idx % ne2] = (idx / ne2 == idx % ne2) ? 1.0 : 0.0;
+  __syncthreads();
+  const int np = ne2 / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) {
+      double off = 0.0, dia = 0.0;
+      for (int i = 0; i < ne2; ++i)
+        for (int j = 0; j < ne2; ++j) (i == j ? dia : off) += B[i][j] * B[i][j];
+      offn = (off <= 1e-30 * dia) ? -1.0 : off;
+    }
+    __syncthreads();
+    if (offn < 0.0) break;
+    for (int rnd = 0; rnd < ne2 - 1; ++rnd) {
+      // round-robin: position 0 fixed, others rotate
+      for (int k = tid; k < np; k += nt) {
+        int a = (k == 0) ? 0 : 1 + (k - 1 + rnd) % (ne2 - 1);
+        int b = 1 + (ne2 - 2 - k + rnd) % (ne2 - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        pairs[k][0] = a;
+        pairs[k][1] = b;
+        const double app = B[a][a], aqq = B[b][b], apq = B[a][b];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300) {
+          const double th = (aqq - app) / (2.0 * apq);
+          const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+        }
+        cs[k][0] = c;
+        cs[k][1] = s;
+      }
+      __syncthreads();
+      // rows: B[a,:], B[b,:]
+      for (int idx = tid; idx < np * ne2; idx += nt) {
+        const int k = idx / ne2, j = idx % ne2;
+        const int a = pairs[k][0], b = pairs[k][1];
+        const double c = cs[k][0], s = cs[k][1];
+        const double x = B[a][j], y = B[b][j];
+        B[a][j] = c * x - s * y;
+        B[b][j] = s * x + c * y;
+      }
+      __syncthreads();
+      // columns: B[:,a], B[:,b] and the vectors Z[:,a], Z[:,b]
+      for (int idx = tid; idx < np * ne2; idx += nt) {
+        const int k = idx / ne2, i = idx % ne2;
+        const int a = pairs[k][0], b = pairs[k][1];
+        const double c = cs[k][0], s = cs[k][1];
+        const double x = B[i][a], y = B[i][b];
+        B[i][a] = c * x - s * y;
+        B[i][b] = s * x + c * y;
+        const double zx = Z[i][a], zy = Z[i][b];
+        Z[i][a] = c * zx - s * zy;
+        Z[i][b] = s * zx + c * zy;
+      }
+      __syncthreads();
+    }
+  }
+  // --- order eigenvalues (descending) among the n real ones
+  for (int i = tid; i < n; i += nt) {
+    int rank = 0;
+    for (int j = 0; j < n; ++j)
+      if (B[j][j] > B[i][i] || (B[j][j] == B[i][i] && j < i)) ++rank;
+    order[rank] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r;
+    if (ranks_in) {
+      r = ranks_in[cell];
+    } else {
+      const double l1 = B[order[0]][order[0]] > 0 ? B[order[0]][order[0]] : 1.0;
+      r = 0;
+      while (r < n && sqrt(fmax(B[order[r]][order[r]], 0.0) / l1) >= tol) ++r;
+    }
+    if (r > max_rank) r = max_rank;
+    if (r < 1) r = 1;
+    if (r > n) r = n;
+    s_rank = r;
+    ranks_out[cell] = r;
+  }
+  for (int i = tid; i < n; i += nt) lam_out[(size_t)cell * n + i] = B[order[i]][order[i]];
+  __syncthreads();
+  const int r = s_rank;
+  // --- zeta_q = R^{-T} w_q (back substitution with the upper factor R^T)
+  double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  for (int idx = tid; idx < d.N2 * d.P0; idx += nt) {
+    const int node = idx / d.P0, col = idx % d.P0;
+    Wc[idx] = col < 4 ? phibar[(size_t)cell * 4 * d.N2 + col * d.N2 + node] : 0.0;
+  }
+  __syncthreads();
+  for (int q = tid; q < r; q += nt) {
+    const int src = order[q];
+    // x = R^{-T} w: solve R^T x = w from the last row up; x stored in B's spare column space
+    for (int i = n - 1; i >= 0; --i) {
+      double s = Z[i][src];
+      for (int k = i + 1; k < n; ++k) s -= R[k][i] * Wc[(size_t)inner_node(k, rho) * d.P0 + 4 + q];
+      Wc[(size_t)inner_node(i, rho) * d.P0 + 4 + q] = s / R[i][i];
+    }
+  }
+}
+
+// T[cell][j][e] (BF16, K-major rows of kPodK) and the load terms
+// wl[cell][alpha] = f int Wfull_alpha.
+__global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_bfloat16* __restrict__ T,
+                                  double* __restrict__ wl) {
+  const int cell = blockIdx.x;
+  const double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  const int rho = d.rho;
+  for (int idx = threadIdx.x; idx < d.Ppad * kPodK; idx += blockDim.x) {
+    const int j = idx / kPodK, e = idx % kPodK;
+    double v = 0.0;
+    if (j < d.P && e < d.ne) {
+      // invert the packed index
+      int a = 0, rem = j;
+      while (rem >= d.P0 - a) { rem -= d.P0 - a; ++a; }
+      const int b = a + rem;
+      const int ex = e % rho, ey = e / rho;
+      const int nodes[4] = {ey * (rho + 1) + ex, ey * (rho + 1) + ex + 1, (ey + 1) * (rho + 1) + ex + 1,
+                            (ey + 1) * (rho + 1) + ex};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double wa = Wc[(size_t)nodes[r] * d.P0 + a];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v += wa * kKref[r][c] * Wc[(size_t)nodes[c] * d.P0 + b];
+      }
+    }
+    T[((size_t)cell * d.Ppad + j) * kPodK + e] = __float2bfloat16_rn((float)v);
+  }
+  const double h = 1.0 / d.nf;
+  for (int al = threadIdx.x; al < d.P0; al += blockDim.x) {
+    double s = 0.0;
+    for (int ey = 0; ey < rho; ++ey)
+      for (int ex = 0; ex < rho; ++ex)
+        s += Wc[(size_t)(ey * (rho + 1) + ex) * d.P0 + al] + Wc[(size_t)(ey * (rho + 1) + ex + 1) * d.P0 + al] +
+             Wc[(size_t)((ey + 1) * (rho + 1) + ex + 1) * d.P0 + al] + Wc[(size_t)((ey + 1) * (rho + 1) + ex) * d.P0 + al];
+    wl[(size_t)cell * d.P0 + al] = d.f * h * h / 4.0 * s;
+  }
+}
+
+// ------------------------------------------------------------------ online
+
+// a [S][nf][nf] -> Ab [cell][Spad][kPodK] BF16 (zero padded rows and columns)
+__global__ void pod_gather_kernel(PodDims d, const double* __restrict__ a, int S, int Spad,
+                                  __nv_bfloat16* __restrict__ Ab) {
+  const long long total = (long long)d.ncell * Spad * kPodK;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(idx % kPodK);
+    const long long t = idx / kPodK;
+    const int s = (int)(t % Spad), cell = (int)(t / Spad);
+    float v = 0.f;
+    if (s < S && e < d.ne) {
+      const int cx = cell % d.nc, cy = cell / d.nc, ex = e % d.rho, ey = e / d.rho;
+      v = (float)a[((size_t)s * d.nf + cy * d.rho + ey) * d.nf + cx * d.rho + ex];
+    }
+    Ab[idx] = __float2bfloat16_rn(v);
+  }
+}
+
+constexpr uint32_t kWaitLimit = 1u << 24;  // about 2 s
+
+// G[cell][s][j] = sum_e Ab[cell][s][e] T[cell][j][e]: one CTA per (128-sample
+// tile, cell); both operands staged once into 128-byte-swizzled shared
+// memory, 4 K-steps of 16 per N-chunk of <= 256, accumulator in TMEM.
+__global__ void __launch_bounds__(128, 1)
+pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
+                const __nv_bfloat16* __restrict__ T, float* __restrict__ G, int32_t* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = smem;                       // 128 rows x 128 B
+  unsigned char* sB = smem + kPodTileM * 128;     // Ppad rows x 128 B
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cell = blockIdx.y;
+  const int s0 = blockIdx.x * kPodTileM;
+  uint32_t ncols = 32;
+  while ((int)ncols < d.Ppad) ncols <<= 1;
+  if (warp == 0) tc::tmem_alloc(&taddr_s, ncols);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  // stage operands (16-byte chunks into the swizzled layout)
+  const uint4* gA = reinterpret_cast<const uint4*>(Ab + ((size_t)cell * Spad + s0) * kPodK);
+  for (int c = tid; c < kPodTileM * 8; c += 128) {
+    const int row = c >> 3, ch = c & 7;
+    *reinterpret_cast<uint4*>(sA + tc::sw128_offset(row, ch * 8)) = gA[c];
+  }
+  const uint4* gB = reinterpret_cast<const uint4*>(T + (size_t)cell * d.Ppad * kPodK);
+  for (int c = tid; c < d.Ppad * 8; c += 128) {
+    const int row = c >> 3, ch = c & 7;
+    *reinterpret_cast<uint4*>(sB + tc::sw128_offset(row, ch * 8)) = gB[c];
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = taddr_s;
+  if (tid == 0) {
+    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+    for (int nb = 0; nb < d.Ppad; nb += 256) {
+      const int nsz = min(256, d.Ppad - nb);
+      const uint32_t idesc = tc::idesc_bf16_f32(kPodTileM, nsz);
+#pragma unroll
+      for (int kk = 0; kk < kPodK / 16; ++kk) {
+        const uint64_t ad = tc::sdesc_sw128(a0 + kk * 32);
+        const uint64_t bd = tc::sdesc_sw128(b0 + nb * 128 + kk * 32);
+        tc::mma_bf16(taddr + nb, ad, bd, idesc, kk > 0 ? 1u : 0u);
+      }
+    }
+    tc::mma_commit(&mbar);
+  }
+  __syncwarp();
+  const bool ok = tc::mbar_wait_bounded(&mbar, 0, kWaitLimit);
+  tc::fence_after_sync();
+  if (!ok) {
+    if (lane == 0) atomicOr(err, 2);
+  } else {
+    float* Grow = G + ((size_t)cell * Spad + s0 + warp * 32 + lane) * d.Ppad;
+    for (int col = 0; col < d.Ppad; col += 16) {
+      float v[16];
+      tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + col, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(Grow + col)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+}
+
+// ---- warp r x r Cholesky with 4 right-hand sides (lane q owns row q)
+
+template <int J>
+__device__ __forceinline__ void small_chol(float (&Mq)[32], float (&Fq)[4], int lane, int r, bool& bad) {
+  if constexpr (J < 32) {
+    if (J < r) {
+      const float dj = __shfl_sync(0xffffffffu, Mq[J], J);
+      if (!(dj > 0.f)) bad = true;
+      const float dinv = rsqrtf(dj > 0.f ? dj : 1.f);
+      float yj[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) yj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
+      const float lj = (lane > J && lane < r) ? Mq[J] * dinv : 0.f;
+      if (lane > J && lane < r) {
+        Mq[J] = lj;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] -= lj * yj[l];
+      }
+      if (lane == J) {
+        Mq[J] = dinv;  // keep the reciprocal pivot
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] = yj[l];
+      }
+#pragma unroll
+      for (int p = J + 1; p < 32; ++p) {
+        const float lp = __shfl_sync(0xffffffffu, lj, p);
+        Mq[p] -= lj * lp;
+      }
+    }
+    small_chol<J + 1>(Mq, Fq, lane, r, bad);
+  }
+}
+
+// forward (L y = f) with the stored factor, lane q holds f_q / y_q
+template <int J>
+__device__ __forceinline__ void small_fwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r) {
+  if constexpr (J < 32) {
+    if (J < r) {
+      const float dinv = __shfl_sync(0xffffffffu, Mq[J], J);
+      float yj[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) yj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
+      if (lane > J && lane < r) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] -= Mq[J] * yj[l];
+      }
+      if (lane == J) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] = yj[l];
+      }
+    }
+    small_fwd<J + 1>(Mq, Fq, lane, r);
+  }
+}
+
+// backward (L^T x = y), column oriented: lane q holds y_q then x_q.  The
+// entry L[p][q] lives in lane p's row at position q.
+template <int J>
+__device__ __forceinline__ void small_bwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r) {
+  if constexpr (J >= 0) {
+    if (J < r) {
+      const float dinv = __shfl_sync(0xffffffffu, Mq[J], J);
+      float xj[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) xj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
+      // lanes q < J need L[J][q] from lane J
+      float lq = 0.f;
+#pragma unroll
+      for (int q = 0; q < J; ++q) {
+        const float v = __shfl_sync(0xffffffffu, Mq[q], J);
+        if (lane == q) lq = v;
+      }
+      if (lane < J) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] -= lq * xj[l];
+      }
+      if (lane == J) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) Fq[l] = xj[l];
+      }
+    }
+    small_bwd<J - 1>(Mq, Fq, lane, r);
+  }
+}
+
+struct PodSolveArgs {
+  PodDims d;
+  int S, Spad, refine;
+  const float* G;
+  const double* W;
+  const double* wl;
+  const int32_t* ranks;
+  const double* a;
+  double* Ke;
+  double* be;
+  int32_t* status;
+  const int32_t* err;
+};
+
+constexpr int kPodSolveWarps = 4;
+constexpr int kPodN2Max = (kPodMaxRho + 1) * (kPodMaxRho + 1);
+
+__global__ void __launch_bounds__(kPodSolveWarps * 32)
+pod_solve_kernel(PodSolveArgs A) {
+  __shared__ double s_c[kPodSolveWarps][32][4];
+  __shared__ double s_u[kPodSolveWarps][kPodN2Max][4];
+  __shared__ double s_au[kPodSolveWarps][kPodN2Max][4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const PodDims& d = A.d;
+  const long long units = (long long)A.S * d.ncell;
+  const int P0 = d.P0;
+  const int rho = d.rho, NN = rho + 1;
+  const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+  for (long long u = (long long)blockIdx.x * kPodSolveWarps + wib; u < units;
+       u += (long long)gridDim.x * kPodSolveWarps) {
+    const int s = (int)(u / d.ncell), cell = (int)(u % d.ncell);
+    double* Ke = A.Ke + (size_t)u * 10;
+    double* be = A.be + (size_t)u * 4;
+    if (A.err[0] != 0) {
+      if (lane < 10) Ke[lane] = nanv;
+      if (lane < 4) be[lane] = nanv;
+      if (lane == 0 && A.status) A.status[u] = STOMSFEM_ETIMEOUT;
+      continue;
+    }
+    const int r = A.ranks[cell];
+    const float* g = A.G + ((size_t)cell * A.Spad + s) * d.Ppad;
+    // row q of V^T A V and right-hand sides -V^T A phibar_l
+    float Mq[32], Fq[4];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+      float v = 0.f;
+      if (lane < r && p < r) v = g[pidx(4 + min(lane, p), 4 + max(lane, p), P0)];
+      Mq[p] = v;
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) Fq[l] = (lane < r) ? -g[pidx(l, 4 + lane, P0)] : 0.f;
+    bool bad = false;
+    small_chol<0>(Mq, Fq, lane, r, bad);
+    small_bwd<31>(Mq, Fq, lane, r);
+    const double* Wc = A.W + (size_t)cell * d.N2 * P0;
+    const double* wl = A.wl + (size_t)cell * P0;
+    double Kv[10], bv[4];
+    if (A.refine == 0) {
+      // K = G_pp + G_pV c ; b = wl_p + wl_V c  (FP32 reduced quantities)
+      int q = 0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int lp = l; lp < 4; ++lp) {
+          float t = (lane < r) ? g[pidx(l, 4 + lane, P0)] * Fq[lp] : 0.f;
+          t = warp_sum(t);
+          Kv[q++] = (double)g[pidx(l, lp, P0)] + (double)t;
+        }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const double t = warp_sum((lane < r) ? wl[4 + lane] * (double)Fq[l] : 0.0);
+        bv[l] = wl[l] + t;
+      }
+    } else {
+      // FP64 refinement of c through the fine stencil of A(omega)
+      const int cx = cell % d.nc, cy = cell / d.nc;
+      const double* ac = A.a + ((size_t)s * d.nf + cy * rho) * d.nf + cx * rho;
+      double cq[4];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) cq[l] = (lane < r) ? (double)Fq[l] : 0.0;
+      for (int it = 0; it <= A.refine; ++it) {
+        if (lane < 32) {
+#pragma unroll
+          for (int l = 0; l < 4; ++l) s_c[wib][lane][l] = cq[l];
+        }
+        __syncwarp();
+        // u_l = phibar_l + V c_l on all cell nodes
+        for (int v = lane; v < d.N2; v += 32) {
+          const double* wr = Wc + (size_t)v * P0;
+          double t[4] = {wr[0], wr[1], wr[2], wr[3]};
+          for (int q = 0; q < r; ++q) {
+            const double vq = wr[4 + q];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) t[l] += vq * s_c[wib][q][l];
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) s_u[wib][v][l] = t[l];
+        }
+        __syncwarp();
+        if (it == A.refine) break;
+        // (A u_l) at interior nodes by the 9-point stencil
+        for (int v = lane; v < d.N2; v += 32) {
+          const int i = v % NN, j = v / NN;
+          double t[4] = {0, 0, 0, 0};
+          if (i > 0 && j > 0 && i < rho && j < rho) {
+            const double aSW = ac[(size_t)(j - 1) * d.nf + i - 1], aSE = ac[(size_t)(j - 1) * d.nf + i];
+            const double aNE = ac[(size_t)j * d.nf + i], aNW = ac[(size_t)j * d.nf + i - 1];
+            const double cC = (2.0 / 3.0) * (aSW + aSE + aNE + aNW);
+            const double cW = -(aSW + aNW) / 6.0, cE = -(aSE + aNE) / 6.0;
+            const double cS = -(aSW + aSE) / 6.0, cN = -(aNE + aNW) / 6.0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              t[l] = cC * s_u[wib][v][l] + cW * s_u[wib][v - 1][l] + cE * s_u[wib][v + 1][l] +
+                     cS * s_u[wib][v - NN][l] + cN * s_u[wib][v + NN][l] -
+                     aSW / 3.0 * s_u[wib][v - NN - 1][l] - aSE / 3.0 * s_u[wib][v - NN + 1][l] -
+                     aNE / 3.0 * s_u[wib][v + NN + 1][l] - aNW / 3.0 * s_u[wib][v + NN - 1][l];
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) s_au[wib][v][l] = t[l];
+        }
+        __syncwarp();
+        // residual R_q = -zeta_q^T (A u) and the correction through the FP32 factor
+        float Rq[4] = {0.f, 0.f, 0.f, 0.f};
+        if (lane < r) {
+          double t[4] = {0, 0, 0, 0};
+          for (int v = 0; v < d.N2; ++v) {
+            const double vq = Wc[(size_t)v * P0 + 4 + lane];
+            if (vq != 0.0) {
+#pragma unroll
+              for (int l = 0; l < 4; ++l) t[l] += vq * s_au[wib][v][l];
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) Rq[l] = (float)(-t[l]);
+        }
+        small_fwd<0>(Mq, Rq, lane, r);
+        small_bwd<31>(Mq, Rq, lane, r);
+        if (lane < r) {
+#pragma unroll
+          for (int l = 0; l < 4; ++l) cq[l] += (double)Rq[l];
+        }
+        __syncwarp();
+      }
+      // K_e by the edge/diagonal difference form of the element energy, b_e
+      double M[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int e = lane; e < d.ne; e += 32) {
+        const int ex = e % rho, ey = e / rho;
+        const int n0 = ey * NN + ex, n1 = n0 + 1, n2 = n0 + NN + 1, n3 = n0 + NN;
+        const double ae = ac[(size_t)ey * d.nf + ex];
+        double dd[4][6];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const double c0 = s_u[wib][n0][l], c1 = s_u[wib][n1][l], c2 = s_u[wib][n2][l], c3 = s_u[wib][n3][l];
+          dd[l][0] = c0 - c1; dd[l][1] = c1 - c2; dd[l][2] = c2 - c3;
+          dd[l][3] = c3 - c0; dd[l][4] = c0 - c2; dd[l][5] = c1 - c3;
+        }
+        int q = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+          for (int lp = l; lp < 4; ++lp) {
+            M[q++] += ae * (dd[l][0] * dd[lp][0] + dd[l][1] * dd[lp][1] + dd[l][2] * dd[lp][2] +
+                            dd[l][3] * dd[lp][3] + 2.0 * (dd[l][4] * dd[lp][4] + dd[l][5] * dd[lp][5]));
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < 10; ++q) Kv[q] = warp_sum(M[q]) / 6.0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const double t = warp_sum((lane < r) ? wl[4 + lane] * s_c[wib][lane][l] : 0.0);
+        bv[l] = wl[l] + t;
+      }
+    }
+    const bool fail = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) Ke[q] = fail ? nanv : Kv[q];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) be[l] = fail ? nanv : bv[l];
+      if (A.status) A.status[u] = fail ? STOMSFEM_ENOTSPD : 0;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace stomsfem
+
+using namespace stomsfem;
+
+struct stomsfem_pod {
+  PodDims d;
+  int max_rank;
+  double* W = nullptr;          // [cell][N2][P0]
+  double* wl = nullptr;         // [cell][P0]
+  double* lam = nullptr;        // [cell][n]
+  __nv_bfloat16* T = nullptr;   // [cell][Ppad][kPodK]
+  int32_t* ranks = nullptr;     // [cell]
+  int32_t* err = nullptr;       // [1] device error word
+};
+
+static void pod_free(stomsfem_pod* p) {
+  if (!p) return;
+  cudaFree(p->W);
+  cudaFree(p->wl);
+  cudaFree(p->lam);
+  cudaFree(p->T);
+  cudaFree(p->ranks);
+  cudaFree(p->err);
+  delete p;
+}
+
+extern "C" int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap,
+                                  const double* a_train, int32_t S_train, double tol,
+                                  int32_t max_rank, const int32_t* ranks_in, stomsfem_pod** out,
+                                  int32_t* ranks_out, stomsfem_stream_t stream) {
+  if (!grid || !out || grid->nf <= 0 || grid->nc <= 0 || grid->nf % grid->nc)
+    return set_error(STOMSFEM_EINVAL, "bad grid / out");
+  const int rho = grid->nf / grid->nc;
+  if (rho < 2 || rho > kPodMaxRho)
+    return set_error(STOMSFEM_EINVAL, "POD needs 2 <= H/h <= %d (got %d)", kPodMaxRho, rho);
+  if (S_train < 1 || !phi_snap || !a_train) return set_error(STOMSFEM_EINVAL, "no training data");
+  if (max_rank < 1 || max_rank > kPodMaxRank)
+    return set_error(STOMSFEM_EINVAL, "max_rank must be in [1, %d]", kPodMaxRank);
+  if (!(tol > 0.0) && !ranks_in) return set_error(STOMSFEM_EINVAL, "tol must be > 0");
+  *out = nullptr;
+  stomsfem_pod* p = new stomsfem_pod();
+  PodDims& d = p->d;
+  d.nf = grid->nf;
+  d.nc = grid->nc;
+  d.rho = rho;
+  d.N2 = (rho + 1) * (rho + 1);
+  d.n = (rho - 1) * (rho - 1);
+  d.ne = rho * rho;
+  d.ncell = grid->nc * grid->nc;
+  d.f = grid->f;
+  const int rcap = max_rank < d.n ? max_rank : d.n;
+  d.P0 = 4 + rcap;
+  d.P = d.P0 * (d.P0 + 1) / 2;
+  d.Ppad = (d.P + 15) & ~15;
+  p->max_rank = rcap;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int32_t* rin_d = nullptr;
+  double *phibar = nullptr, *abar = nullptr, *cov = nullptr;
+  auto fail = [&](int rc) {
+    cudaFree(rin_d);
+    cudaFree(phibar);
+    cudaFree(abar);
+    cudaFree(cov);
+    pod_free(p);
+    return rc;
+  };
+  int rc;
+#define TRY(x)                                   \
+  if ((rc = check_cuda((x), #x)) != STOMSFEM_OK) \
+    return fail(rc);
+  TRY(cudaMalloc(&p->W, sizeof(double) * d.ncell * d.N2 * d.P0));
+  TRY(cudaMalloc(&p->wl, sizeof(double) * d.ncell * d.P0));
+  TRY(cudaMalloc(&p->lam, sizeof(double) * d.ncell * d.n));
+  TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * kPodK));
+  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell));
+  TRY(cudaMalloc(&p->err, sizeof(int32_t)));
+  TRY(cudaMalloc(&phibar, sizeof(double) * d.ncell * 4 * d.N2));
+  TRY(cudaMalloc(&abar, sizeof(double) * d.ncell * d.ne));
+  TRY(cudaMalloc(&cov, sizeof(double) * d.ncell * d.n * d.n));
+  TRY(cudaMemsetAsync(p->err, 0, sizeof(int32_t), st));
+  if (ranks_in) {
+    TRY(cudaMalloc(&rin_d, sizeof(int32_t) * d.ncell));
+    TRY(cudaMemcpyAsync(rin_d, ranks_in, sizeof(int32_t) * d.ncell, cudaMemcpyHostToDevice, st));
+  }
+  pod_mean_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, a_train, S_train, phibar, abar);
+  pod_cov_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
+  const size_t eig_smem = sizeof(double) * 3 * (kPodMaxN + 1) * (kPodMaxN + 1);
+  TRY(cudaFuncSetAttribute(pod_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem));
+  pod_eig_kernel<<<d.ncell, 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W, p->lam,
+                                          p->ranks, p->err);
+  pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->wl);
+  TRY(cudaGetLastError());
+  int32_t herr = 0;
+  TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  std::vector<int32_t> rk(d.ncell);
+  TRY(cudaMemcpyAsync(rk.data(), p->ranks, sizeof(int32_t) * d.ncell, cudaMemcpyDeviceToHost, st));
+  TRY(cudaStreamSynchronize(st));
+#undef TRY
+  if (herr != 0) return fail(set_error(STOMSFEM_ENOTSPD, "training-mean energy matrix not positive definite"));
+  if (ranks_out) std::memcpy(ranks_out, rk.data(), sizeof(int32_t) * d.ncell);
+  cudaFree(rin_d);
+  cudaFree(phibar);
+  cudaFree(abar);
+  cudaFree(cov);
+  *out = p;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_destroy(stomsfem_pod* pod) {
+  pod_free(pod);
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host) {
+  if (!pod || !lam_host) return set_error(STOMSFEM_EINVAL, "NULL argument");
+  STOMSFEM_TRY_CUDA(cudaMemcpy(lam_host, pod->lam, sizeof(double) * pod->d.ncell * pod->d.n,
+                               cudaMemcpyDeviceToHost));
+  return STOMSFEM_OK;
+}
+
+static size_t pod_ws_layout(const PodDims& d, int S, size_t* off_G) {
+  const int Spad = (S + kPodTileM - 1) / kPodTileM * kPodTileM;
+  const size_t ab = ((size_t)d.ncell * Spad * kPodK * 2 + 1023) & ~size_t(1023);
+  *off_G = ab;
+  return ab + (size_t)d.ncell * Spad * d.Ppad * 4;
+}
+
+extern "C" int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* bytes) {
+  if (!pod || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  size_t og;
+  *bytes = pod_ws_layout(pod->d, S, &og);
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S,
+                                    int32_t refine_iters, double* Ke, double* be,
+                                    int32_t* unit_status, void* workspace, size_t workspace_bytes,
+                                    stomsfem_stream_t stream) {
+  if (!pod) return set_error(STOMSFEM_EINVAL, "pod is NULL");
+  if (S < 0 || refine_iters < 0 || refine_iters > 16) return set_error(STOMSFEM_EINVAL, "bad S / refine_iters");
+  if (S == 0) return STOMSFEM_OK;
+  if (!a || !Ke || !be || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  const PodDims& d = pod->d;
+  size_t og;
+  const size_t need = pod_ws_layout(d, S, &og);
+  if (workspace_bytes < need) return set_error(STOMSFEM_ENOMEM, "POD workspace %zu < %zu", workspace_bytes, need);
+  const int Spad = (S + kPodTileM - 1) / kPodTileM * kPodTileM;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  auto* Ab = reinterpret_cast<__nv_bfloat16*>(workspace);
+  float* G = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + og);
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  pod_gather_kernel<<<sms * 8, 256, 0, st>>>(d, a, S, Spad, Ab);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  const size_t smem = 1024 + (size_t)kPodTileM * 128 + (size_t)d.Ppad * 128;
+  const size_t smem_req = smem < 120 * 1024 ? 120 * 1024 : smem;  // one CTA per SM (TMEM)
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(pod_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_req));
+  dim3 grd(Spad / kPodTileM, d.ncell);
+  pod_gemm_kernel<<<grd, 128, smem_req, st>>>(d, Spad, Ab, pod->T, G, pod->err);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  PodSolveArgs A;
+  A.d = d;
+  A.S = S;
+  A.Spad = Spad;
+  A.refine = refine_iters;
+  A.G = G;
+  A.W = pod->W;
+  A.wl = pod->wl;
+  A.ranks = pod->ranks;
+  A.a = a;
+  A.Ke = Ke;
+  A.be = be;
+  A.status = unit_status;
+  A.err = pod->err;
+  const long long units = (long long)S * d.ncell;
+  long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
+  if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+  pod_solve_kernel<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}

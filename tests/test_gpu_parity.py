@@ -220,3 +220,64 @@ def test_status_on_indefinite_unit(orc):
     assert np.all(np.isnan(Kg[0][bad]))
     good = ~bad
     assert np.all(np.isfinite(Kg[0][good]))
+
+
+def _assemble_residual(Ke, be, u, nc):
+    """|| S u - b || / ||b|| for the coarse system assembled from K_e, b_e
+    (written out here independently of both the library and the oracle)."""
+    NN = nc + 1
+    r = np.zeros(NN * NN)
+    b = np.zeros(NN * NN)
+    loc = [(0, 0), (1, 0), (1, 1), (0, 1)]
+    for cell in range(nc * nc):
+        cx, cy = cell % nc, cell // nc
+        K = np.zeros((4, 4))
+        q = 0
+        for l in range(4):
+            for lp in range(l, 4):
+                K[l, lp] = K[lp, l] = Ke[cell, q]
+                q += 1
+        idx = [(cy + dy) * NN + cx + dx for (dx, dy) in loc]
+        r[idx] += K @ u[idx]
+        b[idx] += be[cell]
+    inner = np.zeros((NN, NN), dtype=bool)
+    inner[1:-1, 1:-1] = True
+    inner = inner.reshape(-1)
+    return np.linalg.norm((r - b)[inner]) / np.linalg.norm(b[inner])
+
+
+def test_full_size_contrast_2048_sampled(orc):
+    """High-contrast workload at full size (2048^2 fine, 64^2 coarse, contrast
+    1e4, 32x32 bumps, xi ~ N(0,1)): sampled units against the oracle (which
+    evaluates the coefficient on each sampled patch itself), and the coarse
+    solve checked through the residual of the assembled coarse system."""
+    w = W.workload("contrast_2048")
+    S, nf, nc = 2, w["nf"], w["nc"]
+    xi = W.draw_xi(w["field"], S, w["seed"], w["dist"])
+    g = api.grid(nf, nc, w["f"])
+    a = torch.empty((S, nf, nf), dtype=torch.float64, device=DEV)
+    api.stomsfem_sample_coef(g, api.field_from_dict(w["field"]), torch.from_numpy(xi).to(DEV), a)
+    res = {}
+    for prec in (api.FP64, api.FP32_REFINED, api.FP32):
+        Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=DEV)
+        be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=DEV)
+        api.stomsfem_upscale(g, a, Ke, be, precision=prec)
+        res[prec] = (Ke, be)
+    u = torch.empty((S, (nc + 1) ** 2), dtype=torch.float64, device=DEV)
+    api.stomsfem_coarse_solve(g, res[api.FP64][0], res[api.FP64][1], u)
+    torch.cuda.synchronize()
+    rho = nf // nc
+    r = np.random.default_rng(5)
+    for u_ in list(r.choice(S * nc * nc, size=6, replace=False)) + [S * nc * nc - 1]:
+        s, cell = divmod(int(u_), nc * nc)
+        cx, cy = cell % nc, cell // nc
+        ao = orc.sample_coef_window(nf, w["field"], xi[s], cx * rho, (cx + 1) * rho, cy * rho,
+                                    (cy + 1) * rho)
+        Ko, bo, _, _ = orc.cell(nf, nc, w["f"], ao, cx, cy, 0)
+        for prec, (Ke, be) in res.items():
+            k = Ke[s, cell].cpu().numpy()
+            assert np.linalg.norm(k - Ko) / np.linalg.norm(Ko) <= TOL[prec], (prec, u_)
+            assert np.linalg.norm(be[s, cell].cpu().numpy() - bo) / np.linalg.norm(bo) <= TOL[prec]
+    Kn, bn, un = res[api.FP64][0].cpu().numpy(), res[api.FP64][1].cpu().numpy(), u.cpu().numpy()
+    for s in range(S):
+        assert _assemble_residual(Kn[s], bn[s], un[s], nc) <= 1e-10

@@ -345,3 +345,12 @@ def test_workload_msfem_64_smoke(orc):
     r = w["nf"] // w["nc"]
     uf_c = uf.reshape(w["nf"] + 1, -1)[::r, ::r].reshape(-1)
     assert np.linalg.norm(u[0] - uf_c) / np.linalg.norm(uf_c) < 0.1
+
+
+def test_field_window_matches_full_field(orc):
+    field = dict(kind=1, nbx=3, nby=2, width=0.2, contrast_log=math.log(1e4), gain=8.0)
+    xi = np.random.default_rng(4).standard_normal((1, 6))
+    full = orc.sample_coef(24, field, xi)[0]
+    win = orc.sample_coef_window(24, field, xi[0], 5, 17, 3, 11)
+    np.testing.assert_array_equal(win[3:11, 5:17], full[3:11, 5:17])
+    assert np.isnan(win[0, 0])
