@@ -218,6 +218,66 @@ int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t 
                          double* Ke, double* be, int32_t* unit_status, void* workspace,
                          size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Learned surrogate of the local upscaled quantities (stands in for the
+ * random-interpolation model of S^m(xi_m), b^m(xi_m), Sec. 3.1, Algs. 1-2;
+ * the cell problem depends on the local parameters xi_m only, Eq. MsFEB2).
+ * Cells without oversampling.  Per patch family an MLP
+ *   16 -> 128 -> 128 -> 128 -> 16 (GELU), weights [out][in] per layer,
+ *   flat FP32 layout per family: W1[128][16] b1[128] W2[128][128] b2[128]
+ *   W3[128][128] b3[128] W4[16][128] b4[16]  (37264 floats),
+ * maps the zero-padded xi_m to y; targets y_0..9 = K_e/abar - K_ref,
+ * y_10..12 = b_l/(f H^2) - 1/4 (abar = mean of a over the cell).
+ * ------------------------------------------------------------------- */
+typedef struct stomsfem_surrogate stomsfem_surrogate; /* opaque, library-owned */
+
+typedef struct {
+  int32_t steps;      /* Adam steps (minibatches of 64 rows per family) */
+  double lr, lr_min;  /* cosine decay from lr to lr_min */
+  double beta1, beta2, eps;
+  uint64_t seed;      /* minibatch selection (splitmix64 of seed, family, step, row) */
+} stomsfem_surrogate_cfg;
+
+/* Local parameters of every cell (host computation, no GPU): variable i is
+ * local to a cell when exp(-d^2/width^2) >= tau, d the distance from bump
+ * centre i to the closed cell rectangle; per cell sorted by the centre's
+ * offset from the cell's south-west corner (y then x).  Cells with equal
+ * offset lists form one family.  Outputs (host, any may be NULL):
+ * k_per_cell [nc*nc], var_ids [nc*nc][16] (-1 padded), family [nc*nc],
+ * n_families.  EINVAL if a cell has more than 16 local variables. */
+int stomsfem_local_vars(const stomsfem_grid* grid, const stomsfem_field* field, double tau,
+                        int32_t* k_per_cell, int32_t* var_ids, int32_t* family,
+                        int32_t* n_families);
+
+/* Creates a surrogate with the given initial weights (host [nfam][37264];
+ * the caller draws them, e.g. Xavier-uniform; query nfam with
+ * stomsfem_local_vars).  Allocates device memory (synchronous). */
+int stomsfem_surrogate_create(const stomsfem_grid* grid, const stomsfem_field* field, double tau,
+                              const float* init_weights, stomsfem_surrogate** out,
+                              int32_t* n_families);
+int stomsfem_surrogate_destroy(stomsfem_surrogate* sg);
+/* Copies the FP32 master weights to host [nfam][37264] (synchronous). */
+int stomsfem_surrogate_weights(const stomsfem_surrogate* sg, float* w_host);
+
+/* Trains on the S samples' (xi, a, K_e, b_e) (device: xi [S][nbx*nby],
+ * a [S][nf][nf], Ke [S][nc*nc][10], be [S][nc*nc][4], from the plain
+ * upscaler): one fused forward/backward/Adam kernel, one CTA per family;
+ * every 10th row of a family is held out.  loss_hist (host [steps] or NULL)
+ * receives the family-averaged training loss per step.  Allocates the
+ * training rows and synchronises `stream`.  Successive calls continue the
+ * Adam state and step count. */
+int stomsfem_surrogate_train(stomsfem_surrogate* sg, const stomsfem_surrogate_cfg* cfg,
+                             const double* xi, const double* a, const double* Ke, const double* be,
+                             int32_t S, float* loss_hist, stomsfem_stream_t stream);
+
+/* One forward/backward pass of the training kernel on a batch of exactly 64
+ * rows, no update: weights device [37264], X device [64][16], T device
+ * [64][16] (targets; columns 13..15 ignored), grad device [37264] receives
+ * d loss / d weights for loss = mean over rows and the 13 used outputs of
+ * (y - T)^2; loss device [1] or NULL.  Synchronous.  For gradient checks. */
+int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, float* grad,
+                            float* loss, stomsfem_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,7 +56,21 @@ _SIG = {
     "stomsfem_pod_eigenvalues": (ctypes.c_int, [_P, _P]),
     "stomsfem_pod_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_pod_upscale": (ctypes.c_int, [_P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "stomsfem_local_vars": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double,
+                                           _P, _P, _P, _P]),
+    "stomsfem_surrogate_create": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field),
+                                                 ctypes.c_double, _P, ctypes.POINTER(_P), _P]),
+    "stomsfem_surrogate_destroy": (ctypes.c_int, [_P]),
+    "stomsfem_surrogate_weights": (ctypes.c_int, [_P, _P]),
+    "stomsfem_surrogate_train": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
+    "stomsfem_surrogate_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
 }
+
+
+class SurrogateCfg(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("lr", ctypes.c_double), ("lr_min", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
 
 
 def lib(path: str | None = None):

@@ -154,3 +154,88 @@ def stomsfem_pod_upscale(h, g: Grid, a, Ke, be, refine_iters=0, unit_status=None
         _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
         _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
         _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
+# ---------------------------------------------------------------- surrogate
+
+SURROGATE_PARAMS = 37264
+SURROGATE_IN = 16
+
+
+def stomsfem_local_vars(g: Grid, fld: Field, tau):
+    """(k [ncell], var_ids [ncell][16], family [ncell], n_families) -- host."""
+    import numpy as np
+    ncell = g.nc * g.nc
+    k = np.zeros(ncell, dtype=np.int32)
+    ids = np.zeros((ncell, SURROGATE_IN), dtype=np.int32)
+    fam = np.zeros(ncell, dtype=np.int32)
+    nf = ctypes.c_int32()
+    L.check(L.lib().stomsfem_local_vars(ctypes.byref(g), ctypes.byref(fld), float(tau),
+                                        k.ctypes.data_as(ctypes.c_void_p),
+                                        ids.ctypes.data_as(ctypes.c_void_p),
+                                        fam.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf)))
+    return k, ids, fam, nf.value
+
+
+def xavier_weights(n_families, seed):
+    """Seeded Xavier-uniform initial weights in the flat [out][in] layout
+    (biases zero); the random draw the training starts from."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    shapes = [(128, 16), (128,), (128, 128), (128,), (128, 128), (128,), (16, 128), (16,)]
+    out = np.zeros((n_families, SURROGATE_PARAMS), dtype=np.float32)
+    for f in range(n_families):
+        parts = []
+        for s in shapes:
+            if len(s) == 2:
+                lim = (6.0 / (s[0] + s[1])) ** 0.5
+                parts.append(rng.uniform(-lim, lim, size=s).astype(np.float32).reshape(-1))
+            else:
+                parts.append(np.zeros(s, dtype=np.float32))
+        out[f] = np.concatenate(parts)
+    return out
+
+
+def stomsfem_surrogate_create(g: Grid, fld: Field, tau, init_weights):
+    import numpy as np
+    w = np.ascontiguousarray(init_weights, dtype=np.float32)
+    h = ctypes.c_void_p()
+    nfam = ctypes.c_int32()
+    L.check(L.lib().stomsfem_surrogate_create(ctypes.byref(g), ctypes.byref(fld), float(tau),
+                                              w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h),
+                                              ctypes.byref(nfam)))
+    return h, nfam.value
+
+
+def stomsfem_surrogate_destroy(h):
+    L.check(L.lib().stomsfem_surrogate_destroy(h))
+
+
+def stomsfem_surrogate_weights(h, n_families):
+    import numpy as np
+    w = np.empty((n_families, SURROGATE_PARAMS), dtype=np.float32)
+    L.check(L.lib().stomsfem_surrogate_weights(h, w.ctypes.data_as(ctypes.c_void_p)))
+    return w
+
+
+def stomsfem_surrogate_train(h, xi, a, Ke, be, steps, lr=1e-3, lr_min=1e-5, seed=0, beta1=0.9,
+                             beta2=0.999, eps=1e-8, stream=None):
+    """Returns the per-step training loss (family mean) as a numpy array."""
+    import numpy as np
+    S = xi.shape[0]
+    cfg = L.SurrogateCfg(int(steps), float(lr), float(lr_min), float(beta1), float(beta2), float(eps),
+                         int(seed))
+    loss = np.empty(int(steps), dtype=np.float32)
+    L.check(L.lib().stomsfem_surrogate_train(
+        h, ctypes.byref(cfg), _dev(xi, torch.float64, None, "xi"), _dev(a, torch.float64, None, "a"),
+        _dev(Ke, torch.float64, None, "Ke"), _dev(be, torch.float64, None, "be"), S,
+        loss.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return loss
+
+
+def stomsfem_surrogate_grad(weights, X, T, grad, loss=None, stream=None):
+    L.check(L.lib().stomsfem_surrogate_grad(
+        _dev(weights, torch.float32, (SURROGATE_PARAMS,), "weights"),
+        _dev(X, torch.float32, (64, 16), "X"), _dev(T, torch.float32, (64, 16), "T"),
+        _dev(grad, torch.float32, (SURROGATE_PARAMS,), "grad"), _dev(loss, torch.float32, (1,), "loss"),
+        _stream(stream)))

@@ -177,3 +177,37 @@ def test_zero_row_sum_projector():
     np.testing.assert_allclose(Pm @ k, k, atol=1e-14)
     y = r.standard_normal(10)
     np.testing.assert_allclose(unpack_upper(Pm @ y).sum(axis=1), 0.0, atol=1e-13)
+
+
+def test_surrogate_flat_layout_gradient():
+    """The surrogate oracle's flat-layout loss gradient (13 used outputs)
+    against central differences."""
+    from oracle import surrogate as S
+    r = np.random.default_rng(0)
+    w = r.standard_normal(S.N_PARAMS) * 0.05
+    X = r.standard_normal((8, 16))
+    T = r.standard_normal((8, 16))
+    L, g = S.loss_and_grad(w, X, T)
+
+    def lossf(wv):
+        return float(np.mean((S.forward(wv, X) - T)[:, :13] ** 2))
+
+    assert L == pytest.approx(lossf(w), rel=1e-14)
+    for idx in [0, 2047, 2100, 5000, 20000, 35000, 37250, 37260]:
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += 1e-6
+        wm[idx] -= 1e-6
+        assert g[idx] == pytest.approx((lossf(wp) - lossf(wm)) / 2e-6, rel=1e-6, abs=1e-10)
+    # outputs 13..15 carry no loss: their last-layer rows have zero gradient
+    o = S.N_PARAMS - 16 - 16 * 128
+    assert np.all(g[o + 13 * 128:o + 16 * 128] == 0) and np.all(g[-3:] == 0)
+
+
+def test_surrogate_predict_structure():
+    from oracle import surrogate as S, unpack_upper
+    r = np.random.default_rng(1)
+    K, b = S.predict(r.standard_normal(16) * 0.1, 2.5, 1.3, 0.125)
+    np.testing.assert_allclose(unpack_upper(K).sum(axis=1), 0.0, atol=1e-14)
+    assert b.sum() == pytest.approx(1.3 * 0.125 ** 2, rel=1e-14)
+    K0, b0 = S.predict(np.zeros(16), 2.5, 1.0, 0.125)
+    np.testing.assert_allclose(K0, 2.5 * S.KREF_PACKED, rtol=1e-15)
