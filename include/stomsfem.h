@@ -278,6 +278,26 @@ int stomsfem_surrogate_train(stomsfem_surrogate* sg, const stomsfem_surrogate_cf
 int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, float* grad,
                             float* loss, stomsfem_stream_t stream);
 
+/* Scratch of stomsfem_surrogate_infer for S samples. */
+int stomsfem_surrogate_workspace_size(const stomsfem_surrogate* sg, int32_t S, size_t* bytes);
+
+/* Inference with fallback for S samples (device: xi [S][nbx*nby],
+ * a [S][nf][nf]).  Every (sample, cell) unit goes through its family's
+ * network on the tensor cores (BF16 operands, FP32 accumulation, one
+ * 128-unit tile per CTA); the 10 outputs are projected onto symmetric
+ * zero-row-sum matrices and scaled by abar.  Error indicator, per unit:
+ * an input outside the family's training range (1% margin); for the x- and
+ * y-linear corner vectors v, v^T K v outside [ahar (1 - delta),
+ * abar (1 + delta)] (harmonic and arithmetic cell means of a: the energy
+ * bounds of the cell problem with affine data); K not positive definite
+ * on the complement of the constants.  Flagged units (fell_back device
+ * [S][nc*nc] uint8 set to 1) are recomputed by the plain FP64 upscaler in
+ * the same call.  Outputs Ke [S][nc*nc][10], be [S][nc*nc][4] (device).
+ * A device-side wait that ran out flags every unit (all fall back). */
+int stomsfem_surrogate_infer(stomsfem_surrogate* sg, const double* xi, const double* a, int32_t S,
+                             double delta, double* Ke, double* be, uint8_t* fell_back,
+                             void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,9 @@ _SIG = {
     "stomsfem_surrogate_weights": (ctypes.c_int, [_P, _P]),
     "stomsfem_surrogate_train": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "stomsfem_surrogate_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "stomsfem_surrogate_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_surrogate_infer": (ctypes.c_int, [_P, _P, _P, _I, ctypes.c_double, _P, _P, _P, _P, _SZ,
+                                                _P]),
 }
 
 

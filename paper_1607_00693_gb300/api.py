@@ -239,3 +239,23 @@ def stomsfem_surrogate_grad(weights, X, T, grad, loss=None, stream=None):
         _dev(X, torch.float32, (64, 16), "X"), _dev(T, torch.float32, (64, 16), "T"),
         _dev(grad, torch.float32, (SURROGATE_PARAMS,), "grad"), _dev(loss, torch.float32, (1,), "loss"),
         _stream(stream)))
+
+
+def stomsfem_surrogate_workspace_size(h, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_surrogate_workspace_size(h, int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_surrogate_infer(h, g: Grid, xi, a, Ke, be, fell_back, delta=0.02, workspace=None,
+                             stream=None):
+    S = xi.shape[0]
+    ncell = g.nc * g.nc
+    if workspace is None:
+        workspace = torch.empty(stomsfem_surrogate_workspace_size(h, S), dtype=torch.uint8,
+                                device=xi.device)
+    L.check(L.lib().stomsfem_surrogate_infer(
+        h, _dev(xi, torch.float64, None, "xi"), _dev(a, torch.float64, (S, g.nf, g.nf), "a"), S,
+        float(delta), _dev(Ke, torch.float64, (S, ncell, 10), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"), _dev(fell_back, torch.uint8, (S, ncell), "fell_back"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))

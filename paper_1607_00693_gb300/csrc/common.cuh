@@ -13,6 +13,12 @@ int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 int device_sm_count();
 
+// Internal: FP64 upscaling of a device-side list of units (no oversampling).
+int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, const int32_t* unit_list,
+                      const int32_t* unit_count, double* Ke, double* be, void* workspace,
+                      size_t workspace_bytes, cudaStream_t st);
+size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
+
 #define STOMSFEM_TRY_CUDA(expr)                                  \
   do {                                                           \
     int _rc = ::stomsfem::check_cuda((expr), #expr);             \

@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "stomsfem.h"
+#include "tc_gemm.cuh"
 
 namespace stomsfem {
 
@@ -368,6 +369,265 @@ __global__ void surrogate_box_kernel(const int* __restrict__ fam_row0, const flo
   box[(fm * kIn + j) * 2 + 1] = hi;
 }
 
+// ---------------------------------------------------------------- inference
+
+constexpr int kInPad = 64;    // input features padded to one 128-byte K row
+constexpr int kTile = 128;    // rows (units) per CTA
+// BF16 weights of one family, K-major rows ready for the tensor core:
+// W1 [128][64], W2 [128][128], W3 [128][128], W4 [16][128]
+constexpr int kWb1 = 0, kWb2 = kWb1 + kHid * kInPad, kWb3 = kWb2 + kHid * kHid, kWb4 = kWb3 + kHid * kHid,
+              kWbSize = kWb4 + kOut * kHid;
+
+__global__ void surrogate_pack_kernel(int nfam, const float* __restrict__ W, __nv_bfloat16* __restrict__ Wb) {
+  const long long total = (long long)nfam * kWbSize;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / kWbSize), e = (int)(idx % kWbSize);
+    const float* w = W + (size_t)f * kParams;
+    float v;
+    if (e < kWb2) {
+      const int o = e / kInPad, i = e % kInPad;
+      v = i < kIn ? w[oW1 + o * kIn + i] : 0.f;
+    } else if (e < kWb3) {
+      v = w[oW2 + (e - kWb2)];
+    } else if (e < kWb4) {
+      v = w[oW3 + (e - kWb3)];
+    } else {
+      v = w[oW4 + (e - kWb4)];
+    }
+    Wb[idx] = __float2bfloat16_rn(v);
+  }
+}
+
+// Rows of the inference batch grouped by family (each family padded to
+// whole 128-row tiles): X[row][64] BF16, unit_of_row[row]; per unit the
+// cell means abar (arithmetic) and ahar (harmonic) of a.
+__global__ void surrogate_infer_prepare_kernel(int S, int nc, int rho, int nf, int K, const double* __restrict__ xi,
+                                               const double* __restrict__ a, const int* __restrict__ var_ids,
+                                               const int* __restrict__ cell_fam, const int* __restrict__ cell_pos,
+                                               const int* __restrict__ fam_row0, const int* __restrict__ fam_ncell,
+                                               __nv_bfloat16* __restrict__ X, int* __restrict__ unit_of_row,
+                                               float* __restrict__ Xf, double* __restrict__ abar,
+                                               double* __restrict__ ahar) {
+  const int ncell = nc * nc;
+  const long long units = (long long)S * ncell;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(u / ncell), cell = (int)(u % ncell);
+    const int fm = cell_fam[cell];
+    const long long row = fam_row0[fm] + (long long)s * fam_ncell[fm] + cell_pos[cell];
+    for (int j = 0; j < kInPad; ++j) {
+      const int id = j < kIn ? var_ids[cell * kIn + j] : -1;
+      const float v = id >= 0 ? (float)xi[(size_t)s * K + id] : 0.f;
+      X[row * kInPad + j] = __float2bfloat16_rn(v);
+      if (j < kIn) Xf[u * kIn + j] = v;
+    }
+    unit_of_row[row] = (int)u;
+    const int cx = cell % nc, cy = cell / nc;
+    double sa = 0.0, si = 0.0;
+    for (int ey = 0; ey < rho; ++ey)
+      for (int ex = 0; ex < rho; ++ex) {
+        const double v = a[((size_t)s * nf + cy * rho + ey) * nf + cx * rho + ex];
+        sa += v;
+        si += 1.0 / v;
+      }
+    abar[u] = sa / (rho * rho);
+    ahar[u] = (rho * rho) / si;
+  }
+}
+
+struct InferArgs {
+  const __nv_bfloat16* X;
+  const int* unit_of_row;
+  const int* tile_fam;    // family of each 128-row tile
+  const __nv_bfloat16* Wb;
+  const float* W;         // FP32 master (biases)
+  const float* box;       // [nfam][16][2]
+  const float* Xf;        // [units][16] inputs (FP32) for the range check
+  const double* abar;
+  const double* ahar;
+  double f, H, delta, margin;
+  double* Ke;
+  double* be;
+  uint8_t* flag;
+  int32_t* err;
+};
+
+__device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int rows, int kblocks,
+                                           int ld, int tid) {
+  // src rows of ld BF16 (ld = 64 * kblocks) -> kblocks swizzled [rows][64] blocks
+  const int chunks = rows * kblocks * 8;
+  for (int c = tid; c < chunks; c += 128) {
+    const int row = c / (kblocks * 8), rem = c % (kblocks * 8), kb = rem / 8, ch = rem % 8;
+    const uint4 v = reinterpret_cast<const uint4*>(src + (size_t)row * ld + kb * 64)[ch];
+    *reinterpret_cast<uint4*>(dst + (size_t)kb * rows * 128 + tc::sw128_offset(row, ch * 8)) = v;
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
+  extern __shared__ __align__(1024) unsigned char ism_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ism_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sX = sm;                          // [128][64]            16 KB
+  unsigned char* sH = sX + kTile * 128;            // 2 x [128][64]        32 KB
+  unsigned char* sW1 = sH + 2 * kTile * 128;       // [128][64]            16 KB
+  unsigned char* sW2 = sW1 + kHid * 128;           // 2 x [128][64]        32 KB
+  unsigned char* sW3 = sW2 + 2 * kHid * 128;       // 2 x [128][64]        32 KB
+  unsigned char* sW4 = sW3 + 2 * kHid * 128;       // 2 x [16][64]          4 KB
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int fam = A.tile_fam[tile];
+  const float* Wm = A.W + (size_t)fam * kParams;
+  if (warp == 0) tc::tmem_alloc(&taddr_s, 128);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  const __nv_bfloat16* Wb = A.Wb + (size_t)fam * kWbSize;
+  stage_rows(sX, A.X + (size_t)tile * kTile * kInPad, kTile, 1, kInPad, tid);
+  stage_rows(sW1, Wb + kWb1, kHid, 1, kInPad, tid);
+  stage_rows(sW2, Wb + kWb2, kHid, 2, kHid, tid);
+  stage_rows(sW3, Wb + kWb3, kHid, 2, kHid, tid);
+  stage_rows(sW4, Wb + kWb4, kOut, 2, kHid, tid);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = taddr_s;
+  const uint32_t aX = tc::smem_u32(sX), aH = tc::smem_u32(sH);
+  const uint32_t aW[4] = {tc::smem_u32(sW1), tc::smem_u32(sW2), tc::smem_u32(sW3), tc::smem_u32(sW4)};
+  const int row = warp * 32 + lane;
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int layer = 0; layer < 4 && ok; ++layer) {
+    const int N = layer == 3 ? kOut : kHid;
+    const int ksteps = layer == 0 ? kInPad / 16 : kHid / 16;
+    if (tid == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTile, N);
+      for (int kk = 0; kk < ksteps; ++kk) {
+        const int kb = kk >> 2, ki = kk & 3;
+        const uint32_t a_addr = (layer == 0 ? aX : aH) + kb * (kTile * 128) + ki * 32;
+        const uint32_t b_addr = aW[layer] + kb * (N * 128) + ki * 32;
+        tc::mma_bf16(taddr, tc::sdesc_sw128(a_addr), tc::sdesc_sw128(b_addr), idesc, kk > 0 ? 1u : 0u);
+      }
+      tc::mma_commit(&mbar);
+    }
+    __syncwarp();
+    ok = tc::mbar_wait_bounded(&mbar, phase, 1u << 24);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok) break;
+    if (layer < 3) {
+      const int boff = layer == 0 ? oB1 : (layer == 1 ? oB2 : oB3);
+      for (int col = 0; col < kHid; col += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + col, v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          pk[q] = pack_bf16(gelu(v[2 * q] + Wm[boff + col + 2 * q]), gelu(v[2 * q + 1] + Wm[boff + col + 2 * q + 1]));
+        unsigned char* blk = sH + (col >> 6) * (kTile * 128);
+        const int k0 = col & 63;
+        *reinterpret_cast<uint4*>(blk + tc::sw128_offset(row, k0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(blk + tc::sw128_offset(row, k0 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(A.err, 2);
+  } else {
+    float y[16];
+    tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16), y);
+    const int u = A.unit_of_row[tile * kTile + row];
+    if (u >= 0) {
+      double yd[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) yd[q] = (double)y[q] + (double)Wm[oB4 + q];
+      // projection onto zero-row-sum symmetric 4x4 (packed): keep the 6
+      // off-diagonal entries o = B^T y / ... solved in closed form below
+      const double kref[10] = {4.0 / 6, -1.0 / 6, -2.0 / 6, -1.0 / 6, 4.0 / 6, -1.0 / 6, -2.0 / 6, 4.0 / 6, -1.0 / 6, 4.0 / 6};
+      // packed indices: diag 0,4,7,9; off (0,1)=1 (0,2)=2 (0,3)=3 (1,2)=5 (1,3)=6 (2,3)=8
+      const int offi[6] = {1, 2, 3, 5, 6, 8};
+      const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {1, 2, 3, 2, 3, 3};
+      const int diag[4] = {0, 4, 7, 9};
+      // least squares: minimise sum_off (o - y_off)^2 + sum_l (-sum_{j != l} o_lj - y_ll)^2
+      // normal equations (I + E^T E) o = y_off - E^T y_diag, E the 4x6 incidence
+      double Mn[6][7];
+      for (int p = 0; p < 6; ++p) {
+        for (int q = 0; q < 6; ++q) {
+          int shared = (pa[p] == pa[q]) + (pa[p] == pb[q]) + (pb[p] == pa[q]) + (pb[p] == pb[q]);
+          Mn[p][q] = (p == q ? 1.0 : 0.0) + shared;
+        }
+        Mn[p][6] = yd[offi[p]] - yd[diag[pa[p]]] - yd[diag[pb[p]]];
+      }
+      for (int c = 0; c < 6; ++c) {  // SPD: elimination without pivoting
+        const double piv = 1.0 / Mn[c][c];
+        for (int r2 = c + 1; r2 < 6; ++r2) {
+          const double fct = Mn[r2][c] * piv;
+          for (int k = c; k < 7; ++k) Mn[r2][k] -= fct * Mn[c][k];
+        }
+      }
+      double o[6];
+      for (int c = 5; c >= 0; --c) {
+        double t = Mn[c][6];
+        for (int k = c + 1; k < 6; ++k) t -= Mn[c][k] * o[k];
+        o[c] = t / Mn[c][c];
+      }
+      double Kp[10];
+      for (int q = 0; q < 10; ++q) Kp[q] = 0.0;
+      for (int p = 0; p < 6; ++p) {
+        Kp[offi[p]] = o[p];
+        Kp[diag[pa[p]]] -= o[p];
+        Kp[diag[pb[p]]] -= o[p];
+      }
+      const double ab = A.abar[u], ah = A.ahar[u];
+      double K[10];
+      for (int q = 0; q < 10; ++q) K[q] = ab * (kref[q] + Kp[q]);
+      const double fH2 = A.f * A.H * A.H;
+      double b[4];
+      for (int l = 0; l < 3; ++l) b[l] = fH2 * (0.25 + yd[10 + l]);
+      b[3] = fH2 - b[0] - b[1] - b[2];
+      // error indicator
+      bool bad = false;
+      const float* box = A.box + (size_t)fam * kIn * 2;
+      for (int j = 0; j < kIn; ++j) {
+        const float x = A.Xf[(size_t)u * kIn + j];
+        const float lo = box[2 * j], hi = box[2 * j + 1], m = (float)A.margin * (hi - lo);
+        if (x < lo - m || x > hi + m) bad = true;
+      }
+      // v = x-linear (0,1,1,0) and y-linear (0,0,1,1): harmonic <= v^T K v <= arithmetic mean
+      const double ex = K[4] + 2 * K[5] + K[7];
+      const double ey = K[7] + 2 * K[8] + K[9];
+      if (!(ex >= ah * (1 - A.delta) && ex <= ab * (1 + A.delta))) bad = true;
+      if (!(ey >= ah * (1 - A.delta) && ey <= ab * (1 + A.delta))) bad = true;
+      // positive definite on the complement of the constants: leading minors of rows/cols 0..2
+      const double m1 = K[0], m2 = K[0] * K[4] - K[1] * K[1];
+      const double m3 = K[0] * (K[4] * K[7] - K[5] * K[5]) - K[1] * (K[1] * K[7] - K[5] * K[2]) +
+                        K[2] * (K[1] * K[5] - K[4] * K[2]);
+      if (!(m1 > 0 && m2 > 0 && m3 > 0)) bad = true;
+      for (int q = 0; q < 10; ++q) A.Ke[(size_t)u * 10 + q] = K[q];
+      for (int l = 0; l < 4; ++l) A.be[(size_t)u * 4 + l] = b[l];
+      A.flag[u] = bad ? 1 : 0;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 128);
+}
+
+// Units whose indicator fired (or every unit after a device-side failure).
+__global__ void surrogate_compact_kernel(long long units, uint8_t* __restrict__ flag, const int32_t* __restrict__ err,
+                                         int32_t* __restrict__ list, int32_t* __restrict__ count) {
+  const bool all = err[0] != 0;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    if (all) flag[u] = 1;
+    if (flag[u]) list[atomicAdd(count, 1)] = (int32_t)u;
+  }
+}
+
 }  // namespace stomsfem
 
 using namespace stomsfem;
@@ -641,4 +901,122 @@ extern "C" int stomsfem_surrogate_grad(const float* weights, const float* X, con
   if (rc == STOMSFEM_OK) rc = check_cuda(cudaStreamSynchronize(st), "sync");
   cudaFree(row0_d);
   return rc;
+}
+
+namespace {
+
+struct InferLayout {
+  size_t X, uor, Xf, abar, ahar, Wb, tfam, list, count, err, fb, total;
+  long long rows_pad, units;
+  int ntiles;
+};
+
+InferLayout infer_layout(const stomsfem_surrogate* h, int S, std::vector<int>* row0, std::vector<int>* tfam) {
+  InferLayout L;
+  long long rows = 0;
+  int tiles = 0;
+  if (row0) row0->assign(h->nfam + 1, 0);
+  if (tfam) tfam->clear();
+  for (int f = 0; f < h->nfam; ++f) {
+    const long long n = (long long)S * h->fam_ncell[f];
+    const int t = (int)((n + kTile - 1) / kTile);
+    if (row0) (*row0)[f] = (int)rows;
+    if (tfam)
+      for (int i = 0; i < t; ++i) tfam->push_back(f);
+    rows += (long long)t * kTile;
+    tiles += t;
+  }
+  if (row0) (*row0)[h->nfam] = (int)rows;
+  L.rows_pad = rows;
+  L.ntiles = tiles;
+  L.units = (long long)S * h->ncell;
+  auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+  size_t o = 0;
+  L.X = o;    o += al(rows * kInPad * 2);
+  L.uor = o;  o += al(rows * 4);
+  L.Xf = o;   o += al(L.units * kIn * 4);
+  L.abar = o; o += al(L.units * 8);
+  L.ahar = o; o += al(L.units * 8);
+  L.Wb = o;   o += al((size_t)h->nfam * kWbSize * 2);
+  L.tfam = o; o += al((size_t)tiles * 4);
+  L.list = o; o += al(L.units * 4);
+  L.count = o; o += 1024;
+  L.err = o;  o += 1024;
+  L.fb = o;
+  o += upscale_slot_bytes_fp64(&h->grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 8;
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+extern "C" int stomsfem_surrogate_workspace_size(const stomsfem_surrogate* h, int32_t S, size_t* bytes) {
+  if (!h || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  *bytes = infer_layout(h, S, nullptr, nullptr).total;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi, const double* a, int32_t S,
+                                        double delta, double* Ke, double* be, uint8_t* fell_back,
+                                        void* workspace, size_t workspace_bytes, stomsfem_stream_t stream) {
+  if (!h || S < 0) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  if (S == 0) return STOMSFEM_OK;
+  if (!xi || !a || !Ke || !be || !fell_back || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  if (!(delta >= 0.0)) return set_error(STOMSFEM_EINVAL, "delta must be >= 0");
+  std::vector<int> row0, tfam;
+  const InferLayout L = infer_layout(h, S, &row0, &tfam);
+  if (workspace_bytes < L.total)
+    return set_error(STOMSFEM_ENOMEM, "surrogate workspace %zu < %zu", workspace_bytes, L.total);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  auto* X = reinterpret_cast<__nv_bfloat16*>(ws + L.X);
+  int* uor = reinterpret_cast<int*>(ws + L.uor);
+  float* Xf = reinterpret_cast<float*>(ws + L.Xf);
+  double* abar = reinterpret_cast<double*>(ws + L.abar);
+  double* ahar = reinterpret_cast<double*>(ws + L.ahar);
+  auto* Wb = reinterpret_cast<__nv_bfloat16*>(ws + L.Wb);
+  int* tf = reinterpret_cast<int*>(ws + L.tfam);
+  int32_t* list = reinterpret_cast<int32_t*>(ws + L.list);
+  int32_t* count = reinterpret_cast<int32_t*>(ws + L.count);
+  int32_t* err = reinterpret_cast<int32_t*>(ws + L.err);
+  const int rho = h->grid.nf / h->grid.nc;
+  // family row starts for the prepare kernel (device copy in the count slot's neighbour)
+  int* row0_d = reinterpret_cast<int*>(ws + L.list);  // reused before the list is written
+  STOMSFEM_TRY_CUDA(cudaMemcpyAsync(tf, tfam.data(), sizeof(int) * tfam.size(), cudaMemcpyHostToDevice, st));
+  STOMSFEM_TRY_CUDA(cudaMemcpyAsync(row0_d, row0.data(), sizeof(int) * row0.size(), cudaMemcpyHostToDevice, st));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(uor, 0xFF, L.rows_pad * 4, st));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(X, 0, L.rows_pad * kInPad * 2, st));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(count, 0, 8, st));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(err, 0, 8, st));
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  surrogate_pack_kernel<<<sms * 2, 256, 0, st>>>(h->nfam, h->W, Wb);
+  surrogate_infer_prepare_kernel<<<sms * 8, 128, 0, st>>>(S, h->grid.nc, rho, h->grid.nf, h->K, xi, a, h->var_ids_d,
+                                                         h->cell_fam_d, h->cell_pos_d, row0_d, h->fam_ncell_d, X, uor,
+                                                         Xf, abar, ahar);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  InferArgs A;
+  A.X = X;
+  A.unit_of_row = uor;
+  A.tile_fam = tf;
+  A.Wb = Wb;
+  A.W = h->W;
+  A.box = h->box;
+  A.Xf = Xf;
+  A.abar = abar;
+  A.ahar = ahar;
+  A.f = h->grid.f;
+  A.H = 1.0 / h->grid.nc;
+  A.delta = delta;
+  A.margin = 0.01;
+  A.Ke = Ke;
+  A.be = be;
+  A.flag = fell_back;
+  A.err = err;
+  const size_t smem = 1024 + kTile * 128 * 3 + kHid * 128 * 5 + kOut * 128 * 2;
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  surrogate_infer_kernel<<<L.ntiles, 128, smem, st>>>(A);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  surrogate_compact_kernel<<<sms * 4, 256, 0, st>>>(L.units, fell_back, err, list, count);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return upscale_list_fp64(&h->grid, a, S, list, count, Ke, be, ws + L.fb, L.total - L.fb, st);
 }

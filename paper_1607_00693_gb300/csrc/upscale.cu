@@ -217,6 +217,8 @@ struct UpscaleArgs {
   size_t slot_bytes, l_bytes;
   int bmax, nmax;
   long long units;
+  const int32_t* unit_list;   // optional: process only these units (device list)
+  const int32_t* unit_count;  // device length of unit_list
 };
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
@@ -241,7 +243,9 @@ upscale_kernel(UpscaleArgs A) {
   const int ncell = A.nc * A.nc;
   const int CN = (A.rho + 1) * (A.rho + 1);
 
-  for (long long u = gw; u < A.units; u += nw) {
+  const long long nwork = A.unit_list ? (long long)A.unit_count[0] : A.units;
+  for (long long w = gw; w < nwork; w += nw) {
+    const long long u = A.unit_list ? (long long)A.unit_list[w] : w;
     const int s = (int)(u / ncell);
     const int cell = (int)(u % ncell);
     const int cx = cell % A.nc, cy = cell / A.nc;
@@ -518,8 +522,62 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   A.bmax = bmax;
   A.nmax = nmax;
   A.units = units;
+  A.unit_list = nullptr;
+  A.unit_count = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (precision == STOMSFEM_FP64) return launch_rpl<double, double>(A, max_blocks, st);
   if (precision == STOMSFEM_FP32_REFINED) return launch_rpl<float, double>(A, max_blocks, st);
   return launch_rpl<float, float>(A, max_blocks, st);
 }
+
+namespace stomsfem {
+
+// FP64 upscaling of the units listed on the device (list and count device
+// pointers; the count is read by the kernel), no oversampling; used by the
+// surrogate's fallback.  Launches one grid sized to the resident warps.
+int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, const int32_t* unit_list,
+                      const int32_t* unit_count, double* Ke, double* be, void* workspace,
+                      size_t workspace_bytes, cudaStream_t st) {
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  int nmax, bmax;
+  patch_limits(grid, 0, &nmax, &bmax);
+  if (bmax > kMaxBand) return set_error(STOMSFEM_EINVAL, "bandwidth %d > %d", bmax, kMaxBand);
+  size_t sb, lb;
+  slot_layout(nmax, bmax, STOMSFEM_FP64, &sb, &lb);
+  const long long slots = (long long)(workspace_bytes / sb);
+  if (slots < kUpscaleWarps) return set_error(STOMSFEM_ENOMEM, "fallback workspace too small");
+  UpscaleArgs A;
+  A.a = a;
+  A.oversample = nullptr;
+  A.nf = grid->nf;
+  A.nc = grid->nc;
+  A.rho = grid->nf / grid->nc;
+  A.max_o = 0;
+  A.S = S;
+  A.f = grid->f;
+  A.refine = 0;
+  A.Ke = Ke;
+  A.be = be;
+  A.phi = nullptr;
+  A.status = nullptr;
+  A.ws = static_cast<unsigned char*>(workspace);
+  A.slot_bytes = sb;
+  A.l_bytes = lb;
+  A.bmax = bmax;
+  A.nmax = nmax;
+  A.units = (long long)S * grid->nc * grid->nc;
+  A.unit_list = unit_list;
+  A.unit_count = unit_count;
+  return launch_rpl<double, double>(A, slots / kUpscaleWarps, st);
+}
+
+size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
+  int nmax, bmax;
+  patch_limits(grid, 0, &nmax, &bmax);
+  size_t sb, lb;
+  slot_layout(nmax, bmax, STOMSFEM_FP64, &sb, &lb);
+  return sb;
+}
+
+}  // namespace stomsfem

@@ -72,3 +72,96 @@ def test_training_reduces_loss():
         assert loss[-20:].mean() < 0.05 * loss[:5].mean()
     finally:
         api.stomsfem_surrogate_destroy(h)
+
+
+def _infer(h, g, S, seed, delta=0.02):
+    w = W.workload("surrogate_64")
+    xi = W.draw_xi(w["field"], S, seed)
+    xt = torch.from_numpy(xi).to(DEV)
+    a = torch.empty((S, w["nf"], w["nf"]), dtype=torch.float64, device=DEV)
+    api.stomsfem_sample_coef(g, api.field_from_dict(w["field"]), xt, a)
+    nc2 = w["nc"] ** 2
+    Ke = torch.empty((S, nc2, 10), dtype=torch.float64, device=DEV)
+    be = torch.empty((S, nc2, 4), dtype=torch.float64, device=DEV)
+    fb = torch.empty((S, nc2), dtype=torch.uint8, device=DEV)
+    api.stomsfem_surrogate_infer(h, g, xt, a, Ke, be, fb, delta=delta)
+    Kp = torch.empty_like(Ke)
+    bp = torch.empty_like(be)
+    api.stomsfem_upscale(g, a, Kp, bp)
+    torch.cuda.synchronize()
+    return xi, a, Ke.cpu().numpy(), be.cpu().numpy(), fb.cpu().numpy(), Kp.cpu().numpy(), bp.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    w, g, xt, a, Ke, be = _training_set(1563, w_seed := W.workload("surrogate_64")["train_seed"])
+    fld = api.field_from_dict(w["field"])
+    _, _, _, nfam = api.stomsfem_local_vars(g, fld, 1e-6)
+    h, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.xavier_weights(nfam, 0))
+    loss = api.stomsfem_surrogate_train(h, xt, a, Ke, be, steps=3000, lr=2e-3, lr_min=2e-5, seed=w_seed)
+    yield w, g, h, nfam, loss
+    api.stomsfem_surrogate_destroy(h)
+
+
+def test_inference_matches_oracle_forward(trained):
+    """Units the indicator accepts: the tensor-core forward and the output
+    map agree with the FP64 oracle forward of the same weights (BF16
+    tolerance); units it flags are the plain FP64 upscaler's."""
+    from oracle import surrogate as S
+    import oracle
+    w, g, h, nfam, _ = trained
+    Wt = api.stomsfem_surrogate_weights(h, nfam)
+    xi, a, Ke, be, fb, Kp, bp = _infer(h, g, 24, 77)
+    k, ids, fam, _ = S.local_vars(w["nf"], w["nc"], w["field"], 1e-6)
+    an = a.cpu().numpy()
+    rho = w["nf"] // w["nc"]
+    H = 1.0 / w["nc"]
+    checked = 0
+    for s in range(0, 24, 3):
+        for cell in range(w["nc"] ** 2):
+            if fb[s, cell]:
+                np.testing.assert_allclose(Ke[s, cell], Kp[s, cell], rtol=1e-11, atol=1e-14)
+                continue
+            x = np.zeros(16)
+            x[:k[cell]] = xi[s, ids[cell, :k[cell]]]
+            y = S.forward(Wt[fam[cell]].astype(np.float64), x[None])[0]
+            cx, cy = cell % w["nc"], cell // w["nc"]
+            abar = an[s, cy * rho:(cy + 1) * rho, cx * rho:(cx + 1) * rho].mean()
+            Ko, bo = S.predict(y, abar, w["f"], H)
+            assert np.linalg.norm(Ke[s, cell] - Ko) <= 1e-2 * np.linalg.norm(Ko)
+            assert np.linalg.norm(be[s, cell] - bo) <= 1e-2 * np.linalg.norm(bo)
+            checked += 1
+    assert checked > 100
+    del oracle
+
+
+def test_trained_surrogate_coarse_error(trained):
+    """After training, surrogate K_e (with fallback) give coarse solutions
+    within 1e-3 (relative L2) of the plain FP64 upscaler's; an untrained
+    network of the same shape does far worse (or falls back everywhere)."""
+    w, g, h, nfam, loss = trained
+    xi, a, Ke, be, fb, Kp, bp = _infer(h, g, 200, w["seed"])
+    nc = w["nc"]
+
+    def coarse(K, b):
+        u = torch.empty((K.shape[0], (nc + 1) ** 2), dtype=torch.float64, device=DEV)
+        api.stomsfem_coarse_solve(g, torch.from_numpy(K).to(DEV), torch.from_numpy(b).to(DEV), u)
+        torch.cuda.synchronize()
+        return u.cpu().numpy()
+
+    us, up = coarse(Ke, be), coarse(Kp, bp)
+    err = np.linalg.norm(us - up, axis=1) / np.linalg.norm(up, axis=1)
+    rate = fb.mean()
+    print("surrogate coarse error max %.3e mean %.3e, fallback rate %.4f, final loss %.3e"
+          % (err.max(), err.mean(), rate, loss[-50:].mean()))
+    assert err.max() <= 1e-3
+    assert rate < 0.5
+    # the same network untrained
+    fld = api.field_from_dict(w["field"])
+    h0, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.xavier_weights(nfam, 0))
+    try:
+        _, _, K0, b0, fb0, _, _ = _infer(h0, g, 200, w["seed"], delta=1e9)
+        e0 = np.linalg.norm(coarse(K0, b0) - up, axis=1) / np.linalg.norm(up, axis=1)
+        assert fb0.mean() > 0.9 or e0.max() > 10 * err.max()
+    finally:
+        api.stomsfem_surrogate_destroy(h0)
