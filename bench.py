@@ -193,6 +193,143 @@ def run_reference(args, w, ov):
     return 0
 
 
+def _timed_call(stream, fn, reps=3):
+    """CUDA-event time (ms) of fn() on `stream`, after one warm-up call."""
+    import torch
+    with torch.cuda.stream(stream):
+        fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _coarse_err(api, g, Ka, ba, Kb, bb, dev):
+    import torch
+    S = Ka.shape[0]
+    ua = torch.empty((S, (g.nc + 1) ** 2), dtype=torch.float64, device=dev)
+    ub = torch.empty_like(ua)
+    api.stomsfem_coarse_solve(g, Ka, ba, ua)
+    api.stomsfem_coarse_solve(g, Kb, bb, ub)
+    torch.cuda.synchronize()
+    return float(((ua - ub).norm(dim=1) / ub.norm(dim=1)).max().item())
+
+
+def bench_pod(api, dev, stream):
+    """Reduced-basis form on its workload (64^2 fine, 8^2 coarse): offline
+    basis from 200 training samples, online stage for 10^4 samples (the
+    tensor-core W^T A W GEMM per cell + the reduced solves)."""
+    import torch
+    w = W.workload("pod_64")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    rho = nf // nc
+    Ns, S = w["train_samples"], w["samples"]
+    xtr = torch.from_numpy(W.draw_xi(w["field"], Ns, w["train_seed"])).to(dev)
+    atr = torch.empty((Ns, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xtr, atr)
+    Ktr = torch.empty((Ns, nc * nc, 10), dtype=torch.float64, device=dev)
+    btr = torch.empty((Ns, nc * nc, 4), dtype=torch.float64, device=dev)
+    phi = torch.empty((Ns, nc * nc, 4, (rho + 1) ** 2), dtype=torch.float64, device=dev)
+    api.stomsfem_upscale(g, atr, Ktr, btr, phi=phi)
+    t0 = time.perf_counter()
+    h, ranks = api.stomsfem_pod_build(g, phi, atr, tol=w["tol"], max_rank=27)
+    t_build = time.perf_counter() - t0
+    xi = torch.from_numpy(W.draw_xi(w["field"], S, w["seed"])).to(dev)
+    a = torch.empty((S, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xi, a)
+    Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+    be = torch.empty_like(Ke[..., :4]).contiguous()
+    Kp = torch.empty_like(Ke)
+    bp = torch.empty_like(be)
+    wsp = torch.empty(api.stomsfem_pod_workspace_size(h, S), dtype=torch.uint8, device=dev)
+    _, rb = api.stomsfem_upscale_workspace_size(g, 0, api.FP64)
+    wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+    res = {"workload": "pod_64", "samples": S, "units": S * nc * nc, "build_s": t_build,
+           "rank_min": int(min(ranks)), "rank_max": int(max(ranks)),
+           "rank_mean": float(sum(ranks) / len(ranks))}
+    ms_plain = _timed_call(stream, lambda: api.stomsfem_upscale(g, a, Kp, bp, workspace=wsu, stream=stream))
+    res["fp64_plain_units_per_s"] = S * nc * nc / (ms_plain / 1e3)
+    P0 = 4 + 27
+    gemm_flops = 2.0 * S * nc * nc * 64 * (P0 * (P0 + 1) // 2)
+    for refine in (0, 4):
+        ms = _timed_call(stream, lambda: api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=refine,
+                                                                  workspace=wsp, stream=stream))
+        key = "refined%d" % refine
+        err_k = float(((Ke - Kp).norm(dim=2) / Kp.norm(dim=2)).max().item())
+        res[key] = {"units_per_s": S * nc * nc / (ms / 1e3), "ms": ms, "Ke_rel_vs_plain": err_k,
+                    "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:256].contiguous(),
+                                                         be[:256].contiguous(), Kp[:256].contiguous(),
+                                                         bp[:256].contiguous(), dev),
+                    "tensor_tflops_lower_bound": gemm_flops / (ms / 1e3) / 1e12}
+    api.stomsfem_pod_destroy(h)
+    peaks = _peaks()
+    res["roofline_note"] = ("GEMM flops of the whole call / whole-call time vs bf16 %.0f TFLOP/s "
+                            "(measured burst): launch- and FP64-epilogue-bound at this size"
+                            % peaks.get("bf16_tflops", 1890.2))
+    return res, 4 + 2 * 3 * 4
+
+
+def bench_surrogate(api, dev, stream):
+    """Learned-surrogate form (64^2 / 8^2 workload): training on 1563
+    samples (10^5 cell pairs) from the plain upscaler, inference on 10^5
+    fresh samples (6.4 M units) with indicator and fallback."""
+    import torch
+    w = W.workload("surrogate_64")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    Ns, S = w["train_samples"], w["samples"]
+    xtr = torch.from_numpy(W.draw_xi(w["field"], Ns, w["train_seed"])).to(dev)
+    atr = torch.empty((Ns, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xtr, atr)
+    Ktr = torch.empty((Ns, nc * nc, 10), dtype=torch.float64, device=dev)
+    btr = torch.empty((Ns, nc * nc, 4), dtype=torch.float64, device=dev)
+    api.stomsfem_upscale(g, atr, Ktr, btr)
+    _, _, _, nfam = api.stomsfem_local_vars(g, fld, 1e-6)
+    h, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.xavier_weights(nfam, 0))
+    steps = 3000
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = api.stomsfem_surrogate_train(h, xtr, atr, Ktr, btr, steps=steps, lr=2e-3, lr_min=2e-5,
+                                        seed=w["train_seed"])
+    t_train = time.perf_counter() - t0
+    xi = torch.from_numpy(W.draw_xi(w["field"], S, w["seed"])).to(dev)
+    a = torch.empty((S, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xi, a)
+    Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+    be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=dev)
+    fb = torch.empty((S, nc * nc), dtype=torch.uint8, device=dev)
+    Kp = torch.empty_like(Ke)
+    bp = torch.empty_like(be)
+    wss = torch.empty(api.stomsfem_surrogate_workspace_size(h, S), dtype=torch.uint8, device=dev)
+    _, rb = api.stomsfem_upscale_workspace_size(g, 0, api.FP64)
+    wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+    units = S * nc * nc
+    ms_inf = _timed_call(stream, lambda: api.stomsfem_surrogate_infer(h, g, xi, a, Ke, be, fb, workspace=wss,
+                                                                      stream=stream))
+    ms_plain = _timed_call(stream, lambda: api.stomsfem_upscale(g, a, Kp, bp, workspace=wsu, stream=stream))
+    flops = 2.0 * units * (64 * 128 + 2 * 128 * 128 + 16 * 128)  # padded inputs, as computed
+    res = {"workload": "surrogate_64", "train_pairs": Ns * nc * nc, "train_steps": steps,
+           "train_s": t_train, "train_loss_first": float(loss[:10].mean()),
+           "train_loss_last": float(loss[-50:].mean()), "families": nfam,
+           "infer_units": units, "infer_units_per_s": units / (ms_inf / 1e3),
+           "fp64_plain_units_per_s": units / (ms_plain / 1e3),
+           "speedup_vs_fp64": ms_plain / ms_inf,
+           "fallback_rate": float(fb.double().mean().item()),
+           "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:2000].contiguous(), be[:2000].contiguous(),
+                                                Kp[:2000].contiguous(), bp[:2000].contiguous(), dev),
+           "tensor_tflops_whole_call": flops / (ms_inf / 1e3) / 1e12,
+           "tensor_peak_tflops": _peaks().get("bf16_tflops", 1890.2)}
+    api.stomsfem_surrogate_destroy(h)
+    return res, 6 * 4 + 8
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +344,8 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra-forms", action="store_true",
+                    help="skip the reduced-basis and surrogate measurements")
     args = ap.parse_args()
 
     w = W.workload(args.workload)
@@ -358,6 +497,13 @@ def main():
         e2e = {"value": units_step * ws * steps_e / (mse / 1e3), "unit": "units/s",
                "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)}
 
+    extra = {}
+    launches_extra = 0
+    if not args.no_extra_forms:
+        extra["pod"], n1 = bench_pod(api, dev, stream)
+        extra["surrogate"], n2 = bench_surrogate(api, dev, stream)
+        launches_extra = n1 + n2
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, ov, args.cpu_samples)
@@ -381,10 +527,11 @@ def main():
                          "peak_note": "derived: 152 SMs x %s x 2070 MHz" % (
                              "2 FP64 FMA/clk" if form == "fp64" else "128 FP32 lanes x 2 flops")},
             "e2e": e2e,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 5 * args.steps + launches_extra,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

@@ -77,20 +77,26 @@ extern "C" int stomsfem_sample_coef(const stomsfem_grid* grid, const stomsfem_fi
   if (!(field->width > 0.0)) return set_error(STOMSFEM_EINVAL, "width must be > 0");
   if (S == 0) return STOMSFEM_OK;
   if (!xi || !a) return set_error(STOMSFEM_EINVAL, "xi and a must be device pointers");
-  if (S > 65535) return set_error(STOMSFEM_EINVAL, "S > 65535 per call");
-  dim3 grd((grid->nf + kRows - 1) / kRows, S);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int nbx = field->nbx;
+  const size_t K = (size_t)field->nbx * field->nby;
+  // the sample index runs over gridDim.y (at most 65535 per launch)
+  for (int s0 = 0; s0 < S; s0 += 65535) {
+    const int Sc = S - s0 < 65535 ? S - s0 : 65535;
+    dim3 grd((grid->nf + kRows - 1) / kRows, Sc);
+    const double* xs = xi + (size_t)s0 * K;
+    double* as = a + (size_t)s0 * grid->nf * grid->nf;
 #define LAUNCH(N)                                                                              \
   sample_coef_kernel<N><<<grd, kCoefThreads, 0, st>>>(grid->nf, field->kind, nbx, field->nby,  \
                                                       field->width, field->scale,              \
-                                                      field->contrast_log, field->gain, xi, a)
-  if (nbx <= 4) LAUNCH(4);
-  else if (nbx <= 8) LAUNCH(8);
-  else if (nbx <= 16) LAUNCH(16);
-  else if (nbx <= 32) LAUNCH(32);
-  else LAUNCH(64);
+                                                      field->contrast_log, field->gain, xs, as)
+    if (nbx <= 4) LAUNCH(4);
+    else if (nbx <= 8) LAUNCH(8);
+    else if (nbx <= 16) LAUNCH(16);
+    else if (nbx <= 32) LAUNCH(32);
+    else LAUNCH(64);
 #undef LAUNCH
-  STOMSFEM_TRY_CUDA(cudaGetLastError());
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+  }
   return STOMSFEM_OK;
 }
