@@ -5,23 +5,32 @@
 // (rows/columns [K, K+nb)) the warp
 //   1. factorises the tall panel [K, K+np) x [K, K+nb), np = nb + b: each
 //      lane holds up to RPL panel rows in registers; the block-row
-//      multipliers of each column step are broadcast through shared memory
-//      (128-bit loads); the NR right-hand sides ride along, which is the
-//      forward substitution;
+//      multipliers of each column step are broadcast through a
+//      double-buffered shared vector (128-bit loads, one warp sync per
+//      step); the NR right-hand sides ride along, which is the forward
+//      substitution;
 //   2. applies the rank-nb update to the trailing b x b window with 4 x 4
 //      register tiles (128-bit shared loads of the transposed panel);
-//   3. retires the block's rows and generates the next rows: a 9-point row
-//      has 5 entries at or left of the diagonal, at offsets 0, 1, mx-1, mx,
-//      mx+1, which the row generator returns in one call.
+//   3. retires the block's rows and writes the next rows from values the
+//      row generator loaded one block earlier (so the global-load latency
+//      hides behind the panel and the trailing update).
 // The matrix lives only as a window of RW >= NB + b band rows in shared
 // memory (RW a power of two; row r at slot r & (RW-1), entry A[r][r-d] at
 // column d).  Factor blocks go to global scratch as (NB + bmax) x NB
-// row-major tiles for the back substitution and refinement sweeps.
+// row-major tiles; the substitutions stream them back through two shared
+// staging buffers with asynchronous copies (next block in flight while the
+// current one is used).
 //
 // Row generator interface:
-//   gen.row<T>(r, T e[5], T rhs[NR]) : band entries A[r][r], A[r][r-1],
-//       A[r][r-mx+1], A[r][r-mx], A[r][r-mx-1] (0 where absent) and rhs;
-//   gen.mx : offset of the south neighbour.
+//   typename Gen::Raw                  raw per-row values,
+//   gen.load(r, Raw&)                  issue the global loads of row r,
+//   gen.prefetch(r, double* dst4)      asynchronous copy of row r's values,
+//   gen.from_smem(const double* src4, Raw&)
+//   gen.make<T>(r, const Raw&, T e[5], T rhs[NR])
+//                                      band entries A[r][r], A[r][r-1],
+//                                      A[r][r-mx+1], A[r][r-mx], A[r][r-mx-1]
+//                                      (0 where absent) and the rhs,
+//   gen.mx                             offset of the south neighbour.
 #pragma once
 #include "common.cuh"
 
@@ -32,10 +41,11 @@ constexpr int kNB = 16;
 template <typename T>
 struct BlkSmem {
   T* wnd;  // [RW][PW] band rows
-  T* tb;   // [NB + bmax][NB] factor block staging (aliases wnd)
+  T* tb;   // 2 x [NB + bmax][NB] factor block staging (aliases wnd)
   T* pt;   // [NB][RP] trailing panel, p-major: pt[p*RP + (i - nb)] = L[K+i][K+p]
   T* rhs;  // [RW][4]
-  T* lb;   // [NB] broadcast of the block-row multipliers
+  T* lb;   // 2 x [NB] broadcast of the block-row multipliers
+  double* raw;  // [NB][4] coefficient values of the next rows (async prefetch)
   int RW, PW, RP;
 };
 
@@ -48,7 +58,7 @@ __host__ __device__ inline int blk_ring_rows(int bmax) {
 }
 
 __host__ __device__ inline int blk_wnd_elems(int bmax) {
-  const int a = blk_ring_rows(bmax) * (bmax + 1), b = (kNB + bmax) * kNB;
+  const int a = blk_ring_rows(bmax) * (bmax + 1), b = 2 * (kNB + bmax) * kNB;
   return a > b ? a : b;
 }
 
@@ -56,7 +66,7 @@ template <typename T>
 __host__ __device__ inline size_t blk_smem_bytes(int bmax) {
   const int RW = blk_ring_rows(bmax), RP = (bmax + 3) & ~3;
   return al16(sizeof(T) * blk_wnd_elems(bmax)) + al16(sizeof(T) * kNB * RP) +
-         al16(sizeof(T) * RW * 4) + al16(sizeof(T) * kNB);
+         al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 2 * kNB) + al16(sizeof(double) * kNB * 4);
 }
 
 template <typename T>
@@ -74,6 +84,8 @@ __device__ inline BlkSmem<T> make_blk(unsigned char* base, int bmax) {
   s.rhs = reinterpret_cast<T*>(base + o);
   o += al16(sizeof(T) * s.RW * 4);
   s.lb = reinterpret_cast<T*>(base + o);
+  o += al16(sizeof(T) * 2 * kNB);
+  s.raw = reinterpret_cast<double*>(base + o);
   return s;
 }
 
@@ -81,9 +93,11 @@ __host__ __device__ inline size_t blk_factor_elems(int n, int bmax) {
   return (size_t)((n + kNB - 1) / kNB) * (kNB + bmax) * kNB;
 }
 
-// The pivot and its reciprocal.
+// The pivot and its reciprocal.  FP32: the hardware reciprocal square root
+// (relative error a few ulp), which perturbs the factor at the level of FP32
+// rounding; FP64: correctly rounded.
 __device__ __forceinline__ void pivot_of(float a, float& d, float& dinv) {
-  dinv = __frsqrt_rn(a);
+  dinv = rsqrtf(a);
   d = a * dinv;
 }
 __device__ __forceinline__ void pivot_of(double a, double& d, double& dinv) {
@@ -91,10 +105,27 @@ __device__ __forceinline__ void pivot_of(double a, double& d, double& dinv) {
   dinv = 1.0 / d;
 }
 
-// Fill rows [r0, r1) of the window: zero band, then the generator's entries.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Rows [r0, r1) of the window (at most 32 rows; row r0 + l uses lane l's raw
+// values): zero the band, then the generator's entries and rhs.
 template <typename T, int NR, class Gen>
-__device__ __forceinline__ void blk_fill(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int b,
-                                         int lane) {
+__device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int b, int lane,
+                                             const typename Gen::Raw& raw) {
   const int msk = s.RW - 1;
   for (int r = r0; r < r1; ++r) {
     T* row = s.wnd + (r & msk) * s.PW;
@@ -102,9 +133,10 @@ __device__ __forceinline__ void blk_fill(const Gen& gen, const BlkSmem<T>& s, in
   }
   __syncwarp();
   const int mx = gen.mx;
-  for (int r = r0 + lane; r < r1; r += 32) {
+  const int r = r0 + lane;
+  if (r < r1) {
     T e[5], rh[NR];
-    gen.template row<T>(r, e, rh);
+    gen.template make<T>(r, raw, e, rh);
     T* row = s.wnd + (r & msk) * s.PW;
     row[0] += e[0];
     if (r >= 1 && 1 <= b) row[1] += e[1];
@@ -149,18 +181,19 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T
         lq[q] = l;
       }
       if (J + 1 < kNB) {
-        if (lane < kNB) lb[lane] = lq[0];
+        T* lbj = lb + (J & 1) * kNB;  // alternate buffers: one sync per step
+        if (lane < kNB) lbj[lane] = lq[0];
         __syncwarp();
         T Lv[kNB];
 #pragma unroll
         for (int v = 0; v < kNB / 4; ++v) {
           if (4 * v + 3 > J) {
             if constexpr (sizeof(T) == 4) {
-              const float4 f = reinterpret_cast<const float4*>(lb)[v];
+              const float4 f = reinterpret_cast<const float4*>(lbj)[v];
               Lv[4 * v] = f.x; Lv[4 * v + 1] = f.y; Lv[4 * v + 2] = f.z; Lv[4 * v + 3] = f.w;
             } else {
-              const double2 f0 = reinterpret_cast<const double2*>(lb)[2 * v];
-              const double2 f1 = reinterpret_cast<const double2*>(lb)[2 * v + 1];
+              const double2 f0 = reinterpret_cast<const double2*>(lbj)[2 * v];
+              const double2 f1 = reinterpret_cast<const double2*>(lbj)[2 * v + 1];
               Lv[4 * v] = f0.x; Lv[4 * v + 1] = f0.y; Lv[4 * v + 2] = f1.x; Lv[4 * v + 3] = f1.y;
             }
           } else {
@@ -172,7 +205,6 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T
 #pragma unroll
           for (int q = 0; q < RPL; ++q) pr[q][p] -= lq[q] * Lv[p];
         }
-        __syncwarp();
       }
     }
     panel_col<J + 1, T, NR, RPL>(pr, rh, lb, lane, nb, np, K, fail);
@@ -187,14 +219,32 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
                           T* __restrict__ Lg, TS* __restrict__ yg, int lane) {
   const int LBS = (kNB + bmax) * kNB;
   const int msk = s.RW - 1;
-  int filled = 0;
+  // first window: rows [0, min(n, NB + b)), generated directly
+  int filled = min(n, kNB + b);
+  for (int r0 = 0; r0 < filled; r0 += 32) {
+    typename Gen::Raw raw;
+    if (r0 + lane < filled) gen.load(r0 + lane, raw);
+    blk_fill_raw<T, NR>(gen, s, r0, min(filled, r0 + 32), b, lane, raw);
+    __syncwarp();
+  }
+  // rows of the next fill: their coefficient values are copied one block
+  // ahead into shared memory by asynchronous copies
+  if (filled + lane < min(n, filled + kNB)) gen.prefetch(filled + lane, s.raw + 4 * lane);
+  cp_async_commit();
   for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
     const int nb = min(kNB, n - K);
     const int np = min(nb + b, n - K);
     const int need = min(n, K + kNB + b);
     if (filled < need) {
-      blk_fill<T, NR>(gen, s, filled, need, b, lane);
+      cp_async_wait<0>();
+      __syncwarp();
+      typename Gen::Raw pf;
+      if (lane < kNB) gen.from_smem(s.raw + 4 * lane, pf);
+      blk_fill_raw<T, NR>(gen, s, filled, need, b, lane, pf);
       filled = need;
+      __syncwarp();
+      if (filled + lane < min(n, filled + kNB)) gen.prefetch(filled + lane, s.raw + 4 * lane);
+      cp_async_commit();
     }
     __syncwarp();
     // ---- 1. panel factorisation in registers
@@ -268,6 +318,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
         // need p >= nb + 4 ti - b only
         const int p0 = max(0, nb + 4 * ti - b);
         const T* col = s.pt + p0 * s.RP;
+#pragma unroll 4
         for (int p = p0; p < nb; ++p, col += s.RP) {
           T va[4], vc[4];
           if constexpr (sizeof(T) == 4) {
@@ -305,26 +356,41 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
   return -1;
 }
 
+// Asynchronous copy of factor block kb into a staging buffer (one commit group).
+template <typename T>
+__device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int n, int b, int bmax, T* dst,
+                                          int lane) {
+  const int K = kb * kNB;
+  const int nb = min(kNB, n - K);
+  const int np = min(nb + b, n - K);
+  const T* src = Lg + (size_t)kb * (kNB + bmax) * kNB;
+  const int nv = np * kNB * (int)sizeof(T) / 16;
+  for (int v = lane; v < nv; v += 32)
+    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * v, reinterpret_cast<const unsigned char*>(src) + 16 * v);
+  cp_async_commit();
+}
+
 // Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
 template <typename T, int NR, typename TS>
 __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
                              TS* __restrict__ xg, int lane) {
-  const int LBS = (kNB + bmax) * kNB;
   const int nbk = (n + kNB - 1) / kNB;
   const int msk = s.RW - 1;
+  const int stg = (kNB + bmax) * kNB;
   T* xr = s.rhs;  // ring of solution rows
+  blk_stage<T>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, lane);
   for (int kb = nbk - 1; kb >= 0; --kb) {
     const int K = kb * kNB;
     const int nb = min(kNB, n - K);
     const int np = min(nb + b, n - K);
-    const T* Lb = Lg + (size_t)kb * LBS;
-    {  // stage the factor block in shared memory (128-bit copies)
-      const int nv = np * kNB * (int)sizeof(T) / 16;
-      const int4* src = reinterpret_cast<const int4*>(Lb);
-      int4* dst = reinterpret_cast<int4*>(s.tb);
-      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    if (kb > 0) {
+      blk_stage<T>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, lane);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncwarp();
+    const T* tb = s.tb + (kb & 1) * stg;
     // lane p < nb: yv = y_p - sum over the rows below the block of L[i][p] x_i
     T yv[NR];
 #pragma unroll
@@ -333,8 +399,9 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; ++c) acc[c] = T(0);
+#pragma unroll 4
       for (int i = nb; i < np; ++i) {
-        const T l = s.tb[i * kNB + lane];
+        const T l = tb[i * kNB + lane];
         const T* xi = xr + ((K + i) & msk) * 4;
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[c] += l * xi[c];
@@ -347,12 +414,12 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 #pragma unroll
     for (int p = kNB - 1; p >= 0; --p) {
       if (p < nb) {
-        const T iLpp = s.tb[p * kNB + p];
+        const T iLpp = tb[p * kNB + p];
         T xp[NR];
 #pragma unroll
         for (int c = 0; c < NR; ++c) xp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
         if (lane < p) {
-          const T l = s.tb[p * kNB + lane];
+          const T l = tb[p * kNB + lane];
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] -= l * xp[c];
         }
@@ -362,7 +429,6 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
         }
       }
     }
-    __syncwarp();
     if (lane < nb) {
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
@@ -379,10 +445,12 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 template <typename T, int NR, int RPL>
 __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
                                    const T* __restrict__ Lg, double* __restrict__ rg, int lane) {
-  const int LBS = (kNB + bmax) * kNB;
   const int msk = s.RW - 1;
+  const int stg = (kNB + bmax) * kNB;
+  const int nbk = (n + kNB - 1) / kNB;
   T* rr = s.rhs;  // ring of pending right-hand-side rows
   int filled = 0;
+  blk_stage<T>(Lg, 0, n, b, bmax, s.tb, lane);
   for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
     const int nb = min(kNB, n - K);
     const int np = min(nb + b, n - K);
@@ -392,26 +460,26 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
       for (int c = 0; c < NR; ++c) rr[(r & msk) * 4 + c] = (T)rg[(size_t)r * NR + c];
     }
     filled = max(filled, need);
-    {
-      const T* Lb = Lg + (size_t)kb * LBS;
-      const int nv = np * kNB * (int)sizeof(T) / 16;
-      const int4* src = reinterpret_cast<const int4*>(Lb);
-      int4* dst = reinterpret_cast<int4*>(s.tb);
-      for (int v = lane; v < nv; v += 32) dst[v] = src[v];
+    if (kb + 1 < nbk) {
+      blk_stage<T>(Lg, kb + 1, n, b, bmax, s.tb + ((kb + 1) & 1) * stg, lane);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncwarp();
+    const T* tb = s.tb + (kb & 1) * stg;
     T yv[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) yv[c] = (lane < nb) ? rr[((K + lane) & msk) * 4 + c] : T(0);
 #pragma unroll
     for (int p = 0; p < kNB; ++p) {
       if (p < nb) {
-        const T iLpp = s.tb[p * kNB + p];
+        const T iLpp = tb[p * kNB + p];
         T yp[NR];
 #pragma unroll
         for (int c = 0; c < NR; ++c) yp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
         if (lane > p && lane < nb) {
-          const T l = s.tb[lane * kNB + p];
+          const T l = tb[lane * kNB + p];
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] -= l * yp[c];
         }
@@ -438,7 +506,7 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[c] = T(0);
         for (int p = 0; p < nb; ++p) {
-          const T l = s.tb[i * kNB + p];
+          const T l = tb[i * kNB + p];
 #pragma unroll
           for (int c = 0; c < NR; ++c) acc[c] += l * yb[p * NR + c];
         }

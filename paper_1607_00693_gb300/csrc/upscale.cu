@@ -56,8 +56,11 @@ struct PatchGen {
     return __ldg(a + (size_t)(y0 + ey) * nf + (x0 + ex));
   }
   __device__ __forceinline__ void node(int r, int& i, int& j) const {
-    j = r / mx + 1;
-    i = r - (j - 1) * mx + 1;
+    // j - 1 = floor(r / mx) from a float reciprocal: (r + 1/2) / mx stays at
+    // least 1/(2 mx) away from an integer, far above the rounding error
+    const int q = __float2int_rz(((float)r + 0.5f) * __frcp_rn((float)mx));
+    j = q + 1;
+    i = r - q * mx + 1;
   }
   template <typename T>
   __device__ __forceinline__ T coef(int r, int d) const {
@@ -95,24 +98,53 @@ struct PatchGen {
     if (l == 1) return AXY - AX;
     return -AXY;
   }
-  // Whole row r: band entries at offsets 0, 1 (west), mx-1 (south-east),
-  // mx (south), mx+1 (south-west) and the three right-hand sides, from the
-  // four elements around the node.
-  template <typename T>
-  __device__ __forceinline__ void row(int r, T e[5], T rh[3]) const {
+  // Raw values of row r: the coefficient on the four elements around the node.
+  struct Raw {
+    double sw, se, ne, nw;
+  };
+  __device__ __forceinline__ void load(int r, Raw& w) const {
     int i, j;
     node(r, i, j);
-    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
-    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
-    e[0] = (T(2) / T(3)) * ((aSW + aSE) + (aNE + aNW));
-    e[1] = i > 1 ? -(aSW + aNW) / T(6) : T(0);
-    e[2] = (i < mx && j > 1) ? -aSE / T(3) : T(0);
-    e[3] = j > 1 ? -(aSW + aSE) / T(6) : T(0);
-    e[4] = (i > 1 && j > 1) ? -aSW / T(3) : T(0);
-    const T AX = ((aSW + aNW) - (aSE + aNE)) / (T(2) * (T)Nx);
-    const T AY = ((aSW + aSE) - (aNW + aNE)) / (T(2) * (T)Ny);
-    const T Xc = (T)i / (T)Nx, Yc = (T)j / (T)Ny;
-    const T AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) / (T(3) * (T)Nx * (T)Ny);
+    w.sw = ael(i - 1, j - 1);
+    w.se = ael(i, j - 1);
+    w.ne = ael(i, j);
+    w.nw = ael(i - 1, j);
+  }
+  __device__ __forceinline__ void prefetch(int r, double* dst) const {
+    int i, j;
+    node(r, i, j);
+    const double* p0 = a + (size_t)(y0 + j - 1) * nf + (x0 + i - 1);  // SW element
+    cp_async8(dst + 0, p0);
+    cp_async8(dst + 1, p0 + 1);
+    cp_async8(dst + 2, p0 + nf + 1);
+    cp_async8(dst + 3, p0 + nf);
+  }
+  __device__ __forceinline__ void from_smem(const double* src, Raw& w) const {
+    w.sw = src[0];
+    w.se = src[1];
+    w.ne = src[2];
+    w.nw = src[3];
+  }
+  // Whole row r: band entries at offsets 0, 1 (west), mx-1 (south-east),
+  // mx (south), mx+1 (south-west) and the three right-hand sides.
+  template <typename T>
+  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T rh[3]) const {
+    int i, j;
+    node(r, i, j);
+    const T aSW = (T)w.sw, aSE = (T)w.se;
+    const T aNE = (T)w.ne, aNW = (T)w.nw;
+    // divisions replaced by products with reciprocals (one rounding each)
+    const T r3 = T(1) / T(3), r6 = T(1) / T(6);
+    const T iNx = T(1) / (T)Nx, iNy = T(1) / (T)Ny;
+    e[0] = (T(2) * r3) * ((aSW + aSE) + (aNE + aNW));
+    e[1] = i > 1 ? -(aSW + aNW) * r6 : T(0);
+    e[2] = (i < mx && j > 1) ? -aSE * r3 : T(0);
+    e[3] = j > 1 ? -(aSW + aSE) * r6 : T(0);
+    e[4] = (i > 1 && j > 1) ? -aSW * r3 : T(0);
+    const T AX = T(0.5) * ((aSW + aNW) - (aSE + aNE)) * iNx;
+    const T AY = T(0.5) * ((aSW + aSE) - (aNW + aNE)) * iNy;
+    const T Xc = (T)i * iNx, Yc = (T)j * iNy;
+    const T AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) * r3 * iNx * iNy;
     rh[0] = AX + AY - AXY;
     rh[1] = AXY - AX;
     rh[2] = -AXY;
@@ -226,7 +258,7 @@ __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000
 // TK: factor/solve type; TA: type of the K_e/b_e accumulation and of the
 // recombination; RPL: panel rows per lane (ceil((16 + bmax) / 32)).
 template <typename TK, typename TA, int RPL>
-__global__ void __launch_bounds__(kUpscaleWarps * 32, sizeof(TK) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kUpscaleWarps * 32, sizeof(TK) == 4 ? 4 : 2)
 upscale_kernel(UpscaleArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
