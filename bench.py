@@ -219,7 +219,26 @@ def _coarse_err(api, g, Ka, ba, Kb, bb, dev):
     return float(((ua - ub).norm(dim=1) / ub.norm(dim=1)).max().item())
 
 
-def bench_pod(api, dev, stream):
+def shard(rank, ws, total, batch):
+    """This rank's contiguous slice of the sample stream: (first, count).
+    Every rank gets the same count (at least one batch), so per-GPU work is
+    fixed as the GPU count grows (weak scaling); shards never overlap."""
+    per_rank = max(batch, total // ws)
+    return rank * per_rank, per_rank
+
+
+def max_over_ranks(value, device=None):
+    """Maximum of a float over all ranks (the slowest rank sets the time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_pod(api, dev, stream, samples=None):
     """Reduced-basis form on its workload (64^2 fine, 8^2 coarse): offline
     basis from 200 training samples, online stage for 10^4 samples (the
     tensor-core W^T A W GEMM per cell + the reduced solves)."""
@@ -229,7 +248,7 @@ def bench_pod(api, dev, stream):
     g = api.grid(nf, nc, w["f"])
     fld = api.field_from_dict(w["field"])
     rho = nf // nc
-    Ns, S = w["train_samples"], w["samples"]
+    Ns, S = w["train_samples"], samples or w["samples"]
     xtr = torch.from_numpy(W.draw_xi(w["field"], Ns, w["train_seed"])).to(dev)
     atr = torch.empty((Ns, nf, nf), dtype=torch.float64, device=dev)
     api.stomsfem_sample_coef(g, fld, xtr, atr)
@@ -275,7 +294,7 @@ def bench_pod(api, dev, stream):
     return res, 4 + 2 * 3 * 4
 
 
-def bench_surrogate(api, dev, stream):
+def bench_surrogate(api, dev, stream, samples=None, steps=3000):
     """Learned-surrogate form (64^2 / 8^2 workload): training on 1563
     samples (10^5 cell pairs) from the plain upscaler, inference on 10^5
     fresh samples (6.4 M units) with indicator and fallback."""
@@ -284,7 +303,7 @@ def bench_surrogate(api, dev, stream):
     nf, nc = w["nf"], w["nc"]
     g = api.grid(nf, nc, w["f"])
     fld = api.field_from_dict(w["field"])
-    Ns, S = w["train_samples"], w["samples"]
+    Ns, S = w["train_samples"], samples or w["samples"]
     xtr = torch.from_numpy(W.draw_xi(w["field"], Ns, w["train_seed"])).to(dev)
     atr = torch.empty((Ns, nf, nf), dtype=torch.float64, device=dev)
     api.stomsfem_sample_coef(g, fld, xtr, atr)
@@ -293,7 +312,6 @@ def bench_surrogate(api, dev, stream):
     api.stomsfem_upscale(g, atr, Ktr, btr)
     _, _, _, nfam = api.stomsfem_local_vars(g, fld, 1e-6)
     h, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.xavier_weights(nfam, 0))
-    steps = 3000
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     loss = api.stomsfem_surrogate_train(h, xtr, atr, Ktr, btr, steps=steps, lr=2e-3, lr_min=2e-5,
@@ -346,6 +364,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-forms", action="store_true",
                     help="skip the reduced-basis and surrogate measurements")
+    ap.add_argument("--pod-samples", type=int, default=None, help="online POD samples (default 10^4)")
+    ap.add_argument("--sg-samples", type=int, default=None, help="surrogate inference samples (default 10^5)")
+    ap.add_argument("--sg-steps", type=int, default=3000, help="surrogate training steps")
+    ap.add_argument("--fp32r-batch", type=int, default=64, help="samples per step of the FP32+refinement arm")
     args = ap.parse_args()
 
     w = W.workload(args.workload)
@@ -373,8 +395,8 @@ def main():
     K = W.n_vars(w["field"])
     total = w["samples"]
     # this rank's samples: a contiguous shard of the workload's stream
-    per_rank = max(B, total // ws)
-    xi_host = W.draw_xi(w["field"], per_rank, w["seed"], w["dist"], first=rank * per_rank)
+    first, per_rank = shard(rank, ws, total, B)
+    xi_host = W.draw_xi(w["field"], per_rank, w["seed"], w["dist"], first=first)
     xi = torch.from_numpy(xi_host).to(dev)
     ov_t = torch.from_numpy(ov).to(dev) if ov is not None else None
     mo = int(ov.max()) if ov is not None else 0
@@ -433,13 +455,8 @@ def main():
             clk = clocks.stop() if clocks else None
             barrier()
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dev)
         up_ms = [a.elapsed_time(b) for a, b in evs]
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, up_ms, clk, bf
 
     form = args.form
@@ -466,6 +483,16 @@ def main():
     u64 = bf64["u"][:Bc].cpu().numpy()
     err = float(np.max(np.linalg.norm(uf - u64, axis=1) / np.linalg.norm(u64, axis=1)))
     del bf_c
+    # the FP32 factor + FP64 refinement arm (2 sweeps)
+    ms32r, up32r, _, bf32r = timed("fp32r", args.fp32r_batch, max(1, min(args.steps, 2)), 1)
+    value32r = args.fp32r_batch * ncell * ws * max(1, min(args.steps, 2)) / (ms32r / 1e3)
+    Br = min(args.fp32r_batch, args.fp64_batch)
+    with torch.cuda.stream(stream):
+        step(bf32r, xs_for(0, args.fp32r_batch), "fp32r")
+    stream.synchronize()
+    err32r = float(np.max(np.linalg.norm(bf32r["u"][:Br].cpu().numpy() - u64[:Br], axis=1) /
+                          np.linalg.norm(u64[:Br], axis=1)))
+    del bf32r
 
     e2e = None
     if not args.no_e2e:
@@ -488,20 +515,15 @@ def main():
                 uh.copy_(bf["u"], non_blocking=True)
             e1.record(stream)
             stream.synchronize()
-        mse = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([mse], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mse = float(t.item())
+        mse = max_over_ranks(e0.elapsed_time(e1), dev)
         e2e = {"value": units_step * ws * steps_e / (mse / 1e3), "unit": "units/s",
                "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)}
 
     extra = {}
     launches_extra = 0
     if not args.no_extra_forms:
-        extra["pod"], n1 = bench_pod(api, dev, stream)
-        extra["surrogate"], n2 = bench_surrogate(api, dev, stream)
+        extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)
+        extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
         launches_extra = n1 + n2
 
     cpu = None
@@ -520,7 +542,9 @@ def main():
                        "l2": "inputs larger than L2 (a: %.1f GB per step)" % (B * nf * nf * 8 / 1e9),
                        "parallelism": "replicas (sample shards)" if ws > 1 else "single GPU"},
             "forms": {"chosen": form, "chosen_units_per_s": value, "fp64_units_per_s": value64,
-                      "speedup_vs_fp64": value / value64, "coarse_rel_l2_vs_fp64": err},
+                      "speedup_vs_fp64": value / value64, "coarse_rel_l2_vs_fp64": err,
+                      "fp32r_units_per_s": value32r, "fp32r_speedup_vs_fp64": value32r / value64,
+                      "fp32r_coarse_rel_l2_vs_fp64": err32r},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "upscale_kernel (%s)" % form,
