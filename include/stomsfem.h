@@ -75,6 +75,13 @@ typedef struct {
 const char* stomsfem_version(void);
 const char* stomsfem_last_error(void);
 
+/* Failure-path self test (no paper counterpart): one CTA waits, with a limit
+ * of `iters` polls of about 100 ns, on an mbarrier that nothing arrives at
+ * -- the same bounded wait the tensor-core kernels use -- and reports the
+ * outcome in *status_host (STOMSFEM_ETIMEOUT when the limit ran out).
+ * Synchronous; the device stays usable afterwards.  1 <= iters <= 2^20. */
+int stomsfem_selftest_wait_timeout(int32_t iters, int32_t* status_host);
+
 /* Coefficient sampling (Sec. 2.1.3, the parametrized coefficient of
  * Eq. MsFEB2).  xi: device [S][nbx*nby] float64; a: device [S][nf][nf]
  * float64, a value per fine element at its centroid ((ex+1/2)h, (ey+1/2)h).

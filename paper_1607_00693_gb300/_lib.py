@@ -39,6 +39,7 @@ _SZ = ctypes.c_size_t
 _SIG = {
     "stomsfem_version": (ctypes.c_char_p, []),
     "stomsfem_last_error": (ctypes.c_char_p, []),
+    "stomsfem_selftest_wait_timeout": (ctypes.c_int, [_I, ctypes.POINTER(_I)]),
     "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
     "stomsfem_upscale_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I,
                                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),

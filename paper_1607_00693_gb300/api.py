@@ -52,6 +52,14 @@ def stomsfem_version():
     return L.lib().stomsfem_version().decode()
 
 
+def stomsfem_selftest_wait_timeout(iters=20000):
+    """Run the bounded-wait self test; returns the device status word
+    (STOMSFEM_ETIMEOUT when the wait ran out as it should)."""
+    st = ctypes.c_int32(1)
+    L.check(L.lib().stomsfem_selftest_wait_timeout(int(iters), ctypes.byref(st)))
+    return st.value
+
+
 def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
     S = xi.shape[0]
     L.check(L.lib().stomsfem_sample_coef(ctypes.byref(g), ctypes.byref(fld),

@@ -68,3 +68,11 @@ def test_host_validation_without_gpu(lib):
     assert lib.stomsfem_coarse_workspace_size(ctypes.byref(g), 64, ctypes.byref(cb)) == L.OK
     assert lib.stomsfem_coarse_solve(ctypes.byref(g), None, None, 3, None, None, None, None, None, 0,
                                      None) == L.EINVAL
+
+
+def test_selftest_rejects_bad_limits(lib):
+    import ctypes
+    st = ctypes.c_int32(0)
+    assert lib.stomsfem_selftest_wait_timeout(0, ctypes.byref(st)) == L.EINVAL
+    assert lib.stomsfem_selftest_wait_timeout((1 << 20) + 1, ctypes.byref(st)) == L.EINVAL
+    assert lib.stomsfem_selftest_wait_timeout(10, None) == L.EINVAL
