@@ -40,11 +40,13 @@ constexpr int kNB = 16;
 
 template <typename T>
 struct BlkSmem {
-  T* wnd;  // [RW][PW] band rows
+  T* wnd;  // [RW][PW] band rows; the 16 ring rows of the block just
+           // factorised hold the trailing panel for the update,
+           // p-major: pt[p*RP + (i - nb)] = L[K+i][K+p]
   T* tb;   // 2 x [NB + bmax][NB] factor block staging (aliases wnd)
-  T* pt;   // [NB][RP] trailing panel, p-major: pt[p*RP + (i - nb)] = L[K+i][K+p]
   T* rhs;  // [RW][4]
-  T* lb;   // 2 x [NB] broadcast of the block-row multipliers
+  T* lb;   // 2 x [NB] broadcast of the block-row multipliers; [NB][4]
+           // block solution in the stored forward substitution
   double* raw;  // [NB][4] coefficient values of the next rows (async prefetch)
   int RW, PW, RP;
 };
@@ -57,34 +59,39 @@ __host__ __device__ inline int blk_ring_rows(int bmax) {
   return r;
 }
 
+// Row pitch: b + 1 band entries, and at least RP = bmax rounded up to 4 so
+// that NB rows hold the transposed trailing panel.
+__host__ __device__ inline int blk_pitch(int bmax) {
+  const int rp = (bmax + 3) & ~3;
+  return bmax + 1 > rp ? bmax + 1 : rp;
+}
+
 __host__ __device__ inline int blk_wnd_elems(int bmax) {
-  const int a = blk_ring_rows(bmax) * (bmax + 1), b = 2 * (kNB + bmax) * kNB;
+  const int a = blk_ring_rows(bmax) * blk_pitch(bmax), b = 2 * (kNB + bmax) * kNB;
   return a > b ? a : b;
 }
 
 template <typename T>
 __host__ __device__ inline size_t blk_smem_bytes(int bmax) {
-  const int RW = blk_ring_rows(bmax), RP = (bmax + 3) & ~3;
-  return al16(sizeof(T) * blk_wnd_elems(bmax)) + al16(sizeof(T) * kNB * RP) +
-         al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 2 * kNB) + al16(sizeof(double) * kNB * 4);
+  const int RW = blk_ring_rows(bmax);
+  return al16(sizeof(T) * blk_wnd_elems(bmax)) + al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 4 * kNB) +
+         al16(sizeof(double) * kNB * 4);
 }
 
 template <typename T>
 __device__ inline BlkSmem<T> make_blk(unsigned char* base, int bmax) {
   BlkSmem<T> s;
   s.RW = blk_ring_rows(bmax);
-  s.PW = bmax + 1;
+  s.PW = blk_pitch(bmax);
   s.RP = (bmax + 3) & ~3;
   size_t o = 0;
   s.wnd = reinterpret_cast<T*>(base + o);
   s.tb = s.wnd;
   o += al16(sizeof(T) * blk_wnd_elems(bmax));
-  s.pt = reinterpret_cast<T*>(base + o);
-  o += al16(sizeof(T) * kNB * s.RP);
   s.rhs = reinterpret_cast<T*>(base + o);
   o += al16(sizeof(T) * s.RW * 4);
   s.lb = reinterpret_cast<T*>(base + o);
-  o += al16(sizeof(T) * 2 * kNB);
+  o += al16(sizeof(T) * 4 * kNB);
   s.raw = reinterpret_cast<double*>(base + o);
   return s;
 }
@@ -138,11 +145,20 @@ __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s
     T e[5], rh[NR];
     gen.template make<T>(r, raw, e, rh);
     T* row = s.wnd + (r & msk) * s.PW;
-    row[0] += e[0];
-    if (r >= 1 && 1 <= b) row[1] += e[1];
-    if (mx - 1 >= 0 && r >= mx - 1 && mx - 1 <= b) row[mx - 1] += e[2];
-    if (r >= mx && mx <= b) row[mx] += e[3];
-    if (r >= mx + 1 && mx + 1 <= b) row[mx + 1] += e[4];
+    if (mx >= 3 && mx + 1 <= b) {
+      // offsets 0, 1, mx-1, mx, mx+1 are distinct: plain stores
+      row[0] = e[0];
+      if (r >= 1) row[1] = e[1];
+      if (r >= mx - 1) row[mx - 1] = e[2];
+      if (r >= mx) row[mx] = e[3];
+      if (r >= mx + 1) row[mx + 1] = e[4];
+    } else {
+      row[0] += e[0];
+      if (r >= 1 && 1 <= b) row[1] += e[1];
+      if (mx - 1 >= 0 && r >= mx - 1 && mx - 1 <= b) row[mx - 1] += e[2];
+      if (r >= mx && mx <= b) row[mx] += e[3];
+      if (r >= mx + 1 && mx + 1 <= b) row[mx + 1] += e[4];
+    }
 #pragma unroll
     for (int c = 0; c < NR; ++c) s.rhs[(r & msk) * 4 + c] = rh[c];
   }
@@ -211,6 +227,98 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T
   }
 }
 
+// Columns J and J + 1 of a full panel (nb = NB) in one step: the 2 x 2
+// diagonal block is factorised from three shuffled entries, both columns of
+// multipliers are formed per row, and one broadcast of the two columns
+// feeds the rank-2 update of the remaining columns.
+template <int J, typename T, int NR, int RPL>
+__device__ __forceinline__ void panel_pair(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T* lb, int lane, int K,
+                                           int& fail) {
+  if constexpr (J + 1 < kNB) {
+    constexpr int J1 = J + 1;
+    const T a00 = __shfl_sync(0xffffffffu, pr[0][J], J);
+    const T a10 = __shfl_sync(0xffffffffu, pr[0][J], J1);
+    const T a11 = __shfl_sync(0xffffffffu, pr[0][J1], J1);
+    if (!(a00 > T(0)) && fail < 0) fail = K + J;
+    T d0, i0;
+    pivot_of(a00 > T(0) ? a00 : T(1), d0, i0);
+    const T l10 = a10 * i0;
+    const T s11 = a11 - l10 * l10;
+    if (!(s11 > T(0)) && fail < 0) fail = K + J1;
+    T d1, i1;
+    pivot_of(s11 > T(0) ? s11 : T(1), d1, i1);
+    T y0[NR], y1[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      y0[c] = __shfl_sync(0xffffffffu, rh[0][c], J) * i0;
+      y1[c] = (__shfl_sync(0xffffffffu, rh[0][c], J1) - l10 * y0[c]) * i1;
+    }
+    T l0q[RPL], l1q[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      // rows at or above J hold no multiplier; rows past the panel are zero
+      const bool b0 = q > 0 || lane > J, b1 = q > 0 || lane > J1;
+      const T l0 = b0 ? pr[q][J] * i0 : T(0);
+      const T l1 = b1 ? (pr[q][J1] - l0 * l10) * i1 : T(0);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) rh[q][c] -= l0 * y0[c] + l1 * y1[c];
+      pr[q][J] = l0;
+      pr[q][J1] = l1;
+      if (q == 0) {
+        if (lane == J) {
+          pr[0][J] = i0;  // the factor blocks keep 1 / L_jj
+#pragma unroll
+          for (int c = 0; c < NR; ++c) rh[0][c] = y0[c];
+        }
+        if (lane == J1) {
+          pr[0][J1] = i1;
+#pragma unroll
+          for (int c = 0; c < NR; ++c) rh[0][c] = y1[c];
+        }
+      }
+      l0q[q] = l0;
+      l1q[q] = l1;
+    }
+    if (J1 + 1 < kNB) {
+      T* lbj = lb + ((J >> 1) & 1) * (2 * kNB);  // alternate buffers: one sync per step
+      if (lane < kNB) {
+        lbj[lane] = l0q[0];
+        lbj[kNB + lane] = l1q[0];
+      }
+      __syncwarp();
+      T L0[kNB], L1[kNB];
+#pragma unroll
+      for (int v = 0; v < kNB / 4; ++v) {
+        if (4 * v + 3 > J1) {
+          if constexpr (sizeof(T) == 4) {
+            const float4 f = reinterpret_cast<const float4*>(lbj)[v];
+            const float4 g = reinterpret_cast<const float4*>(lbj + kNB)[v];
+            L0[4 * v] = f.x; L0[4 * v + 1] = f.y; L0[4 * v + 2] = f.z; L0[4 * v + 3] = f.w;
+            L1[4 * v] = g.x; L1[4 * v + 1] = g.y; L1[4 * v + 2] = g.z; L1[4 * v + 3] = g.w;
+          } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const double2 f = reinterpret_cast<const double2*>(lbj)[2 * v + h];
+              const double2 g = reinterpret_cast<const double2*>(lbj + kNB)[2 * v + h];
+              L0[4 * v + 2 * h] = f.x; L0[4 * v + 2 * h + 1] = f.y;
+              L1[4 * v + 2 * h] = g.x; L1[4 * v + 2 * h + 1] = g.y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) L0[4 * v + k] = L1[4 * v + k] = T(0);
+        }
+      }
+#pragma unroll
+      for (int p = J1 + 1; p < kNB; ++p) {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) pr[q][p] -= l0q[q] * L0[p] + l1q[q] * L1[p];
+      }
+    }
+    panel_pair<J + 2, T, NR, RPL>(pr, rh, lb, lane, K, fail);
+  }
+}
+
 // Factorise (and forward-substitute NR rhs).  Lg: blocks of (NB+bmax) x NB;
 // yg[k*NR + c] receives the forward solution.  Returns -1 or the first
 // failing pivot index (warp-uniform).
@@ -264,10 +372,17 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       for (int c = 0; c < NR; ++c) rh[q][c] = in ? s.rhs[((K + i) & msk) * 4 + c] : T(0);
     }
     int fail = -1;
-    panel_col<0, T, NR, RPL>(pr, rh, s.lb, lane, nb, np, K, fail);
+    if (nb == kNB)
+      panel_pair<0, T, NR, RPL>(pr, rh, s.lb, lane, K, fail);
+    else
+      panel_col<0, T, NR, RPL>(pr, rh, s.lb, lane, nb, np, K, fail);
     if (fail >= 0) return fail;
-    // ---- write the factor block, forward solution, trailing rhs and panel
+    // ---- write the factor block, forward solution, trailing rhs and panel;
+    // rows K..K+NB-1 are retired, and their ring slots (contiguous: RW is a
+    // multiple of NB) hold no live row until the next fill
     T* Lb = Lg + (size_t)kb * LBS;
+    T* pt = s.wnd + (K & msk) * s.PW;
+    __syncwarp();
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int i = lane + 32 * q;
@@ -294,7 +409,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
 #pragma unroll
           for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[q][c];
 #pragma unroll
-          for (int p = 0; p < kNB; ++p) s.pt[p * s.RP + (i - nb)] = pr[q][p];
+          for (int p = 0; p < kNB; ++p) pt[p * s.RP + (i - nb)] = pr[q][p];
         }
       }
     }
@@ -317,7 +432,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
         // L[K+nb+ia][K+p] vanishes for nb + ia - p > b: rows of this tile
         // need p >= nb + 4 ti - b only
         const int p0 = max(0, nb + 4 * ti - b);
-        const T* col = s.pt + p0 * s.RP;
+        const T* col = pt + p0 * s.RP;
 #pragma unroll 4
         for (int p = p0; p < nb; ++p, col += s.RP) {
           T va[4], vc[4];
@@ -356,6 +471,16 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
   return -1;
 }
 
+// The four values of a 16-byte-aligned ring row of a shared [RW][4] array.
+__device__ __forceinline__ void ld_row4(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void ld_row4(const double* p, double (&x)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+  x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
+}
+
 // Asynchronous copy of factor block kb into a staging buffer (one commit group).
 template <typename T>
 __device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int n, int b, int bmax, T* dst,
@@ -391,23 +516,27 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
     }
     __syncwarp();
     const T* tb = s.tb + (kb & 1) * stg;
-    // lane p < nb: yv = y_p - sum over the rows below the block of L[i][p] x_i
+    // column p = lane & 15: yv = y_p - sum over the rows below the block of
+    // L[i][p] x_i, the rows split between the two half-warps
     T yv[NR];
-#pragma unroll
-    for (int c = 0; c < NR; ++c) yv[c] = T(0);
-    if (lane < nb) {
+    {
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; ++c) acc[c] = T(0);
+      const int p = lane & (kNB - 1);
 #pragma unroll 4
-      for (int i = nb; i < np; ++i) {
-        const T l = tb[i * kNB + lane];
-        const T* xi = xr + ((K + i) & msk) * 4;
+      for (int i = nb + (lane >> 4); i < np; i += 2) {
+        const T l = tb[i * kNB + p];
+        T xi[4];
+        ld_row4(xr + ((K + i) & msk) * 4, xi);
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[c] += l * xi[c];
       }
 #pragma unroll
-      for (int c = 0; c < NR; ++c) yv[c] = (T)xg[(size_t)(K + lane) * NR + c] - acc[c];
+      for (int c = 0; c < NR; ++c) {
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+        yv[c] = lane < nb ? (T)xg[(size_t)(K + lane) * NR + c] - acc[c] : T(0);
+      }
     }
     // in-block triangular solve, column oriented: x_p = yv_p / L_pp, then
     // rows p'' < p subtract L[p][p''] x_p
@@ -489,7 +618,7 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
         }
       }
     }
-    T* yb = s.pt;  // block solution broadcast
+    T* yb = s.lb;  // block solution broadcast
     if (lane < nb) {
 #pragma unroll
       for (int c = 0; c < NR; ++c) {

@@ -51,6 +51,15 @@ __device__ inline UnitGeom unit_geom(int nf, int rho, int cx, int cy, int o) {
 struct PatchGen {
   const double* a;  // this sample's coefficient [nf][nf]
   int nf, x0, y0, Nx, Ny, mx;
+  float iNxf, iNyf;  // 1/Nx, 1/Ny, set by finish()
+  double iNxd, iNyd;
+
+  __device__ __forceinline__ void finish() {
+    iNxd = 1.0 / (double)Nx;
+    iNyd = 1.0 / (double)Ny;
+    iNxf = 1.0f / (float)Nx;
+    iNyf = 1.0f / (float)Ny;
+  }
 
   __device__ __forceinline__ double ael(int ex, int ey) const {
     return __ldg(a + (size_t)(y0 + ey) * nf + (x0 + ex));
@@ -135,7 +144,14 @@ struct PatchGen {
     const T aNE = (T)w.ne, aNW = (T)w.nw;
     // divisions replaced by products with reciprocals (one rounding each)
     const T r3 = T(1) / T(3), r6 = T(1) / T(6);
-    const T iNx = T(1) / (T)Nx, iNy = T(1) / (T)Ny;
+    T iNx, iNy;
+    if constexpr (sizeof(T) == 4) {
+      iNx = iNxf;
+      iNy = iNyf;
+    } else {
+      iNx = iNxd;
+      iNy = iNyd;
+    }
     e[0] = (T(2) * r3) * ((aSW + aSE) + (aNE + aNW));
     e[1] = i > 1 ? -(aSW + aNW) * r6 : T(0);
     e[2] = (i < mx && j > 1) ? -aSE * r3 : T(0);
@@ -291,7 +307,8 @@ upscale_kernel(UpscaleArgs A) {
       continue;
     }
     const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
-    const PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
+    PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
+    pg.finish();
     int fail = -1;
     if (g.n > 0) {
       fail = blk_factor<TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, lane);
