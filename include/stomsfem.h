@@ -208,6 +208,19 @@ int stomsfem_pod_destroy(stomsfem_pod* pod);
  * (synchronous). */
 int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host);
 
+/* Checkpoint of the offline stage, so that the online stage (Alg. 4) can run
+ * in another process without repeating Alg. 3.  Serialises the basis W,
+ * load weights, eigenvalues, BF16 element tensors and ranks into the
+ * caller's host buffer: with host_buf NULL only *bytes is set (the size
+ * needed); ENOMEM if buf_bytes is smaller (then *bytes holds the size).
+ * Format: magic "STMFPOD1", format version, byte-order probe, dimensions,
+ * arrays in native byte order.  Synchronous. */
+int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t buf_bytes, size_t* bytes);
+/* Rebuilds a handle from a stomsfem_pod_save buffer.  EVERSION if the magic
+ * tag, format version or byte order differ; EINVAL if the buffer is
+ * truncated or its dimensions are inconsistent.  Synchronous. */
+int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfem_pod** out);
+
 /* Scratch of stomsfem_pod_upscale for S samples (BF16 copy of a by cell and
  * the FP32 reduced matrices). */
 int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* bytes);
@@ -265,6 +278,20 @@ int stomsfem_surrogate_create(const stomsfem_grid* grid, const stomsfem_field* f
 int stomsfem_surrogate_destroy(stomsfem_surrogate* sg);
 /* Copies the FP32 master weights to host [nfam][37264] (synchronous). */
 int stomsfem_surrogate_weights(const stomsfem_surrogate* sg, float* w_host);
+
+/* Checkpoint / resume of a surrogate (no paper counterpart; the paper's
+ * interpolation tables play this role for Alg. 1-2): grid, field, tau, the
+ * FP32 master weights, Adam moments, step count and the per-family training
+ * input box, into the caller's host buffer (host_buf NULL: size only;
+ * ENOMEM if too small).  Format: magic "STMFSUR1", format version,
+ * byte-order probe, then fields in native byte order.  Synchronous. */
+int stomsfem_surrogate_save(const stomsfem_surrogate* sg, void* host_buf, size_t buf_bytes, size_t* bytes);
+/* Rebuilds a surrogate from a stomsfem_surrogate_save buffer; the families
+ * are re-derived from grid, field and tau and must match the stored count.
+ * Training resumes at the stored step.  EVERSION on a foreign or other-
+ * version buffer; EINVAL if truncated or inconsistent.  Synchronous. */
+int stomsfem_surrogate_load(const void* host_buf, size_t buf_bytes, stomsfem_surrogate** out,
+                            int32_t* n_families);
 
 /* Trains on the S samples' (xi, a, K_e, b_e) (device: xi [S][nbx*nby],
  * a [S][nf][nf], Ke [S][nc*nc][10], be [S][nc*nc][4], from the plain

@@ -55,6 +55,8 @@ _SIG = {
                                           ctypes.POINTER(_P), _P, _P]),
     "stomsfem_pod_destroy": (ctypes.c_int, [_P]),
     "stomsfem_pod_eigenvalues": (ctypes.c_int, [_P, _P]),
+    "stomsfem_pod_save": (ctypes.c_int, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
+    "stomsfem_pod_load": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_P)]),
     "stomsfem_pod_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_pod_upscale": (ctypes.c_int, [_P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
     "stomsfem_local_vars": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double,
@@ -63,6 +65,8 @@ _SIG = {
                                                  ctypes.c_double, _P, ctypes.POINTER(_P), _P]),
     "stomsfem_surrogate_destroy": (ctypes.c_int, [_P]),
     "stomsfem_surrogate_weights": (ctypes.c_int, [_P, _P]),
+    "stomsfem_surrogate_save": (ctypes.c_int, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
+    "stomsfem_surrogate_load": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_P), _P]),
     "stomsfem_surrogate_train": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "stomsfem_surrogate_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "stomsfem_surrogate_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),

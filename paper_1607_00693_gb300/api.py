@@ -204,6 +204,37 @@ def xavier_weights(n_families, seed):
     return out
 
 
+def _save(fn, h):
+    n = ctypes.c_size_t()
+    L.check(fn(h, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    L.check(fn(h, buf, n.value, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def stomsfem_pod_save(h):
+    """Serialised offline stage as bytes."""
+    return _save(L.lib().stomsfem_pod_save, h)
+
+
+def stomsfem_pod_load(data: bytes):
+    h = ctypes.c_void_p()
+    L.check(L.lib().stomsfem_pod_load(data, len(data), ctypes.byref(h)))
+    return h
+
+
+def stomsfem_surrogate_save(h):
+    """Serialised surrogate (weights, Adam state, step, input box) as bytes."""
+    return _save(L.lib().stomsfem_surrogate_save, h)
+
+
+def stomsfem_surrogate_load(data: bytes):
+    h = ctypes.c_void_p()
+    nfam = ctypes.c_int32()
+    L.check(L.lib().stomsfem_surrogate_load(data, len(data), ctypes.byref(h), ctypes.byref(nfam)))
+    return h, nfam.value
+
+
 def stomsfem_surrogate_create(g: Grid, fld: Field, tau, init_weights):
     import numpy as np
     w = np.ascontiguousarray(init_weights, dtype=np.float32)

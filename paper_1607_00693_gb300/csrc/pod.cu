@@ -23,6 +23,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ckpt.cuh"
 #include "common.cuh"
 #include "tc_gemm.cuh"
 
@@ -797,6 +798,115 @@ extern "C" int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_hos
   if (!pod || !lam_host) return set_error(STOMSFEM_EINVAL, "NULL argument");
   STOMSFEM_TRY_CUDA(cudaMemcpy(lam_host, pod->lam, sizeof(double) * pod->d.ncell * pod->d.n,
                                cudaMemcpyDeviceToHost));
+  return STOMSFEM_OK;
+}
+
+static const char kPodMagic[8] = {'S', 'T', 'M', 'F', 'P', 'O', 'D', '1'};
+
+extern "C" int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t buf_bytes, size_t* bytes) {
+  if (!pod || !bytes) return set_error(STOMSFEM_EINVAL, "NULL pod / bytes");
+  const PodDims& d = pod->d;
+  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0, nlam = (size_t)d.ncell * d.n;
+  const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
+  std::vector<double> W, wl, lam;
+  std::vector<__nv_bfloat16> T;
+  std::vector<int32_t> rk;
+  if (host_buf) {
+    W.resize(nW);
+    wl.resize(nwl);
+    lam.resize(nlam);
+    T.resize(nT);
+    rk.resize(d.ncell);
+    STOMSFEM_TRY_CUDA(cudaMemcpy(W.data(), pod->W, sizeof(double) * nW, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(wl.data(), pod->wl, sizeof(double) * nwl, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(lam.data(), pod->lam, sizeof(double) * nlam, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(T.data(), pod->T, sizeof(__nv_bfloat16) * nT, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(rk.data(), pod->ranks, sizeof(int32_t) * d.ncell, cudaMemcpyDeviceToHost));
+  }
+  CkptWriter w(host_buf, buf_bytes);
+  ckpt_header(w, kPodMagic);
+  const int32_t dims[11] = {d.nf, d.nc, d.rho, d.N2, d.n, d.ne, d.P0, d.P, d.Ppad, d.ncell, pod->max_rank};
+  w.put(dims, sizeof(dims));
+  w.val<double>(d.f);
+  w.put(host_buf ? (const void*)W.data() : nullptr, sizeof(double) * nW);
+  w.put(host_buf ? (const void*)wl.data() : nullptr, sizeof(double) * nwl);
+  w.put(host_buf ? (const void*)lam.data() : nullptr, sizeof(double) * nlam);
+  w.put(host_buf ? (const void*)T.data() : nullptr, sizeof(__nv_bfloat16) * nT);
+  w.put(host_buf ? (const void*)rk.data() : nullptr, sizeof(int32_t) * d.ncell);
+  *bytes = w.pos;
+  if (host_buf && !w.fits()) return set_error(STOMSFEM_ENOMEM, "checkpoint buffer %zu < %zu bytes", buf_bytes, w.pos);
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfem_pod** out) {
+  if (!host_buf || !out) return set_error(STOMSFEM_EINVAL, "NULL buffer / out");
+  *out = nullptr;
+  CkptReader r(host_buf, buf_bytes);
+  const int hc = ckpt_check_header(r, kPodMagic);
+  if (hc == 1) return set_error(STOMSFEM_EVERSION, "not a version-%u POD checkpoint", kCkptVersion);
+  if (hc == 2) return set_error(STOMSFEM_EINVAL, "truncated POD checkpoint");
+  int32_t dims[11];
+  r.get(dims, sizeof(dims));
+  PodDims d;
+  d.nf = dims[0];
+  d.nc = dims[1];
+  d.rho = dims[2];
+  d.N2 = dims[3];
+  d.n = dims[4];
+  d.ne = dims[5];
+  d.P0 = dims[6];
+  d.P = dims[7];
+  d.Ppad = dims[8];
+  d.ncell = dims[9];
+  d.f = r.val<double>();
+  const int rcap = dims[10];
+  // the stored sizes must be the ones the build derives from the grid
+  const bool consistent = r.ok && d.nc > 0 && d.nf % d.nc == 0 && d.rho == d.nf / d.nc && d.rho >= 2 &&
+                          d.rho <= kPodMaxRho && d.N2 == (d.rho + 1) * (d.rho + 1) &&
+                          d.n == (d.rho - 1) * (d.rho - 1) && d.ne == d.rho * d.rho && d.ncell == d.nc * d.nc &&
+                          rcap >= 1 && rcap <= d.n && d.P0 == 4 + rcap && d.P == d.P0 * (d.P0 + 1) / 2 &&
+                          d.Ppad == ((d.P + 15) & ~15);
+  if (!consistent) return set_error(STOMSFEM_EINVAL, "inconsistent POD checkpoint header");
+  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0, nlam = (size_t)d.ncell * d.n;
+  const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
+  const size_t need = r.pos + sizeof(double) * (nW + nwl + nlam) + sizeof(__nv_bfloat16) * nT +
+                      sizeof(int32_t) * d.ncell;
+  if (buf_bytes < need) return set_error(STOMSFEM_EINVAL, "truncated POD checkpoint (%zu < %zu)", buf_bytes, need);
+  const unsigned char* base = static_cast<const unsigned char*>(host_buf) + r.pos;
+  auto* p = new stomsfem_pod();
+  p->d = d;
+  p->max_rank = rcap;
+  int rc;
+#define TRY(x)                                     \
+  if ((rc = check_cuda((x), #x)) != STOMSFEM_OK) { \
+    pod_free(p);                                   \
+    return rc;                                     \
+  }
+  TRY(cudaMalloc(&p->W, sizeof(double) * nW));
+  TRY(cudaMalloc(&p->wl, sizeof(double) * nwl));
+  TRY(cudaMalloc(&p->lam, sizeof(double) * nlam));
+  TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * nT));
+  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell));
+  TRY(cudaMalloc(&p->err, sizeof(int32_t)));
+  TRY(cudaMemcpy(p->W, base, sizeof(double) * nW, cudaMemcpyHostToDevice));
+  base += sizeof(double) * nW;
+  TRY(cudaMemcpy(p->wl, base, sizeof(double) * nwl, cudaMemcpyHostToDevice));
+  base += sizeof(double) * nwl;
+  TRY(cudaMemcpy(p->lam, base, sizeof(double) * nlam, cudaMemcpyHostToDevice));
+  base += sizeof(double) * nlam;
+  TRY(cudaMemcpy(p->T, base, sizeof(__nv_bfloat16) * nT, cudaMemcpyHostToDevice));
+  base += sizeof(__nv_bfloat16) * nT;
+  std::vector<int32_t> rk(d.ncell);
+  std::memcpy(rk.data(), base, sizeof(int32_t) * d.ncell);
+  for (int c = 0; c < d.ncell; ++c)
+    if (rk[c] < 0 || rk[c] > rcap) {
+      pod_free(p);
+      return set_error(STOMSFEM_EINVAL, "POD checkpoint: rank %d of cell %d outside [0, %d]", rk[c], c, rcap);
+    }
+  TRY(cudaMemcpy(p->ranks, rk.data(), sizeof(int32_t) * d.ncell, cudaMemcpyHostToDevice));
+  TRY(cudaMemset(p->err, 0, sizeof(int32_t)));
+#undef TRY
+  *out = p;
   return STOMSFEM_OK;
 }
 

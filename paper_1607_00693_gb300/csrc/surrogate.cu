@@ -25,6 +25,7 @@
 #include <map>
 #include <vector>
 
+#include "ckpt.cuh"
 #include "common.cuh"
 #include "stomsfem.h"
 #include "tc_gemm.cuh"
@@ -786,6 +787,109 @@ extern "C" int stomsfem_surrogate_destroy(stomsfem_surrogate* h) {
 extern "C" int stomsfem_surrogate_weights(const stomsfem_surrogate* h, float* w_host) {
   if (!h || !w_host) return set_error(STOMSFEM_EINVAL, "NULL argument");
   STOMSFEM_TRY_CUDA(cudaMemcpy(w_host, h->W, sizeof(float) * h->nfam * kParams, cudaMemcpyDeviceToHost));
+  return STOMSFEM_OK;
+}
+
+static const char kSgMagic[8] = {'S', 'T', 'M', 'F', 'S', 'U', 'R', '1'};
+
+extern "C" int stomsfem_surrogate_save(const stomsfem_surrogate* h, void* host_buf, size_t buf_bytes,
+                                       size_t* bytes) {
+  if (!h || !bytes) return set_error(STOMSFEM_EINVAL, "NULL surrogate / bytes");
+  const size_t np = (size_t)h->nfam * kParams, nb = (size_t)h->nfam * kIn * 2;
+  std::vector<float> W, m, v, box;
+  if (host_buf) {
+    W.resize(np);
+    m.resize(np);
+    v.resize(np);
+    box.resize(nb);
+    STOMSFEM_TRY_CUDA(cudaMemcpy(W.data(), h->W, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(m.data(), h->m, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(v.data(), h->v, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(box.data(), h->box, sizeof(float) * nb, cudaMemcpyDeviceToHost));
+  }
+  CkptWriter w(host_buf, buf_bytes);
+  ckpt_header(w, kSgMagic);
+  w.val<int32_t>(h->grid.nf);
+  w.val<int32_t>(h->grid.nc);
+  w.val<double>(h->grid.f);
+  w.val<int32_t>(h->field.kind);
+  w.val<int32_t>(h->field.nbx);
+  w.val<int32_t>(h->field.nby);
+  w.val<double>(h->field.width);
+  w.val<double>(h->field.scale);
+  w.val<double>(h->field.contrast_log);
+  w.val<double>(h->field.gain);
+  w.val<double>(h->tau);
+  w.val<int32_t>(h->nfam);
+  w.val<int32_t>(kParams);
+  w.val<int32_t>(h->step);
+  w.put(host_buf ? (const void*)W.data() : nullptr, sizeof(float) * np);
+  w.put(host_buf ? (const void*)m.data() : nullptr, sizeof(float) * np);
+  w.put(host_buf ? (const void*)v.data() : nullptr, sizeof(float) * np);
+  w.put(host_buf ? (const void*)box.data() : nullptr, sizeof(float) * nb);
+  *bytes = w.pos;
+  if (host_buf && !w.fits()) return set_error(STOMSFEM_ENOMEM, "checkpoint buffer %zu < %zu bytes", buf_bytes, w.pos);
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_surrogate_load(const void* host_buf, size_t buf_bytes, stomsfem_surrogate** out,
+                                       int32_t* n_families) {
+  if (!host_buf || !out) return set_error(STOMSFEM_EINVAL, "NULL buffer / out");
+  *out = nullptr;
+  CkptReader r(host_buf, buf_bytes);
+  const int hc = ckpt_check_header(r, kSgMagic);
+  if (hc == 1) return set_error(STOMSFEM_EVERSION, "not a version-%u surrogate checkpoint", kCkptVersion);
+  if (hc == 2) return set_error(STOMSFEM_EINVAL, "truncated surrogate checkpoint");
+  stomsfem_grid g;
+  g.nf = r.val<int32_t>();
+  g.nc = r.val<int32_t>();
+  g.f = r.val<double>();
+  stomsfem_field fd;
+  fd.kind = r.val<int32_t>();
+  fd.nbx = r.val<int32_t>();
+  fd.nby = r.val<int32_t>();
+  fd.width = r.val<double>();
+  fd.scale = r.val<double>();
+  fd.contrast_log = r.val<double>();
+  fd.gain = r.val<double>();
+  const double tau = r.val<double>();
+  const int32_t nfam = r.val<int32_t>(), nparams = r.val<int32_t>(), step = r.val<int32_t>();
+  if (!r.ok || nfam < 1 || nparams != kParams || step < 0)
+    return set_error(STOMSFEM_EINVAL, "inconsistent surrogate checkpoint header");
+  const size_t np = (size_t)nfam * kParams, nb = (size_t)nfam * kIn * 2;
+  if (buf_bytes < r.pos + sizeof(float) * (3 * np + nb))
+    return set_error(STOMSFEM_EINVAL, "truncated surrogate checkpoint");
+  const float* W = reinterpret_cast<const float*>(static_cast<const unsigned char*>(host_buf) + r.pos);
+  std::vector<float> Wc(W, W + np);  // the buffer need not be 4-byte aligned
+  stomsfem_surrogate* h = nullptr;
+  int32_t nf2 = 0;
+  int rc = stomsfem_surrogate_create(&g, &fd, tau, Wc.data(), &h, &nf2);
+  if (rc) return rc;
+  if (nf2 != nfam) {
+    sg_free(h);
+    return set_error(STOMSFEM_EINVAL, "surrogate checkpoint has %d families, the grid/field give %d", nfam, nf2);
+  }
+  std::vector<float> tmp(np > nb ? np : nb);
+  const unsigned char* base = static_cast<const unsigned char*>(host_buf) + r.pos + sizeof(float) * np;
+  std::memcpy(tmp.data(), base, sizeof(float) * np);
+  rc = check_cuda(cudaMemcpy(h->m, tmp.data(), sizeof(float) * np, cudaMemcpyHostToDevice), "copy m");
+  base += sizeof(float) * np;
+  if (!rc) {
+    std::memcpy(tmp.data(), base, sizeof(float) * np);
+    rc = check_cuda(cudaMemcpy(h->v, tmp.data(), sizeof(float) * np, cudaMemcpyHostToDevice), "copy v");
+  }
+  base += sizeof(float) * np;
+  if (!rc) {
+    std::memcpy(tmp.data(), base, sizeof(float) * nb);
+    rc = check_cuda(cudaMemcpy(h->box, tmp.data(), sizeof(float) * nb, cudaMemcpyHostToDevice), "copy box");
+  }
+  if (rc) {
+    sg_free(h);
+    return rc;
+  }
+  h->step = step;
+  if (n_families) *n_families = nfam;
+  *out = h;
   return STOMSFEM_OK;
 }
 

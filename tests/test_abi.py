@@ -76,3 +76,25 @@ def test_selftest_rejects_bad_limits(lib):
     assert lib.stomsfem_selftest_wait_timeout(0, ctypes.byref(st)) == L.EINVAL
     assert lib.stomsfem_selftest_wait_timeout((1 << 20) + 1, ctypes.byref(st)) == L.EINVAL
     assert lib.stomsfem_selftest_wait_timeout(10, None) == L.EINVAL
+
+
+def test_checkpoint_headers_rejected_without_gpu(lib):
+    """Foreign or other-version buffers give EVERSION and truncated ones
+    EINVAL before any device work."""
+    import ctypes
+    h = ctypes.c_void_p()
+    n = ctypes.c_int32()
+    junk = b"NOTACKPT" + b"\x01\x00\x00\x00" + b"\x04\x03\x02\x01" + b"\x00" * 64
+    assert lib.stomsfem_pod_load(junk, len(junk), ctypes.byref(h)) == L.EVERSION
+    assert lib.stomsfem_surrogate_load(junk, len(junk), ctypes.byref(h), ctypes.byref(n)) == L.EVERSION
+    other = b"STMFPOD1" + b"\x02\x00\x00\x00" + b"\x04\x03\x02\x01" + b"\x00" * 64
+    assert lib.stomsfem_pod_load(other, len(other), ctypes.byref(h)) == L.EVERSION
+    assert b"version" in lib.stomsfem_last_error()
+    assert lib.stomsfem_pod_load(b"STMFPOD1", 8, ctypes.byref(h)) == L.EINVAL
+    short = b"STMFSUR1" + b"\x01\x00\x00\x00" + b"\x04\x03\x02\x01" + b"\x00" * 8
+    assert lib.stomsfem_surrogate_load(short, len(short), ctypes.byref(h), ctypes.byref(n)) == L.EINVAL
+    # a POD header whose dimensions do not follow from its grid
+    import struct
+    bad = b"STMFPOD1" + struct.pack("<II", 1, 0x01020304) + struct.pack("<11i", 64, 8, 8, 81, 49, 64, 31,
+                                                                       496, 496, 64, 99) + struct.pack("<d", 1.0)
+    assert lib.stomsfem_pod_load(bad, len(bad), ctypes.byref(h)) == L.EINVAL

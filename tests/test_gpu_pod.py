@@ -107,3 +107,20 @@ def test_pod_vs_plain_msfem(setup):
     Kp, bp = setup["oracle"].upscale(setup["nf"], setup["nc"], 1.0, setup["a_te"])
     Kg, _, _ = _gpu(setup, refine=8)
     assert _rel(Kg, Kp) <= 1e-4
+
+
+def test_pod_checkpoint_roundtrip(setup):
+    """A saved and reloaded offline stage gives bit-identical online results
+    (refined and unrefined) and the same ranks and eigenvalues."""
+    data = api.stomsfem_pod_save(setup["h"])
+    h2 = api.stomsfem_pod_load(data)
+    try:
+        for refine in (0, 2):
+            K1, b1, s1 = _gpu(setup, refine)
+            K2, b2, s2 = _gpu(setup, refine, handle=h2)
+            assert np.array_equal(K1, K2) and np.array_equal(b1, b2) and np.array_equal(s1, s2)
+        g = setup["g"]
+        assert np.array_equal(api.stomsfem_pod_eigenvalues(h2, g), api.stomsfem_pod_eigenvalues(setup["h"], g))
+        assert api.stomsfem_pod_save(h2) == data
+    finally:
+        api.stomsfem_pod_destroy(h2)

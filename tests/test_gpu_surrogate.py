@@ -165,3 +165,55 @@ def test_trained_surrogate_coarse_error(trained):
         assert fb0.mean() > 0.9 or e0.max() > 10 * err.max()
     finally:
         api.stomsfem_surrogate_destroy(h0)
+
+
+def test_surrogate_checkpoint_roundtrip(trained):
+    """Save / load keeps weights, Adam state, step and input box: inference
+    is bit-identical, and resumed training matches uninterrupted training."""
+    w, g, h, nfam, _ = trained
+    data = api.stomsfem_surrogate_save(h)
+    h2, nf2 = api.stomsfem_surrogate_load(data)
+    try:
+        assert nf2 == nfam
+        assert np.array_equal(api.stomsfem_surrogate_weights(h2, nfam), api.stomsfem_surrogate_weights(h, nfam))
+        r1 = _infer(h, g, 6, 91)
+        r2 = _infer(h2, g, 6, 91)
+        for x, y in zip(r1[2:5], r2[2:5]):
+            assert np.array_equal(x, y)
+        assert api.stomsfem_surrogate_save(h2) == data
+    finally:
+        api.stomsfem_surrogate_destroy(h2)
+
+
+def test_surrogate_resume_equals_continuous():
+    """Training 40 steps, saving, loading and training 40 more follows
+    uninterrupted 80-step training (up to the run-to-run jitter of the
+    shared-memory bias-gradient sums), and much more closely than a restart
+    from the same weights with fresh Adam state and step count does."""
+    w, g, xt, a, Ke, be = _training_set(64, 4)
+    fld = api.field_from_dict(w["field"])
+    _, _, _, nfam = api.stomsfem_local_vars(g, fld, 1e-6)
+    w0 = api.xavier_weights(nfam, 1)
+    hs = []
+    try:
+        ha, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, w0)
+        hs.append(ha)
+        hb, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, w0)
+        hs.append(hb)
+        api.stomsfem_surrogate_train(ha, xt, a, Ke, be, steps=40, seed=5)
+        api.stomsfem_surrogate_train(ha, xt, a, Ke, be, steps=40, seed=5)
+        api.stomsfem_surrogate_train(hb, xt, a, Ke, be, steps=40, seed=5)
+        hc, _ = api.stomsfem_surrogate_load(api.stomsfem_surrogate_save(hb))
+        hs.append(hc)
+        hd, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.stomsfem_surrogate_weights(hb, nfam))
+        hs.append(hd)
+        api.stomsfem_surrogate_train(hc, xt, a, Ke, be, steps=40, seed=5)
+        api.stomsfem_surrogate_train(hd, xt, a, Ke, be, steps=40, seed=5)
+        wa, wc, wd = (api.stomsfem_surrogate_weights(h, nfam).astype(np.float64) for h in (ha, hc, hd))
+        resumed = np.linalg.norm(wc - wa)
+        restarted = np.linalg.norm(wd - wa)
+        assert resumed <= 1e-3 * np.linalg.norm(wa)
+        assert resumed <= 0.1 * restarted
+    finally:
+        for h in hs:
+            api.stomsfem_surrogate_destroy(h)
