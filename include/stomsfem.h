@@ -82,6 +82,11 @@ const char* stomsfem_last_error(void);
  * Synchronous; the device stays usable afterwards.  1 <= iters <= 2^20. */
 int stomsfem_selftest_wait_timeout(int32_t iters, int32_t* status_host);
 
+/* Self test of the table-driven FP64 exponential that the coefficient
+ * sampler uses (no paper counterpart): out[i] = exp(t[i]) for device arrays
+ * of n doubles, stream-ordered.  EINVAL for n < 0 or NULL pointers. */
+int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stream_t stream);
+
 /* Coefficient sampling (Sec. 2.1.3, the parametrized coefficient of
  * Eq. MsFEB2).  xi: device [S][nbx*nby] float64; a: device [S][nf][nf]
  * float64, a value per fine element at its centroid ((ex+1/2)h, (ey+1/2)h).

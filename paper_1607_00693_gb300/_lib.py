@@ -40,6 +40,7 @@ _SIG = {
     "stomsfem_version": (ctypes.c_char_p, []),
     "stomsfem_last_error": (ctypes.c_char_p, []),
     "stomsfem_selftest_wait_timeout": (ctypes.c_int, [_I, ctypes.POINTER(_I)]),
+    "stomsfem_selftest_exp": (ctypes.c_int, [_P, _I, _P, _P]),
     "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
     "stomsfem_upscale_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I,
                                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),

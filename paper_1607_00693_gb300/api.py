@@ -60,6 +60,15 @@ def stomsfem_selftest_wait_timeout(iters=20000):
     return st.value
 
 
+def stomsfem_selftest_exp(t, out=None, stream=None):
+    """exp of a float64 device tensor by the sampler's table-driven routine."""
+    if out is None:
+        out = torch.empty_like(t)
+    L.check(L.lib().stomsfem_selftest_exp(_dev(t, torch.float64, None, "t"), t.numel(),
+                                          _dev(out, torch.float64, tuple(t.shape), "out"), _stream(stream)))
+    return out
+
+
 def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
     S = xi.shape[0]
     L.check(L.lib().stomsfem_sample_coef(ctypes.byref(g), ctypes.byref(fld),

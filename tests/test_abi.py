@@ -98,3 +98,9 @@ def test_checkpoint_headers_rejected_without_gpu(lib):
     bad = b"STMFPOD1" + struct.pack("<II", 1, 0x01020304) + struct.pack("<11i", 64, 8, 8, 81, 49, 64, 31,
                                                                        496, 496, 64, 99) + struct.pack("<d", 1.0)
     assert lib.stomsfem_pod_load(bad, len(bad), ctypes.byref(h)) == L.EINVAL
+
+
+def test_selftest_exp_argument_checks(lib):
+    assert lib.stomsfem_selftest_exp(None, -1, None, None) == L.EINVAL
+    assert lib.stomsfem_selftest_exp(None, 0, None, None) == L.OK
+    assert lib.stomsfem_selftest_exp(None, 5, None, None) == L.EINVAL
