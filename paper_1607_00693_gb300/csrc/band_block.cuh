@@ -128,17 +128,20 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Zero n16 consecutive 16-byte chunks of shared memory.
+__device__ __forceinline__ void blk_zero16(void* dst, int n16, int lane) {
+  float4* d = reinterpret_cast<float4*>(dst);
+  for (int v = lane; v < n16; v += 32) d[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Rows [r0, r1) of the window (at most 32 rows; row r0 + l uses lane l's raw
-// values): zero the band, then the generator's entries and rhs.
+// values): the generator's entries and rhs.  The rows' ring slots are zero
+// on entry (the whole window is cleared when a factorisation starts, and each
+// block's slots again once the block is retired).
 template <typename T, int NR, class Gen>
 __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int b, int lane,
                                              const typename Gen::Raw& raw) {
   const int msk = s.RW - 1;
-  for (int r = r0; r < r1; ++r) {
-    T* row = s.wnd + (r & msk) * s.PW;
-    for (int d = lane; d <= b; d += 32) row[d] = T(0);
-  }
-  __syncwarp();
   const int mx = gen.mx;
   const int r = r0 + lane;
   if (r < r1) {
@@ -327,6 +330,9 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
                           T* __restrict__ Lg, TS* __restrict__ yg, int lane) {
   const int LBS = (kNB + bmax) * kNB;
   const int msk = s.RW - 1;
+  const int blk16 = kNB * s.PW * (int)sizeof(T) / 16;  // 16-byte chunks of NB ring rows
+  blk_zero16(s.wnd, s.RW / kNB * blk16, lane);
+  __syncwarp();
   // first window: rows [0, min(n, NB + b)), generated directly
   int filled = min(n, kNB + b);
   for (int r0 = 0; r0 < filled; r0 += 32) {
@@ -467,6 +473,10 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       }
     }
     __syncwarp();
+    // the retired rows' slots (which held the trailing panel) are cleared for
+    // the rows that will occupy them
+    blk_zero16(pt, blk16, lane);
+    __syncwarp();
   }
   return -1;
 }
@@ -516,6 +526,11 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
     }
     __syncwarp();
     const T* tb = s.tb + (kb & 1) * stg;
+    // the block's forward solution, loaded before the sums so that its
+    // latency overlaps them
+    T yin[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) yin[c] = lane < nb ? (T)xg[(size_t)(K + lane) * NR + c] : T(0);
     // column p = lane & 15: yv = y_p - sum over the rows below the block of
     // L[i][p] x_i, the rows split between the two half-warps
     T yv[NR];
@@ -535,26 +550,53 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
         acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
-        yv[c] = lane < nb ? (T)xg[(size_t)(K + lane) * NR + c] - acc[c] : T(0);
+        yv[c] = lane < nb ? yin[c] - acc[c] : T(0);
       }
     }
     // in-block triangular solve, column oriented: x_p = yv_p / L_pp, then
-    // rows p'' < p subtract L[p][p''] x_p
+    // rows q < p subtract L[p][q] x_p; full blocks take the columns in pairs
+    // (p, p-1), which shortens the dependent chain of shuffles
+    if (nb == kNB) {
 #pragma unroll
-    for (int p = kNB - 1; p >= 0; --p) {
-      if (p < nb) {
-        const T iLpp = tb[p * kNB + p];
-        T xp[NR];
+      for (int p = kNB - 1; p >= 1; p -= 2) {
+        const T i1 = tb[p * kNB + p], i0 = tb[(p - 1) * kNB + p - 1], lpq = tb[p * kNB + p - 1];
+        T x1[NR], x0[NR];
 #pragma unroll
-        for (int c = 0; c < NR; ++c) xp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
-        if (lane < p) {
-          const T l = tb[p * kNB + lane];
+        for (int c = 0; c < NR; ++c) {
+          x1[c] = __shfl_sync(0xffffffffu, yv[c], p) * i1;
+          x0[c] = (__shfl_sync(0xffffffffu, yv[c], p - 1) - lpq * x1[c]) * i0;
+        }
+        if (lane < p - 1) {
+          const T l1 = tb[p * kNB + lane], l0 = tb[(p - 1) * kNB + lane];
 #pragma unroll
-          for (int c = 0; c < NR; ++c) yv[c] -= l * xp[c];
+          for (int c = 0; c < NR; ++c) yv[c] -= l1 * x1[c] + l0 * x0[c];
         }
         if (lane == p) {
 #pragma unroll
-          for (int c = 0; c < NR; ++c) yv[c] = xp[c];
+          for (int c = 0; c < NR; ++c) yv[c] = x1[c];
+        }
+        if (lane == p - 1) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) yv[c] = x0[c];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int p = kNB - 1; p >= 0; --p) {
+        if (p < nb) {
+          const T iLpp = tb[p * kNB + p];
+          T xp[NR];
+#pragma unroll
+          for (int c = 0; c < NR; ++c) xp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
+          if (lane < p) {
+            const T l = tb[p * kNB + lane];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) yv[c] -= l * xp[c];
+          }
+          if (lane == p) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c) yv[c] = xp[c];
+          }
         }
       }
     }
