@@ -1,25 +1,31 @@
-// Blocked warp-level banded SPD solver for 9-point-stencil matrices (one
-// warp per system).
+// Blocked banded SPD solver for 9-point-stencil matrices, one system per
+// group of G lanes (G = 32: one system per warp; G = 16: two systems of the
+// same shape per warp, which run in lockstep so that every warp-wide sync
+// and every loop bound is shared by both halves).
 //
-// Right-looking banded Cholesky in column blocks of NB = 16.  For block K
-// (rows/columns [K, K+nb)) the warp
+// Right-looking banded Cholesky in column blocks of NB = G/2.  For block K
+// (rows/columns [K, K+nb)) the group
 //   1. factorises the tall panel [K, K+np) x [K, K+nb), np = nb + b: each
-//      lane holds up to RPL panel rows in registers; the block-row
-//      multipliers of each column step are broadcast through a
-//      double-buffered shared vector (128-bit loads, one warp sync per
-//      step); the NR right-hand sides ride along, which is the forward
-//      substitution;
+//      lane holds up to RPL panel rows in registers; full blocks take the
+//      columns in pairs (the 2 x 2 diagonal block from three shuffled
+//      entries, both columns of multipliers broadcast through a
+//      double-buffered shared vector, one warp sync per pair); the NR
+//      right-hand sides ride along, which is the forward substitution;
 //   2. applies the rank-nb update to the trailing b x b window with 4 x 4
-//      register tiles (128-bit shared loads of the transposed panel);
-//   3. retires the block's rows and writes the next rows from values the
-//      row generator loaded one block earlier (so the global-load latency
-//      hides behind the panel and the trailing update).
+//      register tiles (128-bit shared loads of the transposed panel, which
+//      is kept in the ring slots of the rows just retired);
+//   3. clears the retired slots and writes the next rows from values the
+//      row generator copied into shared memory one block earlier.
 // The matrix lives only as a window of RW >= NB + b band rows in shared
-// memory (RW a power of two; row r at slot r & (RW-1), entry A[r][r-d] at
+// memory (RW a multiple of NB; row r at slot r mod RW, entry A[r][r-d] at
 // column d).  Factor blocks go to global scratch as (NB + bmax) x NB
 // row-major tiles; the substitutions stream them back through two shared
 // staging buffers with asynchronous copies (next block in flight while the
 // current one is used).
+//
+// A failing pivot does not end the factorisation early (the two systems of
+// a warp must stay in lockstep): it is replaced by 1, the first failing
+// index is returned, and the caller discards the results.
 //
 // Row generator interface:
 //   typename Gen::Raw                  raw per-row values,
@@ -36,16 +42,16 @@
 
 namespace stomsfem {
 
-constexpr int kNB = 16;
+constexpr int kMaxNB = 16;
 
 template <typename T>
 struct BlkSmem {
-  T* wnd;  // [RW][PW] band rows; the 16 ring rows of the block just
+  T* wnd;  // [RW][PW] band rows; the NB ring rows of the block just
            // factorised hold the trailing panel for the update,
            // p-major: pt[p*RP + (i - nb)] = L[K+i][K+p]
   T* tb;   // 2 x [NB + bmax][NB] factor block staging (aliases wnd)
   T* rhs;  // [RW][4]
-  T* lb;   // 2 x [NB] broadcast of the block-row multipliers; [NB][4]
+  T* lb;   // 2 x 2 x [NB] broadcast of the block-row multipliers; [NB][4]
            // block solution in the stored forward substitution
   double* raw;  // [NB][4] coefficient values of the next rows (async prefetch)
   int RW, PW, RP;
@@ -53,11 +59,7 @@ struct BlkSmem {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline int blk_ring_rows(int bmax) {
-  int r = 16;
-  while (r < kNB + bmax) r <<= 1;
-  return r;
-}
+__host__ __device__ inline int blk_ring_rows(int NB, int bmax) { return (NB + bmax + NB - 1) / NB * NB; }
 
 // Row pitch: b + 1 band entries, and at least RP = bmax rounded up to 4 so
 // that NB rows hold the transposed trailing panel.
@@ -66,39 +68,43 @@ __host__ __device__ inline int blk_pitch(int bmax) {
   return bmax + 1 > rp ? bmax + 1 : rp;
 }
 
-__host__ __device__ inline int blk_wnd_elems(int bmax) {
-  const int a = blk_ring_rows(bmax) * blk_pitch(bmax), b = 2 * (kNB + bmax) * kNB;
+__host__ __device__ inline int blk_wnd_elems(int NB, int bmax) {
+  const int a = blk_ring_rows(NB, bmax) * blk_pitch(bmax), b = 2 * (NB + bmax) * NB;
   return a > b ? a : b;
 }
 
 template <typename T>
-__host__ __device__ inline size_t blk_smem_bytes(int bmax) {
-  const int RW = blk_ring_rows(bmax);
-  return al16(sizeof(T) * blk_wnd_elems(bmax)) + al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 4 * kNB) +
-         al16(sizeof(double) * kNB * 4);
+__host__ __device__ inline size_t blk_smem_bytes(int NB, int bmax) {
+  const int RW = blk_ring_rows(NB, bmax);
+  return al16(sizeof(T) * blk_wnd_elems(NB, bmax)) + al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 4 * NB) +
+         al16(sizeof(double) * NB * 4);
 }
 
 template <typename T>
-__device__ inline BlkSmem<T> make_blk(unsigned char* base, int bmax) {
+__device__ inline BlkSmem<T> make_blk(unsigned char* base, int NB, int bmax) {
   BlkSmem<T> s;
-  s.RW = blk_ring_rows(bmax);
+  s.RW = blk_ring_rows(NB, bmax);
   s.PW = blk_pitch(bmax);
   s.RP = (bmax + 3) & ~3;
   size_t o = 0;
   s.wnd = reinterpret_cast<T*>(base + o);
   s.tb = s.wnd;
-  o += al16(sizeof(T) * blk_wnd_elems(bmax));
+  o += al16(sizeof(T) * blk_wnd_elems(NB, bmax));
   s.rhs = reinterpret_cast<T*>(base + o);
   o += al16(sizeof(T) * s.RW * 4);
   s.lb = reinterpret_cast<T*>(base + o);
-  o += al16(sizeof(T) * 4 * kNB);
+  o += al16(sizeof(T) * 4 * NB);
   s.raw = reinterpret_cast<double*>(base + o);
   return s;
 }
 
+// Factor scratch (elements) of one system; an upper bound for every NB <= 16.
 __host__ __device__ inline size_t blk_factor_elems(int n, int bmax) {
-  return (size_t)((n + kNB - 1) / kNB) * (kNB + bmax) * kNB;
+  return (size_t)((n + kMaxNB - 1) / kMaxNB) * (kMaxNB + bmax) * kMaxNB;
 }
+
+// x mod RW for 0 <= x < 2 RW.
+__device__ __forceinline__ int ring(int x, int RW) { return x >= RW ? x - RW : x; }
 
 // The pivot and its reciprocal.  FP32: the hardware reciprocal square root
 // (relative error a few ulp), which perturbs the factor at the level of FP32
@@ -110,6 +116,11 @@ __device__ __forceinline__ void pivot_of(float a, float& d, float& dinv) {
 __device__ __forceinline__ void pivot_of(double a, double& d, double& dinv) {
   d = sqrt(a);
   dinv = 1.0 / d;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T gshfl(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src, G);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -128,26 +139,28 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Zero n16 consecutive 16-byte chunks of shared memory.
-__device__ __forceinline__ void blk_zero16(void* dst, int n16, int lane) {
+// Zero n16 consecutive 16-byte chunks of shared memory (lanes gl of G).
+template <int G>
+__device__ __forceinline__ void blk_zero16(void* dst, int n16, int gl) {
   float4* d = reinterpret_cast<float4*>(dst);
-  for (int v = lane; v < n16; v += 32) d[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int v = gl; v < n16; v += G) d[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Rows [r0, r1) of the window (at most 32 rows; row r0 + l uses lane l's raw
-// values): the generator's entries and rhs.  The rows' ring slots are zero
-// on entry (the whole window is cleared when a factorisation starts, and each
-// block's slots again once the block is retired).
-template <typename T, int NR, class Gen>
-__device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int b, int lane,
-                                             const typename Gen::Raw& raw) {
-  const int msk = s.RW - 1;
+// Rows [r0, r1) of the window (at most G rows, in ring slots slot0,
+// slot0 + 1, ... mod RW; row r0 + l uses lane l's raw values): the
+// generator's entries and rhs.  The slots are zero on entry (the whole
+// window is cleared when a factorisation starts, and each block's slots
+// again once the block is retired).
+template <int G, typename T, int NR, class Gen>
+__device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s, int r0, int r1, int slot0, int b,
+                                             int gl, const typename Gen::Raw& raw) {
   const int mx = gen.mx;
-  const int r = r0 + lane;
+  const int r = r0 + gl;
   if (r < r1) {
     T e[5], rh[NR];
     gen.template make<T>(r, raw, e, rh);
-    T* row = s.wnd + (r & msk) * s.PW;
+    const int slot = ring(slot0 + gl, s.RW);
+    T* row = s.wnd + slot * s.PW;
     if (mx >= 3 && mx + 1 <= b) {
       // offsets 0, 1, mx-1, mx, mx+1 are distinct: plain stores
       row[0] = e[0];
@@ -163,28 +176,51 @@ __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s
       if (r >= mx + 1 && mx + 1 <= b) row[mx + 1] += e[4];
     }
 #pragma unroll
-    for (int c = 0; c < NR; ++c) s.rhs[(r & msk) * 4 + c] = rh[c];
+    for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[c];
   }
 }
 
-// One column step j = J of the panel factorisation, then the next; the
-// recursion keeps every register-array index a compile-time constant.
-template <int J, typename T, int NR, int RPL>
-__device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T* lb, int lane,
-                                          int nb, int np, int K, int& fail) {
-  if constexpr (J < kNB) {
-    if (J < nb && fail < 0) {
-      const T dj = __shfl_sync(0xffffffffu, pr[0][J], J);
-      if (!(dj > T(0))) fail = K + J;
+// Load NB consecutive values of a shared buffer into registers (16-byte
+// loads); groups wholly below index `from` are set to zero instead.
+template <int NB, typename T>
+__device__ __forceinline__ void ld_vec(const T* src, T (&v)[NB], int from) {
+#pragma unroll
+  for (int g = 0; g < NB / 4; ++g) {
+    if (4 * g + 3 >= from) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 f = reinterpret_cast<const float4*>(src)[g];
+        v[4 * g] = f.x; v[4 * g + 1] = f.y; v[4 * g + 2] = f.z; v[4 * g + 3] = f.w;
+      } else {
+        const double2 f0 = reinterpret_cast<const double2*>(src)[2 * g];
+        const double2 f1 = reinterpret_cast<const double2*>(src)[2 * g + 1];
+        v[4 * g] = f0.x; v[4 * g + 1] = f0.y; v[4 * g + 2] = f1.x; v[4 * g + 3] = f1.y;
+      }
+    } else {
+      v[4 * g] = v[4 * g + 1] = v[4 * g + 2] = v[4 * g + 3] = T(0);
+    }
+  }
+}
+
+// One column step j = J of the panel factorisation (partial last block),
+// then the next; the recursion keeps every register-array index a
+// compile-time constant.
+template <int J, int G, typename T, int NR, int RPL>
+__device__ __forceinline__ void panel_col(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR], T* lb, int gl, int nb, int np,
+                                          int K, int& fail) {
+  constexpr int NB = G / 2;
+  if constexpr (J < NB) {
+    if (J < nb) {
+      const T dj = gshfl<G>(pr[0][J], J);
+      if (!(dj > T(0)) && fail < 0) fail = K + J;
       T d, dinv;
       pivot_of(dj > T(0) ? dj : T(1), d, dinv);
       T yj[NR];
 #pragma unroll
-      for (int c = 0; c < NR; ++c) yj[c] = __shfl_sync(0xffffffffu, rh[0][c], J) * dinv;
+      for (int c = 0; c < NR; ++c) yj[c] = gshfl<G>(rh[0][c], J) * dinv;
       T lq[RPL];
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
-        const int i = lane + 32 * q;
+        const int i = gl + G * q;
         const bool below = (i > J) && (i < np);
         const T l = below ? pr[q][J] * dinv : T(0);
         if (below) {
@@ -199,34 +235,20 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T
         }
         lq[q] = l;
       }
-      if (J + 1 < kNB) {
-        T* lbj = lb + (J & 1) * kNB;  // alternate buffers: one sync per step
-        if (lane < kNB) lbj[lane] = lq[0];
+      if (J + 1 < NB) {
+        T* lbj = lb + (J & 1) * NB;  // alternate buffers: one sync per step
+        if (gl < NB) lbj[gl] = lq[0];
         __syncwarp();
-        T Lv[kNB];
+        T Lv[NB];
+        ld_vec<NB>(lbj, Lv, J + 1);
 #pragma unroll
-        for (int v = 0; v < kNB / 4; ++v) {
-          if (4 * v + 3 > J) {
-            if constexpr (sizeof(T) == 4) {
-              const float4 f = reinterpret_cast<const float4*>(lbj)[v];
-              Lv[4 * v] = f.x; Lv[4 * v + 1] = f.y; Lv[4 * v + 2] = f.z; Lv[4 * v + 3] = f.w;
-            } else {
-              const double2 f0 = reinterpret_cast<const double2*>(lbj)[2 * v];
-              const double2 f1 = reinterpret_cast<const double2*>(lbj)[2 * v + 1];
-              Lv[4 * v] = f0.x; Lv[4 * v + 1] = f0.y; Lv[4 * v + 2] = f1.x; Lv[4 * v + 3] = f1.y;
-            }
-          } else {
-            Lv[4 * v] = Lv[4 * v + 1] = Lv[4 * v + 2] = Lv[4 * v + 3] = T(0);
-          }
-        }
-#pragma unroll
-        for (int p = J + 1; p < kNB; ++p) {
+        for (int p = J + 1; p < NB; ++p) {
 #pragma unroll
           for (int q = 0; q < RPL; ++q) pr[q][p] -= lq[q] * Lv[p];
         }
       }
     }
-    panel_col<J + 1, T, NR, RPL>(pr, rh, lb, lane, nb, np, K, fail);
+    panel_col<J + 1, G, T, NR, RPL>(pr, rh, lb, gl, nb, np, K, fail);
   }
 }
 
@@ -234,14 +256,15 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T
 // diagonal block is factorised from three shuffled entries, both columns of
 // multipliers are formed per row, and one broadcast of the two columns
 // feeds the rank-2 update of the remaining columns.
-template <int J, typename T, int NR, int RPL>
-__device__ __forceinline__ void panel_pair(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], T* lb, int lane, int K,
+template <int J, int G, typename T, int NR, int RPL>
+__device__ __forceinline__ void panel_pair(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR], T* lb, int gl, int K,
                                            int& fail) {
-  if constexpr (J + 1 < kNB) {
+  constexpr int NB = G / 2;
+  if constexpr (J + 1 < NB) {
     constexpr int J1 = J + 1;
-    const T a00 = __shfl_sync(0xffffffffu, pr[0][J], J);
-    const T a10 = __shfl_sync(0xffffffffu, pr[0][J], J1);
-    const T a11 = __shfl_sync(0xffffffffu, pr[0][J1], J1);
+    const T a00 = gshfl<G>(pr[0][J], J);
+    const T a10 = gshfl<G>(pr[0][J], J1);
+    const T a11 = gshfl<G>(pr[0][J1], J1);
     if (!(a00 > T(0)) && fail < 0) fail = K + J;
     T d0, i0;
     pivot_of(a00 > T(0) ? a00 : T(1), d0, i0);
@@ -253,14 +276,14 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], 
     T y0[NR], y1[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
-      y0[c] = __shfl_sync(0xffffffffu, rh[0][c], J) * i0;
-      y1[c] = (__shfl_sync(0xffffffffu, rh[0][c], J1) - l10 * y0[c]) * i1;
+      y0[c] = gshfl<G>(rh[0][c], J) * i0;
+      y1[c] = (gshfl<G>(rh[0][c], J1) - l10 * y0[c]) * i1;
     }
     T l0q[RPL], l1q[RPL];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       // rows at or above J hold no multiplier; rows past the panel are zero
-      const bool b0 = q > 0 || lane > J, b1 = q > 0 || lane > J1;
+      const bool b0 = q > 0 || gl > J, b1 = q > 0 || gl > J1;
       const T l0 = b0 ? pr[q][J] * i0 : T(0);
       const T l1 = b1 ? (pr[q][J1] - l0 * l10) * i1 : T(0);
 #pragma unroll
@@ -268,12 +291,12 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], 
       pr[q][J] = l0;
       pr[q][J1] = l1;
       if (q == 0) {
-        if (lane == J) {
+        if (gl == J) {
           pr[0][J] = i0;  // the factor blocks keep 1 / L_jj
 #pragma unroll
           for (int c = 0; c < NR; ++c) rh[0][c] = y0[c];
         }
-        if (lane == J1) {
+        if (gl == J1) {
           pr[0][J1] = i1;
 #pragma unroll
           for (int c = 0; c < NR; ++c) rh[0][c] = y1[c];
@@ -282,128 +305,112 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][kNB], T (&rh)[RPL][NR], 
       l0q[q] = l0;
       l1q[q] = l1;
     }
-    if (J1 + 1 < kNB) {
-      T* lbj = lb + ((J >> 1) & 1) * (2 * kNB);  // alternate buffers: one sync per step
-      if (lane < kNB) {
-        lbj[lane] = l0q[0];
-        lbj[kNB + lane] = l1q[0];
+    if (J1 + 1 < NB) {
+      T* lbj = lb + ((J >> 1) & 1) * (2 * NB);  // alternate buffers: one sync per step
+      if (gl < NB) {
+        lbj[gl] = l0q[0];
+        lbj[NB + gl] = l1q[0];
       }
       __syncwarp();
-      T L0[kNB], L1[kNB];
+      T L0[NB], L1[NB];
+      ld_vec<NB>(lbj, L0, J1 + 1);
+      ld_vec<NB>(lbj + NB, L1, J1 + 1);
 #pragma unroll
-      for (int v = 0; v < kNB / 4; ++v) {
-        if (4 * v + 3 > J1) {
-          if constexpr (sizeof(T) == 4) {
-            const float4 f = reinterpret_cast<const float4*>(lbj)[v];
-            const float4 g = reinterpret_cast<const float4*>(lbj + kNB)[v];
-            L0[4 * v] = f.x; L0[4 * v + 1] = f.y; L0[4 * v + 2] = f.z; L0[4 * v + 3] = f.w;
-            L1[4 * v] = g.x; L1[4 * v + 1] = g.y; L1[4 * v + 2] = g.z; L1[4 * v + 3] = g.w;
-          } else {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const double2 f = reinterpret_cast<const double2*>(lbj)[2 * v + h];
-              const double2 g = reinterpret_cast<const double2*>(lbj + kNB)[2 * v + h];
-              L0[4 * v + 2 * h] = f.x; L0[4 * v + 2 * h + 1] = f.y;
-              L1[4 * v + 2 * h] = g.x; L1[4 * v + 2 * h + 1] = g.y;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) L0[4 * v + k] = L1[4 * v + k] = T(0);
-        }
-      }
-#pragma unroll
-      for (int p = J1 + 1; p < kNB; ++p) {
+      for (int p = J1 + 1; p < NB; ++p) {
 #pragma unroll
         for (int q = 0; q < RPL; ++q) pr[q][p] -= l0q[q] * L0[p] + l1q[q] * L1[p];
       }
     }
-    panel_pair<J + 2, T, NR, RPL>(pr, rh, lb, lane, K, fail);
+    panel_pair<J + 2, G, T, NR, RPL>(pr, rh, lb, gl, K, fail);
   }
 }
 
 // Factorise (and forward-substitute NR rhs).  Lg: blocks of (NB+bmax) x NB;
 // yg[k*NR + c] receives the forward solution.  Returns -1 or the first
-// failing pivot index (warp-uniform).
-template <typename T, int NR, int RPL, class Gen, typename TS>
-__device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<T>& s,
-                          T* __restrict__ Lg, TS* __restrict__ yg, int lane) {
-  const int LBS = (kNB + bmax) * kNB;
-  const int msk = s.RW - 1;
-  const int blk16 = kNB * s.PW * (int)sizeof(T) / 16;  // 16-byte chunks of NB ring rows
-  blk_zero16(s.wnd, s.RW / kNB * blk16, lane);
+// failing pivot index (the factorisation runs to the end either way).
+template <int G, typename T, int NR, int RPL, class Gen, typename TS>
+__device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<T>& s, T* __restrict__ Lg,
+                          TS* __restrict__ yg, int gl) {
+  constexpr int NB = G / 2;
+  const int LBS = (NB + bmax) * NB;
+  const int RW = s.RW;
+  const int blk16 = NB * s.PW * (int)sizeof(T) / 16;  // 16-byte chunks of NB ring rows
+  blk_zero16<G>(s.wnd, RW / NB * blk16, gl);
   __syncwarp();
-  // first window: rows [0, min(n, NB + b)), generated directly
-  int filled = min(n, kNB + b);
-  for (int r0 = 0; r0 < filled; r0 += 32) {
+  int fail = -1;
+  // first window: rows [0, min(n, NB + b)) in slots 0.. (no wrap), generated directly
+  int filled = min(n, NB + b);
+  for (int r0 = 0; r0 < filled; r0 += G) {
     typename Gen::Raw raw;
-    if (r0 + lane < filled) gen.load(r0 + lane, raw);
-    blk_fill_raw<T, NR>(gen, s, r0, min(filled, r0 + 32), b, lane, raw);
-    __syncwarp();
+    if (r0 + gl < filled) gen.load(r0 + gl, raw);
+    blk_fill_raw<G, T, NR>(gen, s, r0, min(filled, r0 + G), r0, b, gl, raw);
   }
+  __syncwarp();
+  int fslot = ring(filled, RW);  // slot of row `filled` (filled <= RW)
   // rows of the next fill: their coefficient values are copied one block
   // ahead into shared memory by asynchronous copies
-  if (filled + lane < min(n, filled + kNB)) gen.prefetch(filled + lane, s.raw + 4 * lane);
+  if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + 4 * gl);
   cp_async_commit();
-  for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
-    const int nb = min(kNB, n - K);
+  int kslot = 0;  // slot of row K
+  for (int K = 0, kb = 0; K < n; K += NB, ++kb, kslot = ring(kslot + NB, RW)) {
+    const int nb = min(NB, n - K);
     const int np = min(nb + b, n - K);
-    const int need = min(n, K + kNB + b);
+    const int need = min(n, K + NB + b);
     if (filled < need) {
       cp_async_wait<0>();
       __syncwarp();
       typename Gen::Raw pf;
-      if (lane < kNB) gen.from_smem(s.raw + 4 * lane, pf);
-      blk_fill_raw<T, NR>(gen, s, filled, need, b, lane, pf);
+      if (gl < NB) gen.from_smem(s.raw + 4 * gl, pf);
+      blk_fill_raw<G, T, NR>(gen, s, filled, need, fslot, b, gl, pf);
+      fslot = ring(fslot + (need - filled), RW);
       filled = need;
       __syncwarp();
-      if (filled + lane < min(n, filled + kNB)) gen.prefetch(filled + lane, s.raw + 4 * lane);
+      if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + 4 * gl);
       cp_async_commit();
     }
     __syncwarp();
     // ---- 1. panel factorisation in registers
-    T pr[RPL][kNB];
+    T pr[RPL][NB];
     T rh[RPL][NR];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-      const int i = lane + 32 * q;
-      const T* row = s.wnd + ((K + i) & msk) * s.PW;
+      const int i = gl + G * q;
       const bool in = i < np;
+      const int slot = ring(kslot + (in ? i : 0), RW);
+      const T* row = s.wnd + slot * s.PW;
 #pragma unroll
-      for (int p = 0; p < kNB; ++p) {
+      for (int p = 0; p < NB; ++p) {
         const int d = i - p;
         pr[q][p] = (in && p < nb && d >= 0 && d <= b) ? row[d] : T(0);
       }
 #pragma unroll
-      for (int c = 0; c < NR; ++c) rh[q][c] = in ? s.rhs[((K + i) & msk) * 4 + c] : T(0);
+      for (int c = 0; c < NR; ++c) rh[q][c] = in ? s.rhs[slot * 4 + c] : T(0);
     }
-    int fail = -1;
-    if (nb == kNB)
-      panel_pair<0, T, NR, RPL>(pr, rh, s.lb, lane, K, fail);
+    if (nb == NB)
+      panel_pair<0, G, T, NR, RPL>(pr, rh, s.lb, gl, K, fail);
     else
-      panel_col<0, T, NR, RPL>(pr, rh, s.lb, lane, nb, np, K, fail);
-    if (fail >= 0) return fail;
+      panel_col<0, G, T, NR, RPL>(pr, rh, s.lb, gl, nb, np, K, fail);
     // ---- write the factor block, forward solution, trailing rhs and panel;
     // rows K..K+NB-1 are retired, and their ring slots (contiguous: RW is a
     // multiple of NB) hold no live row until the next fill
     T* Lb = Lg + (size_t)kb * LBS;
-    T* pt = s.wnd + (K & msk) * s.PW;
+    T* pt = s.wnd + kslot * s.PW;
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-      const int i = lane + 32 * q;
+      const int i = gl + G * q;
       if (i < np) {
-        T* dst = Lb + i * kNB;
+        T* dst = Lb + i * NB;
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
-          for (int v = 0; v < kNB / 4; ++v)
+          for (int v = 0; v < NB / 4; ++v)
             reinterpret_cast<float4*>(dst)[v] =
                 make_float4(4 * v <= i ? pr[q][4 * v] : 0.f, 4 * v + 1 <= i ? pr[q][4 * v + 1] : 0.f,
                             4 * v + 2 <= i ? pr[q][4 * v + 2] : 0.f,
                             4 * v + 3 <= i ? pr[q][4 * v + 3] : 0.f);
         } else {
 #pragma unroll
-          for (int v = 0; v < kNB / 2; ++v)
+          for (int v = 0; v < NB / 2; ++v)
             reinterpret_cast<double2*>(dst)[v] = make_double2(
                 2 * v <= i ? pr[q][2 * v] : 0.0, 2 * v + 1 <= i ? pr[q][2 * v + 1] : 0.0);
         }
@@ -411,11 +418,11 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
 #pragma unroll
           for (int c = 0; c < NR; ++c) yg[(size_t)(K + i) * NR + c] = (TS)rh[q][c];
         } else {
-          const int slot = (K + i) & msk;
+          const int slot = ring(kslot + i, RW);
 #pragma unroll
           for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[q][c];
 #pragma unroll
-          for (int p = 0; p < kNB; ++p) pt[p * s.RP + (i - nb)] = pr[q][p];
+          for (int p = 0; p < NB; ++p) pt[p * s.RP + (i - nb)] = pr[q][p];
         }
       }
     }
@@ -425,7 +432,8 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
     if (nt > 0) {
       const int T4 = (nt + 3) >> 2;
       const int ntiles = T4 * (T4 + 1) / 2;
-      for (int t = lane; t < ntiles; t += 32) {
+      const int tslot = ring(kslot + nb, RW);  // slot of row K + nb
+      for (int t = gl; t < ntiles; t += G) {
         int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
         if ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
         if (ti * (ti + 1) / 2 > t) --ti;
@@ -464,7 +472,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
         for (int a = 0; a < 4; ++a) {
           const int ia = 4 * ti + a;
           if (ia < nt) {
-            T* wr = s.wnd + ((K + nb + ia) & msk) * s.PW + ia - 4 * tj;
+            T* wr = s.wnd + ring(tslot + ia, RW) * s.PW + ia - 4 * tj;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
               if (4 * tj + c <= ia) wr[-c] -= acc[a][c];
@@ -475,10 +483,24 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
     __syncwarp();
     // the retired rows' slots (which held the trailing panel) are cleared for
     // the rows that will occupy them
-    blk_zero16(pt, blk16, lane);
+    blk_zero16<G>(pt, blk16, gl);
     __syncwarp();
   }
-  return -1;
+  return fail;
+}
+
+// Asynchronous copy of factor block kb into a staging buffer (one commit group).
+template <int G, typename T>
+__device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int n, int b, int bmax, T* dst, int gl) {
+  constexpr int NB = G / 2;
+  const int K = kb * NB;
+  const int nb = min(NB, n - K);
+  const int np = min(nb + b, n - K);
+  const T* src = Lg + (size_t)kb * (NB + bmax) * NB;
+  const int nv = np * NB * (int)sizeof(T) / 16;
+  for (int v = gl; v < nv; v += G)
+    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * v, reinterpret_cast<const unsigned char*>(src) + 16 * v);
+  cp_async_commit();
 }
 
 // The four values of a 16-byte-aligned ring row of a shared [RW][4] array.
@@ -491,35 +513,23 @@ __device__ __forceinline__ void ld_row4(const double* p, double (&x)[4]) {
   x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
 }
 
-// Asynchronous copy of factor block kb into a staging buffer (one commit group).
-template <typename T>
-__device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int n, int b, int bmax, T* dst,
-                                          int lane) {
-  const int K = kb * kNB;
-  const int nb = min(kNB, n - K);
-  const int np = min(nb + b, n - K);
-  const T* src = Lg + (size_t)kb * (kNB + bmax) * kNB;
-  const int nv = np * kNB * (int)sizeof(T) / 16;
-  for (int v = lane; v < nv; v += 32)
-    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * v, reinterpret_cast<const unsigned char*>(src) + 16 * v);
-  cp_async_commit();
-}
-
 // Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
-template <typename T, int NR, typename TS>
+template <int G, typename T, int NR, typename TS>
 __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
-                             TS* __restrict__ xg, int lane) {
-  const int nbk = (n + kNB - 1) / kNB;
-  const int msk = s.RW - 1;
-  const int stg = (kNB + bmax) * kNB;
+                             TS* __restrict__ xg, int gl) {
+  constexpr int NB = G / 2;
+  const int nbk = (n + NB - 1) / NB;
+  const int RW = s.RW;
+  const int stg = (NB + bmax) * NB;
   T* xr = s.rhs;  // ring of solution rows
-  blk_stage<T>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, lane);
-  for (int kb = nbk - 1; kb >= 0; --kb) {
-    const int K = kb * kNB;
-    const int nb = min(kNB, n - K);
+  blk_stage<G, T>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, gl);
+  int kslot = ((nbk - 1) * NB) % RW;  // slot of row K
+  for (int kb = nbk - 1; kb >= 0; --kb, kslot = kslot >= NB ? kslot - NB : kslot - NB + RW) {
+    const int K = kb * NB;
+    const int nb = min(NB, n - K);
     const int np = min(nb + b, n - K);
     if (kb > 0) {
-      blk_stage<T>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, lane);
+      blk_stage<G, T>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, gl);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -530,81 +540,82 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
     // latency overlaps them
     T yin[NR];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) yin[c] = lane < nb ? (T)xg[(size_t)(K + lane) * NR + c] : T(0);
-    // column p = lane & 15: yv = y_p - sum over the rows below the block of
-    // L[i][p] x_i, the rows split between the two half-warps
+    for (int c = 0; c < NR; ++c) yin[c] = gl < nb ? (T)xg[(size_t)(K + gl) * NR + c] : T(0);
+    // column p = gl mod NB: yv = y_p - sum over the rows below the block of
+    // L[i][p] x_i, the rows split between the two halves of the group
     T yv[NR];
     {
       T acc[NR];
 #pragma unroll
       for (int c = 0; c < NR; ++c) acc[c] = T(0);
-      const int p = lane & (kNB - 1);
+      const int p = gl & (NB - 1);
 #pragma unroll 4
-      for (int i = nb + (lane >> 4); i < np; i += 2) {
-        const T l = tb[i * kNB + p];
+      for (int i = nb + gl / NB; i < np; i += 2) {
+        const T l = tb[i * NB + p];
         T xi[4];
-        ld_row4(xr + ((K + i) & msk) * 4, xi);
+        ld_row4(xr + ring(kslot + i, RW) * 4, xi);
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[c] += l * xi[c];
       }
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
-        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
-        yv[c] = lane < nb ? yin[c] - acc[c] : T(0);
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], NB, G);
+        yv[c] = gl < nb ? yin[c] - acc[c] : T(0);
       }
     }
     // in-block triangular solve, column oriented: x_p = yv_p / L_pp, then
     // rows q < p subtract L[p][q] x_p; full blocks take the columns in pairs
     // (p, p-1), which shortens the dependent chain of shuffles
-    if (nb == kNB) {
+    if (nb == NB) {
 #pragma unroll
-      for (int p = kNB - 1; p >= 1; p -= 2) {
-        const T i1 = tb[p * kNB + p], i0 = tb[(p - 1) * kNB + p - 1], lpq = tb[p * kNB + p - 1];
+      for (int p = NB - 1; p >= 1; p -= 2) {
+        const T i1 = tb[p * NB + p], i0 = tb[(p - 1) * NB + p - 1], lpq = tb[p * NB + p - 1];
         T x1[NR], x0[NR];
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
-          x1[c] = __shfl_sync(0xffffffffu, yv[c], p) * i1;
-          x0[c] = (__shfl_sync(0xffffffffu, yv[c], p - 1) - lpq * x1[c]) * i0;
+          x1[c] = gshfl<G>(yv[c], p) * i1;
+          x0[c] = (gshfl<G>(yv[c], p - 1) - lpq * x1[c]) * i0;
         }
-        if (lane < p - 1) {
-          const T l1 = tb[p * kNB + lane], l0 = tb[(p - 1) * kNB + lane];
+        if (gl < p - 1) {
+          const T l1 = tb[p * NB + gl], l0 = tb[(p - 1) * NB + gl];
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] -= l1 * x1[c] + l0 * x0[c];
         }
-        if (lane == p) {
+        if (gl == p) {
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] = x1[c];
         }
-        if (lane == p - 1) {
+        if (gl == p - 1) {
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] = x0[c];
         }
       }
     } else {
 #pragma unroll
-      for (int p = kNB - 1; p >= 0; --p) {
+      for (int p = NB - 1; p >= 0; --p) {
         if (p < nb) {
-          const T iLpp = tb[p * kNB + p];
+          const T iLpp = tb[p * NB + p];
           T xp[NR];
 #pragma unroll
-          for (int c = 0; c < NR; ++c) xp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
-          if (lane < p) {
-            const T l = tb[p * kNB + lane];
+          for (int c = 0; c < NR; ++c) xp[c] = gshfl<G>(yv[c], p) * iLpp;
+          if (gl < p) {
+            const T l = tb[p * NB + gl];
 #pragma unroll
             for (int c = 0; c < NR; ++c) yv[c] -= l * xp[c];
           }
-          if (lane == p) {
+          if (gl == p) {
 #pragma unroll
             for (int c = 0; c < NR; ++c) yv[c] = xp[c];
           }
         }
       }
     }
-    if (lane < nb) {
+    if (gl < nb) {
+      const int slot = ring(kslot + gl, RW);
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
-        xr[((K + lane) & msk) * 4 + c] = yv[c];
-        xg[(size_t)(K + lane) * NR + c] = (TS)yv[c];
+        xr[slot * 4 + c] = yv[c];
+        xg[(size_t)(K + gl) * NR + c] = (TS)yv[c];
       }
     }
     __syncwarp();
@@ -613,26 +624,30 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 
 // Forward substitution with the stored factor: rg [n][NR] double holds the
 // right-hand side on entry and the forward solution y on exit.
-template <typename T, int NR, int RPL>
-__device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
-                                   const T* __restrict__ Lg, double* __restrict__ rg, int lane) {
-  const int msk = s.RW - 1;
-  const int stg = (kNB + bmax) * kNB;
-  const int nbk = (n + kNB - 1) / kNB;
+template <int G, typename T, int NR, int RPL>
+__device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
+                                   double* __restrict__ rg, int gl) {
+  constexpr int NB = G / 2;
+  const int RW = s.RW;
+  const int stg = (NB + bmax) * NB;
+  const int nbk = (n + NB - 1) / NB;
   T* rr = s.rhs;  // ring of pending right-hand-side rows
   int filled = 0;
-  blk_stage<T>(Lg, 0, n, b, bmax, s.tb, lane);
-  for (int K = 0, kb = 0; K < n; K += kNB, ++kb) {
-    const int nb = min(kNB, n - K);
+  blk_stage<G, T>(Lg, 0, n, b, bmax, s.tb, gl);
+  int kslot = 0;
+  for (int K = 0, kb = 0; K < n; K += NB, ++kb, kslot = ring(kslot + NB, RW)) {
+    const int nb = min(NB, n - K);
     const int np = min(nb + b, n - K);
-    const int need = min(n, K + kNB + b);
-    for (int r = filled + lane; r < need; r += 32) {
+    const int need = min(n, K + NB + b);
+    // rows [filled, need) lie within NB + b of row K: slot = kslot + (r - K)
+    for (int r = filled + gl; r < need; r += G) {
+      const int slot = ring(kslot + (r - K), RW);
 #pragma unroll
-      for (int c = 0; c < NR; ++c) rr[(r & msk) * 4 + c] = (T)rg[(size_t)r * NR + c];
+      for (int c = 0; c < NR; ++c) rr[slot * 4 + c] = (T)rg[(size_t)r * NR + c];
     }
     filled = max(filled, need);
     if (kb + 1 < nbk) {
-      blk_stage<T>(Lg, kb + 1, n, b, bmax, s.tb + ((kb + 1) & 1) * stg, lane);
+      blk_stage<G, T>(Lg, kb + 1, n, b, bmax, s.tb + ((kb + 1) & 1) * stg, gl);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -641,47 +656,47 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s,
     const T* tb = s.tb + (kb & 1) * stg;
     T yv[NR];
 #pragma unroll
-    for (int c = 0; c < NR; ++c) yv[c] = (lane < nb) ? rr[((K + lane) & msk) * 4 + c] : T(0);
+    for (int c = 0; c < NR; ++c) yv[c] = (gl < nb) ? rr[ring(kslot + gl, RW) * 4 + c] : T(0);
 #pragma unroll
-    for (int p = 0; p < kNB; ++p) {
+    for (int p = 0; p < NB; ++p) {
       if (p < nb) {
-        const T iLpp = tb[p * kNB + p];
+        const T iLpp = tb[p * NB + p];
         T yp[NR];
 #pragma unroll
-        for (int c = 0; c < NR; ++c) yp[c] = __shfl_sync(0xffffffffu, yv[c], p) * iLpp;
-        if (lane > p && lane < nb) {
-          const T l = tb[lane * kNB + p];
+        for (int c = 0; c < NR; ++c) yp[c] = gshfl<G>(yv[c], p) * iLpp;
+        if (gl > p && gl < nb) {
+          const T l = tb[gl * NB + p];
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] -= l * yp[c];
         }
-        if (lane == p) {
+        if (gl == p) {
 #pragma unroll
           for (int c = 0; c < NR; ++c) yv[c] = yp[c];
         }
       }
     }
     T* yb = s.lb;  // block solution broadcast
-    if (lane < nb) {
+    if (gl < nb) {
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
-        rg[(size_t)(K + lane) * NR + c] = (double)yv[c];
-        yb[lane * NR + c] = yv[c];
+        rg[(size_t)(K + gl) * NR + c] = (double)yv[c];
+        yb[gl * NR + c] = yv[c];
       }
     }
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-      const int i = lane + 32 * q;
+      const int i = gl + G * q;
       if (i >= nb && i < np) {
         T acc[NR];
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[c] = T(0);
         for (int p = 0; p < nb; ++p) {
-          const T l = tb[i * kNB + p];
+          const T l = tb[i * NB + p];
 #pragma unroll
           for (int c = 0; c < NR; ++c) acc[c] += l * yb[p * NR + c];
         }
-        const int slot = (K + i) & msk;
+        const int slot = ring(kslot + i, RW);
 #pragma unroll
         for (int c = 0; c < NR; ++c) rr[slot * 4 + c] -= acc[c];
       }

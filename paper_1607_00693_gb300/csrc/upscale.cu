@@ -271,18 +271,34 @@ struct UpscaleArgs {
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
 
+// Sum over the G lanes of a group (every lane of the group receives it).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
 // TK: factor/solve type; TA: type of the K_e/b_e accumulation and of the
-// recombination; RPL: panel rows per lane (ceil((16 + bmax) / 32)).
-template <typename TK, typename TA, int RPL>
-__global__ void __launch_bounds__(kUpscaleWarps * 32, sizeof(TK) == 4 ? 4 : 2)
+// recombination; RPL: panel rows per lane (ceil((G/2 + bmax) / G)); G: lanes
+// per unit.  G = 32: one unit per warp (any unit order, including a device
+// list).  G = 16: a warp takes one cell of two consecutive samples, whose
+// patches have the same shape, so its two halves run the same loop bounds
+// in lockstep (an odd last sample is mirrored by the idle half, which
+// writes nothing).
+template <typename TK, typename TA, int RPL, int G>
+__global__ void __launch_bounds__(kUpscaleWarps * 32, G == 16 ? 3 : (sizeof(TK) == 4 ? 4 : 2))
 upscale_kernel(UpscaleArgs A) {
+  constexpr int NB = G / 2;
+  constexpr int GPW = 32 / G;  // units per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
+  const int gl = lane % G, grp = lane / G;
   const int wib = threadIdx.x >> 5;
-  const BlkSmem<TK> sm = make_blk<TK>(smem + wib * blk_smem_bytes<TK>(A.bmax), A.bmax);
+  const BlkSmem<TK> sm = make_blk<TK>(smem + (wib * GPW + grp) * blk_smem_bytes<TK>(NB, A.bmax), NB, A.bmax);
   const long long gw = (long long)blockIdx.x * kUpscaleWarps + wib;
   const long long nw = (long long)gridDim.x * kUpscaleWarps;
-  unsigned char* slot = A.ws + (size_t)gw * A.slot_bytes;
+  unsigned char* slot = A.ws + (size_t)(gw * GPW + grp) * A.slot_bytes;
   // solutions are kept in FP64 except in the all-FP32 form
   using TS = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
   TK* Lg = reinterpret_cast<TK*>(slot);
@@ -291,9 +307,21 @@ upscale_kernel(UpscaleArgs A) {
   const int ncell = A.nc * A.nc;
   const int CN = (A.rho + 1) * (A.rho + 1);
 
-  const long long nwork = A.unit_list ? (long long)A.unit_count[0] : A.units;
+  const long long nwork = A.unit_list ? (long long)A.unit_count[0]
+                                      : (G == 32 ? A.units : (long long)((A.S + 1) / 2) * ncell);
   for (long long w = gw; w < nwork; w += nw) {
-    const long long u = A.unit_list ? (long long)A.unit_list[w] : w;
+    long long u;
+    bool dup = false;  // this half mirrors the other half's unit
+    if (G == 32) {
+      u = A.unit_list ? (long long)A.unit_list[w] : w;
+    } else {
+      int sp = 2 * (int)(w / ncell) + grp;
+      if (sp >= A.S) {
+        sp = A.S - 1;
+        dup = true;
+      }
+      u = (long long)sp * ncell + (int)(w % ncell);
+    }
     const int s = (int)(u / ncell);
     const int cell = (int)(u % ncell);
     const int cx = cell % A.nc, cy = cell / A.nc;
@@ -301,45 +329,41 @@ upscale_kernel(UpscaleArgs A) {
     double* Ke = A.Ke + (size_t)u * 10;
     double* be = A.be + (size_t)u * 4;
     if (o < 0 || o > A.max_o) {
-      if (lane < 10) Ke[lane] = qnan();
-      if (lane < 4) be[lane] = qnan();
-      if (lane == 0 && A.status) A.status[u] = -1;
+      if (!dup) {
+        if (gl < 10) Ke[gl] = qnan();
+        if (gl < 4) be[gl] = qnan();
+        if (gl == 0 && A.status) A.status[u] = -1;
+      }
       continue;
     }
     const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
     PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
     pg.finish();
+    // a failed factorisation still runs every step (the halves of a warp
+    // stay in lockstep); its unit gets NaN results and a status below
     int fail = -1;
     if (g.n > 0) {
-      fail = blk_factor<TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, lane);
-      if (fail < 0) {
-        blk_backward<TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, lane);
-        // FP64 iterative refinement with the factor: corr = residual, solve, add
-        for (int it = 0; it < A.refine; ++it) {
-          __syncwarp();
-          const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
-          for (int k = lane; k < g.n * 3; k += 32) corr[k] = rg.rhs<double>(k / 3, k % 3);
-          __syncwarp();
-          blk_forward_stored<TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, lane);
-          blk_backward<TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, lane);
-          __syncwarp();
-          for (int k = lane; k < g.n * 3; k += 32) psi0[k] += (TS)corr[k];
-        }
+      fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
+      blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
+      // FP64 iterative refinement with the factor: corr = residual, solve, add
+      for (int it = 0; it < A.refine; ++it) {
+        __syncwarp();
+        const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
+        for (int k = gl; k < g.n * 3; k += G) corr[k] = rg.rhs<double>(k / 3, k % 3);
+        __syncwarp();
+        blk_forward_stored<G, TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        __syncwarp();
+        for (int k = gl; k < g.n * 3; k += G) psi0[k] += (TS)corr[k];
       }
     }
     __syncwarp();
-    if (fail >= 0) {
-      if (lane < 10) Ke[lane] = qnan();
-      if (lane < 4) be[lane] = qnan();
-      if (lane == 0 && A.status) A.status[u] = fail + 1;
-      continue;
-    }
     // M_jk = a_cell(psi_j, psi_k) (j, k < 3) by the edge/diagonal difference
     // form of the Q1 element energy, 6 u^T K_ref v = sum_edges du dv +
     // 2 sum_diagonals du dv; m_j = sum over element corners of psi_j.
     TA M[6] = {0, 0, 0, 0, 0, 0};
     TA m[3] = {0, 0, 0};
-    for (int e = lane; e < A.rho * A.rho; e += 32) {
+    for (int e = gl; e < A.rho * A.rho; e += G) {
       const int ex = e % A.rho, ey = e / A.rho;
       const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
       TA c0[3], c1[3], c2[3], c3[3];
@@ -370,9 +394,9 @@ upscale_kernel(UpscaleArgs A) {
         }
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) M[q] = warp_sum(M[q]);
+    for (int q = 0; q < 6; ++q) M[q] = group_sum<G>(M[q]);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) m[l] = warp_sum(m[l]);
+    for (int l = 0; l < 3; ++l) m[l] = group_sum<G>(m[l]);
 
     // recombination D = C^{-1}, C_jk = psi_j(cell corner k); identity when
     // the patch is the cell (its corners carry the bilinear data exactly)
@@ -396,7 +420,12 @@ upscale_kernel(UpscaleArgs A) {
       }
       ok = inv4<TA>(C, D);
     }
-    if (lane == 0) {
+    if (gl == 0 && !dup && fail >= 0) {
+      for (int q = 0; q < 10; ++q) Ke[q] = qnan();
+      for (int q = 0; q < 4; ++q) be[q] = qnan();
+      if (A.status) A.status[u] = fail + 1;
+    }
+    if (gl == 0 && !dup && fail < 0) {
       const double h = 1.0 / A.nf;
       double MM[4][4];
       MM[0][0] = M[0]; MM[0][1] = MM[1][0] = M[1]; MM[0][2] = MM[2][0] = M[2];
@@ -430,9 +459,9 @@ upscale_kernel(UpscaleArgs A) {
       }
       if (A.status) A.status[u] = ok ? 0 : STOMSFEM_ENOTSPD;
     }
-    if (A.phi) {
+    if (A.phi && !dup && fail < 0) {
       double* ph = A.phi + (size_t)u * 4 * CN;
-      for (int q = lane; q < CN; q += 32) {
+      for (int q = gl; q < CN; q += G) {
         const int i = g.cx0 + q % (A.rho + 1), j = g.cy0 + q / (A.rho + 1);
         double v[3];
         psi_at<double, TS>(g, psi0, i, j, v);
@@ -472,10 +501,10 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
   *bmax = m + 1;
 }
 
-template <typename TK, typename TA, int RPL>
+template <typename TK, typename TA, int RPL, int G>
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  auto kern = upscale_kernel<TK, TA, RPL>;
-  const size_t smem = blk_smem_bytes<TK>(A.bmax) * kUpscaleWarps;
+  auto kern = upscale_kernel<TK, TA, RPL, G>;
+  const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * kUpscaleWarps * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUpscaleWarps * 32, smem));
@@ -488,13 +517,22 @@ static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream
   return STOMSFEM_OK;
 }
 
-template <typename TK, typename TA>
+template <typename TK, typename TA, int G>
 static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  const int rpl = (kNB + A.bmax + 31) / 32;
-  if (rpl <= 1) return launch_upscale<TK, TA, 1>(A, max_blocks, st);
-  if (rpl == 2) return launch_upscale<TK, TA, 2>(A, max_blocks, st);
-  return launch_upscale<TK, TA, 3>(A, max_blocks, st);
+  const int rpl = (G / 2 + A.bmax + G - 1) / G;  // <= 3 (G = 32) or 5 (G = 16) for bmax <= 64
+  if (rpl <= 1) return launch_upscale<TK, TA, 1, G>(A, max_blocks, st);
+  if (rpl == 2) return launch_upscale<TK, TA, 2, G>(A, max_blocks, st);
+  if (rpl == 3) return launch_upscale<TK, TA, 3, G>(A, max_blocks, st);
+  if constexpr (G == 16) {
+    if (rpl == 4) return launch_upscale<TK, TA, 4, G>(A, max_blocks, st);
+    return launch_upscale<TK, TA, 5, G>(A, max_blocks, st);
+  }
+  return set_error(STOMSFEM_EINVAL, "bandwidth %d too large", A.bmax);
 }
+
+// Lanes per unit of each form: the FP32 factorisations run two units per
+// warp; FP64 (whose panel registers fill the register file) one per warp.
+constexpr int group_lanes(int precision) { return precision == STOMSFEM_FP64 ? 32 : 16; }
 
 }  // namespace stomsfem
 
@@ -544,11 +582,14 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   slot_layout(nmax, bmax, precision, &sb, &lb);
   const long long units = (long long)S * grid->nc * grid->nc;
   const long long slots = (long long)(workspace_bytes / sb);
-  if (slots < kUpscaleWarps)
+  const int G = group_lanes(precision);
+  const int slots_per_block = kUpscaleWarps * (32 / G);
+  if (slots < slots_per_block)
     return set_error(STOMSFEM_ENOMEM, "workspace %zu bytes < %d slots of %zu bytes", workspace_bytes,
-                     kUpscaleWarps, sb);
-  long long max_blocks = slots / kUpscaleWarps;
-  const long long need = (units + kUpscaleWarps - 1) / kUpscaleWarps;
+                     slots_per_block, sb);
+  long long max_blocks = slots / slots_per_block;
+  const long long items = G == 32 ? units : (long long)((S + 1) / 2) * grid->nc * grid->nc;
+  const long long need = (items + kUpscaleWarps - 1) / kUpscaleWarps;
   if (max_blocks > need) max_blocks = need;
 
   UpscaleArgs A;
@@ -574,9 +615,10 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   A.unit_list = nullptr;
   A.unit_count = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == STOMSFEM_FP64) return launch_rpl<double, double>(A, max_blocks, st);
-  if (precision == STOMSFEM_FP32_REFINED) return launch_rpl<float, double>(A, max_blocks, st);
-  return launch_rpl<float, float>(A, max_blocks, st);
+  if (precision == STOMSFEM_FP64) return launch_rpl<double, double, group_lanes(STOMSFEM_FP64)>(A, max_blocks, st);
+  if (precision == STOMSFEM_FP32_REFINED)
+    return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED)>(A, max_blocks, st);
+  return launch_rpl<float, float, group_lanes(STOMSFEM_FP32)>(A, max_blocks, st);
 }
 
 namespace stomsfem {
@@ -618,7 +660,7 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   A.units = (long long)S * grid->nc * grid->nc;
   A.unit_list = unit_list;
   A.unit_count = unit_count;
-  return launch_rpl<double, double>(A, slots / kUpscaleWarps, st);
+  return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
 }
 
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {

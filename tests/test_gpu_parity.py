@@ -222,6 +222,29 @@ def test_status_on_indefinite_unit(orc):
     assert np.all(np.isfinite(Kg[0][good]))
 
 
+@pytest.mark.parametrize("precision", [api.FP32, api.FP32_REFINED])
+def test_paired_units_one_indefinite(orc, precision):
+    """The FP32 forms factorise one cell of two consecutive samples per warp
+    in lockstep.  Sample 1 has an indefinite cell: that unit alone reports
+    its pivot and NaN outputs; its warp partner (sample 0, same cell), the
+    other cells of sample 1 and the unpaired last sample (S odd) match the
+    oracle."""
+    nf, nc = 64, 2
+    r = np.random.default_rng(5)
+    a = np.exp(r.uniform(-1, 1, size=(3, nf, nf)))
+    a[1, 40:50, 40:50] = -5.0   # inside cell (1, 1) of sample 1
+    ov = np.array([0, 1, 2, 3], dtype=np.int8)
+    Kg, bg, st = gpu_upscale(nf, nc, 1.0, a, ov, precision=precision, status=True)
+    assert st[1, 3] > 0 and np.all(np.isnan(Kg[1, 3])) and np.all(np.isnan(bg[1, 3]))
+    ok = np.ones((3, nc * nc), dtype=bool)
+    ok[1, 3] = False
+    assert np.all(st[ok] == 0)
+    Ko, bo = orc.upscale(nf, nc, 1.0, np.abs(a), ov)
+    num = np.linalg.norm(Kg - Ko, axis=-1)[ok]
+    assert np.max(num / np.linalg.norm(Ko, axis=-1)[ok]) <= TOL[precision]
+    assert np.max(np.linalg.norm(bg - bo, axis=-1)[ok] / np.linalg.norm(bo, axis=-1)[ok]) <= TOL[precision]
+
+
 def _assemble_residual(Ke, be, u, nc):
     """|| S u - b || / ||b|| for the coarse system assembled from K_e, b_e
     (written out here independently of both the library and the oracle)."""
