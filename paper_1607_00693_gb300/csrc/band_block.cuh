@@ -62,10 +62,13 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15)
 __host__ __device__ inline int blk_ring_rows(int NB, int bmax) { return (NB + bmax + NB - 1) / NB * NB; }
 
 // Row pitch: b + 1 band entries, and at least RP = bmax rounded up to 4 so
-// that NB rows hold the transposed trailing panel.
+// that NB rows hold the transposed trailing panel; even, so that the panel
+// load (lane i reads row i at column i - p, a stride of PW + 1 elements)
+// meets distinct banks.
 __host__ __device__ inline int blk_pitch(int bmax) {
   const int rp = (bmax + 3) & ~3;
-  return bmax + 1 > rp ? bmax + 1 : rp;
+  const int pw = bmax + 1 > rp ? bmax + 1 : rp;
+  return pw + (pw & 1);
 }
 
 __host__ __device__ inline int blk_wnd_elems(int NB, int bmax) {
@@ -73,11 +76,16 @@ __host__ __device__ inline int blk_wnd_elems(int NB, int bmax) {
   return a > b ? a : b;
 }
 
+// Shared memory of one system, padded to 64 bytes past a multiple of 128
+// (at most 112 bytes of padding): the two systems of a warp then sit 16
+// banks apart, so that the same access pattern in both halves meets
+// different banks.
 template <typename T>
 __host__ __device__ inline size_t blk_smem_bytes(int NB, int bmax) {
   const int RW = blk_ring_rows(NB, bmax);
-  return al16(sizeof(T) * blk_wnd_elems(NB, bmax)) + al16(sizeof(T) * RW * 4) + al16(sizeof(T) * 4 * NB) +
-         al16(sizeof(double) * NB * 4);
+  const size_t b = al16(sizeof(T) * blk_wnd_elems(NB, bmax)) + al16(sizeof(T) * RW * 4) +
+                   al16(sizeof(T) * 4 * NB) + al16(sizeof(double) * NB * 4);
+  return b + ((64 - (b & 127)) & 127);
 }
 
 template <typename T>
@@ -139,6 +147,29 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// The four values of a 16-byte-aligned ring row of a shared [RW][4] array.
+__device__ __forceinline__ void ld_row4(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void ld_row4(const double* p, double (&x)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+  x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
+}
+// Store NR <= 4 values as one 16-byte-aligned ring row (padding with zeros).
+template <int NR, typename T>
+__device__ __forceinline__ void st_row4(T* p, const T (&x)[NR]) {
+  T v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = c < NR ? x[c] : T(0);
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
 // Zero n16 consecutive 16-byte chunks of shared memory (lanes gl of G).
 template <int G>
 __device__ __forceinline__ void blk_zero16(void* dst, int n16, int gl) {
@@ -175,8 +206,7 @@ __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s
       if (r >= mx && mx <= b) row[mx] += e[3];
       if (r >= mx + 1 && mx + 1 <= b) row[mx + 1] += e[4];
     }
-#pragma unroll
-    for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[c];
+    st_row4<NR>(s.rhs + slot * 4, rh);
   }
 }
 
@@ -383,8 +413,10 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
         const int d = i - p;
         pr[q][p] = (in && p < nb && d >= 0 && d <= b) ? row[d] : T(0);
       }
+      T x4[4];
+      ld_row4(s.rhs + slot * 4, x4);
 #pragma unroll
-      for (int c = 0; c < NR; ++c) rh[q][c] = in ? s.rhs[slot * 4 + c] : T(0);
+      for (int c = 0; c < NR; ++c) rh[q][c] = in ? x4[c] : T(0);
     }
     if (nb == NB)
       panel_pair<0, G, T, NR, RPL>(pr, rh, s.lb, gl, K, fail);
@@ -418,9 +450,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
 #pragma unroll
           for (int c = 0; c < NR; ++c) yg[(size_t)(K + i) * NR + c] = (TS)rh[q][c];
         } else {
-          const int slot = ring(kslot + i, RW);
-#pragma unroll
-          for (int c = 0; c < NR; ++c) s.rhs[slot * 4 + c] = rh[q][c];
+          st_row4<NR>(s.rhs + ring(kslot + i, RW) * 4, rh[q]);
 #pragma unroll
           for (int p = 0; p < NB; ++p) pt[p * s.RP + (i - nb)] = pr[q][p];
         }
@@ -501,16 +531,6 @@ __device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int 
   for (int v = gl; v < nv; v += G)
     cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * v, reinterpret_cast<const unsigned char*>(src) + 16 * v);
   cp_async_commit();
-}
-
-// The four values of a 16-byte-aligned ring row of a shared [RW][4] array.
-__device__ __forceinline__ void ld_row4(const float* p, float (&x)[4]) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-}
-__device__ __forceinline__ void ld_row4(const double* p, double (&x)[4]) {
-  const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
-  x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
 }
 
 // Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
@@ -611,12 +631,9 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
       }
     }
     if (gl < nb) {
-      const int slot = ring(kslot + gl, RW);
+      st_row4<NR>(xr + ring(kslot + gl, RW) * 4, yv);
 #pragma unroll
-      for (int c = 0; c < NR; ++c) {
-        xr[slot * 4 + c] = yv[c];
-        xg[(size_t)(K + gl) * NR + c] = (TS)yv[c];
-      }
+      for (int c = 0; c < NR; ++c) xg[(size_t)(K + gl) * NR + c] = (TS)yv[c];
     }
     __syncwarp();
   }
@@ -641,9 +658,10 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, 
     const int need = min(n, K + NB + b);
     // rows [filled, need) lie within NB + b of row K: slot = kslot + (r - K)
     for (int r = filled + gl; r < need; r += G) {
-      const int slot = ring(kslot + (r - K), RW);
+      T v[NR];
 #pragma unroll
-      for (int c = 0; c < NR; ++c) rr[slot * 4 + c] = (T)rg[(size_t)r * NR + c];
+      for (int c = 0; c < NR; ++c) v[c] = (T)rg[(size_t)r * NR + c];
+      st_row4<NR>(rr + ring(kslot + (r - K), RW) * 4, v);
     }
     filled = max(filled, need);
     if (kb + 1 < nbk) {
@@ -655,8 +673,12 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, 
     __syncwarp();
     const T* tb = s.tb + (kb & 1) * stg;
     T yv[NR];
+    {
+      T x4[4];
+      ld_row4(rr + ring(kslot + (gl < nb ? gl : 0), RW) * 4, x4);
 #pragma unroll
-    for (int c = 0; c < NR; ++c) yv[c] = (gl < nb) ? rr[ring(kslot + gl, RW) * 4 + c] : T(0);
+      for (int c = 0; c < NR; ++c) yv[c] = (gl < nb) ? x4[c] : T(0);
+    }
 #pragma unroll
     for (int p = 0; p < NB; ++p) {
       if (p < nb) {
@@ -696,9 +718,12 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, 
 #pragma unroll
           for (int c = 0; c < NR; ++c) acc[c] += l * yb[p * NR + c];
         }
-        const int slot = ring(kslot + i, RW);
+        T* row = rr + ring(kslot + i, RW) * 4;
+        T x4[4];
+        ld_row4(row, x4);
 #pragma unroll
-        for (int c = 0; c < NR; ++c) rr[slot * 4 + c] -= acc[c];
+        for (int c = 0; c < NR; ++c) acc[c] = x4[c] - acc[c];
+        st_row4<NR>(row, acc);
       }
     }
     __syncwarp();
