@@ -33,6 +33,12 @@ if ROOT not in sys.path:
 from paper_1607_00693_gb300 import workloads as W  # noqa: E402
 
 FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
+
+# Measured DRAM traffic per unit of the upscale kernel (ncu, 32 samples of
+# the H/h = 32 workload), by library version and form.
+DRAM_BYTES_PER_UNIT = {
+    ("stomsfem-gb300 0.2 (sm_103a)", "fp32"): (8.215309e9 + 7.869114e9) / 32768,
+}
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
 
@@ -530,6 +536,14 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, ov, args.cpu_samples)
 
+    # DRAM bytes of one upscale launch: ncu's dram__bytes_read.sum +
+    # dram__bytes_write.sum per unit on a 32-sample launch of the same kernel
+    # (same library version), times the units of this launch; None when the
+    # library differs from the one the counters were taken on
+    per_unit = DRAM_BYTES_PER_UNIT.get((api.stomsfem_version(), form))
+    traffic = per_unit * units_step if per_unit else None
+    traffic_note = ("ncu counters of a 32-sample launch scaled by units (%.0f B/unit)" % per_unit
+                    if per_unit else "no counters for this library version and form")
     if rank == 0:
         line = {
             "metric": "coarse elements upscaled/s at H/h=32",
@@ -546,7 +560,8 @@ def main():
                       "fp32r_units_per_s": value32r, "fp32r_speedup_vs_fp64": value32r / value64,
                       "fp32r_coarse_rel_l2_vs_fp64": err32r},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_note": traffic_note,
                          "kernel": "upscale_kernel (%s)" % form,
                          "peak_note": "derived: 152 SMs x %s x 2070 MHz" % (
                              "2 FP64 FMA/clk" if form == "fp64" else "128 FP32 lanes x 2 flops")},
