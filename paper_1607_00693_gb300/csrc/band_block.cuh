@@ -114,16 +114,23 @@ __host__ __device__ inline size_t blk_factor_elems(int n, int bmax) {
 // x mod RW for 0 <= x < 2 RW.
 __device__ __forceinline__ int ring(int x, int RW) { return x >= RW ? x - RW : x; }
 
-// The pivot and its reciprocal.  FP32: the hardware reciprocal square root
-// (relative error a few ulp), which perturbs the factor at the level of FP32
-// rounding; FP64: correctly rounded.
-__device__ __forceinline__ void pivot_of(float a, float& d, float& dinv) {
-  dinv = rsqrtf(a);
-  d = a * dinv;
-}
-__device__ __forceinline__ void pivot_of(double a, double& d, double& dinv) {
-  d = sqrt(a);
-  dinv = 1.0 / d;
+// Reciprocal of the pivot, 1 / sqrt(a) (the factor keeps only this).
+// FP32: the hardware reciprocal square root (a few ulp).  FP64: the FP32
+// estimate refined by two Newton steps y <- y + y (1 - a y^2) / 2, whose
+// relative error squares each step (2^-23 -> 2^-45 -> below 2^-53 before the
+// final roundings): about ten FP64 operations instead of a correctly rounded
+// square root and division, on a part whose FP64 pipe is narrow.  Outside
+// the FP32 range the library routines are used.
+__device__ __forceinline__ float pivot_rsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double pivot_rsqrt(double a) {
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
+  double y = (double)rsqrtf((float)a);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-a * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
 }
 
 template <int G, typename T>
@@ -242,8 +249,7 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR],
     if (J < nb) {
       const T dj = gshfl<G>(pr[0][J], J);
       if (!(dj > T(0)) && fail < 0) fail = K + J;
-      T d, dinv;
-      pivot_of(dj > T(0) ? dj : T(1), d, dinv);
+      const T dinv = pivot_rsqrt(dj > T(0) ? dj : T(1));
       T yj[NR];
 #pragma unroll
       for (int c = 0; c < NR; ++c) yj[c] = gshfl<G>(rh[0][c], J) * dinv;
@@ -296,13 +302,11 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR]
     const T a10 = gshfl<G>(pr[0][J], J1);
     const T a11 = gshfl<G>(pr[0][J1], J1);
     if (!(a00 > T(0)) && fail < 0) fail = K + J;
-    T d0, i0;
-    pivot_of(a00 > T(0) ? a00 : T(1), d0, i0);
+    const T i0 = pivot_rsqrt(a00 > T(0) ? a00 : T(1));
     const T l10 = a10 * i0;
     const T s11 = a11 - l10 * l10;
     if (!(s11 > T(0)) && fail < 0) fail = K + J1;
-    T d1, i1;
-    pivot_of(s11 > T(0) ? s11 : T(1), d1, i1);
+    const T i1 = pivot_rsqrt(s11 > T(0) ? s11 : T(1));
     T y0[NR], y1[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) {

@@ -20,7 +20,10 @@
 
 namespace stomsfem {
 
-constexpr int kUpscaleWarps = 4;   // warps (units in flight) per block
+// Warps per block: 4, except 2 for two FP64 units per warp (whose 36 KB of
+// shared memory per warp then fit three blocks on an SM).
+__host__ __device__ constexpr int upscale_warps(bool fp64, int G) { return fp64 && G == 16 ? 2 : 4; }
+constexpr int kUpscaleWarps = 4;  // list mode (one FP64 unit per warp)
 constexpr int kMaxBand = 64;       // half bandwidth limit (mx + 1)
 
 struct UnitGeom {
@@ -287,7 +290,8 @@ __device__ __forceinline__ T group_sum(T v) {
 // in lockstep (an odd last sample is mirrored by the idle half, which
 // writes nothing).
 template <typename TK, typename TA, int RPL, int G>
-__global__ void __launch_bounds__(kUpscaleWarps * 32, G == 16 ? 3 : (sizeof(TK) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(upscale_warps(sizeof(TK) == 8, G) * 32,
+                                  sizeof(TK) == 4 ? (G == 16 ? 3 : 4) : (G == 16 ? 3 : 2))
 upscale_kernel(UpscaleArgs A) {
   constexpr int NB = G / 2;
   constexpr int GPW = 32 / G;  // units per warp
@@ -296,8 +300,9 @@ upscale_kernel(UpscaleArgs A) {
   const int gl = lane % G, grp = lane / G;
   const int wib = threadIdx.x >> 5;
   const BlkSmem<TK> sm = make_blk<TK>(smem + (wib * GPW + grp) * blk_smem_bytes<TK>(NB, A.bmax), NB, A.bmax);
-  const long long gw = (long long)blockIdx.x * kUpscaleWarps + wib;
-  const long long nw = (long long)gridDim.x * kUpscaleWarps;
+  constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
+  const long long gw = (long long)blockIdx.x * WPB + wib;
+  const long long nw = (long long)gridDim.x * WPB;
   unsigned char* slot = A.ws + (size_t)(gw * GPW + grp) * A.slot_bytes;
   // solutions are kept in FP64 except in the all-FP32 form
   using TS = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
@@ -504,15 +509,16 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
 template <typename TK, typename TA, int RPL, int G>
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
   auto kern = upscale_kernel<TK, TA, RPL, G>;
-  const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * kUpscaleWarps * (32 / G);
+  constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
+  const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * WPB * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUpscaleWarps * 32, smem));
+  STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
   if (per_sm < 1) return set_error(STOMSFEM_EINVAL, "upscale kernel does not fit on an SM (smem %zu)", smem);
   long long blocks = (long long)per_sm * device_sm_count();
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, kUpscaleWarps * 32, smem, st>>>(A);
+  kern<<<(unsigned)blocks, WPB * 32, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }
@@ -530,9 +536,8 @@ static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t s
   return set_error(STOMSFEM_EINVAL, "bandwidth %d too large", A.bmax);
 }
 
-// Lanes per unit of each form: the FP32 factorisations run two units per
-// warp; FP64 (whose panel registers fill the register file) one per warp.
-constexpr int group_lanes(int precision) { return precision == STOMSFEM_FP64 ? 32 : 16; }
+// Lanes per unit of each form: two units per warp.
+constexpr int group_lanes(int) { return 16; }
 
 }  // namespace stomsfem
 
@@ -583,13 +588,14 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   const long long units = (long long)S * grid->nc * grid->nc;
   const long long slots = (long long)(workspace_bytes / sb);
   const int G = group_lanes(precision);
-  const int slots_per_block = kUpscaleWarps * (32 / G);
+  const int WPB = upscale_warps(precision == STOMSFEM_FP64, G);
+  const int slots_per_block = WPB * (32 / G);
   if (slots < slots_per_block)
     return set_error(STOMSFEM_ENOMEM, "workspace %zu bytes < %d slots of %zu bytes", workspace_bytes,
                      slots_per_block, sb);
   long long max_blocks = slots / slots_per_block;
   const long long items = G == 32 ? units : (long long)((S + 1) / 2) * grid->nc * grid->nc;
-  const long long need = (items + kUpscaleWarps - 1) / kUpscaleWarps;
+  const long long need = (items + WPB - 1) / WPB;
   if (max_blocks > need) max_blocks = need;
 
   UpscaleArgs A;
