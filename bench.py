@@ -37,7 +37,8 @@ FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
 # Measured DRAM traffic per unit of the upscale kernel (ncu, 32 samples of
 # the H/h = 32 workload), by library version and form.
 DRAM_BYTES_PER_UNIT = {
-    ("stomsfem-gb300 0.2 (sm_103a)", "fp32"): (8.215309e9 + 7.869114e9) / 32768,
+    ("stomsfem-gb300 0.3 (sm_103a)", "fp32"): (8.215265e9 + 7.868577e9) / 32768,
+    ("stomsfem-gb300 0.3 (sm_103a)", "fp64"): (1.829177e9 + 1.938842e9) / 4096,
 }
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
