@@ -18,6 +18,9 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
                       const int32_t* unit_count, double* Ke, double* be, void* workspace,
                       size_t workspace_bytes, cudaStream_t st);
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
+// Scratch slots (units in flight) of one block of the upscaling launch for a
+// precision: the least workspace stomsfem_upscale accepts, in slots.
+int upscale_slots_per_block(int precision);
 
 #define STOMSFEM_TRY_CUDA(expr)                                  \
   do {                                                           \

@@ -18,8 +18,8 @@
 
 namespace stomsfem {
 
-// 64 MiB: 157 warp slots for H/h = 32 with oversampling up to 4 in FP32
-// (4 slots are the minimum a launch needs).
+// 64 MiB: about 150 unit slots for H/h = 32 with oversampling up to 4 in
+// FP32 (one block of the launch, 8 slots in FP32, is the minimum it needs).
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;
 constexpr int kMaxDevices = 64;
 
@@ -63,12 +63,13 @@ extern "C" int stomsfem_upscale_noalloc(const stomsfem_grid* grid, const double*
   int rc = stomsfem_upscale_workspace_size(grid, oversample ? max_oversample : 0, precision, &slot,
                                            nullptr);
   if (rc != STOMSFEM_OK) return rc;
-  // the upscaling launch needs at least one block of 4 warp slots
-  if (slot * 4 > kStaticScratchBytes)
+  // the upscaling launch needs at least the slots of one block
+  const int need = upscale_slots_per_block(precision);
+  if (slot * need > kStaticScratchBytes)
     return set_error(STOMSFEM_EINVAL,
-                     "patch too large for the static scratch: 4 slots of %zu bytes exceed %zu bytes "
+                     "patch too large for the static scratch: %d slots of %zu bytes exceed %zu bytes "
                      "(reduce rho + 2*max_oversample or use stomsfem_upscale with a workspace)",
-                     slot, kStaticScratchBytes);
+                     need, slot, kStaticScratchBytes);
   void* ws = nullptr;
   rc = scratch_address(&ws);
   if (rc != STOMSFEM_OK) return rc;

@@ -669,6 +669,11 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
 }
 
+int upscale_slots_per_block(int precision) {
+  const int G = group_lanes(precision);
+  return upscale_warps(precision == STOMSFEM_FP64, G) * (32 / G);
+}
+
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
   int nmax, bmax;
   patch_limits(grid, 0, &nmax, &bmax);
