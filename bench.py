@@ -567,7 +567,9 @@ def main():
                          "peak_note": "derived: 152 SMs x %s x 2070 MHz" % (
                              "2 FP64 FMA/clk" if form == "fp64" else "128 FP32 lanes x 2 flops")},
             "e2e": e2e,
-            "gpu_launches": 5 * args.steps + launches_extra,
+            # per step: sampling, upscaling (FP32 form with oversampling: a
+            # cell-list kernel and two upscale launches), coarse solve, moments, count
+            "gpu_launches": (7 if form == "fp32" and ov is not None else 5) * args.steps + launches_extra,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

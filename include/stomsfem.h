@@ -94,9 +94,11 @@ int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stre
 int stomsfem_sample_coef(const stomsfem_grid* grid, const stomsfem_field* field,
                          const double* xi, int32_t S, double* a, stomsfem_stream_t stream);
 
-/* Scratch needed by stomsfem_upscale for one resident warp ("slot") and the
- * recommended total (one slot per resident warp of the whole GPU).  Each
- * slot holds one unit's banded Cholesky factor and solution vectors. */
+/* Scratch needed by stomsfem_upscale for one unit in flight ("slot") and
+ * the recommended total (a slot per unit the whole GPU keeps in flight, plus
+ * 8 (nc^2 + 1) bytes, rounded up to 256, for the cell lists of the FP32
+ * form).  Each slot holds one unit's banded Cholesky factor and solution
+ * vectors. */
 int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_oversample,
                                     int32_t precision, size_t* slot_bytes,
                                     size_t* recommended_bytes);
@@ -107,7 +109,12 @@ int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_overs
  * elements on each side and clipped to the domain, Remark on oversampling),
  * recombine the patch solutions into the basis that is nodal at the cell
  * corners, and form the upscaled stiffness and load of Eq. stiffness_local
- * on the cell.
+ * on the cell.  In the FP32 form without phi output, cells without
+ * oversampling use K_e(l,m) = p_l^T A p_m - y_l . y_m with y the forward
+ * solutions (the Galerkin identity of the cell problem; no back
+ * substitution); with an oversample array and room at the end of the
+ * workspace for the cell lists, those cells and the others run as two
+ * launches.
  *   a            device [S][nf][nf] float64 coefficient
  *   oversample   device [nc*nc] int8 layer widths, or NULL for none; every
  *                entry must lie in [0, max_oversample] (units with an
@@ -127,10 +134,11 @@ int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_overs
  *                STOMSFEM_ENOTSPD when the corner matrix of the
  *                oversampling recombination is singular.  Failed units
  *                get NaN outputs.
- *   workspace    device scratch of workspace_bytes (>= one slot per warp
- *                launched; more slots = more units in flight)
+ *   workspace    device scratch of workspace_bytes (>= the slots of one
+ *                block: 8 in the FP32 forms, 4 in FP64; more slots = more
+ *                units in flight)
  * Errors: EINVAL (sizes, pointers, precision, bandwidth > 64), ENOMEM
- * (workspace below 4 slots), ECUDA. */
+ * (workspace below one block of slots), ECUDA. */
 int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
                      int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
                      double* Ke, double* be, double* phi, int32_t* unit_status, void* workspace,

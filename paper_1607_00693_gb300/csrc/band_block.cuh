@@ -196,7 +196,7 @@ __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s
   const int r = r0 + gl;
   if (r < r1) {
     T e[5], rh[NR];
-    gen.template make<T>(r, raw, e, rh);
+    gen.template make<T, NR>(r, raw, e, rh);
     const int slot = ring(slot0 + gl, s.RW);
     T* row = s.wnd + slot * s.PW;
     if (mx >= 3 && mx + 1 <= b) {
@@ -362,9 +362,13 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR]
 // Factorise (and forward-substitute NR rhs).  Lg: blocks of (NB+bmax) x NB;
 // yg[k*NR + c] receives the forward solution.  Returns -1 or the first
 // failing pivot index (the factorisation runs to the end either way).
-template <int G, typename T, int NR, int RPL, class Gen, typename TS>
+// FWD_ONLY (NR = 4): neither the factor nor y is stored; each lane adds,
+// over the rows it finishes, y0 y0, y0 y1, y0 y2, y1 y1, y1 y2, y2 y2 and
+// y3 y0, y3 y1, y3 y2 into yy[0..8] (FP64), for the caller to sum over the
+// group.
+template <int G, typename T, int NR, int RPL, class Gen, typename TS, bool FWD_ONLY = false>
 __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<T>& s, T* __restrict__ Lg,
-                          TS* __restrict__ yg, int gl) {
+                          TS* __restrict__ yg, int gl, double* yy = nullptr) {
   constexpr int NB = G / 2;
   const int LBS = (NB + bmax) * NB;
   const int RW = s.RW;
@@ -437,7 +441,9 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       const int i = gl + G * q;
       if (i < np) {
         T* dst = Lb + i * NB;
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (FWD_ONLY) {
+          (void)dst;
+        } else if constexpr (sizeof(T) == 4) {
 #pragma unroll
           for (int v = 0; v < NB / 4; ++v)
             reinterpret_cast<float4*>(dst)[v] =
@@ -451,8 +457,22 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
                 2 * v <= i ? pr[q][2 * v] : 0.0, 2 * v + 1 <= i ? pr[q][2 * v + 1] : 0.0);
         }
         if (i < nb) {
+          if constexpr (FWD_ONLY) {
+            static_assert(NR == 4, "forward-only factorisation carries 4 right-hand sides");
+            const double y0 = rh[q][0], y1 = rh[q][1], y2 = rh[q][2], y3 = rh[q][3];
+            yy[0] = fma(y0, y0, yy[0]);
+            yy[1] = fma(y0, y1, yy[1]);
+            yy[2] = fma(y0, y2, yy[2]);
+            yy[3] = fma(y1, y1, yy[3]);
+            yy[4] = fma(y1, y2, yy[4]);
+            yy[5] = fma(y2, y2, yy[5]);
+            yy[6] = fma(y3, y0, yy[6]);
+            yy[7] = fma(y3, y1, yy[7]);
+            yy[8] = fma(y3, y2, yy[8]);
+          } else {
 #pragma unroll
-          for (int c = 0; c < NR; ++c) yg[(size_t)(K + i) * NR + c] = (TS)rh[q][c];
+            for (int c = 0; c < NR; ++c) yg[(size_t)(K + i) * NR + c] = (TS)rh[q][c];
+          }
         } else {
           st_row4<NR>(s.rhs + ring(kslot + i, RW) * 4, rh[q]);
 #pragma unroll

@@ -138,9 +138,11 @@ struct PatchGen {
     w.nw = src[3];
   }
   // Whole row r: band entries at offsets 0, 1 (west), mx-1 (south-east),
-  // mx (south), mx+1 (south-west) and the three right-hand sides.
-  template <typename T>
-  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T rh[3]) const {
+  // mx (south), mx+1 (south-west) and the three right-hand sides; NR = 4
+  // adds a fourth right-hand side of ones (the load functional of interior
+  // nodes, up to the factor h^2).
+  template <typename T, int NR = 3>
+  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const {
     int i, j;
     node(r, i, j);
     const T aSW = (T)w.sw, aSE = (T)w.se;
@@ -167,6 +169,7 @@ struct PatchGen {
     rh[0] = AX + AY - AXY;
     rh[1] = AXY - AX;
     rh[2] = -AXY;
+    if constexpr (NR == 4) rh[3] = T(1);
   }
 };
 
@@ -207,12 +210,13 @@ struct ResidualGen {
 
 // psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction).
 template <typename T, typename TS>
-__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3]) {
+__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3],
+                                       bool with_psi = true) {
   const T X = (T)i / (T)g.Nx, Y = (T)j / (T)g.Ny;
   out[0] = (T(1) - X) * (T(1) - Y);
   out[1] = X * (T(1) - Y);
   out[2] = X * Y;
-  if (i > 0 && j > 0 && i < g.Nx && j < g.Ny) {
+  if (with_psi && i > 0 && j > 0 && i < g.Nx && j < g.Ny) {
     const TS* p = psi0 + ((size_t)(j - 1) * g.mx + (i - 1)) * 3;
     out[0] += (T)p[0];
     out[1] += (T)p[1];
@@ -270,7 +274,40 @@ struct UpscaleArgs {
   long long units;
   const int32_t* unit_list;   // optional: process only these units (device list)
   const int32_t* unit_count;  // device length of unit_list
+  const int32_t* cell_list;   // optional (MODE 1, 2): process only these cells (device list)
+  const int32_t* cell_count;  // device length of cell_list
 };
+
+// Upscale launch modes: 0 every unit (back-substitution route), 1 the
+// cells without oversampling by the forward-only route, 2 the other cells.
+// Splitting the two routes over two launches keeps one route's code hot per
+// kernel; with both in one kernel the instruction working set of an SM
+// doubled and cost more than the forward-only route saved.
+enum { kModeAll = 0, kModeFwd = 1, kModeRest = 2 };
+
+// Device lists of the cells with o = 0 (list0) and the others (list1), in
+// cell order, and their lengths: one warp, ballot compaction.
+__global__ void upscale_cell_lists_kernel(const int8_t* __restrict__ oversample, int ncell,
+                                          int32_t* __restrict__ list0, int32_t* __restrict__ list1,
+                                          int32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  int n0 = 0, n1 = 0;
+  for (int c0 = 0; c0 < ncell; c0 += 32) {
+    const int c = c0 + lane;
+    const bool valid = c < ncell;
+    const bool z = valid && oversample[c] == 0;
+    const unsigned m0 = __ballot_sync(0xffffffffu, z), m1 = __ballot_sync(0xffffffffu, valid && !z);
+    const unsigned below = (1u << lane) - 1u;
+    if (z) list0[n0 + __popc(m0 & below)] = c;
+    if (valid && !z) list1[n1 + __popc(m1 & below)] = c;
+    n0 += __popc(m0);
+    n1 += __popc(m1);
+  }
+  if (lane == 0) {
+    counts[0] = n0;
+    counts[1] = n1;
+  }
+}
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
 
@@ -289,7 +326,7 @@ __device__ __forceinline__ T group_sum(T v) {
 // patches have the same shape, so its two halves run the same loop bounds
 // in lockstep (an odd last sample is mirrored by the idle half, which
 // writes nothing).
-template <typename TK, typename TA, int RPL, int G>
+template <typename TK, typename TA, int RPL, int G, int MODE>
 __global__ void __launch_bounds__(upscale_warps(sizeof(TK) == 8, G) * 32,
                                   sizeof(TK) == 4 ? (G == 16 ? 3 : 4) : (G == 16 ? 3 : 2))
 upscale_kernel(UpscaleArgs A) {
@@ -312,20 +349,24 @@ upscale_kernel(UpscaleArgs A) {
   const int ncell = A.nc * A.nc;
   const int CN = (A.rho + 1) * (A.rho + 1);
 
+  // cells of this launch (MODE 1, 2: a device list, or all cells when none)
+  const int nlc = (MODE != kModeAll && A.cell_list) ? A.cell_count[0] : ncell;
   const long long nwork = A.unit_list ? (long long)A.unit_count[0]
-                                      : (G == 32 ? A.units : (long long)((A.S + 1) / 2) * ncell);
+                                      : (G == 32 ? (long long)A.S * nlc : (long long)((A.S + 1) / 2) * nlc);
   for (long long w = gw; w < nwork; w += nw) {
     long long u;
     bool dup = false;  // this half mirrors the other half's unit
+    const int ci = (int)(w % nlc);
+    const int cell_w = (MODE != kModeAll && A.cell_list) ? A.cell_list[ci] : ci;
     if (G == 32) {
-      u = A.unit_list ? (long long)A.unit_list[w] : w;
+      u = A.unit_list ? (long long)A.unit_list[w] : (long long)(w / nlc) * ncell + cell_w;
     } else {
-      int sp = 2 * (int)(w / ncell) + grp;
+      int sp = 2 * (int)(w / nlc) + grp;
       if (sp >= A.S) {
         sp = A.S - 1;
         dup = true;
       }
-      u = (long long)sp * ncell + (int)(w % ncell);
+      u = (long long)sp * ncell + cell_w;
     }
     const int s = (int)(u / ncell);
     const int cell = (int)(u % ncell);
@@ -344,10 +385,23 @@ upscale_kernel(UpscaleArgs A) {
     const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
     PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
     pg.finish();
+    // A patch that is the cell itself (no oversampling) in the FP32 form,
+    // without phi output, takes the forward-only route: K_e(l, m) =
+    // p_l^T A p_m - y_l . y_m with y = L^-1 R_l the forward solutions (the
+    // Galerkin identity of the cell problem, Eq. stiffness_local with
+    // phi_l = p_l + psi_l), and the corner sums of psi_l from z . y_l with
+    // z = L^-1 1; no factor is stored and there is no back substitution.
+    // The choice depends only on the cell, so both halves of a warp agree.
+    // The host sends only such cells to MODE 1 launches.
+    constexpr bool fwd_only = MODE == kModeFwd;
+    double yy[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     // a failed factorisation still runs every step (the halves of a warp
     // stay in lockstep); its unit gets NaN results and a status below
     int fail = -1;
-    if (g.n > 0) {
+    if constexpr (fwd_only) {
+      if (g.n > 0)
+        fail = blk_factor<G, TK, 4, RPL, PatchGen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
+    } else if (g.n > 0) {
       fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
       blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
       // FP64 iterative refinement with the factor: corr = residual, solve, add
@@ -372,10 +426,10 @@ upscale_kernel(UpscaleArgs A) {
       const int ex = e % A.rho, ey = e / A.rho;
       const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
       TA c0[3], c1[3], c2[3], c3[3];
-      psi_at<TA, TS>(g, psi0, i0, j0, c0);
-      psi_at<TA, TS>(g, psi0, i0 + 1, j0, c1);
-      psi_at<TA, TS>(g, psi0, i0 + 1, j0 + 1, c2);
-      psi_at<TA, TS>(g, psi0, i0, j0 + 1, c3);
+      psi_at<TA, TS>(g, psi0, i0, j0, c0, !fwd_only);
+      psi_at<TA, TS>(g, psi0, i0 + 1, j0, c1, !fwd_only);
+      psi_at<TA, TS>(g, psi0, i0 + 1, j0 + 1, c2, !fwd_only);
+      psi_at<TA, TS>(g, psi0, i0, j0 + 1, c3, !fwd_only);
       const TA ae = (TA)pg.ael(i0, j0);
       TA dd[3][6];
 #pragma unroll
@@ -402,6 +456,17 @@ upscale_kernel(UpscaleArgs A) {
     for (int q = 0; q < 6; ++q) M[q] = group_sum<G>(M[q]);
 #pragma unroll
     for (int l = 0; l < 3; ++l) m[l] = group_sum<G>(m[l]);
+    if constexpr (fwd_only) {
+      // M holds 6 p_l^T A p_m and m the corner sums of p_l: subtract the
+      // forward-solution products; every interior node is a corner of four
+      // elements, so the corner sums of psi_l are 4 z . y_l
+#pragma unroll
+      for (int q = 0; q < 9; ++q) yy[q] = group_sum<G>(yy[q]);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) M[q] = (TA)((double)M[q] - 6.0 * yy[q]);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) m[l] = (TA)((double)m[l] + 4.0 * yy[6 + l]);
+    }
 
     // recombination D = C^{-1}, C_jk = psi_j(cell corner k); identity when
     // the patch is the cell (its corners carry the bilinear data exactly)
@@ -506,9 +571,9 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
   *bmax = m + 1;
 }
 
-template <typename TK, typename TA, int RPL, int G>
+template <typename TK, typename TA, int RPL, int G, int MODE>
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  auto kern = upscale_kernel<TK, TA, RPL, G>;
+  auto kern = upscale_kernel<TK, TA, RPL, G, MODE>;
   constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
   const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * WPB * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -523,18 +588,22 @@ static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream
   return STOMSFEM_OK;
 }
 
-template <typename TK, typename TA, int G>
+template <typename TK, typename TA, int G, int MODE = kModeAll>
 static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
   const int rpl = (G / 2 + A.bmax + G - 1) / G;  // <= 3 (G = 32) or 5 (G = 16) for bmax <= 64
-  if (rpl <= 1) return launch_upscale<TK, TA, 1, G>(A, max_blocks, st);
-  if (rpl == 2) return launch_upscale<TK, TA, 2, G>(A, max_blocks, st);
-  if (rpl == 3) return launch_upscale<TK, TA, 3, G>(A, max_blocks, st);
+  if (rpl <= 1) return launch_upscale<TK, TA, 1, G, MODE>(A, max_blocks, st);
+  if (rpl == 2) return launch_upscale<TK, TA, 2, G, MODE>(A, max_blocks, st);
+  if (rpl == 3) return launch_upscale<TK, TA, 3, G, MODE>(A, max_blocks, st);
   if constexpr (G == 16) {
-    if (rpl == 4) return launch_upscale<TK, TA, 4, G>(A, max_blocks, st);
-    return launch_upscale<TK, TA, 5, G>(A, max_blocks, st);
+    if (rpl == 4) return launch_upscale<TK, TA, 4, G, MODE>(A, max_blocks, st);
+    return launch_upscale<TK, TA, 5, G, MODE>(A, max_blocks, st);
   }
   return set_error(STOMSFEM_EINVAL, "bandwidth %d too large", A.bmax);
 }
+
+// Bytes at the end of the workspace for the two cell lists of the split
+// FP32 launch.
+static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(int32_t) * (2 * (size_t)g->nc * g->nc + 2)); }
 
 // Lanes per unit of each form: two units per warp.
 constexpr int group_lanes(int) { return 16; }
@@ -557,7 +626,7 @@ extern "C" int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_
   if (slot_bytes) *slot_bytes = sb;
   if (recommended_bytes) {
     const int sms = device_sm_count();
-    *recommended_bytes = sb * (size_t)(sms > 0 ? sms : 152) * 32;
+    *recommended_bytes = sb * (size_t)(sms > 0 ? sms : 152) * 32 + cell_list_bytes(grid);
   }
   return STOMSFEM_OK;
 }
@@ -620,7 +689,34 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   A.units = units;
   A.unit_list = nullptr;
   A.unit_count = nullptr;
+  A.cell_list = nullptr;
+  A.cell_count = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == STOMSFEM_FP32 && !phi) {
+    // FP32 without phi output: cells without oversampling take the
+    // forward-only route in a launch of their own, the others follow
+    constexpr int G = group_lanes(STOMSFEM_FP32);
+    if (!oversample) return launch_rpl<float, float, G, kModeFwd>(A, max_blocks, st);
+    const size_t lbytes = cell_list_bytes(grid);
+    const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
+    if (slots2 >= slots_per_block) {
+      const int ncell = grid->nc * grid->nc;
+      unsigned char* base = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
+      int32_t* list0 = reinterpret_cast<int32_t*>(base);
+      int32_t* list1 = list0 + ncell;
+      int32_t* counts = list1 + ncell;
+      upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, list0, list1, counts);
+      STOMSFEM_TRY_CUDA(cudaGetLastError());
+      const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
+      A.cell_list = list0;
+      A.cell_count = counts;
+      rc = launch_rpl<float, float, G, kModeFwd>(A, mb, st);
+      if (rc) return rc;
+      A.cell_list = list1;
+      A.cell_count = counts + 1;
+      return launch_rpl<float, float, G, kModeRest>(A, mb, st);
+    }
+  }
   if (precision == STOMSFEM_FP64) return launch_rpl<double, double, group_lanes(STOMSFEM_FP64)>(A, max_blocks, st);
   if (precision == STOMSFEM_FP32_REFINED)
     return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED)>(A, max_blocks, st);

@@ -245,6 +245,23 @@ def test_paired_units_one_indefinite(orc, precision):
     assert np.max(np.linalg.norm(bg - bo, axis=-1)[ok] / np.linalg.norm(bo, axis=-1)[ok]) <= TOL[precision]
 
 
+def test_fp32_forward_only_route(orc):
+    """In the FP32 form, cells without oversampling (and no phi output) get
+    K_e = p^T A p - y^T y and the load from z . y (forward substitution
+    only); asking for phi forces the back-substitution route.  Both agree
+    with the FP64 oracle within the FP32 tolerance, and with each other."""
+    nf, nc = 128, 4
+    r = np.random.default_rng(3)
+    a = np.exp(r.uniform(-4.6, 4.6, size=(3, nf, nf)))     # contrast up to 1e4
+    Ko, bo = orc.upscale(nf, nc, 1.0, a)
+    K1, b1 = gpu_upscale(nf, nc, 1.0, a, precision=api.FP32)
+    K2, b2, _ = gpu_upscale(nf, nc, 1.0, a, precision=api.FP32, want_phi=True)
+    for K, b in ((K1, b1), (K2, b2)):
+        assert rel_unit(K, Ko) <= TOL[api.FP32]
+        assert rel_unit(b, bo) <= TOL[api.FP32]
+    assert rel_unit(K1, K2) <= TOL[api.FP32]
+
+
 def _assemble_residual(Ke, be, u, nc):
     """|| S u - b || / ||b|| for the coarse system assembled from K_e, b_e
     (written out here independently of both the library and the oracle)."""
