@@ -182,29 +182,38 @@ struct ResidualGen {
     if (i <= 0 || j <= 0 || i > pg.mx || j > pg.Ny - 1) return 0.0;
     return psi0[((size_t)(j - 1) * pg.mx + (i - 1)) * 3 + l];
   }
-  template <typename T>
-  __device__ __forceinline__ T coef(int, int) const { return T(0); }
-  template <typename T>
-  __device__ __forceinline__ T rhs(int r, int l) const {
+  // All three right-hand sides of row r: the stencil coefficients and the
+  // closed-form -(A p_l) once per node, divisions replaced by products with
+  // reciprocals (each residual term then carries a rounding or two of FP64,
+  // far below what the refinement resolves).
+  __device__ __forceinline__ void rhs3(int r, double out[3]) const {
     int i, j;
     pg.node(r, i, j);
     const double aSW = pg.ael(i - 1, j - 1), aSE = pg.ael(i, j - 1);
     const double aNE = pg.ael(i, j), aNW = pg.ael(i - 1, j);
-    double AX, AY, AXY;
-    pg.ap<double>(i, j, AX, AY, AXY);
-    double r0 = (l == 0) ? AX + AY - AXY : (l == 1 ? AXY - AX : -AXY);
-    // subtract A psi0 with the full 9-point stencil
-    const double c = (2.0 / 3.0) * (aSW + aSE + aNE + aNW);
-    double s = c * psi(i, j, l);
-    s -= (aSW + aNW) / 6.0 * psi(i - 1, j, l);
-    s -= (aSE + aNE) / 6.0 * psi(i + 1, j, l);
-    s -= (aSW + aSE) / 6.0 * psi(i, j - 1, l);
-    s -= (aNE + aNW) / 6.0 * psi(i, j + 1, l);
-    s -= aSW / 3.0 * psi(i - 1, j - 1, l);
-    s -= aSE / 3.0 * psi(i + 1, j - 1, l);
-    s -= aNE / 3.0 * psi(i + 1, j + 1, l);
-    s -= aNW / 3.0 * psi(i - 1, j + 1, l);
-    return (T)(r0 - s);
+    constexpr double r3 = 1.0 / 3.0, r6 = 1.0 / 6.0;
+    const double AX = 0.5 * ((aSW + aNW) - (aSE + aNE)) * pg.iNxd;
+    const double AY = 0.5 * ((aSW + aSE) - (aNW + aNE)) * pg.iNyd;
+    const double AXY = ((double)i * pg.iNxd) * AY + ((double)j * pg.iNyd) * AX +
+                       ((aSE + aNW) - (aNE + aSW)) * r3 * pg.iNxd * pg.iNyd;
+    const double r0[3] = {AX + AY - AXY, AXY - AX, -AXY};
+    // A psi0 with the full 9-point stencil
+    const double cC = (2.0 / 3.0) * ((aSW + aSE) + (aNE + aNW));
+    const double cW = (aSW + aNW) * r6, cE = (aSE + aNE) * r6, cS = (aSW + aSE) * r6, cN = (aNE + aNW) * r6;
+    const double dSW = aSW * r3, dSE = aSE * r3, dNE = aNE * r3, dNW = aNW * r3;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double t = cC * psi(i, j, l);
+      t -= cW * psi(i - 1, j, l);
+      t -= cE * psi(i + 1, j, l);
+      t -= cS * psi(i, j - 1, l);
+      t -= cN * psi(i, j + 1, l);
+      t -= dSW * psi(i - 1, j - 1, l);
+      t -= dSE * psi(i + 1, j - 1, l);
+      t -= dNE * psi(i + 1, j + 1, l);
+      t -= dNW * psi(i - 1, j + 1, l);
+      out[l] = r0[l] - t;
+    }
   }
 };
 
@@ -408,7 +417,7 @@ upscale_kernel(UpscaleArgs A) {
       for (int it = 0; it < A.refine; ++it) {
         __syncwarp();
         const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
-        for (int k = gl; k < g.n * 3; k += G) corr[k] = rg.rhs<double>(k / 3, k % 3);
+        for (int r = gl; r < g.n; r += G) rg.rhs3(r, corr + (size_t)3 * r);
         __syncwarp();
         blk_forward_stored<G, TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
         blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
