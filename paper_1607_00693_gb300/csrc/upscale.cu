@@ -217,11 +217,11 @@ struct ResidualGen {
   }
 };
 
-// psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction).
+// psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction),
+// given its patch coordinates X = i / Nx, Y = j / Ny.
 template <typename T, typename TS>
-__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3],
-                                       bool with_psi = true) {
-  const T X = (T)i / (T)g.Nx, Y = (T)j / (T)g.Ny;
+__device__ __forceinline__ void psi_at_xy(const UnitGeom& g, const TS* psi0, int i, int j, T X, T Y, T out[3],
+                                          bool with_psi = true) {
   out[0] = (T(1) - X) * (T(1) - Y);
   out[1] = X * (T(1) - Y);
   out[2] = X * Y;
@@ -231,6 +231,13 @@ __device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i,
     out[1] += (T)p[1];
     out[2] += (T)p[2];
   }
+}
+
+// The same, computing X and Y.
+template <typename T, typename TS>
+__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3],
+                                       bool with_psi = true) {
+  psi_at_xy<T, TS>(g, psi0, i, j, (T)i / (T)g.Nx, (T)j / (T)g.Ny, out, with_psi);
 }
 
 // 4x4 inverse by Gauss-Jordan elimination without row exchanges, all
@@ -431,14 +438,32 @@ upscale_kernel(UpscaleArgs A) {
     // 2 sum_diagonals du dv; m_j = sum over element corners of psi_j.
     TA M[6] = {0, 0, 0, 0, 0, 0};
     TA m[3] = {0, 0, 0};
+    TA iNx, iNy;
+    if constexpr (sizeof(TA) == 4) {
+      iNx = pg.iNxf;
+      iNy = pg.iNyf;
+    } else {
+      iNx = (TA)pg.iNxd;
+      iNy = (TA)pg.iNyd;
+    }
     for (int e = gl; e < A.rho * A.rho; e += G) {
       const int ex = e % A.rho, ey = e / A.rho;
       const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
       TA c0[3], c1[3], c2[3], c3[3];
-      psi_at<TA, TS>(g, psi0, i0, j0, c0, !fwd_only);
-      psi_at<TA, TS>(g, psi0, i0 + 1, j0, c1, !fwd_only);
-      psi_at<TA, TS>(g, psi0, i0 + 1, j0 + 1, c2, !fwd_only);
-      psi_at<TA, TS>(g, psi0, i0, j0 + 1, c3, !fwd_only);
+      // patch coordinates of the element's corners: the product with 1/Nx
+      // (1/Ny) and one residual correction q + (i - q N) / N, which rounds
+      // like the quotient i / N
+      auto quot = [](TA num, TA den, TA inv) {
+        const TA q = num * inv;
+        return fma(fma(-q, den, num), inv, q);
+      };
+      const TA Nxf = (TA)g.Nx, Nyf = (TA)g.Ny;
+      const TA X0 = quot((TA)i0, Nxf, iNx), X1 = quot((TA)(i0 + 1), Nxf, iNx);
+      const TA Y0 = quot((TA)j0, Nyf, iNy), Y1 = quot((TA)(j0 + 1), Nyf, iNy);
+      psi_at_xy<TA, TS>(g, psi0, i0, j0, X0, Y0, c0, !fwd_only);
+      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0, X1, Y0, c1, !fwd_only);
+      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0 + 1, X1, Y1, c2, !fwd_only);
+      psi_at_xy<TA, TS>(g, psi0, i0, j0 + 1, X0, Y1, c3, !fwd_only);
       const TA ae = (TA)pg.ael(i0, j0);
       TA dd[3][6];
 #pragma unroll
