@@ -54,10 +54,11 @@ __device__ inline UnitGeom unit_geom(int nf, int rho, int cx, int cy, int o) {
 struct PatchGen {
   const double* a;  // this sample's coefficient [nf][nf]
   int nf, x0, y0, Nx, Ny, mx;
-  float iNxf, iNyf;  // 1/Nx, 1/Ny, set by finish()
+  float iNxf, iNyf, rmx;  // 1/Nx, 1/Ny, 1/mx, set by finish()
   double iNxd, iNyd;
 
   __device__ __forceinline__ void finish() {
+    rmx = __frcp_rn((float)mx);
     iNxd = 1.0 / (double)Nx;
     iNyd = 1.0 / (double)Ny;
     iNxf = 1.0f / (float)Nx;
@@ -70,7 +71,7 @@ struct PatchGen {
   __device__ __forceinline__ void node(int r, int& i, int& j) const {
     // j - 1 = floor(r / mx) from a float reciprocal: (r + 1/2) / mx stays at
     // least 1/(2 mx) away from an integer, far above the rounding error
-    const int q = __float2int_rz(((float)r + 0.5f) * __frcp_rn((float)mx));
+    const int q = __float2int_rz(((float)r + 0.5f) * rmx);
     j = q + 1;
     i = r - q * mx + 1;
   }
@@ -290,6 +291,7 @@ struct UpscaleArgs {
   long long units;
   const int32_t* unit_list;   // optional: process only these units (device list)
   const int32_t* unit_count;  // device length of unit_list
+  double fq, fH2;             // f h^2 / 4 and f H^2 (load scaling)
   const int32_t* cell_list;   // optional (MODE 1, 2): process only these cells (device list)
   const int32_t* cell_count;  // device length of cell_list
 };
@@ -530,18 +532,25 @@ upscale_kernel(UpscaleArgs A) {
       if (A.status) A.status[u] = fail + 1;
     }
     if (gl == 0 && !dup && fail < 0) {
-      const double h = 1.0 / A.nf;
+      // one lane per unit: FP64 here runs at the narrow pipe's single-lane
+      // cost, so divisions become products with constants and the identity
+      // recombination of an unoversampled patch is skipped
       double MM[4][4];
       MM[0][0] = M[0]; MM[0][1] = MM[1][0] = M[1]; MM[0][2] = MM[2][0] = M[2];
       MM[1][1] = M[3]; MM[1][2] = MM[2][1] = M[4]; MM[2][2] = M[5];
       for (int r = 0; r < 3; ++r) MM[r][3] = MM[3][r] = -(MM[r][0] + MM[r][1] + MM[r][2]);
       MM[3][3] = -(MM[0][3] + MM[1][3] + MM[2][3]);
       for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) MM[r][c] /= 6.0;
-      const double fq = A.f * h * h / 4.0;
-      double mv[4] = {fq * (double)m[0], fq * (double)m[1], fq * (double)m[2], 0.0};
-      const double H = (double)A.rho * h;
-      mv[3] = A.f * H * H - (mv[0] + mv[1] + mv[2]);
+        for (int c = 0; c < 4; ++c) MM[r][c] *= 1.0 / 6.0;
+      double mv[4] = {A.fq * (double)m[0], A.fq * (double)m[1], A.fq * (double)m[2], 0.0};
+      mv[3] = A.fH2 - (mv[0] + mv[1] + mv[2]);
+      if (patch_is_cell) {
+        int q = 0;
+        for (int r = 0; r < 4; ++r)
+          for (int c = r; c < 4; ++c) Ke[q++] = MM[r][c];
+        for (int r = 0; r < 4; ++r) be[r] = mv[r];
+        if (A.status) A.status[u] = 0;
+      } else {
       double T4[4][4];
       for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) {
@@ -562,6 +571,7 @@ upscale_kernel(UpscaleArgs A) {
         be[r] = ok ? t : qnan();
       }
       if (A.status) A.status[u] = ok ? 0 : STOMSFEM_ENOTSPD;
+      }
     }
     if (A.phi && !dup && fail < 0) {
       double* ph = A.phi + (size_t)u * 4 * CN;
@@ -710,6 +720,8 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
   A.max_o = mo;
   A.S = S;
   A.f = grid->f;
+  A.fq = grid->f / (4.0 * (double)grid->nf * (double)grid->nf);
+  A.fH2 = grid->f / ((double)grid->nc * (double)grid->nc);
   A.refine = precision == STOMSFEM_FP32_REFINED ? refine_iters : 0;
   A.Ke = Ke;
   A.be = be;
@@ -783,6 +795,8 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   A.max_o = 0;
   A.S = S;
   A.f = grid->f;
+  A.fq = grid->f / (4.0 * (double)grid->nf * (double)grid->nf);
+  A.fH2 = grid->f / ((double)grid->nc * (double)grid->nc);
   A.refine = 0;
   A.Ke = Ke;
   A.be = be;
