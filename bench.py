@@ -423,7 +423,10 @@ def main():
         return dict(a=a, Ke=Ke, be=be, u=u, wsu=wsu, wsc=wsc, mean=mom[0], m2=mom[1], cnt=cnt)
 
     def step(bf, xs, form, ev=None):
-        api.stomsfem_sample_coef(g, fld, xs, bf["a"], stream=stream)
+        # the FP32 form samples the coefficient in FP32 arithmetic too
+        api.stomsfem_sample_coef_precision(g, fld, xs, bf["a"],
+                                           precision=api.FP32 if form == "fp32" else api.FP64,
+                                           stream=stream)
         if ev is not None:
             ev[0].record(stream)
         api.stomsfem_upscale(g, bf["a"], bf["Ke"], bf["be"], oversample=ov_t, max_oversample=mo,

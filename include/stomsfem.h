@@ -94,6 +94,17 @@ int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stre
 int stomsfem_sample_coef(const stomsfem_grid* grid, const stomsfem_field* field,
                          const double* xi, int32_t S, double* a, stomsfem_stream_t stream);
 
+/* The same sampling at a chosen arithmetic precision: STOMSFEM_FP64 is
+ * stomsfem_sample_coef; STOMSFEM_FP32 evaluates the bump sums and the
+ * exponentials in FP32 (a is still stored as float64), for the FP32
+ * upscaling form whose cell matrices are FP32 anyway: relative error of a
+ * about |scale * z| x 1e-6 (EXP) and contrast_log * gain * 1e-6
+ * (EXP_SIGMOID).  Errors: as stomsfem_sample_coef, and EINVAL for any other
+ * precision. */
+int stomsfem_sample_coef_precision(const stomsfem_grid* grid, const stomsfem_field* field,
+                                   const double* xi, int32_t S, int32_t precision, double* a,
+                                   stomsfem_stream_t stream);
+
 /* Scratch needed by stomsfem_upscale for one unit in flight ("slot") and
  * the recommended total (a slot per unit the whole GPU keeps in flight, plus
  * 8 (nc^2 + 1) bytes, rounded up to 256, for the cell lists of the FP32

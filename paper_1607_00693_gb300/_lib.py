@@ -42,6 +42,8 @@ _SIG = {
     "stomsfem_selftest_wait_timeout": (ctypes.c_int, [_I, ctypes.POINTER(_I)]),
     "stomsfem_selftest_exp": (ctypes.c_int, [_P, _I, _P, _P]),
     "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
+    "stomsfem_sample_coef_precision": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I,
+                                                      _I, _P, _P]),
     "stomsfem_upscale_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I,
                                                         ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "stomsfem_upscale": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _P, _P, _P, _P,

@@ -76,6 +76,13 @@ def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
                                          _dev(a, torch.float64, (S, g.nf, g.nf), "a"), _stream(stream)))
 
 
+def stomsfem_sample_coef_precision(g: Grid, fld: Field, xi, a, precision=FP64, stream=None):
+    S = xi.shape[0]
+    L.check(L.lib().stomsfem_sample_coef_precision(
+        ctypes.byref(g), ctypes.byref(fld), _dev(xi, torch.float64, (S, fld.nbx * fld.nby), "xi"), S,
+        int(precision), _dev(a, torch.float64, (S, g.nf, g.nf), "a"), _stream(stream)))
+
+
 def stomsfem_upscale_workspace_size(g: Grid, max_oversample=0, precision=FP64):
     sb, rb = ctypes.c_size_t(), ctypes.c_size_t()
     L.check(L.lib().stomsfem_upscale_workspace_size(ctypes.byref(g), int(max_oversample),

@@ -70,6 +70,37 @@ def test_sample_coef_matches_oracle(orc):
         assert np.max(np.abs(got / ref - 1)) < 1e-13, name
 
 
+def test_sample_coef_fp32_arithmetic(orc):
+    """The FP32-arithmetic sampler (for the FP32 upscaling form) against the
+    FP64 oracle: z is a sum of nbx*nby FP32 products, so its absolute error is
+    a few eps32 times the sum of |terms|; a = exp(scale z) turns that into a
+    relative error of |scale| times it (EXP), and exp(c sigma(g z)) into
+    c g / 4 times it (EXP_SIGMOID).  The bounds below are those estimates
+    with the fields' largest sums of |terms|, times 4."""
+    eps = 2.0 ** -24
+    for name in ("msfem_64", "upscale_1024", "contrast_2048"):
+        w = W.workload(name)
+        fld = w["field"]
+        nf = w["nf"] if name == "msfem_64" else 256
+        xi = W.draw_xi(fld, 3, w["seed"], w["dist"])
+        ref = orc.sample_coef(nf, fld, xi)
+        a = torch.empty((3, nf, nf), dtype=torch.float64, device=DEV)
+        api.stomsfem_sample_coef_precision(api.grid(nf, w["nc"]), api.field_from_dict(fld),
+                                           torch.from_numpy(xi).to(DEV), a, precision=api.FP32)
+        got = a.cpu().numpy()
+        # sum of |xi_i psi_i(x)| over the bumps, bounded by max|xi| times the
+        # largest bump sum (<= (1 + 2 sqrt(pi) w n)^2 for a lattice of spacing 1/n)
+        nb = max(fld["nbx"], fld["nby"])
+        tsum = np.abs(xi).max() * (1.0 + 2.0 * np.sqrt(np.pi) * fld["width"] * nb) ** 2
+        if fld["kind"] == api.FIELD_EXP:
+            gain = abs(fld.get("scale", 1.0))
+        else:
+            gain = fld["contrast_log"] * fld["gain"] / 4.0
+        bound = 4 * (gain * tsum * 8 * eps + 4 * eps)
+        err = np.max(np.abs(got / ref - 1))
+        assert err <= bound, (name, err, bound)
+
+
 @pytest.mark.parametrize("precision", [api.FP64, api.FP32_REFINED, api.FP32])
 def test_upscale_msfem_64(orc, precision):
     w = W.workload("msfem_64")
