@@ -38,8 +38,8 @@ FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
 # the H/h = 32 workload), by library version and form.
 DRAM_BYTES_PER_UNIT = {
     # FP32: the forward-only and the back-substitution launches of one call
-    ("stomsfem-gb300 0.4 (sm_103a)", "fp32"): (0.051997e9 + 0.000344e9 + 7.113515e9 + 6.768242e9) / 32768,
-    ("stomsfem-gb300 0.4 (sm_103a)", "fp64"): (1.829177e9 + 1.938842e9) / 4096,
+    ("stomsfem-gb300 0.5 (sm_103a)", "fp32"): (0.051979e9 + 0.000273e9 + 7.112449e9 + 6.768770e9) / 32768,
+    ("stomsfem-gb300 0.5 (sm_103a)", "fp64"): (1.825947e9 + 1.937501e9) / 4096,
 }
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
