@@ -298,7 +298,7 @@ def bench_pod(api, dev, stream, samples=None):
     peaks = _peaks()
     res["roofline_note"] = ("GEMM flops of the whole call / whole-call time vs bf16 %.0f TFLOP/s "
                             "(measured burst): launch- and FP64-epilogue-bound at this size"
-                            % peaks.get("bf16_tflops", 1890.2))
+                            % peaks.get("bf16_tflops", 1900.0))
     return res, 4 + 2 * 3 * 4
 
 
@@ -351,7 +351,7 @@ def bench_surrogate(api, dev, stream, samples=None, steps=3000):
            "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:2000].contiguous(), be[:2000].contiguous(),
                                                 Kp[:2000].contiguous(), bp[:2000].contiguous(), dev),
            "tensor_tflops_whole_call": flops / (ms_inf / 1e3) / 1e12,
-           "tensor_peak_tflops": _peaks().get("bf16_tflops", 1890.2)}
+           "tensor_peak_tflops": _peaks().get("bf16_tflops", 1900.0)}
     api.stomsfem_surrogate_destroy(h)
     return res, 6 * 4 + 8
 
