@@ -30,8 +30,9 @@
 // Row generator interface:
 //   typename Gen::Raw                  raw per-row values,
 //   gen.load(r, Raw&)                  issue the global loads of row r,
-//   gen.prefetch(r, double* dst4)      asynchronous copy of row r's values,
-//   gen.from_smem(const double* src4, Raw&)
+//   gen.prefetch(r, double* dst)       copy of row r's values (at most RAWD
+//                                      doubles; asynchronous where possible),
+//   gen.from_smem(const double* src, Raw&)
 //   gen.make<T>(r, const Raw&, T e[5], T rhs[NR])
 //                                      band entries A[r][r], A[r][r-1],
 //                                      A[r][r-mx+1], A[r][r-mx], A[r][r-mx-1]
@@ -53,8 +54,8 @@ struct BlkSmem {
   T* rhs;  // [RW][4]
   T* lb;   // 2 x 2 x [NB] broadcast of the block-row multipliers; [NB][4]
            // block solution in the stored forward substitution
-  double* raw;  // [NB][4] coefficient values of the next rows (async prefetch)
-  int RW, PW, RP;
+  double* raw;  // [NB][RAWD] generator values of the next rows (prefetched)
+  int RW, PW, RP, RAWD;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -81,16 +82,17 @@ __host__ __device__ inline int blk_wnd_elems(int NB, int bmax) {
 // banks apart, so that the same access pattern in both halves meets
 // different banks.
 template <typename T>
-__host__ __device__ inline size_t blk_smem_bytes(int NB, int bmax) {
+__host__ __device__ inline size_t blk_smem_bytes(int NB, int bmax, int rawd = 4) {
   const int RW = blk_ring_rows(NB, bmax);
   const size_t b = al16(sizeof(T) * blk_wnd_elems(NB, bmax)) + al16(sizeof(T) * RW * 4) +
-                   al16(sizeof(T) * 4 * NB) + al16(sizeof(double) * NB * 4);
+                   al16(sizeof(T) * 4 * NB) + al16(sizeof(double) * NB * rawd);
   return b + ((64 - (b & 127)) & 127);
 }
 
 template <typename T>
-__device__ inline BlkSmem<T> make_blk(unsigned char* base, int NB, int bmax) {
+__device__ inline BlkSmem<T> make_blk(unsigned char* base, int NB, int bmax, int rawd = 4) {
   BlkSmem<T> s;
+  s.RAWD = rawd;
   s.RW = blk_ring_rows(NB, bmax);
   s.PW = blk_pitch(bmax);
   s.RP = (bmax + 3) & ~3;
@@ -387,7 +389,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
   int fslot = ring(filled, RW);  // slot of row `filled` (filled <= RW)
   // rows of the next fill: their coefficient values are copied one block
   // ahead into shared memory by asynchronous copies
-  if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + 4 * gl);
+  if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + s.RAWD * gl);
   cp_async_commit();
   int kslot = 0;  // slot of row K
   for (int K = 0, kb = 0; K < n; K += NB, ++kb, kslot = ring(kslot + NB, RW)) {
@@ -398,12 +400,12 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       cp_async_wait<0>();
       __syncwarp();
       typename Gen::Raw pf;
-      if (gl < NB) gen.from_smem(s.raw + 4 * gl, pf);
+      if (gl < NB) gen.from_smem(s.raw + s.RAWD * gl, pf);
       blk_fill_raw<G, T, NR>(gen, s, filled, need, fslot, b, gl, pf);
       fslot = ring(fslot + (need - filled), RW);
       filled = need;
       __syncwarp();
-      if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + 4 * gl);
+      if (gl < NB && filled + gl < min(n, filled + NB)) gen.prefetch(filled + gl, s.raw + s.RAWD * gl);
       cp_async_commit();
     }
     __syncwarp();

@@ -2,13 +2,12 @@
 // (Eq. MCestimate).  One warp per sample: the coarse matrix over the
 // (nc-1)^2 interior coarse nodes is again a 9-point-stencil SPD matrix,
 // assembled row by row from the K_e of the four cells around each node
-// and factorised with the same warp banded Cholesky as the cell problems.
-#include "band_warp.cuh"
+// and factorised in FP64 with the blocked banded Cholesky of the cell
+// problems (column blocks of 16, rows generated one block ahead).
+#include "band_block.cuh"
 #include "common.cuh"
 
 namespace stomsfem {
-
-constexpr int kCoarseWarps = 4;
 
 __device__ __forceinline__ int kidx(int l, int lp) {
   // packed upper-triangle index of the symmetric 4x4 entry (l, lp)
@@ -16,53 +15,75 @@ __device__ __forceinline__ int kidx(int l, int lp) {
   return l * 4 - (l * (l - 1)) / 2 + (lp - l);
 }
 
-struct CoarseGen {
+// Row generator of the coarse system for the blocked solver: a row's five
+// band entries and its load, summed from the K_e and b_e of the four cells
+// around the node (loads issued one block ahead by prefetch, which stores
+// the six sums in the row's raw slot).
+struct CoarseBlkGen {
   const double* Ke;  // this sample [nc*nc][10]
   const double* be;  // [nc*nc][4]
-  int nc, mi;
+  int nc, mx;        // mx = nc - 1 interior nodes per row
+  static constexpr int kRaw = 8;
+  struct Raw {
+    double e[5], rhs;
+  };
   __device__ __forceinline__ double K(int cx, int cy, int l, int lp) const {
-    return Ke[(size_t)(cy * nc + cx) * 10 + kidx(l, lp)];
+    return __ldg(Ke + (size_t)(cy * nc + cx) * 10 + kidx(l, lp));
   }
-  template <typename T>
-  __device__ __forceinline__ T coef(int r, int d) const {
-    if (d != 0 && d != 1 && d != mi - 1 && d != mi && d != mi + 1) return T(0);
-    const int J = r / mi + 1, I = r - (J - 1) * mi + 1;
-    double v = 0.0;
+  __device__ __forceinline__ void load(int r, Raw& w) const {
+    const int J = r / mx + 1, I = r - (J - 1) * mx + 1;
     // cells around node (I, J): SW (I-1,J-1) node=NE(2); SE (I,J-1) node=NW(3);
     // NE (I,J) node=SW(0); NW (I-1,J) node=SE(1)
-    if (d == 0) v += K(I - 1, J - 1, 2, 2) + K(I, J - 1, 3, 3) + K(I, J, 0, 0) + K(I - 1, J, 1, 1);
-    if (d == 1 && I > 1) v += K(I - 1, J - 1, 2, 3) + K(I - 1, J, 1, 0);
-    if (d == mi && J > 1) v += K(I - 1, J - 1, 2, 1) + K(I, J - 1, 3, 0);
-    if (d == mi + 1 && I > 1 && J > 1) v += K(I - 1, J - 1, 2, 0);
-    if (d == mi - 1 && I < mi && J > 1) v += K(I, J - 1, 3, 1);
-    return (T)v;
+    w.e[0] = K(I - 1, J - 1, 2, 2) + K(I, J - 1, 3, 3) + K(I, J, 0, 0) + K(I - 1, J, 1, 1);
+    w.e[1] = I > 1 ? K(I - 1, J - 1, 2, 3) + K(I - 1, J, 1, 0) : 0.0;           // west
+    w.e[2] = (I < mx && J > 1) ? K(I, J - 1, 3, 1) : 0.0;                       // south-east
+    w.e[3] = J > 1 ? K(I - 1, J - 1, 2, 1) + K(I, J - 1, 3, 0) : 0.0;           // south
+    w.e[4] = (I > 1 && J > 1) ? K(I - 1, J - 1, 2, 0) : 0.0;                   // south-west
+    w.rhs = __ldg(be + (size_t)((J - 1) * nc + I - 1) * 4 + 2) + __ldg(be + (size_t)((J - 1) * nc + I) * 4 + 3) +
+            __ldg(be + (size_t)(J * nc + I) * 4 + 0) + __ldg(be + (size_t)(J * nc + I - 1) * 4 + 1);
   }
-  template <typename T>
-  __device__ __forceinline__ T rhs(int r, int) const {
-    const int J = r / mi + 1, I = r - (J - 1) * mi + 1;
-    return (T)(be[(size_t)((J - 1) * nc + I - 1) * 4 + 2] + be[(size_t)((J - 1) * nc + I) * 4 + 3] +
-               be[(size_t)(J * nc + I) * 4 + 0] + be[(size_t)(J * nc + I - 1) * 4 + 1]);
+  __device__ __forceinline__ void prefetch(int r, double* dst) const {
+    Raw w;
+    load(r, w);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dst[k] = w.e[k];
+    dst[5] = w.rhs;
+  }
+  __device__ __forceinline__ void from_smem(const double* src, Raw& w) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w.e[k] = src[k];
+    w.rhs = src[5];
+  }
+  template <typename T, int NR = 1>
+  __device__ __forceinline__ void make(int, const Raw& w, T e[5], T* rh) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) e[k] = (T)w.e[k];
+    rh[0] = (T)w.rhs;
   }
 };
 
-__global__ void __launch_bounds__(kCoarseWarps * 32)
-coarse_kernel(int nc, int S, const double* __restrict__ Ke, const double* __restrict__ be,
-              double* __restrict__ u, unsigned char* ws, size_t slot_bytes) {
+constexpr int kCoarseBlkWarps = 2;
+
+template <int RPL>
+__global__ void __launch_bounds__(kCoarseBlkWarps * 32)
+coarse_blk_kernel(int nc, int S, const double* __restrict__ Ke, const double* __restrict__ be,
+                  double* __restrict__ u, unsigned char* ws, size_t slot_bytes, size_t l_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int mi = nc - 1, n = mi * mi, b = nc;
-  BandRing<double, 1> ring = make_ring<double, 1>(smem + wib * ring_bytes<double, 1>(b), b);
-  const int gw = blockIdx.x * kCoarseWarps + wib, nw = gridDim.x * kCoarseWarps;
+  const int mx = nc - 1, n = mx * mx, b = nc;
+  const BlkSmem<double> sm =
+      make_blk<double>(smem + wib * blk_smem_bytes<double>(16, b, CoarseBlkGen::kRaw), 16, b, CoarseBlkGen::kRaw);
+  const int gw = blockIdx.x * kCoarseBlkWarps + wib, nw = gridDim.x * kCoarseBlkWarps;
   unsigned char* slot = ws + (size_t)gw * slot_bytes;
   double* Lg = reinterpret_cast<double*>(slot);
-  double* x = reinterpret_cast<double*>(slot + (((size_t)(n > 0 ? n : 1) * (b + 1) * 8 + 255) & ~size_t(255)));
+  double* x = reinterpret_cast<double*>(slot + l_bytes);
   const int NN = nc + 1;
   for (int s = gw; s < S; s += nw) {
-    CoarseGen gen{Ke + (size_t)s * nc * nc * 10, be + (size_t)s * nc * nc * 4, nc, mi};
+    const CoarseBlkGen gen{Ke + (size_t)s * nc * nc * 10, be + (size_t)s * nc * nc * 4, nc, mx};
     int fail = -1;
     if (n > 0) {
-      fail = band_factor_forward<double, 1>(gen, n, b, ring, Lg, x, lane);
-      if (fail < 0) band_backward<double, 1>(n, b, ring.R, Lg, x, ring.rhs, lane);
+      fail = blk_factor<32, double, 1, RPL>(gen, n, b, b, sm, Lg, x, lane);
+      blk_backward<32, double, 1>(n, b, b, sm, Lg, x, lane);
     }
     __syncwarp();
     double* us = u + (size_t)s * NN * NN;
@@ -70,7 +91,7 @@ coarse_kernel(int nc, int S, const double* __restrict__ Ke, const double* __rest
     for (int q = lane; q < NN * NN; q += 32) {
       const int I = q % NN, J = q / NN;
       double v = 0.0;
-      if (I > 0 && J > 0 && I < nc && J < nc) v = fail < 0 ? x[(J - 1) * mi + (I - 1)] : nanv;
+      if (I > 0 && J > 0 && I < nc && J < nc) v = fail < 0 ? x[(J - 1) * mx + (I - 1)] : nanv;
       us[q] = v;
     }
     __syncwarp();
@@ -99,9 +120,14 @@ __global__ void moments_kernel(int nn, int S, const double* __restrict__ u, doub
 
 __global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
 
+// Slot of one sample: the factor blocks, then the solution.
+static size_t coarse_l_bytes(int nc) {
+  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1;
+  return (blk_factor_elems(n, nc) * 8 + 255) & ~size_t(255);
+}
 static size_t coarse_slot_bytes(int nc) {
-  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1, b = nc;
-  return (((size_t)n * (b + 1) * 8 + 255) & ~size_t(255)) + (((size_t)n * 8 + 255) & ~size_t(255));
+  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1;
+  return coarse_l_bytes(nc) + (((size_t)n * 8 + 255) & ~size_t(255));
 }
 
 }  // namespace stomsfem
@@ -113,7 +139,7 @@ extern "C" int stomsfem_coarse_workspace_size(const stomsfem_grid* grid, int32_t
   const int sms = device_sm_count();
   long long slots = (long long)(sms > 0 ? sms : 152) * 8;
   if (slots > S) slots = S;
-  if (slots < kCoarseWarps) slots = kCoarseWarps;
+  if (slots < kCoarseBlkWarps) slots = kCoarseBlkWarps;
   *bytes = coarse_slot_bytes(grid->nc) * (size_t)slots;
   return STOMSFEM_OK;
 }
@@ -132,18 +158,21 @@ extern "C" int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke
     return set_error(STOMSFEM_EINVAL, "mean, m2 and count must be given together");
   const size_t sb = coarse_slot_bytes(grid->nc);
   long long slots = (long long)(workspace_bytes / sb);
-  if (slots < kCoarseWarps)
+  if (slots < kCoarseBlkWarps)
     return set_error(STOMSFEM_ENOMEM, "coarse workspace %zu < %d slots of %zu", workspace_bytes,
-                     kCoarseWarps, sb);
-  long long blocks = slots / kCoarseWarps;
-  const long long need = ((long long)S + kCoarseWarps - 1) / kCoarseWarps;
+                     kCoarseBlkWarps, sb);
+  long long blocks = slots / kCoarseBlkWarps;
+  const long long need = ((long long)S + kCoarseBlkWarps - 1) / kCoarseBlkWarps;
   if (blocks > need) blocks = need;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = ring_bytes<double, 1>(grid->nc) * kCoarseWarps;
-  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-  coarse_kernel<<<(unsigned)blocks, kCoarseWarps * 32, smem, st>>>(
-      grid->nc, S, Ke, be, u, static_cast<unsigned char*>(workspace), sb);
+  const int nc = grid->nc;
+  const size_t smem = blk_smem_bytes<double>(16, nc, CoarseBlkGen::kRaw) * kCoarseBlkWarps;
+  const int rpl = (16 + nc + 31) / 32;
+  auto kern = rpl <= 1 ? coarse_blk_kernel<1> : rpl == 2 ? coarse_blk_kernel<2> : coarse_blk_kernel<3>;
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)blocks, kCoarseBlkWarps * 32, smem, st>>>(nc, S, Ke, be, u,
+                                                              static_cast<unsigned char*>(workspace), sb,
+                                                              coarse_l_bytes(nc));
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   if (mom) {
     const int nn = (grid->nc + 1) * (grid->nc + 1);
