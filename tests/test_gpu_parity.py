@@ -293,6 +293,35 @@ def test_fp32_forward_only_route(orc):
     assert rel_unit(K1, K2) <= TOL[api.FP32]
 
 
+@pytest.mark.parametrize("layout", ["all_zero", "none_zero", "mixed"])
+def test_fp32_split_launch_cell_lists(orc, layout):
+    """The FP32 form with an oversample array runs the cells without
+    oversampling and the others as two launches from device cell lists;
+    either list may be empty.  A workspace without room for the lists after
+    the slots falls back to one launch.  All agree with the oracle."""
+    nf, nc = 64, 4
+    r = np.random.default_rng(11)
+    a = np.exp(r.uniform(-1.5, 1.5, size=(3, nf, nf)))
+    ov = {"all_zero": np.zeros(nc * nc), "none_zero": r.integers(1, 4, size=nc * nc),
+          "mixed": r.integers(0, 3, size=nc * nc)}[layout].astype(np.int8)
+    Ko, bo = orc.upscale(nf, nc, 1.0, a, ov)
+    Kg, bg = gpu_upscale(nf, nc, 1.0, a, ov, precision=api.FP32)
+    assert rel_unit(Kg, Ko) <= TOL[api.FP32]
+    assert rel_unit(bg, bo) <= TOL[api.FP32]
+    # one block of slots exactly: no room for the cell lists, single launch
+    g = api.grid(nf, nc)
+    slot, _ = api.stomsfem_upscale_workspace_size(g, 3, api.FP32)
+    ws = torch.empty(8 * slot, dtype=torch.uint8, device=DEV)
+    at = torch.from_numpy(a).to(DEV)
+    Ke = torch.empty((3, nc * nc, 10), dtype=torch.float64, device=DEV)
+    be = torch.empty((3, nc * nc, 4), dtype=torch.float64, device=DEV)
+    api.stomsfem_upscale(g, at, Ke, be, oversample=torch.from_numpy(ov).to(DEV), max_oversample=3,
+                         precision=api.FP32, workspace=ws)
+    torch.cuda.synchronize()
+    assert rel_unit(Ke.cpu().numpy(), Ko) <= TOL[api.FP32]
+    assert rel_unit(be.cpu().numpy(), bo) <= TOL[api.FP32]
+
+
 def _assemble_residual(Ke, be, u, nc):
     """|| S u - b || / ||b|| for the coarse system assembled from K_e, b_e
     (written out here independently of both the library and the oracle)."""
