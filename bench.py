@@ -356,6 +356,60 @@ def bench_surrogate(api, dev, stream, samples=None, steps=3000):
     return res, 6 * 4 + 8
 
 
+def bench_ri(api, dev, stream, samples=None):
+    """Random-interpolation form (Sec. 3.1, Algorithms 1-2) on the 64^2 / 8^2
+    workload: offline collocation through the FP64 upscaler, online
+    interpolation of K_e and b_e for 10^5 fresh samples (6.4 M units), the
+    direct FP64 fallback armed (a given)."""
+    import torch
+    w = W.workload("ri_64")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    S = samples or w["samples"]
+    fam, _, nu, nfam, npts = api.stomsfem_ri_plan(g, fld, w["eps"], w["nu_max"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, _ = api.stomsfem_ri_build(g, fld, w["eps"], w["nu_max"], w["nodes"], stream=stream)
+    t_build = time.perf_counter() - t0
+    xi = torch.from_numpy(W.draw_xi(w["field"], S, w["seed"])).to(dev)
+    a = torch.empty((S, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xi, a)
+    Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+    be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=dev)
+    fb = torch.empty((S, nc * nc), dtype=torch.uint8, device=dev)
+    Kp = torch.empty_like(Ke)
+    bp = torch.empty_like(be)
+    wsr = torch.empty(api.stomsfem_ri_workspace_size(h, S), dtype=torch.uint8, device=dev)
+    _, rb = api.stomsfem_upscale_workspace_size(g, 0, api.FP64)
+    wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+    units = S * nc * nc
+    ms = _timed_call(stream, lambda: api.stomsfem_ri_upscale(h, g, xi, a, Ke, be, fb, workspace=wsr,
+                                                             stream=stream))
+    ms_plain = _timed_call(stream, lambda: api.stomsfem_upscale(g, a, Kp, bp, workspace=wsu, stream=stream))
+    # algorithmic FP32 flops: 14 multiply-adds per grid point of the unit's family
+    pts_cell = [int(np.prod(nu[c][nu[c] > 0] + 1)) for c in range(nc * nc)]
+    flops = 2.0 * 14 * S * sum(pts_cell)
+    peaks = _peaks()
+    res = {"workload": "ri_64", "eps": w["eps"], "nu_max": w["nu_max"],
+           "nodes": "legendre" if w["nodes"] == 1 else "chebyshev", "families": nfam,
+           "grid_points": int(npts), "grid_points_per_unit_mean": float(np.mean(pts_cell)),
+           "build_s": t_build, "units": units, "units_per_s": units / (ms / 1e3), "ms": ms,
+           "fp64_plain_units_per_s": units / (ms_plain / 1e3), "speedup_vs_fp64": ms_plain / ms,
+           "fallback_rate": float(fb.double().mean().item()),
+           "Ke_rel_vs_plain": float(((Ke - Kp).norm(dim=2) / Kp.norm(dim=2)).max().item()),
+           "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:2000].contiguous(), be[:2000].contiguous(),
+                                                Kp[:2000].contiguous(), bp[:2000].contiguous(), dev),
+           "fp32_tflops_whole_call": flops / (ms / 1e3) / 1e12,
+           "fp32_peak_tflops": alu_peak_tflops("fp32"),
+           "fp32_frac_whole_call": flops / (ms / 1e3) / 1e12 / alu_peak_tflops("fp32"),
+           "roofline_note": "FP32 ALU: 28 flops per grid point per unit over the whole call against "
+                            "the peak derived from unit counts; HBM moves 113 B per unit (K_e, b_e, "
+                            "flag) plus its share of xi, far below the ALU time"}
+    api.stomsfem_ri_destroy(h)
+    return res, 3 * 3 + 3  # (tiles, eval, fallback) x 3 timed calls + the FP64 comparison x 3
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,10 +425,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-forms", action="store_true",
-                    help="skip the reduced-basis and surrogate measurements")
+                    help="skip the reduced-basis, surrogate and interpolation measurements")
     ap.add_argument("--pod-samples", type=int, default=None, help="online POD samples (default 10^4)")
     ap.add_argument("--sg-samples", type=int, default=None, help="surrogate inference samples (default 10^5)")
     ap.add_argument("--sg-steps", type=int, default=3000, help="surrogate training steps")
+    ap.add_argument("--ri-samples", type=int, default=None, help="random-interpolation samples (default 10^5)")
     ap.add_argument("--fp32r-batch", type=int, default=64, help="samples per step of the FP32+refinement arm")
     args = ap.parse_args()
 
@@ -531,11 +586,13 @@ def main():
                "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)}
 
     extra = {}
-    launches_extra = 0
     if not args.no_extra_forms:
         extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)
         extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
-        launches_extra = n1 + n2
+        extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
+        # kernels of each form's own timed calls (outside the step's timed region)
+        for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3)):
+            extra[k]["gpu_launches_timed_calls"] = n
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -573,7 +630,7 @@ def main():
             "e2e": e2e,
             # per step: sampling, upscaling (FP32 form with oversampling: a
             # cell-list kernel and two upscale launches), coarse solve, moments, count
-            "gpu_launches": (7 if form == "fp32" and ov is not None else 5) * args.steps + launches_extra,
+            "gpu_launches": (7 if form == "fp32" and ov is not None else 5) * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -356,6 +356,63 @@ int stomsfem_surrogate_infer(stomsfem_surrogate* sg, const double* xi, const dou
                              double delta, double* Ke, double* be, uint8_t* fell_back,
                              void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Random interpolation of the local upscaled quantities (Sec. 3.1,
+ * Algorithms 1 and 2; accuracy: Thm. approx_S).  Cells without
+ * oversampling.  Per cell, bump i is an interpolated direction with degree
+ * nu_i >= 1 when its strength g_i = max over the closed cell of
+ * |d log a / d xi_i| (scale exp(-d^2/w^2) for the exponential field,
+ * |contrast_log gain| / 4 exp(-d^2/w^2) for the sigmoid one) makes
+ * 2 (g_i/2)^(nu+1) / (nu+1)! > eps for every smaller nu (nu capped at
+ * nu_max); other bumps are frozen at xi_i = 0.  Directions are ordered by
+ * degree, then by the bump's offset from the cell's south-west corner
+ * (y, then x); cells with equal (offset, degree) lists form one family and
+ * share one interpolant, built on the family's first cell.  The family's
+ * collocation grid is the tensor product of nu_i + 1 nodes per direction
+ * (last direction fastest): Chebyshev points of the first kind or
+ * Legendre zeros on [-1, 1].
+ * ------------------------------------------------------------------- */
+enum { STOMSFEM_RI_CHEBYSHEV = 0, STOMSFEM_RI_LEGENDRE = 1 };
+typedef struct stomsfem_ri stomsfem_ri; /* opaque, library-owned */
+
+/* The plan of stomsfem_ri_build without building it (host, no GPU).
+ * Outputs (host, any may be NULL): family [nc*nc]; var_ids [nc*nc][16]
+ * (bump index per direction in table order, -1 padded); nu [nc*nc][16]
+ * (0 padded); n_families; n_points (grid points over all families).
+ * EINVAL: bad arguments, nu_max outside [1, 8], a cell with more than 16
+ * directions, a family with more than 64 node slots or 2560 grid points. */
+int stomsfem_ri_plan(const stomsfem_grid* grid, const stomsfem_field* field, double eps, int32_t nu_max,
+                     int32_t* family, int32_t* var_ids, int32_t* nu, int32_t* n_families,
+                     int64_t* n_points);
+
+/* Offline stage (Alg. 1): for every grid point of every family one
+ * coefficient sample (the family's directions at the point's nodes, every
+ * other xi 0), the family's first cell upscaled by the FP64 path; the
+ * K_e (10) and b_e (4) entries are the interpolation data.  Allocates
+ * device memory, synchronises `stream`.  Errors as stomsfem_ri_plan, plus
+ * ENOMEM / ECUDA. */
+int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field* field, double eps, int32_t nu_max,
+                      int32_t nodes, stomsfem_ri** out, int32_t* n_families, stomsfem_stream_t stream);
+int stomsfem_ri_destroy(stomsfem_ri* ri);
+/* The FP64 interpolation data, host [n_points][14] (K_e packed, then b_e),
+ * families in order, each family's grid points last direction fastest.
+ * Synchronous. */
+int stomsfem_ri_values(const stomsfem_ri* ri, double* V_host, int64_t n_points);
+/* Scratch of stomsfem_ri_upscale for S samples. */
+int stomsfem_ri_workspace_size(const stomsfem_ri* ri, int32_t S, size_t* bytes);
+/* Online stage (Alg. 2) for S samples (device: xi [S][nbx*nby], a
+ * [S][nf][nf] or NULL).  Per (sample, cell) unit the tensor Lagrange
+ * interpolant of the 14 entries at the cell's local parameters (second
+ * barycentric form per direction, FP32 sum over the family's grid held in
+ * shared memory), written as FP64 to Ke [S][nc*nc][10], be [S][nc*nc][4].
+ * A unit with a local parameter outside [-1, 1] (or NaN) is upscaled
+ * directly by the FP64 path from `a` in the same call, fell_back = 1; with
+ * a == NULL it gets NaN entries and fell_back = 2.  Other units:
+ * fell_back = 0.  Errors: EINVAL, ENOMEM (workspace), ECUDA. */
+int stomsfem_ri_upscale(stomsfem_ri* ri, const double* xi, const double* a, int32_t S, double* Ke,
+                        double* be, uint8_t* fell_back, void* workspace, size_t workspace_bytes,
+                        stomsfem_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,14 @@ _SIG = {
     "stomsfem_surrogate_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_surrogate_infer": (ctypes.c_int, [_P, _P, _P, _I, ctypes.c_double, _P, _P, _P, _P, _SZ,
                                                 _P]),
+    "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
+                                        _P, _P, _P, _P, _P]),
+    "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
+                                         _I, ctypes.POINTER(_P), _P, _P]),
+    "stomsfem_ri_destroy": (ctypes.c_int, [_P]),
+    "stomsfem_ri_values": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "stomsfem_ri_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_ri_upscale": (ctypes.c_int, [_P, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 
 

@@ -314,3 +314,64 @@ def stomsfem_surrogate_infer(h, g: Grid, xi, a, Ke, be, fell_back, delta=0.02, w
         float(delta), _dev(Ke, torch.float64, (S, ncell, 10), "Ke"),
         _dev(be, torch.float64, (S, ncell, 4), "be"), _dev(fell_back, torch.uint8, (S, ncell), "fell_back"),
         _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
+RI_CHEBYSHEV, RI_LEGENDRE = 0, 1
+RI_MAX_DIM = 16
+
+
+def stomsfem_ri_plan(g: Grid, fld: Field, eps, nu_max=8):
+    """(family [ncell], var_ids [ncell][16], nu [ncell][16], n_families,
+    n_points) -- host."""
+    import numpy as np
+    ncell = g.nc * g.nc
+    fam = np.zeros(ncell, dtype=np.int32)
+    ids = np.zeros((ncell, RI_MAX_DIM), dtype=np.int32)
+    nu = np.zeros((ncell, RI_MAX_DIM), dtype=np.int32)
+    nfam = ctypes.c_int32()
+    npts = ctypes.c_int64()
+    L.check(L.lib().stomsfem_ri_plan(ctypes.byref(g), ctypes.byref(fld), float(eps), int(nu_max),
+                                     fam.ctypes.data_as(ctypes.c_void_p), ids.ctypes.data_as(ctypes.c_void_p),
+                                     nu.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nfam),
+                                     ctypes.byref(npts)))
+    return fam, ids, nu, nfam.value, npts.value
+
+
+def stomsfem_ri_build(g: Grid, fld: Field, eps, nu_max=8, nodes=RI_CHEBYSHEV, stream=None):
+    h = ctypes.c_void_p()
+    nfam = ctypes.c_int32()
+    L.check(L.lib().stomsfem_ri_build(ctypes.byref(g), ctypes.byref(fld), float(eps), int(nu_max), int(nodes),
+                                      ctypes.byref(h), ctypes.byref(nfam), _stream(stream)))
+    return h, nfam.value
+
+
+def stomsfem_ri_destroy(h):
+    L.check(L.lib().stomsfem_ri_destroy(h))
+
+
+def stomsfem_ri_values(h, n_points):
+    import numpy as np
+    V = np.zeros((int(n_points), 14))
+    L.check(L.lib().stomsfem_ri_values(h, V.ctypes.data_as(ctypes.c_void_p), int(n_points)))
+    return V
+
+
+def stomsfem_ri_workspace_size(h, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_ri_workspace_size(h, int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_ri_upscale(h, g: Grid, xi, a, Ke, be, fell_back, workspace=None, stream=None):
+    """a may be None (units outside the collocation box then get NaN and
+    fell_back = 2)."""
+    S = xi.shape[0]
+    ncell = g.nc * g.nc
+    if workspace is None:
+        workspace = torch.empty(stomsfem_ri_workspace_size(h, S), dtype=torch.uint8, device=xi.device)
+    L.check(L.lib().stomsfem_ri_upscale(
+        h, _dev(xi, torch.float64, None, "xi"),
+        _dev(a, torch.float64, (S, g.nf, g.nf), "a") if a is not None else None, S,
+        _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(fell_back, torch.uint8, (S, ncell), "fell_back"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))

@@ -4,7 +4,7 @@ This module only draws random numbers and states sizes; it holds none of
 the method's arithmetic, so both the CUDA path and the CPU oracle take
 their inputs from here.
 
-Five workloads, sized like the paper's experiments (H/h = 32 as in the
+Six workloads, sized like the paper's experiments (H/h = 32 as in the
 short-correlation example, channel-like high-contrast media as in the
 high-contrast example):
 
@@ -18,6 +18,9 @@ high-contrast example):
 * ``pod_64``       msfem_64 grid; 200 training samples, 10^4 online samples.
 * ``surrogate_64`` msfem_64 grid; 1563 training samples (10^5 cell pairs),
                     10^5 fresh samples for inference.
+* ``ri_64``        msfem_64 grid; random interpolation at eps = 1e-3 (degree
+                    cap 8, Legendre nodes for the uniform xi), 10^5 fresh
+                    samples online.
 * ``contrast_2048`` 2048x2048 fine, 64x64 coarse (H/h = 32), 32x32 bumps of
                     width 1.5H, a = exp(ln(1e4) sigmoid(8 z)), xi ~ N(0,1),
                     2x10^4 samples in batches of 64..4096.
@@ -48,6 +51,10 @@ WORKLOADS = {
                          train_seed=4, oversample=None,
                          field=dict(kind=FIELD_EXP, nbx=4, nby=4, width=0.1, scale=1.0,
                                     contrast_log=0.0, gain=1.0), dist="uniform"),
+    "ri_64": dict(nf=64, nc=8, f=1.0, samples=100000, seed=41, eps=1e-3, nu_max=8, nodes=1,
+                  oversample=None,
+                  field=dict(kind=FIELD_EXP, nbx=4, nby=4, width=0.1, scale=1.0,
+                             contrast_log=0.0, gain=1.0), dist="uniform"),
     "contrast_2048": dict(nf=2048, nc=64, f=1.0, samples=20000, seed=5, oversample=None,
                           batches=dict(lo=64, hi=4096, seed=50),
                           field=dict(kind=FIELD_EXP_SIGMOID, nbx=32, nby=32,

@@ -1,0 +1,48 @@
+"""Random-interpolation set-up that runs on the host (no GPU): the library's
+plan (directions, degrees, families) against the oracle's own."""
+import numpy as np
+import pytest
+
+from paper_1607_00693_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    from oracle import ri
+    oracle.build()
+    return oracle, ri
+
+
+@pytest.mark.parametrize("name,eps,nu_max", [("msfem_64", 1e-3, 8), ("msfem_64", 3e-3, 8),
+                                             ("msfem_64", 1e-2, 3), ("upscale_1024", 1e-1, 4)])
+def test_library_plan_matches_oracle(orc, name, eps, nu_max):
+    from paper_1607_00693_gb300.build import build_library
+    from paper_1607_00693_gb300 import api
+    _, ri = orc
+    build_library()
+    w = W.workload(name)
+    g = api.grid(w["nf"], w["nc"], w["f"])
+    fam, ids, nu, nfam, npts = api.stomsfem_ri_plan(g, api.field_from_dict(w["field"]), eps, nu_max)
+    fo, keys, rep, dims = ri.families(w["nf"], w["nc"], w["field"], eps, nu_max)
+    np.testing.assert_array_equal(fam, fo)
+    assert nfam == len(keys)
+    assert npts == sum(int(np.prod([k[2] + 1 for k in key])) for key in keys)
+    for c, d in enumerate(dims):
+        assert list(ids[c, :len(d)]) == [v for (_, _, _, v) in d] and np.all(ids[c, len(d):] == -1)
+        assert list(nu[c, :len(d)]) == [n for (_, _, n, _) in d] and np.all(nu[c, len(d):] == 0)
+
+
+def test_library_plan_rejects_oversized_grids(orc):
+    from paper_1607_00693_gb300.build import build_library
+    from paper_1607_00693_gb300 import api, _lib
+    build_library()
+    w = W.workload("contrast_2048")
+    g = api.grid(w["nf"], w["nc"], w["f"])
+    with pytest.raises(_lib.StomsfemError):
+        api.stomsfem_ri_plan(g, api.field_from_dict(w["field"]), 1e-3, 8)
+    w = W.workload("msfem_64")
+    g = api.grid(w["nf"], w["nc"], w["f"])
+    for bad in (dict(eps=0.0, nu_max=8), dict(eps=1e-3, nu_max=0), dict(eps=1e-3, nu_max=9)):
+        with pytest.raises(_lib.StomsfemError):
+            api.stomsfem_ri_plan(g, api.field_from_dict(w["field"]), bad["eps"], bad["nu_max"])
