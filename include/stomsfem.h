@@ -380,7 +380,7 @@ typedef struct stomsfem_ri stomsfem_ri; /* opaque, library-owned */
  * (bump index per direction in table order, -1 padded); nu [nc*nc][16]
  * (0 padded); n_families; n_points (grid points over all families).
  * EINVAL: bad arguments, nu_max outside [1, 8], a cell with more than 16
- * directions, a family with more than 64 node slots or 2560 grid points. */
+ * directions, a family with more than 64 node slots or 2048 grid points. */
 int stomsfem_ri_plan(const stomsfem_grid* grid, const stomsfem_field* field, double eps, int32_t nu_max,
                      int32_t* family, int32_t* var_ids, int32_t* nu, int32_t* n_families,
                      int64_t* n_points);
@@ -404,7 +404,7 @@ int stomsfem_ri_workspace_size(const stomsfem_ri* ri, int32_t S, size_t* bytes);
  * [S][nf][nf] or NULL).  Per (sample, cell) unit the tensor Lagrange
  * interpolant of the 14 entries at the cell's local parameters (second
  * barycentric form per direction, FP32 sum over the family's grid held in
- * shared memory), written as FP64 to Ke [S][nc*nc][10], be [S][nc*nc][4].
+ * shared memory, two units per thread), written as FP64 to Ke [S][nc*nc][10], be [S][nc*nc][4].
  * A unit with a local parameter outside [-1, 1] (or NaN) is upscaled
  * directly by the FP64 path from `a` in the same call, fell_back = 1; with
  * a == NULL it gets NaN entries and fell_back = 2.  Other units:

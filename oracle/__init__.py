@@ -20,6 +20,8 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
                         energy inner product (Eq. KLphi) and the Galerkin
                         reduced system (Eqs. localRB, localRBsystem).
 * ``mlp``           -- FP64 MLP forward/backward/Adam for the surrogate.
+* ``ri``            -- random interpolation of K_e and b_e in the local
+                        parameters (Sec. 3.1, Algorithms 1-2).
 
 The C part is compiled on first use (gcc, -O2, OpenMP) into
 ``oracle/_build/liborc.so``.

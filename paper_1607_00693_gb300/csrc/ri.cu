@@ -18,14 +18,17 @@ constexpr int kRiMaxDim = 16;         // interpolated directions per cell
 constexpr int kRiMaxNu = 8;           // degree per direction
 constexpr int kRiMaxNodes = kRiMaxNu + 1;
 constexpr int kRiMaxSlots = 64;       // sum over directions of (nu + 1)
-constexpr int kRiThreads = 256;       // units per CTA (one per thread)
-constexpr long long kRiMaxPoints = 2560;  // one family's table in shared memory, 64 B per point
+constexpr int kRiUnits = 256;         // units per CTA (one tile)
+constexpr int kRiThreads = 128;       // two units per thread
+constexpr int kRiMaxBlock = 16;       // grid points of the inner block (weights kept per unit)
+constexpr long long kRiMaxPoints = 2048;  // one family's table in shared memory, 64 B per point
 
 struct RiFam {
   int ndim, npts, ncell, cell0;  // directions, grid points, cells, first entry in fam_cells
   long long pt0;                 // first point in the concatenated tables
   int radix[kRiMaxDim];          // nu + 1 per direction
   int slot0[kRiMaxDim];          // first node slot of each direction
+  int din, nb, nslot_out;        // inner directions (the last din), their grid points, outer node slots
 };
 
 struct RiPlan {
@@ -130,6 +133,14 @@ static int ri_make_plan(const stomsfem_grid* g, const stomsfem_field* fd, double
         return set_error(STOMSFEM_EINVAL, "family of cell %d has %lld grid points > %lld (raise eps or lower nu_max)",
                          cell, n, kRiMaxPoints);
       F.npts = (int)n;
+      // inner block: the longest run of last directions with <= kRiMaxBlock points
+      F.din = 0;
+      F.nb = 1;
+      while (F.din < F.ndim && F.nb * F.radix[F.ndim - 1 - F.din] <= kRiMaxBlock) {
+        F.nb *= F.radix[F.ndim - 1 - F.din];
+        ++F.din;
+      }
+      F.nslot_out = F.ndim - F.din > 0 ? F.slot0[F.ndim - F.din - 1] + F.radix[F.ndim - F.din - 1] : 0;
       P.F.push_back(F);
       P.rep.push_back(cell);
       members.emplace_back();
@@ -211,13 +222,13 @@ __global__ void ri_gather_kernel(int n, const int32_t* __restrict__ list, const 
   }
 }
 
-// First tile of every family for S samples (tiles of kRiThreads units).
+// First tile of every family for S samples (tiles of kRiUnits units).
 __global__ void ri_tiles_kernel(int nfam, const RiFam* __restrict__ fam, int S, int* __restrict__ tile0) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int t = 0;
   for (int f = 0; f < nfam; ++f) {
     tile0[f] = t;
-    t += (int)(((long long)S * fam[f].ncell + kRiThreads - 1) / kRiThreads);
+    t += (int)(((long long)S * fam[f].ncell + kRiUnits - 1) / kRiUnits);
   }
   tile0[nfam] = t;
 }
@@ -225,6 +236,7 @@ __global__ void ri_tiles_kernel(int nfam, const RiFam* __restrict__ fam, int S, 
 struct RiEvalArgs {
   const double* xi;
   int K, S, ncell, nfam;
+  int max_pts, max_nb, max_slot;  // shared-memory layout of the launch
   const RiFam* fam;
   const int* tile0;      // [nfam + 1]
   const float* x;        // [nfam][kRiMaxSlots] nodes
@@ -239,10 +251,106 @@ struct RiEvalArgs {
   int32_t* count;
 };
 
+// 1-d Lagrange values of one direction at t in the second (true)
+// barycentric form; a node hit exactly gives the unit vector.
+template <int N>
+__device__ __forceinline__ void ri_values(const float* sx, const float* sw, float t, float (&l)[N]) {
+  int hit = -1;
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float d = t - sx[j];
+    if (d == 0.f) hit = j;
+    l[j] = __fdividef(sw[j], d);
+    sum += l[j];
+  }
+  const float inv = 1.f / sum;
+#pragma unroll
+  for (int j = 0; j < N; ++j) l[j] = (hit >= 0) ? (j == hit ? 1.f : 0.f) : l[j] * inv;
+}
+
+// Direction of radix n at t: an inner direction multiplies the unit's
+// block weights sW[0..len) into sW[0..n len) (this direction slowest), an
+// outer one stores its values at its node slots of sL.
+__device__ __forceinline__ void ri_direction(bool inner, int n, const float* sx, const float* sw, float t,
+                                             float* sW, float* sL, int slot0, int q, int len) {
+  switch (n) {
+#define RI_DIR(N)                                                                            \
+  case N: {                                                                                  \
+    float l[N];                                                                              \
+    ri_values<N>(sx, sw, t, l);                                                              \
+    if (inner) {                                                                             \
+      _Pragma("unroll") for (int j = N - 1; j >= 1; --j) for (int i = 0; i < len; ++i)       \
+          sW[(j * len + i) * kRiUnits + q] = l[j] * sW[i * kRiUnits + q];                     \
+      for (int i = 0; i < len; ++i) sW[i * kRiUnits + q] *= l[0];                            \
+    } else {                                                                                 \
+      _Pragma("unroll") for (int j = 0; j < N; ++j) sL[(slot0 + j) * kRiUnits + q] = l[j];   \
+    }                                                                                        \
+    break;                                                                                   \
+  }
+    RI_DIR(2) RI_DIR(3) RI_DIR(4) RI_DIR(5) RI_DIR(6) RI_DIR(7) RI_DIR(8) RI_DIR(9)
+#undef RI_DIR
+    default:
+      break;
+  }
+}
+
+// Sum over the family's grid for the thread's two units: outer index o
+// (the product of the outer directions' 1-d values, at the node slots
+// sO[o][k] of sL) times the NB inner points (block weights held in
+// registers), table rows broadcast from shared memory.
+template <int NB>
+__device__ __forceinline__ void ri_accumulate(const float4* __restrict__ sV, const float* __restrict__ sW,
+                                              const float* __restrict__ sL, const uint8_t* __restrict__ sO,
+                                              const RiFam& F, int tid,
+                                              float (&acc0)[14], float (&acc1)[14]) {
+  float w0[NB], w1[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    w0[b] = sW[b * kRiUnits + tid];
+    w1[b] = sW[b * kRiUnits + tid + kRiThreads];
+  }
+#pragma unroll
+  for (int q = 0; q < 14; ++q) acc0[q] = acc1[q] = 0.f;
+  const int dout = F.ndim - F.din;
+  const int nout = F.npts / NB;
+  const float4* v = sV;
+  const uint8_t* so = sO;
+  for (int o = 0; o < nout; ++o) {
+    float b0 = 1.f, b1 = 1.f;
+    for (int k = 0; k < dout; ++k) {
+      const int sl = so[k] * kRiUnits + tid;
+      b0 *= sL[sl];
+      b1 *= sL[sl + kRiThreads];
+    }
+    so += dout;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const float wa = b0 * w0[b], wb = b1 * w1[b];
+      const float4 v0 = v[4 * b], v1 = v[4 * b + 1], v2 = v[4 * b + 2], v3 = v[4 * b + 3];
+      const float e[14] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x, v3.y};
+#pragma unroll
+      for (int q = 0; q < 14; ++q) {
+        acc0[q] = fmaf(wa, e[q], acc0[q]);
+        acc1[q] = fmaf(wb, e[q], acc1[q]);
+      }
+    }
+    v += 4 * NB;
+  }
+}
+
+// One tile of 256 units of one family; thread t takes units t and t + 128.
+// Shared memory: the family's table [npts][16]; per unit (column q) the
+// inner block weights sW[b][q] (b < nb: products over the last din
+// directions) and the outer directions' 1-d values sL[slot][q]; the outer
+// node slots per outer index sO[o][k] (uniform over the tile).
 __global__ void __launch_bounds__(kRiThreads) ri_eval_kernel(RiEvalArgs A) {
   extern __shared__ float4 sV[];
   __shared__ RiFam F;
   __shared__ float sx[kRiMaxSlots], sw[kRiMaxSlots];
+  float* sW = reinterpret_cast<float*>(sV + (size_t)A.max_pts * 4);
+  float* sL = sW + (size_t)A.max_nb * kRiUnits;
+  uint8_t* sO = reinterpret_cast<uint8_t*>(sL + (size_t)A.max_slot * kRiUnits);
   const int tid = threadIdx.x;
   const int tile = blockIdx.x;
   int lo = 0, hi = A.nfam;  // tile0[lo] <= tile < tile0[hi]
@@ -262,110 +370,83 @@ __global__ void __launch_bounds__(kRiThreads) ri_eval_kernel(RiEvalArgs A) {
     const float4* src = A.tab + F.pt0 * 4;
     for (int i = tid; i < F.npts * 4; i += kRiThreads) sV[i] = src[i];
   }
-  const long long r = (long long)(tile - A.tile0[f]) * kRiThreads + tid;
-  const bool valid = r < (long long)A.S * F.ncell;
-  long long u = 0;
-  bool out = false;
-  float lw[kRiMaxSlots];
-  if (valid) {
+  const int D = F.ndim, dout = F.ndim - F.din;
+  // node slots of the outer directions per outer index (last outer direction fastest)
+  for (int o = tid; o < F.npts / F.nb; o += kRiThreads) {
+    int rem = o;
+    for (int k = dout - 1; k >= 0; --k) {
+      sO[o * dout + k] = (uint8_t)(F.slot0[k] + rem % F.radix[k]);
+      rem /= F.radix[k];
+    }
+  }
+  long long u[2];
+  bool run[2], out[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = tid + h * kRiThreads;
+    const long long r = (long long)(tile - A.tile0[f]) * kRiUnits + q;
+    run[h] = r < (long long)A.S * F.ncell;
+    out[h] = false;
+    u[h] = 0;
+    if (!run[h]) continue;
     const int s = (int)(r / F.ncell), pos = (int)(r % F.ncell);
     const int cell = A.fam_cells[F.cell0 + pos];
-    u = (long long)s * A.ncell + cell;
-    for (int k = 0; k < F.ndim; ++k) {
-      const double t = A.xi[(size_t)s * A.K + A.cell_var[cell * kRiMaxDim + k]];
-      if (!(fabs(t) <= 1.0)) out = true;
-      const float tf = (float)t;
-      const int n = F.radix[k], s0 = F.slot0[k];
-      // second (true) barycentric form; an exact node gives the unit vector
-      int hit = -1;
-      float sum = 0.f;
-      for (int j = 0; j < n; ++j) {
-        const float d = tf - sx[s0 + j];
-        if (d == 0.f) hit = j;
-        const float q = sw[s0 + j] / d;
-        lw[s0 + j] = q;
-        sum += q;
-      }
-      if (hit >= 0) {
-        for (int j = 0; j < n; ++j) lw[s0 + j] = (j == hit) ? 1.f : 0.f;
-      } else {
-        const float inv = 1.f / sum;
-        for (int j = 0; j < n; ++j) lw[s0 + j] *= inv;
-      }
+    u[h] = (long long)s * A.ncell + cell;
+    const double* xs = A.xi + (size_t)s * A.K;
+    const int* vars = A.cell_var + cell * kRiMaxDim;
+    // inner block weights by Kronecker products, last direction first;
+    // then the outer directions' 1-d values
+    sW[q] = 1.f;
+    int len = 1;
+    for (int k = D - 1; k >= 0; --k) {
+      const double t = xs[vars[k]];
+      if (!(fabs(t) <= 1.0)) out[h] = true;
+      const int n = F.radix[k];
+      ri_direction(k >= dout, n, sx + F.slot0[k], sw + F.slot0[k], (float)t, sW, sL, F.slot0[k], q, len);
+      if (k >= dout) len *= n;
     }
   }
   __syncthreads();
-  if (!valid) return;
-  if (out) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!run[h] || !out[h]) continue;
     if (A.list) {
-      A.flag[u] = 1;
-      A.list[atomicAdd(A.count, 1)] = (int32_t)u;
+      A.flag[u[h]] = 1;
+      A.list[atomicAdd(A.count, 1)] = (int32_t)u[h];
     } else {
       const double nanv = __longlong_as_double(0x7ff8000000000000ll);
-      A.flag[u] = 2;
-      for (int q = 0; q < 10; ++q) A.Ke[u * 10 + q] = nanv;
-      for (int l = 0; l < 4; ++l) A.be[u * 4 + l] = nanv;
+      A.flag[u[h]] = 2;
+      for (int q = 0; q < 10; ++q) A.Ke[u[h] * 10 + q] = nanv;
+      for (int l = 0; l < 4; ++l) A.be[u[h] * 4 + l] = nanv;
     }
-    return;
   }
-  A.flag[u] = 0;
-  // sum over the tensor grid, last direction fastest: the weight of a
-  // point is the product of its 1-d Lagrange values (outer directions kept
-  // as prefix products, updated on every carry)
-  const int D = F.ndim;
-  const int nl = D > 0 ? F.radix[D - 1] : 1;
-  float lL[kRiMaxNodes];
-#pragma unroll
-  for (int j = 0; j < kRiMaxNodes; ++j) lL[j] = (D > 0) ? ((j < nl) ? lw[F.slot0[D - 1] + j] : 0.f) : (j == 0 ? 1.f : 0.f);
-  int idx[kRiMaxDim];
-  float pre[kRiMaxDim];
-  pre[0] = 1.f;
-  for (int k = 0; k + 1 < D; ++k) {
-    idx[k] = 0;
-    pre[k + 1] = pre[k] * lw[F.slot0[k]];
+  if (!run[0]) return;  // the second unit of a thread runs only with the first
+  float acc0[14], acc1[14];
+  switch (F.nb) {
+#define RI_NB(N) \
+  case N:        \
+    ri_accumulate<N>(sV, sW, sL, sO, F, tid, acc0, acc1); \
+    break;
+    RI_NB(1) RI_NB(2) RI_NB(3) RI_NB(4) RI_NB(5) RI_NB(6) RI_NB(7) RI_NB(8)
+    RI_NB(9) RI_NB(10) RI_NB(12) RI_NB(14) RI_NB(15) RI_NB(16)
+#undef RI_NB
+    default:
+      for (int q = 0; q < 14; ++q) acc0[q] = acc1[q] = __int_as_float(0x7fc00000);  // unreachable sizes
   }
-  const int last = D > 1 ? D - 1 : 0;
-  const int nout = F.npts / nl;
-  float acc[14];
+  if (!out[0]) {
+    A.flag[u[0]] = 0;
 #pragma unroll
-  for (int q = 0; q < 14; ++q) acc[q] = 0.f;
-  const float4* v = sV;
-  for (int o = 0; o < nout; ++o) {
-    const float base = pre[last];
+    for (int q = 0; q < 10; ++q) A.Ke[u[0] * 10 + q] = (double)acc0[q];
 #pragma unroll
-    for (int j = 0; j < kRiMaxNodes; ++j) {
-      if (j < nl) {
-        const float wt = base * lL[j];
-        const float4 v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3];
-        acc[0] = fmaf(wt, v0.x, acc[0]);
-        acc[1] = fmaf(wt, v0.y, acc[1]);
-        acc[2] = fmaf(wt, v0.z, acc[2]);
-        acc[3] = fmaf(wt, v0.w, acc[3]);
-        acc[4] = fmaf(wt, v1.x, acc[4]);
-        acc[5] = fmaf(wt, v1.y, acc[5]);
-        acc[6] = fmaf(wt, v1.z, acc[6]);
-        acc[7] = fmaf(wt, v1.w, acc[7]);
-        acc[8] = fmaf(wt, v2.x, acc[8]);
-        acc[9] = fmaf(wt, v2.y, acc[9]);
-        acc[10] = fmaf(wt, v2.z, acc[10]);
-        acc[11] = fmaf(wt, v2.w, acc[11]);
-        acc[12] = fmaf(wt, v3.x, acc[12]);
-        acc[13] = fmaf(wt, v3.y, acc[13]);
-        v += 4;
-      }
-    }
-    int k = D - 2;
-    while (k >= 0) {
-      if (++idx[k] < F.radix[k]) break;
-      idx[k] = 0;
-      --k;
-    }
-    for (int kk = k < 0 ? 0 : k; kk + 1 < D; ++kk) pre[kk + 1] = pre[kk] * lw[F.slot0[kk] + idx[kk]];
+    for (int l = 0; l < 4; ++l) A.be[u[0] * 4 + l] = (double)acc0[10 + l];
   }
+  if (run[1] && !out[1]) {
+    A.flag[u[1]] = 0;
 #pragma unroll
-  for (int q = 0; q < 10; ++q) A.Ke[u * 10 + q] = (double)acc[q];
+    for (int q = 0; q < 10; ++q) A.Ke[u[1] * 10 + q] = (double)acc1[q];
 #pragma unroll
-  for (int l = 0; l < 4; ++l) A.be[u * 4 + l] = (double)acc[10 + l];
+    for (int l = 0; l < 4; ++l) A.be[u[1] * 4 + l] = (double)acc1[10 + l];
+  }
 }
 
 }  // namespace stomsfem
@@ -580,10 +661,16 @@ extern "C" int stomsfem_ri_upscale(stomsfem_ri* ri, const double* xi, const doub
   int32_t* list = reinterpret_cast<int32_t*>(ws + o);
   o += 256 * (((size_t)S * P.ncell * 4 + 255) / 256);
   long long tiles = 0;
-  for (int f = 0; f < P.nfam; ++f) tiles += ((long long)S * P.F[f].ncell + kRiThreads - 1) / kRiThreads;
+  for (int f = 0; f < P.nfam; ++f) tiles += ((long long)S * P.F[f].ncell + kRiUnits - 1) / kRiUnits;
   if (tiles > 0x7fffffffll) return set_error(STOMSFEM_EINVAL, "S too large for one call");
-  long long maxpts = 0;
-  for (int f = 0; f < P.nfam; ++f) maxpts = std::max<long long>(maxpts, P.F[f].npts);
+  int maxpts = 0, maxnb = 1, maxslot = 0;
+  size_t maxouter = 0;
+  for (int f = 0; f < P.nfam; ++f) {
+    maxpts = std::max(maxpts, P.F[f].npts);
+    maxnb = std::max(maxnb, P.F[f].nb);
+    maxslot = std::max(maxslot, P.F[f].nslot_out);
+    maxouter = std::max(maxouter, (size_t)(P.F[f].npts / P.F[f].nb) * (P.F[f].ndim - P.F[f].din));
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(count, 0, 4, st));
   ri_tiles_kernel<<<1, 32, 0, st>>>(P.nfam, ri->fam_d, S, tile0);
@@ -594,6 +681,9 @@ extern "C" int stomsfem_ri_upscale(stomsfem_ri* ri, const double* xi, const doub
   A.S = S;
   A.ncell = P.ncell;
   A.nfam = P.nfam;
+  A.max_pts = maxpts;
+  A.max_nb = maxnb;
+  A.max_slot = maxslot;
   A.fam = ri->fam_d;
   A.tile0 = tile0;
   A.x = ri->x_d;
@@ -606,7 +696,8 @@ extern "C" int stomsfem_ri_upscale(stomsfem_ri* ri, const double* xi, const doub
   A.flag = fell_back;
   A.list = a ? list : nullptr;
   A.count = count;
-  const size_t smem = (size_t)maxpts * 64;
+  const size_t smem = (size_t)maxpts * 64 + (size_t)(maxnb + maxslot) * kRiUnits * 4 + ((maxouter + 15) & ~(size_t)15);
+  if (smem > 227 * 1024) return set_error(STOMSFEM_EINVAL, "RI tables need %zu B of shared memory", smem);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(ri_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ri_eval_kernel<<<(unsigned)tiles, kRiThreads, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());

@@ -168,7 +168,7 @@ def test_full_size_sampled_and_coarse_error(setup):
     oracle, ri, w, g, fld, models = setup
     h, m = models[api.RI_LEGENDRE]
     S = 100000
-    xi = W.draw_xi(w["field"], S, w["seed"])
+    xi = W.draw_xi(w["field"], S, W.workload("ri_64")["seed"])
     xt = torch.tensor(xi, device=DEV)
     Ke = torch.empty((S, 64, 10), dtype=torch.float64, device=DEV)
     be = torch.empty((S, 64, 4), dtype=torch.float64, device=DEV)
@@ -190,3 +190,25 @@ def test_full_size_sampled_and_coarse_error(setup):
     u0 = oracle.coarse_solve(8, K0.cpu().numpy(), b0.cpu().numpy())
     u1 = oracle.coarse_solve(8, Ke[:n].cpu().numpy(), be[:n].cpu().numpy())
     assert np.linalg.norm(u1 - u0) / np.linalg.norm(u0) < 1e-4
+
+
+def test_many_directions_low_degree(setup):
+    """eps = 1e-4 with degrees capped at 2: up to 8 directions and 1296 grid
+    points per family, so several outer directions around the inner block."""
+    oracle, ri, w, g, fld, _ = setup
+    h, nfam = api.stomsfem_ri_build(g, fld, 1e-4, 2, api.RI_CHEBYSHEV)
+    try:
+        m = ri.build(w["nf"], w["nc"], w["f"], w["field"], 1e-4, 2, ri.CHEBYSHEV)
+        assert nfam == len(m["keys"]) and max(len(d) for d in m["dims"]) == 8
+        Vo = np.concatenate(m["V"])
+        np.testing.assert_allclose(api.stomsfem_ri_values(h, len(Vo)), Vo, rtol=1e-10, atol=1e-13)
+        xi = W.draw_xi(w["field"], 3, 99)
+        Ke, be, fb = _run(g, h, torch.tensor(xi, device=DEV))
+        assert (fb == 0).all()
+        for s in range(3):
+            for c in range(64):
+                Ko, bo = ri.evaluate(m, xi[s], c)
+                assert _unit_close(Ke[s, c], Ko).all(), (s, c)
+                assert _unit_close(be[s, c], bo).all(), (s, c)
+    finally:
+        api.stomsfem_ri_destroy(h)
