@@ -13,6 +13,10 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
                         fine mesh, oversampling recombination (Remark in
                         Sec. 2.2), K_e and b_e (Eq. stiffness_local); C code.
 * ``coarse_solve``  -- coarse assembly and solve (Eq. upscaleSUF); C code.
+* ``upscale_pg``, ``coarse_solve_pg`` -- the Petrov-Galerkin form (Eq.
+                        stiffness_local_petrov: bilinear test functions,
+                        deterministic load; non-symmetric coarse system by
+                        banded LU); C code.
 * ``fine_fem``      -- standard Q1 FEM on the fine grid; C code.
 * ``mc_moments``    -- Monte Carlo mean and variance (Eq. MCestimate),
                         two-pass.
@@ -66,6 +70,9 @@ def _L():
         lib.orc_coarse_solve.argtypes = [i, p, p, i, p]
         lib.orc_fine_fem.argtypes = [i, d, p, p]
         lib.orc_band_solve_dense.argtypes = [i, i, p, p]
+        lib.orc_cell_pg.argtypes = [i, i, d, p, i, i, i, p, p]
+        lib.orc_upscale_pg.argtypes = [i, i, d, p, p, i, p, p, p, i]
+        lib.orc_coarse_solve_pg.argtypes = [i, p, p, i, p]
         lib.orc_patch_bounds.argtypes = [i, i, i, i, i, p, p, p, p]
         _lib = lib
     return _lib
@@ -155,6 +162,43 @@ def upscale(nf, nc, f, a, oversample=None, want_phi=False, nthreads=0):
     if rc != 0:
         raise ValueError("orc_upscale failed: %d (first bad unit %d)" % (rc, int(np.argmax(st != 0))))
     return (Ke, be, phi) if want_phi else (Ke, be)
+
+
+def cell_pg(nf, nc, f, a2d, cx, cy, o=0):
+    """One unit in the Petrov-Galerkin form: (Kpg[4][4] (row trial l,
+    column test l'), bpg[4])."""
+    a2d = np.ascontiguousarray(a2d, dtype=np.float64)
+    K = np.empty(16)
+    b = np.empty(4)
+    rc = _L().orc_cell_pg(nf, nc, f, _ptr(a2d), cx, cy, o, _ptr(K), _ptr(b))
+    if rc != 0:
+        raise ValueError("orc_cell_pg failed: %d" % rc)
+    return K.reshape(4, 4), b
+
+
+def upscale_pg(nf, nc, f, a, oversample=None, nthreads=0):
+    """Kpg[S][nc*nc][16] (row-major 4x4, row trial, column test), bpg[S][nc*nc][4]."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    S = a.shape[0]
+    K = np.empty((S, nc * nc, 16))
+    b = np.empty((S, nc * nc, 4))
+    st = np.zeros(S * nc * nc, dtype=np.int32)
+    ov = None if oversample is None else np.ascontiguousarray(oversample, dtype=np.int8)
+    rc = _L().orc_upscale_pg(nf, nc, f, _ptr(a), _ptr(ov), S, _ptr(K), _ptr(b), _ptr(st), nthreads)
+    if rc != 0:
+        raise ValueError("orc_upscale_pg failed: %d" % rc)
+    return K, b
+
+
+def coarse_solve_pg(nc, Kpg, bpg):
+    Kpg = np.ascontiguousarray(Kpg, dtype=np.float64)
+    bpg = np.ascontiguousarray(bpg, dtype=np.float64)
+    S = Kpg.shape[0]
+    u = np.empty((S, (nc + 1) ** 2))
+    rc = _L().orc_coarse_solve_pg(nc, _ptr(Kpg), _ptr(bpg), S, _ptr(u))
+    if rc != 0:
+        raise ValueError("orc_coarse_solve_pg failed: %d" % rc)
+    return u
 
 
 def coarse_solve(nc, Ke, be):

@@ -476,3 +476,144 @@ int orc_band_solve_dense(int n, int bw, const double* A, double* b) {
   free(band);
   return rc == 0 ? 0 : -4;
 }
+
+/* ---------------------------------------------------------------- */
+/* Petrov-Galerkin MsFEM (Eq. stiffness_local_petrov): trial functions */
+/* the multiscale basis phi_l (with the oversampling recombination),  */
+/* test functions the bilinear nodal functions q_l' of the coarse      */
+/* cell:  S_ll' = int_cell a grad phi_l . grad q_l',                   */
+/*        b_l   = int_cell f q_l = f H^2 / 4.                          */
+/* Kpg[16] row-major (row l = trial, column l' = test).  q_l' is       */
+/* bilinear on every fine element of the cell, so its nodal values     */
+/* give the integral exactly: sum_e a_e phi_e^T K_ref q_e.             */
+/* ---------------------------------------------------------------- */
+int orc_cell_pg(int nf, int nc, double f, const double* a, int cx, int cy, int o,
+                double* Kpg, double* bpg) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || o < 0) return -1000;
+  const int rho = nf / nc;
+  const int CN = (rho + 1) * (rho + 1);
+  double Ke[10], be[4];
+  double* ph = (double*)malloc(sizeof(double) * 4 * CN);
+  if (!ph) return -1001;
+  const int rc = orc_cell(nf, nc, f, a, cx, cy, o, Ke, be, ph, NULL);
+  if (rc != 0) { free(ph); return rc; }
+  double S[4][4] = {{0}};
+  for (int ey = 0; ey < rho; ++ey)
+    for (int ex = 0; ex < rho; ++ex) {
+      const double ae = a[(size_t)(cy * rho + ey) * nf + (cx * rho + ex)];
+      double loc[4][4], ql[4][4];
+      for (int c = 0; c < 4; ++c) {
+        const double X = (double)(ex + CDX[c]) / rho, Y = (double)(ey + CDY[c]) / rho;
+        ql[0][c] = (1.0 - X) * (1.0 - Y);
+        ql[1][c] = X * (1.0 - Y);
+        ql[2][c] = X * Y;
+        ql[3][c] = (1.0 - X) * Y;
+        for (int l = 0; l < 4; ++l) loc[l][c] = ph[l * CN + (ey + CDY[c]) * (rho + 1) + (ex + CDX[c])];
+      }
+      for (int l = 0; l < 4; ++l)
+        for (int lp = 0; lp < 4; ++lp) {
+          double e = 0.0;
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) e += loc[l][r] * KREF[r][c] * ql[lp][c];
+          S[l][lp] += ae * e;
+        }
+    }
+  for (int l = 0; l < 4; ++l)
+    for (int lp = 0; lp < 4; ++lp) Kpg[l * 4 + lp] = S[l][lp];
+  const double H = 1.0 / nc;
+  for (int l = 0; l < 4; ++l) bpg[l] = f * H * H / 4.0;
+  free(ph);
+  return 0;
+}
+
+/* All units of S samples in the Petrov-Galerkin form: Kpg [S][nc*nc][16],
+ * bpg [S][nc*nc][4], status [S*nc*nc]. */
+int orc_upscale_pg(int nf, int nc, double f, const double* a, const int8_t* oversample, int S,
+                   double* Kpg, double* bpg, int32_t* status, int nthreads) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0) return -1;
+  const long units = (long)S * nc * nc;
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+#endif
+  for (long u = 0; u < units; ++u) {
+    const int s = (int)(u / (nc * nc));
+    const int cell = (int)(u % (nc * nc));
+    const int o = oversample ? oversample[cell] : 0;
+    const int rc = orc_cell_pg(nf, nc, f, a + (size_t)s * nf * nf, cell % nc, cell / nc, o,
+                               Kpg + (size_t)u * 16, bpg + (size_t)u * 4);
+    if (status) status[u] = rc;
+    if (rc != 0) bad = 1;
+  }
+  return bad ? -2 : 0;
+}
+
+/* Banded LU without pivoting of a general matrix with half bandwidth bw
+ * (row i keeps columns i-bw..i+bw at band[i*(2bw+1) + (j-i+bw)]),
+ * forward elimination of rhs alongside, back substitution into rhs.
+ * Returns 0, or k+1 for a zero pivot at step k. */
+static int band_lu_solve(double* band, int n, int bw, double* rhs) {
+  const int W = 2 * bw + 1;
+#define AT(i, j) band[(size_t)(i) * W + ((j) - (i) + bw)]
+  for (int k = 0; k < n; ++k) {
+    const double piv = AT(k, k);
+    if (!(piv != 0.0) || piv != piv) return k + 1;
+    const int last = k + bw < n - 1 ? k + bw : n - 1;
+    for (int i = k + 1; i <= last; ++i) {
+      const double l = AT(i, k) / piv;
+      AT(i, k) = 0.0;
+      for (int j = k + 1; j <= last; ++j) AT(i, j) -= l * AT(k, j);
+      rhs[i] -= l * rhs[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double s = rhs[k];
+    const int last = k + bw < n - 1 ? k + bw : n - 1;
+    for (int j = k + 1; j <= last; ++j) s -= AT(k, j) * rhs[j];
+    rhs[k] = s / AT(k, k);
+  }
+#undef AT
+  return 0;
+}
+
+/* Petrov-Galerkin coarse system: find U with sum_I U_I a(phi_I, q_J) =
+ * (f, q_J) for every interior coarse node J, i.e. row J of the matrix
+ * collects S_e[I_loc][J_loc] over the cells around J (the transpose of the
+ * Galerkin-style assembly).  u [S][(nc+1)^2], boundary entries 0. */
+int orc_coarse_solve_pg(int nc, const double* Kpg, const double* bpg, int S, double* u) {
+  if (nc <= 0 || S < 0) return -1;
+  const int NN = nc + 1;
+  const int mi = nc - 1, n = mi * mi, bw = mi + 1, W = 2 * bw + 1;
+  for (int s = 0; s < S; ++s) {
+    double* band = (double*)calloc((size_t)(n > 0 ? n : 1) * W, sizeof(double));
+    double* rhs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!band || !rhs) { free(band); free(rhs); return -3; }
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cx = 0; cx < nc; ++cx) {
+        const double* K = Kpg + ((size_t)s * nc * nc + cy * nc + cx) * 16;
+        const double* B = bpg + ((size_t)s * nc * nc + cy * nc + cx) * 4;
+        for (int r = 0; r < 4; ++r) { /* test node J */
+          const int ri = cx + CDX[r], rj = cy + CDY[r];
+          if (ri <= 0 || ri >= nc || rj <= 0 || rj >= nc) continue;
+          const int J = (rj - 1) * mi + (ri - 1);
+          rhs[J] += B[r];
+          for (int c = 0; c < 4; ++c) { /* trial node I */
+            const int ci = cx + CDX[c], cj = cy + CDY[c];
+            if (ci <= 0 || ci >= nc || cj <= 0 || cj >= nc) continue;
+            const int I = (cj - 1) * mi + (ci - 1);
+            band[(size_t)J * W + (I - J + bw)] += K[c * 4 + r];
+          }
+        }
+      }
+    int rc = n > 0 ? band_lu_solve(band, n, bw, rhs) : 0;
+    double* us = u + (size_t)s * NN * NN;
+    for (int k = 0; k < NN * NN; ++k) us[k] = 0.0;
+    if (rc == 0)
+      for (int j = 1; j < nc; ++j)
+        for (int i = 1; i < nc; ++i) us[j * NN + i] = rhs[(j - 1) * mi + (i - 1)];
+    free(band); free(rhs);
+    if (rc != 0) return -4;
+  }
+  return 0;
+}
