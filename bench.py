@@ -410,6 +410,62 @@ def bench_ri(api, dev, stream, samples=None):
     return res, 3 * 3 + 3  # (tiles, eval, fallback) x 3 timed calls + the FP64 comparison x 3
 
 
+def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u64_gal):
+    """Petrov-Galerkin form (Eq. stiffness_local_petrov) of the FP32 step on
+    the same workload: sample a, upscale with bilinear test functions (16
+    entries per unit), non-symmetric coarse solve (banded LU) with moments.
+    Its coarse error against the FP64 Petrov-Galerkin step, and how far the
+    Petrov-Galerkin solution is from the Galerkin one (FP64 both)."""
+    import torch
+
+    def bufs(Bs, prec):
+        _, rb = api.stomsfem_upscale_workspace_size(g, mo, prec)
+        return dict(a=torch.empty((Bs, nf, nf), dtype=torch.float64, device=dev),
+                    Ke=torch.empty((Bs, ncell, 16), dtype=torch.float64, device=dev),
+                    be=torch.empty((Bs, ncell, 4), dtype=torch.float64, device=dev),
+                    u=torch.empty((Bs, nn), dtype=torch.float64, device=dev),
+                    wsu=torch.empty(rb, dtype=torch.uint8, device=dev),
+                    wsc=torch.empty(api.stomsfem_coarse_pg_workspace_size(g, Bs), dtype=torch.uint8,
+                                    device=dev),
+                    mean=torch.zeros(nn, dtype=torch.float64, device=dev),
+                    m2=torch.zeros(nn, dtype=torch.float64, device=dev),
+                    cnt=torch.zeros(1, dtype=torch.float64, device=dev))
+
+    def step(bf, xs, prec):
+        api.stomsfem_sample_coef_precision(g, fld, xs, bf["a"], precision=api.FP32 if prec == api.FP32
+                                           else api.FP64, stream=stream)
+        api.stomsfem_upscale_pg(g, bf["a"], bf["Ke"], bf["be"], oversample=ov_t, max_oversample=mo,
+                                precision=prec, workspace=bf["wsu"], stream=stream)
+        api.stomsfem_coarse_solve_pg(g, bf["Ke"], bf["be"], bf["u"], bf["mean"], bf["m2"], bf["cnt"],
+                                     workspace=bf["wsc"], stream=stream)
+
+    bf = bufs(B, api.FP32)
+    steps = 3
+    with torch.cuda.stream(stream):
+        for i in range(2):
+            step(bf, xs_for(i, B), api.FP32)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(bf, xs_for(2 + i, B), api.FP32)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    del bf
+    b32, b64 = bufs(Bc, api.FP32), bufs(Bc, api.FP64)
+    with torch.cuda.stream(stream):
+        step(b32, xs_for(0, Bc), api.FP32)
+        step(b64, xs_for(0, Bc), api.FP64)
+    stream.synchronize()
+    u32, u64 = b32["u"].cpu().numpy(), b64["u"].cpu().numpy()
+    rel = lambda x, y: float(np.max(np.linalg.norm(x - y, axis=1) / np.linalg.norm(y, axis=1)))
+    return {"form": "fp32", "samples_per_step": B, "units_per_s": B * ncell * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "coarse_rel_l2_vs_fp64_pg": rel(u32, u64),
+            "pg_vs_galerkin_fp64_rel_l2": rel(u64, u64_gal[:Bc]),
+            "gpu_launches_per_step": 7}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,6 +486,7 @@ def main():
     ap.add_argument("--sg-samples", type=int, default=None, help="surrogate inference samples (default 10^5)")
     ap.add_argument("--sg-steps", type=int, default=3000, help="surrogate training steps")
     ap.add_argument("--ri-samples", type=int, default=None, help="random-interpolation samples (default 10^5)")
+    ap.add_argument("--pg-batch", type=int, default=128, help="samples per step of the Petrov-Galerkin arm")
     ap.add_argument("--fp32r-batch", type=int, default=64, help="samples per step of the FP32+refinement arm")
     args = ap.parse_args()
 
@@ -587,6 +644,8 @@ def main():
 
     extra = {}
     if not args.no_extra_forms:
+        extra["petrov_galerkin"] = bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for,
+                                            args.pg_batch, Bc, u64)
         extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)
         extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
         extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)

@@ -201,6 +201,37 @@ int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const dou
                           int32_t S, double* u, double* mean, double* m2, double* count,
                           void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* Petrov-Galerkin form of stomsfem_upscale (Eq. stiffness_local_petrov;
+ * the form the paper uses with oversampling): same cell problems, same
+ * arguments, but the test functions are the cell's bilinear nodal
+ * functions q_l', so
+ *   Ke [S][nc*nc][16]  S_ll' = int_cell a grad phi_l . grad q_l', row-major
+ *                      (row l = trial basis function, column l' = test),
+ *   be [S][nc*nc][4]   b_l = int_cell f q_l = f H^2 / 4 (deterministic).
+ * Without oversampling S_ll' equals the Galerkin matrix (phi_l' - q_l'
+ * vanishes on the cell boundary and phi_l is discrete-harmonic), so those
+ * cells give the symmetric 16 entries.  Workspace, precision, refinement,
+ * phi output, statuses and errors as stomsfem_upscale. */
+int stomsfem_upscale_pg(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                        int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
+                        double* Ke, double* be, double* phi, int32_t* unit_status, void* workspace,
+                        size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* Scratch needed by stomsfem_coarse_solve_pg. */
+int stomsfem_coarse_pg_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
+
+/* Coarse solve of the Petrov-Galerkin system: U with
+ * sum_I U_I S(phi_I, q_J) = b_J for every interior coarse node J (row J
+ * collects S_e[I_loc][J_loc] over the cells around J; zero Dirichlet data),
+ * by banded LU without pivoting (half bandwidth nc), one warp per sample.
+ * Ke [S][nc*nc][16], be [S][nc*nc][4] from stomsfem_upscale_pg; u, mean,
+ * m2, count as stomsfem_coarse_solve.  A sample whose elimination meets a
+ * zero or non-finite pivot gets NaN in u.  Errors: EINVAL (also nc < 2 or
+ * nc > 64), ENOMEM, ECUDA. */
+int stomsfem_coarse_solve_pg(const stomsfem_grid* grid, const double* Ke, const double* be, int32_t S,
+                             double* u, double* mean, double* m2, double* count, void* workspace,
+                             size_t workspace_bytes, stomsfem_stream_t stream);
+
 /* ---------------------------------------------------------------------
  * Reduced-basis (POD) upscaling, Sec. 3.2 (Eq. KLphi, Eqs. localRB and
  * localRBsystem, Algs. 3 and 4), for cells without oversampling.

@@ -75,6 +75,11 @@ _SIG = {
     "stomsfem_surrogate_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_surrogate_infer": (ctypes.c_int, [_P, _P, _P, _I, ctypes.c_double, _P, _P, _P, _P, _SZ,
                                                 _P]),
+    "stomsfem_upscale_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P,
+                                           _SZ, _P]),
+    "stomsfem_coarse_pg_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_coarse_solve_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P, _SZ,
+                                                _P]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,

@@ -375,3 +375,45 @@ def stomsfem_ri_upscale(h, g: Grid, xi, a, Ke, be, fell_back, workspace=None, st
         _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
         _dev(fell_back, torch.uint8, (S, ncell), "fell_back"),
         _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
+def stomsfem_upscale_pg(g: Grid, a, Ke, be, oversample=None, max_oversample=0, precision=FP64,
+                        refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None):
+    """Petrov-Galerkin form: Ke [S][ncell][16] (row trial, column test)."""
+    S = a.shape[0]
+    ncell = g.nc * g.nc
+    rho = g.nf // g.nc
+    if workspace is None:
+        _, rb = stomsfem_upscale_workspace_size(g, max_oversample if oversample is not None else 0,
+                                                precision)
+        workspace = torch.empty(rb, dtype=torch.uint8, device=a.device)
+    L.check(L.lib().stomsfem_upscale_pg(
+        ctypes.byref(g), _dev(a, torch.float64, (S, g.nf, g.nf), "a"),
+        _dev(oversample, torch.int8, (ncell,), "oversample"), int(max_oversample), S, int(precision),
+        int(refine_iters), _dev(Ke, torch.float64, (S, ncell, 16), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
+        _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
+def stomsfem_coarse_pg_workspace_size(g: Grid, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_coarse_pg_workspace_size(ctypes.byref(g), int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_coarse_solve_pg(g: Grid, Ke, be, u, mean=None, m2=None, count=None, workspace=None,
+                             stream=None):
+    S = Ke.shape[0]
+    ncell = g.nc * g.nc
+    nn = (g.nc + 1) ** 2
+    if workspace is None:
+        workspace = torch.empty(stomsfem_coarse_pg_workspace_size(g, S), dtype=torch.uint8,
+                                device=Ke.device)
+    L.check(L.lib().stomsfem_coarse_solve_pg(
+        ctypes.byref(g), _dev(Ke, torch.float64, (S, ncell, 16), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"), S, _dev(u, torch.float64, (S, nn), "u"),
+        _dev(mean, torch.float64, (nn,), "mean"), _dev(m2, torch.float64, (nn,), "m2"),
+        _dev(count, torch.float64, (1,), "count"), _dev(workspace, torch.uint8, None, "workspace"),
+        workspace.numel(), _stream(stream)))

@@ -120,6 +120,142 @@ __global__ void moments_kernel(int nn, int S, const double* __restrict__ u, doub
 
 __global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
 
+// ---- Petrov-Galerkin coarse system (Eq. stiffness_local_petrov): row J
+// (test node) collects S_e[I_loc][J_loc] over the cells around J, a
+// non-symmetric band of half width bw = nc.  Banded LU without pivoting,
+// one warp per sample: the rows k..k+bw live in a shared-memory ring (row
+// i keeps columns i-bw..i+bw); step k eliminates column k from the bw rows
+// below (lane t owns rows k+1+t, k+33+t), writes the finished U row and its
+// right-hand side to the sample's scratch, and brings in row k+bw+1, whose
+// 16 contributions (4 cells x 4 trial corners) were loaded one step ahead.
+// Back substitution reads the U rows back with a ring of the last bw
+// unknowns.  A zero or non-finite pivot gives the sample NaN values.
+constexpr int kCoarsePgWarps = 2;
+
+struct PgRowPrefetch {
+  double v;  // contribution of this lane (0 if none)
+  int off;   // column offset within the row (-1: none)
+  double b;  // load contribution (lanes 0..3)
+};
+
+// Lane l < 16 takes cell c = l / 4 around node J and trial corner t = l % 4.
+__device__ __forceinline__ PgRowPrefetch pg_row_load(int nc, const double* __restrict__ Ks,
+                                                     const double* __restrict__ bs, int J, int n, int lane) {
+  PgRowPrefetch p{0.0, -1, 0.0};
+  if (J >= n || lane >= 16) return p;
+  const int mi = nc - 1;
+  const int i = J % mi + 1, j = J / mi + 1;  // coarse node of row J
+  const int c = lane >> 2, t = lane & 3;
+  // cells with node (i, j) as corner r: NE of (i-1, j-1), NW of (i, j-1),
+  // SW of (i, j), SE of (i-1, j)
+  const int cx = i - 1 + (c == 1 || c == 2), cy = j - 1 + (c >= 2), r = (c + 2) & 3;
+  const int tx = cx + (t == 1 || t == 2), ty = cy + (t >= 2);
+  const size_t cell = (size_t)cy * nc + cx;
+  if (tx > 0 && tx < nc && ty > 0 && ty < nc) {
+    const int I = (ty - 1) * mi + (tx - 1);
+    p.v = Ks[cell * 16 + t * 4 + r];
+    p.off = I - J + nc;
+  }
+  if (t == 0) p.b = bs[cell * 4 + r];
+  return p;
+}
+
+__global__ void __launch_bounds__(kCoarsePgWarps * 32)
+coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __restrict__ bpg,
+                 double* __restrict__ u, unsigned char* __restrict__ ws, size_t slot_bytes) {
+  extern __shared__ __align__(16) unsigned char smem_pg[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int bw = nc, W = 2 * nc + 1, R = nc + 1;
+  const int mi = nc - 1, n = mi * mi, NN = nc + 1;
+  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * W + 2 * R);
+  double* yr = Rw + (size_t)R * W;  // right-hand sides of the window rows
+  double* xr = yr + R;              // ring of the last bw unknowns
+  double* Ug = reinterpret_cast<double*>(ws + (size_t)(blockIdx.x * kCoarsePgWarps + wib) * slot_bytes);
+  const long long gw = (long long)blockIdx.x * kCoarsePgWarps + wib;
+  const long long nw = (long long)gridDim.x * kCoarsePgWarps;
+  for (long long sl = gw; sl < S; sl += nw) {
+    const double* Ks = Kpg + (size_t)sl * nc * nc * 16;
+    const double* bs = bpg + (size_t)sl * nc * nc * 4;
+    double* us = u + (size_t)sl * NN * NN;
+    // window: rows 0..bw (zeroed, then their contributions)
+    for (int q = lane; q < R * W; q += 32) Rw[q] = 0.0;
+    for (int q = lane; q < R; q += 32) yr[q] = 0.0;
+    __syncwarp();
+    for (int J = 0; J < R && J < n; ++J) {
+      const PgRowPrefetch p = pg_row_load(nc, Ks, bs, J, n, lane);
+      if (p.off >= 0) atomicAdd(&Rw[(size_t)(J % R) * W + p.off], p.v);
+      if (lane < 16 && (lane & 3) == 0) atomicAdd(&yr[J % R], p.b);
+      __syncwarp();
+    }
+    PgRowPrefetch next = pg_row_load(nc, Ks, bs, R, n, lane);
+    bool bad = false;
+    for (int k = 0; k < n; ++k) {
+      const PgRowPrefetch cur = next;
+      next = pg_row_load(nc, Ks, bs, k + R + 1, n, lane);  // in flight during this step
+      double* P = Rw + (size_t)(k % R) * W;
+      const double piv = P[bw];
+      if (!(fabs(piv) > 0.0) || !(fabs(piv) < 1e300)) bad = true;
+      const double inv = 1.0 / piv;
+      const double yk = yr[k % R];
+      for (int t = lane; t < bw; t += 32) {
+        const int i = k + 1 + t;
+        if (i < n) {
+          double* Ri = Rw + (size_t)(i % R) * W;
+          const double l = Ri[bw - 1 - t] * inv;
+          Ri[bw - 1 - t] = 0.0;
+          if (l != 0.0) {
+            for (int jj = 1; jj <= bw; ++jj) Ri[bw - 1 - t + jj] -= l * P[bw + jj];
+            yr[i % R] -= l * yk;
+          }
+        }
+      }
+      // finished U row k (columns k..k+bw) and its right-hand side
+      for (int q = lane; q <= bw; q += 32) Ug[(size_t)k * (bw + 2) + q] = P[bw + q];
+      if (lane == 0) Ug[(size_t)k * (bw + 2) + bw + 1] = yk;
+      __syncwarp();
+      // slot of row k takes row k + R
+      for (int q = lane; q < W; q += 32) P[q] = 0.0;
+      if (lane == 0) yr[k % R] = 0.0;
+      __syncwarp();
+      if (k + R < n) {
+        if (cur.off >= 0) atomicAdd(&P[cur.off], cur.v);
+        if (lane < 16 && (lane & 3) == 0) atomicAdd(&yr[k % R], cur.b);
+      }
+      __syncwarp();
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    // back substitution, x ring of R entries
+    for (int k = n - 1; k >= 0; --k) {
+      const double* Uk = Ug + (size_t)k * (bw + 2);
+      double part = 0.0;
+      for (int jj = 1 + lane; jj <= bw; jj += 32)
+        if (k + jj < n) part += Uk[jj] * xr[(k + jj) % R];
+      part = warp_sum(part);
+      const double xk = (Uk[bw + 1] - part) / Uk[0];
+      __syncwarp();
+      if (lane == 0) xr[k % R] = xk;
+      __syncwarp();
+      if (lane == 0) {
+        const int i = k % mi + 1, j = k / mi + 1;
+        us[j * NN + i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : xk;
+      }
+    }
+    for (int q = lane; q < NN * NN; q += 32) {
+      const int i = q % NN, j = q / NN;
+      if (i == 0 || j == 0 || i == nc || j == nc) us[q] = 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+static size_t coarse_pg_slot_bytes(int nc) {
+  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1;
+  return ((size_t)n * (nc + 2) * 8 + 255) & ~size_t(255);
+}
+static size_t coarse_pg_smem(int nc) {
+  return (size_t)kCoarsePgWarps * ((size_t)(nc + 1) * (2 * nc + 1) + 2 * (nc + 1)) * 8;
+}
+
 // Slot of one sample: the factor blocks, then the solution.
 static size_t coarse_l_bytes(int nc) {
   const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1;
@@ -173,6 +309,52 @@ extern "C" int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke
   kern<<<(unsigned)blocks, kCoarseBlkWarps * 32, smem, st>>>(nc, S, Ke, be, u,
                                                               static_cast<unsigned char*>(workspace), sb,
                                                               coarse_l_bytes(nc));
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  if (mom) {
+    const int nn = (grid->nc + 1) * (grid->nc + 1);
+    moments_kernel<<<(nn + 127) / 128, 128, 0, st>>>(nn, S, u, mean, m2, count);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+    count_kernel<<<1, 1, 0, st>>>(count, S);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+  }
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_coarse_pg_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes) {
+  if (!grid || grid->nc <= 0 || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  const int sms = device_sm_count();
+  long long slots = (long long)(sms > 0 ? sms : 152) * 4;
+  if (slots > S) slots = S;
+  if (slots < kCoarsePgWarps) slots = kCoarsePgWarps;
+  *bytes = coarse_pg_slot_bytes(grid->nc) * (size_t)slots;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_coarse_solve_pg(const stomsfem_grid* grid, const double* Kpg, const double* bpg,
+                                        int32_t S, double* u, double* mean, double* m2, double* count,
+                                        void* workspace, size_t workspace_bytes, stomsfem_stream_t stream) {
+  if (!grid || grid->nc <= 0) return set_error(STOMSFEM_EINVAL, "bad grid");
+  if (grid->nc < 2) return set_error(STOMSFEM_EINVAL, "nc must be >= 2");
+  if (grid->nc > 64) return set_error(STOMSFEM_EINVAL, "nc %d > 64 (coarse bandwidth limit)", grid->nc);
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (S == 0) return STOMSFEM_OK;
+  if (!Kpg || !bpg || !u || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  const bool mom = mean || m2 || count;
+  if (mom && !(mean && m2 && count))
+    return set_error(STOMSFEM_EINVAL, "mean, m2 and count must be given together");
+  const size_t sb = coarse_pg_slot_bytes(grid->nc);
+  long long slots = (long long)(workspace_bytes / sb);
+  if (slots < kCoarsePgWarps)
+    return set_error(STOMSFEM_ENOMEM, "coarse workspace %zu < %d slots of %zu", workspace_bytes, kCoarsePgWarps,
+                     sb);
+  long long blocks = slots / kCoarsePgWarps;
+  const long long need = ((long long)S + kCoarsePgWarps - 1) / kCoarsePgWarps;
+  if (blocks > need) blocks = need;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = coarse_pg_smem(grid->nc);
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(coarse_pg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  coarse_pg_kernel<<<(unsigned)blocks, kCoarsePgWarps * 32, smem, st>>>(
+      grid->nc, S, Kpg, bpg, u, static_cast<unsigned char*>(workspace), sb);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   if (mom) {
     const int nn = (grid->nc + 1) * (grid->nc + 1);

@@ -1,658 +1,8 @@
-// Simultaneous local upscaling: one warp per (sample, coarse cell) unit.
-//
-// Per unit (Eq. MsFEB, Remark on oversampling, Eq. stiffness_local):
-//   1. patch = cell enlarged by o fine elements per side, clipped to [0,1]^2;
-//   2. cell problems: psi_l = p_l + psi0_l with p_l the bilinear nodal
-//      function of the patch rectangle and psi0_l vanishing on the patch
-//      boundary, A_II psi0_l = -(A p_l)_I for l = SW, SE, NE (the NW one is
-//      1 - the others: the four p_l sum to 1 and A 1 = 0); the 9-point Q1
-//      matrix rows are generated from a on the fly as the banded Cholesky
-//      blocked banded Cholesky needs them (band_block.cuh);
-//   3. optional FP64 iterative refinement of the FP32 solution;
-//   4. M_jk = a_cell(psi_j, psi_k), m_j = int_cell f psi_j over the cell's
-//      fine elements; oversampling recombination phi = D psi with
-//      D = C^{-1}, C_jk = psi_j(cell corner k); K_e = D M D^T, b_e = D m.
-#include <cstdio>
-#include <type_traits>
-
-#include "band_block.cuh"
-#include "common.cuh"
-
-namespace stomsfem {
-
-// Warps per block: 4, except 2 for two FP64 units per warp (whose 36 KB of
-// shared memory per warp then fit three blocks on an SM).
-__host__ __device__ constexpr int upscale_warps(bool fp64, int G) { return fp64 && G == 16 ? 2 : 4; }
-constexpr int kUpscaleWarps = 4;  // list mode (one FP64 unit per warp)
-constexpr int kMaxBand = 64;       // half bandwidth limit (mx + 1)
-
-struct UnitGeom {
-  int x0, y0, Nx, Ny, mx, my, n, b;
-  int cx0, cy0;  // cell origin in patch-local node coordinates
-};
-
-__device__ inline UnitGeom unit_geom(int nf, int rho, int cx, int cy, int o) {
-  UnitGeom g;
-  const int x0 = max(0, cx * rho - o), x1 = min(nf, (cx + 1) * rho + o);
-  const int y0 = max(0, cy * rho - o), y1 = min(nf, (cy + 1) * rho + o);
-  g.x0 = x0;
-  g.y0 = y0;
-  g.Nx = x1 - x0;
-  g.Ny = y1 - y0;
-  g.mx = g.Nx - 1;
-  g.my = g.Ny - 1;
-  g.n = g.mx * g.my;
-  g.b = g.mx + 1;
-  g.cx0 = cx * rho - x0;
-  g.cy0 = cy * rho - y0;
-  return g;
-}
-
-// Row generator of the patch system: matrix rows from a, right-hand sides
-// -(A p_l) at interior nodes in closed form (differences of a only, so the
-// small right-hand sides keep their relative accuracy in FP32).
-struct PatchGen {
-  const double* a;  // this sample's coefficient [nf][nf]
-  int nf, x0, y0, Nx, Ny, mx;
-  float iNxf, iNyf, rmx;  // 1/Nx, 1/Ny, 1/mx, set by finish()
-  double iNxd, iNyd;
-
-  __device__ __forceinline__ void finish() {
-    rmx = __frcp_rn((float)mx);
-    iNxd = 1.0 / (double)Nx;
-    iNyd = 1.0 / (double)Ny;
-    iNxf = 1.0f / (float)Nx;
-    iNyf = 1.0f / (float)Ny;
-  }
-
-  __device__ __forceinline__ double ael(int ex, int ey) const {
-    return __ldg(a + (size_t)(y0 + ey) * nf + (x0 + ex));
-  }
-  __device__ __forceinline__ void node(int r, int& i, int& j) const {
-    // j - 1 = floor(r / mx) from a float reciprocal: (r + 1/2) / mx stays at
-    // least 1/(2 mx) away from an integer, far above the rounding error
-    const int q = __float2int_rz(((float)r + 0.5f) * rmx);
-    j = q + 1;
-    i = r - q * mx + 1;
-  }
-  template <typename T>
-  __device__ __forceinline__ T coef(int r, int d) const {
-    if (d != 0 && d != 1 && d != mx - 1 && d != mx && d != mx + 1) return T(0);
-    int i, j;
-    node(r, i, j);
-    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
-    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
-    T v = T(0);
-    if (d == 0) v += (T(2) / T(3)) * (aSW + aSE + aNE + aNW);
-    if (d == 1 && i > 1) v -= (aSW + aNW) / T(6);                    // west
-    if (d == mx && j > 1) v -= (aSW + aSE) / T(6);                   // south
-    if (d == mx + 1 && i > 1 && j > 1) v -= aSW / T(3);              // south-west
-    if (d == mx - 1 && i < mx && j > 1) v -= aSE / T(3);             // south-east
-    return v;
-  }
-  // (A X), (A Y), (A XY) at interior node (i, j) for the patch coordinates
-  // X = i/Nx, Y = j/Ny; then -(A p_l) for p_SW = 1-X-Y+XY, p_SE = X-XY, p_NE = XY.
-  template <typename T>
-  __device__ __forceinline__ void ap(int i, int j, T& AX, T& AY, T& AXY) const {
-    const T aSW = (T)ael(i - 1, j - 1), aSE = (T)ael(i, j - 1);
-    const T aNE = (T)ael(i, j), aNW = (T)ael(i - 1, j);
-    AX = ((aSW + aNW) - (aSE + aNE)) / (T(2) * (T)Nx);
-    AY = ((aSW + aSE) - (aNW + aNE)) / (T(2) * (T)Ny);
-    const T Xc = (T)i / (T)Nx, Yc = (T)j / (T)Ny;
-    AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) / (T(3) * (T)Nx * (T)Ny);
-  }
-  template <typename T>
-  __device__ __forceinline__ T rhs(int r, int l) const {
-    int i, j;
-    node(r, i, j);
-    T AX, AY, AXY;
-    ap<T>(i, j, AX, AY, AXY);
-    if (l == 0) return AX + AY - AXY;
-    if (l == 1) return AXY - AX;
-    return -AXY;
-  }
-  // Raw values of row r: the coefficient on the four elements around the node.
-  struct Raw {
-    double sw, se, ne, nw;
-  };
-  __device__ __forceinline__ void load(int r, Raw& w) const {
-    int i, j;
-    node(r, i, j);
-    w.sw = ael(i - 1, j - 1);
-    w.se = ael(i, j - 1);
-    w.ne = ael(i, j);
-    w.nw = ael(i - 1, j);
-  }
-  __device__ __forceinline__ void prefetch(int r, double* dst) const {
-    int i, j;
-    node(r, i, j);
-    const double* p0 = a + (size_t)(y0 + j - 1) * nf + (x0 + i - 1);  // SW element
-    cp_async8(dst + 0, p0);
-    cp_async8(dst + 1, p0 + 1);
-    cp_async8(dst + 2, p0 + nf + 1);
-    cp_async8(dst + 3, p0 + nf);
-  }
-  __device__ __forceinline__ void from_smem(const double* src, Raw& w) const {
-    w.sw = src[0];
-    w.se = src[1];
-    w.ne = src[2];
-    w.nw = src[3];
-  }
-  // Whole row r: band entries at offsets 0, 1 (west), mx-1 (south-east),
-  // mx (south), mx+1 (south-west) and the three right-hand sides; NR = 4
-  // adds a fourth right-hand side of ones (the load functional of interior
-  // nodes, up to the factor h^2).
-  template <typename T, int NR = 3>
-  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const {
-    int i, j;
-    node(r, i, j);
-    const T aSW = (T)w.sw, aSE = (T)w.se;
-    const T aNE = (T)w.ne, aNW = (T)w.nw;
-    // divisions replaced by products with reciprocals (one rounding each)
-    const T r3 = T(1) / T(3), r6 = T(1) / T(6);
-    T iNx, iNy;
-    if constexpr (sizeof(T) == 4) {
-      iNx = iNxf;
-      iNy = iNyf;
-    } else {
-      iNx = iNxd;
-      iNy = iNyd;
-    }
-    e[0] = (T(2) * r3) * ((aSW + aSE) + (aNE + aNW));
-    e[1] = i > 1 ? -(aSW + aNW) * r6 : T(0);
-    e[2] = (i < mx && j > 1) ? -aSE * r3 : T(0);
-    e[3] = j > 1 ? -(aSW + aSE) * r6 : T(0);
-    e[4] = (i > 1 && j > 1) ? -aSW * r3 : T(0);
-    const T AX = T(0.5) * ((aSW + aNW) - (aSE + aNE)) * iNx;
-    const T AY = T(0.5) * ((aSW + aSE) - (aNW + aNE)) * iNy;
-    const T Xc = (T)i * iNx, Yc = (T)j * iNy;
-    const T AXY = Xc * AY + Yc * AX + ((aSE + aNW) - (aNE + aSW)) * r3 * iNx * iNy;
-    rh[0] = AX + AY - AXY;
-    rh[1] = AXY - AX;
-    rh[2] = -AXY;
-    if constexpr (NR == 4) rh[3] = T(1);
-  }
-};
-
-// Right-hand side of a refinement step: the FP64 residual
-// -(A (p_l + psi0_l)) at interior nodes, psi0 = 0 on the patch boundary.
-struct ResidualGen {
-  PatchGen pg;
-  const double* psi0;  // [n][3]
-  __device__ __forceinline__ double psi(int i, int j, int l) const {
-    if (i <= 0 || j <= 0 || i > pg.mx || j > pg.Ny - 1) return 0.0;
-    return psi0[((size_t)(j - 1) * pg.mx + (i - 1)) * 3 + l];
-  }
-  // All three right-hand sides of row r: the stencil coefficients and the
-  // closed-form -(A p_l) once per node, divisions replaced by products with
-  // reciprocals (each residual term then carries a rounding or two of FP64,
-  // far below what the refinement resolves).
-  __device__ __forceinline__ void rhs3(int r, double out[3]) const {
-    int i, j;
-    pg.node(r, i, j);
-    const double aSW = pg.ael(i - 1, j - 1), aSE = pg.ael(i, j - 1);
-    const double aNE = pg.ael(i, j), aNW = pg.ael(i - 1, j);
-    constexpr double r3 = 1.0 / 3.0, r6 = 1.0 / 6.0;
-    const double AX = 0.5 * ((aSW + aNW) - (aSE + aNE)) * pg.iNxd;
-    const double AY = 0.5 * ((aSW + aSE) - (aNW + aNE)) * pg.iNyd;
-    const double AXY = ((double)i * pg.iNxd) * AY + ((double)j * pg.iNyd) * AX +
-                       ((aSE + aNW) - (aNE + aSW)) * r3 * pg.iNxd * pg.iNyd;
-    const double r0[3] = {AX + AY - AXY, AXY - AX, -AXY};
-    // A psi0 with the full 9-point stencil
-    const double cC = (2.0 / 3.0) * ((aSW + aSE) + (aNE + aNW));
-    const double cW = (aSW + aNW) * r6, cE = (aSE + aNE) * r6, cS = (aSW + aSE) * r6, cN = (aNE + aNW) * r6;
-    const double dSW = aSW * r3, dSE = aSE * r3, dNE = aNE * r3, dNW = aNW * r3;
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      double t = cC * psi(i, j, l);
-      t -= cW * psi(i - 1, j, l);
-      t -= cE * psi(i + 1, j, l);
-      t -= cS * psi(i, j - 1, l);
-      t -= cN * psi(i, j + 1, l);
-      t -= dSW * psi(i - 1, j - 1, l);
-      t -= dSE * psi(i + 1, j - 1, l);
-      t -= dNE * psi(i + 1, j + 1, l);
-      t -= dNW * psi(i - 1, j + 1, l);
-      out[l] = r0[l] - t;
-    }
-  }
-};
-
-// psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction),
-// given its patch coordinates X = i / Nx, Y = j / Ny.
-template <typename T, typename TS>
-__device__ __forceinline__ void psi_at_xy(const UnitGeom& g, const TS* psi0, int i, int j, T X, T Y, T out[3],
-                                          bool with_psi = true) {
-  out[0] = (T(1) - X) * (T(1) - Y);
-  out[1] = X * (T(1) - Y);
-  out[2] = X * Y;
-  if (with_psi && i > 0 && j > 0 && i < g.Nx && j < g.Ny) {
-    const TS* p = psi0 + ((size_t)(j - 1) * g.mx + (i - 1)) * 3;
-    out[0] += (T)p[0];
-    out[1] += (T)p[1];
-    out[2] += (T)p[2];
-  }
-}
-
-// The same, computing X and Y.
-template <typename T, typename TS>
-__device__ __forceinline__ void psi_at(const UnitGeom& g, const TS* psi0, int i, int j, T out[3],
-                                       bool with_psi = true) {
-  psi_at_xy<T, TS>(g, psi0, i, j, (T)i / (T)g.Nx, (T)j / (T)g.Ny, out, with_psi);
-}
-
-// 4x4 inverse by Gauss-Jordan elimination without row exchanges, all
-// indices static so the matrix stays in registers.  C_jk = psi_j(corner k)
-// is strongly diagonally dominant (the patch basis at the cell corners is
-// close to the patch's own bilinear nodal values), so no pivoting is needed;
-// a vanishing pivot reports failure.
-template <typename T>
-__device__ __forceinline__ bool inv4(T C[4][4], T D[4][4]) {
-  T M[4][8];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) M[r][c] = c < 4 ? C[r][c] : (c - 4 == r ? T(1) : T(0));
-  bool ok = true;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    ok = ok && (M[c][c] != T(0));
-    const T dinv = T(1) / M[c][c];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) M[c][k] *= dinv;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-      if (r != c) {
-        const T f = M[r][c];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
-      }
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) D[r][c] = M[r][c + 4];
-  return ok;
-}
-
-struct UpscaleArgs {
-  const double* a;
-  const int8_t* oversample;
-  int nf, nc, rho, max_o, S;
-  double f;
-  int refine;
-  double* Ke;
-  double* be;
-  double* phi;
-  int32_t* status;
-  unsigned char* ws;
-  size_t slot_bytes, l_bytes;
-  int bmax, nmax;
-  long long units;
-  const int32_t* unit_list;   // optional: process only these units (device list)
-  const int32_t* unit_count;  // device length of unit_list
-  double fq, fH2;             // f h^2 / 4 and f H^2 (load scaling)
-  const int32_t* cell_list;   // optional (MODE 1, 2): process only these cells (device list)
-  const int32_t* cell_count;  // device length of cell_list
-};
-
-// Upscale launch modes: 0 every unit (back-substitution route), 1 the
-// cells without oversampling by the forward-only route, 2 the other cells.
-// Splitting the two routes over two launches keeps one route's code hot per
-// kernel; with both in one kernel the instruction working set of an SM
-// doubled and cost more than the forward-only route saved.
-enum { kModeAll = 0, kModeFwd = 1, kModeRest = 2 };
-
-// Device lists of the cells with o = 0 (list0) and the others (list1), in
-// cell order, and their lengths: one warp, ballot compaction.
-__global__ void upscale_cell_lists_kernel(const int8_t* __restrict__ oversample, int ncell,
-                                          int32_t* __restrict__ list0, int32_t* __restrict__ list1,
-                                          int32_t* __restrict__ counts) {
-  const int lane = threadIdx.x & 31;
-  int n0 = 0, n1 = 0;
-  for (int c0 = 0; c0 < ncell; c0 += 32) {
-    const int c = c0 + lane;
-    const bool valid = c < ncell;
-    const bool z = valid && oversample[c] == 0;
-    const unsigned m0 = __ballot_sync(0xffffffffu, z), m1 = __ballot_sync(0xffffffffu, valid && !z);
-    const unsigned below = (1u << lane) - 1u;
-    if (z) list0[n0 + __popc(m0 & below)] = c;
-    if (valid && !z) list1[n1 + __popc(m1 & below)] = c;
-    n0 += __popc(m0);
-    n1 += __popc(m1);
-  }
-  if (lane == 0) {
-    counts[0] = n0;
-    counts[1] = n1;
-  }
-}
-
-__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
-
-// Sum over the G lanes of a group (every lane of the group receives it).
-template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
-  return v;
-}
-
-// TK: factor/solve type; TA: type of the K_e/b_e accumulation and of the
-// recombination; RPL: panel rows per lane (ceil((G/2 + bmax) / G)); G: lanes
-// per unit.  G = 32: one unit per warp (any unit order, including a device
-// list).  G = 16: a warp takes one cell of two consecutive samples, whose
-// patches have the same shape, so its two halves run the same loop bounds
-// in lockstep (an odd last sample is mirrored by the idle half, which
-// writes nothing).
-template <typename TK, typename TA, int RPL, int G, int MODE>
-__global__ void __launch_bounds__(upscale_warps(sizeof(TK) == 8, G) * 32,
-                                  sizeof(TK) == 4 ? (G == 16 ? 3 : 4) : (G == 16 ? 3 : 2))
-upscale_kernel(UpscaleArgs A) {
-  constexpr int NB = G / 2;
-  constexpr int GPW = 32 / G;  // units per warp
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31;
-  const int gl = lane % G, grp = lane / G;
-  const int wib = threadIdx.x >> 5;
-  const BlkSmem<TK> sm = make_blk<TK>(smem + (wib * GPW + grp) * blk_smem_bytes<TK>(NB, A.bmax), NB, A.bmax);
-  constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
-  const long long gw = (long long)blockIdx.x * WPB + wib;
-  const long long nw = (long long)gridDim.x * WPB;
-  unsigned char* slot = A.ws + (size_t)(gw * GPW + grp) * A.slot_bytes;
-  // solutions are kept in FP64 except in the all-FP32 form
-  using TS = typename std::conditional<std::is_same<TA, float>::value, float, double>::type;
-  TK* Lg = reinterpret_cast<TK*>(slot);
-  TS* psi0 = reinterpret_cast<TS*>(slot + A.l_bytes);
-  double* corr = reinterpret_cast<double*>(slot + A.l_bytes) + (size_t)A.nmax * 3;
-  const int ncell = A.nc * A.nc;
-  const int CN = (A.rho + 1) * (A.rho + 1);
-
-  // cells of this launch (MODE 1, 2: a device list, or all cells when none)
-  const int nlc = (MODE != kModeAll && A.cell_list) ? A.cell_count[0] : ncell;
-  const long long nwork = A.unit_list ? (long long)A.unit_count[0]
-                                      : (G == 32 ? (long long)A.S * nlc : (long long)((A.S + 1) / 2) * nlc);
-  for (long long w = gw; w < nwork; w += nw) {
-    long long u;
-    bool dup = false;  // this half mirrors the other half's unit
-    const int ci = (int)(w % nlc);
-    const int cell_w = (MODE != kModeAll && A.cell_list) ? A.cell_list[ci] : ci;
-    if (G == 32) {
-      u = A.unit_list ? (long long)A.unit_list[w] : (long long)(w / nlc) * ncell + cell_w;
-    } else {
-      int sp = 2 * (int)(w / nlc) + grp;
-      if (sp >= A.S) {
-        sp = A.S - 1;
-        dup = true;
-      }
-      u = (long long)sp * ncell + cell_w;
-    }
-    const int s = (int)(u / ncell);
-    const int cell = (int)(u % ncell);
-    const int cx = cell % A.nc, cy = cell / A.nc;
-    const int o = A.oversample ? (int)A.oversample[cell] : 0;
-    double* Ke = A.Ke + (size_t)u * 10;
-    double* be = A.be + (size_t)u * 4;
-    if (o < 0 || o > A.max_o) {
-      if (!dup) {
-        if (gl < 10) Ke[gl] = qnan();
-        if (gl < 4) be[gl] = qnan();
-        if (gl == 0 && A.status) A.status[u] = -1;
-      }
-      continue;
-    }
-    const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
-    PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
-    pg.finish();
-    // A patch that is the cell itself (no oversampling) in the FP32 form,
-    // without phi output, takes the forward-only route: K_e(l, m) =
-    // p_l^T A p_m - y_l . y_m with y = L^-1 R_l the forward solutions (the
-    // Galerkin identity of the cell problem, Eq. stiffness_local with
-    // phi_l = p_l + psi_l), and the corner sums of psi_l from z . y_l with
-    // z = L^-1 1; no factor is stored and there is no back substitution.
-    // The choice depends only on the cell, so both halves of a warp agree.
-    // The host sends only such cells to MODE 1 launches.
-    constexpr bool fwd_only = MODE == kModeFwd;
-    double yy[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    // a failed factorisation still runs every step (the halves of a warp
-    // stay in lockstep); its unit gets NaN results and a status below
-    int fail = -1;
-    if constexpr (fwd_only) {
-      if (g.n > 0)
-        fail = blk_factor<G, TK, 4, RPL, PatchGen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
-    } else if (g.n > 0) {
-      fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
-      blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
-      // FP64 iterative refinement with the factor: corr = residual, solve, add
-      for (int it = 0; it < A.refine; ++it) {
-        __syncwarp();
-        const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
-        for (int r = gl; r < g.n; r += G) rg.rhs3(r, corr + (size_t)3 * r);
-        __syncwarp();
-        blk_forward_stored<G, TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
-        blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
-        __syncwarp();
-        for (int k = gl; k < g.n * 3; k += G) psi0[k] += (TS)corr[k];
-      }
-    }
-    __syncwarp();
-    // M_jk = a_cell(psi_j, psi_k) (j, k < 3) by the edge/diagonal difference
-    // form of the Q1 element energy, 6 u^T K_ref v = sum_edges du dv +
-    // 2 sum_diagonals du dv; m_j = sum over element corners of psi_j.
-    TA M[6] = {0, 0, 0, 0, 0, 0};
-    TA m[3] = {0, 0, 0};
-    TA iNx, iNy;
-    if constexpr (sizeof(TA) == 4) {
-      iNx = pg.iNxf;
-      iNy = pg.iNyf;
-    } else {
-      iNx = (TA)pg.iNxd;
-      iNy = (TA)pg.iNyd;
-    }
-    for (int e = gl; e < A.rho * A.rho; e += G) {
-      const int ex = e % A.rho, ey = e / A.rho;
-      const int i0 = g.cx0 + ex, j0 = g.cy0 + ey;
-      TA c0[3], c1[3], c2[3], c3[3];
-      // patch coordinates of the element's corners: the product with 1/Nx
-      // (1/Ny) and one residual correction q + (i - q N) / N, which rounds
-      // like the quotient i / N
-      auto quot = [](TA num, TA den, TA inv) {
-        const TA q = num * inv;
-        return fma(fma(-q, den, num), inv, q);
-      };
-      const TA Nxf = (TA)g.Nx, Nyf = (TA)g.Ny;
-      const TA X0 = quot((TA)i0, Nxf, iNx), X1 = quot((TA)(i0 + 1), Nxf, iNx);
-      const TA Y0 = quot((TA)j0, Nyf, iNy), Y1 = quot((TA)(j0 + 1), Nyf, iNy);
-      psi_at_xy<TA, TS>(g, psi0, i0, j0, X0, Y0, c0, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0, X1, Y0, c1, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0 + 1, X1, Y1, c2, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0, j0 + 1, X0, Y1, c3, !fwd_only);
-      const TA ae = (TA)pg.ael(i0, j0);
-      TA dd[3][6];
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        dd[l][0] = c0[l] - c1[l];
-        dd[l][1] = c1[l] - c2[l];
-        dd[l][2] = c2[l] - c3[l];
-        dd[l][3] = c3[l] - c0[l];
-        dd[l][4] = c0[l] - c2[l];
-        dd[l][5] = c1[l] - c3[l];
-        m[l] += (c0[l] + c1[l]) + (c2[l] + c3[l]);
-      }
-      int q = 0;
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int lp = l; lp < 3; ++lp) {
-          const TA v = dd[l][0] * dd[lp][0] + dd[l][1] * dd[lp][1] + dd[l][2] * dd[lp][2] +
-                       dd[l][3] * dd[lp][3] + TA(2) * (dd[l][4] * dd[lp][4] + dd[l][5] * dd[lp][5]);
-          M[q++] += ae * v;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) M[q] = group_sum<G>(M[q]);
-#pragma unroll
-    for (int l = 0; l < 3; ++l) m[l] = group_sum<G>(m[l]);
-    if constexpr (fwd_only) {
-      // M holds 6 p_l^T A p_m and m the corner sums of p_l: subtract the
-      // forward-solution products; every interior node is a corner of four
-      // elements, so the corner sums of psi_l are 4 z . y_l
-#pragma unroll
-      for (int q = 0; q < 9; ++q) yy[q] = group_sum<G>(yy[q]);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) M[q] = (TA)((double)M[q] - 6.0 * yy[q]);
-#pragma unroll
-      for (int l = 0; l < 3; ++l) m[l] = (TA)((double)m[l] + 4.0 * yy[6 + l]);
-    }
-
-    // recombination D = C^{-1}, C_jk = psi_j(cell corner k); identity when
-    // the patch is the cell (its corners carry the bilinear data exactly)
-    TA D[4][4];
-    const bool patch_is_cell = (g.cx0 == 0 && g.cy0 == 0 && g.Nx == A.rho && g.Ny == A.rho);
-    bool ok = true;
-    if (patch_is_cell) {
-      for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) D[r][c] = (r == c) ? TA(1) : TA(0);
-    } else {
-      const int ci[4] = {g.cx0, g.cx0 + A.rho, g.cx0 + A.rho, g.cx0};
-      const int cj[4] = {g.cy0, g.cy0, g.cy0 + A.rho, g.cy0 + A.rho};
-      TA C[4][4];
-      for (int k = 0; k < 4; ++k) {
-        TA v[3];
-        psi_at<TA, TS>(g, psi0, ci[k], cj[k], v);
-        C[0][k] = v[0];
-        C[1][k] = v[1];
-        C[2][k] = v[2];
-        C[3][k] = TA(1) - v[0] - v[1] - v[2];
-      }
-      ok = inv4<TA>(C, D);
-    }
-    if (gl == 0 && !dup && fail >= 0) {
-      for (int q = 0; q < 10; ++q) Ke[q] = qnan();
-      for (int q = 0; q < 4; ++q) be[q] = qnan();
-      if (A.status) A.status[u] = fail + 1;
-    }
-    if (gl == 0 && !dup && fail < 0) {
-      // one lane per unit: FP64 here runs at the narrow pipe's single-lane
-      // cost, so divisions become products with constants and the identity
-      // recombination of an unoversampled patch is skipped
-      double MM[4][4];
-      MM[0][0] = M[0]; MM[0][1] = MM[1][0] = M[1]; MM[0][2] = MM[2][0] = M[2];
-      MM[1][1] = M[3]; MM[1][2] = MM[2][1] = M[4]; MM[2][2] = M[5];
-      for (int r = 0; r < 3; ++r) MM[r][3] = MM[3][r] = -(MM[r][0] + MM[r][1] + MM[r][2]);
-      MM[3][3] = -(MM[0][3] + MM[1][3] + MM[2][3]);
-      for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) MM[r][c] *= 1.0 / 6.0;
-      double mv[4] = {A.fq * (double)m[0], A.fq * (double)m[1], A.fq * (double)m[2], 0.0};
-      mv[3] = A.fH2 - (mv[0] + mv[1] + mv[2]);
-      if (patch_is_cell) {
-        int q = 0;
-        for (int r = 0; r < 4; ++r)
-          for (int c = r; c < 4; ++c) Ke[q++] = MM[r][c];
-        for (int r = 0; r < 4; ++r) be[r] = mv[r];
-        if (A.status) A.status[u] = 0;
-      } else {
-      double T4[4][4];
-      for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += (double)D[r][k] * MM[k][c];
-          T4[r][c] = t;
-        }
-      int q = 0;
-      for (int r = 0; r < 4; ++r)
-        for (int c = r; c < 4; ++c) {
-          double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += T4[r][k] * (double)D[c][k];
-          Ke[q++] = ok ? t : qnan();
-        }
-      for (int r = 0; r < 4; ++r) {
-        double t = 0.0;
-        for (int k = 0; k < 4; ++k) t += (double)D[r][k] * mv[k];
-        be[r] = ok ? t : qnan();
-      }
-      if (A.status) A.status[u] = ok ? 0 : STOMSFEM_ENOTSPD;
-      }
-    }
-    if (A.phi && !dup && fail < 0) {
-      double* ph = A.phi + (size_t)u * 4 * CN;
-      for (int q = gl; q < CN; q += G) {
-        const int i = g.cx0 + q % (A.rho + 1), j = g.cy0 + q / (A.rho + 1);
-        double v[3];
-        psi_at<double, TS>(g, psi0, i, j, v);
-        const double v4[4] = {v[0], v[1], v[2], 1.0 - v[0] - v[1] - v[2]};
-        for (int l = 0; l < 4; ++l) {
-          double t = 0.0;
-          for (int k = 0; k < 4; ++k) t += (double)D[l][k] * v4[k];
-          ph[(size_t)l * CN + q] = t;
-        }
-      }
-    }
-    __syncwarp();
-  }
-}
-
-static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
-static void slot_layout(int nmax, int bmax, int precision, size_t* slot, size_t* l_bytes) {
-  const size_t tk = precision == STOMSFEM_FP64 ? 8 : 4;
-  *l_bytes = round256(blk_factor_elems(nmax, bmax) * tk);
-  *slot = *l_bytes + round256((size_t)nmax * 3 * 8 * 2);
-}
-
-static int validate_grid(const stomsfem_grid* g) {
-  if (!g) return set_error(STOMSFEM_EINVAL, "grid is NULL");
-  if (g->nf <= 0 || g->nc <= 0 || g->nf % g->nc != 0)
-    return set_error(STOMSFEM_EINVAL, "grid: need nf > 0, nc > 0, nf %% nc == 0 (nf=%d nc=%d)",
-                     g->nf, g->nc);
-  return STOMSFEM_OK;
-}
-
-static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax) {
-  const int rho = g->nf / g->nc;
-  const int side = rho + 2 * max_o < g->nf ? rho + 2 * max_o : g->nf;
-  const int m = side - 1;
-  *nmax = m * m > 1 ? m * m : 1;
-  *bmax = m + 1;
-}
-
-template <typename TK, typename TA, int RPL, int G, int MODE>
-static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  auto kern = upscale_kernel<TK, TA, RPL, G, MODE>;
-  constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
-  const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * WPB * (32 / G);
-  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
-  if (per_sm < 1) return set_error(STOMSFEM_EINVAL, "upscale kernel does not fit on an SM (smem %zu)", smem);
-  long long blocks = (long long)per_sm * device_sm_count();
-  if (blocks > max_blocks) blocks = max_blocks;
-  if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, WPB * 32, smem, st>>>(A);
-  STOMSFEM_TRY_CUDA(cudaGetLastError());
-  return STOMSFEM_OK;
-}
-
-template <typename TK, typename TA, int G, int MODE = kModeAll>
-static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  const int rpl = (G / 2 + A.bmax + G - 1) / G;  // <= 3 (G = 32) or 5 (G = 16) for bmax <= 64
-  if (rpl <= 1) return launch_upscale<TK, TA, 1, G, MODE>(A, max_blocks, st);
-  if (rpl == 2) return launch_upscale<TK, TA, 2, G, MODE>(A, max_blocks, st);
-  if (rpl == 3) return launch_upscale<TK, TA, 3, G, MODE>(A, max_blocks, st);
-  if constexpr (G == 16) {
-    if (rpl == 4) return launch_upscale<TK, TA, 4, G, MODE>(A, max_blocks, st);
-    return launch_upscale<TK, TA, 5, G, MODE>(A, max_blocks, st);
-  }
-  return set_error(STOMSFEM_EINVAL, "bandwidth %d too large", A.bmax);
-}
-
-// Bytes at the end of the workspace for the two cell lists of the split
-// FP32 launch.
-static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(int32_t) * (2 * (size_t)g->nc * g->nc + 2)); }
-
-// Lanes per unit of each form: two units per warp.
-constexpr int group_lanes(int) { return 16; }
-
-}  // namespace stomsfem
+// Galerkin local upscaling (Eq. stiffness_local): the C entry points, and
+// the FP64 list mode used by the fallbacks of the surrogate and of the
+// random interpolation.  The kernel and its host runner are in
+// upscale_impl.cuh.
+#include "upscale_impl.cuh"
 
 using namespace stomsfem;
 
@@ -680,93 +30,8 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
                                 int32_t precision, int32_t refine_iters, double* Ke, double* be,
                                 double* phi, int32_t* unit_status, void* workspace,
                                 size_t workspace_bytes, stomsfem_stream_t stream) {
-  int rc = validate_grid(grid);
-  if (rc) return rc;
-  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
-  if (precision < 0 || precision > 2) return set_error(STOMSFEM_EINVAL, "bad precision %d", precision);
-  if (max_oversample < 0) return set_error(STOMSFEM_EINVAL, "bad max_oversample");
-  if (refine_iters < 0 || refine_iters > 8)
-    return set_error(STOMSFEM_EINVAL, "refine_iters must be in [0, 8]");
-  if (S == 0) return STOMSFEM_OK;
-  if (!a || !Ke || !be || !workspace)
-    return set_error(STOMSFEM_EINVAL, "a, Ke, be and workspace must be device pointers");
-  const int mo = oversample ? max_oversample : 0;
-  int nmax, bmax;
-  patch_limits(grid, mo, &nmax, &bmax);
-  if (bmax > kMaxBand)
-    return set_error(STOMSFEM_EINVAL, "patch bandwidth %d exceeds %d (rho + 2*max_o too large)",
-                     bmax, kMaxBand);
-  size_t sb, lb;
-  slot_layout(nmax, bmax, precision, &sb, &lb);
-  const long long units = (long long)S * grid->nc * grid->nc;
-  const long long slots = (long long)(workspace_bytes / sb);
-  const int G = group_lanes(precision);
-  const int WPB = upscale_warps(precision == STOMSFEM_FP64, G);
-  const int slots_per_block = WPB * (32 / G);
-  if (slots < slots_per_block)
-    return set_error(STOMSFEM_ENOMEM, "workspace %zu bytes < %d slots of %zu bytes", workspace_bytes,
-                     slots_per_block, sb);
-  long long max_blocks = slots / slots_per_block;
-  const long long items = G == 32 ? units : (long long)((S + 1) / 2) * grid->nc * grid->nc;
-  const long long need = (items + WPB - 1) / WPB;
-  if (max_blocks > need) max_blocks = need;
-
-  UpscaleArgs A;
-  A.a = a;
-  A.oversample = oversample;
-  A.nf = grid->nf;
-  A.nc = grid->nc;
-  A.rho = grid->nf / grid->nc;
-  A.max_o = mo;
-  A.S = S;
-  A.f = grid->f;
-  A.fq = grid->f / (4.0 * (double)grid->nf * (double)grid->nf);
-  A.fH2 = grid->f / ((double)grid->nc * (double)grid->nc);
-  A.refine = precision == STOMSFEM_FP32_REFINED ? refine_iters : 0;
-  A.Ke = Ke;
-  A.be = be;
-  A.phi = phi;
-  A.status = unit_status;
-  A.ws = static_cast<unsigned char*>(workspace);
-  A.slot_bytes = sb;
-  A.l_bytes = lb;
-  A.bmax = bmax;
-  A.nmax = nmax;
-  A.units = units;
-  A.unit_list = nullptr;
-  A.unit_count = nullptr;
-  A.cell_list = nullptr;
-  A.cell_count = nullptr;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == STOMSFEM_FP32 && !phi) {
-    // FP32 without phi output: cells without oversampling take the
-    // forward-only route in a launch of their own, the others follow
-    constexpr int G = group_lanes(STOMSFEM_FP32);
-    if (!oversample) return launch_rpl<float, float, G, kModeFwd>(A, max_blocks, st);
-    const size_t lbytes = cell_list_bytes(grid);
-    const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
-    if (slots2 >= slots_per_block) {
-      const int ncell = grid->nc * grid->nc;
-      unsigned char* base = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
-      int32_t* list0 = reinterpret_cast<int32_t*>(base);
-      int32_t* list1 = list0 + ncell;
-      int32_t* counts = list1 + ncell;
-      upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, list0, list1, counts);
-      STOMSFEM_TRY_CUDA(cudaGetLastError());
-      const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
-      A.cell_list = list0;
-      A.cell_count = counts;
-      rc = launch_rpl<float, float, G, kModeFwd>(A, mb, st);
-      if (rc) return rc;
-      A.cell_list = list1;
-      A.cell_count = counts + 1;
-      return launch_rpl<float, float, G, kModeRest>(A, mb, st);
-    }
-  }
-  if (precision == STOMSFEM_FP64) return launch_rpl<double, double, group_lanes(STOMSFEM_FP64)>(A, max_blocks, st);
-  if (precision == STOMSFEM_FP32_REFINED)
-    return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED)>(A, max_blocks, st);
-  return launch_rpl<float, float, group_lanes(STOMSFEM_FP32)>(A, max_blocks, st);
+  return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, phi,
+                            unit_status, workspace, workspace_bytes, stream);
 }
 
 namespace stomsfem {
