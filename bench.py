@@ -38,8 +38,8 @@ FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
 # the H/h = 32 workload), by library version and form.
 DRAM_BYTES_PER_UNIT = {
     # FP32: the forward-only and the back-substitution launches of one call
-    ("stomsfem-gb300 0.5 (sm_103a)", "fp32"): (0.051979e9 + 0.000273e9 + 7.112449e9 + 6.768770e9) / 32768,
-    ("stomsfem-gb300 0.5 (sm_103a)", "fp64"): (1.825947e9 + 1.937501e9) / 4096,
+    ("stomsfem-gb300 0.6 (sm_103a)", "fp32"): (0.051981e9 + 0.000175e9 + 7.110618e9 + 6.763874e9) / 32768,
+    ("stomsfem-gb300 0.6 (sm_103a)", "fp64"): (1.827271e9 + 1.937667e9) / 4096,
 }
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
