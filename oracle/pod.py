@@ -139,3 +139,37 @@ def upscale(models, nf, nc, f, a):
             cx, cy = cell % nc, cell // nc
             Ke[s, cell], be[s, cell] = online_cell(models[cell], cell_coef(a[s], nc, cx, cy), f, h)
     return Ke, be
+
+
+def affine_cell_coef(nf, nc, field, xi_row, cell, local_ids):
+    """Eq. RBaffine restricted to the cell's local parameters: the affine
+    field's coefficient on the cell with every non-local xi_i set to 0."""
+    from . import sample_coef_window
+    rho = nf // nc
+    cx, cy = cell % nc, cell // nc
+    x = np.zeros_like(np.asarray(xi_row, dtype=np.float64))
+    ids = [int(i) for i in local_ids if i >= 0]
+    x[ids] = np.asarray(xi_row)[ids]
+    a = sample_coef_window(nf, field, x, cx * rho, (cx + 1) * rho, cy * rho, (cy + 1) * rho)
+    return a[cy * rho:(cy + 1) * rho, cx * rho:(cx + 1) * rho]
+
+
+def upscale_affine(models, nf, nc, f, field, xi, local_ids):
+    """Alg. 4 on the local affine coefficient of every (sample, cell):
+    K_e [S][nc*nc][10], b_e [S][nc*nc][4].  local_ids [nc*nc][16]."""
+    S = xi.shape[0]
+    Ke = np.empty((S, nc * nc, 10))
+    be = np.empty((S, nc * nc, 4))
+    h = 1.0 / nf
+    for s in range(S):
+        for cell in range(nc * nc):
+            a_cell = affine_cell_coef(nf, nc, field, xi[s], cell, local_ids[cell])
+            Ke[s, cell], be[s, cell] = online_cell(models[cell], a_cell, f, h)
+    return Ke, be
+
+
+def reduced_matrix(model, a_cell):
+    """W^T A(a) W with W = [phibar_1..4, V] (the reduced quantities of Eq.
+    localRBsystem and of the K_e assembly)."""
+    Wf = np.concatenate([model["phibar"].T, model["V"]], axis=1)
+    return Wf.T @ cell_stiffness(a_cell) @ Wf

@@ -73,7 +73,9 @@ def influence(field, d2):
     psi = math.exp(-d2 / (w * w))
     if int(field["kind"]) == 0:
         return abs(float(field.get("scale", 1.0))) * psi
-    return abs(float(field.get("contrast_log", 0.0)) * float(field.get("gain", 1.0))) / 4.0 * psi
+    if int(field["kind"]) == 1:
+        return abs(float(field.get("contrast_log", 0.0)) * float(field.get("gain", 1.0))) / 4.0 * psi
+    raise ValueError("the degree rule covers the exponential and sigmoid fields")
 
 
 def choose_nu(g, eps, nu_max):

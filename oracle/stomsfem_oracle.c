@@ -60,7 +60,8 @@ static const int CDY[4] = {0, 0, 1, 1};
 
 /* ---------------------------------------------------------------- */
 /* Coefficient sampling: a(x, xi) at fine-element centroids.          */
-/* kind 0: a = exp(scale * z);  kind 1: a = exp(L / (1 + exp(-g z))) */
+/* kind 0: a = exp(scale * z);  kind 1: a = exp(L / (1 + exp(-g z)));  */
+/* kind 2 (affine, Eq. RBaffine): a = g + scale * z                   */
 /* with z(x) = sum_i xi_i exp(-|x - c_i|^2 / w^2), c_i the lattice     */
 /* cell centres ((bx+1/2)/nbx, (by+1/2)/nby), i = by*nbx + bx.         */
 /* ---------------------------------------------------------------- */
@@ -91,6 +92,8 @@ int orc_sample_coef(int nf, int kind, int nbx, int nby, double width,
         double v;
         if (kind == 0)
           v = exp(scale * z);
+        else if (kind == 2)
+          v = gain + scale * z;
         else
           v = exp(contrast_log / (1.0 + exp(-gain * z)));
         a[((size_t)s * nf + ey) * nf + ex] = v;
@@ -122,7 +125,7 @@ int orc_sample_coef_window(int nf, int kind, int nbx, int nby, double width, dou
         }
       }
       a[(size_t)ey * nf + ex] =
-          kind == 0 ? exp(scale * z) : exp(contrast_log / (1.0 + exp(-gain * z)));
+          kind == 0 ? exp(scale * z) : kind == 2 ? gain + scale * z : exp(contrast_log / (1.0 + exp(-gain * z)));
     }
   }
   return 0;

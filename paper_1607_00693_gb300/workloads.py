@@ -4,7 +4,7 @@ This module only draws random numbers and states sizes; it holds none of
 the method's arithmetic, so both the CUDA path and the CPU oracle take
 their inputs from here.
 
-Six workloads, sized like the paper's experiments (H/h = 32 as in the
+Seven workloads, sized like the paper's experiments (H/h = 32 as in the
 short-correlation example, channel-like high-contrast media as in the
 high-contrast example):
 
@@ -18,6 +18,9 @@ high-contrast example):
 * ``pod_64``       msfem_64 grid; 200 training samples, 10^4 online samples.
 * ``surrogate_64`` msfem_64 grid; 1563 training samples (10^5 cell pairs),
                     10^5 fresh samples for inference.
+* ``pod_affine_64`` msfem_64 grid with the affine field a = 2 + z (Eq.
+                    RBaffine; a in about [0.9, 3.1]); 200 training and 10^4
+                    online samples, local parameters at tau = 1e-6.
 * ``ri_64``        msfem_64 grid; random interpolation at eps = 1e-3 (degree
                     cap 8, Legendre nodes for the uniform xi), 10^5 fresh
                     samples online.
@@ -33,6 +36,7 @@ import numpy as np
 
 FIELD_EXP = 0
 FIELD_EXP_SIGMOID = 1
+FIELD_AFFINE = 2
 
 WORKLOADS = {
     "msfem_64": dict(nf=64, nc=8, f=1.0, samples=64, seed=1, oversample=None,
@@ -51,6 +55,10 @@ WORKLOADS = {
                          train_seed=4, oversample=None,
                          field=dict(kind=FIELD_EXP, nbx=4, nby=4, width=0.1, scale=1.0,
                                     contrast_log=0.0, gain=1.0), dist="uniform"),
+    "pod_affine_64": dict(nf=64, nc=8, f=1.0, samples=10000, seed=32, train_samples=200,
+                          train_seed=6, tol=1e-6, tau=1e-6, oversample=None,
+                          field=dict(kind=FIELD_AFFINE, nbx=4, nby=4, width=0.1, scale=1.0,
+                                     contrast_log=0.0, gain=2.0), dist="uniform"),
     "ri_64": dict(nf=64, nc=8, f=1.0, samples=100000, seed=41, eps=1e-3, nu_max=8, nodes=1,
                   oversample=None,
                   field=dict(kind=FIELD_EXP, nbx=4, nby=4, width=0.1, scale=1.0,
