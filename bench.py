@@ -302,6 +302,51 @@ def bench_pod(api, dev, stream, samples=None):
     return res, 4 + 2 * 3 * 4
 
 
+def bench_pod_affine(api, dev, stream, samples=None):
+    """Affine reduced basis (Sec. 3.2.2, Eqs. RBaffine, localAF) on the 64^2 /
+    8^2 grid with the affine field: basis from 200 training samples, affine
+    parts per cell, online stage for 10^4 samples straight from xi (no fine
+    grid, no workspace) against plain FP64 upscaling of the same samples."""
+    import torch
+    w = W.workload("pod_affine_64")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    rho = nf // nc
+    Ns, S = w["train_samples"], samples or w["samples"]
+    xtr = torch.from_numpy(W.draw_xi(w["field"], Ns, w["train_seed"])).to(dev)
+    atr = torch.empty((Ns, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xtr, atr)
+    Ktr = torch.empty((Ns, nc * nc, 10), dtype=torch.float64, device=dev)
+    btr = torch.empty((Ns, nc * nc, 4), dtype=torch.float64, device=dev)
+    phi = torch.empty((Ns, nc * nc, 4, (rho + 1) ** 2), dtype=torch.float64, device=dev)
+    api.stomsfem_upscale(g, atr, Ktr, btr, phi=phi)
+    h, ranks = api.stomsfem_pod_build(g, phi, atr, tol=w["tol"], max_rank=27)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.stomsfem_pod_set_affine(h, g, fld, w["tau"], stream=stream)
+    t_aff = time.perf_counter() - t0
+    xi = torch.from_numpy(W.draw_xi(w["field"], S, w["seed"])).to(dev)
+    a = torch.empty((S, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xi, a)
+    Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+    be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=dev)
+    Kp, bp = torch.empty_like(Ke), torch.empty_like(be)
+    _, rb = api.stomsfem_upscale_workspace_size(g, 0, api.FP64)
+    wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+    units = S * nc * nc
+    ms = _timed_call(stream, lambda: api.stomsfem_pod_upscale_affine(h, g, xi, Ke, be, stream=stream))
+    ms_plain = _timed_call(stream, lambda: api.stomsfem_upscale(g, a, Kp, bp, workspace=wsu, stream=stream))
+    res = {"workload": "pod_affine_64", "samples": S, "units": units, "affine_parts_s": t_aff,
+           "rank_mean": float(sum(ranks) / len(ranks)), "units_per_s": units / (ms / 1e3), "ms": ms,
+           "fp64_plain_units_per_s": units / (ms_plain / 1e3), "speedup_vs_fp64": ms_plain / ms,
+           "Ke_rel_vs_plain": float(((Ke - Kp).norm(dim=2) / Kp.norm(dim=2)).max().item()),
+           "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:256].contiguous(), be[:256].contiguous(),
+                                                Kp[:256].contiguous(), bp[:256].contiguous(), dev)}
+    api.stomsfem_pod_destroy(h)
+    return res, 3 + 3
+
+
 def bench_surrogate(api, dev, stream, samples=None, steps=3000):
     """Learned-surrogate form (64^2 / 8^2 workload): training on 1563
     samples (10^5 cell pairs) from the plain upscaler, inference on 10^5
@@ -649,8 +694,9 @@ def main():
         extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)
         extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
         extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
+        extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
         # kernels of each form's own timed calls (outside the step's timed region)
-        for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3)):
+        for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3), ("pod_affine", n4)):
             extra[k]["gpu_launches_timed_calls"] = n
 
     cpu = None

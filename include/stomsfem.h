@@ -49,7 +49,7 @@ enum {
 };
 
 enum { STOMSFEM_FP64 = 0, STOMSFEM_FP32_REFINED = 1, STOMSFEM_FP32 = 2 };
-enum { STOMSFEM_FIELD_EXP = 0, STOMSFEM_FIELD_EXP_SIGMOID = 1 };
+enum { STOMSFEM_FIELD_EXP = 0, STOMSFEM_FIELD_EXP_SIGMOID = 1, STOMSFEM_FIELD_AFFINE = 2 };
 
 typedef struct {
   int32_t nf; /* fine elements per side */
@@ -62,7 +62,9 @@ typedef struct {
  *   z(x)  = sum_i xi_i exp(-|x - c_i|^2 / width^2),
  *           c_i = ((bx + 1/2)/nbx, (by + 1/2)/nby),  i = by*nbx + bx;
  *   EXP:          a = exp(scale * z)
- *   EXP_SIGMOID:  a = exp(contrast_log / (1 + exp(-gain * z)))           */
+ *   EXP_SIGMOID:  a = exp(contrast_log / (1 + exp(-gain * z)))
+ *   AFFINE:       a = gain + scale * z   (Eq. RBaffine: affine in xi, gain
+ *                 the mean level; positive while gain > |scale| max|z|)  */
 typedef struct {
   int32_t kind;
   int32_t nbx, nby;
@@ -292,6 +294,33 @@ int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* byte
 int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t refine_iters,
                          double* Ke, double* be, int32_t* unit_status, void* workspace,
                          size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* Affine structure of the coefficient (Sec. 3.2.2, Eqs. RBaffine and
+ * localAF) for an affine field (field->kind == STOMSFEM_FIELD_AFFINE,
+ * a = gain + scale z): with the cell's local parameters xi_m (bump i local
+ * when exp(-d^2/width^2) >= tau, as stomsfem_local_vars; the others are
+ * dropped), every reduced quantity of the handle's basis
+ * W = [phibar_1..4, V] splits as
+ *   W^T A(xi) W = gain G_0 + scale sum_k xi_k G_k,
+ *   G_0 = sum_e W_e^T K_ref W_e,  G_k = sum_e psi_k(x_e) W_e^T K_ref W_e,
+ * computed here once per cell in FP64 (stored FP32).  grid must be the
+ * handle's; EINVAL for another field kind or more than 16 local
+ * parameters.  Allocates device memory, synchronises `stream`.  The parts
+ * are not part of stomsfem_pod_save; call again after a load. */
+int stomsfem_pod_set_affine(stomsfem_pod* pod, const stomsfem_grid* grid, const stomsfem_field* field,
+                            double tau, stomsfem_stream_t stream);
+
+/* Online stage with the affine parts (Alg. 4 without the fine grid): per
+ * (sample, cell) unit the reduced quantities are assembled from xi
+ * (device [S][nbx*nby]) in shared memory, then solved as in
+ * stomsfem_pod_upscale (FP32 reduced Cholesky, K_e and b_e from the
+ * reduced quantities; refine_iters > 0 runs the FP64 stencil refinement,
+ * which needs a, device [S][nf][nf]; a may be NULL otherwise).  No
+ * workspace.  Ke [S][nc*nc][10], be [S][nc*nc][4], unit_status as
+ * stomsfem_pod_upscale.  EINVAL if stomsfem_pod_set_affine was not called. */
+int stomsfem_pod_upscale_affine(stomsfem_pod* pod, const double* xi, const double* a, int32_t S,
+                                int32_t refine_iters, double* Ke, double* be, int32_t* unit_status,
+                                stomsfem_stream_t stream);
 
 /* ---------------------------------------------------------------------
  * Learned surrogate of the local upscaled quantities (stands in for the

@@ -12,7 +12,7 @@ from .build import LIB
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTSPD, ETIMEOUT, EVERSION = 0, -1, -2, -3, -4, -5, -6
 FP64, FP32_REFINED, FP32 = 0, 1, 2
-FIELD_EXP, FIELD_EXP_SIGMOID = 0, 1
+FIELD_EXP, FIELD_EXP_SIGMOID, FIELD_AFFINE = 0, 1, 2
 
 
 class Grid(ctypes.Structure):
@@ -80,6 +80,9 @@ _SIG = {
     "stomsfem_coarse_pg_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
     "stomsfem_coarse_solve_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P, _SZ,
                                                 _P]),
+    "stomsfem_pod_set_affine": (ctypes.c_int, [_P, ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double,
+                                               _P]),
+    "stomsfem_pod_upscale_affine": (ctypes.c_int, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,

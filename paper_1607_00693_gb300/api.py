@@ -12,7 +12,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from ._lib import FP32, FP32_REFINED, FP64, FIELD_EXP, FIELD_EXP_SIGMOID, Grid, Field  # noqa: F401
+from ._lib import FP32, FP32_REFINED, FP64, FIELD_AFFINE, FIELD_EXP, FIELD_EXP_SIGMOID, Grid, Field  # noqa: F401
 
 
 def _dev(t, dtype, shape=None, name="tensor"):
@@ -417,3 +417,17 @@ def stomsfem_coarse_solve_pg(g: Grid, Ke, be, u, mean=None, m2=None, count=None,
         _dev(mean, torch.float64, (nn,), "mean"), _dev(m2, torch.float64, (nn,), "m2"),
         _dev(count, torch.float64, (1,), "count"), _dev(workspace, torch.uint8, None, "workspace"),
         workspace.numel(), _stream(stream)))
+
+
+def stomsfem_pod_set_affine(h, g: Grid, fld: Field, tau=1e-6, stream=None):
+    L.check(L.lib().stomsfem_pod_set_affine(h, ctypes.byref(g), ctypes.byref(fld), float(tau), _stream(stream)))
+
+
+def stomsfem_pod_upscale_affine(h, g: Grid, xi, Ke, be, a=None, refine_iters=0, unit_status=None, stream=None):
+    S = xi.shape[0]
+    ncell = g.nc * g.nc
+    L.check(L.lib().stomsfem_pod_upscale_affine(
+        h, _dev(xi, torch.float64, None, "xi"),
+        _dev(a, torch.float64, (S, g.nf, g.nf), "a") if a is not None else None, S, int(refine_iters),
+        _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(unit_status, torch.int32, (S, ncell), "unit_status"), _stream(stream)))

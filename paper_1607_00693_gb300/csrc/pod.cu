@@ -34,6 +34,7 @@ constexpr int kPodMaxN = 49;       // interior nodes, (rho - 1)^2
 constexpr int kPodMaxRank = 27;    // (4 + r)(5 + r)/2 <= 496 packed entries fit 512 TMEM columns
 constexpr int kPodK = 64;          // GEMM K (elements per cell, zero padded)
 constexpr int kPodTileM = 128;
+constexpr int kPodAffParts = 17;   // affine parts: the constant one and up to 16 local parameters
 
 __device__ __forceinline__ int pidx(int a, int b, int P0) {
   // packed upper-triangle index of (a, b), a <= b < P0
@@ -318,6 +319,47 @@ __global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_
   }
 }
 
+// Affine parts of the reduced quantities (Eq. localAF): for the packed
+// pair j = (alpha, beta) of W = [phibar_1..4, V],
+//   Gaff[cell][0][j] = sum_e Wfull_e,alpha^T K_ref Wfull_e,beta,
+//   Gaff[cell][k][j] = sum_e psi_k(x_e) Wfull_e,alpha^T K_ref Wfull_e,beta,
+// psi_k the k-th local bump at the element centroids (zero past the
+// cell's local parameters).  FP64 sums, stored in FP32.
+__global__ void pod_affine_parts_kernel(PodDims d, const double* __restrict__ W, const double* __restrict__ psi,
+                                        float* __restrict__ Gaff) {
+  const int cell = blockIdx.x;
+  const double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  const double* pc = psi + (size_t)cell * 16 * kPodK;
+  const int rho = d.rho;
+  for (int j = threadIdx.x; j < d.Ppad; j += blockDim.x) {
+    double acc[kPodAffParts];
+#pragma unroll
+    for (int k = 0; k < kPodAffParts; ++k) acc[k] = 0.0;
+    if (j < d.P) {
+      int a = 0, rem = j;
+      while (rem >= d.P0 - a) { rem -= d.P0 - a; ++a; }
+      const int b = a + rem;
+      for (int e = 0; e < d.ne; ++e) {
+        const int ex = e % rho, ey = e / rho;
+        const int nodes[4] = {ey * (rho + 1) + ex, ey * (rho + 1) + ex + 1, (ey + 1) * (rho + 1) + ex + 1,
+                              (ey + 1) * (rho + 1) + ex};
+        double t = 0.0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const double wa = Wc[(size_t)nodes[r] * d.P0 + a];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) t += wa * kKref[r][c] * Wc[(size_t)nodes[c] * d.P0 + b];
+        }
+        acc[0] += t;
+#pragma unroll
+        for (int k = 1; k < kPodAffParts; ++k) acc[k] += pc[(size_t)(k - 1) * kPodK + e] * t;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPodAffParts; ++k) Gaff[((size_t)cell * kPodAffParts + k) * d.Ppad + j] = (float)acc[k];
+  }
+}
+
 // ------------------------------------------------------------------ online
 
 // a [S][nf][nf] -> Ab [cell][Spad][kPodK] BF16 (zero padded rows and columns)
@@ -498,7 +540,12 @@ __device__ __forceinline__ void small_bwd(const float (&Mq)[32], float (&Fq)[4],
 struct PodSolveArgs {
   PodDims d;
   int S, Spad, refine;
-  const float* G;
+  const float* G;         // [cell][Spad][Ppad] reduced quantities, or NULL with Gaff
+  const float* Gaff;      // affine parts [cell][kPodAffParts][Ppad] (Eq. localAF), or NULL
+  const double* xi;       // [S][K] parameters (affine mode)
+  const int* aff_var;     // [cell][16] local parameter ids, -1 padded
+  int K;
+  double gain, scale;
   const double* W;
   const double* wl;
   const int32_t* ranks;
@@ -517,6 +564,8 @@ pod_solve_kernel(PodSolveArgs A) {
   __shared__ double s_c[kPodSolveWarps][32][4];
   __shared__ double s_u[kPodSolveWarps][kPodN2Max][4];
   __shared__ double s_au[kPodSolveWarps][kPodN2Max][4];
+  __shared__ float s_g[kPodSolveWarps][512];
+  __shared__ float s_coef[kPodSolveWarps][kPodAffParts];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const PodDims& d = A.d;
   const long long units = (long long)A.S * d.ncell;
@@ -535,7 +584,33 @@ pod_solve_kernel(PodSolveArgs A) {
       continue;
     }
     const int r = A.ranks[cell];
-    const float* g = A.G + ((size_t)cell * A.Spad + s) * d.Ppad;
+    const float* g;
+    if (A.Gaff) {
+      // Eq. localAF: W^T A(xi) W = gain G_0 + scale sum_k xi_k G_k, the
+      // reduced quantities of this unit assembled in shared memory
+      if (lane < kPodAffParts) {
+        float c = 0.f;
+        if (lane == 0) {
+          c = (float)A.gain;
+        } else if (lane <= 16) {
+          const int v = A.aff_var[cell * 16 + lane - 1];
+          if (v >= 0) c = (float)(A.scale * A.xi[(size_t)s * A.K + v]);
+        }
+        s_coef[wib][lane] = c;
+      }
+      __syncwarp();
+      const float* Gc = A.Gaff + (size_t)cell * kPodAffParts * d.Ppad;
+      for (int p = lane; p < d.P; p += 32) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kPodAffParts; ++k) t = fmaf(s_coef[wib][k], Gc[(size_t)k * d.Ppad + p], t);
+        s_g[wib][p] = t;
+      }
+      __syncwarp();
+      g = s_g[wib];
+    } else {
+      g = A.G + ((size_t)cell * A.Spad + s) * d.Ppad;
+    }
     // row q of V^T A V and right-hand sides -V^T A phibar_l
     float Mq[32], Fq[4];
 #pragma unroll
@@ -687,6 +762,11 @@ using namespace stomsfem;
 
 struct stomsfem_pod {
   PodDims d;
+  float* Gaff = nullptr;    // affine parts [cell][17][Ppad] (stomsfem_pod_set_affine)
+  int32_t* aff_var = nullptr;
+  int32_t* zero = nullptr;  // an error word that stays 0 (the affine online stage has no GEMM)
+  int K = 0;
+  double gain = 0.0, scale = 0.0;
   int max_rank;
   double* W = nullptr;          // [cell][N2][P0]
   double* wl = nullptr;         // [cell][P0]
@@ -698,6 +778,9 @@ struct stomsfem_pod {
 
 static void pod_free(stomsfem_pod* p) {
   if (!p) return;
+  cudaFree(p->Gaff);
+  cudaFree(p->aff_var);
+  cudaFree(p->zero);
   cudaFree(p->W);
   cudaFree(p->wl);
   cudaFree(p->lam);
@@ -956,6 +1039,11 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
   A.Spad = Spad;
   A.refine = refine_iters;
   A.G = G;
+  A.Gaff = nullptr;
+  A.xi = nullptr;
+  A.aff_var = nullptr;
+  A.K = 0;
+  A.gain = A.scale = 0.0;
   A.W = pod->W;
   A.wl = pod->wl;
   A.ranks = pod->ranks;
@@ -964,6 +1052,113 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
   A.be = be;
   A.status = unit_status;
   A.err = pod->err;
+  const long long units = (long long)S * d.ncell;
+  long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
+  if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+  pod_solve_kernel<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_set_affine(stomsfem_pod* pod, const stomsfem_grid* grid, const stomsfem_field* field,
+                                       double tau, stomsfem_stream_t stream) {
+  if (!pod || !grid || !field) return set_error(STOMSFEM_EINVAL, "NULL argument");
+  const PodDims& d = pod->d;
+  if (grid->nf != d.nf || grid->nc != d.nc) return set_error(STOMSFEM_EINVAL, "grid does not match the POD handle");
+  if (field->kind != STOMSFEM_FIELD_AFFINE)
+    return set_error(STOMSFEM_EINVAL, "the affine reduced basis needs an affine field (kind %d)", STOMSFEM_FIELD_AFFINE);
+  if (!(field->width > 0.0) || field->nbx <= 0 || field->nby <= 0) return set_error(STOMSFEM_EINVAL, "bad field");
+  const int ncell = d.ncell, rho = d.rho;
+  std::vector<int32_t> kc(ncell), ids((size_t)ncell * 16), fam(ncell);
+  int32_t nfam = 0;
+  int rc = stomsfem_local_vars(grid, field, tau, kc.data(), ids.data(), fam.data(), &nfam);
+  if (rc) return rc;
+  // local bumps at the element centroids of every cell
+  std::vector<double> psi((size_t)ncell * 16 * kPodK, 0.0);
+  const double w2 = field->width * field->width;
+  for (int cell = 0; cell < ncell; ++cell) {
+    const int cx = cell % d.nc, cy = cell / d.nc;
+    for (int k = 0; k < kc[cell]; ++k) {
+      const int v = ids[(size_t)cell * 16 + k];
+      const double px = (v % field->nbx + 0.5) / field->nbx, py = (v / field->nbx + 0.5) / field->nby;
+      for (int e = 0; e < d.ne; ++e) {
+        const double x = (cx * rho + e % rho + 0.5) / d.nf, y = (cy * rho + e / rho + 0.5) / d.nf;
+        psi[((size_t)cell * 16 + k) * kPodK + e] = std::exp(-((x - px) * (x - px) + (y - py) * (y - py)) / w2);
+      }
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* psi_d = nullptr;
+  cudaFree(pod->Gaff);
+  cudaFree(pod->aff_var);
+  cudaFree(pod->zero);
+  pod->Gaff = nullptr;
+  pod->aff_var = nullptr;
+  pod->zero = nullptr;
+  auto fail = [&](int code) {
+    cudaFree(psi_d);
+    cudaFree(pod->Gaff);
+    cudaFree(pod->aff_var);
+    cudaFree(pod->zero);
+    pod->Gaff = nullptr;
+    pod->aff_var = nullptr;
+    pod->zero = nullptr;
+    return code;
+  };
+#define TRY(x)                                   \
+  if ((rc = check_cuda((x), #x)) != STOMSFEM_OK) \
+    return fail(rc);
+  TRY(cudaMalloc(&psi_d, sizeof(double) * psi.size()));
+  TRY(cudaMalloc(&pod->Gaff, sizeof(float) * (size_t)ncell * kPodAffParts * d.Ppad));
+  TRY(cudaMalloc(&pod->aff_var, sizeof(int32_t) * ids.size()));
+  TRY(cudaMalloc(&pod->zero, sizeof(int32_t)));
+  TRY(cudaMemsetAsync(pod->zero, 0, sizeof(int32_t), st));
+  TRY(cudaMemcpyAsync(psi_d, psi.data(), sizeof(double) * psi.size(), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(pod->aff_var, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, st));
+  pod_affine_parts_kernel<<<ncell, 128, 0, st>>>(d, pod->W, psi_d, pod->Gaff);
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(st));
+#undef TRY
+  cudaFree(psi_d);
+  pod->K = field->nbx * field->nby;
+  pod->gain = field->gain;
+  pod->scale = field->scale;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_upscale_affine(stomsfem_pod* pod, const double* xi, const double* a, int32_t S,
+                                           int32_t refine_iters, double* Ke, double* be, int32_t* unit_status,
+                                           stomsfem_stream_t stream) {
+  if (!pod) return set_error(STOMSFEM_EINVAL, "pod is NULL");
+  if (!pod->Gaff) return set_error(STOMSFEM_EINVAL, "stomsfem_pod_set_affine was not called on this handle");
+  if (S < 0 || refine_iters < 0 || refine_iters > 16) return set_error(STOMSFEM_EINVAL, "bad S / refine_iters");
+  if (S == 0) return STOMSFEM_OK;
+  if (!xi || !Ke || !be) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  if (refine_iters > 0 && !a) return set_error(STOMSFEM_EINVAL, "refinement needs the coefficient a");
+  const PodDims& d = pod->d;
+  if (d.Ppad > 512) return set_error(STOMSFEM_EINVAL, "reduced size %d > 512", d.Ppad);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  PodSolveArgs A;
+  A.d = d;
+  A.S = S;
+  A.Spad = 0;
+  A.refine = refine_iters;
+  A.G = nullptr;
+  A.Gaff = pod->Gaff;
+  A.xi = xi;
+  A.aff_var = pod->aff_var;
+  A.K = pod->K;
+  A.gain = pod->gain;
+  A.scale = pod->scale;
+  A.W = pod->W;
+  A.wl = pod->wl;
+  A.ranks = pod->ranks;
+  A.a = a;
+  A.Ke = Ke;
+  A.be = be;
+  A.status = unit_status;
+  A.err = pod->zero;
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
   const long long units = (long long)S * d.ncell;
   long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
   if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;

@@ -69,6 +69,8 @@ sample_coef_kernel(int nf, int kind, int nbx, int nby, int R, double w, double s
       double v;
       if (kind == STOMSFEM_FIELD_EXP)
         v = fexp(scale * z, tab);
+      else if (kind == STOMSFEM_FIELD_AFFINE)
+        v = fma(scale, z, gain);
       else
         v = fexp(clog / (1.0 + fexp(-gain * z, tab)), tab);
       arow[(size_t)r * nf] = v;
@@ -119,7 +121,9 @@ sample_coef_f32_kernel(int nf, int kind, int nbx, int nby, int R, float w, float
 #pragma unroll
       for (int bx = 0; bx < NBX; ++bx)
         if (bx < nbx) z = fmaf(gx[bx], U[bx * R + r], z);
-      const float v = kind == STOMSFEM_FIELD_EXP ? expf(scale * z) : expf(clog / (1.0f + expf(-gain * z)));
+      const float v = kind == STOMSFEM_FIELD_EXP      ? expf(scale * z)
+                      : kind == STOMSFEM_FIELD_AFFINE ? fmaf(scale, z, gain)
+                                                      : expf(clog / (1.0f + expf(-gain * z)));
       arow[(size_t)r * nf] = (double)v;
     }
   }
@@ -135,7 +139,8 @@ static int sample_coef_impl(const stomsfem_grid* grid, const stomsfem_field* fie
   if (grid->nf <= 0 || S < 0) return set_error(STOMSFEM_EINVAL, "bad nf or S");
   if (precision != STOMSFEM_FP64 && precision != STOMSFEM_FP32)
     return set_error(STOMSFEM_EINVAL, "sampling precision must be STOMSFEM_FP64 or STOMSFEM_FP32");
-  if (field->kind != STOMSFEM_FIELD_EXP && field->kind != STOMSFEM_FIELD_EXP_SIGMOID)
+  if (field->kind != STOMSFEM_FIELD_EXP && field->kind != STOMSFEM_FIELD_EXP_SIGMOID &&
+      field->kind != STOMSFEM_FIELD_AFFINE)
     return set_error(STOMSFEM_EINVAL, "unknown field kind %d", field->kind);
   if (field->nbx <= 0 || field->nby <= 0 || field->nbx > kMaxBumps || field->nby > kMaxBumps)
     return set_error(STOMSFEM_EINVAL, "bump lattice %dx%d outside 1..%d per side", field->nbx,
