@@ -453,17 +453,25 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
 }
 
 // ---- warp r x r Cholesky with 4 right-hand sides (lane q owns row q)
+// Broadcasts go through a per-warp shared scratch sw[40] (a 16-byte
+// aligned float array): sw[0..31] a column or row, sw[32] a pivot,
+// sw[36..39] the pivot row's right-hand sides.
 
 template <int J>
-__device__ __forceinline__ void small_chol(float (&Mq)[32], float (&Fq)[4], int lane, int r, bool& bad) {
+__device__ __forceinline__ void small_chol(float (&Mq)[32], float (&Fq)[4], int lane, int r, bool& bad,
+                                           float* sw) {
   if constexpr (J < 32) {
     if (J < r) {
-      const float dj = __shfl_sync(0xffffffffu, Mq[J], J);
+      if (lane == J) {
+        sw[32] = Mq[J];
+        *reinterpret_cast<float4*>(sw + 36) = make_float4(Fq[0], Fq[1], Fq[2], Fq[3]);
+      }
+      __syncwarp();
+      const float dj = sw[32];
       if (!(dj > 0.f)) bad = true;
       const float dinv = rsqrtf(dj > 0.f ? dj : 1.f);
-      float yj[4];
-#pragma unroll
-      for (int l = 0; l < 4; ++l) yj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
+      const float4 f4 = *reinterpret_cast<const float4*>(sw + 36);
+      const float yj[4] = {f4.x * dinv, f4.y * dinv, f4.z * dinv, f4.w * dinv};
       const float lj = (lane > J && lane < r) ? Mq[J] * dinv : 0.f;
       if (lane > J && lane < r) {
         Mq[J] = lj;
@@ -475,25 +483,29 @@ __device__ __forceinline__ void small_chol(float (&Mq)[32], float (&Fq)[4], int 
 #pragma unroll
         for (int l = 0; l < 4; ++l) Fq[l] = yj[l];
       }
+      sw[lane] = lj;  // the pivot column, zero at and above the pivot
+      __syncwarp();
 #pragma unroll
-      for (int p = J + 1; p < 32; ++p) {
-        const float lp = __shfl_sync(0xffffffffu, lj, p);
-        Mq[p] -= lj * lp;
-      }
+      for (int p = J + 1; p < 32; ++p) Mq[p] -= lj * sw[p];
+      __syncwarp();
     }
-    small_chol<J + 1>(Mq, Fq, lane, r, bad);
+    small_chol<J + 1>(Mq, Fq, lane, r, bad, sw);
   }
 }
 
 // forward (L y = f) with the stored factor, lane q holds f_q / y_q
 template <int J>
-__device__ __forceinline__ void small_fwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r) {
+__device__ __forceinline__ void small_fwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r, float* sw) {
   if constexpr (J < 32) {
     if (J < r) {
-      const float dinv = __shfl_sync(0xffffffffu, Mq[J], J);
-      float yj[4];
-#pragma unroll
-      for (int l = 0; l < 4; ++l) yj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
+      if (lane == J) {
+        sw[32] = Mq[J];
+        *reinterpret_cast<float4*>(sw + 36) = make_float4(Fq[0], Fq[1], Fq[2], Fq[3]);
+      }
+      __syncwarp();
+      const float dinv = sw[32];
+      const float4 f4 = *reinterpret_cast<const float4*>(sw + 36);
+      const float yj[4] = {f4.x * dinv, f4.y * dinv, f4.z * dinv, f4.w * dinv};
       if (lane > J && lane < r) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) Fq[l] -= Mq[J] * yj[l];
@@ -502,29 +514,31 @@ __device__ __forceinline__ void small_fwd(const float (&Mq)[32], float (&Fq)[4],
 #pragma unroll
         for (int l = 0; l < 4; ++l) Fq[l] = yj[l];
       }
+      __syncwarp();
     }
-    small_fwd<J + 1>(Mq, Fq, lane, r);
+    small_fwd<J + 1>(Mq, Fq, lane, r, sw);
   }
 }
 
 // backward (L^T x = y), column oriented: lane q holds y_q then x_q.  The
-// entry L[p][q] lives in lane p's row at position q.
+// entry L[p][q] lives in lane p's row at position q; lane J publishes its
+// row for the lanes q < J.
 template <int J>
-__device__ __forceinline__ void small_bwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r) {
+__device__ __forceinline__ void small_bwd(const float (&Mq)[32], float (&Fq)[4], int lane, int r, float* sw) {
   if constexpr (J >= 0) {
     if (J < r) {
-      const float dinv = __shfl_sync(0xffffffffu, Mq[J], J);
-      float xj[4];
+      if (lane == J) {
 #pragma unroll
-      for (int l = 0; l < 4; ++l) xj[l] = __shfl_sync(0xffffffffu, Fq[l], J) * dinv;
-      // lanes q < J need L[J][q] from lane J
-      float lq = 0.f;
-#pragma unroll
-      for (int q = 0; q < J; ++q) {
-        const float v = __shfl_sync(0xffffffffu, Mq[q], J);
-        if (lane == q) lq = v;
+        for (int q = 0; q < J; ++q) sw[q] = Mq[q];
+        sw[32] = Mq[J];
+        *reinterpret_cast<float4*>(sw + 36) = make_float4(Fq[0], Fq[1], Fq[2], Fq[3]);
       }
+      __syncwarp();
+      const float dinv = sw[32];
+      const float4 f4 = *reinterpret_cast<const float4*>(sw + 36);
+      const float xj[4] = {f4.x * dinv, f4.y * dinv, f4.z * dinv, f4.w * dinv};
       if (lane < J) {
+        const float lq = sw[lane];
 #pragma unroll
         for (int l = 0; l < 4; ++l) Fq[l] -= lq * xj[l];
       }
@@ -532,8 +546,9 @@ __device__ __forceinline__ void small_bwd(const float (&Mq)[32], float (&Fq)[4],
 #pragma unroll
         for (int l = 0; l < 4; ++l) Fq[l] = xj[l];
       }
+      __syncwarp();
     }
-    small_bwd<J - 1>(Mq, Fq, lane, r);
+    small_bwd<J - 1>(Mq, Fq, lane, r, sw);
   }
 }
 
@@ -566,6 +581,7 @@ pod_solve_kernel(PodSolveArgs A) {
   __shared__ double s_au[kPodSolveWarps][kPodN2Max][4];
   __shared__ float s_g[kPodSolveWarps][512];
   __shared__ float s_coef[kPodSolveWarps][kPodAffParts];
+  __shared__ __align__(16) float s_w[kPodSolveWarps][40];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const PodDims& d = A.d;
   const long long units = (long long)A.S * d.ncell;
@@ -622,8 +638,8 @@ pod_solve_kernel(PodSolveArgs A) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) Fq[l] = (lane < r) ? -g[pidx(l, 4 + lane, P0)] : 0.f;
     bool bad = false;
-    small_chol<0>(Mq, Fq, lane, r, bad);
-    small_bwd<31>(Mq, Fq, lane, r);
+    small_chol<0>(Mq, Fq, lane, r, bad, s_w[wib]);
+    small_bwd<31>(Mq, Fq, lane, r, s_w[wib]);
     const double* Wc = A.W + (size_t)cell * d.N2 * P0;
     const double* wl = A.wl + (size_t)cell * P0;
     double Kv[10], bv[4];
@@ -706,8 +722,8 @@ pod_solve_kernel(PodSolveArgs A) {
 #pragma unroll
           for (int l = 0; l < 4; ++l) Rq[l] = (float)(-t[l]);
         }
-        small_fwd<0>(Mq, Rq, lane, r);
-        small_bwd<31>(Mq, Rq, lane, r);
+        small_fwd<0>(Mq, Rq, lane, r, s_w[wib]);
+        small_bwd<31>(Mq, Rq, lane, r, s_w[wib]);
         if (lane < r) {
 #pragma unroll
           for (int l = 0; l < 4; ++l) cq[l] += (double)Rq[l];
