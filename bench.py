@@ -347,6 +347,69 @@ def bench_pod_affine(api, dev, stream, samples=None):
     return res, 3 + 3
 
 
+def bench_two_level(api, dev, stream, n0=10000, n1=256):
+    """Two-level Monte Carlo (Eq. MCmean2level) on the 64^2 / 8^2 grid:
+    N_0 = 10^4 coarse samples (random interpolation online + coarse solve),
+    N_1 = 256 independent samples on both levels (fine Q1 FEM on the GPU
+    and the coarse solution), against plain Monte Carlo with the same 256
+    fine solves: the sampling standard deviation of the mean (root of the
+    node-averaged variance of the estimator)."""
+    import torch
+    w = W.workload("ri_64")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    nn = (nc + 1) ** 2
+    h, _ = api.stomsfem_ri_build(g, fld, w["eps"], w["nu_max"], w["nodes"], stream=stream)
+
+    def mom():
+        return [torch.zeros(nn, dtype=torch.float64, device=dev), torch.zeros(nn, dtype=torch.float64, device=dev),
+                torch.zeros(1, dtype=torch.float64, device=dev)]
+
+    def coarse_ri(xi, S, m):
+        Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+        be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=dev)
+        fb = torch.empty((S, nc * nc), dtype=torch.uint8, device=dev)
+        u = torch.empty((S, nn), dtype=torch.float64, device=dev)
+        api.stomsfem_ri_upscale(h, g, xi, None, Ke, be, fb, stream=stream)
+        api.stomsfem_coarse_solve(g, Ke, be, u, *m, stream=stream)
+        return u
+
+    x0 = torch.from_numpy(W.draw_xi(w["field"], n0, 501)).to(dev)
+    x1 = torch.from_numpy(W.draw_xi(w["field"], n1, 502)).to(dev)
+    a1 = torch.empty((n1, nf, nf), dtype=torch.float64, device=dev)
+    uh = torch.empty((n1, (nf + 1) ** 2), dtype=torch.float64, device=dev)
+    wsf = torch.empty(api.stomsfem_fine_fem_workspace_size(g, n1), dtype=torch.uint8, device=dev)
+    d = torch.empty((n1, nn), dtype=torch.float64, device=dev)
+    uhc = torch.empty((n1, nn), dtype=torch.float64, device=dev)
+    m0, m1, mp = mom(), mom(), mom()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        coarse_ri(x0, n0, m0)
+        e[1].record(stream)
+        api.stomsfem_sample_coef(g, fld, x1, a1, stream=stream)
+        api.stomsfem_fine_fem(g, a1, uh, workspace=wsf, stream=stream)
+        uH1 = coarse_ri(x1, n1, [None, None, None])
+        api.stomsfem_restrict_to_coarse(g, uh, d, u_coarse=uH1, stream=stream)
+        api.stomsfem_mc_moments(d, *m1, stream=stream)
+        e[2].record(stream)
+        api.stomsfem_restrict_to_coarse(g, uh, uhc, stream=stream)
+        api.stomsfem_mc_moments(uhc, *mp, stream=stream)
+    stream.synchronize()
+    sd2 = float(((m0[1] / n0 / n0) + (m1[1] / n1 / n1)).mean().sqrt().item())
+    sdp = float((mp[1] / n1 / n1).mean().sqrt().item())
+    diff = float(((m0[0] + m1[0]) - mp[0]).norm().item() / mp[0].norm().item())
+    api.stomsfem_ri_destroy(h)
+    return {"workload": "ri_64 grid, level 0 by random interpolation", "n0_coarse": n0, "n1_fine": n1,
+            "level0_ms": e[0].elapsed_time(e[1]), "level1_ms": e[1].elapsed_time(e[2]),
+            "fine_fem_samples_per_s": n1 / (e[1].elapsed_time(e[2]) / 1e3),
+            "sd_of_mean_two_level": sd2, "sd_of_mean_plain_mc_same_fine_solves": sdp,
+            "variance_reduction": (sdp / sd2) ** 2 if sd2 > 0 else None,
+            "two_level_vs_plain_mean_rel": diff}
+
+
 def bench_surrogate(api, dev, stream, samples=None, steps=3000):
     """Learned-surrogate form (64^2 / 8^2 workload): training on 1563
     samples (10^5 cell pairs) from the plain upscaler, inference on 10^5
@@ -695,6 +758,7 @@ def main():
         extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
         extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
         extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
+        extra["two_level_mc"] = bench_two_level(api, dev, stream)
         # kernels of each form's own timed calls (outside the step's timed region)
         for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3), ("pod_affine", n4)):
             extra[k]["gpu_launches_timed_calls"] = n

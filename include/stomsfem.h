@@ -203,6 +203,38 @@ int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const dou
                           int32_t S, double* u, double* mean, double* m2, double* count,
                           void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Two-level Monte Carlo (Remark in Sec. 4.1.1, Eq. MCmean2level):
+ *   M2 = mean over N_H samples of u_H
+ *      + mean over N_h other samples of (u_h - u_H at the coarse nodes),
+ * u_h the standard Q1 FEM on the fine grid.  The pieces below compose it:
+ * stomsfem_coarse_solve (u_H and its moments), stomsfem_fine_fem (u_h),
+ * stomsfem_restrict_to_coarse (the differences) and stomsfem_mc_moments.
+ * ------------------------------------------------------------------- */
+
+/* Scratch needed by stomsfem_fine_fem. */
+int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
+
+/* Standard Q1 FEM on the fine grid with zero Dirichlet data and load f
+ * (element matrices a_e K_ref, load f h^2/4 per element corner), one warp
+ * per sample on the blocked banded Cholesky of the coarse solve.
+ * a device [S][nf][nf], u device [S][(nf+1)^2] (boundary entries 0; NaN
+ * for a sample whose matrix is not positive definite).  EINVAL for
+ * nf > 64 (the band limit of the solver). */
+int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int32_t S, double* u, void* workspace,
+                      size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* d [S][(nc+1)^2] = u_fine [S][(nf+1)^2] at the coarse nodes, minus
+ * u_coarse [S][(nc+1)^2] when it is not NULL (device arrays). */
+int stomsfem_restrict_to_coarse(const stomsfem_grid* grid, const double* u_fine, const double* u_coarse,
+                                int32_t S, double* d, stomsfem_stream_t stream);
+
+/* Running Monte Carlo moments of S samples u [S][n] (device) merged into
+ * mean [n], m2 [n] and count [1] (device, zero before the first batch), as
+ * stomsfem_coarse_solve does for its solutions. */
+int stomsfem_mc_moments(int32_t n, int32_t S, const double* u, double* mean, double* m2, double* count,
+                        stomsfem_stream_t stream);
+
 /* Petrov-Galerkin form of stomsfem_upscale (Eq. stiffness_local_petrov;
  * the form the paper uses with oversampling): same cell problems, same
  * arguments, but the test functions are the cell's bilinear nodal

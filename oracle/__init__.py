@@ -20,6 +20,9 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
 * ``fine_fem``      -- standard Q1 FEM on the fine grid; C code.
 * ``mc_moments``    -- Monte Carlo mean and variance (Eq. MCestimate),
                         two-pass.
+* ``two_level_mean`` -- the two-level estimator of Eq. MCmean2level with
+                        ``restrict_to_coarse`` (fine solution at the coarse
+                        nodes).
 * ``pod``           -- reduced basis by KL of the basis functions in the
                         energy inner product (Eq. KLphi) and the Galerkin
                         reduced system (Eqs. localRB, localRBsystem).
@@ -229,6 +232,23 @@ def band_solve_dense(A, bw, b):
     if rc != 0:
         raise ValueError("orc_band_solve_dense failed: %d" % rc)
     return x
+
+
+def restrict_to_coarse(u_fine, nf, nc):
+    """u_fine [S][(nf+1)^2] at the coarse nodes -> [S][(nc+1)^2]."""
+    rho = nf // nc
+    S = u_fine.shape[0]
+    return u_fine.reshape(S, nf + 1, nf + 1)[:, ::rho, ::rho].reshape(S, -1)
+
+
+def two_level_mean(uH_0, uh_1, uH_1):
+    """Eq. MCmean2level: mean of u_H over the level-0 samples plus the mean
+    of (u_h - u_H) over the level-1 samples (u_h at the coarse nodes); also
+    the sampling variance estimate var_0/N_0 + var_1/N_1 per node."""
+    d = uh_1 - uH_1
+    est = uH_0.mean(axis=0) + d.mean(axis=0)
+    var = uH_0.var(axis=0) / uH_0.shape[0] + d.var(axis=0) / d.shape[0]
+    return est, var
 
 
 def mc_moments(u):

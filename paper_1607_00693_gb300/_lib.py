@@ -83,6 +83,10 @@ _SIG = {
     "stomsfem_pod_set_affine": (ctypes.c_int, [_P, ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double,
                                                _P]),
     "stomsfem_pod_upscale_affine": (ctypes.c_int, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "stomsfem_fine_fem_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_fine_fem": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _I, _P, _P, _SZ, _P]),
+    "stomsfem_restrict_to_coarse": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P]),
+    "stomsfem_mc_moments": (ctypes.c_int, [_I, _I, _P, _P, _P, _P, _P]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,

@@ -431,3 +431,35 @@ def stomsfem_pod_upscale_affine(h, g: Grid, xi, Ke, be, a=None, refine_iters=0, 
         _dev(a, torch.float64, (S, g.nf, g.nf), "a") if a is not None else None, S, int(refine_iters),
         _dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
         _dev(unit_status, torch.int32, (S, ncell), "unit_status"), _stream(stream)))
+
+
+def stomsfem_fine_fem_workspace_size(g: Grid, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_fine_fem_workspace_size(ctypes.byref(g), int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_fine_fem(g: Grid, a, u, workspace=None, stream=None):
+    S = a.shape[0]
+    if workspace is None:
+        workspace = torch.empty(stomsfem_fine_fem_workspace_size(g, S), dtype=torch.uint8, device=a.device)
+    L.check(L.lib().stomsfem_fine_fem(
+        ctypes.byref(g), _dev(a, torch.float64, (S, g.nf, g.nf), "a"), S,
+        _dev(u, torch.float64, (S, (g.nf + 1) ** 2), "u"), _dev(workspace, torch.uint8, None, "workspace"),
+        workspace.numel(), _stream(stream)))
+
+
+def stomsfem_restrict_to_coarse(g: Grid, u_fine, d, u_coarse=None, stream=None):
+    S = u_fine.shape[0]
+    nn = (g.nc + 1) ** 2
+    L.check(L.lib().stomsfem_restrict_to_coarse(
+        ctypes.byref(g), _dev(u_fine, torch.float64, (S, (g.nf + 1) ** 2), "u_fine"),
+        _dev(u_coarse, torch.float64, (S, nn), "u_coarse") if u_coarse is not None else None, S,
+        _dev(d, torch.float64, (S, nn), "d"), _stream(stream)))
+
+
+def stomsfem_mc_moments(u, mean, m2, count, stream=None):
+    S, n = u.shape
+    L.check(L.lib().stomsfem_mc_moments(
+        int(n), int(S), _dev(u, torch.float64, (S, n), "u"), _dev(mean, torch.float64, (n,), "mean"),
+        _dev(m2, torch.float64, (n,), "m2"), _dev(count, torch.float64, (1,), "count"), _stream(stream)))

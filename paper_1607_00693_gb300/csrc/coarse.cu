@@ -64,6 +64,102 @@ struct CoarseBlkGen {
 
 constexpr int kCoarseBlkWarps = 2;
 
+// Row generator of the standard Q1 FEM on the fine grid (the u_h of the
+// two-level estimator, Eq. MCmean2level): the element matrices are
+// a_e K_ref, so a row's five band entries come from the four elements
+// around the node (SW, SE, NE, NW of the node), and its load is f h^2.
+struct FineFemGen {
+  const double* a;  // this sample [nf][nf]
+  int nf, mx;       // mx = nf - 1 interior nodes per row
+  double fh2;       // f h^2
+  static constexpr int kRaw = 4;
+  struct Raw {
+    double sw, se, ne, nw;
+  };
+  __device__ __forceinline__ void load(int r, Raw& w) const {
+    const int J = r / mx + 1, I = r - (J - 1) * mx + 1;
+    w.sw = __ldg(a + (size_t)(J - 1) * nf + I - 1);
+    w.se = __ldg(a + (size_t)(J - 1) * nf + I);
+    w.ne = __ldg(a + (size_t)J * nf + I);
+    w.nw = __ldg(a + (size_t)J * nf + I - 1);
+  }
+  __device__ __forceinline__ void prefetch(int r, double* dst) const {
+    Raw w;
+    load(r, w);
+    dst[0] = w.sw;
+    dst[1] = w.se;
+    dst[2] = w.ne;
+    dst[3] = w.nw;
+  }
+  __device__ __forceinline__ void from_smem(const double* src, Raw& w) const {
+    w.sw = src[0];
+    w.se = src[1];
+    w.ne = src[2];
+    w.nw = src[3];
+  }
+  // K_ref = [4 -1 -2 -1; -1 4 -1 -2; -2 -1 4 -1; -1 -2 -1 4] / 6 (SW, SE, NE, NW)
+  template <typename T, int NR = 1>
+  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const {
+    const int J = r / mx + 1, I = r - (J - 1) * mx + 1;
+    const double s6 = 1.0 / 6.0;
+    e[0] = (T)(4.0 * s6 * (w.sw + w.se + w.ne + w.nw));
+    e[1] = (T)(I > 1 ? -s6 * (w.sw + w.nw) : 0.0);                 // west
+    e[2] = (T)((I < mx && J > 1) ? -2.0 * s6 * w.se : 0.0);        // south-east
+    e[3] = (T)(J > 1 ? -s6 * (w.sw + w.se) : 0.0);                 // south
+    e[4] = (T)((I > 1 && J > 1) ? -2.0 * s6 * w.sw : 0.0);         // south-west
+    rh[0] = (T)fh2;
+  }
+};
+
+template <int RPL>
+__global__ void __launch_bounds__(kCoarseBlkWarps * 32)
+fine_fem_kernel(int nf, int S, double f, const double* __restrict__ a, double* __restrict__ u, unsigned char* ws,
+                size_t slot_bytes, size_t l_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int mx = nf - 1, n = mx * mx, b = nf;
+  const BlkSmem<double> sm = make_blk<double>(smem + wib * blk_smem_bytes<double>(16, b), 16, b);
+  const int gw = blockIdx.x * kCoarseBlkWarps + wib, nw = gridDim.x * kCoarseBlkWarps;
+  unsigned char* slot = ws + (size_t)gw * slot_bytes;
+  double* Lg = reinterpret_cast<double*>(slot);
+  double* x = reinterpret_cast<double*>(slot + l_bytes);
+  const int NN = nf + 1;
+  const double h = 1.0 / nf;
+  for (int s = gw; s < S; s += nw) {
+    const FineFemGen gen{a + (size_t)s * nf * nf, nf, mx, f * h * h};
+    int fail = -1;
+    if (n > 0) {
+      fail = blk_factor<32, double, 1, RPL>(gen, n, b, b, sm, Lg, x, lane);
+      blk_backward<32, double, 1>(n, b, b, sm, Lg, x, lane);
+    }
+    __syncwarp();
+    double* us = u + (size_t)s * NN * NN;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    for (int q = lane; q < NN * NN; q += 32) {
+      const int I = q % NN, J = q / NN;
+      double v = 0.0;
+      if (I > 0 && J > 0 && I < nf && J < nf) v = fail < 0 ? x[(J - 1) * mx + (I - 1)] : nanv;
+      us[q] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// d[s][coarse node] = u_fine at that node (minus u_coarse when given).
+__global__ void restrict_kernel(int nf, int nc, int S, const double* __restrict__ uf, const double* __restrict__ uc,
+                                double* __restrict__ d) {
+  const int NC = nc + 1, NF = nf + 1, rho = nf / nc;
+  const long long total = (long long)S * NC * NC;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / (NC * NC)), q = (int)(i % (NC * NC));
+    const int I = q % NC, J = q / NC;
+    double v = uf[(size_t)s * NF * NF + (size_t)(J * rho) * NF + I * rho];
+    if (uc) v -= uc[i];
+    d[i] = v;
+  }
+}
+
 template <int RPL>
 __global__ void __launch_bounds__(kCoarseBlkWarps * 32)
 coarse_blk_kernel(int nc, int S, const double* __restrict__ Ke, const double* __restrict__ be,
@@ -363,5 +459,70 @@ extern "C" int stomsfem_coarse_solve_pg(const stomsfem_grid* grid, const double*
     count_kernel<<<1, 1, 0, st>>>(count, S);
     STOMSFEM_TRY_CUDA(cudaGetLastError());
   }
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes) {
+  if (!grid || grid->nf <= 0 || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  const int sms = device_sm_count();
+  long long slots = (long long)(sms > 0 ? sms : 152) * 8;
+  if (slots > S) slots = S;
+  if (slots < kCoarseBlkWarps) slots = kCoarseBlkWarps;
+  *bytes = coarse_slot_bytes(grid->nf) * (size_t)slots;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int32_t S, double* u, void* workspace,
+                                 size_t workspace_bytes, stomsfem_stream_t stream) {
+  if (!grid || grid->nf <= 0) return set_error(STOMSFEM_EINVAL, "bad grid");
+  if (grid->nf > 64) return set_error(STOMSFEM_EINVAL, "nf %d > 64 (fine-grid bandwidth limit)", grid->nf);
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (S == 0) return STOMSFEM_OK;
+  if (!a || !u || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  const int nf = grid->nf;
+  const size_t sb = coarse_slot_bytes(nf);
+  long long slots = (long long)(workspace_bytes / sb);
+  if (slots < kCoarseBlkWarps)
+    return set_error(STOMSFEM_ENOMEM, "fine FEM workspace %zu < %d slots of %zu", workspace_bytes, kCoarseBlkWarps, sb);
+  long long blocks = slots / kCoarseBlkWarps;
+  const long long need = ((long long)S + kCoarseBlkWarps - 1) / kCoarseBlkWarps;
+  if (blocks > need) blocks = need;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = blk_smem_bytes<double>(16, nf) * kCoarseBlkWarps;
+  const int rpl = (16 + nf + 31) / 32;
+  auto kern = rpl <= 1 ? fine_fem_kernel<1> : rpl == 2 ? fine_fem_kernel<2> : fine_fem_kernel<3>;
+  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)blocks, kCoarseBlkWarps * 32, smem, st>>>(nf, S, grid->f, a, u, static_cast<unsigned char*>(workspace),
+                                                             sb, coarse_l_bytes(nf));
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_restrict_to_coarse(const stomsfem_grid* grid, const double* u_fine, const double* u_coarse,
+                                           int32_t S, double* d, stomsfem_stream_t stream) {
+  if (!grid || grid->nf <= 0 || grid->nc <= 0 || grid->nf % grid->nc) return set_error(STOMSFEM_EINVAL, "bad grid");
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (S == 0) return STOMSFEM_OK;
+  if (!u_fine || !d) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long total = (long long)S * (grid->nc + 1) * (grid->nc + 1);
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  long long blocks = (total + 255) / 256;
+  if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+  restrict_kernel<<<(unsigned)blocks, 256, 0, st>>>(grid->nf, grid->nc, S, u_fine, u_coarse, d);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_mc_moments(int32_t n, int32_t S, const double* u, double* mean, double* m2, double* count,
+                                   stomsfem_stream_t stream) {
+  if (n <= 0 || S < 0) return set_error(STOMSFEM_EINVAL, "bad n / S");
+  if (S == 0) return STOMSFEM_OK;
+  if (!u || !mean || !m2 || !count) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  moments_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, S, u, mean, m2, count);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  count_kernel<<<1, 1, 0, st>>>(count, S);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }

@@ -354,3 +354,26 @@ def test_field_window_matches_full_field(orc):
     win = orc.sample_coef_window(24, field, xi[0], 5, 17, 3, 11)
     np.testing.assert_array_equal(win[3:11, 5:17], full[3:11, 5:17])
     assert np.isnan(win[0, 0])
+
+
+def test_two_level_estimator_telescopes():
+    """Eq. MCmean2level with the same samples on both levels is the plain
+    fine-grid mean; the coarse-node restriction picks every rho-th node."""
+    import oracle
+    oracle.build()
+    nf, nc = 32, 4
+    fld = dict(kind=0, nbx=4, nby=4, width=0.1, scale=1.0)
+    a = oracle.sample_coef(nf, fld, W.draw_xi(fld, 6, 41))
+    Ke, be = oracle.upscale(nf, nc, 1.0, a)
+    uH = oracle.coarse_solve(nc, Ke, be)
+    uh = np.stack([oracle.fine_fem(nf, 1.0, a[s]) for s in range(6)])
+    uhc = oracle.restrict_to_coarse(uh, nf, nc)
+    assert uhc.shape == uH.shape
+    np.testing.assert_array_equal(uhc.reshape(6, nc + 1, nc + 1)[:, 1, 2],
+                                  uh.reshape(6, nf + 1, nf + 1)[:, 8, 16])
+    est, var = oracle.two_level_mean(uH, uhc, uH)
+    np.testing.assert_allclose(est, uhc.mean(axis=0), rtol=1e-13, atol=1e-16)
+    # independent halves: the estimate is the coarse mean plus the mean correction
+    est2, var2 = oracle.two_level_mean(uH[:3], uhc[3:], uH[3:])
+    np.testing.assert_allclose(est2, uH[:3].mean(0) + (uhc[3:] - uH[3:]).mean(0), rtol=1e-13, atol=1e-16)
+    assert np.all(var2 >= 0)
