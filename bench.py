@@ -518,6 +518,34 @@ def bench_ri(api, dev, stream, samples=None):
     return res, 3 * 3 + 3  # (tiles, eval, fallback) x 3 timed calls + the FP64 comparison x 3
 
 
+def bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, direct_ms):
+    """The same step through a plan: launch shapes picked by its autotuner on
+    the first batch, then the whole step replayed as one CUDA graph."""
+    import torch
+    h = api.stomsfem_plan_create(g, fld, B, FORMS[form], oversample=ov_t, max_oversample=mo)
+    u = torch.empty((B, nn), dtype=torch.float64, device=dev)
+    mean = torch.zeros(nn, dtype=torch.float64, device=dev)
+    m2 = torch.zeros_like(mean)
+    cnt = torch.zeros(1, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        bps, split, tune_ms = api.stomsfem_plan_tune(h, xs_for(0, B), u, stream=stream)
+        xs = [xs_for(i, B).contiguous() for i in range(4)]
+        api.stomsfem_plan_step(h, xs[0], u, mean, m2, cnt, stream=stream)   # capture
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(3):
+            api.stomsfem_plan_step(h, xs[0], u, mean, m2, cnt, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    info = api.stomsfem_plan_info(h)
+    api.stomsfem_plan_destroy(h)
+    ms_graph = e0.elapsed_time(e1) / 3
+    return {"samples_per_step": B, "blocks_per_sm": bps, "split_fp32": split, "tune_best_ms": tune_ms,
+            "graph_ms_per_step": ms_graph, "graph_units_per_s": B * g.nc * g.nc / (ms_graph / 1e3),
+            "direct_ms_per_step": direct_ms, "graph_ready": info[2], "device_bytes": info[3]}
+
+
 def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u64_gal):
     """Petrov-Galerkin form (Eq. stiffness_local_petrov) of the FP32 step on
     the same workload: sample a, upscale with bilinear test functions (16
@@ -752,6 +780,7 @@ def main():
 
     extra = {}
     if not args.no_extra_forms:
+        extra["plan"] = bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, ms / args.steps)
         extra["petrov_galerkin"] = bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for,
                                             args.pg_batch, Bc, u64)
         extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)

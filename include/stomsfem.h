@@ -204,6 +204,52 @@ int stomsfem_coarse_solve(const stomsfem_grid* grid, const double* Ke, const dou
                           void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
 /* ---------------------------------------------------------------------
+ * Plans (no paper counterpart: the Monte Carlo driver of Sec. 4.1.1 for
+ * one batch shape).  A plan owns the intermediate device buffers of a step
+ * over S samples -- a [S][nf][nf], Ke [S][nc*nc][10], be [S][nc*nc][4] and
+ * the upscaling and coarse workspaces -- and runs
+ *   stomsfem_sample_coef_precision (FP32 arithmetic for the FP32 form)
+ *   -> stomsfem_upscale -> stomsfem_coarse_solve (+ moments)
+ * with launch shapes chosen by stomsfem_plan_tune and the whole step
+ * captured once as a CUDA graph.
+ * ------------------------------------------------------------------- */
+typedef struct stomsfem_plan stomsfem_plan; /* opaque, library-owned */
+
+/* oversample: device [nc*nc] or NULL (owned by the caller, must outlive
+ * the plan); precision and refine_iters as stomsfem_upscale.  Allocates
+ * device memory (synchronous).  EINVAL on bad arguments, ENOMEM/ECUDA. */
+int stomsfem_plan_create(const stomsfem_grid* grid, const stomsfem_field* field, const int8_t* oversample,
+                         int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
+                         stomsfem_plan** out);
+int stomsfem_plan_destroy(stomsfem_plan* plan);
+
+/* Autotuner: runs the step on xi (device [S][nbx*nby]; u device
+ * [S][(nc+1)^2] receives the solutions, no moments) for every launch
+ * choice -- at most 1, 2 or all resident upscaling CTAs per SM, and for
+ * the FP32 form with oversampling the separate forward-only launch for the
+ * unoversampled cells or one launch -- timing two runs of each with CUDA
+ * events after one untimed run, and keeps the fastest (host outputs, any
+ * may be NULL: blocks per SM, 0 meaning all that fit; split flag; its time
+ * per step in ms).  Synchronises `stream`; drops the captured graph.  The
+ * FP32 results depend on the split choice within the FP32 tolerance. */
+int stomsfem_plan_tune(stomsfem_plan* plan, const double* xi, double* u, int32_t* blocks_per_sm,
+                       int32_t* split_fp32, float* ms_best, stomsfem_stream_t stream);
+
+/* One step: xi (device [S][nbx*nby]) -> u (device [S][(nc+1)^2]) and the
+ * running moments (mean, m2, count as stomsfem_coarse_solve, or all NULL).
+ * With use_graph != 0 on a created stream the step is captured as a CUDA
+ * graph on first use and replayed afterwards; it is captured again when
+ * the stream or any of the five pointers changes.  The default streams
+ * run the launches directly.  Stream-ordered. */
+int stomsfem_plan_step(stomsfem_plan* plan, const double* xi, double* u, double* mean, double* m2,
+                       double* count, int32_t use_graph, stomsfem_stream_t stream);
+
+/* The plan's launch choice, whether a graph is instantiated, and the
+ * device memory it owns (host outputs, any may be NULL). */
+int stomsfem_plan_info(const stomsfem_plan* plan, int32_t* blocks_per_sm, int32_t* split_fp32,
+                       int32_t* graph_ready, size_t* device_bytes);
+
+/* ---------------------------------------------------------------------
  * Two-level Monte Carlo (Remark in Sec. 4.1.1, Eq. MCmean2level):
  *   M2 = mean over N_H samples of u_H
  *      + mean over N_h other samples of (u_h - u_H at the coarse nodes),

@@ -87,6 +87,12 @@ _SIG = {
     "stomsfem_fine_fem": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _I, _P, _P, _SZ, _P]),
     "stomsfem_restrict_to_coarse": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P]),
     "stomsfem_mc_moments": (ctypes.c_int, [_I, _I, _P, _P, _P, _P, _P]),
+    "stomsfem_plan_create": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _I, _I, _I,
+                                            ctypes.POINTER(_P)]),
+    "stomsfem_plan_destroy": (ctypes.c_int, [_P]),
+    "stomsfem_plan_tune": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "stomsfem_plan_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P]),
+    "stomsfem_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,

@@ -463,3 +463,40 @@ def stomsfem_mc_moments(u, mean, m2, count, stream=None):
     L.check(L.lib().stomsfem_mc_moments(
         int(n), int(S), _dev(u, torch.float64, (S, n), "u"), _dev(mean, torch.float64, (n,), "mean"),
         _dev(m2, torch.float64, (n,), "m2"), _dev(count, torch.float64, (1,), "count"), _stream(stream)))
+
+
+def stomsfem_plan_create(g: Grid, fld: Field, S, precision=FP64, oversample=None, max_oversample=0,
+                         refine_iters=2):
+    h = ctypes.c_void_p()
+    ncell = g.nc * g.nc
+    L.check(L.lib().stomsfem_plan_create(ctypes.byref(g), ctypes.byref(fld),
+                                         _dev(oversample, torch.int8, (ncell,), "oversample"),
+                                         int(max_oversample), int(S), int(precision), int(refine_iters),
+                                         ctypes.byref(h)))
+    return h
+
+
+def stomsfem_plan_destroy(h):
+    L.check(L.lib().stomsfem_plan_destroy(h))
+
+
+def stomsfem_plan_tune(h, xi, u, stream=None):
+    """-> (blocks_per_sm, split_fp32, ms per step)."""
+    b, sp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    L.check(L.lib().stomsfem_plan_tune(h, _dev(xi, torch.float64, None, "xi"), _dev(u, torch.float64, None, "u"),
+                                       ctypes.byref(b), ctypes.byref(sp), ctypes.byref(ms), _stream(stream)))
+    return b.value, sp.value, ms.value
+
+
+def stomsfem_plan_step(h, xi, u, mean=None, m2=None, count=None, use_graph=True, stream=None):
+    L.check(L.lib().stomsfem_plan_step(h, _dev(xi, torch.float64, None, "xi"), _dev(u, torch.float64, None, "u"),
+                                       _dev(mean, torch.float64, None, "mean"), _dev(m2, torch.float64, None, "m2"),
+                                       _dev(count, torch.float64, (1,), "count"), 1 if use_graph else 0,
+                                       _stream(stream)))
+
+
+def stomsfem_plan_info(h):
+    """-> (blocks_per_sm, split_fp32, graph_ready, device_bytes)."""
+    b, sp, gr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(gr), ctypes.byref(nb)))
+    return b.value, sp.value, gr.value, nb.value

@@ -21,6 +21,12 @@ size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
 // Scratch slots (units in flight) of one block of the upscaling launch for a
 // precision: the least workspace stomsfem_upscale accepts, in slots.
 int upscale_slots_per_block(int precision);
+// stomsfem_upscale (Galerkin, no phi/status) with the plan's launch
+// choices: at most blocks_per_sm resident CTAs per SM (0: as many as fit),
+// split_fp32 = 0 runs the FP32 form as one launch.
+int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
+                  int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32);
 
 #define STOMSFEM_TRY_CUDA(expr)                                  \
   do {                                                           \

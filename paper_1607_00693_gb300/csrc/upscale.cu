@@ -75,6 +75,9 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   A.units = (long long)S * grid->nc * grid->nc;
   A.unit_list = unit_list;
   A.unit_count = unit_count;
+  A.cell_list = nullptr;
+  A.cell_count = nullptr;
+  A.blocks_per_sm_cap = 0;
   return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
 }
 
@@ -89,6 +92,17 @@ size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
   size_t sb, lb;
   slot_layout(nmax, bmax, STOMSFEM_FP64, &sb, &lb);
   return sb;
+}
+
+// stomsfem_upscale with launch choices (the plan's autotuner).
+int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
+                  int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32) {
+  UpscaleTuning t;
+  t.blocks_per_sm = blocks_per_sm;
+  t.split_fp32 = split_fp32;
+  return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, nullptr,
+                            nullptr, workspace, workspace_bytes, reinterpret_cast<stomsfem_stream_t>(st), t);
 }
 
 }  // namespace stomsfem

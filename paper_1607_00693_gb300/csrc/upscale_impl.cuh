@@ -301,6 +301,14 @@ struct UpscaleArgs {
   double fq, fH2;             // f h^2 / 4 and f H^2 (load scaling)
   const int32_t* cell_list;   // optional (MODE 1, 2): process only these cells (device list)
   const int32_t* cell_count;  // device length of cell_list
+  int blocks_per_sm_cap;      // host-side launch shape: at most this many resident CTAs per SM (0: occupancy)
+};
+
+// Launch choices a plan's autotuner may set (stomsfem_plan_tune); the
+// defaults are what stomsfem_upscale uses.
+struct UpscaleTuning {
+  int blocks_per_sm = 0;  // 0: as many as fit
+  int split_fp32 = 1;     // FP32 form: separate forward-only launch for the cells without oversampling
 };
 
 // Upscale launch modes: 0 every unit (back-substitution route), 1 the
@@ -691,6 +699,7 @@ static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream
   int per_sm = 0;
   STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
   if (per_sm < 1) return set_error(STOMSFEM_EINVAL, "upscale kernel does not fit on an SM (smem %zu)", smem);
+  if (A.blocks_per_sm_cap > 0 && per_sm > A.blocks_per_sm_cap) per_sm = A.blocks_per_sm_cap;
   long long blocks = (long long)per_sm * device_sm_count();
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
@@ -724,7 +733,8 @@ constexpr int group_lanes(int) { return 16; }
 template <bool PG>
 int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                 int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, double* phi,
-                int32_t* unit_status, void* workspace, size_t workspace_bytes, stomsfem_stream_t stream) {
+                int32_t* unit_status, void* workspace, size_t workspace_bytes, stomsfem_stream_t stream,
+                const UpscaleTuning& tune = UpscaleTuning()) {
   int rc = validate_grid(grid);
   if (rc) return rc;
   if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
@@ -782,8 +792,9 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
   A.unit_count = nullptr;
   A.cell_list = nullptr;
   A.cell_count = nullptr;
+  A.blocks_per_sm_cap = tune.blocks_per_sm;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == STOMSFEM_FP32 && !phi) {
+  if (precision == STOMSFEM_FP32 && !phi && tune.split_fp32) {
     // FP32 without phi output: cells without oversampling take the
     // forward-only route in a launch of their own, the others follow
     constexpr int G = group_lanes(STOMSFEM_FP32);

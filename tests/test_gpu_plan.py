@@ -1,0 +1,116 @@
+"""Plans on the GPU: the captured step (sample -> upscale -> coarse solve
+-> moments) reproduces the direct calls bit for bit, replays and
+re-captures, the autotuner's choices, and the default-stream path."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1607_00693_gb300 import api
+from paper_1607_00693_gb300 import workloads as W
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_1607_00693_gb300.build import build_library
+    build_library()
+    nf, nc, S = 128, 4, 6
+    fld_d = dict(W.workload("upscale_1024")["field"], nbx=4, nby=4, width=0.125)
+    g = api.grid(nf, nc, 1.0)
+    fld = api.field_from_dict(fld_d)
+    ov = np.random.default_rng(20).integers(0, 5, size=nc * nc).astype(np.int8)
+    xt = torch.from_numpy(W.draw_xi(fld_d, S, 77)).to(DEV)
+    return dict(g=g, fld=fld, ov=torch.from_numpy(ov).to(DEV), mo=int(ov.max()), xt=xt, S=S, nn=(nc + 1) ** 2)
+
+
+def _direct(c, prec):
+    g, S = c["g"], c["S"]
+    a = torch.empty((S, g.nf, g.nf), dtype=torch.float64, device=DEV)
+    api.stomsfem_sample_coef_precision(g, c["fld"], c["xt"], a, precision=api.FP32 if prec == api.FP32 else api.FP64)
+    Ke = torch.empty((S, g.nc * g.nc, 10), dtype=torch.float64, device=DEV)
+    be = torch.empty((S, g.nc * g.nc, 4), dtype=torch.float64, device=DEV)
+    api.stomsfem_upscale(g, a, Ke, be, oversample=c["ov"], max_oversample=c["mo"], precision=prec, refine_iters=2)
+    u = torch.empty((S, c["nn"]), dtype=torch.float64, device=DEV)
+    api.stomsfem_coarse_solve(g, Ke, be, u)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [api.FP64, api.FP32_REFINED, api.FP32])
+def test_plan_step_equals_direct_calls(case, prec):
+    c = case
+    u0 = _direct(c, prec)
+    h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], prec, oversample=c["ov"], max_oversample=c["mo"])
+    try:
+        st = torch.cuda.Stream()
+        u = torch.empty((c["S"], c["nn"]), dtype=torch.float64, device=DEV)
+        with torch.cuda.stream(st):
+            api.stomsfem_plan_step(h, c["xt"], u, use_graph=False, stream=st)
+            st.synchronize()
+            np.testing.assert_array_equal(u.cpu().numpy(), u0)
+            u.fill_(0.0)
+            api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # capture + launch
+            st.synchronize()
+            np.testing.assert_array_equal(u.cpu().numpy(), u0)
+            assert api.stomsfem_plan_info(h)[2] == 1
+            u.fill_(0.0)
+            api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # replay
+            st.synchronize()
+            np.testing.assert_array_equal(u.cpu().numpy(), u0)
+            # moments through the graph: the same batch twice
+            mean = torch.zeros(c["nn"], dtype=torch.float64, device=DEV)
+            m2 = torch.zeros_like(mean)
+            cnt = torch.zeros(1, dtype=torch.float64, device=DEV)
+            for _ in range(2):
+                api.stomsfem_plan_step(h, c["xt"], u, mean, m2, cnt, stream=st)
+            st.synchronize()
+        assert cnt.item() == 2 * c["S"]
+        np.testing.assert_allclose(mean.cpu().numpy(), u0.mean(axis=0), rtol=1e-12, atol=1e-18)
+        np.testing.assert_allclose(m2.cpu().numpy() / (2 * c["S"]), u0.var(axis=0), rtol=1e-9, atol=1e-20)
+    finally:
+        api.stomsfem_plan_destroy(h)
+
+
+def test_plan_tune_and_recapture(case):
+    """FP32 with oversampling: six launch choices timed; the chosen one
+    reproduces the direct result (bit for bit with the split launch, within
+    the FP32 tolerance with one launch); a new output buffer re-captures."""
+    c = case
+    u0 = _direct(c, api.FP32)
+    h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], api.FP32, oversample=c["ov"], max_oversample=c["mo"])
+    try:
+        st = torch.cuda.Stream()
+        u = torch.empty((c["S"], c["nn"]), dtype=torch.float64, device=DEV)
+        with torch.cuda.stream(st):
+            bps, split, ms = api.stomsfem_plan_tune(h, c["xt"], u, stream=st)
+            assert bps in (0, 1, 2) and split in (0, 1) and ms > 0
+            assert api.stomsfem_plan_info(h)[:3] == (bps, split, 0)
+            api.stomsfem_plan_step(h, c["xt"], u, stream=st)
+            u2 = torch.empty_like(u)
+            api.stomsfem_plan_step(h, c["xt"], u2, stream=st)
+            st.synchronize()
+        for x in (u.cpu().numpy(), u2.cpu().numpy()):
+            if split:
+                np.testing.assert_array_equal(x, u0)
+            else:
+                assert np.max(np.linalg.norm(x - u0, axis=1) / np.linalg.norm(u0, axis=1)) <= 1e-5
+    finally:
+        api.stomsfem_plan_destroy(h)
+
+
+def test_plan_default_stream_runs_directly(case):
+    c = case
+    u0 = _direct(c, api.FP64)
+    h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], api.FP64, oversample=c["ov"], max_oversample=c["mo"])
+    try:
+        u = torch.empty((c["S"], c["nn"]), dtype=torch.float64, device=DEV)
+        api.stomsfem_plan_step(h, c["xt"], u)      # the current (default) stream: no capture
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(u.cpu().numpy(), u0)
+        assert api.stomsfem_plan_info(h)[2] == 0
+    finally:
+        api.stomsfem_plan_destroy(h)
