@@ -536,6 +536,20 @@ int stomsfem_ri_destroy(stomsfem_ri* ri);
  * families in order, each family's grid points last direction fastest.
  * Synchronous. */
 int stomsfem_ri_values(const stomsfem_ri* ri, double* V_host, int64_t n_points);
+/* Checkpoint of an interpolation handle (no paper counterpart; the
+ * interpolation data are the offline stage's whole output): grid, field,
+ * eps, nu_max, node family and the FP64 data, into the caller's host
+ * buffer (host_buf NULL: size only; ENOMEM if too small).  Format: magic
+ * "STMFRIT1", format version, byte-order probe, then fixed-width fields in
+ * native byte order.  Synchronous. */
+int stomsfem_ri_save(const stomsfem_ri* ri, void* host_buf, size_t buf_bytes, size_t* bytes);
+/* Rebuilds a handle from a stomsfem_ri_save buffer without the offline
+ * solves: the plan is re-derived from the stored grid, field, eps and
+ * nu_max and must have the stored number of grid points.  EVERSION on a
+ * foreign or other-version buffer; EINVAL if truncated or inconsistent.
+ * Allocates device memory (synchronous). */
+int stomsfem_ri_load(const void* host_buf, size_t buf_bytes, stomsfem_ri** out, int32_t* n_families);
+
 /* Scratch of stomsfem_ri_upscale for S samples. */
 int stomsfem_ri_workspace_size(const stomsfem_ri* ri, int32_t S, size_t* bytes);
 /* Online stage (Alg. 2) for S samples (device: xi [S][nbx*nby], a

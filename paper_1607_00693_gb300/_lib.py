@@ -99,6 +99,8 @@ _SIG = {
                                          _I, ctypes.POINTER(_P), _P, _P]),
     "stomsfem_ri_destroy": (ctypes.c_int, [_P]),
     "stomsfem_ri_values": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "stomsfem_ri_save": (ctypes.c_int, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
+    "stomsfem_ri_load": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_P), _P]),
     "stomsfem_ri_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_ri_upscale": (ctypes.c_int, [_P, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
 }

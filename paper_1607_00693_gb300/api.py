@@ -500,3 +500,15 @@ def stomsfem_plan_info(h):
     b, sp, gr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
     L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(gr), ctypes.byref(nb)))
     return b.value, sp.value, gr.value, nb.value
+
+
+def stomsfem_ri_save(h):
+    return _save(L.lib().stomsfem_ri_save, h)
+
+
+def stomsfem_ri_load(data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    h = ctypes.c_void_p()
+    nfam = ctypes.c_int32()
+    L.check(L.lib().stomsfem_ri_load(buf, len(data), ctypes.byref(h), ctypes.byref(nfam)))
+    return h, nfam.value

@@ -10,6 +10,7 @@
 #include <map>
 #include <vector>
 
+#include "ckpt.cuh"
 #include "common.cuh"
 
 namespace stomsfem {
@@ -495,10 +496,10 @@ extern "C" int stomsfem_ri_plan(const stomsfem_grid* grid, const stomsfem_field*
   return STOMSFEM_OK;
 }
 
-extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field* field, double eps,
-                                 int32_t nu_max, int32_t nodes, stomsfem_ri** out, int32_t* n_families,
-                                 stomsfem_stream_t stream) {
-  if (!out) return set_error(STOMSFEM_EINVAL, "out is NULL");
+// A handle with its plan, node tables and (unfilled) interpolation tables
+// on the device; xd receives the FP64 nodes per family and slot.
+static int ri_setup(const stomsfem_grid* grid, const stomsfem_field* field, double eps, int32_t nu_max,
+                    int32_t nodes, stomsfem_ri** out, std::vector<double>& xd) {
   *out = nullptr;
   if (nodes != STOMSFEM_RI_CHEBYSHEV && nodes != STOMSFEM_RI_LEGENDRE)
     return set_error(STOMSFEM_EINVAL, "unknown node family %d", nodes);
@@ -514,10 +515,9 @@ extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field
   h->nu_max = nu_max;
   h->kind = nodes;
   RiPlan& P = h->P;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // nodes and barycentric weights per family and direction
   std::vector<float> xs((size_t)P.nfam * kRiMaxSlots, 0.f), ws((size_t)P.nfam * kRiMaxSlots, 0.f);
-  std::vector<double> xd((size_t)P.nfam * kRiMaxSlots, 0.0);
+  xd.assign((size_t)P.nfam * kRiMaxSlots, 0.0);
   for (int f = 0; f < P.nfam; ++f)
     for (int k = 0; k < P.F[f].ndim; ++k) {
       const int n = P.F[f].radix[k], s0 = P.F[f].slot0[k];
@@ -530,6 +530,40 @@ extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field
         ws[(size_t)f * kRiMaxSlots + s0 + j] = (float)w[j];
       }
     }
+#define TRY(x)                                     \
+  if ((rc = check_cuda((x), #x)) != STOMSFEM_OK) { \
+    ri_free(h);                                    \
+    return rc;                                     \
+  }
+  TRY(cudaMalloc(&h->fam_d, sizeof(RiFam) * P.nfam));
+  TRY(cudaMalloc(&h->x_d, sizeof(float) * xs.size()));
+  TRY(cudaMalloc(&h->w_d, sizeof(float) * ws.size()));
+  TRY(cudaMalloc(&h->tab32, sizeof(float) * 16 * P.npoints));
+  TRY(cudaMalloc(&h->tab64, sizeof(double) * 14 * P.npoints));
+  TRY(cudaMalloc(&h->cell_var_d, sizeof(int) * P.var.size()));
+  TRY(cudaMalloc(&h->fam_cells_d, sizeof(int) * P.fam_cells.size()));
+  TRY(cudaMemcpy(h->fam_d, P.F.data(), sizeof(RiFam) * P.nfam, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(h->x_d, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(h->w_d, ws.data(), sizeof(float) * ws.size(), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(h->cell_var_d, P.var.data(), sizeof(int) * P.var.size(), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(h->fam_cells_d, P.fam_cells.data(), sizeof(int) * P.fam_cells.size(), cudaMemcpyHostToDevice));
+#undef TRY
+  *out = h;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field* field, double eps,
+                                 int32_t nu_max, int32_t nodes, stomsfem_ri** out, int32_t* n_families,
+                                 stomsfem_stream_t stream) {
+  if (!out) return set_error(STOMSFEM_EINVAL, "out is NULL");
+  std::vector<double> xd;
+  stomsfem_ri* h = nullptr;
+  int rc = ri_setup(grid, field, eps, nu_max, nodes, out, xd);
+  if (rc) return rc;
+  h = *out;
+  *out = nullptr;
+  RiPlan& P = h->P;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int ncell = P.ncell, nf = grid->nf, K = P.K;
   double *xi_c = nullptr, *a_c = nullptr, *Ke_c = nullptr, *be_c = nullptr;
   int32_t* list_c = nullptr;
@@ -547,18 +581,6 @@ extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field
 #define TRY(x)                                     \
   if ((rc = check_cuda((x), #x)) != STOMSFEM_OK) \
     return fail(rc);
-  TRY(cudaMalloc(&h->fam_d, sizeof(RiFam) * P.nfam));
-  TRY(cudaMalloc(&h->x_d, sizeof(float) * xs.size()));
-  TRY(cudaMalloc(&h->w_d, sizeof(float) * ws.size()));
-  TRY(cudaMalloc(&h->tab32, sizeof(float) * 16 * P.npoints));
-  TRY(cudaMalloc(&h->tab64, sizeof(double) * 14 * P.npoints));
-  TRY(cudaMalloc(&h->cell_var_d, sizeof(int) * P.var.size()));
-  TRY(cudaMalloc(&h->fam_cells_d, sizeof(int) * P.fam_cells.size()));
-  TRY(cudaMemcpy(h->fam_d, P.F.data(), sizeof(RiFam) * P.nfam, cudaMemcpyHostToDevice));
-  TRY(cudaMemcpy(h->x_d, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice));
-  TRY(cudaMemcpy(h->w_d, ws.data(), sizeof(float) * ws.size(), cudaMemcpyHostToDevice));
-  TRY(cudaMemcpy(h->cell_var_d, P.var.data(), sizeof(int) * P.var.size(), cudaMemcpyHostToDevice));
-  TRY(cudaMemcpy(h->fam_cells_d, P.fam_cells.data(), sizeof(int) * P.fam_cells.size(), cudaMemcpyHostToDevice));
   // collocation: every grid point of a family is one sample of the
   // coefficient (local parameters at the point's nodes, the others 0);
   // the family's first cell of that sample is upscaled in FP64
@@ -703,4 +725,93 @@ extern "C" int stomsfem_ri_upscale(stomsfem_ri* ri, const double* xi, const doub
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   if (!a) return STOMSFEM_OK;
   return upscale_list_fp64(&ri->grid, a, S, list, count, Ke, be, ws + o, workspace_bytes - o, st);
+}
+
+static const char kRiMagic[8] = {'S', 'T', 'M', 'F', 'R', 'I', 'T', '1'};
+
+extern "C" int stomsfem_ri_save(const stomsfem_ri* ri, void* host_buf, size_t buf_bytes, size_t* bytes) {
+  if (!ri || !bytes) return set_error(STOMSFEM_EINVAL, "NULL ri / bytes");
+  const size_t nv = (size_t)ri->P.npoints * 14;
+  std::vector<double> V;
+  if (host_buf) {
+    V.resize(nv);
+    STOMSFEM_TRY_CUDA(cudaMemcpy(V.data(), ri->tab64, sizeof(double) * nv, cudaMemcpyDeviceToHost));
+  }
+  CkptWriter w(host_buf, buf_bytes);
+  ckpt_header(w, kRiMagic);
+  w.val<int32_t>(ri->grid.nf);
+  w.val<int32_t>(ri->grid.nc);
+  w.val<double>(ri->grid.f);
+  w.val<int32_t>(ri->field.kind);
+  w.val<int32_t>(ri->field.nbx);
+  w.val<int32_t>(ri->field.nby);
+  w.val<double>(ri->field.width);
+  w.val<double>(ri->field.scale);
+  w.val<double>(ri->field.contrast_log);
+  w.val<double>(ri->field.gain);
+  w.val<double>(ri->eps);
+  w.val<int32_t>(ri->nu_max);
+  w.val<int32_t>(ri->kind);
+  w.val<int64_t>(ri->P.npoints);
+  w.put(host_buf ? (const void*)V.data() : nullptr, sizeof(double) * nv);
+  *bytes = w.pos;
+  if (host_buf && !w.fits()) return set_error(STOMSFEM_ENOMEM, "checkpoint buffer %zu < %zu bytes", buf_bytes, w.pos);
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_ri_load(const void* host_buf, size_t buf_bytes, stomsfem_ri** out, int32_t* n_families) {
+  if (!host_buf || !out) return set_error(STOMSFEM_EINVAL, "NULL buffer / out");
+  *out = nullptr;
+  CkptReader r(host_buf, buf_bytes);
+  const int hc = ckpt_check_header(r, kRiMagic);
+  if (hc == 1) return set_error(STOMSFEM_EVERSION, "not a version-%u interpolation checkpoint", kCkptVersion);
+  if (hc == 2) return set_error(STOMSFEM_EINVAL, "truncated interpolation checkpoint");
+  stomsfem_grid grid;
+  grid.nf = r.val<int32_t>();
+  grid.nc = r.val<int32_t>();
+  grid.f = r.val<double>();
+  stomsfem_field field;
+  field.kind = r.val<int32_t>();
+  field.nbx = r.val<int32_t>();
+  field.nby = r.val<int32_t>();
+  field.width = r.val<double>();
+  field.scale = r.val<double>();
+  field.contrast_log = r.val<double>();
+  field.gain = r.val<double>();
+  const double eps = r.val<double>();
+  const int32_t nu_max = r.val<int32_t>(), kind = r.val<int32_t>();
+  const int64_t npts = r.val<int64_t>();
+  if (!r.ok) return set_error(STOMSFEM_EINVAL, "truncated interpolation checkpoint");
+  if (kind != STOMSFEM_RI_CHEBYSHEV && kind != STOMSFEM_RI_LEGENDRE)
+    return set_error(STOMSFEM_EINVAL, "interpolation checkpoint with node family %d", kind);
+  {
+    // the families are re-derived on the host: their grid must be the stored one
+    RiPlan P0;
+    const int rp = ri_make_plan(&grid, &field, eps, nu_max, P0);
+    if (rp) return set_error(STOMSFEM_EINVAL, "inconsistent interpolation checkpoint header");
+    if (P0.npoints != npts)
+      return set_error(STOMSFEM_EINVAL, "interpolation checkpoint holds %lld grid points, its plan %lld",
+                       (long long)npts, P0.npoints);
+  }
+  const size_t nv = (size_t)npts * 14;
+  if (buf_bytes < r.pos + sizeof(double) * nv) return set_error(STOMSFEM_EINVAL, "truncated interpolation checkpoint");
+  std::vector<double> xd;
+  stomsfem_ri* h = nullptr;
+  int rc = ri_setup(&grid, &field, eps, nu_max, kind, &h, xd);
+  if (rc) return rc;
+  std::vector<double> V(nv);
+  r.get(V.data(), sizeof(double) * nv);
+  std::vector<float> V32((size_t)npts * 16, 0.f);
+  for (int64_t p = 0; p < npts; ++p)
+    for (int q = 0; q < 14; ++q) V32[(size_t)p * 16 + q] = (float)V[(size_t)p * 14 + q];
+  rc = check_cuda(cudaMemcpy(h->tab64, V.data(), sizeof(double) * nv, cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (rc == STOMSFEM_OK)
+    rc = check_cuda(cudaMemcpy(h->tab32, V32.data(), sizeof(float) * V32.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (rc) {
+    ri_free(h);
+    return rc;
+  }
+  if (n_families) *n_families = h->P.nfam;
+  *out = h;
+  return STOMSFEM_OK;
 }

@@ -98,6 +98,18 @@ def test_checkpoint_headers_rejected_without_gpu(lib):
     bad = b"STMFPOD1" + struct.pack("<II", 1, 0x01020304) + struct.pack("<11i", 64, 8, 8, 81, 49, 64, 31,
                                                                        496, 496, 64, 99) + struct.pack("<d", 1.0)
     assert lib.stomsfem_pod_load(bad, len(bad), ctypes.byref(h)) == L.EINVAL
+    # interpolation checkpoints: foreign, truncated, and a header whose plan
+    # has another number of grid points (msfem_64 grid, eps 1e-3: 4040)
+    assert lib.stomsfem_ri_load(junk, len(junk), ctypes.byref(h), ctypes.byref(n)) == L.EVERSION
+    assert lib.stomsfem_ri_load(b"STMFRIT1", 8, ctypes.byref(h), ctypes.byref(n)) == L.EINVAL
+    hdr = b"STMFRIT1" + struct.pack("<II", 1, 0x01020304)
+    body = (struct.pack("<iid", 64, 8, 1.0) + struct.pack("<iii", 0, 4, 4) + struct.pack("<dddd", 0.1, 1.0, 0.0, 1.0)
+            + struct.pack("<dii", 1e-3, 8, 1))
+    wrong = hdr + body + struct.pack("<q", 4041) + b"\x00" * 8
+    assert lib.stomsfem_ri_load(wrong, len(wrong), ctypes.byref(h), ctypes.byref(n)) == L.EINVAL
+    assert b"grid points" in lib.stomsfem_last_error()
+    short_v = hdr + body + struct.pack("<q", 4040) + b"\x00" * 64
+    assert lib.stomsfem_ri_load(short_v, len(short_v), ctypes.byref(h), ctypes.byref(n)) == L.EINVAL
 
 
 def test_selftest_exp_argument_checks(lib):

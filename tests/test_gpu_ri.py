@@ -212,3 +212,23 @@ def test_many_directions_low_degree(setup):
                 assert _unit_close(be[s, c], bo).all(), (s, c)
     finally:
         api.stomsfem_ri_destroy(h)
+
+
+def test_checkpoint_roundtrip(setup):
+    """save -> load gives the same data and the same online results, with no
+    offline solves; the stored plan is checked against the re-derived one."""
+    _, _, w, g, _, models = setup
+    h, m = models[api.RI_LEGENDRE]
+    blob = api.stomsfem_ri_save(h)
+    assert blob[:8] == b"STMFRIT1"
+    h2, nfam = api.stomsfem_ri_load(blob)
+    try:
+        assert nfam == len(m["keys"])
+        n = sum(len(v) for v in m["V"])
+        np.testing.assert_array_equal(api.stomsfem_ri_values(h2, n), api.stomsfem_ri_values(h, n))
+        xi = torch.tensor(W.draw_xi(w["field"], 11, 5), device=DEV)
+        r1, r2 = _run(g, h, xi), _run(g, h2, xi)
+        for x, y in zip(r1, r2):
+            np.testing.assert_array_equal(x, y)
+    finally:
+        api.stomsfem_ri_destroy(h2)
