@@ -220,7 +220,7 @@ __global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
 // (test node) collects S_e[I_loc][J_loc] over the cells around J, a
 // non-symmetric band of half width bw = nc.  Banded LU without pivoting,
 // one warp per sample: the rows k..k+bw live in a shared-memory ring (row
-// i keeps columns i-bw..i+bw); step k eliminates column k from the bw rows
+// i keeps columns i-bw..i+bw, pitch 2 bw + 2); step k eliminates column k from the bw rows
 // below (lane t owns rows k+1+t, k+33+t), writes the finished U row and its
 // right-hand side to the sample's scratch, and brings in row k+bw+1, whose
 // 16 contributions (4 cells x 4 trial corners) were loaded one step ahead.
@@ -261,10 +261,12 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
                  double* __restrict__ u, unsigned char* __restrict__ ws, size_t slot_bytes) {
   extern __shared__ __align__(16) unsigned char smem_pg[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int bw = nc, W = 2 * nc + 1, R = nc + 1;
+  // row pitch PW = W + 1 (even): consecutive lanes, one row apart, then
+  // differ by an odd number of doubles and meet different banks
+  const int bw = nc, W = 2 * nc + 1, PW = W + 1, R = nc + 1;
   const int mi = nc - 1, n = mi * mi, NN = nc + 1;
-  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * W + 2 * R);
-  double* yr = Rw + (size_t)R * W;  // right-hand sides of the window rows
+  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 2 * R);
+  double* yr = Rw + (size_t)R * PW;  // right-hand sides of the window rows
   double* xr = yr + R;              // ring of the last bw unknowns
   double* Ug = reinterpret_cast<double*>(ws + (size_t)(blockIdx.x * kCoarsePgWarps + wib) * slot_bytes);
   const long long gw = (long long)blockIdx.x * kCoarsePgWarps + wib;
@@ -274,12 +276,12 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
     const double* bs = bpg + (size_t)sl * nc * nc * 4;
     double* us = u + (size_t)sl * NN * NN;
     // window: rows 0..bw (zeroed, then their contributions)
-    for (int q = lane; q < R * W; q += 32) Rw[q] = 0.0;
+    for (int q = lane; q < R * PW; q += 32) Rw[q] = 0.0;
     for (int q = lane; q < R; q += 32) yr[q] = 0.0;
     __syncwarp();
     for (int J = 0; J < R && J < n; ++J) {
       const PgRowPrefetch p = pg_row_load(nc, Ks, bs, J, n, lane);
-      if (p.off >= 0) atomicAdd(&Rw[(size_t)(J % R) * W + p.off], p.v);
+      if (p.off >= 0) atomicAdd(&Rw[(size_t)(J % R) * PW + p.off], p.v);
       if (lane < 16 && (lane & 3) == 0) atomicAdd(&yr[J % R], p.b);
       __syncwarp();
     }
@@ -288,7 +290,7 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
     for (int k = 0; k < n; ++k) {
       const PgRowPrefetch cur = next;
       next = pg_row_load(nc, Ks, bs, k + R + 1, n, lane);  // in flight during this step
-      double* P = Rw + (size_t)(k % R) * W;
+      double* P = Rw + (size_t)(k % R) * PW;
       const double piv = P[bw];
       if (!(fabs(piv) > 0.0) || !(fabs(piv) < 1e300)) bad = true;
       const double inv = 1.0 / piv;
@@ -296,7 +298,7 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       for (int t = lane; t < bw; t += 32) {
         const int i = k + 1 + t;
         if (i < n) {
-          double* Ri = Rw + (size_t)(i % R) * W;
+          double* Ri = Rw + (size_t)(i % R) * PW;
           const double l = Ri[bw - 1 - t] * inv;
           Ri[bw - 1 - t] = 0.0;
           if (l != 0.0) {
@@ -349,7 +351,7 @@ static size_t coarse_pg_slot_bytes(int nc) {
   return ((size_t)n * (nc + 2) * 8 + 255) & ~size_t(255);
 }
 static size_t coarse_pg_smem(int nc) {
-  return (size_t)kCoarsePgWarps * ((size_t)(nc + 1) * (2 * nc + 1) + 2 * (nc + 1)) * 8;
+  return (size_t)kCoarsePgWarps * ((size_t)(nc + 1) * (2 * nc + 2) + 2 * (nc + 1)) * 8;
 }
 
 // Slot of one sample: the factor blocks, then the solution.
