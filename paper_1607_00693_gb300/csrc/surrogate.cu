@@ -417,20 +417,33 @@ __global__ void surrogate_infer_prepare_kernel(int S, int nc, int rho, int nf, i
     const int s = (int)(u / ncell), cell = (int)(u % ncell);
     const int fm = cell_fam[cell];
     const long long row = fam_row0[fm] + (long long)s * fam_ncell[fm] + cell_pos[cell];
-    for (int j = 0; j < kInPad; ++j) {
-      const int id = j < kIn ? var_ids[cell * kIn + j] : -1;
-      const float v = id >= 0 ? (float)xi[(size_t)s * K + id] : 0.f;
-      X[row * kInPad + j] = __float2bfloat16_rn(v);
-      if (j < kIn) Xf[u * kIn + j] = v;
+    // the unit's 16 inputs: one 128-byte BF16 row (zero padded) and 64
+    // bytes of FP32, written as 16-byte vectors
+    float v[kIn];
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) {
+      const int id = var_ids[cell * kIn + j];
+      v[j] = id >= 0 ? (float)xi[(size_t)s * K + id] : 0.f;
     }
+    uint4* xr = reinterpret_cast<uint4*>(X + row * kInPad);
+    xr[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    xr[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                       pack_bf16(v[14], v[15]));
+#pragma unroll
+    for (int c = 2; c < kInPad / 8; ++c) xr[c] = make_uint4(0u, 0u, 0u, 0u);
+    float4* xf = reinterpret_cast<float4*>(Xf + u * kIn);
+#pragma unroll
+    for (int c = 0; c < kIn / 4; ++c) xf[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     unit_of_row[row] = (int)u;
     const int cx = cell % nc, cy = cell / nc;
+    // arithmetic mean in FP64 (it scales K_e); the harmonic mean only bounds
+    // the indicator's energy test, so its reciprocals are FP32 (summed in FP64)
     double sa = 0.0, si = 0.0;
     for (int ey = 0; ey < rho; ++ey)
       for (int ex = 0; ex < rho; ++ex) {
-        const double v = a[((size_t)s * nf + cy * rho + ey) * nf + cx * rho + ex];
-        sa += v;
-        si += 1.0 / v;
+        const double av = a[((size_t)s * nf + cy * rho + ey) * nf + cx * rho + ex];
+        sa += av;
+        si += (double)__frcp_rn((float)av);
       }
     abar[u] = sa / (rho * rho);
     ahar[u] = (rho * rho) / si;
