@@ -450,6 +450,57 @@ __global__ void surrogate_infer_prepare_kernel(int S, int nc, int rho, int nf, i
   }
 }
 
+// Orthogonal projector, in the packed coordinates of a symmetric 4x4
+// matrix, onto the matrices with zero row sums (row-major [10][10]); set
+// by the host before each inference launch.
+__constant__ float kZeroRowSumProj[100];
+
+// P = B (B^T B)^{-1} B^T with B [10][6]: a zero-row-sum symmetric matrix is
+// fixed by its 6 off-diagonal entries o, its diagonal being -(row sums).
+static void zero_row_sum_projector(float* P) {
+  const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {1, 2, 3, 2, 3, 3};
+  auto packed = [](int l, int lp) { return l * 4 - (l * (l - 1)) / 2 + (lp - l); };
+  double B[10][6] = {};
+  for (int j = 0; j < 6; ++j) {
+    B[packed(pa[j], pb[j])][j] = 1.0;
+    B[packed(pa[j], pa[j])][j] = -1.0;
+    B[packed(pb[j], pb[j])][j] = -1.0;
+  }
+  double G[6][16] = {};  // [B^T B | B^T]
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j < 6; ++j)
+      for (int q = 0; q < 10; ++q) G[i][j] += B[q][i] * B[q][j];
+    for (int q = 0; q < 10; ++q) G[i][6 + q] = B[q][i];
+  }
+  for (int c = 0; c < 6; ++c) {  // Gauss-Jordan, B^T B is SPD
+    const double inv = 1.0 / G[c][c];
+    for (int k = 0; k < 16; ++k) G[c][k] *= inv;
+    for (int r = 0; r < 6; ++r)
+      if (r != c) {
+        const double f = G[r][c];
+        for (int k = 0; k < 16; ++k) G[r][k] -= f * G[c][k];
+      }
+  }
+  for (int q = 0; q < 10; ++q)
+    for (int r = 0; r < 10; ++r) {
+      double t = 0.0;
+      for (int j = 0; j < 6; ++j) t += B[q][j] * G[j][6 + r];
+      P[q * 10 + r] = (float)t;
+    }
+}
+
+// Zero inputs for the padding rows of every family's last tile (the
+// prepare kernel writes every unit's row; a padding row only feeds its own,
+// discarded output row).
+__global__ void surrogate_zero_pad_kernel(const int* __restrict__ fam_row0, const int* __restrict__ fam_ncell, int S,
+                                          __nv_bfloat16* __restrict__ X) {
+  const int f = blockIdx.x;
+  const long long r0 = fam_row0[f] + (long long)S * fam_ncell[f], r1 = fam_row0[f + 1];
+  uint4* x = reinterpret_cast<uint4*>(X);
+  for (long long i = r0 * (kInPad / 8) + threadIdx.x; i < r1 * (kInPad / 8); i += blockDim.x)
+    x[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 struct InferArgs {
   const __nv_bfloat16* X;
   const int* unit_of_row;
@@ -556,52 +607,27 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
     tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16), y);
     const int u = A.unit_of_row[tile * kTile + row];
     if (u >= 0) {
-      double yd[16];
+      float yf[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) yd[q] = (double)y[q] + (double)Wm[oB4 + q];
-      // projection onto zero-row-sum symmetric 4x4 (packed): keep the 6
-      // off-diagonal entries o = B^T y / ... solved in closed form below
+      for (int q = 0; q < 16; ++q) yf[q] = y[q] + Wm[oB4 + q];
+      // projection onto symmetric zero-row-sum 4x4 matrices (packed): the
+      // orthogonal projector of the packed coordinates, a constant 10x10
+      // matrix built on the host (FP32 suffices next to the BF16 network)
       const double kref[10] = {4.0 / 6, -1.0 / 6, -2.0 / 6, -1.0 / 6, 4.0 / 6, -1.0 / 6, -2.0 / 6, 4.0 / 6, -1.0 / 6, 4.0 / 6};
-      // packed indices: diag 0,4,7,9; off (0,1)=1 (0,2)=2 (0,3)=3 (1,2)=5 (1,3)=6 (2,3)=8
-      const int offi[6] = {1, 2, 3, 5, 6, 8};
-      const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {1, 2, 3, 2, 3, 3};
-      const int diag[4] = {0, 4, 7, 9};
-      // least squares: minimise sum_off (o - y_off)^2 + sum_l (-sum_{j != l} o_lj - y_ll)^2
-      // normal equations (I + E^T E) o = y_off - E^T y_diag, E the 4x6 incidence
-      double Mn[6][7];
-      for (int p = 0; p < 6; ++p) {
-        for (int q = 0; q < 6; ++q) {
-          int shared = (pa[p] == pa[q]) + (pa[p] == pb[q]) + (pb[p] == pa[q]) + (pb[p] == pb[q]);
-          Mn[p][q] = (p == q ? 1.0 : 0.0) + shared;
-        }
-        Mn[p][6] = yd[offi[p]] - yd[diag[pa[p]]] - yd[diag[pb[p]]];
-      }
-      for (int c = 0; c < 6; ++c) {  // SPD: elimination without pivoting
-        const double piv = 1.0 / Mn[c][c];
-        for (int r2 = c + 1; r2 < 6; ++r2) {
-          const double fct = Mn[r2][c] * piv;
-          for (int k = c; k < 7; ++k) Mn[r2][k] -= fct * Mn[c][k];
-        }
-      }
-      double o[6];
-      for (int c = 5; c >= 0; --c) {
-        double t = Mn[c][6];
-        for (int k = c + 1; k < 6; ++k) t -= Mn[c][k] * o[k];
-        o[c] = t / Mn[c][c];
-      }
-      double Kp[10];
-      for (int q = 0; q < 10; ++q) Kp[q] = 0.0;
-      for (int p = 0; p < 6; ++p) {
-        Kp[offi[p]] = o[p];
-        Kp[diag[pa[p]]] -= o[p];
-        Kp[diag[pb[p]]] -= o[p];
+      float Kp[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) {
+        float t = 0.f;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) t = fmaf(kZeroRowSumProj[q * 10 + r], yf[r], t);
+        Kp[q] = t;
       }
       const double ab = A.abar[u], ah = A.ahar[u];
       double K[10];
-      for (int q = 0; q < 10; ++q) K[q] = ab * (kref[q] + Kp[q]);
+      for (int q = 0; q < 10; ++q) K[q] = ab * (kref[q] + (double)Kp[q]);
       const double fH2 = A.f * A.H * A.H;
       double b[4];
-      for (int l = 0; l < 3; ++l) b[l] = fH2 * (0.25 + yd[10 + l]);
+      for (int l = 0; l < 3; ++l) b[l] = fH2 * (0.25 + (double)yf[10 + l]);
       b[3] = fH2 - b[0] - b[1] - b[2];
       // error indicator
       bool bad = false;
@@ -1102,7 +1128,6 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   STOMSFEM_TRY_CUDA(cudaMemcpyAsync(tf, tfam.data(), sizeof(int) * tfam.size(), cudaMemcpyHostToDevice, st));
   STOMSFEM_TRY_CUDA(cudaMemcpyAsync(row0_d, row0.data(), sizeof(int) * row0.size(), cudaMemcpyHostToDevice, st));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(uor, 0xFF, L.rows_pad * 4, st));
-  STOMSFEM_TRY_CUDA(cudaMemsetAsync(X, 0, L.rows_pad * kInPad * 2, st));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(count, 0, 8, st));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(err, 0, 8, st));
   const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
@@ -1110,6 +1135,8 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   surrogate_infer_prepare_kernel<<<sms * 8, 128, 0, st>>>(S, h->grid.nc, rho, h->grid.nf, h->K, xi, a, h->var_ids_d,
                                                          h->cell_fam_d, h->cell_pos_d, row0_d, h->fam_ncell_d, X, uor,
                                                          Xf, abar, ahar);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  surrogate_zero_pad_kernel<<<h->nfam, 128, 0, st>>>(row0_d, h->fam_ncell_d, S, X);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   InferArgs A;
   A.X = X;
@@ -1131,6 +1158,9 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   A.err = err;
   const size_t smem = 1024 + kTile * 128 * 3 + kHid * 128 * 5 + kOut * 128 * 2;
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(surrogate_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  float proj[100];
+  zero_row_sum_projector(proj);
+  STOMSFEM_TRY_CUDA(cudaMemcpyToSymbolAsync(kZeroRowSumProj, proj, sizeof(proj), 0, cudaMemcpyHostToDevice, st));
   surrogate_infer_kernel<<<L.ntiles, 128, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   surrogate_compact_kernel<<<sms * 4, 256, 0, st>>>(L.units, fell_back, err, list, count);
