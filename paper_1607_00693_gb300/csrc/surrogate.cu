@@ -518,18 +518,22 @@ struct InferArgs {
   int32_t* err;
 };
 
+// Threads of the inference CTA: two warps per TMEM lane quadrant, each
+// taking half of the hidden columns in the epilogues.
+constexpr int kInferThreads = 256;
+
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int rows, int kblocks,
                                            int ld, int tid) {
   // src rows of ld BF16 (ld = 64 * kblocks) -> kblocks swizzled [rows][64] blocks
   const int chunks = rows * kblocks * 8;
-  for (int c = tid; c < chunks; c += 128) {
+  for (int c = tid; c < chunks; c += kInferThreads) {
     const int row = c / (kblocks * 8), rem = c % (kblocks * 8), kb = rem / 8, ch = rem % 8;
     const uint4 v = reinterpret_cast<const uint4*>(src + (size_t)row * ld + kb * 64)[ch];
     *reinterpret_cast<uint4*>(dst + (size_t)kb * rows * 128 + tc::sw128_offset(row, ch * 8)) = v;
   }
 }
 
-__global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
+__global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(InferArgs A) {
   extern __shared__ __align__(1024) unsigned char ism_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ism_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sX = sm;                          // [128][64]            16 KB
@@ -559,7 +563,9 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
   const uint32_t taddr = taddr_s;
   const uint32_t aX = tc::smem_u32(sX), aH = tc::smem_u32(sH);
   const uint32_t aW[4] = {tc::smem_u32(sW1), tc::smem_u32(sW2), tc::smem_u32(sW3), tc::smem_u32(sW4)};
-  const int row = warp * 32 + lane;
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, half of the hidden columns
+  const int row = quad * 32 + lane;
+  const uint32_t tlane = (uint32_t)(quad * 32) << 16;
   bool ok = true;
   uint32_t phase = 0;
   for (int layer = 0; layer < 4 && ok; ++layer) {
@@ -582,9 +588,9 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
     if (!ok) break;
     if (layer < 3) {
       const int boff = layer == 0 ? oB1 : (layer == 1 ? oB2 : oB3);
-      for (int col = 0; col < kHid; col += 16) {
+      for (int col = half * (kHid / 2); col < (half + 1) * (kHid / 2); col += 16) {
         float v[16];
-        tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + col, v);
+        tc::tmem_ld16(taddr + tlane + col, v);
         uint32_t pk[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -602,9 +608,9 @@ __global__ void __launch_bounds__(128, 1) surrogate_infer_kernel(InferArgs A) {
   }
   if (!ok) {
     if (lane == 0) atomicOr(A.err, 2);
-  } else {
+  } else if (half == 0) {
     float y[16];
-    tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16), y);
+    tc::tmem_ld16(taddr + tlane, y);
     const int u = A.unit_of_row[tile * kTile + row];
     if (u >= 0) {
       float yf[16];
@@ -1161,7 +1167,7 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   float proj[100];
   zero_row_sum_projector(proj);
   STOMSFEM_TRY_CUDA(cudaMemcpyToSymbolAsync(kZeroRowSumProj, proj, sizeof(proj), 0, cudaMemcpyHostToDevice, st));
-  surrogate_infer_kernel<<<L.ntiles, 128, smem, st>>>(A);
+  surrogate_infer_kernel<<<L.ntiles, kInferThreads, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   surrogate_compact_kernel<<<sms * 4, 256, 0, st>>>(L.units, fell_back, err, list, count);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
