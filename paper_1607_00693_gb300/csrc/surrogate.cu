@@ -518,9 +518,10 @@ struct InferArgs {
   int32_t* err;
 };
 
-// Threads of the inference CTA: two warps per TMEM lane quadrant, each
-// taking half of the hidden columns in the epilogues.
-constexpr int kInferThreads = 256;
+// Threads of the inference CTA: kInferSplit warps per TMEM lane quadrant,
+// each taking kHid / kInferSplit of the hidden columns in the epilogues.
+constexpr int kInferSplit = 4;
+constexpr int kInferThreads = 128 * kInferSplit;
 
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int rows, int kblocks,
                                            int ld, int tid) {
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(Infer
   const uint32_t taddr = taddr_s;
   const uint32_t aX = tc::smem_u32(sX), aH = tc::smem_u32(sH);
   const uint32_t aW[4] = {tc::smem_u32(sW1), tc::smem_u32(sW2), tc::smem_u32(sW3), tc::smem_u32(sW4)};
-  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, half of the hidden columns
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, share of the hidden columns
   const int row = quad * 32 + lane;
   const uint32_t tlane = (uint32_t)(quad * 32) << 16;
   bool ok = true;
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(Infer
     if (!ok) break;
     if (layer < 3) {
       const int boff = layer == 0 ? oB1 : (layer == 1 ? oB2 : oB3);
-      for (int col = half * (kHid / 2); col < (half + 1) * (kHid / 2); col += 16) {
+      for (int col = half * (kHid / kInferSplit); col < (half + 1) * (kHid / kInferSplit); col += 16) {
         float v[16];
         tc::tmem_ld16(taddr + tlane + col, v);
         uint32_t pk[8];
