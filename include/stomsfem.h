@@ -8,6 +8,12 @@
  * the fine-grid Q1 stiffness of the sampled coefficient, solves the cell
  * problems that give the multiscale basis, forms the upscaled stiffness
  * and load, and then assembles and solves each sample's coarse system.
+ * Beside this plain path (FP64, FP32, FP32 + FP64 refinement) it offers
+ * the paper's other forms of the local upscaling -- the Petrov-Galerkin
+ * form, random interpolation in the local parameters, the reduced basis
+ * (also with an affine coefficient) -- a learned surrogate, the pieces of
+ * the two-level Monte Carlo estimator, and plans that replay a batch's
+ * whole step as one CUDA graph.
  *
  * Conventions shared by every call
  *  - Unit square, zero Dirichlet data on its boundary, constant load f.
