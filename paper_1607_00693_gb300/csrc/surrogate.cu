@@ -501,10 +501,27 @@ __global__ void surrogate_zero_pad_kernel(const int* __restrict__ fam_row0, cons
     x[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// Row and tile starts of every family for S samples (each family padded to
+// whole tiles of kTile rows), computed on the device so that a call copies
+// nothing from the host.
+__global__ void surrogate_tiles_kernel(int nfam, const int* __restrict__ fam_ncell, int S, int* __restrict__ row0,
+                                       int* __restrict__ tile0) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int t = 0;
+  for (int f = 0; f < nfam; ++f) {
+    row0[f] = t * kTile;
+    tile0[f] = t;
+    t += (int)(((long long)S * fam_ncell[f] + kTile - 1) / kTile);
+  }
+  row0[nfam] = t * kTile;
+  tile0[nfam] = t;
+}
+
 struct InferArgs {
   const __nv_bfloat16* X;
   const int* unit_of_row;
-  const int* tile_fam;    // family of each 128-row tile
+  const int* tile0;       // [nfam + 1] first tile of every family (rows of 128 units)
+  int nfam;
   const __nv_bfloat16* Wb;
   const float* W;         // FP32 master (biases)
   const float* box;       // [nfam][16][2]
@@ -547,7 +564,13 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(Infer
   __shared__ uint32_t taddr_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x;
-  const int fam = A.tile_fam[tile];
+  int lo = 0, hi = A.nfam;  // tile0[lo] <= tile < tile0[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (A.tile0[mid] <= tile) lo = mid;
+    else hi = mid;
+  }
+  const int fam = lo;
   const float* Wm = A.W + (size_t)fam * kParams;
   if (warp == 0) tc::tmem_alloc(&taddr_s, 128);
   if (tid == 0) tc::mbar_init(&mbar, 1);
@@ -1088,7 +1111,7 @@ InferLayout infer_layout(const stomsfem_surrogate* h, int S, std::vector<int>* r
   L.abar = o; o += al(L.units * 8);
   L.ahar = o; o += al(L.units * 8);
   L.Wb = o;   o += al((size_t)h->nfam * kWbSize * 2);
-  L.tfam = o; o += al((size_t)tiles * 4);
+  L.tfam = o; o += al((size_t)(h->nfam + 1) * 4);
   L.list = o; o += al(L.units * 4);
   L.count = o; o += 1024;
   L.err = o;  o += 1024;
@@ -1113,8 +1136,7 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   if (S == 0) return STOMSFEM_OK;
   if (!xi || !a || !Ke || !be || !fell_back || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
   if (!(delta >= 0.0)) return set_error(STOMSFEM_EINVAL, "delta must be >= 0");
-  std::vector<int> row0, tfam;
-  const InferLayout L = infer_layout(h, S, &row0, &tfam);
+  const InferLayout L = infer_layout(h, S, nullptr, nullptr);
   if (workspace_bytes < L.total)
     return set_error(STOMSFEM_ENOMEM, "surrogate workspace %zu < %zu", workspace_bytes, L.total);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1130,10 +1152,10 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   int32_t* count = reinterpret_cast<int32_t*>(ws + L.count);
   int32_t* err = reinterpret_cast<int32_t*>(ws + L.err);
   const int rho = h->grid.nf / h->grid.nc;
-  // family row starts for the prepare kernel (device copy in the count slot's neighbour)
-  int* row0_d = reinterpret_cast<int*>(ws + L.list);  // reused before the list is written
-  STOMSFEM_TRY_CUDA(cudaMemcpyAsync(tf, tfam.data(), sizeof(int) * tfam.size(), cudaMemcpyHostToDevice, st));
-  STOMSFEM_TRY_CUDA(cudaMemcpyAsync(row0_d, row0.data(), sizeof(int) * row0.size(), cudaMemcpyHostToDevice, st));
+  // family row starts (in the list slot, written before the list is) and tile starts
+  int* row0_d = reinterpret_cast<int*>(ws + L.list);
+  surrogate_tiles_kernel<<<1, 32, 0, st>>>(h->nfam, h->fam_ncell_d, S, row0_d, tf);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(uor, 0xFF, L.rows_pad * 4, st));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(count, 0, 8, st));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(err, 0, 8, st));
@@ -1148,7 +1170,8 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   InferArgs A;
   A.X = X;
   A.unit_of_row = uor;
-  A.tile_fam = tf;
+  A.tile0 = tf;
+  A.nfam = h->nfam;
   A.Wb = Wb;
   A.W = h->W;
   A.box = h->box;
