@@ -70,6 +70,50 @@ def test_host_validation_without_gpu(lib):
                                      None) == L.EINVAL
 
 
+def test_host_validation_of_the_further_forms(lib):
+    """Petrov-Galerkin, two-level Monte Carlo, affine reduced basis and plan
+    calls reject bad arguments on the host, before any device work."""
+    g = L.Grid(64, 8, 1.0)
+    v = ctypes.c_void_p(16)
+    # Petrov-Galerkin: bad precision; coarse band limit and NULL pointers
+    assert lib.stomsfem_upscale_pg(ctypes.byref(g), None, None, 0, 1, 5, 0, None, None, None, None, None, 0,
+                                   None) == L.EINVAL
+    assert lib.stomsfem_upscale_pg(ctypes.byref(g), None, None, 0, 0, 0, 0, None, None, None, None, None, 0,
+                                   None) == L.OK
+    g65 = L.Grid(130, 65, 1.0)
+    assert lib.stomsfem_coarse_solve_pg(ctypes.byref(g65), v, v, 1, v, None, None, None, v, 1 << 20,
+                                        None) == L.EINVAL
+    assert lib.stomsfem_coarse_solve_pg(ctypes.byref(g), None, None, 2, None, None, None, None, None, 0,
+                                        None) == L.EINVAL
+    assert lib.stomsfem_coarse_solve_pg(ctypes.byref(g), v, v, 2, v, v, None, None, v, 1 << 20,
+                                        None) == L.EINVAL   # moments given partly
+    # two-level pieces
+    big = L.Grid(128, 8, 1.0)
+    assert lib.stomsfem_fine_fem(ctypes.byref(big), v, 1, v, v, 1 << 20, None) == L.EINVAL
+    assert b"nf 128 > 64" in lib.stomsfem_last_error()
+    assert lib.stomsfem_fine_fem(ctypes.byref(g), v, -1, v, v, 1 << 20, None) == L.EINVAL
+    bad = L.Grid(64, 6, 1.0)
+    assert lib.stomsfem_restrict_to_coarse(ctypes.byref(bad), v, None, 1, v, None) == L.EINVAL
+    assert lib.stomsfem_mc_moments(0, 1, v, v, v, v, None) == L.EINVAL
+    assert lib.stomsfem_mc_moments(4, 1, v, None, v, v, None) == L.EINVAL
+    # affine reduced basis on a NULL handle
+    fld = L.Field(2, 4, 4, 0.1, 1.0, 0.0, 2.0)
+    assert lib.stomsfem_pod_set_affine(None, ctypes.byref(g), ctypes.byref(fld), 1e-6, None) == L.EINVAL
+    assert lib.stomsfem_pod_upscale_affine(None, v, None, 1, 0, v, v, None, None) == L.EINVAL
+    # plans
+    h = ctypes.c_void_p()
+    assert lib.stomsfem_plan_create(ctypes.byref(g), ctypes.byref(fld), None, 0, 0, 2, 2,
+                                    ctypes.byref(h)) == L.EINVAL            # S = 0
+    assert lib.stomsfem_plan_create(ctypes.byref(g), ctypes.byref(fld), None, 0, 4, 5, 2,
+                                    ctypes.byref(h)) == L.EINVAL            # precision
+    assert lib.stomsfem_plan_create(ctypes.byref(bad), ctypes.byref(fld), None, 0, 4, 2, 2,
+                                    ctypes.byref(h)) == L.EINVAL            # grid
+    assert lib.stomsfem_plan_step(None, v, v, None, None, None, 1, None) == L.EINVAL
+    assert lib.stomsfem_plan_tune(None, v, v, None, None, None, None) == L.EINVAL
+    assert lib.stomsfem_plan_info(None, None, None, None, None) == L.EINVAL
+    assert lib.stomsfem_plan_destroy(None) == L.OK
+
+
 def test_selftest_rejects_bad_limits(lib):
     import ctypes
     st = ctypes.c_int32(0)
