@@ -800,10 +800,11 @@ def main():
     # dram__bytes_write.sum per unit on a 32-sample launch of the same kernel
     # (same library version), times the units of this launch; None when the
     # library differs from the one the counters were taken on
-    per_unit = DRAM_BYTES_PER_UNIT.get((api.stomsfem_version(), form))
+    per_unit = (DRAM_BYTES_PER_UNIT.get((api.stomsfem_version(), form))
+                if args.workload == "upscale_1024" else None)
     traffic = per_unit * units_step if per_unit else None
     traffic_note = ("ncu counters of a 32-sample launch scaled by units (%.0f B/unit)" % per_unit
-                    if per_unit else "no counters for this library version and form")
+                    if per_unit else "no counters for this library version, form and workload")
     if rank == 0:
         line = {
             "metric": "coarse elements upscaled/s at H/h=32",
