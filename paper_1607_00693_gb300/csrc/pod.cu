@@ -574,6 +574,9 @@ struct PodSolveArgs {
 constexpr int kPodSolveWarps = 4;
 constexpr int kPodN2Max = (kPodMaxRho + 1) * (kPodMaxRho + 1);
 
+// REFINE: the FP64 stencil refinement of c (refine_iters > 0) is compiled
+// into its own kernel, so the unrefined launch carries only its own code.
+template <bool REFINE>
 __global__ void __launch_bounds__(kPodSolveWarps * 32)
 pod_solve_kernel(PodSolveArgs A) {
   __shared__ double s_c[kPodSolveWarps][32][4];
@@ -643,7 +646,7 @@ pod_solve_kernel(PodSolveArgs A) {
     const double* Wc = A.W + (size_t)cell * d.N2 * P0;
     const double* wl = A.wl + (size_t)cell * P0;
     double Kv[10], bv[4];
-    if (A.refine == 0) {
+    if constexpr (!REFINE) {
       // K = G_pp + G_pV c ; b = wl_p + wl_V c  (FP32 reduced quantities)
       int q = 0;
 #pragma unroll
@@ -1071,7 +1074,10 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
   const long long units = (long long)S * d.ncell;
   long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
   if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-  pod_solve_kernel<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  {
+    auto kern = A.refine > 0 ? pod_solve_kernel<true> : pod_solve_kernel<false>;
+    kern<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  }
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }
@@ -1178,7 +1184,10 @@ extern "C" int stomsfem_pod_upscale_affine(stomsfem_pod* pod, const double* xi, 
   const long long units = (long long)S * d.ncell;
   long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
   if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
-  pod_solve_kernel<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  {
+    auto kern = A.refine > 0 ? pod_solve_kernel<true> : pod_solve_kernel<false>;
+    kern<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
+  }
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }
