@@ -21,6 +21,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "ckpt.cuh"
@@ -645,9 +646,12 @@ pod_solve_kernel(PodSolveArgs A) {
     small_bwd<31>(Mq, Fq, lane, r, s_w[wib]);
     const double* Wc = A.W + (size_t)cell * d.N2 * P0;
     const double* wl = A.wl + (size_t)cell * P0;
-    double Kv[10], bv[4];
+    using TOut = typename std::conditional<REFINE, double, float>::type;
+    TOut Kv[10], bv[4];
     if constexpr (!REFINE) {
-      // K = G_pp + G_pV c ; b = wl_p + wl_V c  (FP32 reduced quantities)
+      // K = G_pp + G_pV c ; b = wl_p + wl_V c, in FP32 like the reduced
+      // solve itself (the warp-wide FP64 sums cost the narrow FP64 pipe
+      // more than the solve); converted to FP64 once, at the store
       int q = 0;
 #pragma unroll
       for (int l = 0; l < 4; ++l)
@@ -655,13 +659,11 @@ pod_solve_kernel(PodSolveArgs A) {
         for (int lp = l; lp < 4; ++lp) {
           float t = (lane < r) ? g[pidx(l, 4 + lane, P0)] * Fq[lp] : 0.f;
           t = warp_sum(t);
-          Kv[q++] = (double)g[pidx(l, lp, P0)] + (double)t;
+          Kv[q++] = g[pidx(l, lp, P0)] + t;
         }
+      const float wv = (lane < r) ? (float)wl[4 + lane] : 0.f;
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const double t = warp_sum((lane < r) ? wl[4 + lane] * (double)Fq[l] : 0.0);
-        bv[l] = wl[l] + t;
-      }
+      for (int l = 0; l < 4; ++l) bv[l] = (float)wl[l] + warp_sum(wv * Fq[l]);
     } else {
       // FP64 refinement of c through the fine stencil of A(omega)
       const int cx = cell % d.nc, cy = cell / d.nc;
