@@ -46,3 +46,23 @@ def test_library_plan_rejects_oversized_grids(orc):
     for bad in (dict(eps=0.0, nu_max=8), dict(eps=1e-3, nu_max=0), dict(eps=1e-3, nu_max=9)):
         with pytest.raises(_lib.StomsfemError):
             api.stomsfem_ri_plan(g, api.field_from_dict(w["field"]), bad["eps"], bad["nu_max"])
+
+
+def test_library_plan_matches_oracle_sigmoid_field(orc):
+    """The sigmoid transform's strength |L gain| / 4 exp(-d^2/w^2) (a field
+    with contrast 10 on the 64^2 / 8^2 grid): same families, directions and
+    degrees as the oracle."""
+    import math
+    from paper_1607_00693_gb300.build import build_library
+    from paper_1607_00693_gb300 import api
+    _, ri = orc
+    build_library()
+    fld = dict(kind=1, nbx=4, nby=4, width=0.1, scale=1.0, contrast_log=math.log(10.0), gain=1.0)
+    g = api.grid(64, 8, 1.0)
+    fam, ids, nu, nfam, npts = api.stomsfem_ri_plan(g, api.field_from_dict(fld), 1e-3, 6)
+    fo, keys, rep, dims = ri.families(64, 8, fld, 1e-3, 6)
+    np.testing.assert_array_equal(fam, fo)
+    assert nfam == len(keys) == 36
+    for c, d in enumerate(dims):
+        assert list(ids[c, :len(d)]) == [v for (_, _, _, v) in d]
+        assert list(nu[c, :len(d)]) == [n for (_, _, n, _) in d]
