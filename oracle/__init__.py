@@ -17,6 +17,10 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
                         stiffness_local_petrov: bilinear test functions,
                         deterministic load; non-symmetric coarse system by
                         banded LU); C code.
+* ``coarse_solve_bc`` -- the coarse system with prescribed values on chosen
+                        nodes and zero flux elsewhere (Sec. 5.2, Eqs.
+                        xsquarewave / ysquarewave), Galerkin or
+                        Petrov-Galerkin; C code.
 * ``fine_fem``      -- standard Q1 FEM on the fine grid; C code.
 * ``mc_moments``    -- Monte Carlo mean and variance (Eq. MCestimate),
                         two-pass.
@@ -76,6 +80,7 @@ def _L():
         lib.orc_cell_pg.argtypes = [i, i, d, p, i, i, i, p, p]
         lib.orc_upscale_pg.argtypes = [i, i, d, p, p, i, p, p, p, i]
         lib.orc_coarse_solve_pg.argtypes = [i, p, p, i, p]
+        lib.orc_coarse_solve_bc.argtypes = [i, i, p, p, p, p, i, p]
         lib.orc_patch_bounds.argtypes = [i, i, i, i, i, p, p, p, p]
         _lib = lib
     return _lib
@@ -201,6 +206,26 @@ def coarse_solve_pg(nc, Kpg, bpg):
     rc = _L().orc_coarse_solve_pg(nc, _ptr(Kpg), _ptr(bpg), S, _ptr(u))
     if rc != 0:
         raise ValueError("orc_coarse_solve_pg failed: %d" % rc)
+    return u
+
+
+def coarse_solve_bc(nc, K, b, dirichlet, g, pg=False):
+    """Coarse solve with mixed boundary data (Sec. 5.2, Eqs. xsquarewave /
+    ysquarewave): u = g where ``dirichlet`` [(nc+1)^2] is nonzero, zero flux
+    on the rest of the boundary; every coarse node is an unknown.  ``K`` is
+    the packed Galerkin K_e [S][nc*nc][10], or with ``pg`` the
+    Petrov-Galerkin S_e [S][nc*nc][16].  Returns u [S][(nc+1)^2]; raises on
+    a zero pivot (e.g. no Dirichlet node)."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    dm = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    assert dm.size == (nc + 1) ** 2 and g.size == dm.size
+    S = K.shape[0]
+    u = np.empty((S, (nc + 1) ** 2))
+    rc = _L().orc_coarse_solve_bc(nc, 1 if pg else 0, _ptr(K), _ptr(b), _ptr(dm), _ptr(g), S, _ptr(u))
+    if rc != 0:
+        raise ValueError("orc_coarse_solve_bc failed: %d" % rc)
     return u
 
 

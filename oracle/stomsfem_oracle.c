@@ -620,3 +620,63 @@ int orc_coarse_solve_pg(int nc, const double* Kpg, const double* bpg, int S, dou
   }
   return 0;
 }
+
+/* Mixed boundary data for the coarse system: the boundary conditions of
+ * the anisotropy study of the high-contrast example (Sec. 5.2, Eqs.
+ * xsquarewave and ysquarewave), i.e. prescribed values on chosen coarse
+ * nodes (lines inside the domain included) and zero flux on the rest of
+ * the boundary.  Every coarse node is an unknown.  The system over all
+ * (nc+1)^2 nodes is assembled from every cell, with no boundary row
+ * dropped (the natural condition needs nothing more): pg = 0 Galerkin from
+ * the packed K_e [S][nc*nc][10], pg = 1 Petrov-Galerkin from K [S][nc*nc][16]
+ * (row = test node J collects S_e[I_loc][J_loc]).  Then the row of every
+ * node k with dmask[k] != 0 is replaced by u_k = g[k], and the band is
+ * solved by the LU above.  A zero pivot (for instance no Dirichlet node at
+ * all, whose pure Neumann matrix is singular) returns -4 and leaves that
+ * sample's u NaN.  u [S][(nc+1)^2]. */
+int orc_coarse_solve_bc(int nc, int pg, const double* K, const double* b, const uint8_t* dmask,
+                        const double* g, int S, double* u) {
+  if (nc <= 0 || S < 0 || (pg != 0 && pg != 1)) return -1;
+  const int NN = nc + 1, n = NN * NN, bw = NN + 1, W = 2 * bw + 1;
+  const int KN = pg ? 16 : 10;
+  int ret = 0;
+  for (int s = 0; s < S; ++s) {
+    double* band = (double*)calloc((size_t)n * W, sizeof(double));
+    double* rhs = (double*)calloc((size_t)n, sizeof(double));
+    if (!band || !rhs) { free(band); free(rhs); return -3; }
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cx = 0; cx < nc; ++cx) {
+        const double* Kc = K + ((size_t)s * nc * nc + cy * nc + cx) * KN;
+        const double* B = b + ((size_t)s * nc * nc + cy * nc + cx) * 4;
+        double M[4][4]; /* M[row node][column node] of this cell's contribution */
+        if (pg) {
+          for (int t = 0; t < 4; ++t)
+            for (int c = 0; c < 4; ++c) M[t][c] = Kc[c * 4 + t];
+        } else {
+          int q = 0;
+          for (int l = 0; l < 4; ++l)
+            for (int lp = l; lp < 4; ++lp) { M[l][lp] = Kc[q]; M[lp][l] = Kc[q]; ++q; }
+        }
+        for (int r = 0; r < 4; ++r) {
+          const int rk = (cy + CDY[r]) * NN + (cx + CDX[r]);
+          rhs[rk] += B[r];
+          for (int c = 0; c < 4; ++c) {
+            const int ck = (cy + CDY[c]) * NN + (cx + CDX[c]);
+            band[(size_t)rk * W + (ck - rk + bw)] += M[r][c];
+          }
+        }
+      }
+    for (int k = 0; k < n; ++k)
+      if (dmask[k]) {
+        for (int d = 0; d < W; ++d) band[(size_t)k * W + d] = 0.0;
+        band[(size_t)k * W + bw] = 1.0;
+        rhs[k] = g[k];
+      }
+    const int rc = band_lu_solve(band, n, bw, rhs);
+    double* us = u + (size_t)s * n;
+    for (int k = 0; k < n; ++k) us[k] = rc == 0 ? rhs[k] : NAN;
+    free(band); free(rhs);
+    if (rc != 0) ret = -4;
+  }
+  return ret;
+}

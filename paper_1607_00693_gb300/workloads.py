@@ -99,6 +99,31 @@ def draw_oversample(nc, spec):
     return rng.integers(spec["lo"], spec["hi"] + 1, size=nc * nc).astype(np.int8)
 
 
+def mixed_bc(nc, axis="x", lines=(0.1, 0.9), period=0.5):
+    """Boundary data of the anisotropy study (Sec. 5.2, Eqs. xsquarewave /
+    ysquarewave): the values g on two coarse node lines, zero flux on the
+    rest of the boundary.  ``axis`` "x": lines x = lines[k] carrying g(y);
+    "y": lines y = lines[k] carrying g(x).  Each line snaps to the nearest
+    coarse node line; g is a 0/1 square wave of the given period (the
+    paper shows its oscillatory function only as a figure).  Returns
+    (dirichlet uint8 [(nc+1)^2], g float64 [(nc+1)^2]), node (i, j) at
+    j*(nc+1)+i."""
+    NN = nc + 1
+    t = np.arange(NN) / nc
+    wave = (np.mod(t, period) < 0.5 * period).astype(np.float64)
+    mask = np.zeros((NN, NN), dtype=np.uint8)
+    g = np.zeros((NN, NN))
+    for x in lines:
+        k = int(round(x * nc))
+        if axis == "x":
+            mask[:, k] = 1
+            g[:, k] = wave
+        else:
+            mask[k, :] = 1
+            g[k, :] = wave
+    return mask.reshape(-1), g.reshape(-1)
+
+
 def draw_batches(total, spec):
     """Uneven batch sizes summing to ``total``."""
     rng = np.random.default_rng(spec["seed"])
