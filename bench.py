@@ -546,6 +546,46 @@ def bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, direct_m
             "direct_ms_per_step": direct_ms, "graph_ready": info[2], "device_bytes": info[3]}
 
 
+def bench_mixed_bc(api, g, nn, stream, dev, K, b, pg, reps=5):
+    """Coarse solve with mixed boundary data (Sec. 5.2, Eqs. xsquarewave /
+    ysquarewave: the square-wave lines x = 0.1 and 0.9, zero flux on the
+    rest of the boundary) on a step's own K_e and b_e, timed beside the
+    plain zero-Dirichlet solve of the same batch."""
+    import torch
+    from paper_1607_00693_gb300 import workloads as W
+    S = K.shape[0]
+    dm_np, gv_np = W.mixed_bc(g.nc, axis="x")
+    dm, gv = torch.from_numpy(dm_np).to(dev), torch.from_numpy(gv_np).to(dev)
+    u = torch.empty((S, nn), dtype=torch.float64, device=dev)
+    ws = torch.empty(api.stomsfem_coarse_bc_workspace_size(g, pg, S), dtype=torch.uint8, device=dev)
+    if pg:
+        ws0 = torch.empty(api.stomsfem_coarse_pg_workspace_size(g, S), dtype=torch.uint8, device=dev)
+        plain = lambda: api.stomsfem_coarse_solve_pg(g, K, b, u, workspace=ws0, stream=stream)
+    else:
+        ws0 = torch.empty(api.stomsfem_coarse_workspace_size(g, S), dtype=torch.uint8, device=dev)
+        plain = lambda: api.stomsfem_coarse_solve(g, K, b, u, workspace=ws0, stream=stream)
+    mixed = lambda: api.stomsfem_coarse_solve_bc(g, pg, K, b, dm, gv, u, workspace=ws, stream=stream)
+
+    def timed_ms(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms0 = timed_ms(plain)
+    ms = timed_ms(mixed)
+    return {"form": "petrov_galerkin" if pg else "galerkin", "samples": S, "nodes": nn, "ms_per_call": ms,
+            "samples_per_s": S / (ms / 1e3), "zero_dirichlet_ms_per_call": ms0,
+            "finite": bool(torch.isfinite(u).all().item()), "gpu_launches_per_call": 1}
+
+
 def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u64_gal):
     """Petrov-Galerkin form (Eq. stiffness_local_petrov) of the FP32 step on
     the same workload: sample a, upscale with bilinear test functions (16
@@ -588,6 +628,7 @@ def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u
         e1.record(stream)
         stream.synchronize()
     ms = e0.elapsed_time(e1)
+    mixed = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 1)
     del bf
     b32, b64 = bufs(Bc, api.FP32), bufs(Bc, api.FP64)
     with torch.cuda.stream(stream):
@@ -599,7 +640,7 @@ def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u
     return {"form": "fp32", "samples_per_step": B, "units_per_s": B * ncell * steps / (ms / 1e3),
             "ms_per_step": ms / steps, "coarse_rel_l2_vs_fp64_pg": rel(u32, u64),
             "pg_vs_galerkin_fp64_rel_l2": rel(u64, u64_gal[:Bc]),
-            "gpu_launches_per_step": 7}
+            "gpu_launches_per_step": 7, "mixed_bc": mixed}
 
 
 def main():
@@ -788,6 +829,7 @@ def main():
         extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
         extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
         extra["two_level_mc"] = bench_two_level(api, dev, stream)
+        extra["mixed_bc"] = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)
         # kernels of each form's own timed calls (outside the step's timed region)
         for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3), ("pod_affine", n4)):
             extra[k]["gpu_launches_timed_calls"] = n

@@ -318,6 +318,36 @@ int stomsfem_coarse_solve_pg(const stomsfem_grid* grid, const double* Ke, const 
                              double* u, double* mean, double* m2, double* count, void* workspace,
                              size_t workspace_bytes, stomsfem_stream_t stream);
 
+/* Scratch needed by stomsfem_coarse_solve_bc for the form pg (0 Galerkin,
+ * 1 Petrov-Galerkin). */
+int stomsfem_coarse_bc_workspace_size(const stomsfem_grid* grid, int32_t pg, int32_t S, size_t* bytes);
+
+/* Coarse solve with mixed boundary data, the boundary conditions of the
+ * anisotropy study of the high-contrast example (Sec. 5.2, Eqs.
+ * xsquarewave and ysquarewave: prescribed values on node lines, zero flux
+ * on the rest of the boundary).  Every coarse node is an unknown:
+ *   dirichlet [(nc+1)^2] uint8 (device)  nonzero: u is prescribed there
+ *                                        (any node, interior lines too),
+ *   g         [(nc+1)^2] float64 (device) the prescribed values (read
+ *                                        where dirichlet is nonzero),
+ * node (i, j) at j*(nc+1)+i, shared by the S samples.  The other nodes
+ * carry the natural condition (zero flux on the boundary).  pg = 0:
+ * Galerkin, K = Ke [S][nc*nc][10] and b = be [S][nc*nc][4] of
+ * stomsfem_upscale, symmetric elimination of the prescribed nodes and the
+ * blocked banded Cholesky (half bandwidth nc + 2); pg = 1:
+ * Petrov-Galerkin, K [S][nc*nc][16] and b [S][nc*nc][4] of
+ * stomsfem_upscale_pg, banded LU without pivoting.  One warp per sample.
+ * u [S][(nc+1)^2] takes every node (g at the prescribed ones); mean, m2,
+ * count as stomsfem_coarse_solve.  The caller makes the problem well posed
+ * (at least one prescribed node in every part of the domain the cells
+ * connect): a sample whose factorisation meets a non-positive (pg = 0) or
+ * a zero or non-finite (pg = 1) pivot gets NaN in u.  Errors: EINVAL (also
+ * nc > 62, pg not 0 or 1), ENOMEM (workspace below two slots), ECUDA. */
+int stomsfem_coarse_solve_bc(const stomsfem_grid* grid, int32_t pg, const double* K, const double* b,
+                             const uint8_t* dirichlet, const double* g, int32_t S, double* u, double* mean,
+                             double* m2, double* count, void* workspace, size_t workspace_bytes,
+                             stomsfem_stream_t stream);
+
 /* ---------------------------------------------------------------------
  * Reduced-basis (POD) upscaling, Sec. 3.2 (Eq. KLphi, Eqs. localRB and
  * localRBsystem, Algs. 3 and 4), for cells without oversampling.

@@ -80,6 +80,9 @@ _SIG = {
     "stomsfem_coarse_pg_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
     "stomsfem_coarse_solve_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P, _SZ,
                                                 _P]),
+    "stomsfem_coarse_bc_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(_SZ)]),
+    "stomsfem_coarse_solve_bc": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P,
+                                                _SZ, _P]),
     "stomsfem_pod_set_affine": (ctypes.c_int, [_P, ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double,
                                                _P]),
     "stomsfem_pod_upscale_affine": (ctypes.c_int, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),

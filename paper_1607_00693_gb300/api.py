@@ -419,6 +419,31 @@ def stomsfem_coarse_solve_pg(g: Grid, Ke, be, u, mean=None, m2=None, count=None,
         workspace.numel(), _stream(stream)))
 
 
+def stomsfem_coarse_bc_workspace_size(g: Grid, pg, S):
+    b = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_coarse_bc_workspace_size(ctypes.byref(g), int(bool(pg)), int(S), ctypes.byref(b)))
+    return b.value
+
+
+def stomsfem_coarse_solve_bc(g: Grid, pg, K, b, dirichlet, gval, u, mean=None, m2=None, count=None,
+                             workspace=None, stream=None):
+    """Mixed boundary data: u = gval where ``dirichlet`` (uint8
+    [(nc+1)^2]) is nonzero, zero flux on the rest of the boundary; ``pg``
+    selects the Petrov-Galerkin system (K [S][nc*nc][16])."""
+    S = K.shape[0]
+    ncell = g.nc * g.nc
+    nn = (g.nc + 1) ** 2
+    if workspace is None:
+        workspace = torch.empty(stomsfem_coarse_bc_workspace_size(g, pg, S), dtype=torch.uint8, device=K.device)
+    L.check(L.lib().stomsfem_coarse_solve_bc(
+        ctypes.byref(g), int(bool(pg)), _dev(K, torch.float64, (S, ncell, 16 if pg else 10), "K"),
+        _dev(b, torch.float64, (S, ncell, 4), "b"), _dev(dirichlet, torch.uint8, (nn,), "dirichlet"),
+        _dev(gval, torch.float64, (nn,), "g"), S, _dev(u, torch.float64, (S, nn), "u"),
+        _dev(mean, torch.float64, (nn,), "mean"), _dev(m2, torch.float64, (nn,), "m2"),
+        _dev(count, torch.float64, (1,), "count"), _dev(workspace, torch.uint8, None, "workspace"),
+        workspace.numel(), _stream(stream)))
+
+
 def stomsfem_pod_set_affine(h, g: Grid, fld: Field, tau=1e-6, stream=None):
     L.check(L.lib().stomsfem_pod_set_affine(h, ctypes.byref(g), ctypes.byref(fld), float(tau), _stream(stream)))
 

@@ -1,5 +1,6 @@
 // Coarse assembly and solve (Eq. upscaleSUF) and Monte Carlo moments
-// (Eq. MCestimate).  One warp per sample: the coarse matrix over the
+// (Eq. MCestimate); the same with mixed boundary data (Sec. 5.2, Eqs.
+// xsquarewave / ysquarewave).  One warp per sample: the coarse matrix over the
 // (nc-1)^2 interior coarse nodes is again a 9-point-stencil SPD matrix,
 // assembled row by row from the K_e of the four cells around each node
 // and factorised in FP64 with the blocked banded Cholesky of the cell
@@ -194,6 +195,136 @@ coarse_blk_kernel(int nc, int S, const double* __restrict__ Ke, const double* __
   }
 }
 
+// Mixed boundary data (the anisotropy study of Sec. 5.2, Eqs. xsquarewave
+// and ysquarewave): every coarse node is an unknown (mx = nc + 1 nodes per
+// row, half bandwidth mx + 1).  A node with dm != 0 has the row u = g; a
+// free node's row sums the cells around it that exist (zero flux needs no
+// other term on the boundary), and each coupling to a prescribed neighbour
+// moves, times its g, to the right-hand side (symmetric elimination, so the
+// matrix stays SPD for the blocked Cholesky).
+struct CoarseBcGen {
+  const double* Ke;   // this sample [nc*nc][10]
+  const double* be;   // [nc*nc][4]
+  const uint8_t* dm;  // [(nc+1)^2] nonzero: prescribed value
+  const double* gv;   // [(nc+1)^2] the prescribed values
+  int nc, mx;         // mx = nc + 1 nodes per row
+  static constexpr int kRaw = 8;
+  using Raw = CoarseBlkGen::Raw;
+  __device__ __forceinline__ double K(int cx, int cy, int l, int lp) const {
+    return __ldg(Ke + (size_t)(cy * nc + cx) * 10 + kidx(l, lp));
+  }
+  __device__ __forceinline__ double B(int cx, int cy, int l) const {
+    return __ldg(be + (size_t)(cy * nc + cx) * 4 + l);
+  }
+  __device__ __forceinline__ void load(int r, Raw& w) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w.e[k] = 0.0;
+    if (__ldg(dm + r)) {
+      w.e[0] = 1.0;
+      w.rhs = __ldg(gv + r);
+      return;
+    }
+    const int J = r / mx, I = r - J * mx;
+    const bool hw = I > 0, he = I < nc, hs = J > 0, hn = J < nc;
+    // couplings to the eight neighbours, from the cells around (I, J):
+    // SW cell (I-1, J-1) has the node as corner 2, SE cell (I, J-1) as 3,
+    // NE cell (I, J) as 0, NW cell (I-1, J) as 1
+    double cW = 0, cE = 0, cS = 0, cN = 0, cSW = 0, cSE = 0, cNE = 0, cNW = 0, d = 0, f = 0;
+    if (hw && hs) {
+      d += K(I - 1, J - 1, 2, 2);
+      cSW += K(I - 1, J - 1, 2, 0);
+      cS += K(I - 1, J - 1, 2, 1);
+      cW += K(I - 1, J - 1, 2, 3);
+      f += B(I - 1, J - 1, 2);
+    }
+    if (he && hs) {
+      d += K(I, J - 1, 3, 3);
+      cS += K(I, J - 1, 3, 0);
+      cSE += K(I, J - 1, 3, 1);
+      cE += K(I, J - 1, 3, 2);
+      f += B(I, J - 1, 3);
+    }
+    if (he && hn) {
+      d += K(I, J, 0, 0);
+      cE += K(I, J, 0, 1);
+      cNE += K(I, J, 0, 2);
+      cN += K(I, J, 0, 3);
+      f += B(I, J, 0);
+    }
+    if (hw && hn) {
+      d += K(I - 1, J, 1, 1);
+      cW += K(I - 1, J, 1, 0);
+      cN += K(I - 1, J, 1, 2);
+      cNW += K(I - 1, J, 1, 3);
+      f += B(I - 1, J, 1);
+    }
+    // a neighbour that exists is either prescribed (to the right-hand side)
+    // or free; the free ones below the diagonal are the band entries
+    auto nb = [&](bool exists, int q, double c, double* band) {
+      if (!exists) return;
+      if (__ldg(dm + q))
+        f -= c * __ldg(gv + q);
+      else if (band)
+        *band = c;
+    };
+    nb(hw, r - 1, cW, &w.e[1]);
+    nb(he && hs, r - mx + 1, cSE, &w.e[2]);
+    nb(hs, r - mx, cS, &w.e[3]);
+    nb(hw && hs, r - mx - 1, cSW, &w.e[4]);
+    nb(he, r + 1, cE, nullptr);
+    nb(hn, r + mx, cN, nullptr);
+    nb(he && hn, r + mx + 1, cNE, nullptr);
+    nb(hw && hn, r + mx - 1, cNW, nullptr);
+    w.e[0] = d;
+    w.rhs = f;
+  }
+  __device__ __forceinline__ void prefetch(int r, double* dst) const {
+    Raw w;
+    load(r, w);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dst[k] = w.e[k];
+    dst[5] = w.rhs;
+  }
+  __device__ __forceinline__ void from_smem(const double* src, Raw& w) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w.e[k] = src[k];
+    w.rhs = src[5];
+  }
+  template <typename T, int NR = 1>
+  __device__ __forceinline__ void make(int, const Raw& w, T e[5], T* rh) const {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) e[k] = (T)w.e[k];
+    rh[0] = (T)w.rhs;
+  }
+};
+
+// One warp per sample, as coarse_blk_kernel, over all (nc+1)^2 nodes.
+template <int RPL>
+__global__ void __launch_bounds__(kCoarseBlkWarps * 32)
+coarse_bc_kernel(int nc, int S, const double* __restrict__ Ke, const double* __restrict__ be,
+                 const uint8_t* __restrict__ dm, const double* __restrict__ gv, double* __restrict__ u,
+                 unsigned char* ws, size_t slot_bytes, size_t l_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int mx = nc + 1, n = mx * mx, b = mx + 1;
+  const BlkSmem<double> sm =
+      make_blk<double>(smem + wib * blk_smem_bytes<double>(16, b, CoarseBcGen::kRaw), 16, b, CoarseBcGen::kRaw);
+  const int gw = blockIdx.x * kCoarseBlkWarps + wib, nw = gridDim.x * kCoarseBlkWarps;
+  unsigned char* slot = ws + (size_t)gw * slot_bytes;
+  double* Lg = reinterpret_cast<double*>(slot);
+  double* x = reinterpret_cast<double*>(slot + l_bytes);
+  for (int s = gw; s < S; s += nw) {
+    const CoarseBcGen gen{Ke + (size_t)s * nc * nc * 10, be + (size_t)s * nc * nc * 4, dm, gv, nc, mx};
+    const int fail = blk_factor<32, double, 1, RPL>(gen, n, b, b, sm, Lg, x, lane);
+    blk_backward<32, double, 1>(n, b, b, sm, Lg, x, lane);
+    __syncwarp();
+    double* us = u + (size_t)s * n;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    for (int q = lane; q < n; q += 32) us[q] = fail < 0 ? x[q] : nanv;
+    __syncwarp();
+  }
+}
+
 // Merge this batch's moments into the running ones (pairwise update of
 // Chan, Golub and LeVeque): batch mean/M2 two-pass, then combine.
 __global__ void moments_kernel(int nn, int S, const double* __restrict__ u, double* mean, double* m2,
@@ -256,15 +387,65 @@ __device__ __forceinline__ PgRowPrefetch pg_row_load(int nc, const double* __res
   return p;
 }
 
+// Row J of the system with mixed boundary data (every node a row, nc + 1
+// per row, half bandwidth nc + 2): a prescribed node's row is u_J = g_J
+// (lane 0); in a free row the lanes take the cells and trial corners as
+// above, cells outside the domain give nothing (zero flux), and a trial
+// node with a prescribed value moves its contribution times g to the load.
+__device__ __forceinline__ PgRowPrefetch pg_row_load_bc(int nc, const double* __restrict__ Ks,
+                                                        const double* __restrict__ bs, const uint8_t* __restrict__ dm,
+                                                        const double* __restrict__ gv, int J, int n, int lane) {
+  PgRowPrefetch p{0.0, -1, 0.0};
+  if (J >= n || lane >= 16) return p;
+  const int NN = nc + 1, bw = nc + 2;
+  if (dm[J]) {
+    if (lane == 0) {
+      p.v = 1.0;
+      p.off = bw;
+      p.b = gv[J];
+    }
+    return p;
+  }
+  const int i = J % NN, j = J / NN;
+  const int c = lane >> 2, t = lane & 3;
+  const int cx = i - 1 + (c == 1 || c == 2), cy = j - 1 + (c >= 2), r = (c + 2) & 3;
+  if (cx < 0 || cx >= nc || cy < 0 || cy >= nc) return p;
+  const int tx = cx + (t == 1 || t == 2), ty = cy + (t >= 2);
+  const size_t cell = (size_t)cy * nc + cx;
+  const int I = ty * NN + tx;
+  const double v = Ks[cell * 16 + t * 4 + r];
+  if (dm[I]) {
+    p.b = -v * gv[I];
+  } else {
+    p.v = v;
+    p.off = I - J + bw;
+  }
+  if (t == 0) p.b += bs[cell * 4 + r];
+  return p;
+}
+
+// BC: the system over every node with mixed boundary data (pg_row_load_bc),
+// else the interior nodes with zero Dirichlet data.
+template <bool BC>
 __global__ void __launch_bounds__(kCoarsePgWarps * 32)
 coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __restrict__ bpg,
-                 double* __restrict__ u, unsigned char* __restrict__ ws, size_t slot_bytes) {
+                 const uint8_t* __restrict__ dm, const double* __restrict__ gv, double* __restrict__ u,
+                 unsigned char* __restrict__ ws, size_t slot_bytes) {
   extern __shared__ __align__(16) unsigned char smem_pg[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // row pitch PW = W + 1 (even): consecutive lanes, one row apart, then
   // differ by an odd number of doubles and meet different banks
-  const int bw = nc, W = 2 * nc + 1, PW = W + 1, R = nc + 1;
-  const int mi = nc - 1, n = mi * mi, NN = nc + 1;
+  const int bw = BC ? nc + 2 : nc, W = 2 * bw + 1, PW = W + 1, R = bw + 1;
+  const int mi = BC ? nc + 1 : nc - 1, n = mi * mi, NN = nc + 1;
+  auto row_load = [&](const double* Ks, const double* bs, int J) {
+    if constexpr (BC)
+      return pg_row_load_bc(nc, Ks, bs, dm, gv, J, n, lane);
+    else
+      return pg_row_load(nc, Ks, bs, J, n, lane);
+  };
+  // lanes whose load term is added: one per cell, or (BC) every lane with
+  // a term (prescribed trial nodes move theirs to the load)
+  auto adds_b = [&](const PgRowPrefetch& p) { return lane < 16 && (BC ? p.b != 0.0 : (lane & 3) == 0); };
   double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 2 * R);
   double* yr = Rw + (size_t)R * PW;  // right-hand sides of the window rows
   double* xr = yr + R;              // ring of the last bw unknowns
@@ -280,16 +461,16 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
     for (int q = lane; q < R; q += 32) yr[q] = 0.0;
     __syncwarp();
     for (int J = 0; J < R && J < n; ++J) {
-      const PgRowPrefetch p = pg_row_load(nc, Ks, bs, J, n, lane);
+      const PgRowPrefetch p = row_load(Ks, bs, J);
       if (p.off >= 0) atomicAdd(&Rw[(size_t)(J % R) * PW + p.off], p.v);
-      if (lane < 16 && (lane & 3) == 0) atomicAdd(&yr[J % R], p.b);
+      if (adds_b(p)) atomicAdd(&yr[J % R], p.b);
       __syncwarp();
     }
-    PgRowPrefetch next = pg_row_load(nc, Ks, bs, R, n, lane);
+    PgRowPrefetch next = row_load(Ks, bs, R);
     bool bad = false;
     for (int k = 0; k < n; ++k) {
       const PgRowPrefetch cur = next;
-      next = pg_row_load(nc, Ks, bs, k + R + 1, n, lane);  // in flight during this step
+      next = row_load(Ks, bs, k + R + 1);  // in flight during this step
       double* P = Rw + (size_t)(k % R) * PW;
       const double piv = P[bw];
       if (!(fabs(piv) > 0.0) || !(fabs(piv) < 1e300)) bad = true;
@@ -317,7 +498,7 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       __syncwarp();
       if (k + R < n) {
         if (cur.off >= 0) atomicAdd(&P[cur.off], cur.v);
-        if (lane < 16 && (lane & 3) == 0) atomicAdd(&yr[k % R], cur.b);
+        if (adds_b(cur)) atomicAdd(&yr[k % R], cur.b);
       }
       __syncwarp();
     }
@@ -334,24 +515,40 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       if (lane == 0) xr[k % R] = xk;
       __syncwarp();
       if (lane == 0) {
-        const int i = k % mi + 1, j = k / mi + 1;
-        us[j * NN + i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : xk;
+        const int q = BC ? k : (k / mi + 1) * NN + (k % mi + 1);
+        us[q] = bad ? __longlong_as_double(0x7ff8000000000000ll) : xk;
       }
     }
-    for (int q = lane; q < NN * NN; q += 32) {
-      const int i = q % NN, j = q / NN;
-      if (i == 0 || j == 0 || i == nc || j == nc) us[q] = 0.0;
+    if constexpr (!BC) {
+      for (int q = lane; q < NN * NN; q += 32) {
+        const int i = q % NN, j = q / NN;
+        if (i == 0 || j == 0 || i == nc || j == nc) us[q] = 0.0;
+      }
     }
     __syncwarp();
   }
 }
 
-static size_t coarse_pg_slot_bytes(int nc) {
-  const int mi = nc - 1, n = mi * mi > 0 ? mi * mi : 1;
-  return ((size_t)n * (nc + 2) * 8 + 255) & ~size_t(255);
+// Sizes of the Petrov-Galerkin solve: half bandwidth bw (nc, or nc + 2 with
+// mixed boundary data, whose rows are all (nc+1)^2 nodes).
+static size_t coarse_pg_slot_bytes(int nc, bool bc = false) {
+  const int mi = bc ? nc + 1 : nc - 1, n = mi * mi > 0 ? mi * mi : 1, bw = bc ? nc + 2 : nc;
+  return ((size_t)n * (bw + 2) * 8 + 255) & ~size_t(255);
 }
-static size_t coarse_pg_smem(int nc) {
-  return (size_t)kCoarsePgWarps * ((size_t)(nc + 1) * (2 * nc + 2) + 2 * (nc + 1)) * 8;
+static size_t coarse_pg_smem(int nc, bool bc = false) {
+  const int bw = bc ? nc + 2 : nc;
+  return (size_t)kCoarsePgWarps * ((size_t)(bw + 1) * (2 * bw + 2) + 2 * (bw + 1)) * 8;
+}
+
+// Galerkin solve with mixed boundary data: factor blocks of the (nc+1)^2
+// node system (half bandwidth nc + 2), then the solution.
+static size_t coarse_bc_l_bytes(int nc) {
+  const int n = (nc + 1) * (nc + 1);
+  return (blk_factor_elems(n, nc + 2) * 8 + 255) & ~size_t(255);
+}
+static size_t coarse_bc_slot_bytes(int nc) {
+  const int n = (nc + 1) * (nc + 1);
+  return coarse_bc_l_bytes(nc) + (((size_t)n * 8 + 255) & ~size_t(255));
 }
 
 // Slot of one sample: the factor blocks, then the solution.
@@ -450,12 +647,80 @@ extern "C" int stomsfem_coarse_solve_pg(const stomsfem_grid* grid, const double*
   if (blocks > need) blocks = need;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t smem = coarse_pg_smem(grid->nc);
-  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(coarse_pg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  coarse_pg_kernel<<<(unsigned)blocks, kCoarsePgWarps * 32, smem, st>>>(
-      grid->nc, S, Kpg, bpg, u, static_cast<unsigned char*>(workspace), sb);
+  STOMSFEM_TRY_CUDA(
+      cudaFuncSetAttribute(coarse_pg_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  coarse_pg_kernel<false><<<(unsigned)blocks, kCoarsePgWarps * 32, smem, st>>>(
+      grid->nc, S, Kpg, bpg, nullptr, nullptr, u, static_cast<unsigned char*>(workspace), sb);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   if (mom) {
     const int nn = (grid->nc + 1) * (grid->nc + 1);
+    moments_kernel<<<(nn + 127) / 128, 128, 0, st>>>(nn, S, u, mean, m2, count);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+    count_kernel<<<1, 1, 0, st>>>(count, S);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+  }
+  return STOMSFEM_OK;
+}
+
+// Largest coarse grid of the solves with mixed boundary data: their half
+// bandwidth nc + 2 stays within the 64 of the other coarse solves.
+constexpr int kCoarseBcMaxNc = 62;
+
+extern "C" int stomsfem_coarse_bc_workspace_size(const stomsfem_grid* grid, int32_t pg, int32_t S, size_t* bytes) {
+  if (!grid || grid->nc <= 0 || S < 0 || !bytes || (pg != 0 && pg != 1))
+    return set_error(STOMSFEM_EINVAL, "bad arguments");
+  const int sms = device_sm_count();
+  const int warps = pg ? kCoarsePgWarps : kCoarseBlkWarps;
+  long long slots = (long long)(sms > 0 ? sms : 152) * (pg ? 4 : 8);
+  if (slots > S) slots = S;
+  if (slots < warps) slots = warps;
+  *bytes = (pg ? coarse_pg_slot_bytes(grid->nc, true) : coarse_bc_slot_bytes(grid->nc)) * (size_t)slots;
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_coarse_solve_bc(const stomsfem_grid* grid, int32_t pg, const double* K, const double* b,
+                                        const uint8_t* dirichlet, const double* g, int32_t S, double* u,
+                                        double* mean, double* m2, double* count, void* workspace,
+                                        size_t workspace_bytes, stomsfem_stream_t stream) {
+  if (!grid || grid->nc <= 0) return set_error(STOMSFEM_EINVAL, "bad grid");
+  if (grid->nc > kCoarseBcMaxNc)
+    return set_error(STOMSFEM_EINVAL, "nc %d > %d (bandwidth limit with mixed boundary data)", grid->nc,
+                     kCoarseBcMaxNc);
+  if (pg != 0 && pg != 1) return set_error(STOMSFEM_EINVAL, "pg must be 0 or 1");
+  if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
+  if (S == 0) return STOMSFEM_OK;
+  if (!K || !b || !dirichlet || !g || !u || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  const bool mom = mean || m2 || count;
+  if (mom && !(mean && m2 && count))
+    return set_error(STOMSFEM_EINVAL, "mean, m2 and count must be given together");
+  const int nc = grid->nc;
+  const int warps = pg ? kCoarsePgWarps : kCoarseBlkWarps;
+  const size_t sb = pg ? coarse_pg_slot_bytes(nc, true) : coarse_bc_slot_bytes(nc);
+  long long slots = (long long)(workspace_bytes / sb);
+  if (slots < warps)
+    return set_error(STOMSFEM_ENOMEM, "coarse workspace %zu < %d slots of %zu", workspace_bytes, warps, sb);
+  long long blocks = slots / warps;
+  const long long need = ((long long)S + warps - 1) / warps;
+  if (blocks > need) blocks = need;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  if (pg) {
+    const size_t smem = coarse_pg_smem(nc, true);
+    STOMSFEM_TRY_CUDA(
+        cudaFuncSetAttribute(coarse_pg_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    coarse_pg_kernel<true><<<(unsigned)blocks, kCoarsePgWarps * 32, smem, st>>>(nc, S, K, b, dirichlet, g, u, ws, sb);
+  } else {
+    const int bnd = nc + 2;
+    const size_t smem = blk_smem_bytes<double>(16, bnd, CoarseBcGen::kRaw) * kCoarseBlkWarps;
+    const int rpl = (16 + bnd + 31) / 32;
+    auto kern = rpl <= 1 ? coarse_bc_kernel<1> : rpl == 2 ? coarse_bc_kernel<2> : coarse_bc_kernel<3>;
+    STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)blocks, kCoarseBlkWarps * 32, smem, st>>>(nc, S, K, b, dirichlet, g, u, ws, sb,
+                                                                coarse_bc_l_bytes(nc));
+  }
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  if (mom) {
+    const int nn = (nc + 1) * (nc + 1);
     moments_kernel<<<(nn + 127) / 128, 128, 0, st>>>(nn, S, u, mean, m2, count);
     STOMSFEM_TRY_CUDA(cudaGetLastError());
     count_kernel<<<1, 1, 0, st>>>(count, S);

@@ -71,8 +71,9 @@ def test_host_validation_without_gpu(lib):
 
 
 def test_host_validation_of_the_further_forms(lib):
-    """Petrov-Galerkin, two-level Monte Carlo, affine reduced basis and plan
-    calls reject bad arguments on the host, before any device work."""
+    """Petrov-Galerkin, mixed boundary data, two-level Monte Carlo, affine
+    reduced basis and plan calls reject bad arguments on the host, before
+    any device work."""
     g = L.Grid(64, 8, 1.0)
     v = ctypes.c_void_p(16)
     # Petrov-Galerkin: bad precision; coarse band limit and NULL pointers
@@ -87,6 +88,23 @@ def test_host_validation_of_the_further_forms(lib):
                                         None) == L.EINVAL
     assert lib.stomsfem_coarse_solve_pg(ctypes.byref(g), v, v, 2, v, v, None, None, v, 1 << 20,
                                         None) == L.EINVAL   # moments given partly
+    # mixed boundary data: form, band limit, NULL pointers, partial moments
+    sz = ctypes.c_size_t()
+    assert lib.stomsfem_coarse_bc_workspace_size(ctypes.byref(g), 2, 4, ctypes.byref(sz)) == L.EINVAL
+    assert lib.stomsfem_coarse_bc_workspace_size(ctypes.byref(g), 1, 4, ctypes.byref(sz)) == L.OK
+    assert sz.value >= 2 * 81 * 12 * 8      # two slots of 81 U rows of half bandwidth 10
+    assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g), 0, None, None, None, None, 0, None, None, None, None,
+                                        None, 0, None) == L.OK
+    g63 = L.Grid(63, 63, 1.0)
+    assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g63), 0, v, v, v, v, 1, v, None, None, None, v, 1 << 20,
+                                        None) == L.EINVAL
+    assert b"nc 63 > 62" in lib.stomsfem_last_error()
+    assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g), 2, v, v, v, v, 1, v, None, None, None, v, 1 << 20,
+                                        None) == L.EINVAL
+    assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g), 0, v, v, None, v, 1, v, None, None, None, v, 1 << 20,
+                                        None) == L.EINVAL
+    assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g), 1, v, v, v, v, 1, v, v, None, None, v, 1 << 20,
+                                        None) == L.EINVAL
     # two-level pieces
     big = L.Grid(128, 8, 1.0)
     assert lib.stomsfem_fine_fem(ctypes.byref(big), v, 1, v, v, 1 << 20, None) == L.EINVAL
