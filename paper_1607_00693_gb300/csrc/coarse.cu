@@ -388,43 +388,67 @@ __device__ __forceinline__ PgRowPrefetch pg_row_load(int nc, const double* __res
 }
 
 // Row J of the system with mixed boundary data (every node a row, nc + 1
-// per row, half bandwidth nc + 2): a prescribed node's row is u_J = g_J
-// (lane 0); in a free row the lanes take the cells and trial corners as
-// above, cells outside the domain give nothing (zero flux), and a trial
-// node with a prescribed value moves its contribution times g to the load.
-__device__ __forceinline__ PgRowPrefetch pg_row_load_bc(int nc, const double* __restrict__ Ks,
-                                                        const double* __restrict__ bs, const uint8_t* __restrict__ dm,
-                                                        const double* __restrict__ gv, int J, int n, int lane) {
-  PgRowPrefetch p{0.0, -1, 0.0};
-  if (J >= n || lane >= 16) return p;
+// per row, half bandwidth nc + 2), in two parts so that the loads of the
+// next row overlap a whole elimination step: pg_row_fetch_bc issues every
+// load with control flow on indices only (no branch waits for a loaded
+// value), pg_row_resolve_bc combines the values where the row is consumed.
+// A prescribed node's row is u_J = g_J (lane 0); in a free row the lanes
+// take the cells and trial corners as pg_row_load, cells outside the domain
+// give nothing (zero flux), and a prescribed trial node moves its
+// contribution times g to the load.
+struct PgRowRawBc {
+  double v, b, gJ, gI;  // S_e entry, cell load, prescribed values of row and trial node
+  int off;              // column offset of the trial node, -1: no cell
+  int t0;               // this lane adds the cell's load
+  uint8_t dJ, dI;       // row / trial node prescribed
+};
+
+__device__ __forceinline__ PgRowRawBc pg_row_fetch_bc(int nc, const double* __restrict__ Ks,
+                                                      const double* __restrict__ bs, const uint8_t* __restrict__ dm,
+                                                      const double* __restrict__ gv, int J, int n, int lane) {
+  PgRowRawBc q{0.0, 0.0, 0.0, 0.0, -1, 0, 0, 0};
+  if (J >= n || lane >= 16) return q;
   const int NN = nc + 1, bw = nc + 2;
-  if (dm[J]) {
-    if (lane == 0) {
-      p.v = 1.0;
-      p.off = bw;
-      p.b = gv[J];
-    }
-    return p;
-  }
+  q.dJ = dm[J];
+  q.gJ = gv[J];
   const int i = J % NN, j = J / NN;
   const int c = lane >> 2, t = lane & 3;
   const int cx = i - 1 + (c == 1 || c == 2), cy = j - 1 + (c >= 2), r = (c + 2) & 3;
-  if (cx < 0 || cx >= nc || cy < 0 || cy >= nc) return p;
+  if (cx < 0 || cx >= nc || cy < 0 || cy >= nc) return q;
   const int tx = cx + (t == 1 || t == 2), ty = cy + (t >= 2);
   const size_t cell = (size_t)cy * nc + cx;
   const int I = ty * NN + tx;
-  const double v = Ks[cell * 16 + t * 4 + r];
-  if (dm[I]) {
-    p.b = -v * gv[I];
-  } else {
-    p.v = v;
-    p.off = I - J + bw;
+  q.v = Ks[cell * 16 + t * 4 + r];
+  q.dI = dm[I];
+  q.gI = gv[I];
+  q.off = I - J + bw;
+  q.t0 = t == 0;
+  if (t == 0) q.b = bs[cell * 4 + r];
+  return q;
+}
+
+__device__ __forceinline__ PgRowPrefetch pg_row_resolve_bc(const PgRowRawBc& q, int bw, int lane) {
+  PgRowPrefetch p{0.0, -1, 0.0};
+  if (q.dJ) {
+    if (lane == 0) {
+      p.v = 1.0;
+      p.off = bw;
+      p.b = q.gJ;
+    }
+    return p;
   }
-  if (t == 0) p.b += bs[cell * 4 + r];
+  if (q.off < 0) return p;
+  if (q.dI) {
+    p.b = -q.v * q.gI;
+  } else {
+    p.v = q.v;
+    p.off = q.off;
+  }
+  if (q.t0) p.b += q.b;
   return p;
 }
 
-// BC: the system over every node with mixed boundary data (pg_row_load_bc),
+// BC: the system over every node with mixed boundary data (pg_row_fetch_bc),
 // else the interior nodes with zero Dirichlet data.
 template <bool BC>
 __global__ void __launch_bounds__(kCoarsePgWarps * 32)
@@ -437,11 +461,19 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
   // differ by an odd number of doubles and meet different banks
   const int bw = BC ? nc + 2 : nc, W = 2 * bw + 1, PW = W + 1, R = bw + 1;
   const int mi = BC ? nc + 1 : nc - 1, n = mi * mi, NN = nc + 1;
+  // row loads in flight during a step (raw values with mixed boundary
+  // data), and the contributions they give where the row is consumed
   auto row_load = [&](const double* Ks, const double* bs, int J) {
     if constexpr (BC)
-      return pg_row_load_bc(nc, Ks, bs, dm, gv, J, n, lane);
+      return pg_row_fetch_bc(nc, Ks, bs, dm, gv, J, n, lane);
     else
       return pg_row_load(nc, Ks, bs, J, n, lane);
+  };
+  auto resolve = [&](const auto& q) {
+    if constexpr (BC)
+      return pg_row_resolve_bc(q, bw, lane);
+    else
+      return q;
   };
   // lanes whose load term is added: one per cell, or (BC) every lane with
   // a term (prescribed trial nodes move theirs to the load)
@@ -461,15 +493,15 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
     for (int q = lane; q < R; q += 32) yr[q] = 0.0;
     __syncwarp();
     for (int J = 0; J < R && J < n; ++J) {
-      const PgRowPrefetch p = row_load(Ks, bs, J);
+      const PgRowPrefetch p = resolve(row_load(Ks, bs, J));
       if (p.off >= 0) atomicAdd(&Rw[(size_t)(J % R) * PW + p.off], p.v);
       if (adds_b(p)) atomicAdd(&yr[J % R], p.b);
       __syncwarp();
     }
-    PgRowPrefetch next = row_load(Ks, bs, R);
+    auto next = row_load(Ks, bs, R);
     bool bad = false;
     for (int k = 0; k < n; ++k) {
-      const PgRowPrefetch cur = next;
+      const auto cur_raw = next;
       next = row_load(Ks, bs, k + R + 1);  // in flight during this step
       double* P = Rw + (size_t)(k % R) * PW;
       const double piv = P[bw];
@@ -497,6 +529,7 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       if (lane == 0) yr[k % R] = 0.0;
       __syncwarp();
       if (k + R < n) {
+        const PgRowPrefetch cur = resolve(cur_raw);
         if (cur.off >= 0) atomicAdd(&P[cur.off], cur.v);
         if (adds_b(cur)) atomicAdd(&yr[k % R], cur.b);
       }
