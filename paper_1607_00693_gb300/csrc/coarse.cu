@@ -478,10 +478,9 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
   // lanes whose load term is added: one per cell, or (BC) every lane with
   // a term (prescribed trial nodes move theirs to the load)
   auto adds_b = [&](const PgRowPrefetch& p) { return lane < 16 && (BC ? p.b != 0.0 : (lane & 3) == 0); };
-  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 3 * R);
+  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 2 * R);
   double* yr = Rw + (size_t)R * PW;  // right-hand sides of the window rows
   double* xr = yr + R;              // ring of the last bw unknowns
-  double* lm = xr + R;              // multipliers of the current step
   double* Ug = reinterpret_cast<double*>(ws + (size_t)(blockIdx.x * kCoarsePgWarps + wib) * slot_bytes);
   const long long gw = (long long)blockIdx.x * kCoarsePgWarps + wib;
   const long long nw = (long long)gridDim.x * kCoarsePgWarps;
@@ -509,31 +508,15 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       if (!(fabs(piv) > 0.0) || !(fabs(piv) < 1e300)) bad = true;
       const double inv = 1.0 / piv;
       const double yk = yr[k % R];
-      // multipliers of the bw rows below (lane t owns rows k+1+t, k+33+t)
       for (int t = lane; t < bw; t += 32) {
         const int i = k + 1 + t;
-        double l = 0.0;
         if (i < n) {
           double* Ri = Rw + (size_t)(i % R) * PW;
-          l = Ri[bw - 1 - t] * inv;
+          const double l = Ri[bw - 1 - t] * inv;
           Ri[bw - 1 - t] = 0.0;
-          if (l != 0.0) yr[i % R] -= l * yk;
-        }
-        lm[t] = l;
-      }
-      __syncwarp();
-      // rank-1 update: the bw x bw (row t, column jj) pairs spread evenly
-      // over the lanes, consecutive lanes on consecutive columns (with one
-      // row per lane, a band wider than 32 took a second full pass)
-      {
-        int t = lane / bw, c = lane - t * bw;
-        while (t < bw) {
-          const double l = lm[t];
-          if (l != 0.0) Rw[(size_t)((k + 1 + t) % R) * PW + bw + c - t] -= l * P[bw + 1 + c];
-          c += 32;
-          while (c >= bw) {
-            c -= bw;
-            ++t;
+          if (l != 0.0) {
+            for (int jj = 1; jj <= bw; ++jj) Ri[bw - 1 - t + jj] -= l * P[bw + jj];
+            yr[i % R] -= l * yk;
           }
         }
       }
@@ -587,7 +570,7 @@ static size_t coarse_pg_slot_bytes(int nc, bool bc = false) {
 }
 static size_t coarse_pg_smem(int nc, bool bc = false) {
   const int bw = bc ? nc + 2 : nc;
-  return (size_t)kCoarsePgWarps * ((size_t)(bw + 1) * (2 * bw + 2) + 3 * (bw + 1)) * 8;
+  return (size_t)kCoarsePgWarps * ((size_t)(bw + 1) * (2 * bw + 2) + 2 * (bw + 1)) * 8;
 }
 
 // Galerkin solve with mixed boundary data: factor blocks of the (nc+1)^2
