@@ -352,7 +352,9 @@ __global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
 // non-symmetric band of half width bw = nc.  Banded LU without pivoting,
 // one warp per sample: the rows k..k+bw live in a shared-memory ring (row
 // i keeps columns i-bw..i+bw, pitch 2 bw + 2); step k eliminates column k from the bw rows
-// below (lane t owns rows k+1+t, k+33+t), writes the finished U row and its
+// below (lane t owns rows k+1+t, k+33+t; with mixed boundary data the
+// columns of rows past k+32 are shared by all lanes), writes the finished
+// U row and its
 // right-hand side to the sample's scratch, and brings in row k+bw+1, whose
 // 16 contributions (4 cells x 4 trial corners) were loaded one step ahead.
 // Back substitution reads the U rows back with a ring of the last bw
@@ -478,9 +480,10 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
   // lanes whose load term is added: one per cell, or (BC) every lane with
   // a term (prescribed trial nodes move theirs to the load)
   auto adds_b = [&](const PgRowPrefetch& p) { return lane < 16 && (BC ? p.b != 0.0 : (lane & 3) == 0); };
-  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 2 * R);
+  double* Rw = reinterpret_cast<double*>(smem_pg) + (size_t)wib * (R * PW + 3 * R);
   double* yr = Rw + (size_t)R * PW;  // right-hand sides of the window rows
   double* xr = yr + R;              // ring of the last bw unknowns
+  double* lm = xr + R;              // multipliers of the rows beyond 32
   double* Ug = reinterpret_cast<double*>(ws + (size_t)(blockIdx.x * kCoarsePgWarps + wib) * slot_bytes);
   const long long gw = (long long)blockIdx.x * kCoarsePgWarps + wib;
   const long long nw = (long long)gridDim.x * kCoarsePgWarps;
@@ -508,15 +511,33 @@ coarse_pg_kernel(int nc, int S, const double* __restrict__ Kpg, const double* __
       if (!(fabs(piv) > 0.0) || !(fabs(piv) < 1e300)) bad = true;
       const double inv = 1.0 / piv;
       const double yk = yr[k % R];
+      // lane t takes row k+1+t whole (and row k+33+t); with mixed boundary
+      // data the band is nc + 2, just past 32 at nc = 32, so there rows
+      // k+33..k+bw give lane t-32 only their multipliers and all lanes then
+      // share their columns (a second row per lane would double the step's
+      // serial update)
       for (int t = lane; t < bw; t += 32) {
         const int i = k + 1 + t;
+        double l = 0.0;
         if (i < n) {
           double* Ri = Rw + (size_t)(i % R) * PW;
-          const double l = Ri[bw - 1 - t] * inv;
+          l = Ri[bw - 1 - t] * inv;
           Ri[bw - 1 - t] = 0.0;
           if (l != 0.0) {
-            for (int jj = 1; jj <= bw; ++jj) Ri[bw - 1 - t + jj] -= l * P[bw + jj];
+            if (!BC || t < 32)
+              for (int jj = 1; jj <= bw; ++jj) Ri[bw - 1 - t + jj] -= l * P[bw + jj];
             yr[i % R] -= l * yk;
+          }
+        }
+        if (BC && t >= 32) lm[t - 32] = l;
+      }
+      if (BC && bw > 32) {
+        __syncwarp();
+        for (int t = 32; t < bw; ++t) {
+          const double l = lm[t - 32];
+          if (l != 0.0) {
+            double* Ri = Rw + (size_t)((k + 1 + t) % R) * PW;
+            for (int c = lane; c < bw; c += 32) Ri[bw + c - t] -= l * P[bw + 1 + c];
           }
         }
       }
@@ -570,7 +591,7 @@ static size_t coarse_pg_slot_bytes(int nc, bool bc = false) {
 }
 static size_t coarse_pg_smem(int nc, bool bc = false) {
   const int bw = bc ? nc + 2 : nc;
-  return (size_t)kCoarsePgWarps * ((size_t)(bw + 1) * (2 * bw + 2) + 2 * (bw + 1)) * 8;
+  return (size_t)kCoarsePgWarps * ((size_t)(bw + 1) * (2 * bw + 2) + 3 * (bw + 1)) * 8;
 }
 
 // Galerkin solve with mixed boundary data: factor blocks of the (nc+1)^2
