@@ -12,6 +12,11 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
 * ``upscale``       -- per-sample MsFEM: cell problems (Eq. MsFEB) on the
                         fine mesh, oversampling recombination (Remark in
                         Sec. 2.2), K_e and b_e (Eq. stiffness_local); C code.
+                        ``bc=BC_OSCILLATORY`` gives the cell problems the
+                        oscillatory boundary data of Sec. 5.3 (harmonic
+                        coordinate along each patch edge) instead of the
+                        bilinear data; ``cell``, ``cell_pg`` and
+                        ``upscale_pg`` take it too.
 * ``coarse_solve``  -- coarse assembly and solve (Eq. upscaleSUF); C code.
 * ``upscale_pg``, ``coarse_solve_pg`` -- the Petrov-Galerkin form (Eq.
                         stiffness_local_petrov: bilinear test functions,
@@ -78,6 +83,10 @@ def _L():
         lib.orc_fine_fem.argtypes = [i, d, p, p]
         lib.orc_band_solve_dense.argtypes = [i, i, p, p]
         lib.orc_cell_pg.argtypes = [i, i, d, p, i, i, i, p, p]
+        lib.orc_cell_bc.argtypes = [i, i, d, p, i, i, i, i, p, p, p, p]
+        lib.orc_upscale_bc.argtypes = [i, i, d, p, p, i, i, p, p, p, p, i]
+        lib.orc_cell_pg_bc.argtypes = [i, i, d, p, i, i, i, i, p, p]
+        lib.orc_upscale_pg_bc.argtypes = [i, i, d, p, p, i, i, p, p, p, i]
         lib.orc_upscale_pg.argtypes = [i, i, d, p, p, i, p, p, p, i]
         lib.orc_coarse_solve_pg.argtypes = [i, p, p, i, p]
         lib.orc_coarse_solve_bc.argtypes = [i, i, p, p, p, p, i, p]
@@ -137,9 +146,13 @@ def patch_bounds(nf, nc, cx, cy, o):
     return tuple(x.value for x in v)  # x0, x1, y0, y1
 
 
-def cell(nf, nc, f, a2d, cx, cy, o=0):
+BC_BILINEAR = 0      # Eq. MsFEB: bilinear nodal functions on the patch boundary
+BC_OSCILLATORY = 1   # harmonic coordinate along each patch edge (Sec. 5.3)
+
+
+def cell(nf, nc, f, a2d, cx, cy, o=0, bc=BC_BILINEAR):
     """One unit.  Returns (Ke[10], be[4], phi[4][rho+1][rho+1],
-    psi[4][Ny+1][Nx+1])."""
+    psi[4][Ny+1][Nx+1]); ``bc`` selects the cell problems' boundary data."""
     a2d = np.ascontiguousarray(a2d, dtype=np.float64)
     rho = nf // nc
     x0, x1, y0, y1 = patch_bounds(nf, nc, cx, cy, o)
@@ -147,13 +160,13 @@ def cell(nf, nc, f, a2d, cx, cy, o=0):
     be = np.empty(4)
     phi = np.empty((4, rho + 1, rho + 1))
     psi = np.empty((4, y1 - y0 + 1, x1 - x0 + 1))
-    rc = _L().orc_cell(nf, nc, f, _ptr(a2d), cx, cy, o, _ptr(Ke), _ptr(be), _ptr(phi), _ptr(psi))
+    rc = _L().orc_cell_bc(nf, nc, f, _ptr(a2d), cx, cy, o, bc, _ptr(Ke), _ptr(be), _ptr(phi), _ptr(psi))
     if rc != 0:
         raise ValueError("orc_cell failed: %d" % rc)
     return Ke, be, phi, psi
 
 
-def upscale(nf, nc, f, a, oversample=None, want_phi=False, nthreads=0):
+def upscale(nf, nc, f, a, oversample=None, want_phi=False, nthreads=0, bc=BC_BILINEAR):
     """Ke[S][nc*nc][10], be[S][nc*nc][4] (and phi[S][nc*nc][4][(rho+1)^2])."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     S = a.shape[0]
@@ -165,26 +178,26 @@ def upscale(nf, nc, f, a, oversample=None, want_phi=False, nthreads=0):
     ov = None
     if oversample is not None:
         ov = np.ascontiguousarray(oversample, dtype=np.int8)
-    rc = _L().orc_upscale(nf, nc, f, _ptr(a), _ptr(ov), S, _ptr(Ke), _ptr(be), _ptr(phi),
-                          _ptr(st), nthreads)
+    rc = _L().orc_upscale_bc(nf, nc, f, _ptr(a), _ptr(ov), bc, S, _ptr(Ke), _ptr(be), _ptr(phi),
+                             _ptr(st), nthreads)
     if rc != 0:
         raise ValueError("orc_upscale failed: %d (first bad unit %d)" % (rc, int(np.argmax(st != 0))))
     return (Ke, be, phi) if want_phi else (Ke, be)
 
 
-def cell_pg(nf, nc, f, a2d, cx, cy, o=0):
+def cell_pg(nf, nc, f, a2d, cx, cy, o=0, bc=BC_BILINEAR):
     """One unit in the Petrov-Galerkin form: (Kpg[4][4] (row trial l,
     column test l'), bpg[4])."""
     a2d = np.ascontiguousarray(a2d, dtype=np.float64)
     K = np.empty(16)
     b = np.empty(4)
-    rc = _L().orc_cell_pg(nf, nc, f, _ptr(a2d), cx, cy, o, _ptr(K), _ptr(b))
+    rc = _L().orc_cell_pg_bc(nf, nc, f, _ptr(a2d), cx, cy, o, bc, _ptr(K), _ptr(b))
     if rc != 0:
         raise ValueError("orc_cell_pg failed: %d" % rc)
     return K.reshape(4, 4), b
 
 
-def upscale_pg(nf, nc, f, a, oversample=None, nthreads=0):
+def upscale_pg(nf, nc, f, a, oversample=None, nthreads=0, bc=BC_BILINEAR):
     """Kpg[S][nc*nc][16] (row-major 4x4, row trial, column test), bpg[S][nc*nc][4]."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     S = a.shape[0]
@@ -192,7 +205,7 @@ def upscale_pg(nf, nc, f, a, oversample=None, nthreads=0):
     b = np.empty((S, nc * nc, 4))
     st = np.zeros(S * nc * nc, dtype=np.int32)
     ov = None if oversample is None else np.ascontiguousarray(oversample, dtype=np.int8)
-    rc = _L().orc_upscale_pg(nf, nc, f, _ptr(a), _ptr(ov), S, _ptr(K), _ptr(b), _ptr(st), nthreads)
+    rc = _L().orc_upscale_pg_bc(nf, nc, f, _ptr(a), _ptr(ov), bc, S, _ptr(K), _ptr(b), _ptr(st), nthreads)
     if rc != 0:
         raise ValueError("orc_upscale_pg failed: %d" % rc)
     return K, b

@@ -16,7 +16,9 @@
  *   - fine Q1 finite elements (the fine mesh T_h of Sec. 2.2);
  *   - the MsFEM cell problem  -div(a grad phi) = 0 in the patch,
  *                             phi = bilinear nodal function on the patch
- *                             boundary (Eq. MsFEB), solved on T_h;
+ *                             boundary (Eq. MsFEB), solved on T_h, or the
+ *                             oscillatory boundary data (harmonic
+ *                             coordinate along each edge, Sec. 5.3);
  *   - oversampling            (Remark on oversampling, Sec. 2.2): solve on
  *                             the enlarged patch, recombine the patch
  *                             solutions so the basis is nodal at the cell
@@ -228,8 +230,45 @@ void orc_patch_bounds(int nf, int nc, int cx, int cy, int o, int* x0, int* x1,
   *y1 = (cy + 1) * rho + o > nf ? nf : (cy + 1) * rho + o;
 }
 
+/* Oscillatory boundary data of one patch edge: the harmonic coordinate
+ * t_k = sum_{e<k} 1/a_e / sum_e 1/a_e at the edge's nodes k = 0..N, a_e the
+ * coefficient of the patch element next to edge segment e, i.e. the
+ * solution of the reduced problem (a u')' = 0 along the edge with u = 0, 1
+ * at its ends.  a0 points at the first such element, step is the distance
+ * between consecutive ones. */
+static void edge_harmonic(const double* a0, long step, int N, double* t) {
+  double tot = 0.0;
+  for (int e = 0; e < N; ++e) tot += 1.0 / a0[(size_t)e * step];
+  double acc = 0.0;
+  t[0] = 0.0;
+  for (int e = 0; e < N; ++e) {
+    acc += 1.0 / a0[(size_t)e * step];
+    t[e + 1] = acc / tot;
+  }
+  t[N] = 1.0;
+}
+
+/* One unit with boundary data bc: 0 the bilinear nodal functions of the
+ * patch (Eq. MsFEB), 1 the oscillatory boundary condition (the MsFEM option
+ * of the short-correlation example, Sec. 5.3): on every patch edge the
+ * nodal function interpolates its two corner values linearly in the edge's
+ * harmonic coordinate (edge_harmonic) instead of in arc length. */
+static int cell_solve(int nf, int nc, double f, const double* a, int cx, int cy, int o, int bc,
+                      double* Ke, double* be, double* phi, double* psi);
+
 int orc_cell(int nf, int nc, double f, const double* a, int cx, int cy, int o,
              double* Ke, double* be, double* phi, double* psi) {
+  return cell_solve(nf, nc, f, a, cx, cy, o, 0, Ke, be, phi, psi);
+}
+
+int orc_cell_bc(int nf, int nc, double f, const double* a, int cx, int cy, int o, int bc,
+                double* Ke, double* be, double* phi, double* psi) {
+  if (bc != 0 && bc != 1) return -1000;
+  return cell_solve(nf, nc, f, a, cx, cy, o, bc, Ke, be, phi, psi);
+}
+
+static int cell_solve(int nf, int nc, double f, const double* a, int cx, int cy, int o, int bc,
+                      double* Ke, double* be, double* phi, double* psi) {
   if (nf <= 0 || nc <= 0 || nf % nc != 0 || o < 0) return -1000;
   const int rho = nf / nc;
   int x0, x1, y0, y1;
@@ -257,6 +296,35 @@ int orc_cell(int nf, int nc, double f, const double* a, int cx, int cy, int o,
       pv[2 * PN + k] = X * Y;
       pv[3 * PN + k] = (1.0 - X) * Y;
     }
+  if (bc == 1) {
+    /* oscillatory data on the four edges; interior values are unknowns
+     * (the assembly reads pv at boundary nodes only) */
+    double* tb = (double*)malloc(sizeof(double) * (size_t)(2 * (Nx + 1) + 2 * (Ny + 1)));
+    if (!tb) { free(band); free(rhs); free(pv); return -1001; }
+    double* tt = tb + (Nx + 1);
+    double* tl = tt + (Nx + 1);
+    double* tr = tl + (Ny + 1);
+    edge_harmonic(a + (size_t)y0 * nf + x0, 1, Nx, tb);                 /* bottom: row y0 */
+    edge_harmonic(a + (size_t)(y1 - 1) * nf + x0, 1, Nx, tt);           /* top: row y1-1 */
+    edge_harmonic(a + (size_t)y0 * nf + x0, nf, Ny, tl);                /* left: column x0 */
+    edge_harmonic(a + (size_t)y0 * nf + (x1 - 1), nf, Ny, tr);          /* right: column x1-1 */
+    for (int k = 0; k < 4 * PN; ++k) pv[k] = 0.0;
+    for (int i = 0; i <= Nx; ++i) {
+      const int kb = i, kt = Ny * (Nx + 1) + i;
+      pv[0 * PN + kb] = 1.0 - tb[i]; /* SW..SE along the bottom */
+      pv[1 * PN + kb] = tb[i];
+      pv[3 * PN + kt] = 1.0 - tt[i]; /* NW..NE along the top */
+      pv[2 * PN + kt] = tt[i];
+    }
+    for (int j = 0; j <= Ny; ++j) {
+      const int kl = j * (Nx + 1), kr = j * (Nx + 1) + Nx;
+      pv[0 * PN + kl] = 1.0 - tl[j]; /* SW..NW along the left */
+      pv[3 * PN + kl] = tl[j];
+      pv[1 * PN + kr] = 1.0 - tr[j]; /* SE..NE along the right */
+      pv[2 * PN + kr] = tr[j];
+    }
+    free(tb);
+  }
 
   /* Element-by-element assembly of A_II and of -A_IB p_l. */
   for (int ey = 0; ey < Ny; ++ey)
@@ -353,10 +421,19 @@ int orc_cell(int nf, int nc, double f, const double* a, int cx, int cy, int o,
 /* All units of S samples.  oversample: [nc*nc] layer widths or NULL (0).
  * Ke [S][nc*nc][10], be [S][nc*nc][4], phi optional
  * [S][nc*nc][4][(rho+1)^2].  status [S*nc*nc] (0 ok). */
+int orc_upscale_bc(int nf, int nc, double f, const double* a, const int8_t* oversample, int bc,
+                   int S, double* Ke, double* be, double* phi, int32_t* status, int nthreads);
+
 int orc_upscale(int nf, int nc, double f, const double* a, const int8_t* oversample,
                 int S, double* Ke, double* be, double* phi, int32_t* status,
                 int nthreads) {
-  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0) return -1;
+  return orc_upscale_bc(nf, nc, f, a, oversample, 0, S, Ke, be, phi, status, nthreads);
+}
+
+/* orc_upscale with the boundary data bc of cell_solve. */
+int orc_upscale_bc(int nf, int nc, double f, const double* a, const int8_t* oversample, int bc,
+                   int S, double* Ke, double* be, double* phi, int32_t* status, int nthreads) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0 || (bc != 0 && bc != 1)) return -1;
   const int rho = nf / nc;
   const int CN = (rho + 1) * (rho + 1);
   const long units = (long)S * nc * nc;
@@ -370,9 +447,9 @@ int orc_upscale(int nf, int nc, double f, const double* a, const int8_t* oversam
     const int cell = (int)(u % (nc * nc));
     const int cx = cell % nc, cy = cell / nc;
     const int o = oversample ? oversample[cell] : 0;
-    const int rc = orc_cell(nf, nc, f, a + (size_t)s * nf * nf, cx, cy, o,
-                            Ke + (size_t)u * 10, be + (size_t)u * 4,
-                            phi ? phi + (size_t)u * 4 * CN : NULL, NULL);
+    const int rc = cell_solve(nf, nc, f, a + (size_t)s * nf * nf, cx, cy, o, bc,
+                              Ke + (size_t)u * 10, be + (size_t)u * 4,
+                              phi ? phi + (size_t)u * 4 * CN : NULL, NULL);
     if (status) status[u] = rc;
     if (rc != 0) bad = 1;
   }
@@ -490,15 +567,25 @@ int orc_band_solve_dense(int n, int bw, const double* A, double* b) {
 /* bilinear on every fine element of the cell, so its nodal values     */
 /* give the integral exactly: sum_e a_e phi_e^T K_ref q_e.             */
 /* ---------------------------------------------------------------- */
+int orc_cell_pg_bc(int nf, int nc, double f, const double* a, int cx, int cy, int o, int bc,
+                   double* Kpg, double* bpg);
+
 int orc_cell_pg(int nf, int nc, double f, const double* a, int cx, int cy, int o,
                 double* Kpg, double* bpg) {
-  if (nf <= 0 || nc <= 0 || nf % nc != 0 || o < 0) return -1000;
+  return orc_cell_pg_bc(nf, nc, f, a, cx, cy, o, 0, Kpg, bpg);
+}
+
+/* orc_cell_pg with the trial basis from the boundary data bc of
+ * cell_solve (the test functions stay the cell's bilinears). */
+int orc_cell_pg_bc(int nf, int nc, double f, const double* a, int cx, int cy, int o, int bc,
+                   double* Kpg, double* bpg) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || o < 0 || (bc != 0 && bc != 1)) return -1000;
   const int rho = nf / nc;
   const int CN = (rho + 1) * (rho + 1);
   double Ke[10], be[4];
   double* ph = (double*)malloc(sizeof(double) * 4 * CN);
   if (!ph) return -1001;
-  const int rc = orc_cell(nf, nc, f, a, cx, cy, o, Ke, be, ph, NULL);
+  const int rc = cell_solve(nf, nc, f, a, cx, cy, o, bc, Ke, be, ph, NULL);
   if (rc != 0) { free(ph); return rc; }
   double S[4][4] = {{0}};
   for (int ey = 0; ey < rho; ++ey)
@@ -531,9 +618,18 @@ int orc_cell_pg(int nf, int nc, double f, const double* a, int cx, int cy, int o
 
 /* All units of S samples in the Petrov-Galerkin form: Kpg [S][nc*nc][16],
  * bpg [S][nc*nc][4], status [S*nc*nc]. */
+int orc_upscale_pg_bc(int nf, int nc, double f, const double* a, const int8_t* oversample, int bc, int S,
+                      double* Kpg, double* bpg, int32_t* status, int nthreads);
+
 int orc_upscale_pg(int nf, int nc, double f, const double* a, const int8_t* oversample, int S,
                    double* Kpg, double* bpg, int32_t* status, int nthreads) {
-  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0) return -1;
+  return orc_upscale_pg_bc(nf, nc, f, a, oversample, 0, S, Kpg, bpg, status, nthreads);
+}
+
+/* orc_upscale_pg with the boundary data bc of cell_solve. */
+int orc_upscale_pg_bc(int nf, int nc, double f, const double* a, const int8_t* oversample, int bc, int S,
+                      double* Kpg, double* bpg, int32_t* status, int nthreads) {
+  if (nf <= 0 || nc <= 0 || nf % nc != 0 || S < 0 || (bc != 0 && bc != 1)) return -1;
   const long units = (long)S * nc * nc;
   int bad = 0;
 #ifdef _OPENMP
@@ -544,8 +640,8 @@ int orc_upscale_pg(int nf, int nc, double f, const double* a, const int8_t* over
     const int s = (int)(u / (nc * nc));
     const int cell = (int)(u % (nc * nc));
     const int o = oversample ? oversample[cell] : 0;
-    const int rc = orc_cell_pg(nf, nc, f, a + (size_t)s * nf * nf, cell % nc, cell / nc, o,
-                               Kpg + (size_t)u * 16, bpg + (size_t)u * 4);
+    const int rc = orc_cell_pg_bc(nf, nc, f, a + (size_t)s * nf * nf, cell % nc, cell / nc, o, bc,
+                                  Kpg + (size_t)u * 16, bpg + (size_t)u * 4);
     if (status) status[u] = rc;
     if (rc != 0) bad = 1;
   }
