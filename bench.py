@@ -586,6 +586,39 @@ def bench_mixed_bc(api, g, nn, stream, dev, K, b, pg, reps=5):
             "finite": bool(torch.isfinite(u).all().item()), "gpu_launches_per_call": 1}
 
 
+def bench_oscillatory(api, g, bf, ov_t, mo, precision, stream, reps=3):
+    """Upscaling with the oscillatory boundary data of the cell problems (the
+    MsFEM option of Sec. 5.3) on a step's own coefficient batch, timed
+    beside the bilinear data through the same call, and how much it changes
+    K_e."""
+    import torch
+    B = bf["a"].shape[0]
+    ncell = g.nc * g.nc
+    Ko, bo = torch.empty_like(bf["Ke"]), torch.empty_like(bf["be"])
+
+    def timed_ms(bc, K, b):
+        run = lambda: api.stomsfem_upscale_bc(g, False, bc, bf["a"], K, b, oversample=ov_t, max_oversample=mo,
+                                              precision=precision, refine_iters=2, workspace=bf["wsu"],
+                                              stream=stream)
+        with torch.cuda.stream(stream):
+            run()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_b = timed_ms(api.BC_BILINEAR, bf["Ke"], bf["be"])
+    ms_o = timed_ms(api.BC_OSCILLATORY, Ko, bo)
+    rel = float(((Ko - bf["Ke"]).norm(dim=-1) / bf["Ke"].norm(dim=-1)).max())
+    return {"samples": B, "units_per_s": B * ncell / (ms_o / 1e3), "ms_per_call": ms_o,
+            "bilinear_ms_per_call": ms_b, "max_rel_change_of_Ke": rel,
+            "finite": bool(torch.isfinite(Ko).all().item()), "gpu_launches_per_call": 1}
+
+
 def bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for, B, Bc, u64_gal):
     """Petrov-Galerkin form (Eq. stiffness_local_petrov) of the FP32 step on
     the same workload: sample a, upscale with bilinear test functions (16
@@ -830,6 +863,7 @@ def main():
         extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
         extra["two_level_mc"] = bench_two_level(api, dev, stream)
         extra["mixed_bc"] = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)
+        extra["oscillatory_bc"] = dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form], stream))
         # kernels of each form's own timed calls (outside the step's timed region)
         for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3), ("pod_affine", n4)):
             extra[k]["gpu_launches_timed_calls"] = n

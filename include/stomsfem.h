@@ -56,6 +56,8 @@ enum {
 
 enum { STOMSFEM_FP64 = 0, STOMSFEM_FP32_REFINED = 1, STOMSFEM_FP32 = 2 };
 enum { STOMSFEM_FIELD_EXP = 0, STOMSFEM_FIELD_EXP_SIGMOID = 1, STOMSFEM_FIELD_AFFINE = 2 };
+/* Boundary data of the cell problems (stomsfem_upscale_bc). */
+enum { STOMSFEM_BC_BILINEAR = 0, STOMSFEM_BC_OSCILLATORY = 1 };
 
 typedef struct {
   int32_t nf; /* fine elements per side */
@@ -302,6 +304,25 @@ int stomsfem_upscale_pg(const stomsfem_grid* grid, const double* a, const int8_t
                         int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
                         double* Ke, double* be, double* phi, int32_t* unit_status, void* workspace,
                         size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* Local upscaling with a choice of boundary data for the cell problems:
+ * bc = STOMSFEM_BC_BILINEAR is stomsfem_upscale (pg = 0) or
+ * stomsfem_upscale_pg (pg = 1); bc = STOMSFEM_BC_OSCILLATORY gives every
+ * patch edge the oscillatory data of the short-correlation example's MsFEM
+ * (Sec. 5.3): each nodal function interpolates its two corner values
+ * linearly in the edge's harmonic coordinate sum_{e<k} 1/a_e / sum_e 1/a_e
+ * (a_e the patch element next to edge segment e, the reduced problem
+ * (a u')' = 0 along the edge) instead of in arc length.  In a medium that
+ * does not vary along an edge the two coincide there.  Arguments, layouts
+ * (Ke 10 entries per unit, or 16 with pg = 1), workspace (that of
+ * stomsfem_upscale_workspace_size), statuses and errors as those calls; with
+ * oscillatory data every cell takes the back-substitution route in one
+ * launch, also in FP32.  Errors: EINVAL also for pg not 0 or 1 and an
+ * unknown bc. */
+int stomsfem_upscale_bc(const stomsfem_grid* grid, int32_t pg, int32_t bc, const double* a,
+                        const int8_t* oversample, int32_t max_oversample, int32_t S, int32_t precision,
+                        int32_t refine_iters, double* Ke, double* be, double* phi, int32_t* unit_status,
+                        void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
 
 /* Scratch needed by stomsfem_coarse_solve_pg. */
 int stomsfem_coarse_pg_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);

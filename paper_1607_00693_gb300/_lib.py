@@ -77,6 +77,8 @@ _SIG = {
                                                 _P]),
     "stomsfem_upscale_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P,
                                            _SZ, _P]),
+    "stomsfem_upscale_bc": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P,
+                                           _P, _SZ, _P]),
     "stomsfem_coarse_pg_workspace_size": (ctypes.c_int, [ctypes.POINTER(Grid), _I, ctypes.POINTER(_SZ)]),
     "stomsfem_coarse_solve_pg": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _P, _P, _P, _P, _P, _SZ,
                                                 _P]),

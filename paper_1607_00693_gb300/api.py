@@ -397,6 +397,31 @@ def stomsfem_upscale_pg(g: Grid, a, Ke, be, oversample=None, max_oversample=0, p
         _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
 
 
+BC_BILINEAR, BC_OSCILLATORY = 0, 1
+
+
+def stomsfem_upscale_bc(g: Grid, pg, bc, a, Ke, be, oversample=None, max_oversample=0, precision=FP64,
+                        refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None):
+    """Upscaling with the cell problems' boundary data ``bc`` (BC_BILINEAR or
+    BC_OSCILLATORY), Galerkin (Ke [S][ncell][10]) or with ``pg``
+    Petrov-Galerkin (Ke [S][ncell][16])."""
+    S = a.shape[0]
+    ncell = g.nc * g.nc
+    rho = g.nf // g.nc
+    if workspace is None:
+        _, rb = stomsfem_upscale_workspace_size(g, max_oversample if oversample is not None else 0,
+                                                precision)
+        workspace = torch.empty(rb, dtype=torch.uint8, device=a.device)
+    L.check(L.lib().stomsfem_upscale_bc(
+        ctypes.byref(g), int(bool(pg)), int(bc), _dev(a, torch.float64, (S, g.nf, g.nf), "a"),
+        _dev(oversample, torch.int8, (ncell,), "oversample"), int(max_oversample), S, int(precision),
+        int(refine_iters), _dev(Ke, torch.float64, (S, ncell, 16 if pg else 10), "Ke"),
+        _dev(be, torch.float64, (S, ncell, 4), "be"),
+        _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
+        _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
+        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+
+
 def stomsfem_coarse_pg_workspace_size(g: Grid, S):
     b = ctypes.c_size_t()
     L.check(L.lib().stomsfem_coarse_pg_workspace_size(ctypes.byref(g), int(S), ctypes.byref(b)))

@@ -28,6 +28,13 @@ int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* over
                   int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
                   size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32);
 
+// Petrov-Galerkin upscaling with the oscillatory boundary data of the cell
+// problems (the Petrov-Galerkin half of stomsfem_upscale_bc).
+int upscale_pg_oscillatory(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                           int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters, double* Ke,
+                           double* be, double* phi, int32_t* unit_status, void* workspace, size_t workspace_bytes,
+                           stomsfem_stream_t stream);
+
 #define STOMSFEM_TRY_CUDA(expr)                                  \
   do {                                                           \
     int _rc = ::stomsfem::check_cuda((expr), #expr);             \

@@ -225,6 +225,111 @@ struct ResidualGen {
   }
 };
 
+// Oscillatory boundary data (the MsFEM option of the short-correlation
+// example, Sec. 5.3): on every patch edge the nodal functions interpolate
+// their corner values linearly in the edge's harmonic coordinate
+// t_k = sum_{e<k} 1/a_e / sum_e 1/a_e (a_e the patch element next to segment
+// e: the reduced problem (a u')' = 0 along the edge) instead of in arc
+// length.  The unknowns stay psi0_l (zero on the boundary), with the lifting
+// p_l = bilinear + d_l, d_l nonzero on the boundary only: on an edge whose
+// corner values are c0 (k = 0) and c1 (k = N), d_l(k) = (c1 - c0) delta(k),
+// delta(k) = t_k - k / N.  Both d_l at a boundary node and its share
+// -(A d_l) of the right-hand side at the interior nodes next to the
+// boundary are computed from a along the edge when needed (O(N) loads,
+// FP64), so nothing is stored.
+
+// delta at the nodes k-1, k, k+1 of edge E (0 bottom, 1 top, 2 left,
+// 3 right); 0 at the corners and outside the edge.  Not inlined: it runs
+// for the rows next to the boundary only, and one copy keeps the kernels
+// that inline the row generator small.
+static __device__ __noinline__ void osc_delta3(const PatchGen& pg, int E, int k, double d[3]) {
+  const int N = E < 2 ? pg.Nx : pg.Ny;
+  const size_t row0 = (size_t)(pg.y0 + (E == 1 ? pg.Ny - 1 : 0)) * pg.nf;
+  const double* p = pg.a + row0 + pg.x0 + (E == 3 ? pg.Nx - 1 : 0);
+  const size_t step = E < 2 ? 1 : (size_t)pg.nf;
+  double tot = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int e = 0; e < N; ++e) {
+    const double v = 1.0 / __ldg(p + (size_t)e * step);
+    tot += v;
+    if (e < k - 1) s0 += v;
+    if (e < k) s1 += v;
+    if (e < k + 1) s2 += v;
+  }
+  const double it = 1.0 / tot, iN = 1.0 / (double)N;
+  d[0] = (k - 1 > 0 && k - 1 < N) ? s0 * it - (double)(k - 1) * iN : 0.0;
+  d[1] = (k > 0 && k < N) ? s1 * it - (double)k * iN : 0.0;
+  d[2] = (k + 1 > 0 && k + 1 < N) ? s2 * it - (double)(k + 1) * iN : 0.0;
+}
+
+// Adds d_l (l = SW, SE, NE) at patch node (i, j) when it lies on the
+// boundary: bottom d_SW = -delta, d_SE = +delta; top d_NE = +delta; left
+// d_SW = -delta; right d_SE = -delta, d_NE = +delta.
+template <typename T>
+__device__ inline void osc_boundary(const PatchGen& pg, int i, int j, T out[3]) {
+  double d[3];
+  if (j == 0 && i > 0 && i < pg.Nx) {
+    osc_delta3(pg, 0, i, d);
+    out[0] -= (T)d[1];
+    out[1] += (T)d[1];
+  } else if (j == pg.Ny && i > 0 && i < pg.Nx) {
+    osc_delta3(pg, 1, i, d);
+    out[2] += (T)d[1];
+  } else if (i == 0 && j > 0 && j < pg.Ny) {
+    osc_delta3(pg, 2, j, d);
+    out[0] -= (T)d[1];
+  } else if (i == pg.Nx && j > 0 && j < pg.Ny) {
+    osc_delta3(pg, 3, j, d);
+    out[1] -= (T)d[1];
+    out[2] += (T)d[1];
+  }
+}
+
+// Adds -(A d_l) at interior node (i, j) next to the boundary: the stencil
+// couplings to its boundary neighbours (a_SW/3, (a_SW + a_NW)/6, a_NW/3 to
+// the west nodes j-1, j, j+1, and likewise on the other sides) times d_l.
+template <typename T>
+__device__ inline void osc_ring(const PatchGen& pg, int i, int j, double aSW, double aSE, double aNE, double aNW,
+                                T rh[3]) {
+  constexpr double r3 = 1.0 / 3.0, r6 = 1.0 / 6.0;
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0, d[3];
+  if (j == 1) {  // bottom edge nodes i-1, i, i+1
+    osc_delta3(pg, 0, i, d);
+    const double t = aSW * r3 * d[0] + (aSW + aSE) * r6 * d[1] + aSE * r3 * d[2];
+    r0 -= t;
+    r1 += t;
+  }
+  if (j == pg.Ny - 1) {  // top edge
+    osc_delta3(pg, 1, i, d);
+    r2 += aNW * r3 * d[0] + (aNW + aNE) * r6 * d[1] + aNE * r3 * d[2];
+  }
+  if (i == 1) {  // left edge nodes j-1, j, j+1
+    osc_delta3(pg, 2, j, d);
+    r0 -= aSW * r3 * d[0] + (aSW + aNW) * r6 * d[1] + aNW * r3 * d[2];
+  }
+  if (i == pg.mx) {  // right edge
+    osc_delta3(pg, 3, j, d);
+    const double t = aSE * r3 * d[0] + (aSE + aNE) * r6 * d[1] + aNE * r3 * d[2];
+    r1 -= t;
+    r2 += t;
+  }
+  rh[0] += (T)r0;
+  rh[1] += (T)r1;
+  rh[2] += (T)r2;
+}
+
+// Row generator with the oscillatory data: the rows of PatchGen plus the
+// ring term in the right-hand sides (the fourth right-hand side of ones of
+// the forward-only route is unchanged).
+struct PatchGenOsc : PatchGen {
+  template <typename T, int NR = 3>
+  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const {
+    PatchGen::make<T, NR>(r, w, e, rh);
+    int i, j;
+    node(r, i, j);
+    if (i == 1 || j == 1 || i == mx || j == Ny - 1) osc_ring<T>(*this, i, j, w.sw, w.se, w.ne, w.nw, rh);
+  }
+};
+
 // psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction),
 // given its patch coordinates X = i / Nx, Y = j / Ny.
 template <typename T, typename TS>
@@ -359,10 +464,13 @@ __device__ __forceinline__ T group_sum(T v) {
 // patches have the same shape, so its two halves run the same loop bounds
 // in lockstep (an odd last sample is mirrored by the idle half, which
 // writes nothing).
-template <typename TK, typename TA, int RPL, int G, int MODE, bool PG>
+// OSC: the oscillatory boundary data of the cell problems (PatchGenOsc).
+template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false>
 __global__ void __launch_bounds__(upscale_warps(sizeof(TK) == 8, G) * 32,
                                   sizeof(TK) == 4 ? (G == 16 ? 3 : 4) : (G == 16 ? 3 : 2))
 upscale_kernel(UpscaleArgs A) {
+  // the oscillatory data run every cell by back substitution (one launch)
+  static_assert(!OSC || MODE == kModeAll, "oscillatory data: back-substitution route only");
   constexpr int NB = G / 2;
   constexpr int GPW = 32 / G;  // units per warp
   extern __shared__ __align__(16) unsigned char smem[];
@@ -417,8 +525,22 @@ upscale_kernel(UpscaleArgs A) {
       continue;
     }
     const UnitGeom g = unit_geom(A.nf, A.rho, cx, cy, o);
-    PatchGen pg{A.a + (size_t)s * A.nf * A.nf, A.nf, g.x0, g.y0, g.Nx, g.Ny, g.mx};
+    using Gen = typename std::conditional<OSC, PatchGenOsc, PatchGen>::type;
+    Gen pg;
+    pg.a = A.a + (size_t)s * A.nf * A.nf;
+    pg.nf = A.nf;
+    pg.x0 = g.x0;
+    pg.y0 = g.y0;
+    pg.Nx = g.Nx;
+    pg.Ny = g.Ny;
+    pg.mx = g.mx;
     pg.finish();
+    // psi_l at a patch node, with the boundary data's d_l on the boundary
+    auto psi_node = [&](int i, int j, TA X, TA Y, TA out[3], bool with_psi) {
+      psi_at_xy<TA, TS>(g, psi0, i, j, X, Y, out, with_psi);
+      if constexpr (OSC)
+        if (i == 0 || j == 0 || i == g.Nx || j == g.Ny) osc_boundary<TA>(pg, i, j, out);
+    };
     // A patch that is the cell itself (no oversampling) in the FP32 form,
     // without phi output, takes the forward-only route: K_e(l, m) =
     // p_l^T A p_m - y_l . y_m with y = L^-1 R_l the forward solutions (the
@@ -434,7 +556,7 @@ upscale_kernel(UpscaleArgs A) {
     int fail = -1;
     if constexpr (fwd_only) {
       if (g.n > 0)
-        fail = blk_factor<G, TK, 4, RPL, PatchGen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
+        fail = blk_factor<G, TK, 4, RPL, Gen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
     } else if (g.n > 0) {
       fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
       blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
@@ -442,7 +564,16 @@ upscale_kernel(UpscaleArgs A) {
       for (int it = 0; it < A.refine; ++it) {
         __syncwarp();
         const ResidualGen rg{pg, reinterpret_cast<const double*>(psi0)};
-        for (int r = gl; r < g.n; r += G) rg.rhs3(r, corr + (size_t)3 * r);
+        for (int r = gl; r < g.n; r += G) {
+          rg.rhs3(r, corr + (size_t)3 * r);
+          if constexpr (OSC) {
+            int i, j;
+            pg.node(r, i, j);
+            if (i == 1 || j == 1 || i == g.mx || j == g.Ny - 1)
+              osc_ring<double>(pg, i, j, pg.ael(i - 1, j - 1), pg.ael(i, j - 1), pg.ael(i, j), pg.ael(i - 1, j),
+                               corr + (size_t)3 * r);
+          }
+        }
         __syncwarp();
         blk_forward_stored<G, TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
         blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
@@ -458,10 +589,11 @@ upscale_kernel(UpscaleArgs A) {
     TA m[3] = {0, 0, 0};
     const bool patch_is_cell = (g.cx0 == 0 && g.cy0 == 0 && g.Nx == A.rho && g.Ny == A.rho);
     // Petrov-Galerkin: N_jk = a_cell(psi_j, q_k), j, k < 3 (needed only with
-    // oversampling: without it a(phi_l, q_k) = a(phi_l, phi_k), since
-    // phi_k - q_k vanishes on the cell boundary and phi_l is discrete-harmonic)
+    // oversampling or the oscillatory data: otherwise a(phi_l, q_k) =
+    // a(phi_l, phi_k), since phi_k - q_k vanishes on the cell boundary and
+    // phi_l is discrete-harmonic)
     TA N[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const bool pg_sum = PG && !patch_is_cell;
+    const bool pg_sum = PG && (OSC || !patch_is_cell);
     const TA irho = TA(1) / (TA)A.rho;
     TA iNx, iNy;
     if constexpr (sizeof(TA) == 4) {
@@ -485,10 +617,10 @@ upscale_kernel(UpscaleArgs A) {
       const TA Nxf = (TA)g.Nx, Nyf = (TA)g.Ny;
       const TA X0 = quot((TA)i0, Nxf, iNx), X1 = quot((TA)(i0 + 1), Nxf, iNx);
       const TA Y0 = quot((TA)j0, Nyf, iNy), Y1 = quot((TA)(j0 + 1), Nyf, iNy);
-      psi_at_xy<TA, TS>(g, psi0, i0, j0, X0, Y0, c0, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0, X1, Y0, c1, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0 + 1, j0 + 1, X1, Y1, c2, !fwd_only);
-      psi_at_xy<TA, TS>(g, psi0, i0, j0 + 1, X0, Y1, c3, !fwd_only);
+      psi_node(i0, j0, X0, Y0, c0, !fwd_only);
+      psi_node(i0 + 1, j0, X1, Y0, c1, !fwd_only);
+      psi_node(i0 + 1, j0 + 1, X1, Y1, c2, !fwd_only);
+      psi_node(i0, j0 + 1, X0, Y1, c3, !fwd_only);
       const TA ae = (TA)pg.ael(i0, j0);
       TA dd[3][6];
 #pragma unroll
@@ -567,7 +699,7 @@ upscale_kernel(UpscaleArgs A) {
       TA C[4][4];
       for (int k = 0; k < 4; ++k) {
         TA v[3];
-        psi_at<TA, TS>(g, psi0, ci[k], cj[k], v);
+        psi_node(ci[k], cj[k], (TA)ci[k] / (TA)g.Nx, (TA)cj[k] / (TA)g.Ny, v, true);
         C[0][k] = v[0];
         C[1][k] = v[1];
         C[2][k] = v[2];
@@ -598,7 +730,7 @@ upscale_kernel(UpscaleArgs A) {
         // do the psi_j, and a(1, .) = 0), scaled by 1/6; without
         // oversampling S_pg = the Galerkin matrix
         double S4[4][4];
-        if (patch_is_cell) {
+        if (patch_is_cell && !OSC) {
           for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) S4[r][c] = MM[r][c];
         } else {
@@ -654,6 +786,8 @@ upscale_kernel(UpscaleArgs A) {
         const int i = g.cx0 + q % (A.rho + 1), j = g.cy0 + q / (A.rho + 1);
         double v[3];
         psi_at<double, TS>(g, psi0, i, j, v);
+        if constexpr (OSC)
+          if (i == 0 || j == 0 || i == g.Nx || j == g.Ny) osc_boundary<double>(pg, i, j, v);
         const double v4[4] = {v[0], v[1], v[2], 1.0 - v[0] - v[1] - v[2]};
         for (int l = 0; l < 4; ++l) {
           double t = 0.0;
@@ -690,9 +824,9 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
   *bmax = m + 1;
 }
 
-template <typename TK, typename TA, int RPL, int G, int MODE, bool PG>
+template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false>
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  auto kern = upscale_kernel<TK, TA, RPL, G, MODE, PG>;
+  auto kern = upscale_kernel<TK, TA, RPL, G, MODE, PG, OSC>;
   constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
   const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * WPB * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -708,15 +842,15 @@ static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream
   return STOMSFEM_OK;
 }
 
-template <typename TK, typename TA, int G, int MODE = kModeAll, bool PG = false>
+template <typename TK, typename TA, int G, int MODE = kModeAll, bool PG = false, bool OSC = false>
 static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
   const int rpl = (G / 2 + A.bmax + G - 1) / G;  // <= 3 (G = 32) or 5 (G = 16) for bmax <= 64
-  if (rpl <= 1) return launch_upscale<TK, TA, 1, G, MODE, PG>(A, max_blocks, st);
-  if (rpl == 2) return launch_upscale<TK, TA, 2, G, MODE, PG>(A, max_blocks, st);
-  if (rpl == 3) return launch_upscale<TK, TA, 3, G, MODE, PG>(A, max_blocks, st);
+  if (rpl <= 1) return launch_upscale<TK, TA, 1, G, MODE, PG, OSC>(A, max_blocks, st);
+  if (rpl == 2) return launch_upscale<TK, TA, 2, G, MODE, PG, OSC>(A, max_blocks, st);
+  if (rpl == 3) return launch_upscale<TK, TA, 3, G, MODE, PG, OSC>(A, max_blocks, st);
   if constexpr (G == 16) {
-    if (rpl == 4) return launch_upscale<TK, TA, 4, G, MODE, PG>(A, max_blocks, st);
-    return launch_upscale<TK, TA, 5, G, MODE, PG>(A, max_blocks, st);
+    if (rpl == 4) return launch_upscale<TK, TA, 4, G, MODE, PG, OSC>(A, max_blocks, st);
+    return launch_upscale<TK, TA, 5, G, MODE, PG, OSC>(A, max_blocks, st);
   }
   return set_error(STOMSFEM_EINVAL, "bandwidth %d too large", A.bmax);
 }
@@ -729,8 +863,9 @@ static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(i
 constexpr int group_lanes(int) { return 16; }
 
 // The host side of stomsfem_upscale / stomsfem_upscale_pg (PG: Ke holds
-// 16 entries per unit).
-template <bool PG>
+// 16 entries per unit; OSC: the oscillatory boundary data of the cell
+// problems, stomsfem_upscale_bc).
+template <bool PG, bool OSC = false>
 int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                 int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, double* phi,
                 int32_t* unit_status, void* workspace, size_t workspace_bytes, stomsfem_stream_t stream,
@@ -794,35 +929,41 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
   A.cell_count = nullptr;
   A.blocks_per_sm_cap = tune.blocks_per_sm;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == STOMSFEM_FP32 && !phi && tune.split_fp32) {
-    // FP32 without phi output: cells without oversampling take the
-    // forward-only route in a launch of their own, the others follow
-    constexpr int G = group_lanes(STOMSFEM_FP32);
-    if (!oversample) return launch_rpl<float, float, G, kModeFwd, PG>(A, max_blocks, st);
-    const size_t lbytes = cell_list_bytes(grid);
-    const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
-    if (slots2 >= slots_per_block) {
-      const int ncell = grid->nc * grid->nc;
-      unsigned char* base = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
-      int32_t* list0 = reinterpret_cast<int32_t*>(base);
-      int32_t* list1 = list0 + ncell;
-      int32_t* counts = list1 + ncell;
-      upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, list0, list1, counts);
-      STOMSFEM_TRY_CUDA(cudaGetLastError());
-      const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
-      A.cell_list = list0;
-      A.cell_count = counts;
-      rc = launch_rpl<float, float, G, kModeFwd, PG>(A, mb, st);
-      if (rc) return rc;
-      A.cell_list = list1;
-      A.cell_count = counts + 1;
-      return launch_rpl<float, float, G, kModeRest, PG>(A, mb, st);
+  // the oscillatory data: every cell by back substitution in one launch
+  // (the forward-only route never forms psi0, which the Petrov-Galerkin
+  // sums then need, and one launch mode keeps the compile short)
+  if constexpr (!OSC) {
+    if (precision == STOMSFEM_FP32 && !phi && tune.split_fp32) {
+      // FP32 without phi output: cells without oversampling take the
+      // forward-only route in a launch of their own, the others follow
+      constexpr int G = group_lanes(STOMSFEM_FP32);
+      if (!oversample) return launch_rpl<float, float, G, kModeFwd, PG, OSC>(A, max_blocks, st);
+      const size_t lbytes = cell_list_bytes(grid);
+      const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
+      if (slots2 >= slots_per_block) {
+        const int ncell = grid->nc * grid->nc;
+        unsigned char* base = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
+        int32_t* list0 = reinterpret_cast<int32_t*>(base);
+        int32_t* list1 = list0 + ncell;
+        int32_t* counts = list1 + ncell;
+        upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, list0, list1, counts);
+        STOMSFEM_TRY_CUDA(cudaGetLastError());
+        const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
+        A.cell_list = list0;
+        A.cell_count = counts;
+        rc = launch_rpl<float, float, G, kModeFwd, PG, OSC>(A, mb, st);
+        if (rc) return rc;
+        A.cell_list = list1;
+        A.cell_count = counts + 1;
+        return launch_rpl<float, float, G, kModeRest, PG, OSC>(A, mb, st);
+      }
     }
   }
-  if (precision == STOMSFEM_FP64) return launch_rpl<double, double, group_lanes(STOMSFEM_FP64), kModeAll, PG>(A, max_blocks, st);
+  if (precision == STOMSFEM_FP64)
+    return launch_rpl<double, double, group_lanes(STOMSFEM_FP64), kModeAll, PG, OSC>(A, max_blocks, st);
   if (precision == STOMSFEM_FP32_REFINED)
-    return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED), kModeAll, PG>(A, max_blocks, st);
-  return launch_rpl<float, float, group_lanes(STOMSFEM_FP32), kModeAll, PG>(A, max_blocks, st);
+    return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED), kModeAll, PG, OSC>(A, max_blocks, st);
+  return launch_rpl<float, float, group_lanes(STOMSFEM_FP32), kModeAll, PG, OSC>(A, max_blocks, st);
 }
 
 

@@ -88,6 +88,15 @@ def test_host_validation_of_the_further_forms(lib):
                                         None) == L.EINVAL
     assert lib.stomsfem_coarse_solve_pg(ctypes.byref(g), v, v, 2, v, v, None, None, v, 1 << 20,
                                         None) == L.EINVAL   # moments given partly
+    # boundary data of the cell problems: unknown bc or form; bilinear S = 0
+    assert lib.stomsfem_upscale_bc(ctypes.byref(g), 0, 2, None, None, 0, 1, 0, 0, None, None, None, None, None, 0,
+                                   None) == L.EINVAL
+    assert lib.stomsfem_upscale_bc(ctypes.byref(g), 3, 1, None, None, 0, 1, 0, 0, None, None, None, None, None, 0,
+                                   None) == L.EINVAL
+    assert lib.stomsfem_upscale_bc(ctypes.byref(g), 1, 1, None, None, 0, 0, 0, 0, None, None, None, None, None, 0,
+                                   None) == L.OK
+    assert lib.stomsfem_upscale_bc(ctypes.byref(g), 0, 1, None, None, 0, 1, 5, 0, None, None, None, None, None, 0,
+                                   None) == L.EINVAL   # precision
     # mixed boundary data: form, band limit, NULL pointers, partial moments
     sz = ctypes.c_size_t()
     assert lib.stomsfem_coarse_bc_workspace_size(ctypes.byref(g), 2, 4, ctypes.byref(sz)) == L.EINVAL
