@@ -10,7 +10,9 @@ oversampling (patch == cell):
   a_bar the training-mean coefficient; keep the leading modes while
   sqrt(lambda_q / lambda_1) >= tol (the truncation rule of Sec. 5.1).
   One basis V per cell serves all four l (the shared-basis reading used
-  for the high-contrast example, Sec. 5.2).
+  for the high-contrast example, Sec. 5.2); ``build_cell_per_l`` /
+  ``online_cell_per_l`` give each of phi^1..phi^3 its own basis (the
+  patch study, Sec. 5.1) with phi^4 from the partition of unity.
 * online (Alg. 4): phi_rb,l = phi_bar_l + V c_l with the Galerkin system
   (V^T A(omega) V) c_l = -V^T A(omega) phi_bar_l (Eqs. localRB,
   localRBsystem); S_ll' and b_l from phi_rb by Eq. stiffness_local.
@@ -69,20 +71,13 @@ def cell_coef(a, nc, cx, cy):
     return a[..., cy * rho:(cy + 1) * rho, cx * rho:(cx + 1) * rho]
 
 
-def build_cell(phi_snap, a_train_cell, tol=1e-6, max_rank=None, rank=None):
-    """phi_snap [Ns][4][(rho+1)^2] training basis functions of one cell;
-    a_train_cell [Ns][rho][rho].  Returns dict(phibar[4][N2], V[N2][r]
-    (zero on the boundary), lam (all eigenvalues, descending), rank)."""
-    Ns = phi_snap.shape[0]
-    rho = a_train_cell.shape[-1]
-    inner = interior_mask(rho)
-    phibar = phi_snap.mean(axis=0)                       # [4][N2]
-    abar = a_train_cell.mean(axis=0)                     # [rho][rho]
-    Abar = cell_stiffness(abar)[np.ix_(inner, inner)]    # energy inner product on H^1_0
-    X = (phi_snap - phibar[None]).transpose(1, 0, 2).reshape(4 * Ns, -1)[:, inner].T  # n x 4Ns
-    R = np.linalg.cholesky(Abar)                         # Abar = R R^T
+def _kl_basis(X, R, n_nodes, inner, tol, max_rank, rank):
+    """Eq. KLphi for centred snapshots X [n_interior][columns] in the energy
+    inner product Abar = R R^T: eigenpairs of the covariance R^T X X^T R /
+    columns, truncation, and the Abar-orthonormal modes R^{-T} w_q on the
+    cell's nodes (zero on the boundary).  Returns (V, lam, rank)."""
     Y = R.T @ X
-    C = (Y @ Y.T) / (4 * Ns)                             # covariance in the energy metric
+    C = (Y @ Y.T) / X.shape[1]                           # covariance in the energy metric
     lam, Wv = np.linalg.eigh(C)
     order = np.argsort(lam)[::-1]
     lam = lam[order]
@@ -95,9 +90,48 @@ def build_cell(phi_snap, a_train_cell, tol=1e-6, max_rank=None, rank=None):
             rank = min(rank, int(max_rank))
     rank = max(1, min(rank, X.shape[0]))
     Z = np.linalg.solve(R.T, Wv[:, :rank])               # zeta_q = R^{-T} w_q (Abar-orthonormal)
-    V = np.zeros((phi_snap.shape[-1], rank))
+    V = np.zeros((n_nodes, rank))
     V[inner] = Z
+    return V, lam, rank
+
+
+def build_cell(phi_snap, a_train_cell, tol=1e-6, max_rank=None, rank=None):
+    """phi_snap [Ns][4][(rho+1)^2] training basis functions of one cell;
+    a_train_cell [Ns][rho][rho].  Returns dict(phibar[4][N2], V[N2][r]
+    (zero on the boundary), lam (all eigenvalues, descending), rank)."""
+    Ns = phi_snap.shape[0]
+    rho = a_train_cell.shape[-1]
+    inner = interior_mask(rho)
+    phibar = phi_snap.mean(axis=0)                       # [4][N2]
+    abar = a_train_cell.mean(axis=0)                     # [rho][rho]
+    Abar = cell_stiffness(abar)[np.ix_(inner, inner)]    # energy inner product on H^1_0
+    X = (phi_snap - phibar[None]).transpose(1, 0, 2).reshape(4 * Ns, -1)[:, inner].T  # n x 4Ns
+    R = np.linalg.cholesky(Abar)                         # Abar = R R^T
+    V, lam, rank = _kl_basis(X, R, phi_snap.shape[-1], inner, tol, max_rank, rank)
     return {"phibar": phibar, "V": V, "lam": lam, "rank": rank, "abar": abar}
+
+
+def build_cell_per_l(phi_snap, a_train_cell, tol=1e-6, max_rank=None, ranks=None):
+    """One reduced basis per basis function, the reading of the patch study
+    (Sec. 5.1: the KL expansions of phi^1, phi^2, phi^3 separately, 15, 13
+    and 15 modes there); phi^4 follows from the partition of unity.
+    Returns dict(phibar[4][N2], V [three arrays N2 x r_l], lam [three
+    spectra], rank [r_1, r_2, r_3], abar)."""
+    Ns = phi_snap.shape[0]
+    rho = a_train_cell.shape[-1]
+    inner = interior_mask(rho)
+    phibar = phi_snap.mean(axis=0)
+    abar = a_train_cell.mean(axis=0)
+    R = np.linalg.cholesky(cell_stiffness(abar)[np.ix_(inner, inner)])
+    Vs, lams, rks = [], [], []
+    for l in range(3):
+        X = (phi_snap[:, l] - phibar[l][None])[:, inner].T   # n x Ns
+        V, lam, r = _kl_basis(X, R, phi_snap.shape[-1], inner, tol, max_rank,
+                              None if ranks is None else int(ranks[l]))
+        Vs.append(V)
+        lams.append(lam)
+        rks.append(r)
+    return {"phibar": phibar, "V": Vs, "lam": lams, "rank": rks, "abar": abar, "per_l": True}
 
 
 def online_cell(model, a_cell, f, h):
@@ -114,6 +148,44 @@ def online_cell(model, a_cell, f, h):
     b = load_weights(rho, f, h) @ phi_rb
     Ke = np.array([S[l, lp] for l in range(4) for lp in range(l, 4)])
     return Ke, b
+
+
+def online_cell_per_l(model, a_cell, f, h):
+    """Alg. 4 with one basis per basis function: for l = 1..3 the Galerkin
+    system (V_l^T A V_l) c_l = -V_l^T A phi_bar_l, phi_rb,l = phi_bar_l +
+    V_l c_l; phi_rb,4 = 1 - sum_l phi_rb,l; S and b by Eq.
+    stiffness_local.  Returns (Ke[10], be[4])."""
+    A = cell_stiffness(a_cell)
+    phibar = model["phibar"]
+    phi_rb = np.empty((phibar.shape[1], 4))
+    for l in range(3):
+        V = model["V"][l]
+        c = np.linalg.solve(V.T @ A @ V, -(V.T @ A @ phibar[l]))
+        phi_rb[:, l] = phibar[l] + V @ c
+    phi_rb[:, 3] = 1.0 - phi_rb[:, :3].sum(axis=1)
+    S = phi_rb.T @ A @ phi_rb
+    b = load_weights(a_cell.shape[-1], f, h) @ phi_rb
+    Ke = np.array([S[l, lp] for l in range(4) for lp in range(l, 4)])
+    return Ke, b
+
+
+def build_per_l(nf, nc, phi_train, a_train, tol=1e-6, max_rank=None):
+    """Per-cell models with one basis per basis function (build_cell_per_l)."""
+    return [build_cell_per_l(phi_train[:, cell], cell_coef(a_train, nc, cell % nc, cell // nc), tol=tol,
+                             max_rank=max_rank) for cell in range(nc * nc)]
+
+
+def upscale_per_l(models, nf, nc, f, a):
+    """a [S][nf][nf] -> Ke [S][nc*nc][10], be [S][nc*nc][4] with per-l bases."""
+    S = a.shape[0]
+    Ke = np.empty((S, nc * nc, 10))
+    be = np.empty((S, nc * nc, 4))
+    h = 1.0 / nf
+    for s in range(S):
+        for cell in range(nc * nc):
+            Ke[s, cell], be[s, cell] = online_cell_per_l(models[cell], cell_coef(a[s], nc, cell % nc, cell // nc),
+                                                         f, h)
+    return Ke, be
 
 
 def build(nf, nc, phi_train, a_train, tol=1e-6, max_rank=None, ranks=None):
