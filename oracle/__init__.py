@@ -38,6 +38,9 @@ Parts (each follows the paper's definitions, Hou-Li-Zhang, arXiv 1607.00693):
 * ``mlp``           -- FP64 MLP forward/backward/Adam for the surrogate.
 * ``ri``            -- random interpolation of K_e and b_e in the local
                         parameters (Sec. 3.1, Algorithms 1-2).
+* ``local_kl``      -- the local KL expansion of a random field on a patch
+                        (Sec. 2.1.1): restricted covariance, eigenpairs,
+                        local parameters, truncation.
 
 The C part is compiled on first use (gcc, -O2, OpenMP) into
 ``oracle/_build/liborc.so``.
