@@ -205,6 +205,23 @@ def test_invariants(orc, o):
         np.testing.assert_allclose(b.sum(), f / nc ** 2, rtol=1e-12)
 
 
+def test_golden_single_interior_node(orc):
+    """Hand-derived centre values of tests/golden/cell_rho2_centre.txt for
+    both boundary data (one interior node, H = 2h)."""
+    import os
+    from fractions import Fraction
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "cell_rho2_centre.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            rows[k] = v
+    a = np.array([float(x) for x in rows["a"]]).reshape(2, 2)
+    for bc, key in ((orc.BC_BILINEAR, "bilinear"), (orc.BC_OSCILLATORY, "oscillatory")):
+        ref = np.array([float(Fraction(x)) for x in rows[key]])
+        _, _, _, psi = orc.cell(2, 1, 1.0, a, 0, 0, 0, bc=bc)
+        np.testing.assert_allclose(psi[:, 1, 1], ref, rtol=0, atol=1e-15)
+
+
 def test_oscillatory_data_change_a_rough_medium(orc):
     """The option does something: in a rough medium the oscillatory and the
     bilinear data give different K_e (by far more than rounding), while both
