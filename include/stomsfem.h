@@ -10,13 +10,15 @@
  * and load, and then assembles and solves each sample's coarse system.
  * Beside this plain path (FP64, FP32, FP32 + FP64 refinement) it offers
  * the paper's other forms of the local upscaling -- the Petrov-Galerkin
- * form, random interpolation in the local parameters, the reduced basis
- * (also with an affine coefficient) -- a learned surrogate, the pieces of
- * the two-level Monte Carlo estimator, and plans that replay a batch's
- * whole step as one CUDA graph.
+ * form, the oscillatory boundary condition of the cell problems, random
+ * interpolation in the local parameters, the reduced basis (also with an
+ * affine coefficient) -- a learned surrogate, the coarse solve with mixed
+ * boundary data, the pieces of the two-level Monte Carlo estimator, and
+ * plans that replay a batch's whole step as one CUDA graph.
  *
  * Conventions shared by every call
- *  - Unit square, zero Dirichlet data on its boundary, constant load f.
+ *  - Unit square, zero Dirichlet data on its boundary (except
+ *    stomsfem_coarse_solve_bc, which takes its own), constant load f.
  *    Fine grid nf x nf square elements (h = 1/nf); coarse grid nc x nc
  *    cells (H = 1/nc); rho = nf/nc must be an integer.
  *  - Arrays are row-major and y-major: coefficient a[s][ey][ex] (one value
