@@ -164,15 +164,26 @@ def cpu_oracle_step(w, xi, ov, nthreads=0):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(w, ov, samples=2):
+def cpu_baseline(w, ov, samples=2, single_core_samples=2):
+    """The oracle on the host cores, and on one core (a smaller sample of the
+    same workload, timed after the all-core run; the OpenMP thread count is
+    set back afterwards)."""
     import oracle
     oracle.build()
+    cores = oracle.ncores()
     xi = W.draw_xi(w["field"], samples, w["seed"], w["dist"])
-    dt = cpu_oracle_step(w, xi, ov)
+    dt = cpu_oracle_step(w, xi, ov, nthreads=cores)
     units = samples * w["nc"] ** 2
-    return {"value": units / dt, "unit": "units/s", "cores": oracle.ncores(), "kind": "oracle",
-            "sample": "%d samples x %d cells of %s (FP64 oracle: a, cell problems, coarse solve), "
-                      "%.1f s" % (samples, w["nc"] ** 2, w["name"], dt)}
+    out = {"value": units / dt, "unit": "units/s", "cores": cores, "kind": "oracle",
+           "sample": "%d samples x %d cells of %s (FP64 oracle: a, cell problems, coarse solve), "
+                     "%.1f s" % (samples, w["nc"] ** 2, w["name"], dt)}
+    if single_core_samples > 0:
+        xi1 = W.draw_xi(w["field"], single_core_samples, w["seed"], w["dist"], first=samples)
+        dt1 = cpu_oracle_step(w, xi1, ov, nthreads=1)
+        oracle.sample_coef(w["nf"], w["field"], xi1[:1], nthreads=cores)   # thread count back
+        out["single_core"] = {"value": single_core_samples * w["nc"] ** 2 / dt1, "unit": "units/s",
+                              "sample": "%d samples, 1 thread, %.1f s" % (single_core_samples, dt1)}
+    return out
 
 
 def run_reference(args, w, ov):
