@@ -233,54 +233,71 @@ struct ResidualGen {
 // length.  The unknowns stay psi0_l (zero on the boundary), with the lifting
 // p_l = bilinear + d_l, d_l nonzero on the boundary only: on an edge whose
 // corner values are c0 (k = 0) and c1 (k = N), d_l(k) = (c1 - c0) delta(k),
-// delta(k) = t_k - k / N.  Both d_l at a boundary node and its share
-// -(A d_l) of the right-hand side at the interior nodes next to the
-// boundary are computed from a along the edge when needed (O(N) loads,
-// FP64), so nothing is stored.
+// delta(k) = t_k - k / N.  Each unit tabulates delta for its four edges
+// once, in shared memory (osc_fill_tables); d_l at a boundary node and its
+// share -(A d_l) of the right-hand side at the interior nodes next to the
+// boundary read the tables.
 
-// delta at the nodes k-1, k, k+1 of edge E (0 bottom, 1 top, 2 left,
-// 3 right); 0 at the corners and outside the edge.  Not inlined: it runs
-// for the rows next to the boundary only, and one copy keeps the kernels
-// that inline the row generator small.
-static __device__ __noinline__ void osc_delta3(const PatchGen& pg, int E, int k, double d[3]) {
+// Shared-memory bytes of one unit's tables: 4 edges x (bmax + 1) nodes.
+__host__ __device__ inline size_t osc_tab_bytes(int bmax) { return al16(sizeof(double) * 4 * (size_t)(bmax + 1)); }
+
+// Row generator with the oscillatory data: the rows of PatchGen plus the
+// ring term in the right-hand sides.
+struct PatchGenOsc : PatchGen {
+  const double* tab;  // [4][ts] delta of the edges bottom, top, left, right
+  int ts;             // table stride (bmax + 1)
+  template <typename T, int NR = 3>
+  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const;
+};
+
+// delta at node k of edge E (0 bottom, 1 top, 2 left, 3 right); the table
+// holds 0 at both corners.
+__device__ __forceinline__ double osc_delta(const PatchGenOsc& pg, int E, int k) { return pg.tab[E * pg.ts + k]; }
+
+// Lanes 0..3 of a unit's group fill the tables of edges 0..3 (the other
+// lanes wait at the caller's __syncwarp): 1/a_e along the edge, then the
+// running sums; FP64.
+__device__ inline void osc_fill_tables(const PatchGen& pg, double* tab, int ts, int gl) {
+  if (gl >= 4) return;
+  const int E = gl;
   const int N = E < 2 ? pg.Nx : pg.Ny;
   const size_t row0 = (size_t)(pg.y0 + (E == 1 ? pg.Ny - 1 : 0)) * pg.nf;
   const double* p = pg.a + row0 + pg.x0 + (E == 3 ? pg.Nx - 1 : 0);
   const size_t step = E < 2 ? 1 : (size_t)pg.nf;
-  double tot = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  double* t = tab + E * ts;
+  double tot = 0.0;
   for (int e = 0; e < N; ++e) {
     const double v = 1.0 / __ldg(p + (size_t)e * step);
+    t[e + 1] = v;
     tot += v;
-    if (e < k - 1) s0 += v;
-    if (e < k) s1 += v;
-    if (e < k + 1) s2 += v;
   }
   const double it = 1.0 / tot, iN = 1.0 / (double)N;
-  d[0] = (k - 1 > 0 && k - 1 < N) ? s0 * it - (double)(k - 1) * iN : 0.0;
-  d[1] = (k > 0 && k < N) ? s1 * it - (double)k * iN : 0.0;
-  d[2] = (k + 1 > 0 && k + 1 < N) ? s2 * it - (double)(k + 1) * iN : 0.0;
+  double acc = 0.0;
+  t[0] = 0.0;
+  for (int k = 1; k < N; ++k) {
+    acc += t[k];
+    t[k] = acc * it - (double)k * iN;
+  }
+  t[N] = 0.0;
 }
 
 // Adds d_l (l = SW, SE, NE) at patch node (i, j) when it lies on the
 // boundary: bottom d_SW = -delta, d_SE = +delta; top d_NE = +delta; left
 // d_SW = -delta; right d_SE = -delta, d_NE = +delta.
 template <typename T>
-__device__ inline void osc_boundary(const PatchGen& pg, int i, int j, T out[3]) {
-  double d[3];
+__device__ inline void osc_boundary(const PatchGenOsc& pg, int i, int j, T out[3]) {
   if (j == 0 && i > 0 && i < pg.Nx) {
-    osc_delta3(pg, 0, i, d);
-    out[0] -= (T)d[1];
-    out[1] += (T)d[1];
+    const double d = osc_delta(pg, 0, i);
+    out[0] -= (T)d;
+    out[1] += (T)d;
   } else if (j == pg.Ny && i > 0 && i < pg.Nx) {
-    osc_delta3(pg, 1, i, d);
-    out[2] += (T)d[1];
+    out[2] += (T)osc_delta(pg, 1, i);
   } else if (i == 0 && j > 0 && j < pg.Ny) {
-    osc_delta3(pg, 2, j, d);
-    out[0] -= (T)d[1];
+    out[0] -= (T)osc_delta(pg, 2, j);
   } else if (i == pg.Nx && j > 0 && j < pg.Ny) {
-    osc_delta3(pg, 3, j, d);
-    out[1] -= (T)d[1];
-    out[2] += (T)d[1];
+    const double d = osc_delta(pg, 3, j);
+    out[1] -= (T)d;
+    out[2] += (T)d;
   }
 }
 
@@ -288,27 +305,25 @@ __device__ inline void osc_boundary(const PatchGen& pg, int i, int j, T out[3]) 
 // couplings to its boundary neighbours (a_SW/3, (a_SW + a_NW)/6, a_NW/3 to
 // the west nodes j-1, j, j+1, and likewise on the other sides) times d_l.
 template <typename T>
-__device__ inline void osc_ring(const PatchGen& pg, int i, int j, double aSW, double aSE, double aNE, double aNW,
+__device__ inline void osc_ring(const PatchGenOsc& pg, int i, int j, double aSW, double aSE, double aNE, double aNW,
                                 T rh[3]) {
   constexpr double r3 = 1.0 / 3.0, r6 = 1.0 / 6.0;
-  double r0 = 0.0, r1 = 0.0, r2 = 0.0, d[3];
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0;
   if (j == 1) {  // bottom edge nodes i-1, i, i+1
-    osc_delta3(pg, 0, i, d);
-    const double t = aSW * r3 * d[0] + (aSW + aSE) * r6 * d[1] + aSE * r3 * d[2];
+    const double t = aSW * r3 * osc_delta(pg, 0, i - 1) + (aSW + aSE) * r6 * osc_delta(pg, 0, i) +
+                     aSE * r3 * osc_delta(pg, 0, i + 1);
     r0 -= t;
     r1 += t;
   }
-  if (j == pg.Ny - 1) {  // top edge
-    osc_delta3(pg, 1, i, d);
-    r2 += aNW * r3 * d[0] + (aNW + aNE) * r6 * d[1] + aNE * r3 * d[2];
-  }
-  if (i == 1) {  // left edge nodes j-1, j, j+1
-    osc_delta3(pg, 2, j, d);
-    r0 -= aSW * r3 * d[0] + (aSW + aNW) * r6 * d[1] + aNW * r3 * d[2];
-  }
+  if (j == pg.Ny - 1)  // top edge
+    r2 += aNW * r3 * osc_delta(pg, 1, i - 1) + (aNW + aNE) * r6 * osc_delta(pg, 1, i) +
+          aNE * r3 * osc_delta(pg, 1, i + 1);
+  if (i == 1)  // left edge nodes j-1, j, j+1
+    r0 -= aSW * r3 * osc_delta(pg, 2, j - 1) + (aSW + aNW) * r6 * osc_delta(pg, 2, j) +
+          aNW * r3 * osc_delta(pg, 2, j + 1);
   if (i == pg.mx) {  // right edge
-    osc_delta3(pg, 3, j, d);
-    const double t = aSE * r3 * d[0] + (aSE + aNE) * r6 * d[1] + aNE * r3 * d[2];
+    const double t = aSE * r3 * osc_delta(pg, 3, j - 1) + (aSE + aNE) * r6 * osc_delta(pg, 3, j) +
+                     aNE * r3 * osc_delta(pg, 3, j + 1);
     r1 -= t;
     r2 += t;
   }
@@ -317,18 +332,13 @@ __device__ inline void osc_ring(const PatchGen& pg, int i, int j, double aSW, do
   rh[2] += (T)r2;
 }
 
-// Row generator with the oscillatory data: the rows of PatchGen plus the
-// ring term in the right-hand sides (the fourth right-hand side of ones of
-// the forward-only route is unchanged).
-struct PatchGenOsc : PatchGen {
-  template <typename T, int NR = 3>
-  __device__ __forceinline__ void make(int r, const Raw& w, T e[5], T* rh) const {
-    PatchGen::make<T, NR>(r, w, e, rh);
-    int i, j;
-    node(r, i, j);
-    if (i == 1 || j == 1 || i == mx || j == Ny - 1) osc_ring<T>(*this, i, j, w.sw, w.se, w.ne, w.nw, rh);
-  }
-};
+template <typename T, int NR>
+__device__ __forceinline__ void PatchGenOsc::make(int r, const Raw& w, T e[5], T* rh) const {
+  PatchGen::make<T, NR>(r, w, e, rh);
+  int i, j;
+  node(r, i, j);
+  if (i == 1 || j == 1 || i == mx || j == Ny - 1) osc_ring<T>(*this, i, j, w.sw, w.se, w.ne, w.nw, rh);
+}
 
 // psi_l at patch node (i, j) for l = 0..2 (bilinear part + correction),
 // given its patch coordinates X = i / Nx, Y = j / Ny.
@@ -535,6 +545,13 @@ upscale_kernel(UpscaleArgs A) {
     pg.Ny = g.Ny;
     pg.mx = g.mx;
     pg.finish();
+    if constexpr (OSC) {
+      pg.tab = reinterpret_cast<const double*>(smem + (size_t)WPB * GPW * blk_smem_bytes<TK>(NB, A.bmax) +
+                                               (size_t)(wib * GPW + grp) * osc_tab_bytes(A.bmax));
+      pg.ts = A.bmax + 1;
+      osc_fill_tables(pg, const_cast<double*>(pg.tab), pg.ts, gl);
+      __syncwarp();
+    }
     // psi_l at a patch node, with the boundary data's d_l on the boundary
     auto psi_node = [&](int i, int j, TA X, TA Y, TA out[3], bool with_psi) {
       psi_at_xy<TA, TS>(g, psi0, i, j, X, Y, out, with_psi);
@@ -828,7 +845,8 @@ template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC 
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
   auto kern = upscale_kernel<TK, TA, RPL, G, MODE, PG, OSC>;
   constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
-  const size_t smem = blk_smem_bytes<TK>(G / 2, A.bmax) * WPB * (32 / G);
+  // (oscillatory data: each unit's edge tables after all the windows)
+  const size_t smem = (blk_smem_bytes<TK>(G / 2, A.bmax) + (OSC ? osc_tab_bytes(A.bmax) : 0)) * WPB * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
