@@ -66,3 +66,26 @@ def test_library_plan_matches_oracle_sigmoid_field(orc):
     for c, d in enumerate(dims):
         assert list(ids[c, :len(d)]) == [v for (_, _, _, v) in d]
         assert list(nu[c, :len(d)]) == [n for (_, _, n, _) in d]
+
+
+def test_degree_rule_golden(orc):
+    """Hand-worked degrees of tests/golden/ri_degree_rule.txt: the oracle's
+    rule, and the library's plan for one bump centred in the only cell
+    (influence g = scale)."""
+    import os
+    from paper_1607_00693_gb300.build import build_library
+    from paper_1607_00693_gb300 import api
+    _, ri = orc
+    build_library()
+    rows = [line.split() for line in open(os.path.join(os.path.dirname(__file__), "golden", "ri_degree_rule.txt"))
+            if line.strip() and not line.startswith("#")]
+    for g_s, eps_s, nm_s, nu_s in rows:
+        g, eps, nm, nu = float(g_s), float(eps_s), int(nm_s), int(nu_s)
+        assert ri.choose_nu(g, eps, nm) == nu, (g, eps, nm)
+        fld = dict(kind=0, nbx=1, nby=1, width=0.3, scale=g, contrast_log=0.0, gain=1.0)
+        _, ids, nus, _, npts = api.stomsfem_ri_plan(api.grid(8, 1, 1.0), api.field_from_dict(fld), eps, nm)
+        if nu == 0:
+            assert np.all(ids[0] == -1) and npts == 1
+        else:
+            assert ids[0, 0] == 0 and nus[0, 0] == nu and np.all(ids[0, 1:] == -1), (g, eps, nm)
+            assert npts == nu + 1
