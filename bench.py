@@ -244,11 +244,15 @@ def _coarse_err(api, g, Ka, ba, Kb, bb, dev):
 
 
 def shard(rank, ws, total, batch):
-    """This rank's contiguous slice of the sample stream: (first, count).
-    Every rank gets the same count (at least one batch), so per-GPU work is
-    fixed as the GPU count grows (weak scaling); shards never overlap."""
+    """This rank's contiguous slice of the workload's sample stream: (first,
+    count).  Every rank gets the same count (at least one batch), so per-GPU
+    work is fixed as the GPU count grows (weak scaling).  Shards are
+    disjoint while ws x count <= total; beyond that the last ranks take the
+    workload's final slice again (every shard stays inside the workload)."""
     per_rank = max(batch, total // ws)
-    return rank * per_rank, per_rank
+    if per_rank >= total:
+        return 0, per_rank
+    return min(rank * per_rank, total - per_rank), per_rank
 
 
 def max_over_ranks(value, device=None):
@@ -534,6 +538,9 @@ def bench_ri(api, dev, stream, samples=None):
     return res, 3 * 3 + 3  # (tiles, eval, fallback) x 3 timed calls + the FP64 comparison x 3
 
 
+ENGINE_NAMES = {0: "auto", 1: "blocked_fma", 2: "tc_tf32x3", 3: "tc_tf32x2"}
+
+
 def bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, direct_ms):
     """The same step through a plan: launch shapes picked by its autotuner on
     the first batch, then the whole step replayed as one CUDA graph."""
@@ -557,9 +564,10 @@ def bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, direct_m
     info = api.stomsfem_plan_info(h)
     api.stomsfem_plan_destroy(h)
     ms_graph = e0.elapsed_time(e1) / 3
-    return {"samples_per_step": B, "blocks_per_sm": bps, "split_fp32": split, "tune_best_ms": tune_ms,
+    return {"samples_per_step": B, "blocks_per_sm": bps, "split_fp32": split, "engine": ENGINE_NAMES[info[2]],
+            "tune_best_ms": tune_ms,
             "graph_ms_per_step": ms_graph, "graph_units_per_s": B * g.nc * g.nc / (ms_graph / 1e3),
-            "direct_ms_per_step": direct_ms, "graph_ready": info[2], "device_bytes": info[3]}
+            "direct_ms_per_step": direct_ms, "graph_ready": info[3], "device_bytes": info[4]}
 
 
 def bench_mixed_bc(api, g, nn, stream, dev, K, b, pg, reps=5):

@@ -99,6 +99,15 @@ int stomsfem_selftest_wait_timeout(int32_t iters, int32_t* status_host);
  * of n doubles, stream-ordered.  EINVAL for n < 0 or NULL pointers. */
 int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stream_t stream);
 
+/* Measured peak of the non-tensor FMA pipe (no paper counterpart; the
+ * denominator of the upscaling kernels' ALU roofline): every SM runs 8
+ * blocks of 256 threads, each thread 8 independent FMA chains (FP32: 16384
+ * steps, FP64: 512 steps), timed with CUDA events after a warm-up launch,
+ * best of three.  *tflops_host = 2 x FMAs / time in TFLOP/s.  precision
+ * STOMSFEM_FP32 or STOMSFEM_FP64.  Allocates a small device buffer and
+ * synchronises the device.  EINVAL on a bad precision or NULL. */
+int stomsfem_selftest_fma_rate(int32_t precision, float* tflops_host);
+
 /* Coefficient sampling (Sec. 2.1.3, the parametrized coefficient of
  * Eq. MsFEB2).  xi: device [S][nbx*nby] float64; a: device [S][nf][nf]
  * float64, a value per fine element at its centroid ((ex+1/2)h, (ey+1/2)h).
@@ -158,8 +167,9 @@ int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_overs
  *                oversampling recombination is singular.  Failed units
  *                get NaN outputs.
  *   workspace    device scratch of workspace_bytes (>= the slots of one
- *                block: 8 in the FP32 forms, 4 in FP64; more slots = more
- *                units in flight)
+ *                block: 4 in the FP32 forms with 4 <= nf/nc and a half
+ *                bandwidth of at most 40, 8 in the other FP32 cases, 4 in
+ *                FP64; more slots = more units in flight)
  * Errors: EINVAL (sizes, pointers, precision, bandwidth > 64), ENOMEM
  * (workspace below one block of slots), ECUDA. */
 int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
@@ -180,14 +190,22 @@ int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* o
  *    that device) and is held until the process exits.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is cached per device and
+ *    context: after a device reset (cudaDeviceReset, or the primary context
+ *    released and created again) the old address is invalid, and the next
+ *    call, seeing a new context, looks it up again (make that call outside
+ *    a stream capture too).
  *  - Every call uses the same array.  Nothing in it needs to start at zero
  *    (each unit overwrites what it reads), but calls that can overlap on
  *    the GPU (different streams, or different host threads) race on it and
  *    must be serialised by the caller.
- *  - Errors: EINVAL when 4 warp slots of the requested patch size do not fit
- *    in the array (message gives the sizes), plus those of stomsfem_upscale.
- *    Fewer slots than the workspace path may mean lower throughput. */
+ *  - Errors: EINVAL when the slots of one block of the upscaling launch do
+ *    not fit in the array (message gives the sizes): 4 slots in the FP32
+ *    forms when 4 <= nf/nc and the half bandwidth nf/nc + 2 max_oversample
+ *    is at most 40 (the tensor-core factorisation), 8 slots in the other
+ *    FP32 cases, 4 in FP64 (stomsfem_upscale_workspace_size gives the slot
+ *    size); plus those of stomsfem_upscale.  Fewer slots than the workspace
+ *    path may mean lower throughput. */
 int stomsfem_upscale_noalloc(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
                              int32_t max_oversample, int32_t S, int32_t precision,
                              int32_t refine_iters, double* Ke, double* be, double* phi,
@@ -233,17 +251,49 @@ int stomsfem_plan_create(const stomsfem_grid* grid, const stomsfem_field* field,
                          stomsfem_plan** out);
 int stomsfem_plan_destroy(stomsfem_plan* plan);
 
+/* Factorisation engines of the FP32 forms' cell problems (launch choices,
+ * no paper counterpart):
+ *   STOMSFEM_ENGINE_AUTO     the default for the patch size (TC3 when
+ *                            eligible, else BLOCKED);
+ *   STOMSFEM_ENGINE_BLOCKED  banded Cholesky with FP32 FMA updates, two
+ *                            units per warp, any half bandwidth <= 64;
+ *   STOMSFEM_ENGINE_TC3      banded Cholesky whose trailing updates run on
+ *                            the tensor cores (mma TF32) with every operand
+ *                            split exactly into three TF32 parts (six
+ *                            products; rounding no worse than FP32), one
+ *                            unit per warp, needs 4 <= nf/nc and a half
+ *                            bandwidth <= 40;
+ *   STOMSFEM_ENGINE_TC2      the same with two parts (three products, about
+ *                            2^-21 per product: several times the FP32
+ *                            rounding; offered for measurement, never
+ *                            picked by the tuner).
+ * FP64 always uses its own FMA factorisation. */
+enum {
+  STOMSFEM_ENGINE_AUTO = 0,
+  STOMSFEM_ENGINE_BLOCKED = 1,
+  STOMSFEM_ENGINE_TC3 = 2,
+  STOMSFEM_ENGINE_TC2 = 3
+};
+
 /* Autotuner: runs the step on xi (device [S][nbx*nby]; u device
  * [S][(nc+1)^2] receives the solutions, no moments) for every launch
- * choice -- at most 1, 2 or all resident upscaling CTAs per SM, and for
- * the FP32 form with oversampling the separate forward-only launch for the
- * unoversampled cells or one launch -- timing two runs of each with CUDA
- * events after one untimed run, and keeps the fastest (host outputs, any
- * may be NULL: blocks per SM, 0 meaning all that fit; split flag; its time
- * per step in ms).  Synchronises `stream`; drops the captured graph.  The
- * FP32 results depend on the split choice within the FP32 tolerance. */
+ * choice -- at most 1, 2 or all resident upscaling CTAs per SM; for the
+ * FP32 forms with a tensor-core-eligible patch the engines TC3 and
+ * BLOCKED; for the FP32 form with oversampling the separate forward-only
+ * launch for the unoversampled cells or one launch -- timing two runs of
+ * each with CUDA events after one untimed run, and keeps the fastest (host
+ * outputs, any may be NULL: blocks per SM, 0 meaning all that fit; split
+ * flag; its time per step in ms; the engine through stomsfem_plan_info).
+ * Synchronises `stream`; drops the captured graph.  The FP32 results
+ * depend on the split and engine choices within the FP32 tolerance. */
 int stomsfem_plan_tune(stomsfem_plan* plan, const double* xi, double* u, int32_t* blocks_per_sm,
                        int32_t* split_fp32, float* ms_best, stomsfem_stream_t stream);
+
+/* Sets the launch choice without timing: blocks per SM (0 = all that fit),
+ * split flag (0 or 1), engine (STOMSFEM_ENGINE_*).  Drops the captured
+ * graph.  EINVAL for values out of range or a tensor-core engine the
+ * plan's patches are not eligible for. */
+int stomsfem_plan_set_choice(stomsfem_plan* plan, int32_t blocks_per_sm, int32_t split_fp32, int32_t engine);
 
 /* One step: xi (device [S][nbx*nby]) -> u (device [S][(nc+1)^2]) and the
  * running moments (mean, m2, count as stomsfem_coarse_solve, or all NULL).
@@ -254,10 +304,11 @@ int stomsfem_plan_tune(stomsfem_plan* plan, const double* xi, double* u, int32_t
 int stomsfem_plan_step(stomsfem_plan* plan, const double* xi, double* u, double* mean, double* m2,
                        double* count, int32_t use_graph, stomsfem_stream_t stream);
 
-/* The plan's launch choice, whether a graph is instantiated, and the
- * device memory it owns (host outputs, any may be NULL). */
+/* The plan's launch choice (engine: the one AUTO resolves to for this
+ * plan), whether a graph is instantiated, and the device memory it owns
+ * (host outputs, any may be NULL). */
 int stomsfem_plan_info(const stomsfem_plan* plan, int32_t* blocks_per_sm, int32_t* split_fp32,
-                       int32_t* graph_ready, size_t* device_bytes);
+                       int32_t* engine, int32_t* graph_ready, size_t* device_bytes);
 
 /* ---------------------------------------------------------------------
  * Two-level Monte Carlo (Remark in Sec. 4.1.1, Eq. MCmean2level):
@@ -394,6 +445,11 @@ typedef struct stomsfem_pod stomsfem_pod; /* opaque, owned by the library */
 int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
                        int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
                        stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
+/* The same call under the name of the method's offline step ("build the
+ * POD basis"); identical arguments, results and errors. */
+int stomsfem_build_pod(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                       int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
+                       stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
 
 /* Frees the handle (synchronous). */
 int stomsfem_pod_destroy(stomsfem_pod* pod);
@@ -477,6 +533,9 @@ typedef struct {
   double lr, lr_min;  /* cosine decay from lr to lr_min */
   double beta1, beta2, eps;
   uint64_t seed;      /* minibatch selection (splitmix64 of seed, family, step, row) */
+  int32_t fp32_products; /* 0: BF16 products, FP32 accumulation (the training
+                            mode); 1: FP32 products and activations (the
+                            slower check mode, for comparisons with FP64) */
 } stomsfem_surrogate_cfg;
 
 /* Local parameters of every cell (host computation, no GPU): variable i is
@@ -490,8 +549,15 @@ int stomsfem_local_vars(const stomsfem_grid* grid, const stomsfem_field* field, 
                         int32_t* k_per_cell, int32_t* var_ids, int32_t* family,
                         int32_t* n_families);
 
-/* Creates a surrogate with the given initial weights (host [nfam][37264];
- * the caller draws them, e.g. Xavier-uniform; query nfam with
+/* Seeded Xavier-uniform initial weights for n_families networks into the
+ * host buffer w_host [n_families][37264] (flat layout above): each weight
+ * lim (2 u - 1), lim = sqrt(6 / (fan_in + fan_out)), u uniform in [0, 1)
+ * from the top 53 bits of SplitMix64(seed ^ family << 48 ^ parameter
+ * index); biases zero.  Host only; EINVAL for n_families < 1 or NULL. */
+int stomsfem_surrogate_init_weights(int32_t n_families, uint64_t seed, float* w_host);
+
+/* Creates a surrogate with the given initial weights (host [nfam][37264],
+ * e.g. from stomsfem_surrogate_init_weights; query nfam with
  * stomsfem_local_vars).  Allocates device memory (synchronous). */
 int stomsfem_surrogate_create(const stomsfem_grid* grid, const stomsfem_field* field, double tau,
                               const float* init_weights, stomsfem_surrogate** out,
@@ -529,9 +595,11 @@ int stomsfem_surrogate_train(stomsfem_surrogate* sg, const stomsfem_surrogate_cf
  * rows, no update: weights device [37264], X device [64][16], T device
  * [64][16] (targets; columns 13..15 ignored), grad device [37264] receives
  * d loss / d weights for loss = mean over rows and the 13 used outputs of
- * (y - T)^2; loss device [1] or NULL.  Synchronous.  For gradient checks. */
-int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, float* grad,
-                            float* loss, stomsfem_stream_t stream);
+ * (y - T)^2; loss device [1] or NULL.  fp32_products as in
+ * stomsfem_surrogate_cfg.  Stream-ordered, allocates nothing.  For
+ * gradient checks. */
+int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, int32_t fp32_products,
+                            float* grad, float* loss, stomsfem_stream_t stream);
 
 /* Scratch of stomsfem_surrogate_infer for S samples. */
 int stomsfem_surrogate_workspace_size(const stomsfem_surrogate* sg, int32_t S, size_t* bytes);

@@ -41,6 +41,7 @@ _SIG = {
     "stomsfem_last_error": (ctypes.c_char_p, []),
     "stomsfem_selftest_wait_timeout": (ctypes.c_int, [_I, ctypes.POINTER(_I)]),
     "stomsfem_selftest_exp": (ctypes.c_int, [_P, _I, _P, _P]),
+    "stomsfem_selftest_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_float)]),
     "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
     "stomsfem_sample_coef_precision": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I,
                                                       _I, _P, _P]),
@@ -55,6 +56,8 @@ _SIG = {
                                                 _P, _P, _P]),
     "stomsfem_upscale_static_scratch_bytes": (ctypes.c_size_t, []),
     "stomsfem_pod_build": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, ctypes.c_double, _I, _P,
+                                          ctypes.POINTER(_P), _P, _P]),
+    "stomsfem_build_pod": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, ctypes.c_double, _I, _P,
                                           ctypes.POINTER(_P), _P, _P]),
     "stomsfem_pod_destroy": (ctypes.c_int, [_P]),
     "stomsfem_pod_eigenvalues": (ctypes.c_int, [_P, _P]),
@@ -71,7 +74,8 @@ _SIG = {
     "stomsfem_surrogate_save": (ctypes.c_int, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
     "stomsfem_surrogate_load": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_P), _P]),
     "stomsfem_surrogate_train": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
-    "stomsfem_surrogate_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "stomsfem_surrogate_grad": (ctypes.c_int, [_P, _P, _P, _I, _P, _P, _P]),
+    "stomsfem_surrogate_init_weights": (ctypes.c_int, [_I, ctypes.c_uint64, _P]),
     "stomsfem_surrogate_workspace_size": (ctypes.c_int, [_P, _I, ctypes.POINTER(_SZ)]),
     "stomsfem_surrogate_infer": (ctypes.c_int, [_P, _P, _P, _I, ctypes.c_double, _P, _P, _P, _P, _SZ,
                                                 _P]),
@@ -97,7 +101,8 @@ _SIG = {
     "stomsfem_plan_destroy": (ctypes.c_int, [_P]),
     "stomsfem_plan_tune": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "stomsfem_plan_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P]),
-    "stomsfem_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "stomsfem_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "stomsfem_plan_set_choice": (ctypes.c_int, [_P, _I, _I, _I]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
@@ -114,7 +119,7 @@ _SIG = {
 class SurrogateCfg(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("lr", ctypes.c_double), ("lr_min", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("fp32_products", ctypes.c_int32)]
 
 
 def lib(path: str | None = None):

@@ -69,6 +69,13 @@ def stomsfem_selftest_exp(t, out=None, stream=None):
     return out
 
 
+def stomsfem_selftest_fma_rate(precision=FP32):
+    """Measured FMA-pipe peak in TFLOP/s (FP32 or FP64)."""
+    v = ctypes.c_float()
+    L.check(L.lib().stomsfem_selftest_fma_rate(int(precision), ctypes.byref(v)))
+    return v.value
+
+
 def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
     S = xi.shape[0]
     L.check(L.lib().stomsfem_sample_coef(ctypes.byref(g), ctypes.byref(fld),
@@ -149,6 +156,11 @@ def stomsfem_pod_build(g: Grid, phi_snap, a_train, tol=1e-6, max_rank=27, ranks=
     return h, list(rk)
 
 
+def stomsfem_build_pod(g: Grid, phi_snap, a_train, tol=1e-6, max_rank=27, ranks=None, stream=None):
+    """The POD offline step under its method name: as stomsfem_pod_build."""
+    return stomsfem_pod_build(g, phi_snap, a_train, tol, max_rank, ranks, stream)
+
+
 def stomsfem_pod_destroy(h):
     L.check(L.lib().stomsfem_pod_destroy(h))
 
@@ -203,20 +215,11 @@ def stomsfem_local_vars(g: Grid, fld: Field, tau):
 
 def xavier_weights(n_families, seed):
     """Seeded Xavier-uniform initial weights in the flat [out][in] layout
-    (biases zero); the random draw the training starts from."""
+    (biases zero), drawn by the library (stomsfem_surrogate_init_weights)."""
     import numpy as np
-    rng = np.random.default_rng(seed)
-    shapes = [(128, 16), (128,), (128, 128), (128,), (128, 128), (128,), (16, 128), (16,)]
-    out = np.zeros((n_families, SURROGATE_PARAMS), dtype=np.float32)
-    for f in range(n_families):
-        parts = []
-        for s in shapes:
-            if len(s) == 2:
-                lim = (6.0 / (s[0] + s[1])) ** 0.5
-                parts.append(rng.uniform(-lim, lim, size=s).astype(np.float32).reshape(-1))
-            else:
-                parts.append(np.zeros(s, dtype=np.float32))
-        out[f] = np.concatenate(parts)
+    out = np.empty((n_families, SURROGATE_PARAMS), dtype=np.float32)
+    L.check(L.lib().stomsfem_surrogate_init_weights(int(n_families), int(seed) & ((1 << 64) - 1),
+                                                    out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 
@@ -274,12 +277,12 @@ def stomsfem_surrogate_weights(h, n_families):
 
 
 def stomsfem_surrogate_train(h, xi, a, Ke, be, steps, lr=1e-3, lr_min=1e-5, seed=0, beta1=0.9,
-                             beta2=0.999, eps=1e-8, stream=None):
+                             beta2=0.999, eps=1e-8, fp32_products=False, stream=None):
     """Returns the per-step training loss (family mean) as a numpy array."""
     import numpy as np
     S = xi.shape[0]
     cfg = L.SurrogateCfg(int(steps), float(lr), float(lr_min), float(beta1), float(beta2), float(eps),
-                         int(seed))
+                         int(seed), int(bool(fp32_products)))
     loss = np.empty(int(steps), dtype=np.float32)
     L.check(L.lib().stomsfem_surrogate_train(
         h, ctypes.byref(cfg), _dev(xi, torch.float64, None, "xi"), _dev(a, torch.float64, None, "a"),
@@ -288,10 +291,11 @@ def stomsfem_surrogate_train(h, xi, a, Ke, be, steps, lr=1e-3, lr_min=1e-5, seed
     return loss
 
 
-def stomsfem_surrogate_grad(weights, X, T, grad, loss=None, stream=None):
+def stomsfem_surrogate_grad(weights, X, T, grad, loss=None, fp32_products=False, stream=None):
     L.check(L.lib().stomsfem_surrogate_grad(
         _dev(weights, torch.float32, (SURROGATE_PARAMS,), "weights"),
         _dev(X, torch.float32, (64, 16), "X"), _dev(T, torch.float32, (64, 16), "T"),
+        int(bool(fp32_products)),
         _dev(grad, torch.float32, (SURROGATE_PARAMS,), "grad"), _dev(loss, torch.float32, (1,), "loss"),
         _stream(stream)))
 
@@ -545,11 +549,19 @@ def stomsfem_plan_step(h, xi, u, mean=None, m2=None, count=None, use_graph=True,
                                        _stream(stream)))
 
 
+ENGINE_AUTO, ENGINE_BLOCKED, ENGINE_TC3, ENGINE_TC2 = 0, 1, 2, 3
+
+
+def stomsfem_plan_set_choice(h, blocks_per_sm=0, split_fp32=1, engine=ENGINE_AUTO):
+    L.check(L.lib().stomsfem_plan_set_choice(h, int(blocks_per_sm), int(split_fp32), int(engine)))
+
+
 def stomsfem_plan_info(h):
-    """-> (blocks_per_sm, split_fp32, graph_ready, device_bytes)."""
-    b, sp, gr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
-    L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(gr), ctypes.byref(nb)))
-    return b.value, sp.value, gr.value, nb.value
+    """-> (blocks_per_sm, split_fp32, engine, graph_ready, device_bytes)."""
+    b, sp, en, gr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(en), ctypes.byref(gr),
+                                       ctypes.byref(nb)))
+    return b.value, sp.value, en.value, gr.value, nb.value
 
 
 def stomsfem_ri_save(h):

@@ -243,10 +243,9 @@ __device__ __forceinline__ void ld_vec(const T* src, T (&v)[NB], int from) {
 // One column step j = J of the panel factorisation (partial last block),
 // then the next; the recursion keeps every register-array index a
 // compile-time constant.
-template <int J, int G, typename T, int NR, int RPL>
-__device__ __forceinline__ void panel_col(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR], T* lb, int gl, int nb, int np,
+template <int J, int G, typename T, int NR, int RPL, int NB = G / 2>
+__device__ __forceinline__ void panel_col(T (&pr)[RPL][NB], T (&rh)[RPL][NR], T* lb, int gl, int nb, int np,
                                           int K, int& fail) {
-  constexpr int NB = G / 2;
   if constexpr (J < NB) {
     if (J < nb) {
       const T dj = gshfl<G>(pr[0][J], J);
@@ -286,7 +285,7 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR],
         }
       }
     }
-    panel_col<J + 1, G, T, NR, RPL>(pr, rh, lb, gl, nb, np, K, fail);
+    panel_col<J + 1, G, T, NR, RPL, NB>(pr, rh, lb, gl, nb, np, K, fail);
   }
 }
 
@@ -294,10 +293,9 @@ __device__ __forceinline__ void panel_col(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR],
 // diagonal block is factorised from three shuffled entries, both columns of
 // multipliers are formed per row, and one broadcast of the two columns
 // feeds the rank-2 update of the remaining columns.
-template <int J, int G, typename T, int NR, int RPL>
-__device__ __forceinline__ void panel_pair(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR], T* lb, int gl, int K,
+template <int J, int G, typename T, int NR, int RPL, int NB = G / 2>
+__device__ __forceinline__ void panel_pair(T (&pr)[RPL][NB], T (&rh)[RPL][NR], T* lb, int gl, int K,
                                            int& fail) {
-  constexpr int NB = G / 2;
   if constexpr (J + 1 < NB) {
     constexpr int J1 = J + 1;
     const T a00 = gshfl<G>(pr[0][J], J);
@@ -357,7 +355,7 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][G / 2], T (&rh)[RPL][NR]
         for (int q = 0; q < RPL; ++q) pr[q][p] -= l0q[q] * L0[p] + l1q[q] * L1[p];
       }
     }
-    panel_pair<J + 2, G, T, NR, RPL>(pr, rh, lb, gl, K, fail);
+    panel_pair<J + 2, G, T, NR, RPL, NB>(pr, rh, lb, gl, K, fail);
   }
 }
 
@@ -546,9 +544,8 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
 }
 
 // Asynchronous copy of factor block kb into a staging buffer (one commit group).
-template <int G, typename T>
+template <int G, typename T, int NB = G / 2>
 __device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int n, int b, int bmax, T* dst, int gl) {
-  constexpr int NB = G / 2;
   const int K = kb * NB;
   const int nb = min(NB, n - K);
   const int np = min(nb + b, n - K);
@@ -560,22 +557,24 @@ __device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int 
 }
 
 // Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
-template <int G, typename T, int NR, typename TS>
+// Factor blocks of NB columns (NB <= G; G / NB lane groups share the rows
+// below each block).
+template <int G, typename T, int NR, typename TS, int NB = G / 2>
 __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
                              TS* __restrict__ xg, int gl) {
-  constexpr int NB = G / 2;
+  static_assert(G % NB == 0 && NB % 2 == 0, "lane groups of whole blocks");
   const int nbk = (n + NB - 1) / NB;
   const int RW = s.RW;
   const int stg = (NB + bmax) * NB;
   T* xr = s.rhs;  // ring of solution rows
-  blk_stage<G, T>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, gl);
+  blk_stage<G, T, NB>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, gl);
   int kslot = ((nbk - 1) * NB) % RW;  // slot of row K
   for (int kb = nbk - 1; kb >= 0; --kb, kslot = kslot >= NB ? kslot - NB : kslot - NB + RW) {
     const int K = kb * NB;
     const int nb = min(NB, n - K);
     const int np = min(nb + b, n - K);
     if (kb > 0) {
-      blk_stage<G, T>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, gl);
+      blk_stage<G, T, NB>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, gl);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -588,7 +587,7 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 #pragma unroll
     for (int c = 0; c < NR; ++c) yin[c] = gl < nb ? (T)xg[(size_t)(K + gl) * NR + c] : T(0);
     // column p = gl mod NB: yv = y_p - sum over the rows below the block of
-    // L[i][p] x_i, the rows split between the two halves of the group
+    // L[i][p] x_i, the rows split between the G / NB lane groups
     T yv[NR];
     {
       T acc[NR];
@@ -596,7 +595,7 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
       for (int c = 0; c < NR; ++c) acc[c] = T(0);
       const int p = gl & (NB - 1);
 #pragma unroll 4
-      for (int i = nb + gl / NB; i < np; i += 2) {
+      for (int i = nb + gl / NB; i < np; i += G / NB) {
         const T l = tb[i * NB + p];
         T xi[4];
         ld_row4(xr + ring(kslot + i, RW) * 4, xi);
@@ -605,7 +604,8 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
       }
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
-        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], NB, G);
+#pragma unroll
+        for (int o = NB; o < G; o <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
         yv[c] = gl < nb ? yin[c] - acc[c] : T(0);
       }
     }
@@ -667,16 +667,15 @@ __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const 
 
 // Forward substitution with the stored factor: rg [n][NR] double holds the
 // right-hand side on entry and the forward solution y on exit.
-template <int G, typename T, int NR, int RPL>
+template <int G, typename T, int NR, int RPL, int NB = G / 2>
 __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
                                    double* __restrict__ rg, int gl) {
-  constexpr int NB = G / 2;
   const int RW = s.RW;
   const int stg = (NB + bmax) * NB;
   const int nbk = (n + NB - 1) / NB;
   T* rr = s.rhs;  // ring of pending right-hand-side rows
   int filled = 0;
-  blk_stage<G, T>(Lg, 0, n, b, bmax, s.tb, gl);
+  blk_stage<G, T, NB>(Lg, 0, n, b, bmax, s.tb, gl);
   int kslot = 0;
   for (int K = 0, kb = 0; K < n; K += NB, ++kb, kslot = ring(kslot + NB, RW)) {
     const int nb = min(NB, n - K);
@@ -691,7 +690,7 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, 
     }
     filled = max(filled, need);
     if (kb + 1 < nbk) {
-      blk_stage<G, T>(Lg, kb + 1, n, b, bmax, s.tb + ((kb + 1) & 1) * stg, gl);
+      blk_stage<G, T, NB>(Lg, kb + 1, n, b, bmax, s.tb + ((kb + 1) & 1) * stg, gl);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();

@@ -19,14 +19,20 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
                       size_t workspace_bytes, cudaStream_t st);
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
 // Scratch slots (units in flight) of one block of the upscaling launch for a
-// precision: the least workspace stomsfem_upscale accepts, in slots.
-int upscale_slots_per_block(int precision);
+// grid, oversampling limit and precision: the least workspace
+// stomsfem_upscale accepts, in slots (4 with the tensor-core FP32
+// factorisation, 8 with the two-units-per-warp FP32 kernel, 4 in FP64).
+int upscale_slots_per_block(const stomsfem_grid* grid, int32_t max_oversample, int precision);
 // stomsfem_upscale (Galerkin, no phi/status) with the plan's launch
 // choices: at most blocks_per_sm resident CTAs per SM (0: as many as fit),
-// split_fp32 = 0 runs the FP32 form as one launch.
+// split_fp32 = 0 runs the FP32 form as one launch, engine picks the FP32
+// forms' factorisation (STOMSFEM_ENGINE_*).
 int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                   int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
-                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32);
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine);
+// The factorisation engine (STOMSFEM_ENGINE_*) a request resolves to for a
+// grid, oversampling limit and precision.
+int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int precision, int requested);
 
 // Petrov-Galerkin upscaling with the oscillatory boundary data of the cell
 // problems (the Petrov-Galerkin half of stomsfem_upscale_bc).

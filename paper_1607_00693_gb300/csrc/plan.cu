@@ -3,8 +3,9 @@
 // coarse systems and merge the moments) as a reusable object.  A plan owns
 // the step's intermediate device buffers and workspaces, picks its launch
 // shapes by timing them on the caller's batch (blocks per SM of the
-// persistent upscaling launch; for the FP32 form, the separate
-// forward-only launch for unoversampled cells or a single launch), and
+// persistent upscaling launch; for the FP32 forms, the factorisation engine
+// (tensor-core or FMA); for the FP32 form, the separate forward-only launch
+// for unoversampled cells or a single launch), and
 // replays the whole step as one CUDA graph captured on first use.
 #include <vector>
 
@@ -22,7 +23,7 @@ struct stomsfem_plan {
   size_t wsu_bytes = 0;
   void* wsc = nullptr;
   size_t wsc_bytes = 0;
-  int blocks_per_sm = 0, split = 1;
+  int blocks_per_sm = 0, split = 1, engine = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   const void* key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // xi, u, mean, m2, count of the graph
@@ -55,7 +56,7 @@ static int plan_launch(stomsfem_plan* p, const double* xi, double* u, double* me
                                           p->precision == STOMSFEM_FP32 ? STOMSFEM_FP32 : STOMSFEM_FP64, p->a, s);
   if (rc) return rc;
   rc = upscale_tuned(&p->grid, p->a, p->oversample, p->max_o, p->S, p->precision, p->refine, p->Ke, p->be, p->wsu,
-                     p->wsu_bytes, st, p->blocks_per_sm, p->split);
+                     p->wsu_bytes, st, p->blocks_per_sm, p->split, p->engine);
   if (rc) return rc;
   return stomsfem_coarse_solve(&p->grid, p->Ke, p->be, p->S, u, mean, m2, count, p->wsc, p->wsc_bytes, s);
 }
@@ -110,22 +111,30 @@ extern "C" int stomsfem_plan_tune(stomsfem_plan* p, const double* xi, double* u,
   if (!p || !xi || !u) return set_error(STOMSFEM_EINVAL, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   struct Cand {
-    int bps, split;
+    int bps, split, engine;
   };
+  // FP32 forms: the exact tensor-core factorisation and the FMA one (the
+  // two-part split is left out: its rounding exceeds the FP32 form's)
+  std::vector<int> engines = {STOMSFEM_ENGINE_AUTO};
+  if (p->precision != STOMSFEM_FP64 && upscale_engine_of(&p->grid, p->max_o, p->precision, STOMSFEM_ENGINE_AUTO) !=
+                                            STOMSFEM_ENGINE_BLOCKED)
+    engines = {STOMSFEM_ENGINE_TC3, STOMSFEM_ENGINE_BLOCKED};
   std::vector<Cand> cands;
-  for (int bps : {0, 2, 1}) {
-    cands.push_back({bps, 1});
-    if (p->precision == STOMSFEM_FP32 && p->oversample) cands.push_back({bps, 0});
-  }
+  for (int eng : engines)
+    for (int bps : {0, 2, 1}) {
+      cands.push_back({bps, 1, eng});
+      if (p->precision == STOMSFEM_FP32 && p->oversample) cands.push_back({bps, 0, eng});
+    }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   STOMSFEM_TRY_CUDA(cudaEventCreate(&e0));
   int rc = check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
   float best = -1.f;
-  Cand pick{0, 1};
+  Cand pick{0, 1, STOMSFEM_ENGINE_AUTO};
   for (const Cand& c : cands) {
     if (rc) break;
     p->blocks_per_sm = c.bps;
     p->split = c.split;
+    p->engine = c.engine;
     // one untimed run, then two timed
     rc = plan_launch(p, xi, u, nullptr, nullptr, nullptr, st);
     if (rc) break;
@@ -146,6 +155,7 @@ extern "C" int stomsfem_plan_tune(stomsfem_plan* p, const double* xi, double* u,
   if (e1) cudaEventDestroy(e1);
   p->blocks_per_sm = pick.bps;
   p->split = pick.split;
+  p->engine = pick.engine;
   plan_drop_graph(p);
   if (rc) return rc;
   if (blocks_per_sm) *blocks_per_sm = pick.bps;
@@ -190,11 +200,28 @@ extern "C" int stomsfem_plan_step(stomsfem_plan* p, const double* xi, double* u,
   return STOMSFEM_OK;
 }
 
+extern "C" int stomsfem_plan_set_choice(stomsfem_plan* p, int32_t blocks_per_sm, int32_t split_fp32,
+                                        int32_t engine) {
+  if (!p) return set_error(STOMSFEM_EINVAL, "plan is NULL");
+  if (blocks_per_sm < 0 || split_fp32 < 0 || split_fp32 > 1 || engine < STOMSFEM_ENGINE_AUTO ||
+      engine > STOMSFEM_ENGINE_TC2)
+    return set_error(STOMSFEM_EINVAL, "bad launch choice (%d, %d, %d)", blocks_per_sm, split_fp32, engine);
+  if (engine != STOMSFEM_ENGINE_AUTO && engine != STOMSFEM_ENGINE_BLOCKED &&
+      upscale_engine_of(&p->grid, p->max_o, p->precision, STOMSFEM_ENGINE_AUTO) == STOMSFEM_ENGINE_BLOCKED)
+    return set_error(STOMSFEM_EINVAL, "the tensor-core engines need an FP32 form, 4 <= nf/nc and a half bandwidth <= 40");
+  p->blocks_per_sm = blocks_per_sm;
+  p->split = split_fp32;
+  p->engine = engine;
+  plan_drop_graph(p);
+  return STOMSFEM_OK;
+}
+
 extern "C" int stomsfem_plan_info(const stomsfem_plan* p, int32_t* blocks_per_sm, int32_t* split_fp32,
-                                  int32_t* graph_ready, size_t* device_bytes) {
+                                  int32_t* engine, int32_t* graph_ready, size_t* device_bytes) {
   if (!p) return set_error(STOMSFEM_EINVAL, "plan is NULL");
   if (blocks_per_sm) *blocks_per_sm = p->blocks_per_sm;
   if (split_fp32) *split_fp32 = p->split;
+  if (engine) *engine = upscale_engine_of(&p->grid, p->max_o, p->precision, p->engine);
   if (graph_ready) *graph_ready = p->exec ? 1 : 0;
   if (device_bytes) {
     const size_t ncell = (size_t)p->grid.nc * p->grid.nc;

@@ -1193,3 +1193,9 @@ extern "C" int stomsfem_pod_upscale_affine(stomsfem_pod* pod, const double* xi, 
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }
+
+extern "C" int stomsfem_build_pod(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                                  int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
+                                  stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream) {
+  return stomsfem_pod_build(grid, phi_snap, a_train, S_train, tol, max_rank, ranks_in, out, ranks_out, stream);
+}

@@ -24,9 +24,60 @@ __global__ void exp_selftest_kernel(const double* __restrict__ t, int n, double*
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = fexp(t[i], tab);
 }
 
+// Peak FMA rate probe: every thread runs 8 independent FMA chains (no
+// memory traffic but one store per thread at the end).
+template <typename T>
+__global__ void __launch_bounds__(256) fma_rate_kernel(T* out, T s, int iters) {
+  T a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = (T)(threadIdx.x * 1e-3 + i);
+  const T c = (T)1e-7;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], s, c);
+  }
+  T t = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += a[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+template <typename T>
+static int fma_rate(int iters, float* tflops) {
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  const int blocks = sms * 8, threads = 256;
+  T* d = nullptr;
+  STOMSFEM_TRY_CUDA(cudaMalloc(&d, sizeof(T) * (size_t)blocks * threads));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = check_cuda(cudaEventCreate(&e0), "event");
+  if (!rc) rc = check_cuda(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  for (int r = 0; r < 4 && !rc; ++r) {  // the first run warms up (clocks, module)
+    cudaEventRecord(e0);
+    fma_rate_kernel<T><<<blocks, threads>>>(d, (T)0.999, iters);
+    cudaEventRecord(e1);
+    rc = check_cuda(cudaEventSynchronize(e1), "fma probe");
+    float ms = 0.f;
+    if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    if (!rc && r > 0 && ms < best) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  if (rc) return rc;
+  *tflops = (float)(2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12);
+  return STOMSFEM_OK;
+}
+
 }  // namespace stomsfem
 
 using namespace stomsfem;
+
+extern "C" int stomsfem_selftest_fma_rate(int32_t precision, float* tflops_host) {
+  if (!tflops_host || (precision != STOMSFEM_FP64 && precision != STOMSFEM_FP32))
+    return set_error(STOMSFEM_EINVAL, "precision must be STOMSFEM_FP64 or STOMSFEM_FP32, tflops non-NULL");
+  return precision == STOMSFEM_FP32 ? fma_rate<float>(16384, tflops_host) : fma_rate<double>(512, tflops_host);
+}
 
 extern "C" int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stream_t stream) {
   if (n < 0) return set_error(STOMSFEM_EINVAL, "n < 0");

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -88,7 +89,7 @@ struct ColMajor {  // element (i, k) = p[k * ld + i]
   __device__ __forceinline__ float operator()(int i, int k) const { return __bfloat162float(p[k * ld + i]); }
 };
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
@@ -97,7 +98,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 // ---------------------------------------------------------------- training
 
-struct TrainSmem {
+// Shared memory of one family's training CTA.  BF16 products: BF16
+// copies of the weights and every activation.  FP32 products: FP32
+// activations, the weights read from the FP32 master copy in global memory,
+// and GELU(Z) recomputed from Z where it is an operand (the stored H of the
+// BF16 mode would not fit next to FP32 Z and dZ).
+template <bool F32>
+struct TrainSmemT;
+template <>
+struct TrainSmemT<false> {
   __nv_bfloat16 W1[kHid * kIn], W2[kHid * kHid], W3[kHid * kHid], W4[kOut * kHid];  // [out][in]
   __nv_bfloat16 X[kBatch * kIn];
   __nv_bfloat16 Z1[kBatch * kHid], Z2[kBatch * kHid], Z3[kBatch * kHid];  // pre-activations
@@ -105,14 +114,26 @@ struct TrainSmem {
   __nv_bfloat16 D1[kBatch * kHid], D2[kBatch * kHid];                     // dZ ping-pong
   __nv_bfloat16 DY[kBatch * kOut];
   float T[kBatch * kOut];
-  float gb[kHid];  // bias gradient of the layer being processed
+  float gb[2][kHid];  // bias gradients: the layer being applied and the next
+  float loss;
+  int rows[kBatch];
+};
+template <>
+struct TrainSmemT<true> {
+  float X[kBatch * kIn];
+  float Z1[kBatch * kHid], Z2[kBatch * kHid], Z3[kBatch * kHid];
+  float D1[kBatch * kHid], D2[kBatch * kHid];
+  float DY[kBatch * kOut];
+  float T[kBatch * kOut];
+  float gb[2][kHid];
   float loss;
   int rows[kBatch];
 };
 
 struct TrainArgs {
   int nfam;
-  const int* fam_row0;   // [nfam + 1] row ranges of each family in X/Y
+  const int* fam_row0;   // [nfam + 1] row ranges of each family in X/Y, or NULL: rows [row_lo, row_hi)
+  int row_lo, row_hi;
   const float* X;        // [N][kIn]
   const float* Y;        // [N][kOut]
   float* W;              // [nfam][kParams] FP32 master weights
@@ -135,24 +156,108 @@ __device__ __forceinline__ float adam(float& w, float& m, float& v, float g, flo
   return w;
 }
 
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename E>
+__device__ __forceinline__ E from_f(float v) {
+  if constexpr (std::is_same<E, float>::value)
+    return v;
+  else
+    return __float2bfloat16_rn(v);
+}
+template <typename E>
+struct RowM {  // element (i, k) = p[i * ld + k]
+  const E* p;
+  int ld;
+  __device__ __forceinline__ float operator()(int i, int k) const { return to_f(p[i * ld + k]); }
+};
+template <typename E>
+struct ColM {  // element (i, k) = p[k * ld + i]
+  const E* p;
+  int ld;
+  __device__ __forceinline__ float operator()(int i, int k) const { return to_f(p[k * ld + i]); }
+};
+struct GeluRowM {  // element (i, k) = GELU(z[i * ld + k])
+  const float* z;
+  int ld;
+  __device__ __forceinline__ float operator()(int i, int k) const { return gelu(z[i * ld + k]); }
+};
+
+// The same 16 x 8 tile as mma_tile (same lane layout) with FP32 products
+// and FP32 sums in k order.
+template <class FA, class FB>
+__device__ __forceinline__ void fma_tile(const FA& A, const FB& B, int m0, int n0, int K, float c[4], int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = m0 + g, r1 = m0 + g + 8, c0 = n0 + 2 * t, c1 = n0 + 2 * t + 1;
+  for (int k = 0; k < K; ++k) {
+    const float a0 = A(r0, k), a1 = A(r1, k), b0 = B(k, c0), b1 = B(k, c1);
+    c[0] = fmaf(a0, b0, c[0]);
+    c[1] = fmaf(a0, b1, c[1]);
+    c[2] = fmaf(a1, b0, c[2]);
+    c[3] = fmaf(a1, b1, c[3]);
+  }
+}
+template <bool F32, class FA, class FB>
+__device__ __forceinline__ void tile_op(const FA& A, const FB& B, int m0, int n0, int K, float c[4], int lane) {
+  if constexpr (F32)
+    fma_tile(A, B, m0, n0, K, c, lane);
+  else
+    mma_tile(A, B, m0, n0, K, c, lane);
+}
+
+// One CTA (8 warps) per family: minibatch of 64 rows, forward, backward and
+// Adam (bias corrected, cosine learning-rate decay over the call's steps),
+// every step.  F32: FP32 products and activations (the check mode of the
+// gradients); otherwise BF16 products with FP32 accumulation.
+template <bool F32>
 __global__ void __launch_bounds__(256) surrogate_train_kernel(TrainArgs A) {
+  using E = typename std::conditional<F32, float, __nv_bfloat16>::type;
+  using HAcc = typename std::conditional<F32, GeluRowM, RowM<__nv_bfloat16>>::type;
   extern __shared__ __align__(16) unsigned char tsm_raw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(tsm_raw);
+  TrainSmemT<F32>& S = *reinterpret_cast<TrainSmemT<F32>*>(tsm_raw);
   const int fam = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   float* Wm = A.W + (size_t)fam * kParams;
   float* Mm = A.m + (size_t)fam * kParams;
   float* Vm = A.v + (size_t)fam * kParams;
-  const int r0 = A.fam_row0[fam], r1 = A.fam_row0[fam + 1];
+  const int r0 = A.fam_row0 ? A.fam_row0[fam] : A.row_lo, r1 = A.fam_row0 ? A.fam_row0[fam + 1] : A.row_hi;
   const int nrows = r1 - r0;
   if (nrows <= 0) return;
-  for (int i = tid; i < kHid * kIn; i += 256) S.W1[i] = __float2bfloat16_rn(Wm[oW1 + i]);
-  for (int i = tid; i < kHid * kHid; i += 256) {
-    S.W2[i] = __float2bfloat16_rn(Wm[oW2 + i]);
-    S.W3[i] = __float2bfloat16_rn(Wm[oW3 + i]);
+  // weight operands: the BF16 copies, or the FP32 master weights
+  const E *pW1, *pW2, *pW3, *pW4;
+  HAcc H1, H2, H3;
+  if constexpr (F32) {
+    pW1 = Wm + oW1;
+    pW2 = Wm + oW2;
+    pW3 = Wm + oW3;
+    pW4 = Wm + oW4;
+    H1 = GeluRowM{S.Z1, kHid};
+    H2 = GeluRowM{S.Z2, kHid};
+    H3 = GeluRowM{S.Z3, kHid};
+  } else {
+    for (int i = tid; i < kHid * kIn; i += 256) S.W1[i] = __float2bfloat16_rn(Wm[oW1 + i]);
+    for (int i = tid; i < kHid * kHid; i += 256) {
+      S.W2[i] = __float2bfloat16_rn(Wm[oW2 + i]);
+      S.W3[i] = __float2bfloat16_rn(Wm[oW3 + i]);
+    }
+    for (int i = tid; i < kOut * kHid; i += 256) S.W4[i] = __float2bfloat16_rn(Wm[oW4 + i]);
+    pW1 = S.W1;
+    pW2 = S.W2;
+    pW3 = S.W3;
+    pW4 = S.W4;
+    H1 = RowM<__nv_bfloat16>{S.H1, kHid};
+    H2 = RowM<__nv_bfloat16>{S.H2, kHid};
+    H3 = RowM<__nv_bfloat16>{S.H3, kHid};
   }
-  for (int i = tid; i < kOut * kHid; i += 256) S.W4[i] = __float2bfloat16_rn(Wm[oW4 + i]);
+  // refresh of a BF16 weight copy after its update (the FP32 mode reads the
+  // master weights directly)
+  auto refresh = [&](__nv_bfloat16* dst, int off, int n) {
+    if constexpr (!F32) {
+      if (!A.grad_only)
+        for (int i = tid; i < n; i += 256) dst[i] = __float2bfloat16_rn(Wm[off + i]);
+    }
+  };
   const int steps = A.grad_only ? 1 : A.steps;
   for (int step = 0; step < steps; ++step) {
     const int gstep = A.step0 + step;
@@ -170,46 +275,51 @@ __global__ void __launch_bounds__(256) surrogate_train_kernel(TrainArgs A) {
     }
     if (tid == 0) S.loss = 0.f;
     __syncthreads();
-    for (int i = tid; i < kBatch * kIn; i += 256) S.X[i] = __float2bfloat16_rn(A.X[(size_t)S.rows[i / kIn] * kIn + i % kIn]);
+    for (int i = tid; i < kBatch * kIn; i += 256) S.X[i] = from_f<E>(A.X[(size_t)S.rows[i / kIn] * kIn + i % kIn]);
     for (int i = tid; i < kBatch * kOut; i += 256) S.T[i] = A.Y[(size_t)S.rows[i / kOut] * kOut + i % kOut];
     __syncthreads();
     // ---- forward: hidden layers [64 x 128]; warp w owns columns [16w, 16w+16)
-#define FWD_LAYER(AIN, KIN, WS, BOFF, ZOUT, HOUT)                                              \
-  {                                                                                            \
-    for (int mt = 0; mt < kBatch / 16; ++mt)                                                   \
-      for (int nt = 0; nt < 2; ++nt) {                                                         \
-        const int m0 = mt * 16, n0 = warp * 16 + nt * 8;                                       \
-        float c[4] = {0, 0, 0, 0};                                                             \
-        mma_tile(RowMajor{AIN, KIN}, ColMajor{WS, KIN}, m0, n0, KIN, c, lane);                \
-        for (int q = 0; q < 4; ++q) {                                                          \
-          const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);                \
-          const float z = c[q] + Wm[BOFF + col];                                               \
-          ZOUT[row * kHid + col] = __float2bfloat16_rn(z);                                     \
-          HOUT[row * kHid + col] = __float2bfloat16_rn(gelu(z));                               \
-        }                                                                                      \
-      }                                                                                        \
-    __syncthreads();                                                                           \
-  }
-    FWD_LAYER(S.X, kIn, S.W1, oB1, S.Z1, S.H1)
-    FWD_LAYER(S.H1, kHid, S.W2, oB2, S.Z2, S.H2)
-    FWD_LAYER(S.H2, kHid, S.W3, oB3, S.Z3, S.H3)
-#undef FWD_LAYER
+    auto fwd_layer = [&](const auto& Ain, int KIN, const E* WS, int BOFF, E* ZOUT, __nv_bfloat16* HOUT) {
+      for (int mt = 0; mt < kBatch / 16; ++mt)
+        for (int nt = 0; nt < 2; ++nt) {
+          const int m0 = mt * 16, n0 = warp * 16 + nt * 8;
+          float c[4] = {0, 0, 0, 0};
+          tile_op<F32>(Ain, ColM<E>{WS, KIN}, m0, n0, KIN, c, lane);
+          for (int q = 0; q < 4; ++q) {
+            const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);
+            const float z = c[q] + Wm[BOFF + col];
+            ZOUT[row * kHid + col] = from_f<E>(z);
+            if constexpr (!F32) HOUT[row * kHid + col] = __float2bfloat16_rn(gelu(z));
+          }
+        }
+      __syncthreads();
+    };
+    __nv_bfloat16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+    if constexpr (!F32) {
+      h1 = S.H1;
+      h2 = S.H2;
+      h3 = S.H3;
+    }
+    fwd_layer(RowM<E>{S.X, kIn}, kIn, pW1, oB1, S.Z1, h1);
+    fwd_layer(H1, kHid, pW2, oB2, S.Z2, h2);
+    fwd_layer(H2, kHid, pW3, oB3, S.Z3, h3);
     // ---- output layer [64 x 16]: 8 tiles, one per warp; dY = 2 (Y - T) / (B * 13)
     {
       const int m0 = (warp >> 1) * 16, n0 = (warp & 1) * 8;
       float c[4] = {0, 0, 0, 0};
-      mma_tile(RowMajor{S.H3, kHid}, ColMajor{S.W4, kHid}, m0, n0, kHid, c, lane);
+      tile_op<F32>(H3, ColM<E>{pW4, kHid}, m0, n0, kHid, c, lane);
       float ls = 0.f;
       for (int q = 0; q < 4; ++q) {
         const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);
         const float y = c[q] + Wm[oB4 + col];
         const float d = (col < kOutUsed) ? (y - S.T[row * kOut + col]) : 0.f;
         ls += d * d;
-        S.DY[row * kOut + col] = __float2bfloat16_rn(2.f * d / (kBatch * kOutUsed));
+        S.DY[row * kOut + col] = from_f<E>(2.f * d / (kBatch * kOutUsed));
       }
       ls = warp_sum(ls);
       if (lane == 0) atomicAdd(&S.loss, ls / (kBatch * kOutUsed));
     }
+    if (tid < kHid) S.gb[0][tid] = 0.f;
     __syncthreads();
     if (tid == 0 && A.loss_out) A.loss_out[(size_t)fam * A.steps + step] = S.loss;
     const float lr = A.lr_min + 0.5f * (A.lr - A.lr_min) * (1.f + cosf(3.14159265358979f * gstep / fmaxf(1.f, (float)(A.step0 + A.steps))));
@@ -222,102 +332,81 @@ __global__ void __launch_bounds__(256) surrogate_train_kernel(TrainArgs A) {
         adam(Wm[off], Mm[off], Vm[off], gr, lr, A.beta1, A.beta2, A.eps, c1, c2);
       }
     };
-    // ---- layer 4: dW4 [16 x 128] = dY^T H3 ; db4 ; dZ3 = (dY W4) * gelu'(Z3)
+    // dZ_in = (dZ W) * gelu'(Z_in) with the layer's weights before their
+    // update, and the column sums of dZ_in (the next bias gradient) into gb
+    auto back_in = [&](const auto& DZa, int KD, const auto& Wa, const E* ZIN, E* DZOUT, float* gb) {
+      for (int mt = 0; mt < kBatch / 16; ++mt)
+        for (int nt = 0; nt < 2; ++nt) {
+          const int m0 = mt * 16, n0 = warp * 16 + nt * 8;
+          float c[4] = {0, 0, 0, 0};
+          tile_op<F32>(DZa, Wa, m0, n0, KD, c, lane);
+          float cs0 = 0.f, cs1 = 0.f;
+          for (int q = 0; q < 4; ++q) {
+            const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);
+            const float dz = c[q] * gelu_grad(to_f(ZIN[row * kHid + col]));
+            DZOUT[row * kHid + col] = from_f<E>(dz);
+            if (q & 1) cs1 += dz; else cs0 += dz;
+          }
+          // column sums over the 16 rows of this tile: reduce over g (lanes with equal t4)
+          for (int o = 4; o < 32; o <<= 1) {
+            cs0 += __shfl_xor_sync(0xffffffffu, cs0, o);
+            cs1 += __shfl_xor_sync(0xffffffffu, cs1, o);
+          }
+          if (g == 0) {
+            atomicAdd(&gb[n0 + 2 * t4], cs0);
+            atomicAdd(&gb[n0 + 2 * t4 + 1], cs1);
+          }
+        }
+      __syncthreads();
+    };
+    // ---- layer 4: dZ3 = (dY W4) * gelu'(Z3) (W4 [out][in]: B(k = o, n = i) = W4[o][i]), then dW4 = dY^T H3, db4
+    back_in(RowM<E>{S.DY, kOut}, kOut, RowM<E>{pW4, kHid}, S.Z3, S.D1, S.gb[0]);
     for (int tt = warp; tt < 16; tt += 8) {
       const int n0 = tt * 8;
       float c[4] = {0, 0, 0, 0};
-      mma_tile(ColMajor{S.DY, kOut}, RowMajor{S.H3, kHid}, 0, n0, kBatch, c, lane);
+      tile_op<F32>(ColM<E>{S.DY, kOut}, H3, 0, n0, kBatch, c, lane);
       for (int q = 0; q < 4; ++q) {
         const int o = g + (q >> 1) * 8, i = n0 + 2 * t4 + (q & 1);
         apply(oW4 + o * kHid + i, c[q]);
       }
     }
     if (tid < kOut) {
-      float s = 0.f;
-      for (int b = 0; b < kBatch; ++b) s += __bfloat162float(S.DY[b * kOut + tid]);
-      apply(oB4 + tid, s);
+      float sacc = 0.f;
+      for (int b = 0; b < kBatch; ++b) sacc += to_f(S.DY[b * kOut + tid]);
+      apply(oB4 + tid, sacc);
     }
-    if (tid < kHid) S.gb[tid] = 0.f;
     __syncthreads();
-    // dH3 = dY W4 (W4 [out][in]: B(k = o, n = i) = W4[o][i])
-    for (int mt = 0; mt < kBatch / 16; ++mt)
-      for (int nt = 0; nt < 2; ++nt) {
-        const int m0 = mt * 16, n0 = warp * 16 + nt * 8;
+    if constexpr (!F32) refresh(S.W4, oW4, kOut * kHid);
+    // ---- hidden layers 3, 2, 1: dZ_in first (old weights), then dW = dZ^T H_in and db
+    auto back_w = [&](const E* DZ, const auto& HIN, int KIN, int WOFF, int BOFF, const float* gb) {
+      // dW [128 x KIN]: warp w owns rows [16w, 16w + 16)
+      for (int nt = 0; nt < KIN / 8; ++nt) {
+        const int m0 = warp * 16, n0 = nt * 8;
         float c[4] = {0, 0, 0, 0};
-        mma_tile(RowMajor{S.DY, kOut}, RowMajor{S.W4, kHid}, m0, n0, kOut, c, lane);
-        float cs0 = 0.f, cs1 = 0.f;
+        tile_op<F32>(ColM<E>{DZ, kHid}, HIN, m0, n0, kBatch, c, lane);
         for (int q = 0; q < 4; ++q) {
-          const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);
-          const float dz = c[q] * gelu_grad(__bfloat162float(S.Z3[row * kHid + col]));
-          S.D1[row * kHid + col] = __float2bfloat16_rn(dz);
-          if (q & 1) cs1 += dz; else cs0 += dz;
-        }
-        // column sums over the 16 rows of this tile: reduce over g (lanes with equal t4)
-        for (int o = 4; o < 32; o <<= 1) {
-          cs0 += __shfl_xor_sync(0xffffffffu, cs0, o);
-          cs1 += __shfl_xor_sync(0xffffffffu, cs1, o);
-        }
-        if (g == 0) {
-          atomicAdd(&S.gb[n0 + 2 * t4], cs0);
-          atomicAdd(&S.gb[n0 + 2 * t4 + 1], cs1);
+          const int o = m0 + g + (q >> 1) * 8, i = n0 + 2 * t4 + (q & 1);
+          apply(WOFF + o * KIN + i, c[q]);
         }
       }
+      if (tid < kHid) apply(BOFF + tid, gb[tid]);
+      __syncthreads();
+    };
+    // layer 3 (dZ3 in D1, its bias gradient in gb[0])
+    if (tid < kHid) S.gb[1][tid] = 0.f;
     __syncthreads();
-    // W4 may now change (its old values were used above)
-    if (!A.grad_only)
-      for (int i = tid; i < kOut * kHid; i += 256) S.W4[i] = __float2bfloat16_rn(Wm[oW4 + i]);
-    // ---- hidden layers 3, 2, 1: dW = dZ^T H_in, db, dZ_in = (dZ W) * gelu'(Z_in)
-#define BWD_LAYER(DZ, HIN, KIN, WS, WOFF, BOFF, ZIN, DZOUT, HAS_IN)                           \
-  {                                                                                            \
-    /* dW [128 x KIN]: warp w owns rows [16w, 16w + 16) */                                    \
-    for (int nt = 0; nt < KIN / 8; ++nt) {                                                     \
-      const int m0 = warp * 16, n0 = nt * 8;                                                   \
-      float c[4] = {0, 0, 0, 0};                                                               \
-      mma_tile(ColMajor{DZ, kHid}, RowMajor{HIN, KIN}, m0, n0, kBatch, c, lane);              \
-      for (int q = 0; q < 4; ++q) {                                                            \
-        const int o = m0 + g + (q >> 1) * 8, i = n0 + 2 * t4 + (q & 1);                       \
-        apply(WOFF + o * KIN + i, c[q]);                                                       \
-      }                                                                                        \
-    }                                                                                          \
-    if (tid < kHid) apply(BOFF + tid, S.gb[tid]);                                              \
-    __syncthreads();                                                                           \
-    if (HAS_IN) {                                                                              \
-      if (tid < kHid) S.gb[tid] = 0.f;                                                         \
-      __syncthreads();                                                                         \
-      for (int mt = 0; mt < kBatch / 16; ++mt)                                                 \
-        for (int nt = 0; nt < 2; ++nt) {                                                       \
-          const int m0 = mt * 16, n0 = warp * 16 + nt * 8;                                     \
-          float c[4] = {0, 0, 0, 0};                                                           \
-          mma_tile(RowMajor{DZ, kHid}, RowMajor{WS, kHid}, m0, n0, kHid, c, lane);            \
-          float cs0 = 0.f, cs1 = 0.f;                                                          \
-          for (int q = 0; q < 4; ++q) {                                                        \
-            const int row = m0 + g + (q >> 1) * 8, col = n0 + 2 * t4 + (q & 1);              \
-            const float dz = c[q] * gelu_grad(__bfloat162float(ZIN[row * kHid + col]));       \
-            DZOUT[row * kHid + col] = __float2bfloat16_rn(dz);                                 \
-            if (q & 1) cs1 += dz; else cs0 += dz;                                              \
-          }                                                                                    \
-          for (int o = 4; o < 32; o <<= 1) {                                                   \
-            cs0 += __shfl_xor_sync(0xffffffffu, cs0, o);                                       \
-            cs1 += __shfl_xor_sync(0xffffffffu, cs1, o);                                       \
-          }                                                                                    \
-          if (g == 0) {                                                                        \
-            atomicAdd(&S.gb[n0 + 2 * t4], cs0);                                                \
-            atomicAdd(&S.gb[n0 + 2 * t4 + 1], cs1);                                            \
-          }                                                                                    \
-        }                                                                                      \
-      __syncthreads();                                                                         \
-    }                                                                                          \
-  }
-    BWD_LAYER(S.D1, S.H2, kHid, S.W3, oW3, oB3, S.Z2, S.D2, 1)
-    if (!A.grad_only)
-      for (int i = tid; i < kHid * kHid; i += 256) S.W3[i] = __float2bfloat16_rn(Wm[oW3 + i]);
-    BWD_LAYER(S.D2, S.H1, kHid, S.W2, oW2, oB2, S.Z1, S.D1, 1)
-    if (!A.grad_only)
-      for (int i = tid; i < kHid * kHid; i += 256) S.W2[i] = __float2bfloat16_rn(Wm[oW2 + i]);
-    BWD_LAYER(S.D1, S.X, kIn, S.W1, oW1, oB1, S.Z1, S.D2, 0)
-    if (!A.grad_only)
-      for (int i = tid; i < kHid * kIn; i += 256) S.W1[i] = __float2bfloat16_rn(Wm[oW1 + i]);
-#undef BWD_LAYER
+    back_in(RowM<E>{S.D1, kHid}, kHid, RowM<E>{pW3, kHid}, S.Z2, S.D2, S.gb[1]);
+    back_w(S.D1, H2, kHid, oW3, oB3, S.gb[0]);
+    if constexpr (!F32) refresh(S.W3, oW3, kHid * kHid);
+    // layer 2 (dZ2 in D2, bias gradient in gb[1])
+    if (tid < kHid) S.gb[0][tid] = 0.f;
+    __syncthreads();
+    back_in(RowM<E>{S.D2, kHid}, kHid, RowM<E>{pW2, kHid}, S.Z1, S.D1, S.gb[0]);
+    back_w(S.D2, H1, kHid, oW2, oB2, S.gb[1]);
+    if constexpr (!F32) refresh(S.W2, oW2, kHid * kHid);
+    // layer 1 (dZ1 in D1, bias gradient in gb[0]; its input is X)
+    back_w(S.D1, RowM<E>{S.X, kIn}, kIn, oW1, oB1, S.gb[0]);
+    if constexpr (!F32) refresh(S.W1, oW1, kHid * kIn);
     __syncthreads();
   }
 }
@@ -962,12 +1051,17 @@ extern "C" int stomsfem_surrogate_load(const void* host_buf, size_t buf_bytes, s
   return STOMSFEM_OK;
 }
 
-static int train_launch(const TrainArgs& A, int nfam, cudaStream_t st) {
-  const size_t smem = sizeof(TrainSmem);
-  STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(surrogate_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  surrogate_train_kernel<<<nfam, 256, smem, st>>>(A);
+template <bool F32>
+static int train_launch_t(const TrainArgs& A, int nfam, cudaStream_t st) {
+  const size_t smem = sizeof(TrainSmemT<F32>);
+  STOMSFEM_TRY_CUDA(
+      cudaFuncSetAttribute(surrogate_train_kernel<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  surrogate_train_kernel<F32><<<nfam, 256, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
+}
+static int train_launch(const TrainArgs& A, int nfam, bool fp32, cudaStream_t st) {
+  return fp32 ? train_launch_t<true>(A, nfam, st) : train_launch_t<false>(A, nfam, st);
 }
 
 extern "C" int stomsfem_surrogate_train(stomsfem_surrogate* h, const stomsfem_surrogate_cfg* cfg,
@@ -1009,6 +1103,7 @@ extern "C" int stomsfem_surrogate_train(stomsfem_surrogate* h, const stomsfem_su
   TrainArgs A;
   A.nfam = h->nfam;
   A.fam_row0 = row0_d;
+  A.row_lo = A.row_hi = 0;
   A.X = X;
   A.Y = Y;
   A.W = h->W;
@@ -1025,7 +1120,7 @@ extern "C" int stomsfem_surrogate_train(stomsfem_surrogate* h, const stomsfem_su
   A.eps = (float)cfg->eps;
   A.seed = cfg->seed;
   A.grad_only = 0;
-  if ((rc = train_launch(A, h->nfam, st)) != STOMSFEM_OK) {
+  if ((rc = train_launch(A, h->nfam, cfg->fp32_products != 0, st)) != STOMSFEM_OK) {
     cleanup();
     return rc;
   }
@@ -1047,33 +1142,48 @@ extern "C" int stomsfem_surrogate_train(stomsfem_surrogate* h, const stomsfem_su
   return STOMSFEM_OK;
 }
 
-extern "C" int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, float* grad,
-                                       float* loss, stomsfem_stream_t stream) {
+extern "C" int stomsfem_surrogate_grad(const float* weights, const float* X, const float* T, int32_t fp32_products,
+                                       float* grad, float* loss, stomsfem_stream_t stream) {
   if (!weights || !X || !T || !grad) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int* row0_d = nullptr;
-  STOMSFEM_TRY_CUDA(cudaMalloc(&row0_d, sizeof(int) * 2));
-  const int row0[2] = {0, kBatch};
-  int rc = check_cuda(cudaMemcpyAsync(row0_d, row0, sizeof(row0), cudaMemcpyHostToDevice, st), "memcpy");
-  if (rc == STOMSFEM_OK) {
-    TrainArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.nfam = 1;
-    A.fam_row0 = row0_d;
-    A.X = X;
-    A.Y = T;
-    A.W = const_cast<float*>(weights);
-    A.m = const_cast<float*>(weights);
-    A.v = const_cast<float*>(weights);
-    A.grad_out = grad;
-    A.loss_out = loss;
-    A.steps = 1;
-    A.grad_only = 1;
-    rc = train_launch(A, 1, st);
+  TrainArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.nfam = 1;
+  A.fam_row0 = nullptr;  // the batch's rows are [0, 64)
+  A.row_lo = 0;
+  A.row_hi = kBatch;
+  A.X = X;
+  A.Y = T;
+  A.W = const_cast<float*>(weights);  // read only in the gradient mode
+  A.m = const_cast<float*>(weights);
+  A.v = const_cast<float*>(weights);
+  A.grad_out = grad;
+  A.loss_out = loss;
+  A.steps = 1;
+  A.grad_only = 1;
+  return train_launch(A, 1, fp32_products != 0, st);
+}
+
+// Seeded Xavier-uniform initial weights: W[o][i] = lim (2 u - 1), lim =
+// sqrt(6 / (fan_in + fan_out)), u the top 53 bits of SplitMix64 of (seed,
+// family, parameter index) over 2^53; biases zero.
+extern "C" int stomsfem_surrogate_init_weights(int32_t n_families, uint64_t seed, float* w_host) {
+  if (n_families < 1 || !w_host) return set_error(STOMSFEM_EINVAL, "need n_families >= 1 and a host buffer");
+  const int wo[4] = {oW1, oW2, oW3, oW4}, bo[4] = {oB1, oB2, oB3, oB4};
+  const int fin[4] = {kIn, kHid, kHid, kHid}, fout[4] = {kHid, kHid, kHid, kOut};
+  for (int f = 0; f < n_families; ++f) {
+    float* w = w_host + (size_t)f * kParams;
+    for (int l = 0; l < 4; ++l) {
+      const double lim = std::sqrt(6.0 / (double)(fin[l] + fout[l]));
+      for (int q = 0; q < fin[l] * fout[l]; ++q) {
+        const uint64_t key = seed ^ ((uint64_t)f << 48) ^ (uint64_t)(wo[l] + q);
+        const double u = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
+        w[wo[l] + q] = (float)(lim * (2.0 * u - 1.0));
+      }
+      for (int q = 0; q < fout[l]; ++q) w[bo[l] + q] = 0.f;
+    }
   }
-  if (rc == STOMSFEM_OK) rc = check_cuda(cudaStreamSynchronize(st), "sync");
-  cudaFree(row0_d);
-  return rc;
+  return STOMSFEM_OK;
 }
 
 namespace {

@@ -81,9 +81,17 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
 }
 
-int upscale_slots_per_block(int precision) {
-  const int G = group_lanes(precision);
+int upscale_slots_per_block(const stomsfem_grid* grid, int32_t max_oversample, int precision) {
+  int nmax, bmax;
+  patch_limits(grid, max_oversample, &nmax, &bmax);
+  const int G = upscale_uses_tc(precision, grid->nf / grid->nc, bmax) ? 32 : group_lanes(precision);
   return upscale_warps(precision == STOMSFEM_FP64, G) * (32 / G);
+}
+
+int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int precision, int requested) {
+  int nmax, bmax;
+  patch_limits(grid, max_oversample, &nmax, &bmax);
+  return upscale_engine(requested, precision, grid->nf / grid->nc, bmax);
 }
 
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
@@ -97,10 +105,11 @@ size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
 // stomsfem_upscale with launch choices (the plan's autotuner).
 int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                   int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
-                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32) {
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine) {
   UpscaleTuning t;
   t.blocks_per_sm = blocks_per_sm;
   t.split_fp32 = split_fp32;
+  t.engine = engine;
   return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, nullptr,
                             nullptr, workspace, workspace_bytes, reinterpret_cast<stomsfem_stream_t>(st), t);
 }

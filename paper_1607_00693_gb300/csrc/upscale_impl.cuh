@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "band_block.cuh"
+#include "band_tc.cuh"
 #include "common.cuh"
 
 namespace stomsfem {
@@ -424,6 +425,7 @@ struct UpscaleArgs {
 struct UpscaleTuning {
   int blocks_per_sm = 0;  // 0: as many as fit
   int split_fp32 = 1;     // FP32 form: separate forward-only launch for the cells without oversampling
+  int engine = 0;         // FP32 forms: factorisation engine (kEngine*; 0 = the default for the patch size)
 };
 
 // Upscale launch modes: 0 every unit (back-substitution route), 1 the
@@ -467,6 +469,16 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Shared-memory view of one unit for the substitutions (and, without TC,
+// the factorisation).
+template <typename TK, int TC>
+__device__ inline BlkSmem<TK> unit_blk(unsigned char* base, const TcSmem& tsm, int NB, int bmax) {
+  if constexpr (TC > 0)
+    return tc_blk_view(tsm);
+  else
+    return make_blk<TK>(base, NB, bmax);
+}
+
 // TK: factor/solve type; TA: type of the K_e/b_e accumulation and of the
 // recombination; RPL: panel rows per lane (ceil((G/2 + bmax) / G)); G: lanes
 // per unit.  G = 32: one unit per warp (any unit order, including a device
@@ -475,19 +487,27 @@ __device__ __forceinline__ T group_sum(T v) {
 // in lockstep (an odd last sample is mirrored by the idle half, which
 // writes nothing).
 // OSC: the oscillatory boundary data of the cell problems (PatchGenOsc).
-template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false>
+// TC > 0 (FP32 factor, G = 32): the factorisation of band_tc.cuh (window
+// in mma accumulator registers, trailing update on the tensor cores with
+// operands split into TC TF32 parts, column blocks of 8), b <= 40; the
+// substitutions read its 8-column blocks.
+template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false, int TC = 0>
 __global__ void __launch_bounds__(upscale_warps(sizeof(TK) == 8, G) * 32,
                                   sizeof(TK) == 4 ? (G == 16 ? 3 : 4) : (G == 16 ? 3 : 2))
 upscale_kernel(UpscaleArgs A) {
   // the oscillatory data run every cell by back substitution (one launch)
   static_assert(!OSC || MODE == kModeAll, "oscillatory data: back-substitution route only");
-  constexpr int NB = G / 2;
+  static_assert(TC == 0 || (G == 32 && sizeof(TK) == 4), "tensor-core factorisation: FP32 factor, one unit per warp");
+  constexpr int NB = TC > 0 ? kTcNB : G / 2;
   constexpr int GPW = 32 / G;  // units per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int gl = lane % G, grp = lane / G;
   const int wib = threadIdx.x >> 5;
-  const BlkSmem<TK> sm = make_blk<TK>(smem + (wib * GPW + grp) * blk_smem_bytes<TK>(NB, A.bmax), NB, A.bmax);
+  // per-unit shared memory (the oscillatory tables follow all of it)
+  const size_t unit_smem = TC > 0 ? kTcSmemWarp : blk_smem_bytes<TK>(NB, A.bmax);
+  const TcSmem tsm = make_tc(smem + wib * kTcSmemWarp);
+  const BlkSmem<TK> sm = unit_blk<TK, TC>(smem + (wib * GPW + grp) * unit_smem, tsm, NB, A.bmax);
   constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
   const long long gw = (long long)blockIdx.x * WPB + wib;
   const long long nw = (long long)gridDim.x * WPB;
@@ -546,7 +566,7 @@ upscale_kernel(UpscaleArgs A) {
     pg.mx = g.mx;
     pg.finish();
     if constexpr (OSC) {
-      pg.tab = reinterpret_cast<const double*>(smem + (size_t)WPB * GPW * blk_smem_bytes<TK>(NB, A.bmax) +
+      pg.tab = reinterpret_cast<const double*>(smem + (size_t)WPB * GPW * unit_smem +
                                                (size_t)(wib * GPW + grp) * osc_tab_bytes(A.bmax));
       pg.ts = A.bmax + 1;
       osc_fill_tables(pg, const_cast<double*>(pg.tab), pg.ts, gl);
@@ -572,11 +592,19 @@ upscale_kernel(UpscaleArgs A) {
     // stay in lockstep); its unit gets NaN results and a status below
     int fail = -1;
     if constexpr (fwd_only) {
-      if (g.n > 0)
-        fail = blk_factor<G, TK, 4, RPL, Gen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
+      if (g.n > 0) {
+        if constexpr (TC > 0)
+          fail = tc_factor<4, true, Gen, TS, TC>(pg, g.n, g.b, A.bmax, tsm, reinterpret_cast<float*>(Lg), psi0, gl,
+                                                 yy);
+        else
+          fail = blk_factor<G, TK, 4, RPL, Gen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
+      }
     } else if (g.n > 0) {
-      fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
-      blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
+      if constexpr (TC > 0)
+        fail = tc_factor<3, false, Gen, TS, TC>(pg, g.n, g.b, A.bmax, tsm, reinterpret_cast<float*>(Lg), psi0, gl);
+      else
+        fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
+      blk_backward<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
       // FP64 iterative refinement with the factor: corr = residual, solve, add
       for (int it = 0; it < A.refine; ++it) {
         __syncwarp();
@@ -592,8 +620,8 @@ upscale_kernel(UpscaleArgs A) {
           }
         }
         __syncwarp();
-        blk_forward_stored<G, TK, 3, RPL>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
-        blk_backward<G, TK, 3>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        blk_forward_stored<G, TK, 3, RPL, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        blk_backward<G, TK, 3, double, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
         __syncwarp();
         for (int k = gl; k < g.n * 3; k += G) psi0[k] += (TS)corr[k];
       }
@@ -841,12 +869,13 @@ static void patch_limits(const stomsfem_grid* g, int max_o, int* nmax, int* bmax
   *bmax = m + 1;
 }
 
-template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false>
+template <typename TK, typename TA, int RPL, int G, int MODE, bool PG, bool OSC = false, int TC = 0>
 static int launch_upscale(const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
-  auto kern = upscale_kernel<TK, TA, RPL, G, MODE, PG, OSC>;
+  auto kern = upscale_kernel<TK, TA, RPL, G, MODE, PG, OSC, TC>;
   constexpr int WPB = upscale_warps(sizeof(TK) == 8, G);
   // (oscillatory data: each unit's edge tables after all the windows)
-  const size_t smem = (blk_smem_bytes<TK>(G / 2, A.bmax) + (OSC ? osc_tab_bytes(A.bmax) : 0)) * WPB * (32 / G);
+  const size_t unit_smem = TC > 0 ? kTcSmemWarp : blk_smem_bytes<TK>(G / 2, A.bmax);
+  const size_t smem = (unit_smem + (OSC ? osc_tab_bytes(A.bmax) : 0)) * WPB * (32 / G);
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STOMSFEM_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
@@ -880,6 +909,39 @@ static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(i
 // Lanes per unit of each form: two units per warp.
 constexpr int group_lanes(int) { return 16; }
 
+// Factorisation engines of the FP32 forms: the tensor-core factorisation of
+// band_tc.cuh with operands in three TF32 parts (exact; the default when
+// every patch has a half bandwidth in [4, 40]) or two parts (about 2^-21 per
+// product, faster), or the two-units-per-warp FMA factorisation of
+// band_block.cuh (any bandwidth).
+enum {
+  kEngineAuto = STOMSFEM_ENGINE_AUTO,
+  kEngineBlocked = STOMSFEM_ENGINE_BLOCKED,
+  kEngineTc3 = STOMSFEM_ENGINE_TC3,
+  kEngineTc2 = STOMSFEM_ENGINE_TC2
+};
+
+static bool upscale_tc_eligible(int precision, int rho, int bmax) {
+  return precision != STOMSFEM_FP64 && rho >= 4 && bmax <= kTcBMax;
+}
+static int upscale_engine(int requested, int precision, int rho, int bmax) {
+  if (precision == STOMSFEM_FP64 || !upscale_tc_eligible(precision, rho, bmax)) return kEngineBlocked;
+  return requested == kEngineAuto ? kEngineTc3 : requested;
+}
+static bool upscale_uses_tc(int precision, int rho, int bmax) {
+  return upscale_engine(kEngineAuto, precision, rho, bmax) != kEngineBlocked;
+}
+
+// Launch of an FP32-factor form with the chosen engine.
+template <typename TA, int MODE, bool PG, bool OSC>
+static int launch_fp32(int engine, const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
+  if (engine == kEngineTc3) return launch_upscale<float, TA, 2, 32, MODE, PG, OSC, 3>(A, max_blocks, st);
+  if constexpr (!PG && !OSC)
+    if (engine == kEngineTc2) return launch_upscale<float, TA, 2, 32, MODE, PG, OSC, 2>(A, max_blocks, st);
+  if (engine != kEngineBlocked) return set_error(STOMSFEM_EINVAL, "engine %d not offered for this form", engine);
+  return launch_rpl<float, TA, 16, MODE, PG, OSC>(A, max_blocks, st);
+}
+
 // The host side of stomsfem_upscale / stomsfem_upscale_pg (PG: Ke holds
 // 16 entries per unit; OSC: the oscillatory boundary data of the cell
 // problems, stomsfem_upscale_bc).
@@ -908,7 +970,8 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
   slot_layout(nmax, bmax, precision, &sb, &lb);
   const long long units = (long long)S * grid->nc * grid->nc;
   const long long slots = (long long)(workspace_bytes / sb);
-  const int G = group_lanes(precision);
+  const int engine = upscale_engine(tune.engine, precision, grid->nf / grid->nc, bmax);
+  const int G = engine != kEngineBlocked ? 32 : group_lanes(precision);
   const int WPB = upscale_warps(precision == STOMSFEM_FP64, G);
   const int slots_per_block = WPB * (32 / G);
   if (slots < slots_per_block)
@@ -954,8 +1017,7 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
     if (precision == STOMSFEM_FP32 && !phi && tune.split_fp32) {
       // FP32 without phi output: cells without oversampling take the
       // forward-only route in a launch of their own, the others follow
-      constexpr int G = group_lanes(STOMSFEM_FP32);
-      if (!oversample) return launch_rpl<float, float, G, kModeFwd, PG, OSC>(A, max_blocks, st);
+      if (!oversample) return launch_fp32<float, kModeFwd, PG, OSC>(engine, A, max_blocks, st);
       const size_t lbytes = cell_list_bytes(grid);
       const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
       if (slots2 >= slots_per_block) {
@@ -969,19 +1031,18 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
         const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
         A.cell_list = list0;
         A.cell_count = counts;
-        rc = launch_rpl<float, float, G, kModeFwd, PG, OSC>(A, mb, st);
+        rc = launch_fp32<float, kModeFwd, PG, OSC>(engine, A, mb, st);
         if (rc) return rc;
         A.cell_list = list1;
         A.cell_count = counts + 1;
-        return launch_rpl<float, float, G, kModeRest, PG, OSC>(A, mb, st);
+        return launch_fp32<float, kModeRest, PG, OSC>(engine, A, mb, st);
       }
     }
   }
   if (precision == STOMSFEM_FP64)
     return launch_rpl<double, double, group_lanes(STOMSFEM_FP64), kModeAll, PG, OSC>(A, max_blocks, st);
-  if (precision == STOMSFEM_FP32_REFINED)
-    return launch_rpl<float, double, group_lanes(STOMSFEM_FP32_REFINED), kModeAll, PG, OSC>(A, max_blocks, st);
-  return launch_rpl<float, float, group_lanes(STOMSFEM_FP32), kModeAll, PG, OSC>(A, max_blocks, st);
+  if (precision == STOMSFEM_FP32_REFINED) return launch_fp32<double, kModeAll, PG, OSC>(engine, A, max_blocks, st);
+  return launch_fp32<float, kModeAll, PG, OSC>(engine, A, max_blocks, st);
 }
 
 

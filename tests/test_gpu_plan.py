@@ -56,7 +56,7 @@ def test_plan_step_equals_direct_calls(case, prec):
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # capture + launch
             st.synchronize()
             np.testing.assert_array_equal(u.cpu().numpy(), u0)
-            assert api.stomsfem_plan_info(h)[2] == 1
+            assert api.stomsfem_plan_info(h)[3] == 1
             u.fill_(0.0)
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # replay
             st.synchronize()
@@ -76,9 +76,10 @@ def test_plan_step_equals_direct_calls(case, prec):
 
 
 def test_plan_tune_and_recapture(case):
-    """FP32 with oversampling: six launch choices timed; the chosen one
-    reproduces the direct result (bit for bit with the split launch, within
-    the FP32 tolerance with one launch); a new output buffer re-captures."""
+    """FP32 with oversampling: launch choices (blocks per SM, split, engine)
+    timed; the chosen one reproduces the direct result (bit for bit with
+    the split launch and the default engine, within the FP32 tolerance
+    otherwise); a new output buffer re-captures."""
     c = case
     u0 = _direct(c, api.FP32)
     h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], api.FP32, oversample=c["ov"], max_oversample=c["mo"])
@@ -88,18 +89,52 @@ def test_plan_tune_and_recapture(case):
         with torch.cuda.stream(st):
             bps, split, ms = api.stomsfem_plan_tune(h, c["xt"], u, stream=st)
             assert bps in (0, 1, 2) and split in (0, 1) and ms > 0
-            assert api.stomsfem_plan_info(h)[:3] == (bps, split, 0)
+            info = api.stomsfem_plan_info(h)
+            assert info[:2] == (bps, split) and info[2] in (api.ENGINE_TC3, api.ENGINE_BLOCKED) and info[3] == 0
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)
             u2 = torch.empty_like(u)
             api.stomsfem_plan_step(h, c["xt"], u2, stream=st)
             st.synchronize()
         for x in (u.cpu().numpy(), u2.cpu().numpy()):
-            if split:
+            if split and info[2] == api.ENGINE_TC3:
                 np.testing.assert_array_equal(x, u0)
             else:
                 assert np.max(np.linalg.norm(x - u0, axis=1) / np.linalg.norm(u0, axis=1)) <= 1e-5
     finally:
         api.stomsfem_plan_destroy(h)
+
+
+@pytest.mark.parametrize("prec,engine", [(api.FP32, api.ENGINE_BLOCKED), (api.FP32, api.ENGINE_TC3),
+                                         (api.FP32_REFINED, api.ENGINE_BLOCKED),
+                                         (api.FP32_REFINED, api.ENGINE_TC3),
+                                         (api.FP32_REFINED, api.ENGINE_TC2)])
+def test_plan_engines_match_oracle(case, orc, prec, engine):
+    """Each factorisation engine a plan can be set to, with oversampled
+    patches: K_e and the coarse solution against the FP64 oracle within the
+    form's tolerance (FP32 1e-5, FP32 + two FP64 refinement sweeps 1e-10)."""
+    c = case
+    g, S = c["g"], c["S"]
+    tol = 1e-5 if prec == api.FP32 else 1e-10
+    h = api.stomsfem_plan_create(g, c["fld"], S, prec, oversample=c["ov"], max_oversample=c["mo"], refine_iters=2)
+    try:
+        api.stomsfem_plan_set_choice(h, 0, 1, engine)
+        assert api.stomsfem_plan_info(h)[2] == engine
+        st = torch.cuda.Stream()
+        u = torch.empty((S, c["nn"]), dtype=torch.float64, device=DEV)
+        with torch.cuda.stream(st):
+            api.stomsfem_plan_step(h, c["xt"], u, use_graph=False, stream=st)
+            st.synchronize()
+    finally:
+        api.stomsfem_plan_destroy(h)
+    xi = c["xt"].cpu().numpy()
+    fld_d = dict(W.workload("upscale_1024")["field"], nbx=4, nby=4, width=0.125)
+    a = orc.sample_coef(g.nf, fld_d, xi)
+    ov = c["ov"].cpu().numpy()
+    Ko, bo = orc.upscale(g.nf, g.nc, 1.0, a, ov)
+    uo = orc.coarse_solve(g.nc, Ko, bo)
+    err = np.max(np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1))
+    print("engine %d precision %d: coarse error %.3e" % (engine, prec, err))
+    assert err <= tol
 
 
 def test_plan_default_stream_runs_directly(case):
@@ -111,6 +146,6 @@ def test_plan_default_stream_runs_directly(case):
         api.stomsfem_plan_step(h, c["xt"], u)      # the current (default) stream: no capture
         torch.cuda.synchronize()
         np.testing.assert_array_equal(u.cpu().numpy(), u0)
-        assert api.stomsfem_plan_info(h)[2] == 0
+        assert api.stomsfem_plan_info(h)[3] == 0
     finally:
         api.stomsfem_plan_destroy(h)

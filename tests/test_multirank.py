@@ -59,6 +59,12 @@ def test_shards_and_max_time(ws):
 def test_single_rank_helpers():
     import bench
     assert bench.shard(0, 1, 4096, 512) == (0, 4096)
-    # fewer samples than a batch per rank: every rank still gets one batch
+    # fewer samples than a batch per rank: every rank still gets one batch,
+    # and every shard stays inside the workload's 4096 samples
     assert bench.shard(3, 16, 4096, 512) == (1536, 512)
+    assert bench.shard(8, 16, 4096, 512) == (3584, 512)
+    assert bench.shard(15, 16, 4096, 512) == (3584, 512)
+    for r in range(16):
+        first, count = bench.shard(r, 16, 4096, 512)
+        assert 0 <= first and first + count <= 4096
     assert bench.max_over_ranks(3.5) == 3.5
