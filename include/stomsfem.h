@@ -311,6 +311,48 @@ int stomsfem_plan_info(const stomsfem_plan* plan, int32_t* blocks_per_sm, int32_
                        int32_t* engine, int32_t* graph_ready, size_t* device_bytes);
 
 /* ---------------------------------------------------------------------
+ * Local KL parametrization (Sec. 2.1.1, Def. of the local KL expansion,
+ * Eqs. localCov, localKL, local_KL_truncation).  On the patch P_m of every
+ * coarse cell (the cell plus an oversampling layer of `oversample` fine
+ * elements, clipped to the domain) the field's covariance restricted to
+ * P_m has eigenpairs (lambda_k, f_k), int_P f_k^2 = 1; a field sample
+ * kappa has the local parameters
+ *   xi_k = lambda_k^{-1/2} int_P (kappa - kappa_bar) f_k,  k < K_m,
+ * and kappa ~ kappa_bar + sum_k sqrt(lambda_k) xi_k f_k on P_m.  The field
+ * is piecewise constant on the fine elements (centroid values), integrals
+ * use the midpoint rule (weight h^2 per element), so the patch operator is
+ * h^2 C_m between element centroids and f_k = u_k / h (u_k orthonormal).
+ * ------------------------------------------------------------------- */
+typedef struct stomsfem_local_kl stomsfem_local_kl; /* opaque, library-owned */
+enum { STOMSFEM_KL_BUMPS = 0, STOMSFEM_KL_GAUSSIAN = 1 };
+
+/* Offline stage on the GPU (FP64, one CTA per cell, Jacobi eigensolver).
+ * cov_kind STOMSFEM_KL_BUMPS: the covariance of the bump fields'
+ * log-coefficient s z, s^2 var sum_i psi_i(x) psi_i(y) (field: nbx, nby,
+ * width, scale; var the variance of each xi_i, 1/3 for U[-1,1], 1 for
+ * N(0,1)); STOMSFEM_KL_GAUSSIAN: sigma^2 exp(-|x - y|^2 / beta^2) (field
+ * may be NULL).  Modes kept: with energy > 0 the fewest whose eigenvalues
+ * reach that share of the patch's spectrum, else kmax; at most kmax (1..32)
+ * and only positive eigenvalues (> 1e-12 lambda_1).  k_out host [nc*nc]
+ * (or NULL) receives K_m.  Patches of at most 112 fine elements.
+ * Synchronises `stream`.  EINVAL on bad arguments, ECUDA. */
+int stomsfem_local_kl_build(const stomsfem_grid* grid, int32_t oversample, int32_t cov_kind,
+                            const stomsfem_field* field, double var, double beta, double sigma, int32_t kmax,
+                            double energy, stomsfem_local_kl** out, int32_t* k_out, stomsfem_stream_t stream);
+int stomsfem_local_kl_destroy(stomsfem_local_kl* kl);
+/* Host copies (either may be NULL): lam [nc*nc][kmax] (descending, 0 past
+ * K_m) and the projection weights w [nc*nc][kmax][112], w_k(e) = h u_k(e) /
+ * sqrt(lambda_k) over the patch's elements in y-major order (0 past the
+ * patch and past K_m).  Synchronous. */
+int stomsfem_local_kl_modes(const stomsfem_local_kl* kl, double* lam_host, double* w_host);
+/* Online stage: kappa device [S][nf][nf] (the field, e.g. log a),
+ * kappa_bar device [nf][nf] or NULL (zero mean) -> xi device
+ * [S][nc*nc][kmax] (0 past K_m), xi_k = sum_e w_k(e) (kappa_e -
+ * kappa_bar_e), FP64.  Stream-ordered. */
+int stomsfem_local_kl_project(const stomsfem_local_kl* kl, const double* kappa, const double* kappa_bar,
+                              int32_t S, double* xi, stomsfem_stream_t stream);
+
+/* ---------------------------------------------------------------------
  * Two-level Monte Carlo (Remark in Sec. 4.1.1, Eq. MCmean2level):
  *   M2 = mean over N_H samples of u_H
  *      + mean over N_h other samples of (u_h - u_H at the coarse nodes),
@@ -451,11 +493,28 @@ int stomsfem_build_pod(const stomsfem_grid* grid, const double* phi_snap, const 
                        int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
                        stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
 
+/* Offline stage with one reduced basis per basis function (the patch study
+ * of Sec. 5.1 expands phi^1, phi^2, phi^3 separately): per cell and
+ * l = 1..3, the KL expansion of the centred interior snapshots of phi_l
+ * alone in the same energy inner product, truncated by the same rule at
+ * most max_rank_per_l modes (or exactly ranks_in[cell][l], host
+ * [nc*nc][3]); phi_4 follows online from the partition of unity,
+ * phi_4 = 1 - phi_1 - phi_2 - phi_3.  The extended basis is
+ * W = [phibar_1..4, V_1, V_2, V_3] (each V_l in a block of max_rank_per_l
+ * columns), the online reduced systems block diagonal (one per l, one
+ * right-hand side each).  ranks_out host [nc*nc][3] or NULL.  Limits:
+ * 2 <= rho <= 8, 1 <= max_rank_per_l <= 9.  The handle serves
+ * stomsfem_pod_upscale, stomsfem_pod_set_affine / _upscale_affine, save and
+ * load like a shared-basis one.  Errors as stomsfem_pod_build. */
+int stomsfem_pod_build_per_l(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                             int32_t S_train, double tol, int32_t max_rank_per_l, const int32_t* ranks_in,
+                             stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
+
 /* Frees the handle (synchronous). */
 int stomsfem_pod_destroy(stomsfem_pod* pod);
 
-/* Copies all KL eigenvalues, host [nc*nc][(rho-1)^2], descending per cell
- * (synchronous). */
+/* Copies all KL eigenvalues, host [nc*nc][(rho-1)^2] (per-l handles:
+ * [nc*nc][3][(rho-1)^2]), descending per cell (and l) (synchronous). */
 int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host);
 
 /* Checkpoint of the offline stage, so that the online stage (Alg. 4) can run
@@ -463,8 +522,8 @@ int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host);
  * load weights, eigenvalues, BF16 element tensors and ranks into the
  * caller's host buffer: with host_buf NULL only *bytes is set (the size
  * needed); ENOMEM if buf_bytes is smaller (then *bytes holds the size).
- * Format: magic "STMFPOD1", format version, byte-order probe, dimensions,
- * arrays in native byte order.  Synchronous. */
+ * Format: magic "STMFPOD1" ("STMFPODL" for per-l bases), format version,
+ * byte-order probe, dimensions, arrays in native byte order.  Synchronous. */
 int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t buf_bytes, size_t* bytes);
 /* Rebuilds a handle from a stomsfem_pod_save buffer.  EVERSION if the magic
  * tag, format version or byte order differ; EINVAL if the buffer is

@@ -59,6 +59,8 @@ _SIG = {
                                           ctypes.POINTER(_P), _P, _P]),
     "stomsfem_build_pod": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, ctypes.c_double, _I, _P,
                                           ctypes.POINTER(_P), _P, _P]),
+    "stomsfem_pod_build_per_l": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, ctypes.c_double, _I, _P,
+                                                ctypes.POINTER(_P), _P, _P]),
     "stomsfem_pod_destroy": (ctypes.c_int, [_P]),
     "stomsfem_pod_eigenvalues": (ctypes.c_int, [_P, _P]),
     "stomsfem_pod_save": (ctypes.c_int, [_P, _P, _SZ, ctypes.POINTER(_SZ)]),
@@ -103,6 +105,12 @@ _SIG = {
     "stomsfem_plan_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _I, _P]),
     "stomsfem_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "stomsfem_plan_set_choice": (ctypes.c_int, [_P, _I, _I, _I]),
+    "stomsfem_local_kl_build": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Field),
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _I,
+                                               ctypes.c_double, ctypes.POINTER(_P), _P, _P]),
+    "stomsfem_local_kl_destroy": (ctypes.c_int, [_P]),
+    "stomsfem_local_kl_modes": (ctypes.c_int, [_P, _P, _P]),
+    "stomsfem_local_kl_project": (ctypes.c_int, [_P, _P, _P, _I, _P, _P]),
     "stomsfem_ri_plan": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,
                                         _P, _P, _P, _P, _P]),
     "stomsfem_ri_build": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), ctypes.c_double, _I,

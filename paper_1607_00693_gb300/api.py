@@ -156,6 +156,25 @@ def stomsfem_pod_build(g: Grid, phi_snap, a_train, tol=1e-6, max_rank=27, ranks=
     return h, list(rk)
 
 
+def stomsfem_pod_build_per_l(g: Grid, phi_snap, a_train, tol=1e-6, max_rank_per_l=9, ranks=None, stream=None):
+    """One basis per basis function: returns (handle, ranks [nc*nc][3] list)."""
+    S = a_train.shape[0]
+    ncell = g.nc * g.nc
+    rho = g.nf // g.nc
+    h = ctypes.c_void_p()
+    rk = (ctypes.c_int32 * (3 * ncell))()
+    rin = None
+    if ranks is not None:
+        flat = [int(x) for row in ranks for x in row]
+        rin = (ctypes.c_int32 * (3 * ncell))(*flat)
+    L.check(L.lib().stomsfem_pod_build_per_l(
+        ctypes.byref(g), _dev(phi_snap, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi_snap"),
+        _dev(a_train, torch.float64, (S, g.nf, g.nf), "a_train"), S, float(tol), int(max_rank_per_l),
+        ctypes.cast(rin, ctypes.c_void_p) if rin is not None else None, ctypes.byref(h),
+        ctypes.cast(rk, ctypes.c_void_p), _stream(stream)))
+    return h, [list(rk[3 * c:3 * c + 3]) for c in range(ncell)]
+
+
 def stomsfem_build_pod(g: Grid, phi_snap, a_train, tol=1e-6, max_rank=27, ranks=None, stream=None):
     """The POD offline step under its method name: as stomsfem_pod_build."""
     return stomsfem_pod_build(g, phi_snap, a_train, tol, max_rank, ranks, stream)
@@ -165,10 +184,11 @@ def stomsfem_pod_destroy(h):
     L.check(L.lib().stomsfem_pod_destroy(h))
 
 
-def stomsfem_pod_eigenvalues(h, g: Grid):
+def stomsfem_pod_eigenvalues(h, g: Grid, per_l=False):
+    """[nc*nc][n] (per-l handles: [nc*nc][3][n]) KL eigenvalues, descending."""
     import numpy as np
     rho = g.nf // g.nc
-    lam = np.empty((g.nc * g.nc, (rho - 1) ** 2))
+    lam = np.empty((g.nc * g.nc, 3, (rho - 1) ** 2) if per_l else (g.nc * g.nc, (rho - 1) ** 2))
     L.check(L.lib().stomsfem_pod_eigenvalues(h, lam.ctypes.data_as(ctypes.c_void_p)))
     return lam
 
@@ -574,3 +594,42 @@ def stomsfem_ri_load(data: bytes):
     nfam = ctypes.c_int32()
     L.check(L.lib().stomsfem_ri_load(buf, len(data), ctypes.byref(h), ctypes.byref(nfam)))
     return h, nfam.value
+
+
+# ---------------------------------------------------------------- local KL
+
+KL_BUMPS, KL_GAUSSIAN, KL_MAX_N = 0, 1, 112
+
+
+def stomsfem_local_kl_build(g: Grid, oversample, cov_kind, fld: Field = None, var=1.0 / 3.0, beta=0.1,
+                            sigma=1.0, kmax=16, energy=0.0, stream=None):
+    """Returns (handle, K per cell list)."""
+    h = ctypes.c_void_p()
+    ncell = g.nc * g.nc
+    k = (ctypes.c_int32 * ncell)()
+    L.check(L.lib().stomsfem_local_kl_build(ctypes.byref(g), int(oversample), int(cov_kind),
+                                            ctypes.byref(fld) if fld is not None else None, float(var),
+                                            float(beta), float(sigma), int(kmax), float(energy), ctypes.byref(h),
+                                            ctypes.cast(k, ctypes.c_void_p), _stream(stream)))
+    return h, list(k)
+
+
+def stomsfem_local_kl_destroy(h):
+    L.check(L.lib().stomsfem_local_kl_destroy(h))
+
+
+def stomsfem_local_kl_modes(h, g: Grid, kmax):
+    """(lam [ncell][kmax], w [ncell][kmax][112]) host arrays."""
+    import numpy as np
+    ncell = g.nc * g.nc
+    lam = np.empty((ncell, kmax))
+    w = np.empty((ncell, kmax, KL_MAX_N))
+    L.check(L.lib().stomsfem_local_kl_modes(h, lam.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)))
+    return lam, w
+
+
+def stomsfem_local_kl_project(h, kappa, xi, kappa_bar=None, stream=None):
+    S = kappa.shape[0]
+    L.check(L.lib().stomsfem_local_kl_project(h, _dev(kappa, torch.float64, None, "kappa"),
+                                              _dev(kappa_bar, torch.float64, None, "kappa_bar"), S,
+                                              _dev(xi, torch.float64, None, "xi"), _stream(stream)))

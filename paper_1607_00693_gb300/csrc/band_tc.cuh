@@ -124,9 +124,9 @@ __device__ __forceinline__ void tf32_parts(float x, uint32_t (&p)[TERMS]) {
   }
 }
 
-// C += A B with A, B given by their TF32 parts, smallest products first.
-// The products go into a zero accumulator D, which is then added to C with
-// FP32 additions: the tensor core's own accumulation (truncating, not
+// C -= A B with A, B given by their TF32 parts, smallest products first.
+// The products go into a zero accumulator D, which is then subtracted from C
+// with FP32 operations: the tensor core's own accumulation (truncating, not
 // rounding to nearest) then errs relative to the update, not to the window
 // entry it updates.  TERMS = 2: hi*lo, lo*hi, hi*hi (drops lo*lo and the
 // parts' remainders: about 2^-21 of each product).  TERMS = 3: the six
@@ -150,7 +150,7 @@ __device__ __forceinline__ void tc_tile_update(float (&c)[4], const uint32_t (&a
     mma_tf32(d, a[0], b[0]);
   }
 #pragma unroll
-  for (int e = 0; e < 4; ++e) c[e] += d[e];
+  for (int e = 0; e < 4; ++e) c[e] -= d[e];
 }
 
 // Rows [wr0, wr0 + 8) of the window (absolute rows r0 + q, r0 = K + wr0):
@@ -317,15 +317,17 @@ __device__ int tc_factor(const Gen& gen, int n, int b, int bmax, const TcSmem& s
     __syncwarp();
     // ---- 2. trailing update on the tensor cores: tiles (i, j), j >= 1
     if (np > nb) {
-      // A operands (-L, rows of tile i; rows 0..7 of tile 0 are the panel's
-      // own rows, whose results are discarded: zero there), split into
-      // TF32 parts
+      // A operand of row tile i: L[16 i + m][k] (m16n8k8 layout a0 = (g, t),
+      // a1 = (g + 8, t), a2 = (g, t + 4), a3 = (g + 8, t + 4)), split into
+      // TF32 parts.  The B operand of column tile j, B[k][n] = L[8 j + n][k]
+      // (b0 = (k = t, n = g), b1 = (t + 4, g)), is the same data: (a0, a2)
+      // of row tile j / 2 for even j, (a1, a3) for odd j.
       uint32_t ap[3][TERMS][4];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const float* r0 = s.pn + (16 * i + g) * kTcPP;
         const float* r1 = r0 + 8 * kTcPP;
-        const float x[4] = {i == 0 ? 0.f : -r0[t], -r1[t], i == 0 ? 0.f : -r0[t + 4], -r1[t + 4]};
+        const float x[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           uint32_t part[TERMS];
@@ -336,19 +338,14 @@ __device__ int tc_factor(const Gen& gen, int n, int b, int bmax, const TcSmem& s
       }
 #pragma unroll
       for (int j = 1; j < 6; ++j) {
-        // B operand of column tile j: B[k][n] = L[8 j + n][k]
         uint32_t bp[TERMS][2];
-        {
-          const float* rowp = s.pn + (8 * j + g) * kTcPP;
-          uint32_t p0[TERMS], p1[TERMS];
-          tf32_parts<TERMS>(rowp[t], p0);
-          tf32_parts<TERMS>(rowp[t + 4], p1);
 #pragma unroll
-          for (int q = 0; q < TERMS; ++q) {
-            bp[q][0] = p0[q];
-            bp[q][1] = p1[q];
-          }
+        for (int q = 0; q < TERMS; ++q) {
+          bp[q][0] = ap[j / 2][q][(j & 1) ? 1 : 0];
+          bp[q][1] = ap[j / 2][q][(j & 1) ? 3 : 2];
         }
+        // rows 0..7 of row tile 0 are the panel's own rows: their results
+        // are never used (the shift discards them)
 #pragma unroll
         for (int i = (j - 1) / 2; i < 3; ++i) tc_tile_update<TERMS>(W[tc_tile(i, j)], ap[i], bp);
       }

@@ -33,6 +33,9 @@ int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* over
 // The factorisation engine (STOMSFEM_ENGINE_*) a request resolves to for a
 // grid, oversampling limit and precision.
 int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int precision, int requested);
+// Whether the tensor-core engines can serve a grid, oversampling limit and
+// precision (FP32 forms, 4 <= nf/nc, half bandwidth <= 40).
+bool upscale_tc_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision);
 
 // Petrov-Galerkin upscaling with the oscillatory boundary data of the cell
 // problems (the Petrov-Galerkin half of stomsfem_upscale_bc).

@@ -116,9 +116,7 @@ extern "C" int stomsfem_plan_tune(stomsfem_plan* p, const double* xi, double* u,
   // FP32 forms: the exact tensor-core factorisation and the FMA one (the
   // two-part split is left out: its rounding exceeds the FP32 form's)
   std::vector<int> engines = {STOMSFEM_ENGINE_AUTO};
-  if (p->precision != STOMSFEM_FP64 && upscale_engine_of(&p->grid, p->max_o, p->precision, STOMSFEM_ENGINE_AUTO) !=
-                                            STOMSFEM_ENGINE_BLOCKED)
-    engines = {STOMSFEM_ENGINE_TC3, STOMSFEM_ENGINE_BLOCKED};
+  if (upscale_tc_ok(&p->grid, p->max_o, p->precision)) engines = {STOMSFEM_ENGINE_TC3, STOMSFEM_ENGINE_BLOCKED};
   std::vector<Cand> cands;
   for (int eng : engines)
     for (int bps : {0, 2, 1}) {
@@ -207,7 +205,7 @@ extern "C" int stomsfem_plan_set_choice(stomsfem_plan* p, int32_t blocks_per_sm,
       engine > STOMSFEM_ENGINE_TC2)
     return set_error(STOMSFEM_EINVAL, "bad launch choice (%d, %d, %d)", blocks_per_sm, split_fp32, engine);
   if (engine != STOMSFEM_ENGINE_AUTO && engine != STOMSFEM_ENGINE_BLOCKED &&
-      upscale_engine_of(&p->grid, p->max_o, p->precision, STOMSFEM_ENGINE_AUTO) == STOMSFEM_ENGINE_BLOCKED)
+      !upscale_tc_ok(&p->grid, p->max_o, p->precision))
     return set_error(STOMSFEM_EINVAL, "the tensor-core engines need an FP32 form, 4 <= nf/nc and a half bandwidth <= 40");
   p->blocks_per_sm = blocks_per_sm;
   p->split = split_fp32;

@@ -50,7 +50,13 @@ __device__ __constant__ double kKref[4][4] = {{4.0 / 6, -1.0 / 6, -2.0 / 6, -1.0
 struct PodDims {
   int nf, nc, rho, N2, n, ne, P0, P, Ppad, ncell;
   double f;
+  int per_l;  // 1: one basis per basis function l = 1..3 (columns 4 + l * rcl ..), else one shared basis
+  int rcl;    // per-l: the column block of each basis (its rank cap)
 };
+
+// Number of reduced unknowns a solve lane set spans: r (shared basis) or
+// 3 blocks of rcl (per-l bases).
+__host__ __device__ inline int pod_vcols(const PodDims& d) { return d.P0 - 4; }
 
 // ------------------------------------------------------------------ offline
 
@@ -101,7 +107,42 @@ __global__ void pod_cov_kernel(PodDims d, const double* __restrict__ phi, int Ns
   }
 }
 
-// One CTA per cell: energy metric, KL eigenproblem, rank, basis.
+// Per-l bases: covariance of the centred interior snapshots of phi_l alone,
+// cov[cell][l][n][n] for l = 0..2 (blockIdx.y = l).
+__global__ void pod_cov_per_l_kernel(PodDims d, const double* __restrict__ phi, int Ns,
+                                     const double* __restrict__ phibar, double* __restrict__ cov) {
+  const int cell = blockIdx.x, l = blockIdx.y;
+  const int n = d.n;
+  const double* pb = phibar + (size_t)cell * 4 * d.N2 + (size_t)l * d.N2;
+  double* C = cov + ((size_t)cell * 3 + l) * n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    if (j < i) continue;
+    const int vi = inner_node(i, d.rho), vj = inner_node(j, d.rho);
+    double s = 0.0;
+    for (int t = 0; t < Ns; ++t) {
+      const double* ph = phi + ((size_t)t * d.ncell + cell) * 4 * d.N2 + (size_t)l * d.N2;
+      s += (ph[vi] - pb[vi]) * (ph[vj] - pb[vj]);
+    }
+    s /= (double)Ns;
+    C[i * n + j] = s;
+    C[j * n + i] = s;
+  }
+}
+
+// W[cell][N2][P0] = [phibar_1..4, 0 ...] (the per-l eigen blocks then write
+// their own columns).
+__global__ void pod_w_init_kernel(PodDims d, const double* __restrict__ phibar, double* __restrict__ W) {
+  const int cell = blockIdx.x;
+  double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  for (int idx = threadIdx.x; idx < d.N2 * d.P0; idx += blockDim.x) {
+    const int node = idx / d.P0, col = idx % d.P0;
+    Wc[idx] = col < 4 ? phibar[(size_t)cell * 4 * d.N2 + col * d.N2 + node] : 0.0;
+  }
+}
+
+// One CTA per cell (and, per-l, per basis function blockIdx.y): energy
+// metric, KL eigenproblem, rank, basis.
 //   W [cell][N2][P0]: columns 0..3 = phibar_l, 4..4+r-1 = zeta_q (0 on the
 //   boundary), the rest 0.  lam [cell][n] eigenvalues, descending.
 __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
@@ -109,6 +150,11 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
                                double tol, int max_rank, const int32_t* __restrict__ ranks_in,
                                double* __restrict__ W, double* __restrict__ lam_out,
                                int32_t* __restrict__ ranks_out, int32_t* __restrict__ err) {
+  // per-l: problem (cell, l) = rank / eigenvalue slot cell * 3 + l, basis
+  // columns from 4 + l * rcl; shared: slot cell, columns from 4
+  const int l_blk = d.per_l ? (int)blockIdx.y : 0;
+  const int slot_id = d.per_l ? (int)blockIdx.x * 3 + l_blk : (int)blockIdx.x;
+  const int col0 = 4 + l_blk * (d.per_l ? d.rcl : 0);
   extern __shared__ double eig_smem[];  // three (kPodMaxN+1)^2 matrices
   typedef double Mat[kPodMaxN + 1];
   Mat* R = reinterpret_cast<Mat*>(eig_smem);
@@ -164,7 +210,7 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
   }
   __syncthreads();
   // --- B = R^T C R: Z = C R, then B = R^T Z
-  const double* C = cov + (size_t)cell * n * n;
+  const double* C = cov + (size_t)slot_id * n * n;
   for (int idx = tid; idx < ne2 * ne2; idx += nt) {
     const int i = idx / ne2, j = idx % ne2;
     double s = 0.0;
@@ -249,7 +295,7 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
   if (tid == 0) {
     int r;
     if (ranks_in) {
-      r = ranks_in[cell];
+      r = ranks_in[slot_id];
     } else {
       const double l1 = B[order[0]][order[0]] > 0 ? B[order[0]][order[0]] : 1.0;
       r = 0;
@@ -259,25 +305,27 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
     if (r < 1) r = 1;
     if (r > n) r = n;
     s_rank = r;
-    ranks_out[cell] = r;
+    ranks_out[slot_id] = r;
   }
-  for (int i = tid; i < n; i += nt) lam_out[(size_t)cell * n + i] = B[order[i]][order[i]];
+  for (int i = tid; i < n; i += nt) lam_out[(size_t)slot_id * n + i] = B[order[i]][order[i]];
   __syncthreads();
   const int r = s_rank;
   // --- zeta_q = R^{-T} w_q (back substitution with the upper factor R^T)
   double* Wc = W + (size_t)cell * d.N2 * d.P0;
-  for (int idx = tid; idx < d.N2 * d.P0; idx += nt) {
-    const int node = idx / d.P0, col = idx % d.P0;
-    Wc[idx] = col < 4 ? phibar[(size_t)cell * 4 * d.N2 + col * d.N2 + node] : 0.0;
+  if (!d.per_l) {  // per-l: pod_w_init_kernel wrote phibar and the zeros
+    for (int idx = tid; idx < d.N2 * d.P0; idx += nt) {
+      const int node = idx / d.P0, col = idx % d.P0;
+      Wc[idx] = col < 4 ? phibar[(size_t)cell * 4 * d.N2 + col * d.N2 + node] : 0.0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int q = tid; q < r; q += nt) {
     const int src = order[q];
-    // x = R^{-T} w: solve R^T x = w from the last row up; x stored in B's spare column space
+    // x = R^{-T} w: solve R^T x = w from the last row up
     for (int i = n - 1; i >= 0; --i) {
       double s = Z[i][src];
-      for (int k = i + 1; k < n; ++k) s -= R[k][i] * Wc[(size_t)inner_node(k, rho) * d.P0 + 4 + q];
-      Wc[(size_t)inner_node(i, rho) * d.P0 + 4 + q] = s / R[i][i];
+      for (int k = i + 1; k < n; ++k) s -= R[k][i] * Wc[(size_t)inner_node(k, rho) * d.P0 + col0 + q];
+      Wc[(size_t)inner_node(i, rho) * d.P0 + col0 + q] = s / R[i][i];
     }
   }
 }
@@ -576,8 +624,9 @@ constexpr int kPodSolveWarps = 4;
 constexpr int kPodN2Max = (kPodMaxRho + 1) * (kPodMaxRho + 1);
 
 // REFINE: the FP64 stencil refinement of c (refine_iters > 0) is compiled
-// into its own kernel, so the unrefined launch carries only its own code.
-template <bool REFINE>
+// into its own kernel, so the unrefined launch carries only its own code;
+// PER_L: the handle has one basis per basis function (PodDims::per_l).
+template <bool REFINE, bool PER_L>
 __global__ void __launch_bounds__(kPodSolveWarps * 32)
 pod_solve_kernel(PodSolveArgs A) {
   __shared__ double s_c[kPodSolveWarps][32][4];
@@ -586,6 +635,7 @@ pod_solve_kernel(PodSolveArgs A) {
   __shared__ float s_g[kPodSolveWarps][512];
   __shared__ float s_coef[kPodSolveWarps][kPodAffParts];
   __shared__ __align__(16) float s_w[kPodSolveWarps][40];
+  __shared__ float s_cf[kPodSolveWarps][32][4];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const PodDims& d = A.d;
   const long long units = (long long)A.S * d.ncell;
@@ -603,7 +653,22 @@ pod_solve_kernel(PodSolveArgs A) {
       if (lane == 0 && A.status) A.status[u] = STOMSFEM_ETIMEOUT;
       continue;
     }
-    const int r = A.ranks[cell];
+    // reduced unknowns: the shared basis's r, or the per-l blocks of rcl
+    // columns (ranks rl[0..2]; the columns past a block's rank are zero)
+    int r, rl0 = 0, rl1 = 0, rl2 = 0;
+    if (PER_L) {
+      rl0 = A.ranks[cell * 3];
+      rl1 = A.ranks[cell * 3 + 1];
+      rl2 = A.ranks[cell * 3 + 2];
+      r = 3 * d.rcl;
+    } else {
+      r = A.ranks[cell];
+    }
+    auto vact = [&](int q) {  // reduced unknown q is a basis vector
+      if (!PER_L) return q < r;
+      const int b = q / d.rcl;
+      return b < 3 && q - b * d.rcl < (b == 0 ? rl0 : (b == 1 ? rl1 : rl2));
+    };
     const float* g;
     if (A.Gaff) {
       // Eq. localAF: W^T A(xi) W = gain G_0 + scale sum_k xi_k G_k, the
@@ -631,16 +696,27 @@ pod_solve_kernel(PodSolveArgs A) {
     } else {
       g = A.G + ((size_t)cell * A.Spad + s) * d.Ppad;
     }
-    // row q of V^T A V and right-hand sides -V^T A phibar_l
+    // row q of V^T A V and right-hand sides -V^T A phibar_l; per-l bases:
+    // the block-diagonal system of the three (V_l^T A V_l) c_l =
+    // -V_l^T A phibar_l, identity rows past each block's rank, and no
+    // fourth right-hand side (phi_4 = 1 - sum, the partition of unity)
+    const bool qa = vact(lane);
+    const int qb = PER_L ? lane / d.rcl : 0;
     float Mq[32], Fq[4];
 #pragma unroll
     for (int p = 0; p < 32; ++p) {
       float v = 0.f;
-      if (lane < r && p < r) v = g[pidx(4 + min(lane, p), 4 + max(lane, p), P0)];
+      if (lane < r && p < r) {
+        if (qa && vact(p) && (!PER_L || p / d.rcl == qb))
+          v = g[pidx(4 + min(lane, p), 4 + max(lane, p), P0)];
+        else if (p == lane && !qa)
+          v = 1.f;
+      }
       Mq[p] = v;
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) Fq[l] = (lane < r) ? -g[pidx(l, 4 + lane, P0)] : 0.f;
+    for (int l = 0; l < 4; ++l)
+      Fq[l] = (lane < r && qa && (!PER_L || l == qb)) ? -g[pidx(l, 4 + lane, P0)] : 0.f;
     bool bad = false;
     small_chol<0>(Mq, Fq, lane, r, bad, s_w[wib]);
     small_bwd<31>(Mq, Fq, lane, r, s_w[wib]);
@@ -649,6 +725,60 @@ pod_solve_kernel(PodSolveArgs A) {
     using TOut = typename std::conditional<REFINE, double, float>::type;
     TOut Kv[10], bv[4];
     if constexpr (!REFINE) {
+      if (PER_L) {
+        // S[l][l'] = x_l^T G x_l' with x_l = e_l + c_l (c_l in block l), l,
+        // l' < 3; row / column 4 from the zero row sums (phi_4 = 1 - sum and
+        // A 1 = 0); b_l = wl^T x_l, b_4 = f H^2 - sum.  FP32, like the solve.
+#pragma unroll
+        for (int l = 0; l < 4; ++l) s_cf[wib][lane][l] = lane < r ? Fq[l] : 0.f;
+        __syncwarp();
+        float gx[3];  // (G x_l')[alpha], alpha = lane < P0
+#pragma unroll
+        for (int lp = 0; lp < 3; ++lp) {
+          float t = 0.f;
+          if (lane < P0) {
+            t = g[pidx(min(lane, lp), max(lane, lp), P0)];
+            for (int q = 0; q < r; ++q) t = fmaf(g[pidx(min(lane, 4 + q), max(lane, 4 + q), P0)], s_cf[wib][q][lp], t);
+          }
+          gx[lp] = t;
+        }
+        float S3[3][3];
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+          for (int lp = 0; lp < 3; ++lp) {
+            const float t = (lane >= 4 && lane < 4 + r) ? s_cf[wib][lane - 4][l] * gx[lp] : 0.f;
+            S3[l][lp] = __shfl_sync(0xffffffffu, gx[lp], l) + warp_sum(t);
+          }
+        float Sf[4][4];
+        float tot = 0.f;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          float rs = 0.f;
+#pragma unroll
+          for (int lp = 0; lp < 3; ++lp) {
+            Sf[l][lp] = 0.5f * (S3[l][lp] + S3[lp][l]);
+            rs += Sf[l][lp];
+          }
+          Sf[l][3] = -rs;
+          tot += rs;
+        }
+        Sf[3][3] = tot;
+        int q = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+          for (int lp = l; lp < 4; ++lp) Kv[q++] = Sf[l][lp];
+        const float wv = (lane < r) ? (float)wl[4 + lane] : 0.f;
+        const double fH2 = d.f / ((double)d.nc * (double)d.nc);
+        double bsum = 0.0;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          bv[l] = (float)wl[l] + warp_sum(wv * Fq[l]);
+          bsum += (double)bv[l];
+        }
+        bv[3] = (float)(fH2 - bsum);
+      } else {
       // K = G_pp + G_pV c ; b = wl_p + wl_V c, in FP32 like the reduced
       // solve itself (the warp-wide FP64 sums cost the narrow FP64 pipe
       // more than the solve); converted to FP64 once, at the store
@@ -664,6 +794,7 @@ pod_solve_kernel(PodSolveArgs A) {
       const float wv = (lane < r) ? (float)wl[4 + lane] : 0.f;
 #pragma unroll
       for (int l = 0; l < 4; ++l) bv[l] = (float)wl[l] + warp_sum(wv * Fq[l]);
+      }
     } else {
       // FP64 refinement of c through the fine stencil of A(omega)
       const int cx = cell % d.nc, cy = cell / d.nc;
@@ -686,6 +817,7 @@ pod_solve_kernel(PodSolveArgs A) {
 #pragma unroll
             for (int l = 0; l < 4; ++l) t[l] += vq * s_c[wib][q][l];
           }
+          if (PER_L) t[3] = 1.0 - t[0] - t[1] - t[2];  // the partition of unity
 #pragma unroll
           for (int l = 0; l < 4; ++l) s_u[wib][v][l] = t[l];
         }
@@ -726,6 +858,11 @@ pod_solve_kernel(PodSolveArgs A) {
           }
 #pragma unroll
           for (int l = 0; l < 4; ++l) Rq[l] = (float)(-t[l]);
+          if (PER_L) {  // each block's residual is its own basis function's
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+              if (l != qb || !qa) Rq[l] = 0.f;
+          }
         }
         small_fwd<0>(Mq, Rq, lane, r, s_w[wib]);
         small_bwd<31>(Mq, Rq, lane, r, s_w[wib]);
@@ -764,6 +901,7 @@ pod_solve_kernel(PodSolveArgs A) {
         const double t = warp_sum((lane < r) ? wl[4 + lane] * s_c[wib][lane][l] : 0.0);
         bv[l] = wl[l] + t;
       }
+      if (PER_L) bv[3] = d.f / ((double)d.nc * (double)d.nc) - bv[0] - bv[1] - bv[2];
     }
     const bool fail = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
@@ -811,18 +949,21 @@ static void pod_free(stomsfem_pod* p) {
   delete p;
 }
 
-extern "C" int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap,
-                                  const double* a_train, int32_t S_train, double tol,
-                                  int32_t max_rank, const int32_t* ranks_in, stomsfem_pod** out,
-                                  int32_t* ranks_out, stomsfem_stream_t stream) {
+// The offline stage, one shared basis per cell (per_l = 0: ranks [ncell])
+// or one basis per basis function l = 1..3 (per_l = 1: ranks [ncell][3],
+// max_rank per basis).
+static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                          int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
+                          stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream, int per_l) {
   if (!grid || !out || grid->nf <= 0 || grid->nc <= 0 || grid->nf % grid->nc)
     return set_error(STOMSFEM_EINVAL, "bad grid / out");
   const int rho = grid->nf / grid->nc;
   if (rho < 2 || rho > kPodMaxRho)
     return set_error(STOMSFEM_EINVAL, "POD needs 2 <= H/h <= %d (got %d)", kPodMaxRho, rho);
   if (S_train < 1 || !phi_snap || !a_train) return set_error(STOMSFEM_EINVAL, "no training data");
-  if (max_rank < 1 || max_rank > kPodMaxRank)
-    return set_error(STOMSFEM_EINVAL, "max_rank must be in [1, %d]", kPodMaxRank);
+  const int rank_cap = per_l ? kPodMaxRank / 3 : kPodMaxRank;
+  if (max_rank < 1 || max_rank > rank_cap)
+    return set_error(STOMSFEM_EINVAL, "max_rank must be in [1, %d]", rank_cap);
   if (!(tol > 0.0) && !ranks_in) return set_error(STOMSFEM_EINVAL, "tol must be > 0");
   *out = nullptr;
   stomsfem_pod* p = new stomsfem_pod();
@@ -836,7 +977,10 @@ extern "C" int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_s
   d.ncell = grid->nc * grid->nc;
   d.f = grid->f;
   const int rcap = max_rank < d.n ? max_rank : d.n;
-  d.P0 = 4 + rcap;
+  const int nslot = per_l ? 3 : 1;  // eigenproblems per cell
+  d.per_l = per_l;
+  d.rcl = per_l ? rcap : 0;
+  d.P0 = 4 + nslot * rcap;
   d.P = d.P0 * (d.P0 + 1) / 2;
   d.Ppad = (d.P + 15) & ~15;
   p->max_rank = rcap;
@@ -857,40 +1001,59 @@ extern "C" int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_s
     return fail(rc);
   TRY(cudaMalloc(&p->W, sizeof(double) * d.ncell * d.N2 * d.P0));
   TRY(cudaMalloc(&p->wl, sizeof(double) * d.ncell * d.P0));
-  TRY(cudaMalloc(&p->lam, sizeof(double) * d.ncell * d.n));
+  TRY(cudaMalloc(&p->lam, sizeof(double) * d.ncell * nslot * d.n));
   TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * kPodK));
-  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell));
+  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell * nslot));
   TRY(cudaMalloc(&p->err, sizeof(int32_t)));
   TRY(cudaMalloc(&phibar, sizeof(double) * d.ncell * 4 * d.N2));
   TRY(cudaMalloc(&abar, sizeof(double) * d.ncell * d.ne));
-  TRY(cudaMalloc(&cov, sizeof(double) * d.ncell * d.n * d.n));
+  TRY(cudaMalloc(&cov, sizeof(double) * d.ncell * nslot * d.n * d.n));
   TRY(cudaMemsetAsync(p->err, 0, sizeof(int32_t), st));
   if (ranks_in) {
-    TRY(cudaMalloc(&rin_d, sizeof(int32_t) * d.ncell));
-    TRY(cudaMemcpyAsync(rin_d, ranks_in, sizeof(int32_t) * d.ncell, cudaMemcpyHostToDevice, st));
+    TRY(cudaMalloc(&rin_d, sizeof(int32_t) * d.ncell * nslot));
+    TRY(cudaMemcpyAsync(rin_d, ranks_in, sizeof(int32_t) * d.ncell * nslot, cudaMemcpyHostToDevice, st));
   }
   pod_mean_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, a_train, S_train, phibar, abar);
-  pod_cov_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
+  if (per_l) {
+    pod_cov_per_l_kernel<<<dim3(d.ncell, 3), 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
+    pod_w_init_kernel<<<d.ncell, 256, 0, st>>>(d, phibar, p->W);
+  } else {
+    pod_cov_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
+  }
   const size_t eig_smem = sizeof(double) * 3 * (kPodMaxN + 1) * (kPodMaxN + 1);
   TRY(cudaFuncSetAttribute(pod_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem));
-  pod_eig_kernel<<<d.ncell, 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W, p->lam,
-                                          p->ranks, p->err);
+  pod_eig_kernel<<<dim3(d.ncell, nslot), 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W, p->lam,
+                                                               p->ranks, p->err);
   pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->wl);
   TRY(cudaGetLastError());
   int32_t herr = 0;
   TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  std::vector<int32_t> rk(d.ncell);
-  TRY(cudaMemcpyAsync(rk.data(), p->ranks, sizeof(int32_t) * d.ncell, cudaMemcpyDeviceToHost, st));
+  std::vector<int32_t> rk(d.ncell * nslot);
+  TRY(cudaMemcpyAsync(rk.data(), p->ranks, sizeof(int32_t) * d.ncell * nslot, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
 #undef TRY
   if (herr != 0) return fail(set_error(STOMSFEM_ENOTSPD, "training-mean energy matrix not positive definite"));
-  if (ranks_out) std::memcpy(ranks_out, rk.data(), sizeof(int32_t) * d.ncell);
+  if (ranks_out) std::memcpy(ranks_out, rk.data(), sizeof(int32_t) * d.ncell * nslot);
   cudaFree(rin_d);
   cudaFree(phibar);
   cudaFree(abar);
   cudaFree(cov);
   *out = p;
   return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap,
+                                  const double* a_train, int32_t S_train, double tol,
+                                  int32_t max_rank, const int32_t* ranks_in, stomsfem_pod** out,
+                                  int32_t* ranks_out, stomsfem_stream_t stream) {
+  return pod_build_impl(grid, phi_snap, a_train, S_train, tol, max_rank, ranks_in, out, ranks_out, stream, 0);
+}
+
+extern "C" int stomsfem_pod_build_per_l(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
+                                        int32_t S_train, double tol, int32_t max_rank_per_l,
+                                        const int32_t* ranks_in, stomsfem_pod** out, int32_t* ranks_out,
+                                        stomsfem_stream_t stream) {
+  return pod_build_impl(grid, phi_snap, a_train, S_train, tol, max_rank_per_l, ranks_in, out, ranks_out, stream, 1);
 }
 
 extern "C" int stomsfem_pod_destroy(stomsfem_pod* pod) {
@@ -900,17 +1063,21 @@ extern "C" int stomsfem_pod_destroy(stomsfem_pod* pod) {
 
 extern "C" int stomsfem_pod_eigenvalues(const stomsfem_pod* pod, double* lam_host) {
   if (!pod || !lam_host) return set_error(STOMSFEM_EINVAL, "NULL argument");
-  STOMSFEM_TRY_CUDA(cudaMemcpy(lam_host, pod->lam, sizeof(double) * pod->d.ncell * pod->d.n,
+  STOMSFEM_TRY_CUDA(cudaMemcpy(lam_host, pod->lam,
+                               sizeof(double) * pod->d.ncell * (pod->d.per_l ? 3 : 1) * pod->d.n,
                                cudaMemcpyDeviceToHost));
   return STOMSFEM_OK;
 }
 
 static const char kPodMagic[8] = {'S', 'T', 'M', 'F', 'P', 'O', 'D', '1'};
+static const char kPodMagicPerL[8] = {'S', 'T', 'M', 'F', 'P', 'O', 'D', 'L'};  // per-l bases
 
 extern "C" int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t buf_bytes, size_t* bytes) {
   if (!pod || !bytes) return set_error(STOMSFEM_EINVAL, "NULL pod / bytes");
   const PodDims& d = pod->d;
-  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0, nlam = (size_t)d.ncell * d.n;
+  const int nslot = d.per_l ? 3 : 1;
+  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0,
+               nlam = (size_t)d.ncell * nslot * d.n;
   const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
   std::vector<double> W, wl, lam;
   std::vector<__nv_bfloat16> T;
@@ -920,15 +1087,15 @@ extern "C" int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t
     wl.resize(nwl);
     lam.resize(nlam);
     T.resize(nT);
-    rk.resize(d.ncell);
+    rk.resize((size_t)d.ncell * nslot);
     STOMSFEM_TRY_CUDA(cudaMemcpy(W.data(), pod->W, sizeof(double) * nW, cudaMemcpyDeviceToHost));
     STOMSFEM_TRY_CUDA(cudaMemcpy(wl.data(), pod->wl, sizeof(double) * nwl, cudaMemcpyDeviceToHost));
     STOMSFEM_TRY_CUDA(cudaMemcpy(lam.data(), pod->lam, sizeof(double) * nlam, cudaMemcpyDeviceToHost));
     STOMSFEM_TRY_CUDA(cudaMemcpy(T.data(), pod->T, sizeof(__nv_bfloat16) * nT, cudaMemcpyDeviceToHost));
-    STOMSFEM_TRY_CUDA(cudaMemcpy(rk.data(), pod->ranks, sizeof(int32_t) * d.ncell, cudaMemcpyDeviceToHost));
+    STOMSFEM_TRY_CUDA(cudaMemcpy(rk.data(), pod->ranks, sizeof(int32_t) * d.ncell * nslot, cudaMemcpyDeviceToHost));
   }
   CkptWriter w(host_buf, buf_bytes);
-  ckpt_header(w, kPodMagic);
+  ckpt_header(w, d.per_l ? kPodMagicPerL : kPodMagic);
   const int32_t dims[11] = {d.nf, d.nc, d.rho, d.N2, d.n, d.ne, d.P0, d.P, d.Ppad, d.ncell, pod->max_rank};
   w.put(dims, sizeof(dims));
   w.val<double>(d.f);
@@ -936,7 +1103,7 @@ extern "C" int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t
   w.put(host_buf ? (const void*)wl.data() : nullptr, sizeof(double) * nwl);
   w.put(host_buf ? (const void*)lam.data() : nullptr, sizeof(double) * nlam);
   w.put(host_buf ? (const void*)T.data() : nullptr, sizeof(__nv_bfloat16) * nT);
-  w.put(host_buf ? (const void*)rk.data() : nullptr, sizeof(int32_t) * d.ncell);
+  w.put(host_buf ? (const void*)rk.data() : nullptr, sizeof(int32_t) * d.ncell * nslot);
   *bytes = w.pos;
   if (host_buf && !w.fits()) return set_error(STOMSFEM_ENOMEM, "checkpoint buffer %zu < %zu bytes", buf_bytes, w.pos);
   return STOMSFEM_OK;
@@ -946,9 +1113,16 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   if (!host_buf || !out) return set_error(STOMSFEM_EINVAL, "NULL buffer / out");
   *out = nullptr;
   CkptReader r(host_buf, buf_bytes);
-  const int hc = ckpt_check_header(r, kPodMagic);
+  int hc = ckpt_check_header(r, kPodMagic);
+  int per_l = 0;
+  if (hc == 1) {  // the per-l kind?
+    r = CkptReader(host_buf, buf_bytes);
+    hc = ckpt_check_header(r, kPodMagicPerL);
+    per_l = 1;
+  }
   if (hc == 1) return set_error(STOMSFEM_EVERSION, "not a version-%u POD checkpoint", kCkptVersion);
   if (hc == 2) return set_error(STOMSFEM_EINVAL, "truncated POD checkpoint");
+  const int nslot = per_l ? 3 : 1;
   int32_t dims[11];
   r.get(dims, sizeof(dims));
   PodDims d;
@@ -964,17 +1138,21 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   d.ncell = dims[9];
   d.f = r.val<double>();
   const int rcap = dims[10];
+  d.per_l = per_l;
+  d.rcl = per_l ? rcap : 0;
   // the stored sizes must be the ones the build derives from the grid
   const bool consistent = r.ok && d.nc > 0 && d.nf % d.nc == 0 && d.rho == d.nf / d.nc && d.rho >= 2 &&
                           d.rho <= kPodMaxRho && d.N2 == (d.rho + 1) * (d.rho + 1) &&
                           d.n == (d.rho - 1) * (d.rho - 1) && d.ne == d.rho * d.rho && d.ncell == d.nc * d.nc &&
-                          rcap >= 1 && rcap <= d.n && d.P0 == 4 + rcap && d.P == d.P0 * (d.P0 + 1) / 2 &&
+                          rcap >= 1 && rcap <= d.n && rcap * nslot <= kPodMaxRank && d.P0 == 4 + nslot * rcap &&
+                          d.P == d.P0 * (d.P0 + 1) / 2 &&
                           d.Ppad == ((d.P + 15) & ~15);
   if (!consistent) return set_error(STOMSFEM_EINVAL, "inconsistent POD checkpoint header");
-  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0, nlam = (size_t)d.ncell * d.n;
+  const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0,
+               nlam = (size_t)d.ncell * nslot * d.n;
   const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
   const size_t need = r.pos + sizeof(double) * (nW + nwl + nlam) + sizeof(__nv_bfloat16) * nT +
-                      sizeof(int32_t) * d.ncell;
+                      sizeof(int32_t) * d.ncell * nslot;
   if (buf_bytes < need) return set_error(STOMSFEM_EINVAL, "truncated POD checkpoint (%zu < %zu)", buf_bytes, need);
   const unsigned char* base = static_cast<const unsigned char*>(host_buf) + r.pos;
   auto* p = new stomsfem_pod();
@@ -990,7 +1168,7 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   TRY(cudaMalloc(&p->wl, sizeof(double) * nwl));
   TRY(cudaMalloc(&p->lam, sizeof(double) * nlam));
   TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * nT));
-  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell));
+  TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell * nslot));
   TRY(cudaMalloc(&p->err, sizeof(int32_t)));
   TRY(cudaMemcpy(p->W, base, sizeof(double) * nW, cudaMemcpyHostToDevice));
   base += sizeof(double) * nW;
@@ -1000,14 +1178,14 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   base += sizeof(double) * nlam;
   TRY(cudaMemcpy(p->T, base, sizeof(__nv_bfloat16) * nT, cudaMemcpyHostToDevice));
   base += sizeof(__nv_bfloat16) * nT;
-  std::vector<int32_t> rk(d.ncell);
-  std::memcpy(rk.data(), base, sizeof(int32_t) * d.ncell);
-  for (int c = 0; c < d.ncell; ++c)
+  std::vector<int32_t> rk((size_t)d.ncell * nslot);
+  std::memcpy(rk.data(), base, sizeof(int32_t) * d.ncell * nslot);
+  for (int c = 0; c < d.ncell * nslot; ++c)
     if (rk[c] < 0 || rk[c] > rcap) {
       pod_free(p);
-      return set_error(STOMSFEM_EINVAL, "POD checkpoint: rank %d of cell %d outside [0, %d]", rk[c], c, rcap);
+      return set_error(STOMSFEM_EINVAL, "POD checkpoint: rank %d of slot %d outside [0, %d]", rk[c], c, rcap);
     }
-  TRY(cudaMemcpy(p->ranks, rk.data(), sizeof(int32_t) * d.ncell, cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(p->ranks, rk.data(), sizeof(int32_t) * d.ncell * nslot, cudaMemcpyHostToDevice));
   TRY(cudaMemset(p->err, 0, sizeof(int32_t)));
 #undef TRY
   *out = p;
@@ -1077,7 +1255,8 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
   long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
   if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
   {
-    auto kern = A.refine > 0 ? pod_solve_kernel<true> : pod_solve_kernel<false>;
+    auto kern = A.refine > 0 ? (d.per_l ? pod_solve_kernel<true, true> : pod_solve_kernel<true, false>)
+                             : (d.per_l ? pod_solve_kernel<false, true> : pod_solve_kernel<false, false>);
     kern<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
   }
   STOMSFEM_TRY_CUDA(cudaGetLastError());
@@ -1187,7 +1366,8 @@ extern "C" int stomsfem_pod_upscale_affine(stomsfem_pod* pod, const double* xi, 
   long long blocks = (units + kPodSolveWarps - 1) / kPodSolveWarps;
   if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
   {
-    auto kern = A.refine > 0 ? pod_solve_kernel<true> : pod_solve_kernel<false>;
+    auto kern = A.refine > 0 ? (d.per_l ? pod_solve_kernel<true, true> : pod_solve_kernel<true, false>)
+                             : (d.per_l ? pod_solve_kernel<false, true> : pod_solve_kernel<false, false>);
     kern<<<(unsigned)blocks, kPodSolveWarps * 32, 0, st>>>(A);
   }
   STOMSFEM_TRY_CUDA(cudaGetLastError());

@@ -94,6 +94,12 @@ int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int pre
   return upscale_engine(requested, precision, grid->nf / grid->nc, bmax);
 }
 
+bool upscale_tc_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision) {
+  int nmax, bmax;
+  patch_limits(grid, max_oversample, &nmax, &bmax);
+  return upscale_tc_eligible(precision, grid->nf / grid->nc, bmax);
+}
+
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
   int nmax, bmax;
   patch_limits(grid, 0, &nmax, &bmax);

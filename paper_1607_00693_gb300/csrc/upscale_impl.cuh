@@ -910,10 +910,9 @@ static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(i
 constexpr int group_lanes(int) { return 16; }
 
 // Factorisation engines of the FP32 forms: the tensor-core factorisation of
-// band_tc.cuh with operands in three TF32 parts (exact; the default when
-// every patch has a half bandwidth in [4, 40]) or two parts (about 2^-21 per
-// product, faster), or the two-units-per-warp FMA factorisation of
-// band_block.cuh (any bandwidth).
+// band_tc.cuh with operands in three TF32 parts (exact) or two parts (about
+// 2^-21 per product), for patches with a half bandwidth in [4, 40], or the
+// two-units-per-warp FMA factorisation of band_block.cuh (any bandwidth).
 enum {
   kEngineAuto = STOMSFEM_ENGINE_AUTO,
   kEngineBlocked = STOMSFEM_ENGINE_BLOCKED,
@@ -921,12 +920,15 @@ enum {
   kEngineTc2 = STOMSFEM_ENGINE_TC2
 };
 
+// The engine AUTO resolves to where the tensor-core engines are eligible.
+constexpr int kEngineDefault = kEngineBlocked;
+
 static bool upscale_tc_eligible(int precision, int rho, int bmax) {
   return precision != STOMSFEM_FP64 && rho >= 4 && bmax <= kTcBMax;
 }
 static int upscale_engine(int requested, int precision, int rho, int bmax) {
   if (precision == STOMSFEM_FP64 || !upscale_tc_eligible(precision, rho, bmax)) return kEngineBlocked;
-  return requested == kEngineAuto ? kEngineTc3 : requested;
+  return requested == kEngineAuto ? kEngineDefault : requested;
 }
 static bool upscale_uses_tc(int precision, int rho, int bmax) {
   return upscale_engine(kEngineAuto, precision, rho, bmax) != kEngineBlocked;
