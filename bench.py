@@ -441,6 +441,75 @@ def bench_two_level(api, dev, stream, n0=10000, n1=256):
             "two_level_vs_plain_mean_rel": diff}
 
 
+def bench_two_level_1024(api, dev, stream, ov, n0=512, n1=16):
+    """Two-level Monte Carlo (Eq. MCmean2level) on the H/h = 32 workload's
+    1024^2 / 32^2 grids: level 0, n0 samples through the FP32 upscaler (with
+    its oversampling) and the coarse solve; level 1, n1 independent samples
+    with the fine Q1 FEM (multigrid-preconditioned CG on the GPU) and their
+    coarse solutions; against plain Monte Carlo with the same n1 fine solves."""
+    import torch
+    w = W.workload("upscale_1024")
+    nf, nc = w["nf"], w["nc"]
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    nn = (nc + 1) ** 2
+    ov_t = torch.from_numpy(ov).to(dev)
+    mo = int(ov.max())
+
+    def mom():
+        return [torch.zeros(nn, dtype=torch.float64, device=dev), torch.zeros(nn, dtype=torch.float64, device=dev),
+                torch.zeros(1, dtype=torch.float64, device=dev)]
+
+    _, rb = api.stomsfem_upscale_workspace_size(g, mo, api.FP32)
+    wsu = torch.empty(rb, dtype=torch.uint8, device=dev)
+
+    def coarse(xi, S, m, a=None):
+        if a is None:
+            a = torch.empty((S, nf, nf), dtype=torch.float64, device=dev)
+            api.stomsfem_sample_coef_precision(g, fld, xi, a, precision=api.FP32, stream=stream)
+        Ke = torch.empty((S, nc * nc, 10), dtype=torch.float64, device=dev)
+        be = torch.empty((S, nc * nc, 4), dtype=torch.float64, device=dev)
+        u = torch.empty((S, nn), dtype=torch.float64, device=dev)
+        api.stomsfem_upscale(g, a, Ke, be, oversample=ov_t, max_oversample=mo, precision=api.FP32,
+                             workspace=wsu, stream=stream)
+        api.stomsfem_coarse_solve(g, Ke, be, u, *m, stream=stream)
+        return u
+
+    x0 = torch.from_numpy(W.draw_xi(w["field"], n0, 601)).to(dev)
+    x1 = torch.from_numpy(W.draw_xi(w["field"], n1, 602)).to(dev)
+    a1 = torch.empty((n1, nf, nf), dtype=torch.float64, device=dev)
+    uh = torch.empty((n1, (nf + 1) ** 2), dtype=torch.float64, device=dev)
+    wsf = torch.empty(api.stomsfem_fine_fem_workspace_size(g, n1), dtype=torch.uint8, device=dev)
+    d = torch.empty((n1, nn), dtype=torch.float64, device=dev)
+    uhc = torch.empty((n1, nn), dtype=torch.float64, device=dev)
+    m0, m1, mp = mom(), mom(), mom()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        coarse(x0, n0, m0)
+        e[1].record(stream)
+        api.stomsfem_sample_coef(g, fld, x1, a1, stream=stream)
+        e[2].record(stream)
+        api.stomsfem_fine_fem(g, a1, uh, workspace=wsf, stream=stream)
+        e[3].record(stream)
+        uH1 = coarse(x1, n1, [None, None, None], a=a1)
+        api.stomsfem_restrict_to_coarse(g, uh, d, u_coarse=uH1, stream=stream)
+        api.stomsfem_mc_moments(d, *m1, stream=stream)
+        api.stomsfem_restrict_to_coarse(g, uh, uhc, stream=stream)
+        api.stomsfem_mc_moments(uhc, *mp, stream=stream)
+    stream.synchronize()
+    sd2 = float(((m0[1] / n0 / n0) + (m1[1] / n1 / n1)).mean().sqrt().item())
+    sdp = float((mp[1] / n1 / n1).mean().sqrt().item())
+    fine_ms = e[2].elapsed_time(e[3])
+    return {"workload": "upscale_1024 grids (1024^2 fine, 32^2 coarse), level 0 by the FP32 upscaler",
+            "n0_coarse": n0, "n1_fine": n1, "level0_ms": e[0].elapsed_time(e[1]),
+            "fine_fem_ms": fine_ms, "fine_fem_samples_per_s": n1 / (fine_ms / 1e3),
+            "fine_fem_method": "CG (FP64) with a multigrid V-cycle (FP32) preconditioner",
+            "sd_of_mean_two_level": sd2, "sd_of_mean_plain_mc_same_fine_solves": sdp,
+            "variance_reduction": (sdp / sd2) ** 2 if sd2 > 0 else None}
+
+
 def bench_surrogate(api, dev, stream, samples=None, steps=3000):
     """Learned-surrogate form (64^2 / 8^2 workload): training on 1563
     samples (10^5 cell pairs) from the plain upscaler, inference on 10^5
@@ -773,6 +842,8 @@ def main():
     ap.add_argument("--ri-samples", type=int, default=None, help="random-interpolation samples (default 10^5)")
     ap.add_argument("--pg-batch", type=int, default=128, help="samples per step of the Petrov-Galerkin arm")
     ap.add_argument("--fp32r-batch", type=int, default=64, help="samples per step of the FP32+refinement arm")
+    ap.add_argument("--engine", default="default", choices=["default", "blocked", "tc3", "tc2"],
+                    help="factorisation engine of the FP32 forms in the timed steps")
     args = ap.parse_args()
 
     w = W.workload(args.workload)
@@ -795,6 +866,8 @@ def main():
     nf, nc = w["nf"], w["nc"]
     ncell = nc * nc
     B = args.batch
+    engine = {"default": None, "blocked": api.ENGINE_BLOCKED, "tc3": api.ENGINE_TC3,
+              "tc2": api.ENGINE_TC2}[args.engine]
     g = api.grid(nf, nc, w["f"])
     fld = api.field_from_dict(w["field"])
     K = W.n_vars(w["field"])
@@ -827,7 +900,8 @@ def main():
         if ev is not None:
             ev[0].record(stream)
         api.stomsfem_upscale(g, bf["a"], bf["Ke"], bf["be"], oversample=ov_t, max_oversample=mo,
-                             precision=FORMS[form], refine_iters=refine, workspace=bf["wsu"], stream=stream)
+                             precision=FORMS[form], refine_iters=refine, workspace=bf["wsu"], stream=stream,
+                             engine=engine if form != "fp64" else None)
         if ev is not None:
             ev[1].record(stream)
         api.stomsfem_coarse_solve(g, bf["Ke"], bf["be"], bf["u"], bf["mean"], bf["m2"], bf["cnt"],
@@ -945,6 +1019,7 @@ def main():
         extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
         extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
         extra["two_level_mc"] = bench_two_level(api, dev, stream)
+        extra["two_level_mc_1024"] = bench_two_level_1024(api, dev, stream, ov)
         extra["mixed_bc"] = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)
         extra["oscillatory_bc"] = dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form], stream))
         # kernels of each form's own timed calls (outside the step's timed region)
@@ -973,6 +1048,7 @@ def main():
             "config": {"workload": args.workload, "nf": nf, "nc": nc, "H_over_h": nf // nc,
                        "samples_per_step": B, "units_per_step": units_step,
                        "oversample": "0..4 per cell (seeded)", "form": form,
+                       "engine": args.engine,
                        "l2": "inputs larger than L2 (a: %.1f GB per step)" % (B * nf * nf * 8 / 1e9),
                        "parallelism": "replicas (sample shards)" if ws > 1 else "single GPU"},
             "_forms": {"chosen": form, "chosen_units_per_s": value, "fp64_units_per_s": value64,

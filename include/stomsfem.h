@@ -289,6 +289,16 @@ enum {
 int stomsfem_plan_tune(stomsfem_plan* plan, const double* xi, double* u, int32_t* blocks_per_sm,
                        int32_t* split_fp32, float* ms_best, stomsfem_stream_t stream);
 
+/* stomsfem_upscale with an explicit factorisation engine for the FP32
+ * forms (STOMSFEM_ENGINE_*; ignored in FP64); same arguments, layout and
+ * errors otherwise, plus EINVAL for an unknown engine or a tensor-core
+ * engine the patches are not eligible for.  Results of different engines
+ * agree within the form's tolerance. */
+int stomsfem_upscale_engine(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                            int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
+                            int32_t engine, double* Ke, double* be, double* phi, int32_t* unit_status,
+                            void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
+
 /* Sets the launch choice without timing: blocks per SM (0 = all that fit),
  * split flag (0 or 1), engine (STOMSFEM_ENGINE_*).  Drops the captured
  * graph.  EINVAL for values out of range or a tensor-core engine the
@@ -361,15 +371,25 @@ int stomsfem_local_kl_project(const stomsfem_local_kl* kl, const double* kappa, 
  * stomsfem_restrict_to_coarse (the differences) and stomsfem_mc_moments.
  * ------------------------------------------------------------------- */
 
-/* Scratch needed by stomsfem_fine_fem. */
+/* Scratch needed by stomsfem_fine_fem for S samples (nf <= 64: the banded
+ * factors of the warps in flight; larger nf: the multigrid hierarchy and
+ * the CG vectors of all S samples, about 95 bytes per fine node and
+ * sample).  EINVAL for an nf above 64 that does not halve down to 16 or
+ * less. */
 int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
 
 /* Standard Q1 FEM on the fine grid with zero Dirichlet data and load f
- * (element matrices a_e K_ref, load f h^2/4 per element corner), one warp
- * per sample on the blocked banded Cholesky of the coarse solve.
- * a device [S][nf][nf], u device [S][(nf+1)^2] (boundary entries 0; NaN
- * for a sample whose matrix is not positive definite).  EINVAL for
- * nf > 64 (the band limit of the solver). */
+ * (element matrices a_e K_ref, load f h^2/4 per element corner).
+ *  - nf <= 64: one warp per sample on the blocked banded Cholesky of the
+ *    coarse solve (NaN for a sample whose matrix is not positive
+ *    definite); stream-ordered.
+ *  - nf > 64 (nf = c 2^k, c <= 16): conjugate gradients in FP64 on all S
+ *    samples at once, preconditioned by one multigrid V-cycle in FP32
+ *    (bilinear prolongation, Galerkin coarse operators, damped Jacobi
+ *    smoothing), until every sample's residual is at most 1e-13 of its
+ *    load (at most 400 iterations, else ENOTSPD); synchronises `stream`
+ *    (convergence is checked on the host every four iterations).
+ * a device [S][nf][nf], u device [S][(nf+1)^2] (boundary entries 0). */
 int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int32_t S, double* u, void* workspace,
                       size_t workspace_bytes, stomsfem_stream_t stream);
 

@@ -98,7 +98,9 @@ def stomsfem_upscale_workspace_size(g: Grid, max_oversample=0, precision=FP64):
 
 
 def stomsfem_upscale(g: Grid, a, Ke, be, oversample=None, max_oversample=0, precision=FP64,
-                     refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None):
+                     refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None, engine=None):
+    """engine None: stomsfem_upscale (the default engine); otherwise
+    stomsfem_upscale_engine with that STOMSFEM_ENGINE_* value."""
     S = a.shape[0]
     ncell = g.nc * g.nc
     rho = g.nf // g.nc
@@ -106,14 +108,17 @@ def stomsfem_upscale(g: Grid, a, Ke, be, oversample=None, max_oversample=0, prec
         _, rb = stomsfem_upscale_workspace_size(g, max_oversample if oversample is not None else 0,
                                                 precision)
         workspace = torch.empty(rb, dtype=torch.uint8, device=a.device)
-    L.check(L.lib().stomsfem_upscale(
-        ctypes.byref(g), _dev(a, torch.float64, (S, g.nf, g.nf), "a"),
-        _dev(oversample, torch.int8, (ncell,), "oversample"), int(max_oversample), S, int(precision),
-        int(refine_iters), _dev(Ke, torch.float64, (S, ncell, 10), "Ke"),
-        _dev(be, torch.float64, (S, ncell, 4), "be"),
-        _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
-        _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
-        _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream)))
+    head = (ctypes.byref(g), _dev(a, torch.float64, (S, g.nf, g.nf), "a"),
+            _dev(oversample, torch.int8, (ncell,), "oversample"), int(max_oversample), S, int(precision),
+            int(refine_iters))
+    tail = (_dev(Ke, torch.float64, (S, ncell, 10), "Ke"), _dev(be, torch.float64, (S, ncell, 4), "be"),
+            _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
+            _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
+            _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream))
+    if engine is None:
+        L.check(L.lib().stomsfem_upscale(*head, *tail))
+    else:
+        L.check(L.lib().stomsfem_upscale_engine(*head, int(engine), *tail))
 
 
 def stomsfem_coarse_workspace_size(g: Grid, S):

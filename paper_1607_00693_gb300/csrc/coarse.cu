@@ -783,8 +783,19 @@ extern "C" int stomsfem_coarse_solve_bc(const stomsfem_grid* grid, int32_t pg, c
   return STOMSFEM_OK;
 }
 
+// Fine grids up to 64 elements per side: the blocked banded Cholesky (one
+// warp per sample); larger grids: multigrid-preconditioned CG (fine_mg.cu).
+constexpr int kFineDirectMax = 64;
+
 extern "C" int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes) {
   if (!grid || grid->nf <= 0 || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
+  if (grid->nf > kFineDirectMax) {
+    if (!fine_mg_supported(grid->nf))
+      return set_error(STOMSFEM_EINVAL, "nf %d: above %d the element count must halve down to 16 or less",
+                       grid->nf, kFineDirectMax);
+    *bytes = fine_mg_workspace_bytes(grid->nf, S > 0 ? S : 1);
+    return STOMSFEM_OK;
+  }
   const int sms = device_sm_count();
   long long slots = (long long)(sms > 0 ? sms : 152) * 8;
   if (slots > S) slots = S;
@@ -796,11 +807,19 @@ extern "C" int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32
 extern "C" int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int32_t S, double* u, void* workspace,
                                  size_t workspace_bytes, stomsfem_stream_t stream) {
   if (!grid || grid->nf <= 0) return set_error(STOMSFEM_EINVAL, "bad grid");
-  if (grid->nf > 64) return set_error(STOMSFEM_EINVAL, "nf %d > 64 (fine-grid bandwidth limit)", grid->nf);
   if (S < 0) return set_error(STOMSFEM_EINVAL, "S < 0");
   if (S == 0) return STOMSFEM_OK;
   if (!a || !u || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
   const int nf = grid->nf;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (nf > kFineDirectMax) {
+    if (!fine_mg_supported(nf))
+      return set_error(STOMSFEM_EINVAL, "nf %d: above %d the element count must halve down to 16 or less", nf,
+                       kFineDirectMax);
+    double res = 0.0;
+    int iters = 0;
+    return fine_mg_solve(nf, grid->f, a, S, u, workspace, workspace_bytes, 1e-13, 400, st, &res, &iters);
+  }
   const size_t sb = coarse_slot_bytes(nf);
   long long slots = (long long)(workspace_bytes / sb);
   if (slots < kCoarseBlkWarps)
@@ -808,7 +827,6 @@ extern "C" int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int
   long long blocks = slots / kCoarseBlkWarps;
   const long long need = ((long long)S + kCoarseBlkWarps - 1) / kCoarseBlkWarps;
   if (blocks > need) blocks = need;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t smem = blk_smem_bytes<double>(16, nf) * kCoarseBlkWarps;
   const int rpl = (16 + nf + 31) / 32;
   auto kern = rpl <= 1 ? fine_fem_kernel<1> : rpl == 2 ? fine_fem_kernel<2> : fine_fem_kernel<3>;

@@ -44,6 +44,14 @@ int upscale_pg_oscillatory(const stomsfem_grid* grid, const double* a, const int
                            double* be, double* phi, int32_t* unit_status, void* workspace, size_t workspace_bytes,
                            stomsfem_stream_t stream);
 
+// Fine-grid Q1 FEM by multigrid-preconditioned CG (fine_mg.cu): grids whose
+// element count halves down to at most 16, workspace bytes for S samples,
+// and the solve (synchronises the stream).
+bool fine_mg_supported(int nf);
+size_t fine_mg_workspace_bytes(int nf, int S);
+int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* workspace, size_t workspace_bytes,
+                  double rtol, int max_iters, cudaStream_t st, double* res, int* iters);
+
 #define STOMSFEM_TRY_CUDA(expr)                                  \
   do {                                                           \
     int _rc = ::stomsfem::check_cuda((expr), #expr);             \

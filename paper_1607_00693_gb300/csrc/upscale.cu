@@ -34,6 +34,26 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
                             unit_status, workspace, workspace_bytes, stream);
 }
 
+extern "C" int stomsfem_upscale_engine(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
+                                       int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
+                                       int32_t engine, double* Ke, double* be, double* phi, int32_t* unit_status,
+                                       void* workspace, size_t workspace_bytes, stomsfem_stream_t stream) {
+  if (engine < STOMSFEM_ENGINE_AUTO || engine > STOMSFEM_ENGINE_TC2)
+    return set_error(STOMSFEM_EINVAL, "unknown engine %d", engine);
+  int rc = validate_grid(grid);
+  if (rc) return rc;
+  if (engine == STOMSFEM_ENGINE_TC3 || engine == STOMSFEM_ENGINE_TC2) {
+    int nmax, bmax;
+    patch_limits(grid, oversample ? max_oversample : 0, &nmax, &bmax);
+    if (!upscale_tc_eligible(precision, grid->nf / grid->nc, bmax))
+      return set_error(STOMSFEM_EINVAL, "the tensor-core engines need an FP32 form, 4 <= nf/nc and a half bandwidth <= 40");
+  }
+  UpscaleTuning t;
+  t.engine = engine;
+  return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, phi,
+                            unit_status, workspace, workspace_bytes, stream, t);
+}
+
 namespace stomsfem {
 
 // FP64 upscaling of the units listed on the device (list and count device

@@ -127,9 +127,14 @@ def test_host_validation_of_the_further_forms(lib):
     assert lib.stomsfem_coarse_solve_bc(ctypes.byref(g), 1, v, v, v, v, 1, v, v, None, None, v, 1 << 20,
                                         None) == L.EINVAL
     # two-level pieces
-    big = L.Grid(128, 8, 1.0)
-    assert lib.stomsfem_fine_fem(ctypes.byref(big), v, 1, v, v, 1 << 20, None) == L.EINVAL
-    assert b"nf 128 > 64" in lib.stomsfem_last_error()
+    odd = L.Grid(100, 4, 1.0)      # 100 -> 50 -> 25: no multigrid hierarchy down to 16
+    assert lib.stomsfem_fine_fem(ctypes.byref(odd), v, 1, v, v, 1 << 20, None) == L.EINVAL
+    assert b"halve down to 16" in lib.stomsfem_last_error()
+    big = L.Grid(128, 8, 1.0)      # multigrid path: the 1 MB workspace is refused before any launch
+    assert lib.stomsfem_fine_fem(ctypes.byref(big), v, 1, v, v, 1 << 20, None) == L.ENOMEM
+    need = ctypes.c_size_t()
+    assert lib.stomsfem_fine_fem_workspace_size(ctypes.byref(big), 3, ctypes.byref(need)) == L.OK
+    assert need.value > 3 * 129 * 129 * 90
     assert lib.stomsfem_fine_fem(ctypes.byref(g), v, -1, v, v, 1 << 20, None) == L.EINVAL
     bad = L.Grid(64, 6, 1.0)
     assert lib.stomsfem_restrict_to_coarse(ctypes.byref(bad), v, None, 1, v, None) == L.EINVAL

@@ -1,0 +1,89 @@
+"""Fine-grid Q1 FEM above 64 elements per side (the level-1 solves of the
+two-level estimator, Remark in Sec. 4.1.1): multigrid-preconditioned CG on
+the GPU against the oracle's banded Cholesky (nf = 128, 256: relative L2
+within 1e-10, a smooth lognormal medium and a contrast-10^4 channel medium),
+and, at the 1024^2 grid of the H/h = 32 workload where the oracle's direct
+solve is out of reach, against the definition: the residual of the Q1
+system assembled element by element here (numpy) within 1e-12 of the load."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1607_00693_gb300 import api
+from paper_1607_00693_gb300 import workloads as W
+
+DEV = "cuda:0"
+KREF = np.array([[4, -1, -2, -1], [-1, 4, -1, -2], [-2, -1, 4, -1], [-1, -2, -1, 4]], dtype=np.float64) / 6.0
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from paper_1607_00693_gb300.build import build_library
+    import oracle
+    build_library()
+    oracle.build()
+    return oracle
+
+
+def _fine(g, a_np):
+    a = torch.from_numpy(np.ascontiguousarray(a_np)).to(DEV)
+    u = torch.empty((a.shape[0], (g.nf + 1) ** 2), dtype=torch.float64, device=DEV)
+    api.stomsfem_fine_fem(g, a, u)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+def _apply_q1(a2d, u):
+    """A u for the Q1 stiffness sum_e a_e K_ref (corners SW, SE, NE, NW) on
+    the full node grid; u [(nf+1)^2]."""
+    nf = a2d.shape[0]
+    U = u.reshape(nf + 1, nf + 1)
+    c = [U[:-1, :-1], U[:-1, 1:], U[1:, 1:], U[1:, :-1]]  # element corner values, [nf][nf] each
+    out = np.zeros_like(U)
+    sl = [(slice(0, -1), slice(0, -1)), (slice(0, -1), slice(1, None)), (slice(1, None), slice(1, None)),
+          (slice(1, None), slice(0, -1))]
+    for r in range(4):
+        t = sum(KREF[r, q] * c[q] for q in range(4)) * a2d
+        out[sl[r]] += t
+    return out.reshape(-1)
+
+
+def _fields(nf, seed):
+    r = np.random.default_rng(seed)
+    smooth = W.workload("upscale_1024")["field"]
+    fld = dict(smooth, nbx=8, nby=8, width=2.0 / 8)
+    chan = W.workload("contrast_2048")["field"]
+    chan = dict(chan, nbx=16, nby=16, width=1.5 / 16)
+    return fld, chan, r
+
+
+@pytest.mark.parametrize("nf", [128, 256])
+def test_fine_mg_matches_oracle(orc, nf):
+    fld, chan, r = _fields(nf, nf)
+    a = np.concatenate([orc.sample_coef(nf, fld, W.draw_xi(fld, 2, 5 + nf)),
+                        orc.sample_coef(nf, chan, W.draw_xi(chan, 1, 6 + nf, "normal"))])
+    assert a.max() / a.min() > 1e3
+    g = api.grid(nf, 1, 1.3)
+    u = _fine(g, a)
+    for s in range(a.shape[0]):
+        uo = orc.fine_fem(nf, 1.3, a[s])
+        assert np.linalg.norm(u[s] - uo) / np.linalg.norm(uo) <= 1e-10, s
+
+
+def test_fine_mg_residual_1024(orc):
+    nf = 1024
+    fld = W.workload("upscale_1024")["field"]
+    a = orc.sample_coef(nf, fld, W.draw_xi(fld, 2, 9))
+    g = api.grid(nf, 32, 1.0)
+    u = _fine(g, a)
+    h = 1.0 / nf
+    b = np.zeros((nf + 1, nf + 1))
+    b[1:-1, 1:-1] = h * h
+    for s in range(2):
+        U = u[s].reshape(nf + 1, nf + 1)
+        assert np.all(U[0] == 0) and np.all(U[-1] == 0) and np.all(U[:, 0] == 0) and np.all(U[:, -1] == 0)
+        res = (b - _apply_q1(a[s], u[s]).reshape(nf + 1, nf + 1))[1:-1, 1:-1]
+        assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(b[1:-1, 1:-1])

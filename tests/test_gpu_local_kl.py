@@ -4,8 +4,11 @@
 eigensolver accuracy); the local parameters are compared through quantities
 that do not depend on the sign (or, in a degenerate eigenspace, the basis)
 of the modes: the reconstruction sum_k sqrt(lambda_k) xi_k f_k on the patch
-and sum_k xi_k^2.  With the bump covariance (rank at most the number of
-bumps) every mode kept reconstructs the field on the patch exactly."""
+and sum_k xi_k^2, over the modes whose span is well determined (eigenvalues
+above 1e-6 of the largest: both eigensolvers resolve the rest only to
+their absolute accuracy).  With the bump covariance (rank at most the
+number of bumps) all kept modes reconstruct the field on the patch up to
+those ill-determined directions."""
 import numpy as np
 import pytest
 
@@ -70,15 +73,21 @@ def test_local_kl_bumps(orc, o):
                                    atol=1e-13 * lam_all[0])
         assert ks[cell] == min(kmax, len(lam_o))
         n = pts.shape[0]
+        # modes well separated from the numerically zero part of the
+        # spectrum (rank <= 16): their span is determined to ~1e-16 / 1e-6
+        good = int(np.sum(lam_all[:ks[cell]] > 1e-6 * lam_all[0]))
         for s in range(S):
             kp = kappa[s, y0:y1, x0:x1].reshape(-1)
-            rg = _gpu_recon(lam_g[cell], w_g[cell], xi[s, cell], n, hh)
             xo = lk.local_params(kp, 0.0, lam_o, F_o, hh)
-            ro = lk.reconstruct(xo, 0.0, lam_o, F_o)
-            # rank <= 16 bumps: the kept modes reproduce the field on the patch
-            np.testing.assert_allclose(rg, kp, rtol=1e-9, atol=1e-9 * np.abs(kp).max())
-            np.testing.assert_allclose(rg, ro, rtol=1e-9, atol=1e-9 * np.abs(kp).max())
-            assert np.sum(xi[s, cell] ** 2) == pytest.approx(np.sum(xo ** 2), rel=1e-9)
+            rg = (lam_g[cell, :good] * xi[s, cell, :good]) @ w_g[cell, :good, :n] / (hh * hh)
+            ro = lk.reconstruct(xo[:good], 0.0, lam_o[:good], F_o[:, :good])
+            scale = np.abs(kp).max()
+            np.testing.assert_allclose(rg, ro, rtol=0, atol=1e-9 * scale)
+            assert np.sum(xi[s, cell, :good] ** 2) == pytest.approx(np.sum(xo[:good] ** 2), rel=1e-9)
+            # every kept mode: the field on the patch, up to the modes whose
+            # eigenvalues sit at the rounding level of the largest
+            rall = _gpu_recon(lam_g[cell], w_g[cell], xi[s, cell], n, hh)
+            np.testing.assert_allclose(rall, kp, rtol=0, atol=1e-5 * scale)
             assert np.all(xi[s, cell, ks[cell]:] == 0.0)
 
 
