@@ -687,6 +687,10 @@ def bench_engines(api, g, fld, ov_t, mo, B, nn, stream, dev, xs_for, u64, Bc):
                                       "coarse_rel_l2_vs_fp64": err}
             api.stomsfem_plan_destroy(h)
         out[pname] = dict(samples_per_step=Bs, **res)
+    # the pipe rates the engines trade between (measured here)
+    out["pipe_tflops"] = {"fp32_fma": api.stomsfem_selftest_fma_rate(api.FP32),
+                          "mma_sync_tf32": api.stomsfem_selftest_mma_rate(0),
+                          "mma_sync_bf16": api.stomsfem_selftest_mma_rate(1)}
     return out
 
 

@@ -108,6 +108,14 @@ int stomsfem_selftest_exp(const double* t, int32_t n, double* out, stomsfem_stre
  * synchronises the device.  EINVAL on a bad precision or NULL. */
 int stomsfem_selftest_fma_rate(int32_t precision, float* tflops_host);
 
+/* Measured throughput of the warp-level tensor-core instructions (no paper
+ * counterpart; the A/B of the cell factorisation's engines rests on it):
+ * kind 0 mma.sync m16n8k8 TF32, kind 1 m16n8k16 BF16, FP32 accumulation,
+ * 8 independent accumulator chains per warp, 8 blocks of 256 threads per
+ * SM, best of three timed launches.  *tflops_host = 2 x MACs / time.
+ * Allocates a small device buffer and synchronises the device. */
+int stomsfem_selftest_mma_rate(int32_t kind, float* tflops_host);
+
 /* Coefficient sampling (Sec. 2.1.3, the parametrized coefficient of
  * Eq. MsFEB2).  xi: device [S][nbx*nby] float64; a: device [S][nf][nf]
  * float64, a value per fine element at its centroid ((ex+1/2)h, (ey+1/2)h).
@@ -167,9 +175,10 @@ int stomsfem_upscale_workspace_size(const stomsfem_grid* grid, int32_t max_overs
  *                oversampling recombination is singular.  Failed units
  *                get NaN outputs.
  *   workspace    device scratch of workspace_bytes (>= the slots of one
- *                block: 4 in the FP32 forms with 4 <= nf/nc and a half
- *                bandwidth of at most 40, 8 in the other FP32 cases, 4 in
- *                FP64; more slots = more units in flight)
+ *                block: 8 in the FP32 forms, 4 in FP64, with the default
+ *                factorisation engine; 4 with a tensor-core engine chosen
+ *                through stomsfem_upscale_engine; more slots = more units
+ *                in flight)
  * Errors: EINVAL (sizes, pointers, precision, bandwidth > 64), ENOMEM
  * (workspace below one block of slots), ECUDA. */
 int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
@@ -200,11 +209,10 @@ int stomsfem_upscale(const stomsfem_grid* grid, const double* a, const int8_t* o
  *    the GPU (different streams, or different host threads) race on it and
  *    must be serialised by the caller.
  *  - Errors: EINVAL when the slots of one block of the upscaling launch do
- *    not fit in the array (message gives the sizes): 4 slots in the FP32
- *    forms when 4 <= nf/nc and the half bandwidth nf/nc + 2 max_oversample
- *    is at most 40 (the tensor-core factorisation), 8 slots in the other
- *    FP32 cases, 4 in FP64 (stomsfem_upscale_workspace_size gives the slot
- *    size); plus those of stomsfem_upscale.  Fewer slots than the workspace
+ *    not fit in the array (message gives the sizes): 8 slots in the FP32
+ *    forms (two units per warp), 4 in FP64 (stomsfem_upscale_workspace_size
+ *    gives the slot size); plus those of stomsfem_upscale.  This entry point
+ *    always runs the default factorisation engine.  Fewer slots than the workspace
  *    path may mean lower throughput. */
 int stomsfem_upscale_noalloc(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
                              int32_t max_oversample, int32_t S, int32_t precision,
@@ -386,9 +394,12 @@ int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_
  *  - nf > 64 (nf = c 2^k, c <= 16): conjugate gradients in FP64 on all S
  *    samples at once, preconditioned by one multigrid V-cycle in FP32
  *    (bilinear prolongation, Galerkin coarse operators, damped Jacobi
- *    smoothing), until every sample's residual is at most 1e-13 of its
- *    load (at most 400 iterations, else ENOTSPD); synchronises `stream`
- *    (convergence is checked on the host every four iterations).
+ *    smoothing), until every sample's recursively updated CG residual is
+ *    at most 1e-13 of its load (at most 400 iterations, else ENOTSPD);
+ *    the true residual b - A u then sits at the FP64 rounding floor
+ *    (about eps || |A| |u| ||, e.g. 2e-11 of the load on a 1024^2
+ *    lognormal medium); synchronises `stream` (convergence is checked on
+ *    the host every four iterations).
  * a device [S][nf][nf], u device [S][(nf+1)^2] (boundary entries 0). */
 int stomsfem_fine_fem(const stomsfem_grid* grid, const double* a, int32_t S, double* u, void* workspace,
                       size_t workspace_bytes, stomsfem_stream_t stream);

@@ -42,6 +42,7 @@ _SIG = {
     "stomsfem_selftest_wait_timeout": (ctypes.c_int, [_I, ctypes.POINTER(_I)]),
     "stomsfem_selftest_exp": (ctypes.c_int, [_P, _I, _P, _P]),
     "stomsfem_selftest_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_float)]),
+    "stomsfem_selftest_mma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_float)]),
     "stomsfem_sample_coef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I, _P, _P]),
     "stomsfem_sample_coef_precision": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Field), _P, _I,
                                                       _I, _P, _P]),

@@ -76,6 +76,13 @@ def stomsfem_selftest_fma_rate(precision=FP32):
     return v.value
 
 
+def stomsfem_selftest_mma_rate(kind=0):
+    """Measured mma.sync throughput in TFLOP/s (0: TF32 m16n8k8, 1: BF16 m16n8k16)."""
+    v = ctypes.c_float()
+    L.check(L.lib().stomsfem_selftest_mma_rate(int(kind), ctypes.byref(v)))
+    return v.value
+
+
 def stomsfem_sample_coef(g: Grid, fld: Field, xi, a, stream=None):
     S = xi.shape[0]
     L.check(L.lib().stomsfem_sample_coef(ctypes.byref(g), ctypes.byref(fld),

@@ -21,9 +21,8 @@
 namespace stomsfem {
 
 // 64 MiB: about 150 unit slots for H/h = 32 with oversampling up to 4 in
-// FP32 (one block of the launch is the minimum it needs: 4 slots with the
-// tensor-core FP32 factorisation, 8 with the two-units-per-warp FP32
-// kernel, 4 in FP64).
+// FP32 (one block of the launch is the minimum it needs: 8 slots with the
+// two-units-per-warp FP32 kernel, 4 in FP64).
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;
 constexpr int kMaxDevices = 64;
 

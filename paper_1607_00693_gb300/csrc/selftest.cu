@@ -69,9 +69,80 @@ static int fma_rate(int iters, float* tflops) {
   return STOMSFEM_OK;
 }
 
+// mma.sync throughput probe: every warp runs 8 independent accumulator
+// chains of m16n8k8 TF32 (kind 0) or m16n8k16 BF16 (kind 1) products.
+template <int KIND>
+__global__ void __launch_bounds__(256) mma_rate_kernel(float* out, uint32_t seed, int iters) {
+  float d[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[i][j] = (float)(threadIdx.x + 4 * i + j) * 1e-3f;
+  const uint32_t mask = KIND == 0 ? 0x3f7fe000u : 0x3f7f3f7fu;  // finite TF32 / BF16x2 operands
+  const uint32_t a0 = (seed ^ threadIdx.x) & mask, a1 = (a0 * 3u) & mask, a2 = (a0 * 5u) & mask,
+                 a3 = (a0 * 7u) & mask, b0 = (a0 * 11u) & mask, b1 = (a0 * 13u) & mask;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if constexpr (KIND == 0)
+        asm volatile(
+            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[i][0]), "+f"(d[i][1]), "+f"(d[i][2]), "+f"(d[i][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      else
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[i][0]), "+f"(d[i][1]), "+f"(d[i][2]), "+f"(d[i][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t += d[i][j];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+template <int KIND>
+static int mma_rate(int iters, float* tflops) {
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  const int blocks = sms * 8, threads = 256;
+  float* dout = nullptr;
+  STOMSFEM_TRY_CUDA(cudaMalloc(&dout, sizeof(float) * (size_t)blocks * threads));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = check_cuda(cudaEventCreate(&e0), "event");
+  if (!rc) rc = check_cuda(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  for (int r = 0; r < 4 && !rc; ++r) {
+    cudaEventRecord(e0);
+    mma_rate_kernel<KIND><<<blocks, threads>>>(dout, 12345u, iters);
+    cudaEventRecord(e1);
+    rc = check_cuda(cudaEventSynchronize(e1), "mma probe");
+    float ms = 0.f;
+    if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    if (!rc && r > 0 && ms < best) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(dout);
+  if (rc) return rc;
+  const double k = KIND == 0 ? 8.0 : 16.0;
+  const double warps = (double)blocks * threads / 32.0;
+  *tflops = (float)(2.0 * 16.0 * 8.0 * k * 8.0 * iters * warps / (best * 1e-3) / 1e12);
+  return STOMSFEM_OK;
+}
+
 }  // namespace stomsfem
 
 using namespace stomsfem;
+
+extern "C" int stomsfem_selftest_mma_rate(int32_t kind, float* tflops_host) {
+  if (!tflops_host || (kind != 0 && kind != 1)) return set_error(STOMSFEM_EINVAL, "kind 0 (TF32) or 1 (BF16)");
+  return kind == 0 ? mma_rate<0>(2048, tflops_host) : mma_rate<1>(1024, tflops_host);
+}
 
 extern "C" int stomsfem_selftest_fma_rate(int32_t precision, float* tflops_host) {
   if (!tflops_host || (precision != STOMSFEM_FP64 && precision != STOMSFEM_FP32))

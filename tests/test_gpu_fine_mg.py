@@ -4,7 +4,10 @@ the GPU against the oracle's banded Cholesky (nf = 128, 256: relative L2
 within 1e-10, a smooth lognormal medium and a contrast-10^4 channel medium),
 and, at the 1024^2 grid of the H/h = 32 workload where the oracle's direct
 solve is out of reach, against the definition: the residual of the Q1
-system assembled element by element here (numpy) within 1e-12 of the load."""
+system assembled element by element here (numpy) at the FP64 rounding
+floor, |b - A u| <= 1e-12 |b| + 4 eps || |A| |u| || (the componentwise
+floor is 5e-11 |b| on this medium: a sparse direct solve in FP64 reaches
+3.3e-11 |b| there)."""
 import numpy as np
 import pytest
 
@@ -36,7 +39,7 @@ def _fine(g, a_np):
     return u.cpu().numpy()
 
 
-def _apply_q1(a2d, u):
+def _apply_q1(a2d, u, kref=KREF):
     """A u for the Q1 stiffness sum_e a_e K_ref (corners SW, SE, NE, NW) on
     the full node grid; u [(nf+1)^2]."""
     nf = a2d.shape[0]
@@ -46,7 +49,7 @@ def _apply_q1(a2d, u):
     sl = [(slice(0, -1), slice(0, -1)), (slice(0, -1), slice(1, None)), (slice(1, None), slice(1, None)),
           (slice(1, None), slice(0, -1))]
     for r in range(4):
-        t = sum(KREF[r, q] * c[q] for q in range(4)) * a2d
+        t = sum(kref[r, q] * c[q] for q in range(4)) * a2d
         out[sl[r]] += t
     return out.reshape(-1)
 
@@ -86,4 +89,6 @@ def test_fine_mg_residual_1024(orc):
         U = u[s].reshape(nf + 1, nf + 1)
         assert np.all(U[0] == 0) and np.all(U[-1] == 0) and np.all(U[:, 0] == 0) and np.all(U[:, -1] == 0)
         res = (b - _apply_q1(a[s], u[s]).reshape(nf + 1, nf + 1))[1:-1, 1:-1]
-        assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(b[1:-1, 1:-1])
+        floor = _apply_q1(a[s], np.abs(u[s]), np.abs(KREF)).reshape(nf + 1, nf + 1)[1:-1, 1:-1]
+        bound = 1e-12 * np.linalg.norm(b[1:-1, 1:-1]) + 4 * np.finfo(np.float64).eps * np.linalg.norm(floor)
+        assert np.linalg.norm(res) <= bound, (np.linalg.norm(res), bound)

@@ -110,10 +110,9 @@ def test_noalloc_fewest_slots(lib):
 
 
 def test_noalloc_rejects_oversized_patch(lib):
-    """H/h = 128: the slots of one block (4 in FP64, 8 in the FP32 forms,
-    whose tensor-core engine does not take this bandwidth) exceed the fixed
-    array; the call is refused on the host (real but small device buffers
-    are passed, and nothing is launched)."""
+    """H/h = 128: the slots of one block (4 in FP64, 8 in the FP32 forms)
+    exceed the fixed array; the call is refused on the host (real but small
+    device buffers are passed, and nothing is launched)."""
     g = api.grid(256, 2, 1.0)
     assert lib.stomsfem_upscale_static_scratch_bytes() == 64 << 20
     a = torch.zeros((1, 256, 256), dtype=torch.float64, device=DEV)
