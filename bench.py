@@ -618,36 +618,64 @@ def bench_ri(api, dev, stream, samples=None):
     return res, 3 * 3 + 3  # (tiles, eval, fallback) x 3 timed calls + the FP64 comparison x 3
 
 
-ENGINE_NAMES = {0: "auto", 1: "blocked_fma", 2: "tc_tf32x3", 3: "tc_tf32x2"}
+ENGINE_NAMES = {0: "auto", 1: "blocked_fma", 2: "tc_tf32x3", 3: "tc_tf32x2", 4: "wide_fma"}
+ORDER_NAMES = {0: "cell", 1: "patch_size"}
 
 
-def bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, direct_ms):
-    """The same step through a plan: launch shapes picked by its autotuner on
-    the first batch, then the whole step replayed as one CUDA graph."""
-    import torch
-    h = api.stomsfem_plan_create(g, fld, B, FORMS[form], oversample=ov_t, max_oversample=mo)
-    u = torch.empty((B, nn), dtype=torch.float64, device=dev)
-    mean = torch.zeros(nn, dtype=torch.float64, device=dev)
-    m2 = torch.zeros_like(mean)
-    cnt = torch.zeros(1, dtype=torch.float64, device=dev)
-    with torch.cuda.stream(stream):
-        bps, split, tune_ms = api.stomsfem_plan_tune(h, xs_for(0, B), u, stream=stream)
-        xs = [xs_for(i, B).contiguous() for i in range(4)]
-        api.stomsfem_plan_step(h, xs[0], u, mean, m2, cnt, stream=stream)   # capture
+class PlanArm:
+    """The headline step through the library's plan: launch choices picked
+    by its autotuner on the first batch (or fixed), then every step replayed
+    as one captured CUDA graph.  Each step's batch is copied into the
+    plan's fixed input buffer first (a device-to-device copy of the xi rows,
+    part of the step), and the device time of its upscaling launches is read
+    from the plan's timing events right after the step is queued."""
+
+    def __init__(self, api, g, fld, ov_t, mo, Bs, form, nn, K, stream, dev, engine=None, tune_xi=None, refine=2):
+        import torch
+        self.api, self.stream, self.Bs = api, stream, Bs
+        self.h = api.stomsfem_plan_create(g, fld, Bs, FORMS[form], oversample=ov_t, max_oversample=mo,
+                                          refine_iters=refine)
+        self.u = torch.empty((Bs, nn), dtype=torch.float64, device=dev)
+        self.mean = torch.zeros(nn, dtype=torch.float64, device=dev)
+        self.m2 = torch.zeros_like(self.mean)
+        self.cnt = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.xd = torch.empty((Bs, K), dtype=torch.float64, device=dev)
+        self.tune_ms = None
+        with torch.cuda.stream(stream):
+            if engine is None:
+                self.xd.copy_(tune_xi)
+                _, _, self.tune_ms = api.stomsfem_plan_tune(self.h, self.xd, self.u, stream=stream)
+            else:
+                api.stomsfem_plan_set_choice(self.h, 0, 1, engine)
         stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(3):
-            api.stomsfem_plan_step(h, xs[0], u, mean, m2, cnt, stream=stream)
-        e1.record(stream)
-        stream.synchronize()
-    info = api.stomsfem_plan_info(h)
-    api.stomsfem_plan_destroy(h)
-    ms_graph = e0.elapsed_time(e1) / 3
-    return {"samples_per_step": B, "blocks_per_sm": bps, "split_fp32": split, "engine": ENGINE_NAMES[info[2]],
-            "tune_best_ms": tune_ms,
-            "graph_ms_per_step": ms_graph, "graph_units_per_s": B * g.nc * g.nc / (ms_graph / 1e3),
-            "direct_ms_per_step": direct_ms, "graph_ready": info[3], "device_bytes": info[4]}
+
+    def step(self, xs):
+        """Queue one step on xs (device [Bs][K]); returns the upscaling time (ms)."""
+        self.xd.copy_(xs, non_blocking=True)
+        self.api.stomsfem_plan_step(self.h, self.xd, self.u, self.mean, self.m2, self.cnt, stream=self.stream)
+        return self.api.stomsfem_plan_upscale_ms(self.h)
+
+    def info(self):
+        bps, split, eng, order, ready, nbytes = self.api.stomsfem_plan_info(self.h)
+        return {"blocks_per_sm": bps, "split_fp32": split, "engine": ENGINE_NAMES[eng],
+                "order": ORDER_NAMES[order], "graph_ready": ready, "device_bytes": nbytes,
+                "tune_best_ms": self.tune_ms}
+
+    def launches_per_step(self, form, oversampled):
+        """Kernels of one step: sampling, the upscaling launches (the
+        cell-list kernel and one or two upscale_kernel launches), and the
+        coarse assembly/solve, moments and count kernels."""
+        _, split, _, order, _, _ = self.api.stomsfem_plan_info(self.h)
+        if oversampled and form == "fp32" and split:
+            n_up = 3
+        elif oversampled and order == 1:
+            n_up = 2
+        else:
+            n_up = 1
+        return 1 + n_up + 3
+
+    def close(self):
+        self.api.stomsfem_plan_destroy(self.h)
 
 
 def bench_engines(api, g, fld, ov_t, mo, B, nn, stream, dev, xs_for, u64, Bc):
@@ -661,13 +689,15 @@ def bench_engines(api, g, fld, ov_t, mo, B, nn, stream, dev, xs_for, u64, Bc):
         return out
     for pname, prec, Bs in (("fp32", api.FP32, B), ("fp32r", api.FP32_REFINED, max(Bc, B // 4))):
         res = {}
-        for eng in (api.ENGINE_BLOCKED, api.ENGINE_TC3, api.ENGINE_TC2):
+        for eng, order in ((api.ENGINE_BLOCKED, 0), (api.ENGINE_BLOCKED, 1), (api.ENGINE_WIDE, 0),
+                           (api.ENGINE_TC3, 0), (api.ENGINE_TC2, 0)):
+            name = ENGINE_NAMES[eng] + ("" if order == 0 else "+" + ORDER_NAMES[order] + "_order")
             h = api.stomsfem_plan_create(g, fld, Bs, prec, oversample=ov_t, max_oversample=mo, refine_iters=2)
             try:
-                api.stomsfem_plan_set_choice(h, 0, 1, eng)
+                api.stomsfem_plan_set_choice(h, 0, 1, eng, order)
             except Exception as e:  # not eligible for this grid
                 api.stomsfem_plan_destroy(h)
-                res[ENGINE_NAMES[eng]] = {"unavailable": str(e)}
+                res[name] = {"unavailable": str(e)}
                 continue
             u = torch.empty((Bs, nn), dtype=torch.float64, device=dev)
             xs = xs_for(0, Bs).contiguous()
@@ -683,8 +713,8 @@ def bench_engines(api, g, fld, ov_t, mo, B, nn, stream, dev, xs_for, u64, Bc):
             ms = e0.elapsed_time(e1) / 3
             ub = u[:Bc].cpu().numpy()
             err = float(np.max(np.linalg.norm(ub - u64[:Bc], axis=1) / np.linalg.norm(u64[:Bc], axis=1)))
-            res[ENGINE_NAMES[eng]] = {"units_per_s": Bs * g.nc * g.nc / (ms / 1e3), "ms_per_step": ms,
-                                      "coarse_rel_l2_vs_fp64": err}
+            res[name] = {"units_per_s": Bs * g.nc * g.nc / (ms / 1e3), "ms_per_step": ms,
+                         "coarse_rel_l2_vs_fp64": err}
             api.stomsfem_plan_destroy(h)
         out[pname] = dict(samples_per_step=Bs, **res)
     # the pipe rates the engines trade between (measured here)
@@ -846,8 +876,9 @@ def main():
     ap.add_argument("--ri-samples", type=int, default=None, help="random-interpolation samples (default 10^5)")
     ap.add_argument("--pg-batch", type=int, default=128, help="samples per step of the Petrov-Galerkin arm")
     ap.add_argument("--fp32r-batch", type=int, default=64, help="samples per step of the FP32+refinement arm")
-    ap.add_argument("--engine", default="default", choices=["default", "blocked", "tc3", "tc2"],
-                    help="factorisation engine of the FP32 forms in the timed steps")
+    ap.add_argument("--engine", default="tuned", choices=["tuned", "default", "blocked", "wide", "tc3", "tc2"],
+                    help="factorisation engine of the FP32 forms in the timed steps (tuned: the plan's "
+                         "autotuner picks the launch choices)")
     args = ap.parse_args()
 
     w = W.workload(args.workload)
@@ -870,8 +901,8 @@ def main():
     nf, nc = w["nf"], w["nc"]
     ncell = nc * nc
     B = args.batch
-    engine = {"default": None, "blocked": api.ENGINE_BLOCKED, "tc3": api.ENGINE_TC3,
-              "tc2": api.ENGINE_TC2}[args.engine]
+    engine = {"tuned": None, "default": None, "blocked": api.ENGINE_BLOCKED, "wide": api.ENGINE_WIDE,
+              "tc3": api.ENGINE_TC3, "tc2": api.ENGINE_TC2}[args.engine]
     g = api.grid(nf, nc, w["f"])
     fld = api.field_from_dict(w["field"])
     K = W.n_vars(w["field"])
@@ -896,7 +927,7 @@ def main():
         cnt = torch.zeros(1, dtype=torch.float64, device=dev)
         return dict(a=a, Ke=Ke, be=be, u=u, wsu=wsu, wsc=wsc, mean=mom[0], m2=mom[1], cnt=cnt)
 
-    def step(bf, xs, form, ev=None, refine=2):
+    def step(bf, xs, form, ev=None, refine=2, engine=None):
         # the FP32 form samples the coefficient in FP32 arithmetic too
         api.stomsfem_sample_coef_precision(g, fld, xs, bf["a"],
                                            precision=api.FP32 if form == "fp32" else api.FP64,
@@ -905,7 +936,7 @@ def main():
             ev[0].record(stream)
         api.stomsfem_upscale(g, bf["a"], bf["Ke"], bf["be"], oversample=ov_t, max_oversample=mo,
                              precision=FORMS[form], refine_iters=refine, workspace=bf["wsu"], stream=stream,
-                             engine=engine if form != "fp64" else None)
+                             engine=engine if form != "fp64" else None)  # None: the default
         if ev is not None:
             ev[1].record(stream)
         api.stomsfem_coarse_solve(g, bf["Ke"], bf["be"], bf["u"], bf["mean"], bf["m2"], bf["cnt"],
@@ -920,11 +951,11 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(form, Bs, steps, warmup, clocks=None, refine=2):
+    def timed(form, Bs, steps, warmup, clocks=None, refine=2, engine=None):
         bf = buffers(Bs, form)
         with torch.cuda.stream(stream):
             for i in range(warmup):
-                step(bf, xs_for(i, Bs), form, refine=refine)
+                step(bf, xs_for(i, Bs), form, refine=refine, engine=engine)
             stream.synchronize()
             barrier()
             torch.cuda.synchronize()
@@ -935,7 +966,7 @@ def main():
                 clocks.start()
             e0.record(stream)
             for i in range(steps):
-                step(bf, xs_for(warmup + i, Bs), form, evs[i], refine=refine)
+                step(bf, xs_for(warmup + i, Bs), form, evs[i], refine=refine, engine=engine)
             e1.record(stream)
             stream.synchronize()
             clk = clocks.stop() if clocks else None
@@ -949,72 +980,120 @@ def main():
     # roofline denominator: the FMA pipe's peak, measured here before timing
     peak, peak_note = alu_peak_tflops(form, api)
     clocks = ClockSampler(local)
-    ms, up_ms, clk, bf = timed(form, B, args.steps, args.warmup, clocks)
+    # the headline: the step through a plan (autotuned launch choices, one
+    # captured graph per step)
+    arm = PlanArm(api, g, fld, ov_t, mo, B, form, nn, K, stream, dev,
+                  engine=engine if args.engine not in ("tuned", "default") else
+                  (api.ENGINE_AUTO if args.engine == "default" else None),
+                  tune_xi=xs_for(0, B))
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            arm.step(xs_for(i, B))
+        stream.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks.start()
+        e0.record(stream)
+        up_ms = [arm.step(xs_for(args.warmup + i, B)) for i in range(args.steps)]
+        e1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        barrier()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    plan_info = arm.info()
+    launches = arm.launches_per_step(form, ov is not None)
     units_step = B * ncell
     value = units_step * ws * args.steps / (ms / 1e3)
     fl = unit_flops(nf, nc, ov, form) * B
     up_avg = sum(up_ms) / len(up_ms)
     achieved = fl / (up_avg / 1e3) / 1e12
+    # the same step by direct calls with the default launch choice
+    msd, _, _, bf = timed(form, B, max(1, min(args.steps, 3)), 1,
+                          engine=engine if args.engine not in ("tuned", "default") else None)
+    value_direct = units_step * ws * max(1, min(args.steps, 3)) / (msd / 1e3)
 
-    # the plain FP64 arm (same path, FP64 throughout), smaller batch
-    ms64, up64, _, bf64 = timed("fp64", args.fp64_batch, max(1, min(args.steps, 2)), 1)
-    value64 = args.fp64_batch * ncell * ws * max(1, min(args.steps, 2)) / (ms64 / 1e3)
-    # coarse-solution error of the chosen form vs the FP64 path on the same samples
+    # the chosen form's coarse solution on the first batch (for its error)
     Bc = min(args.fp64_batch, B)
-    bf_c = buffers(Bc, form)
     with torch.cuda.stream(stream):
-        step(bf_c, xs_for(0, Bc), form)
-        step(bf64, xs_for(0, args.fp64_batch), "fp64")
-    stream.synchronize()
-    uf = bf_c["u"].double().cpu().numpy()
-    u64 = bf64["u"][:Bc].cpu().numpy()
+        arm.step(xs_for(0, B))
+        stream.synchronize()
+    uf = arm.u[:Bc].cpu().numpy()
+
+    def plan_timed(form_, Bs, steps, warmup, refine=2):
+        """A tuned plan of another form: warm-up, timed steps (CUDA events),
+        then one step on the first batch, whose solutions stay in .u."""
+        a = PlanArm(api, g, fld, ov_t, mo, Bs, form_, nn, K, stream, dev, tune_xi=xs_for(0, Bs), refine=refine)
+        with torch.cuda.stream(stream):
+            for i in range(warmup):
+                a.step(xs_for(i, Bs))
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for i in range(steps):
+                a.step(xs_for(warmup + i, Bs))
+            t1.record(stream)
+            stream.synchronize()
+            a.step(xs_for(0, Bs))
+            stream.synchronize()
+        return max_over_ranks(t0.elapsed_time(t1), dev), a
+
+    # the plain FP64 arm (same path, FP64 throughout, its own tuned plan),
+    # smaller batch
+    steps_s = max(1, min(args.steps, 3))
+    ms64, arm64 = plan_timed("fp64", args.fp64_batch, steps_s, 1)
+    value64 = args.fp64_batch * ncell * ws * steps_s / (ms64 / 1e3)
+    plan64 = arm64.info()
+    u64 = arm64.u[:Bc].cpu().numpy()
+    arm64.close()
+    # coarse-solution error of the chosen form vs the FP64 path on the same samples
     err = float(np.max(np.linalg.norm(uf - u64, axis=1) / np.linalg.norm(u64, axis=1)))
-    del bf_c
     # the FP32 factor + FP64 refinement arm: the fewest sweeps (1, then 2)
     # that bring the coarse solution within 1e-10 of the FP64 path
     Br = min(args.fp32r_batch, args.fp64_batch)
     fp32r = {}
     for sweeps in (1, 2):
-        ms32r, _, _, bf32r = timed("fp32r", args.fp32r_batch, max(1, min(args.steps, 2)), 1, refine=sweeps)
-        v = args.fp32r_batch * ncell * ws * max(1, min(args.steps, 2)) / (ms32r / 1e3)
-        with torch.cuda.stream(stream):
-            step(bf32r, xs_for(0, args.fp32r_batch), "fp32r", refine=sweeps)
-        stream.synchronize()
-        e = float(np.max(np.linalg.norm(bf32r["u"][:Br].cpu().numpy() - u64[:Br], axis=1) /
+        ms32r, arm32r = plan_timed("fp32r", args.fp32r_batch, steps_s, 1, refine=sweeps)
+        v = args.fp32r_batch * ncell * ws * steps_s / (ms32r / 1e3)
+        e = float(np.max(np.linalg.norm(arm32r.u[:Br].cpu().numpy() - u64[:Br], axis=1) /
                          np.linalg.norm(u64[:Br], axis=1)))
-        fp32r[sweeps] = (v, e)
-        del bf32r
+        fp32r[sweeps] = (v, e, arm32r.info())
+        arm32r.close()
     sweeps_chosen = 1 if fp32r[1][1] <= 1e-10 else 2
-    value32r, err32r = fp32r[sweeps_chosen]
+    value32r, err32r, plan32r = fp32r[sweeps_chosen]
 
     e2e = None
     if not args.no_e2e:
-        # end to end through the public calls: pinned host xi in, u out
+        # end to end through the public calls (the plan): pinned host xi in,
+        # u out, every step
         steps_e = args.steps
         xh = torch.from_numpy(xi_host[:B].copy()).pin_memory()
         uh = torch.empty((B, nn), dtype=torch.float64).pin_memory()
-        xd = torch.empty((B, K), dtype=torch.float64, device=dev)
         with torch.cuda.stream(stream):
-            xd.copy_(xh, non_blocking=True)
-            step(bf, xd, form)
-            uh.copy_(bf["u"], non_blocking=True)
+            arm.xd.copy_(xh, non_blocking=True)
+            api.stomsfem_plan_step(arm.h, arm.xd, arm.u, arm.mean, arm.m2, arm.cnt, stream=stream)
+            uh.copy_(arm.u, non_blocking=True)
             stream.synchronize()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for i in range(steps_e):
-                xd.copy_(xh, non_blocking=True)
-                step(bf, xd, form)
-                uh.copy_(bf["u"], non_blocking=True)
+                arm.xd.copy_(xh, non_blocking=True)
+                api.stomsfem_plan_step(arm.h, arm.xd, arm.u, arm.mean, arm.m2, arm.cnt, stream=stream)
+                uh.copy_(arm.u, non_blocking=True)
             e1.record(stream)
             stream.synchronize()
         mse = max_over_ranks(e0.elapsed_time(e1), dev)
         e2e = {"value": units_step * ws * steps_e / (mse / 1e3), "unit": "units/s",
-               "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)}
+               "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8),
+               "api": "stomsfem_plan_step (captured graph)"}
+    arm.close()
 
     extra = {}
     if not args.no_extra_forms:
-        extra["plan"] = bench_plan(api, g, fld, ov_t, mo, B, form, nn, stream, dev, xs_for, ms / args.steps)
         extra["engines"] = bench_engines(api, g, fld, ov_t, mo, min(B, 256), nn, stream, dev, xs_for, u64, Bc)
         extra["petrov_galerkin"] = bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for,
                                             args.pg_batch, Bc, u64)
@@ -1053,6 +1132,8 @@ def main():
                        "samples_per_step": B, "units_per_step": units_step,
                        "oversample": "0..4 per cell (seeded)", "form": form,
                        "engine": args.engine,
+                       "plan": plan_info,
+                       "direct_calls_units_per_s": round(value_direct, 1),
                        "l2": "inputs larger than L2 (a: %.1f GB per step)" % (B * nf * nf * 8 / 1e9),
                        "parallelism": "replicas (sample shards)" if ws > 1 else "single GPU"},
             "_forms": {"chosen": form, "chosen_units_per_s": value, "fp64_units_per_s": value64,
@@ -1060,7 +1141,8 @@ def main():
                       "fp32r_units_per_s": value32r, "fp32r_speedup_vs_fp64": value32r / value64,
                       "fp32r_coarse_rel_l2_vs_fp64": err32r, "fp32r_sweeps": sweeps_chosen,
                       "fp32r_by_sweeps": {str(k): {"units_per_s": v[0], "coarse_rel_l2_vs_fp64": v[1]}
-                                          for k, v in fp32r.items()}},
+                                          for k, v in fp32r.items()},
+                      "plans": {"fp64": plan64, "fp32r": plan32r}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "traffic_note": traffic_note,
@@ -1069,7 +1151,7 @@ def main():
             "e2e": e2e,
             # per step: sampling, upscaling (FP32 form with oversampling: a
             # cell-list kernel and two upscale launches), coarse solve, moments, count
-            "gpu_launches": (7 if form == "fp32" and ov is not None else 5) * args.steps,
+            "gpu_launches": launches * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -261,10 +261,10 @@ int stomsfem_plan_destroy(stomsfem_plan* plan);
 
 /* Factorisation engines of the FP32 forms' cell problems (launch choices,
  * no paper counterpart):
- *   STOMSFEM_ENGINE_AUTO     the default for the patch size (TC3 when
- *                            eligible, else BLOCKED);
+ *   STOMSFEM_ENGINE_AUTO     the default (BLOCKED);
  *   STOMSFEM_ENGINE_BLOCKED  banded Cholesky with FP32 FMA updates, two
- *                            units per warp, any half bandwidth <= 64;
+ *                            units per warp, column blocks of 8, any half
+ *                            bandwidth <= 64;
  *   STOMSFEM_ENGINE_TC3      banded Cholesky whose trailing updates run on
  *                            the tensor cores (mma TF32) with every operand
  *                            split exactly into three TF32 parts (six
@@ -274,44 +274,67 @@ int stomsfem_plan_destroy(stomsfem_plan* plan);
  *   STOMSFEM_ENGINE_TC2      the same with two parts (three products, about
  *                            2^-21 per product: several times the FP32
  *                            rounding; offered for measurement, never
- *                            picked by the tuner).
- * FP64 always uses its own FMA factorisation. */
+ *                            picked by the tuner);
+ *   STOMSFEM_ENGINE_WIDE     the FMA factorisation with one unit per warp
+ *                            and column blocks of 16, any half bandwidth
+ *                            <= 64 (Galerkin form without oscillatory
+ *                            data).
+ * FP64 always uses its own FMA factorisation (BLOCKED). */
 enum {
   STOMSFEM_ENGINE_AUTO = 0,
   STOMSFEM_ENGINE_BLOCKED = 1,
   STOMSFEM_ENGINE_TC3 = 2,
-  STOMSFEM_ENGINE_TC2 = 3
+  STOMSFEM_ENGINE_TC2 = 3,
+  STOMSFEM_ENGINE_WIDE = 4
 };
 
+/* Unit orders of the persistent upscaling launches (launch choices):
+ *   STOMSFEM_ORDER_CELL   cells fastest (a warp's consecutive units are
+ *                         neighbouring cells of one sample);
+ *   STOMSFEM_ORDER_PATCH  by patch size, largest first: the cells sorted by
+ *                         decreasing oversampling, the samples fastest
+ *                         within a cell, so that the longest units start
+ *                         first and the launch ends on the shortest ones.
+ * Results do not depend on the order. */
+enum { STOMSFEM_ORDER_CELL = 0, STOMSFEM_ORDER_PATCH = 1 };
+
 /* Autotuner: runs the step on xi (device [S][nbx*nby]; u device
- * [S][(nc+1)^2] receives the solutions, no moments) for every launch
- * choice -- at most 1, 2 or all resident upscaling CTAs per SM; for the
- * FP32 forms with a tensor-core-eligible patch the engines TC3 and
- * BLOCKED; for the FP32 form with oversampling the separate forward-only
- * launch for the unoversampled cells or one launch -- timing two runs of
- * each with CUDA events after one untimed run, and keeps the fastest (host
- * outputs, any may be NULL: blocks per SM, 0 meaning all that fit; split
- * flag; its time per step in ms; the engine through stomsfem_plan_info).
- * Synchronises `stream`; drops the captured graph.  The FP32 results
- * depend on the split and engine choices within the FP32 tolerance. */
+ * [S][(nc+1)^2] receives the solutions, no moments) under launch choices
+ * and keeps the fastest.  Coordinate descent from (all CTAs per SM, split,
+ * BLOCKED, ORDER_CELL): first the engine (FP32 forms: BLOCKED, WIDE, and
+ * TC3 where the patches are eligible), then the unit order (with
+ * oversampling: CELL or PATCH), then the split (FP32 form with
+ * oversampling: the separate forward-only launch for the unoversampled
+ * cells or one launch), then at most 1, 2 or all resident upscaling CTAs
+ * per SM; each candidate is timed over two runs with CUDA events after one
+ * untimed run.  Host outputs, any may be NULL: blocks per SM (0 meaning all
+ * that fit), split flag, the best time per step in ms; the engine and the
+ * order through stomsfem_plan_info.  Synchronises `stream`; drops the
+ * captured graph.  The FP32 results depend on the split and engine
+ * choices within the FP32 tolerance. */
 int stomsfem_plan_tune(stomsfem_plan* plan, const double* xi, double* u, int32_t* blocks_per_sm,
                        int32_t* split_fp32, float* ms_best, stomsfem_stream_t stream);
 
 /* stomsfem_upscale with an explicit factorisation engine for the FP32
- * forms (STOMSFEM_ENGINE_*; ignored in FP64); same arguments, layout and
- * errors otherwise, plus EINVAL for an unknown engine or a tensor-core
- * engine the patches are not eligible for.  Results of different engines
- * agree within the form's tolerance. */
+ * forms (STOMSFEM_ENGINE_*; ignored in FP64) and unit order
+ * (STOMSFEM_ORDER_*; the patch order needs oversampling and room for the
+ * cell lists past the slots of one block, else it falls back to the cell
+ * order); same arguments, layout and errors otherwise, plus EINVAL for an
+ * unknown engine or order, or an engine the form or patches are not
+ * eligible for.  Results of different engines agree within the form's
+ * tolerance; the order does not change them. */
 int stomsfem_upscale_engine(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
                             int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
-                            int32_t engine, double* Ke, double* be, double* phi, int32_t* unit_status,
-                            void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
+                            int32_t engine, int32_t order, double* Ke, double* be, double* phi,
+                            int32_t* unit_status, void* workspace, size_t workspace_bytes,
+                            stomsfem_stream_t stream);
 
 /* Sets the launch choice without timing: blocks per SM (0 = all that fit),
- * split flag (0 or 1), engine (STOMSFEM_ENGINE_*).  Drops the captured
- * graph.  EINVAL for values out of range or a tensor-core engine the
- * plan's patches are not eligible for. */
-int stomsfem_plan_set_choice(stomsfem_plan* plan, int32_t blocks_per_sm, int32_t split_fp32, int32_t engine);
+ * split flag (0 or 1), engine (STOMSFEM_ENGINE_*), unit order
+ * (STOMSFEM_ORDER_*).  Drops the captured graph.  EINVAL for values out of
+ * range or an engine the plan's form or patches are not eligible for. */
+int stomsfem_plan_set_choice(stomsfem_plan* plan, int32_t blocks_per_sm, int32_t split_fp32, int32_t engine,
+                             int32_t order);
 
 /* One step: xi (device [S][nbx*nby]) -> u (device [S][(nc+1)^2]) and the
  * running moments (mean, m2, count as stomsfem_coarse_solve, or all NULL).
@@ -323,10 +346,18 @@ int stomsfem_plan_step(stomsfem_plan* plan, const double* xi, double* u, double*
                        double* count, int32_t use_graph, stomsfem_stream_t stream);
 
 /* The plan's launch choice (engine: the one AUTO resolves to for this
- * plan), whether a graph is instantiated, and the device memory it owns
- * (host outputs, any may be NULL). */
+ * plan; unit order), whether a graph is instantiated, and the device
+ * memory it owns (host outputs, any may be NULL). */
 int stomsfem_plan_info(const stomsfem_plan* plan, int32_t* blocks_per_sm, int32_t* split_fp32,
-                       int32_t* engine, int32_t* graph_ready, size_t* device_bytes);
+                       int32_t* engine, int32_t* order, int32_t* graph_ready, size_t* device_bytes);
+
+/* Device time of the upscaling launches (the cell-list kernel and the one
+ * or two upscale_kernel launches) of the plan's most recent step, in ms:
+ * two timing events of the plan are recorded around them in every step
+ * (inside the captured graph as external event nodes).  Waits for the
+ * second event (a host wait on that step's upscaling, not on the
+ * stream).  EINVAL before the first step. */
+int stomsfem_plan_upscale_ms(stomsfem_plan* plan, float* ms);
 
 /* ---------------------------------------------------------------------
  * Local KL parametrization (Sec. 2.1.1, Def. of the local KL expansion,

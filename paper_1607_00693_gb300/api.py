@@ -105,9 +105,11 @@ def stomsfem_upscale_workspace_size(g: Grid, max_oversample=0, precision=FP64):
 
 
 def stomsfem_upscale(g: Grid, a, Ke, be, oversample=None, max_oversample=0, precision=FP64,
-                     refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None, engine=None):
-    """engine None: stomsfem_upscale (the default engine); otherwise
-    stomsfem_upscale_engine with that STOMSFEM_ENGINE_* value."""
+                     refine_iters=2, phi=None, unit_status=None, workspace=None, stream=None, engine=None,
+                     order=None):
+    """engine and order None: stomsfem_upscale (the default engine, cell
+    order); otherwise stomsfem_upscale_engine with those STOMSFEM_ENGINE_*
+    and STOMSFEM_ORDER_* values (None: AUTO, CELL)."""
     S = a.shape[0]
     ncell = g.nc * g.nc
     rho = g.nf // g.nc
@@ -122,10 +124,11 @@ def stomsfem_upscale(g: Grid, a, Ke, be, oversample=None, max_oversample=0, prec
             _dev(phi, torch.float64, (S, ncell, 4, (rho + 1) ** 2), "phi"),
             _dev(unit_status, torch.int32, (S, ncell), "unit_status"),
             _dev(workspace, torch.uint8, None, "workspace"), workspace.numel(), _stream(stream))
-    if engine is None:
+    if engine is None and order is None:
         L.check(L.lib().stomsfem_upscale(*head, *tail))
     else:
-        L.check(L.lib().stomsfem_upscale_engine(*head, int(engine), *tail))
+        L.check(L.lib().stomsfem_upscale_engine(*head, int(engine or ENGINE_AUTO), int(order or ORDER_CELL),
+                                                *tail))
 
 
 def stomsfem_coarse_workspace_size(g: Grid, S):
@@ -581,19 +584,28 @@ def stomsfem_plan_step(h, xi, u, mean=None, m2=None, count=None, use_graph=True,
                                        _stream(stream)))
 
 
-ENGINE_AUTO, ENGINE_BLOCKED, ENGINE_TC3, ENGINE_TC2 = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_BLOCKED, ENGINE_TC3, ENGINE_TC2, ENGINE_WIDE = 0, 1, 2, 3, 4
+ORDER_CELL, ORDER_PATCH = 0, 1
 
 
-def stomsfem_plan_set_choice(h, blocks_per_sm=0, split_fp32=1, engine=ENGINE_AUTO):
-    L.check(L.lib().stomsfem_plan_set_choice(h, int(blocks_per_sm), int(split_fp32), int(engine)))
+def stomsfem_plan_set_choice(h, blocks_per_sm=0, split_fp32=1, engine=ENGINE_AUTO, order=ORDER_CELL):
+    L.check(L.lib().stomsfem_plan_set_choice(h, int(blocks_per_sm), int(split_fp32), int(engine), int(order)))
 
 
 def stomsfem_plan_info(h):
-    """-> (blocks_per_sm, split_fp32, engine, graph_ready, device_bytes)."""
-    b, sp, en, gr, nb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
-    L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(en), ctypes.byref(gr),
-                                       ctypes.byref(nb)))
-    return b.value, sp.value, en.value, gr.value, nb.value
+    """-> (blocks_per_sm, split_fp32, engine, order, graph_ready, device_bytes)."""
+    b, sp, en, od, gr = (ctypes.c_int32() for _ in range(5))
+    nb = ctypes.c_size_t()
+    L.check(L.lib().stomsfem_plan_info(h, ctypes.byref(b), ctypes.byref(sp), ctypes.byref(en), ctypes.byref(od),
+                                       ctypes.byref(gr), ctypes.byref(nb)))
+    return b.value, sp.value, en.value, od.value, gr.value, nb.value
+
+
+def stomsfem_plan_upscale_ms(h):
+    """Device time (ms) of the upscaling launches of the plan's last step."""
+    v = ctypes.c_float()
+    L.check(L.lib().stomsfem_plan_upscale_ms(h, ctypes.byref(v)))
+    return v.value
 
 
 def stomsfem_ri_save(h):

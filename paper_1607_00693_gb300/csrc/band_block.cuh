@@ -13,12 +13,19 @@
 //      right-hand sides ride along, which is the forward substitution;
 //   2. applies the rank-nb update to the trailing b x b window with 4 x 4
 //      register tiles (128-bit shared loads of the transposed panel, which
-//      is kept in the ring slots of the rows just retired);
+//      is kept in the ring slots of the rows just retired; each tile row
+//      read, updated and written back as one 128-bit access);
 //   3. clears the retired slots and writes the next rows from values the
 //      row generator copied into shared memory one block earlier.
 // The matrix lives only as a window of RW >= NB + b band rows in shared
 // memory (RW a multiple of NB; row r at slot r mod RW, entry A[r][r-d] at
-// column d).  Factor blocks go to global scratch as (NB + bmax) x NB
+// wnd[kWndOff + slot * PW + d]).  With PW = 3 (mod 8) and the offset of 3,
+// the four entries A[r][c..c+3] of any column group c = 0 (mod 4) of the
+// trailing window, and the four entries d = i-4g-3 .. i-4g of panel row i,
+// sit in one aligned 16-byte group: element (r, d) lies at r (PW + 1) - (r
+// - d) + const, and PW + 1 = 4 (mod 8), so rows whose slots differ by one
+// start an odd number of groups apart, which also keeps eight lanes on
+// eight different groups in the panel loads.  Factor blocks go to global scratch as (NB + bmax) x NB
 // row-major tiles; the substitutions stream them back through two shared
 // staging buffers with asynchronous copies (next block in flight while the
 // current one is used).
@@ -63,17 +70,20 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15)
 __host__ __device__ inline int blk_ring_rows(int NB, int bmax) { return (NB + bmax + NB - 1) / NB * NB; }
 
 // Row pitch: b + 1 band entries, and at least RP = bmax rounded up to 4 so
-// that NB rows hold the transposed trailing panel; even, so that the panel
-// load (lane i reads row i at column i - p, a stride of PW + 1 elements)
-// meets distinct banks.
+// that NB rows hold the transposed trailing panel (which starts 4 elements
+// into the retired rows' span, 16-byte aligned); rounded up to 3 (mod 8),
+// the layout of the aligned groups above.
 __host__ __device__ inline int blk_pitch(int bmax) {
   const int rp = (bmax + 3) & ~3;
   const int pw = bmax + 1 > rp ? bmax + 1 : rp;
-  return pw + (pw & 1);
+  return pw + ((3 - pw) & 7);
 }
 
+// Offset of slot 0's entry d = 0 in the window (elements).
+constexpr int kWndOff = 3;
+
 __host__ __device__ inline int blk_wnd_elems(int NB, int bmax) {
-  const int a = blk_ring_rows(NB, bmax) * blk_pitch(bmax), b = 2 * (NB + bmax) * NB;
+  const int a = kWndOff + blk_ring_rows(NB, bmax) * blk_pitch(bmax), b = 2 * (NB + bmax) * NB;
   return a > b ? a : b;
 }
 
@@ -186,6 +196,37 @@ __device__ __forceinline__ void blk_zero16(void* dst, int n16, int gl) {
   for (int v = gl; v < n16; v += G) d[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Zero n elements from p (any element alignment): the elements before the
+// first 16-byte boundary and after the last one singly, the rest in
+// 16-byte chunks (lanes gl of G).
+template <int G, typename T>
+__device__ __forceinline__ void blk_zero_span(T* p, int n, int gl) {
+  constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
+  const int head = min(n, (int)(((16u - ((uint32_t)__cvta_generic_to_shared(p) & 15u)) & 15u) / sizeof(T)));
+  const int body = (n - head) / E;
+  const int tail0 = head + body * E;
+  if (gl < head) p[gl] = T(0);
+  blk_zero16<G>(p + head, body, gl);
+  if (gl < n - tail0) p[tail0 + gl] = T(0);
+}
+
+// Four consecutive elements at a 16-byte-aligned shared address.
+__device__ __forceinline__ void ld_grp4(const float* p, float (&v)[4]) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void ld_grp4(const double* p, double (&v)[4]) {
+  const double2 f0 = reinterpret_cast<const double2*>(p)[0], f1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+}
+__device__ __forceinline__ void st_grp4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st_grp4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // Rows [r0, r1) of the window (at most G rows, in ring slots slot0,
 // slot0 + 1, ... mod RW; row r0 + l uses lane l's raw values): the
 // generator's entries and rhs.  The slots are zero on entry (the whole
@@ -200,7 +241,7 @@ __device__ __forceinline__ void blk_fill_raw(const Gen& gen, const BlkSmem<T>& s
     T e[5], rh[NR];
     gen.template make<T, NR>(r, raw, e, rh);
     const int slot = ring(slot0 + gl, s.RW);
-    T* row = s.wnd + slot * s.PW;
+    T* row = s.wnd + kWndOff + slot * s.PW;
     if (mx >= 3 && mx + 1 <= b) {
       // offsets 0, 1, mx-1, mx, mx+1 are distinct: plain stores
       row[0] = e[0];
@@ -372,8 +413,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
   constexpr int NB = G / 2;
   const int LBS = (NB + bmax) * NB;
   const int RW = s.RW;
-  const int blk16 = NB * s.PW * (int)sizeof(T) / 16;  // 16-byte chunks of NB ring rows
-  blk_zero16<G>(s.wnd, RW / NB * blk16, gl);
+  blk_zero16<G>(s.wnd, (int)(al16(sizeof(T) * (size_t)(kWndOff + RW * s.PW)) / 16), gl);
   __syncwarp();
   int fail = -1;
   // first window: rows [0, min(n, NB + b)) in slots 0.. (no wrap), generated directly
@@ -415,11 +455,20 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       const int i = gl + G * q;
       const bool in = i < np;
       const int slot = ring(kslot + (in ? i : 0), RW);
-      const T* row = s.wnd + slot * s.PW;
+      const T* row = s.wnd + kWndOff + slot * s.PW;
+      // entries d = i - p, p < NB, as NB / 4 aligned groups: group g4 holds
+      // d = i - 4 g4 - 3 .. i - 4 g4 (p = 4 g4 + 3 .. 4 g4); entries outside
+      // [0, b] (the neighbouring rows' ends and the gaps) are masked
 #pragma unroll
-      for (int p = 0; p < NB; ++p) {
-        const int d = i - p;
-        pr[q][p] = (in && p < nb && d >= 0 && d <= b) ? row[d] : T(0);
+      for (int g4 = 0; g4 < NB / 4; ++g4) {
+        const int d0 = i - 4 * g4 - 3;
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        if (in && d0 + 3 >= 0 && d0 <= b) ld_grp4(row + d0, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int p = 4 * g4 + 3 - k, d = d0 + k;
+          pr[q][p] = (p < nb && d >= 0 && d <= b) ? v[k] : T(0);
+        }
       }
       T x4[4];
       ld_row4(s.rhs + slot * 4, x4);
@@ -434,7 +483,9 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
     // rows K..K+NB-1 are retired, and their ring slots (contiguous: RW is a
     // multiple of NB) hold no live row until the next fill
     T* Lb = Lg + (size_t)kb * LBS;
-    T* pt = s.wnd + kslot * s.PW;
+    // the transposed trailing panel: 16-byte aligned inside the retired
+    // rows' span [kWndOff + kslot PW, kWndOff + (kslot + NB) PW)
+    T* pt = s.wnd + kslot * s.PW + 4;
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -522,14 +573,22 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][c] += va[a] * vc[c];
         }
+        // row ia's columns 4 tj + 3 .. 4 tj are its entries d = ia - 4 tj - 3
+        // .. ia - 4 tj: one aligned group (element k is column 4 tj + 3 - k);
+        // on a diagonal tile the entries above the diagonal (d < 0: the
+        // previous row's end and the gap) are written back unchanged
+        const bool diag = ti == tj;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int ia = 4 * ti + a;
           if (ia < nt) {
-            T* wr = s.wnd + ring(tslot + ia, RW) * s.PW + ia - 4 * tj;
+            T* wr = s.wnd + kWndOff + ring(tslot + ia, RW) * s.PW + (ia - 4 * tj - 3);
+            T v[4];
+            ld_grp4(wr, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (4 * tj + c <= ia) wr[-c] -= acc[a][c];
+            for (int k = 0; k < 4; ++k)
+              if (!diag || 3 - k <= a) v[k] -= acc[a][3 - k];
+            st_grp4(wr, v);
           }
         }
       }
@@ -537,7 +596,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
     __syncwarp();
     // the retired rows' slots (which held the trailing panel) are cleared for
     // the rows that will occupy them
-    blk_zero16<G>(pt, blk16, gl);
+    blk_zero_span<G>(s.wnd + kWndOff + kslot * s.PW, NB * s.PW, gl);
     __syncwarp();
   }
   return fail;

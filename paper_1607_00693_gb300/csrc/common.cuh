@@ -19,23 +19,26 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
                       size_t workspace_bytes, cudaStream_t st);
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
 // Scratch slots (units in flight) of one block of the upscaling launch for a
-// grid, oversampling limit and precision: the least workspace
-// stomsfem_upscale accepts, in slots (4 with the tensor-core FP32
-// factorisation, 8 with the two-units-per-warp FP32 kernel, 4 in FP64).
+// grid, oversampling limit and precision with the default engine: the least
+// workspace stomsfem_upscale accepts, in slots (8 in the FP32 forms, two
+// units per warp; 4 in FP64).
 int upscale_slots_per_block(const stomsfem_grid* grid, int32_t max_oversample, int precision);
 // stomsfem_upscale (Galerkin, no phi/status) with the plan's launch
 // choices: at most blocks_per_sm resident CTAs per SM (0: as many as fit),
 // split_fp32 = 0 runs the FP32 form as one launch, engine picks the FP32
-// forms' factorisation (STOMSFEM_ENGINE_*).
+// forms' factorisation (STOMSFEM_ENGINE_*), order the unit order
+// (STOMSFEM_ORDER_*).
 int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                   int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
-                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine);
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine,
+                  int order);
 // The factorisation engine (STOMSFEM_ENGINE_*) a request resolves to for a
 // grid, oversampling limit and precision.
 int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int precision, int requested);
-// Whether the tensor-core engines can serve a grid, oversampling limit and
-// precision (FP32 forms, 4 <= nf/nc, half bandwidth <= 40).
-bool upscale_tc_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision);
+// Whether engine (not AUTO) can serve a grid, oversampling limit and
+// precision: BLOCKED always, WIDE in the FP32 forms, the tensor-core
+// engines in the FP32 forms with 4 <= nf/nc and a half bandwidth <= 40.
+bool upscale_engine_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision, int engine);
 
 // Petrov-Galerkin upscaling with the oscillatory boundary data of the cell
 // problems (the Petrov-Galerkin half of stomsfem_upscale_bc).

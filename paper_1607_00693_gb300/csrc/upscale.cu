@@ -36,20 +36,27 @@ extern "C" int stomsfem_upscale(const stomsfem_grid* grid, const double* a,
 
 extern "C" int stomsfem_upscale_engine(const stomsfem_grid* grid, const double* a, const int8_t* oversample,
                                        int32_t max_oversample, int32_t S, int32_t precision, int32_t refine_iters,
-                                       int32_t engine, double* Ke, double* be, double* phi, int32_t* unit_status,
-                                       void* workspace, size_t workspace_bytes, stomsfem_stream_t stream) {
-  if (engine < STOMSFEM_ENGINE_AUTO || engine > STOMSFEM_ENGINE_TC2)
+                                       int32_t engine, int32_t order, double* Ke, double* be, double* phi,
+                                       int32_t* unit_status, void* workspace, size_t workspace_bytes,
+                                       stomsfem_stream_t stream) {
+  if (engine < STOMSFEM_ENGINE_AUTO || engine > STOMSFEM_ENGINE_WIDE)
     return set_error(STOMSFEM_EINVAL, "unknown engine %d", engine);
+  if (order != STOMSFEM_ORDER_CELL && order != STOMSFEM_ORDER_PATCH)
+    return set_error(STOMSFEM_EINVAL, "unknown unit order %d", order);
   int rc = validate_grid(grid);
   if (rc) return rc;
-  if (engine == STOMSFEM_ENGINE_TC3 || engine == STOMSFEM_ENGINE_TC2) {
+  if (precision < 0 || precision > 2) return set_error(STOMSFEM_EINVAL, "bad precision %d", precision);
+  if (engine != STOMSFEM_ENGINE_AUTO) {
     int nmax, bmax;
     patch_limits(grid, oversample ? max_oversample : 0, &nmax, &bmax);
-    if (!upscale_tc_eligible(precision, grid->nf / grid->nc, bmax))
-      return set_error(STOMSFEM_EINVAL, "the tensor-core engines need an FP32 form, 4 <= nf/nc and a half bandwidth <= 40");
+    if (!upscale_engine_eligible(engine, precision, grid->nf / grid->nc, bmax))
+      return set_error(STOMSFEM_EINVAL,
+                       "engine %d is not offered here (FP64: BLOCKED only; tensor-core engines: 4 <= nf/nc and a "
+                       "half bandwidth <= 40)", engine);
   }
   UpscaleTuning t;
   t.engine = engine;
+  t.order = order;
   return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, phi,
                             unit_status, workspace, workspace_bytes, stream, t);
 }
@@ -98,13 +105,14 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   A.cell_list = nullptr;
   A.cell_count = nullptr;
   A.blocks_per_sm_cap = 0;
+  A.order = 0;
   return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
 }
 
 int upscale_slots_per_block(const stomsfem_grid* grid, int32_t max_oversample, int precision) {
   int nmax, bmax;
   patch_limits(grid, max_oversample, &nmax, &bmax);
-  const int G = upscale_uses_tc(precision, grid->nf / grid->nc, bmax) ? 32 : group_lanes(precision);
+  const int G = upscale_engine_lanes(upscale_engine(kEngineAuto, precision, grid->nf / grid->nc, bmax));
   return upscale_warps(precision == STOMSFEM_FP64, G) * (32 / G);
 }
 
@@ -114,10 +122,10 @@ int upscale_engine_of(const stomsfem_grid* grid, int32_t max_oversample, int pre
   return upscale_engine(requested, precision, grid->nf / grid->nc, bmax);
 }
 
-bool upscale_tc_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision) {
+bool upscale_engine_ok(const stomsfem_grid* grid, int32_t max_oversample, int precision, int engine) {
   int nmax, bmax;
   patch_limits(grid, max_oversample, &nmax, &bmax);
-  return upscale_tc_eligible(precision, grid->nf / grid->nc, bmax);
+  return upscale_engine_eligible(engine, precision, grid->nf / grid->nc, bmax);
 }
 
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
@@ -131,11 +139,13 @@ size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
 // stomsfem_upscale with launch choices (the plan's autotuner).
 int upscale_tuned(const stomsfem_grid* grid, const double* a, const int8_t* oversample, int32_t max_oversample,
                   int32_t S, int32_t precision, int32_t refine_iters, double* Ke, double* be, void* workspace,
-                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine) {
+                  size_t workspace_bytes, cudaStream_t st, int blocks_per_sm, int split_fp32, int engine,
+                  int order) {
   UpscaleTuning t;
   t.blocks_per_sm = blocks_per_sm;
   t.split_fp32 = split_fp32;
   t.engine = engine;
+  t.order = order;
   return upscale_run<false>(grid, a, oversample, max_oversample, S, precision, refine_iters, Ke, be, nullptr,
                             nullptr, workspace, workspace_bytes, reinterpret_cast<stomsfem_stream_t>(st), t);
 }

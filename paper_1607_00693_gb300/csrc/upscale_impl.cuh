@@ -415,9 +415,10 @@ struct UpscaleArgs {
   const int32_t* unit_list;   // optional: process only these units (device list)
   const int32_t* unit_count;  // device length of unit_list
   double fq, fH2;             // f h^2 / 4 and f H^2 (load scaling)
-  const int32_t* cell_list;   // optional (MODE 1, 2): process only these cells (device list)
+  const int32_t* cell_list;   // optional: process only these cells (device list)
   const int32_t* cell_count;  // device length of cell_list
   int blocks_per_sm_cap;      // host-side launch shape: at most this many resident CTAs per SM (0: occupancy)
+  int order;                  // 0: cells fastest; 1: samples fastest, cells in list order
 };
 
 // Launch choices a plan's autotuner may set (stomsfem_plan_tune); the
@@ -426,6 +427,7 @@ struct UpscaleTuning {
   int blocks_per_sm = 0;  // 0: as many as fit
   int split_fp32 = 1;     // FP32 form: separate forward-only launch for the cells without oversampling
   int engine = 0;         // FP32 forms: factorisation engine (kEngine*; 0 = the default for the patch size)
+  int order = 0;          // STOMSFEM_ORDER_*: unit order of the persistent launches
 };
 
 // Upscale launch modes: 0 every unit (back-substitution route), 1 the
@@ -435,27 +437,43 @@ struct UpscaleTuning {
 // doubled and cost more than the forward-only route saved.
 enum { kModeAll = 0, kModeFwd = 1, kModeRest = 2 };
 
-// Device lists of the cells with o = 0 (list0) and the others (list1), in
-// cell order, and their lengths: one warp, ballot compaction.
-static __global__ void upscale_cell_lists_kernel(const int8_t* __restrict__ oversample, int ncell,
-                                          int32_t* __restrict__ list0, int32_t* __restrict__ list1,
-                                          int32_t* __restrict__ counts) {
+// Cell lists of the launches (one warp, ballot compaction): list0 the
+// cells without oversampling, list1 the others (cells with an oversampling
+// outside [0, max_o] included: the kernel flags them), listall every cell;
+// counts = {|list0|, |list1|, |listall|}.  sorted = 0: ascending cell index
+// (listall unused); sorted = 1: by patch size, largest first (decreasing
+// oversampling, the flagged cells last), ascending cell index within one
+// size, so that a launch that walks its list with the samples fastest
+// takes the longest units first.
+static __global__ void upscale_cell_lists_kernel(const int8_t* __restrict__ oversample, int ncell, int max_o,
+                                          int sorted, int32_t* __restrict__ list0, int32_t* __restrict__ list1,
+                                          int32_t* __restrict__ listall, int32_t* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
-  int n0 = 0, n1 = 0;
-  for (int c0 = 0; c0 < ncell; c0 += 32) {
-    const int c = c0 + lane;
-    const bool valid = c < ncell;
-    const bool z = valid && oversample[c] == 0;
-    const unsigned m0 = __ballot_sync(0xffffffffu, z), m1 = __ballot_sync(0xffffffffu, valid && !z);
-    const unsigned below = (1u << lane) - 1u;
-    if (z) list0[n0 + __popc(m0 & below)] = c;
-    if (valid && !z) list1[n1 + __popc(m1 & below)] = c;
-    n0 += __popc(m0);
-    n1 += __popc(m1);
+  const unsigned below = (1u << lane) - 1u;
+  int n0 = 0, n1 = 0, na = 0;
+  // pass k: sorted, k = max_o .. 0 the cells of oversampling k, then k = -1
+  // the flagged ones; unsorted, one pass (k = -2) over all cells
+  for (int k = sorted ? max_o : -2; k >= (sorted ? -1 : -2); --k) {
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+      const int c = c0 + lane;
+      const bool valid = c < ncell;
+      const int v = valid ? (int)oversample[c] : 0;
+      const bool take = valid && (k == -2 || (k >= 0 ? v == k : (v < 0 || v > max_o)));
+      const bool z = take && v == 0;
+      const unsigned m0 = __ballot_sync(0xffffffffu, z), m1 = __ballot_sync(0xffffffffu, take && !z);
+      const unsigned ma = __ballot_sync(0xffffffffu, take);
+      if (z) list0[n0 + __popc(m0 & below)] = c;
+      if (take && !z) list1[n1 + __popc(m1 & below)] = c;
+      if (sorted && take) listall[na + __popc(ma & below)] = c;
+      n0 += __popc(m0);
+      n1 += __popc(m1);
+      na += __popc(ma);
+    }
   }
   if (lane == 0) {
     counts[0] = n0;
     counts[1] = n1;
+    counts[2] = na;
   }
 }
 
@@ -521,18 +539,20 @@ upscale_kernel(UpscaleArgs A) {
   const int CN = (A.rho + 1) * (A.rho + 1);
 
   // cells of this launch (MODE 1, 2: a device list, or all cells when none)
-  const int nlc = (MODE != kModeAll && A.cell_list) ? A.cell_count[0] : ncell;
-  const long long nwork = A.unit_list ? (long long)A.unit_count[0]
-                                      : (G == 32 ? (long long)A.S * nlc : (long long)((A.S + 1) / 2) * nlc);
+  const int nlc = A.cell_list ? A.cell_count[0] : ncell;
+  // work items: (sample, cell) for G = 32, (pair of samples, cell) for G = 16
+  const long long npair = G == 32 ? (long long)A.S : (long long)((A.S + 1) / 2);
+  const long long nwork = A.unit_list ? (long long)A.unit_count[0] : npair * nlc;
   for (long long w = gw; w < nwork; w += nw) {
     long long u;
     bool dup = false;  // this half mirrors the other half's unit
-    const int ci = (int)(w % nlc);
-    const int cell_w = (MODE != kModeAll && A.cell_list) ? A.cell_list[ci] : ci;
+    const int ci = A.order ? (int)(w / npair) : (int)(w % nlc);
+    const long long pw = A.order ? w % npair : w / nlc;
+    const int cell_w = A.cell_list ? A.cell_list[ci] : ci;
     if (G == 32) {
-      u = A.unit_list ? (long long)A.unit_list[w] : (long long)(w / nlc) * ncell + cell_w;
+      u = A.unit_list ? (long long)A.unit_list[w] : pw * ncell + cell_w;
     } else {
-      int sp = 2 * (int)(w / nlc) + grp;
+      int sp = 2 * (int)pw + grp;
       if (sp >= A.S) {
         sp = A.S - 1;
         dup = true;
@@ -904,42 +924,61 @@ static int launch_rpl(const UpscaleArgs& A, long long max_blocks, cudaStream_t s
 
 // Bytes at the end of the workspace for the two cell lists of the split
 // FP32 launch.
-static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(int32_t) * (2 * (size_t)g->nc * g->nc + 2)); }
+static size_t cell_list_bytes(const stomsfem_grid* g) { return round256(sizeof(int32_t) * (3 * (size_t)g->nc * g->nc + 4)); }
 
 // Lanes per unit of each form: two units per warp.
 constexpr int group_lanes(int) { return 16; }
 
-// Factorisation engines of the FP32 forms: the tensor-core factorisation of
-// band_tc.cuh with operands in three TF32 parts (exact) or two parts (about
-// 2^-21 per product), for patches with a half bandwidth in [4, 40], or the
-// two-units-per-warp FMA factorisation of band_block.cuh (any bandwidth).
+// Factorisation engines of the FP32 forms: the two-units-per-warp FMA
+// factorisation of band_block.cuh in column blocks of 8 (any bandwidth),
+// the same with one unit per warp in column blocks of 16 (WIDE), or the
+// tensor-core factorisation of band_tc.cuh with operands in three TF32
+// parts (exact) or two parts (about 2^-21 per product), for patches with a
+// half bandwidth in [4, 40].
 enum {
   kEngineAuto = STOMSFEM_ENGINE_AUTO,
   kEngineBlocked = STOMSFEM_ENGINE_BLOCKED,
   kEngineTc3 = STOMSFEM_ENGINE_TC3,
-  kEngineTc2 = STOMSFEM_ENGINE_TC2
+  kEngineTc2 = STOMSFEM_ENGINE_TC2,
+  kEngineWide = STOMSFEM_ENGINE_WIDE
 };
 
-// The engine AUTO resolves to where the tensor-core engines are eligible.
+// The engine AUTO resolves to.
 constexpr int kEngineDefault = kEngineBlocked;
 
 static bool upscale_tc_eligible(int precision, int rho, int bmax) {
   return precision != STOMSFEM_FP64 && rho >= 4 && bmax <= kTcBMax;
 }
+// Whether `engine` (not AUTO) may run these patches in this form.
+static bool upscale_engine_eligible(int engine, int precision, int rho, int bmax) {
+  if (engine == kEngineBlocked) return true;
+  if (precision == STOMSFEM_FP64) return false;
+  if (engine == kEngineWide) return true;
+  return (engine == kEngineTc3 || engine == kEngineTc2) && upscale_tc_eligible(precision, rho, bmax);
+}
 static int upscale_engine(int requested, int precision, int rho, int bmax) {
-  if (precision == STOMSFEM_FP64 || !upscale_tc_eligible(precision, rho, bmax)) return kEngineBlocked;
-  return requested == kEngineAuto ? kEngineDefault : requested;
+  if (precision == STOMSFEM_FP64) return kEngineBlocked;
+  const int e = requested == kEngineAuto ? kEngineDefault : requested;
+  return upscale_engine_eligible(e, precision, rho, bmax) ? e : kEngineBlocked;
 }
+// Lanes per unit of the resolved engine.
+static int upscale_engine_lanes(int engine) { return engine == kEngineBlocked ? 16 : 32; }
 static bool upscale_uses_tc(int precision, int rho, int bmax) {
-  return upscale_engine(kEngineAuto, precision, rho, bmax) != kEngineBlocked;
+  return upscale_engine_lanes(upscale_engine(kEngineAuto, precision, rho, bmax)) == 32;
 }
+
+// The WIDE engine's launches (upscale_wide.cu; the Galerkin form without
+// the oscillatory data).  fp64_acc: TA = double (the FP32 + refinement form).
+int launch_wide(bool fp64_acc, int mode, const UpscaleArgs& A, long long max_blocks, cudaStream_t st);
 
 // Launch of an FP32-factor form with the chosen engine.
 template <typename TA, int MODE, bool PG, bool OSC>
 static int launch_fp32(int engine, const UpscaleArgs& A, long long max_blocks, cudaStream_t st) {
   if (engine == kEngineTc3) return launch_upscale<float, TA, 2, 32, MODE, PG, OSC, 3>(A, max_blocks, st);
-  if constexpr (!PG && !OSC)
+  if constexpr (!PG && !OSC) {
     if (engine == kEngineTc2) return launch_upscale<float, TA, 2, 32, MODE, PG, OSC, 2>(A, max_blocks, st);
+    if (engine == kEngineWide) return launch_wide(std::is_same<TA, double>::value, MODE, A, max_blocks, st);
+  }
   if (engine != kEngineBlocked) return set_error(STOMSFEM_EINVAL, "engine %d not offered for this form", engine);
   return launch_rpl<float, TA, 16, MODE, PG, OSC>(A, max_blocks, st);
 }
@@ -973,7 +1012,7 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
   const long long units = (long long)S * grid->nc * grid->nc;
   const long long slots = (long long)(workspace_bytes / sb);
   const int engine = upscale_engine(tune.engine, precision, grid->nf / grid->nc, bmax);
-  const int G = engine != kEngineBlocked ? 32 : group_lanes(precision);
+  const int G = upscale_engine_lanes(engine);
   const int WPB = upscale_warps(precision == STOMSFEM_FP64, G);
   const int slots_per_block = WPB * (32 / G);
   if (slots < slots_per_block)
@@ -1011,7 +1050,21 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
   A.cell_list = nullptr;
   A.cell_count = nullptr;
   A.blocks_per_sm_cap = tune.blocks_per_sm;
+  A.order = tune.order;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // cell lists at the end of the workspace (the split launch, or the order
+  // by patch size), when the slots of one block still fit before them
+  const int ncell = grid->nc * grid->nc;
+  const size_t lbytes = cell_list_bytes(grid);
+  const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
+  const bool lists_fit = oversample && slots2 >= slots_per_block;
+  unsigned char* lbase = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
+  int32_t* list0 = reinterpret_cast<int32_t*>(lbase);
+  int32_t* list1 = list0 + ncell;
+  int32_t* listall = list1 + ncell;
+  int32_t* counts = listall + ncell;
+  const bool sorted = tune.order == 1 && lists_fit;
+  const long long mb = lists_fit && max_blocks > slots2 / slots_per_block ? slots2 / slots_per_block : max_blocks;
   // the oscillatory data: every cell by back substitution in one launch
   // (the forward-only route never forms psi0, which the Petrov-Galerkin
   // sums then need, and one launch mode keeps the compile short)
@@ -1020,17 +1073,10 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
       // FP32 without phi output: cells without oversampling take the
       // forward-only route in a launch of their own, the others follow
       if (!oversample) return launch_fp32<float, kModeFwd, PG, OSC>(engine, A, max_blocks, st);
-      const size_t lbytes = cell_list_bytes(grid);
-      const long long slots2 = workspace_bytes > lbytes ? (long long)((workspace_bytes - lbytes) / sb) : 0;
-      if (slots2 >= slots_per_block) {
-        const int ncell = grid->nc * grid->nc;
-        unsigned char* base = static_cast<unsigned char*>(workspace) + ((workspace_bytes - lbytes) & ~size_t(255));
-        int32_t* list0 = reinterpret_cast<int32_t*>(base);
-        int32_t* list1 = list0 + ncell;
-        int32_t* counts = list1 + ncell;
-        upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, list0, list1, counts);
+      if (lists_fit) {
+        upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, mo, sorted ? 1 : 0, list0, list1, listall,
+                                                    counts);
         STOMSFEM_TRY_CUDA(cudaGetLastError());
-        const long long mb = max_blocks < slots2 / slots_per_block ? max_blocks : slots2 / slots_per_block;
         A.cell_list = list0;
         A.cell_count = counts;
         rc = launch_fp32<float, kModeFwd, PG, OSC>(engine, A, mb, st);
@@ -1040,6 +1086,14 @@ int upscale_run(const stomsfem_grid* grid, const double* a, const int8_t* oversa
         return launch_fp32<float, kModeRest, PG, OSC>(engine, A, mb, st);
       }
     }
+  }
+  if (sorted) {
+    // one launch over every cell, largest patches first
+    upscale_cell_lists_kernel<<<1, 32, 0, st>>>(oversample, ncell, mo, 1, list0, list1, listall, counts);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+    A.cell_list = listall;
+    A.cell_count = counts + 2;
+    max_blocks = mb;
   }
   if (precision == STOMSFEM_FP64)
     return launch_rpl<double, double, group_lanes(STOMSFEM_FP64), kModeAll, PG, OSC>(A, max_blocks, st);

@@ -154,8 +154,9 @@ def test_host_validation_of_the_further_forms(lib):
                                     ctypes.byref(h)) == L.EINVAL            # grid
     assert lib.stomsfem_plan_step(None, v, v, None, None, None, 1, None) == L.EINVAL
     assert lib.stomsfem_plan_tune(None, v, v, None, None, None, None) == L.EINVAL
-    assert lib.stomsfem_plan_info(None, None, None, None, None, None) == L.EINVAL
-    assert lib.stomsfem_plan_set_choice(None, 0, 1, 0) == L.EINVAL
+    assert lib.stomsfem_plan_info(None, None, None, None, None, None, None) == L.EINVAL
+    assert lib.stomsfem_plan_set_choice(None, 0, 1, 0, 0) == L.EINVAL
+    assert lib.stomsfem_plan_upscale_ms(None, None) == L.EINVAL
     assert lib.stomsfem_plan_destroy(None) == L.OK
 
 

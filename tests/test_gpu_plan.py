@@ -1,6 +1,8 @@
 """Plans on the GPU: the captured step (sample -> upscale -> coarse solve
 -> moments) reproduces the direct calls bit for bit, replays and
-re-captures, the autotuner's choices, and the default-stream path."""
+re-captures, its timing events, the autotuner's choices, every
+factorisation engine and unit order against the oracle, and the
+default-stream path."""
 import numpy as np
 import pytest
 
@@ -56,7 +58,9 @@ def test_plan_step_equals_direct_calls(case, prec):
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # capture + launch
             st.synchronize()
             np.testing.assert_array_equal(u.cpu().numpy(), u0)
-            assert api.stomsfem_plan_info(h)[3] == 1
+            assert api.stomsfem_plan_info(h)[4] == 1
+            t_up = api.stomsfem_plan_upscale_ms(h)     # events inside the graph
+            assert 0.0 < t_up < 1e4
             u.fill_(0.0)
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)       # replay
             st.synchronize()
@@ -76,10 +80,11 @@ def test_plan_step_equals_direct_calls(case, prec):
 
 
 def test_plan_tune_and_recapture(case):
-    """FP32 with oversampling: launch choices (blocks per SM, split, engine)
-    timed; the chosen one reproduces the direct result (bit for bit with
-    the split launch and the default engine, within the FP32 tolerance
-    otherwise); a new output buffer re-captures."""
+    """FP32 with oversampling: launch choices (engine, unit order, split,
+    blocks per SM) timed; the chosen one reproduces the direct result (bit
+    for bit with the split launch and the default engine, whatever the
+    order and blocks per SM; within the FP32 tolerance otherwise); a new
+    output buffer re-captures."""
     c = case
     u0 = _direct(c, api.FP32)
     h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], api.FP32, oversample=c["ov"], max_oversample=c["mo"])
@@ -90,13 +95,15 @@ def test_plan_tune_and_recapture(case):
             bps, split, ms = api.stomsfem_plan_tune(h, c["xt"], u, stream=st)
             assert bps in (0, 1, 2) and split in (0, 1) and ms > 0
             info = api.stomsfem_plan_info(h)
-            assert info[:2] == (bps, split) and info[2] in (api.ENGINE_TC3, api.ENGINE_BLOCKED) and info[3] == 0
+            assert info[:2] == (bps, split)
+            assert info[2] in (api.ENGINE_TC3, api.ENGINE_BLOCKED, api.ENGINE_WIDE)
+            assert info[3] in (api.ORDER_CELL, api.ORDER_PATCH) and info[4] == 0
             api.stomsfem_plan_step(h, c["xt"], u, stream=st)
             u2 = torch.empty_like(u)
             api.stomsfem_plan_step(h, c["xt"], u2, stream=st)
             st.synchronize()
         for x in (u.cpu().numpy(), u2.cpu().numpy()):
-            if split and info[2] == api.ENGINE_TC3:
+            if split and info[2] == api.ENGINE_BLOCKED:
                 np.testing.assert_array_equal(x, u0)
             else:
                 assert np.max(np.linalg.norm(x - u0, axis=1) / np.linalg.norm(u0, axis=1)) <= 1e-5
@@ -104,21 +111,26 @@ def test_plan_tune_and_recapture(case):
         api.stomsfem_plan_destroy(h)
 
 
-@pytest.mark.parametrize("prec,engine", [(api.FP32, api.ENGINE_BLOCKED), (api.FP32, api.ENGINE_TC3),
-                                         (api.FP32_REFINED, api.ENGINE_BLOCKED),
-                                         (api.FP32_REFINED, api.ENGINE_TC3),
-                                         (api.FP32_REFINED, api.ENGINE_TC2)])
-def test_plan_engines_match_oracle(case, orc, prec, engine):
-    """Each factorisation engine a plan can be set to, with oversampled
-    patches: K_e and the coarse solution against the FP64 oracle within the
-    form's tolerance (FP32 1e-5, FP32 + two FP64 refinement sweeps 1e-10)."""
+@pytest.mark.parametrize("prec,engine,order", [
+    (api.FP32, api.ENGINE_BLOCKED, api.ORDER_CELL), (api.FP32, api.ENGINE_TC3, api.ORDER_CELL),
+    (api.FP32, api.ENGINE_WIDE, api.ORDER_CELL), (api.FP32, api.ENGINE_BLOCKED, api.ORDER_PATCH),
+    (api.FP32, api.ENGINE_WIDE, api.ORDER_PATCH),
+    (api.FP32_REFINED, api.ENGINE_BLOCKED, api.ORDER_CELL), (api.FP32_REFINED, api.ENGINE_TC3, api.ORDER_CELL),
+    (api.FP32_REFINED, api.ENGINE_TC2, api.ORDER_CELL), (api.FP32_REFINED, api.ENGINE_WIDE, api.ORDER_CELL),
+    (api.FP32_REFINED, api.ENGINE_WIDE, api.ORDER_PATCH),
+    (api.FP64, api.ENGINE_BLOCKED, api.ORDER_PATCH)])
+def test_plan_engines_match_oracle(case, orc, prec, engine, order):
+    """Each factorisation engine and unit order a plan can be set to, with
+    oversampled patches: the coarse solution against the FP64 oracle within
+    the form's tolerance (FP32 1e-5, FP32 + two FP64 refinement sweeps
+    1e-10, FP64 1e-9)."""
     c = case
     g, S = c["g"], c["S"]
-    tol = 1e-5 if prec == api.FP32 else 1e-10
+    tol = {api.FP32: 1e-5, api.FP32_REFINED: 1e-10, api.FP64: 1e-9}[prec]
     h = api.stomsfem_plan_create(g, c["fld"], S, prec, oversample=c["ov"], max_oversample=c["mo"], refine_iters=2)
     try:
-        api.stomsfem_plan_set_choice(h, 0, 1, engine)
-        assert api.stomsfem_plan_info(h)[2] == engine
+        api.stomsfem_plan_set_choice(h, 0, 1, engine, order)
+        assert api.stomsfem_plan_info(h)[2:4] == (engine, order)
         st = torch.cuda.Stream()
         u = torch.empty((S, c["nn"]), dtype=torch.float64, device=DEV)
         with torch.cuda.stream(st):
@@ -133,8 +145,63 @@ def test_plan_engines_match_oracle(case, orc, prec, engine):
     Ko, bo = orc.upscale(g.nf, g.nc, 1.0, a, ov)
     uo = orc.coarse_solve(g.nc, Ko, bo)
     err = np.max(np.linalg.norm(u.cpu().numpy() - uo, axis=1) / np.linalg.norm(uo, axis=1))
-    print("engine %d precision %d: coarse error %.3e" % (engine, prec, err))
+    print("engine %d order %d precision %d: coarse error %.3e" % (engine, order, prec, err))
     assert err <= tol
+
+
+@pytest.mark.parametrize("prec,engine,split", [(api.FP32, api.ENGINE_BLOCKED, 1), (api.FP32, api.ENGINE_BLOCKED, 0),
+                                               (api.FP32, api.ENGINE_WIDE, 1), (api.FP32, api.ENGINE_TC3, 1),
+                                               (api.FP32_REFINED, api.ENGINE_BLOCKED, 1),
+                                               (api.FP64, api.ENGINE_BLOCKED, 1)])
+def test_plan_order_and_blocks_do_not_change_results(case, prec, engine, split):
+    """The unit order (cells fastest or by patch size) and the resident CTAs
+    per SM only reorder independent units: the solutions agree bit for bit,
+    with the flagged-cell handling included (an oversampling entry outside
+    [0, max_oversample] gives NaN for its cell in either order)."""
+    c = case
+    g, S = c["g"], c["S"]
+    ov_bad = c["ov"].clone()
+    ov_bad[3] = c["mo"] + 1
+    outs = []
+    for order, bps in ((api.ORDER_CELL, 0), (api.ORDER_PATCH, 0), (api.ORDER_PATCH, 1)):
+        h = api.stomsfem_plan_create(g, c["fld"], S, prec, oversample=c["ov"], max_oversample=c["mo"],
+                                     refine_iters=2)
+        try:
+            api.stomsfem_plan_set_choice(h, bps, split, engine, order)
+            st = torch.cuda.Stream()
+            u = torch.empty((S, c["nn"]), dtype=torch.float64, device=DEV)
+            with torch.cuda.stream(st):
+                api.stomsfem_plan_step(h, c["xt"], u, stream=st)
+                st.synchronize()
+            outs.append(u.cpu().numpy())
+        finally:
+            api.stomsfem_plan_destroy(h)
+        a = torch.empty((S, g.nf, g.nf), dtype=torch.float64, device=DEV)
+        api.stomsfem_sample_coef(g, c["fld"], c["xt"], a)
+        Ke = torch.empty((S, g.nc * g.nc, 10), dtype=torch.float64, device=DEV)
+        be = torch.empty((S, g.nc * g.nc, 4), dtype=torch.float64, device=DEV)
+        stt = torch.full((S, g.nc * g.nc), 7, dtype=torch.int32, device=DEV)
+        api.stomsfem_upscale(g, a, Ke, be, oversample=ov_bad, max_oversample=c["mo"], precision=prec,
+                             unit_status=stt, engine=engine, order=order)
+        torch.cuda.synchronize()
+        st_h = stt.cpu().numpy()
+        assert np.all(st_h[:, 3] == -1) and np.all(np.delete(st_h, 3, axis=1) == 0)
+        assert np.all(np.isnan(Ke.cpu().numpy()[:, 3])) and np.all(np.isfinite(np.delete(Ke.cpu().numpy(), 3, 1)))
+    for x in outs[1:]:
+        np.testing.assert_array_equal(x, outs[0])
+
+
+def test_plan_rejects_ineligible_engine(case):
+    c = case
+    h = api.stomsfem_plan_create(c["g"], c["fld"], c["S"], api.FP64, oversample=c["ov"], max_oversample=c["mo"])
+    try:
+        for eng in (api.ENGINE_WIDE, api.ENGINE_TC3):
+            with pytest.raises(Exception):
+                api.stomsfem_plan_set_choice(h, 0, 1, eng)
+        with pytest.raises(Exception):
+            api.stomsfem_plan_set_choice(h, 0, 1, api.ENGINE_BLOCKED, 2)
+    finally:
+        api.stomsfem_plan_destroy(h)
 
 
 def test_plan_default_stream_runs_directly(case):
@@ -146,6 +213,6 @@ def test_plan_default_stream_runs_directly(case):
         api.stomsfem_plan_step(h, c["xt"], u)      # the current (default) stream: no capture
         torch.cuda.synchronize()
         np.testing.assert_array_equal(u.cpu().numpy(), u0)
-        assert api.stomsfem_plan_info(h)[3] == 0
+        assert api.stomsfem_plan_info(h)[4] == 0
     finally:
         api.stomsfem_plan_destroy(h)
