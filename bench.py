@@ -1090,6 +1090,22 @@ def main():
         e2e = {"value": units_step * ws * steps_e / (mse / 1e3), "unit": "units/s",
                "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8),
                "api": "stomsfem_plan_step (captured graph)"}
+    merged = None
+    if ws > 1:
+        # the method's one exchange, after the timed region: every rank's
+        # running moments gathered and folded into one set on each rank
+        import torch.distributed as dist
+        with torch.cuda.stream(stream):
+            parts = []
+            for t in (arm.mean, arm.m2, arm.cnt):
+                lst = [torch.empty_like(t) for _ in range(ws)]
+                dist.all_gather(lst, t)
+                parts.append(lst)
+            mean_t, m2_t, cnt_t = (parts[k][0].clone() for k in range(3))
+            for r in range(1, ws):
+                api.stomsfem_mc_merge(mean_t, m2_t, cnt_t, parts[0][r], parts[1][r], parts[2][r], stream=stream)
+            stream.synchronize()
+        merged = {"samples": int(cnt_t.item()), "ranks": ws}
     arm.close()
 
     extra = {}
@@ -1152,6 +1168,7 @@ def main():
             # per step: sampling, upscaling (FP32 form with oversampling: a
             # cell-list kernel and two upscale launches), coarse solve, moments, count
             "gpu_launches": launches * args.steps,
+            "moments_merged": merged,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -446,6 +446,15 @@ int stomsfem_restrict_to_coarse(const stomsfem_grid* grid, const double* u_fine,
 int stomsfem_mc_moments(int32_t n, int32_t S, const double* u, double* mean, double* m2, double* count,
                         stomsfem_stream_t stream);
 
+/* Merges a second set of running moments (mean_b [n], m2_b [n], count_b
+ * [1], device; e.g. another rank's, gathered after a multi-GPU run) into
+ * (mean, m2, count) in place, by the pairwise update of Chan, Golub and
+ * LeVeque: the result equals the moments of both sample sets together (up
+ * to rounding).  A zero count_b leaves the first set unchanged.
+ * Stream-ordered.  EINVAL on n <= 0 or a NULL pointer. */
+int stomsfem_mc_merge(int32_t n, double* mean, double* m2, double* count, const double* mean_b,
+                      const double* m2_b, const double* count_b, stomsfem_stream_t stream);
+
 /* Petrov-Galerkin form of stomsfem_upscale (Eq. stiffness_local_petrov;
  * the form the paper uses with oversampling): same cell problems, same
  * arguments, but the test functions are the cell's bilinear nodal

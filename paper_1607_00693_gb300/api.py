@@ -554,6 +554,15 @@ def stomsfem_mc_moments(u, mean, m2, count, stream=None):
         _dev(m2, torch.float64, (n,), "m2"), _dev(count, torch.float64, (1,), "count"), _stream(stream)))
 
 
+def stomsfem_mc_merge(mean, m2, count, mean_b, m2_b, count_b, stream=None):
+    """Merges the moments (mean_b, m2_b, count_b) into (mean, m2, count) in place."""
+    n = mean.shape[0]
+    L.check(L.lib().stomsfem_mc_merge(
+        int(n), _dev(mean, torch.float64, (n,), "mean"), _dev(m2, torch.float64, (n,), "m2"),
+        _dev(count, torch.float64, (1,), "count"), _dev(mean_b, torch.float64, (n,), "mean_b"),
+        _dev(m2_b, torch.float64, (n,), "m2_b"), _dev(count_b, torch.float64, (1,), "count_b"), _stream(stream)))
+
+
 def stomsfem_plan_create(g: Grid, fld: Field, S, precision=FP64, oversample=None, max_oversample=0,
                          refine_iters=2):
     h = ctypes.c_void_p()

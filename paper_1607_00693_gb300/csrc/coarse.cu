@@ -347,6 +347,22 @@ __global__ void moments_kernel(int nn, int S, const double* __restrict__ u, doub
 
 __global__ void count_kernel(double* count, int S) { count[0] += (double)S; }
 
+// Merge a second set of running moments (mean_b, m2_b, count_b: another
+// rank's, or another stream's) into (mean, m2, count): the same pairwise
+// update; one block, the counts read before any is written.
+__global__ void moments_merge_kernel(int nn, double* mean, double* m2, double* count, const double* __restrict__ mean_b,
+                                     const double* __restrict__ m2_b, const double* __restrict__ count_b) {
+  const double na = count[0], nb = count_b[0], nt = na + nb;
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+    if (nb == 0.0) break;
+    const double delta = mean_b[q] - mean[q];
+    mean[q] = mean[q] + delta * (nb / nt);
+    m2[q] = m2[q] + m2_b[q] + delta * delta * (na * nb / nt);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) count[0] = nt;
+}
+
 // ---- Petrov-Galerkin coarse system (Eq. stiffness_local_petrov): row J
 // (test node) collects S_e[I_loc][J_loc] over the cells around J, a
 // non-symmetric band of half width bw = nc.  Banded LU without pivoting,
@@ -862,6 +878,17 @@ extern "C" int stomsfem_mc_moments(int32_t n, int32_t S, const double* u, double
   moments_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, S, u, mean, m2, count);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   count_kernel<<<1, 1, 0, st>>>(count, S);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  return STOMSFEM_OK;
+}
+
+extern "C" int stomsfem_mc_merge(int32_t n, double* mean, double* m2, double* count, const double* mean_b,
+                                 const double* m2_b, const double* count_b, stomsfem_stream_t stream) {
+  if (n <= 0) return set_error(STOMSFEM_EINVAL, "bad n");
+  if (!mean || !m2 || !count || !mean_b || !m2_b || !count_b)
+    return set_error(STOMSFEM_EINVAL, "NULL device pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  moments_merge_kernel<<<1, 1024, 0, st>>>(n, mean, m2, count, mean_b, m2_b, count_b);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return STOMSFEM_OK;
 }

@@ -157,6 +157,8 @@ def test_host_validation_of_the_further_forms(lib):
     assert lib.stomsfem_plan_info(None, None, None, None, None, None, None) == L.EINVAL
     assert lib.stomsfem_plan_set_choice(None, 0, 1, 0, 0) == L.EINVAL
     assert lib.stomsfem_plan_upscale_ms(None, None) == L.EINVAL
+    assert lib.stomsfem_mc_merge(0, None, None, None, None, None, None, None) == L.EINVAL
+    assert lib.stomsfem_mc_merge(4, None, None, None, None, None, None, None) == L.EINVAL
     assert lib.stomsfem_plan_destroy(None) == L.OK
 
 
