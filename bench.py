@@ -333,6 +333,115 @@ def bench_pod(api, dev, stream, samples=None):
     return res, 4 + 2 * 3 * 4
 
 
+def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
+    """The high-contrast comparison (contrast_2048: 2048^2 fine, 64^2 coarse,
+    H/h = 32, contrast 10^4, xi ~ N(0,1), no oversampling): plain FP64, the
+    FP32 form, FP32 + one refinement sweep (tuned plans, one graph per
+    step) and the POD form (offline basis from n_train training samples in
+    snapshot space; online BF16 tensor-core W^T A W with K = 1024 per cell
+    and the FP32 reduced solves, no refinement) on the same GPU, each a
+    whole step (sampling, upscaling, coarse solve), with the coarse error
+    against plain FP64 on the first fp64_batch samples.  CUDA events, one
+    warm-up step and two timed steps per arm."""
+    import torch
+    w = W.workload("contrast_2048")
+    nf, nc = w["nf"], w["nc"]
+    ncell = nc * nc
+    nn = (nc + 1) ** 2
+    rho = nf // nc
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    K = W.n_vars(w["field"])
+    xi = torch.from_numpy(W.draw_xi(w["field"], batch, w["seed"], w["dist"])).to(dev)
+    out = {"workload": "contrast_2048", "H_over_h": rho, "samples_per_step": batch, "fp64_samples": fp64_batch}
+
+    def run_arm(form, Bs, refine=2):
+        arm = PlanArm(api, g, fld, None, 0, Bs, form, nn, K, stream, dev, tune_xi=xi[:Bs], refine=refine)
+        with torch.cuda.stream(stream):
+            arm.step(xi[:Bs])
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                arm.step(xi[:Bs])
+            e1.record(stream)
+            stream.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        u = arm.u[:fp64_batch].cpu().numpy()
+        info = arm.info()
+        arm.close()
+        return Bs * ncell / (ms / 1e3), u, info
+
+    v64, u64, _ = run_arm("fp64", fp64_batch)
+    out["fp64_units_per_s"] = v64
+
+    def err(u):
+        return float(np.max(np.linalg.norm(u - u64, axis=1) / np.linalg.norm(u64, axis=1)))
+
+    v32, u32, info32 = run_arm("fp32", batch)
+    out["fp32"] = {"units_per_s": v32, "speedup_vs_fp64": v32 / v64, "coarse_rel_l2_vs_fp64": err(u32),
+                   "plan": info32}
+    v32r, u32r, _ = run_arm("fp32r", batch, refine=1)
+    out["fp32r_1_sweep"] = {"units_per_s": v32r, "speedup_vs_fp64": v32r / v64,
+                            "coarse_rel_l2_vs_fp64": err(u32r)}
+    # POD: offline from n_train FP64 snapshots, then the online step
+    xtr = torch.from_numpy(W.draw_xi(w["field"], n_train, w["seed"] + 1000, w["dist"])).to(dev)
+    atr = torch.empty((n_train, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xtr, atr)
+    Ktr = torch.empty((n_train, ncell, 10), dtype=torch.float64, device=dev)
+    btr = torch.empty((n_train, ncell, 4), dtype=torch.float64, device=dev)
+    phi = torch.empty((n_train, ncell, 4, (rho + 1) ** 2), dtype=torch.float64, device=dev)
+    api.stomsfem_upscale(g, atr, Ktr, btr, phi=phi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, ranks = api.stomsfem_pod_build(g, phi, atr, tol=1e-6, max_rank=27)
+    t_build = time.perf_counter() - t0
+    del phi, Ktr, btr, atr
+    a = torch.empty((batch, nf, nf), dtype=torch.float64, device=dev)
+    Ke = torch.empty((batch, ncell, 10), dtype=torch.float64, device=dev)
+    be = torch.empty((batch, ncell, 4), dtype=torch.float64, device=dev)
+    u = torch.empty((batch, nn), dtype=torch.float64, device=dev)
+    wsp = torch.empty(api.stomsfem_pod_workspace_size(h, batch), dtype=torch.uint8, device=dev)
+    wsc = torch.empty(api.stomsfem_coarse_workspace_size(g, batch), dtype=torch.uint8, device=dev)
+    evs = []
+
+    def pod_step(ev=None):
+        api.stomsfem_sample_coef(g, fld, xi, a, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=0, workspace=wsp, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        api.stomsfem_coarse_solve(g, Ke, be, u, workspace=wsc, stream=stream)
+
+    with torch.cuda.stream(stream):
+        pod_step()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            evs.append(ev)
+            pod_step(ev)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    ms_up = sum(a_.elapsed_time(b_) for a_, b_ in evs) / len(evs)
+    P0 = 4 + int(max(ranks))
+    Ppad = (P0 * (P0 + 1) // 2 + 15) // 16 * 16
+    gemm_flops = 2.0 * batch * ncell * (rho * rho) * Ppad
+    out["pod"] = {"units_per_s": batch * ncell / (ms / 1e3), "speedup_vs_fp64": batch * ncell / (ms / 1e3) / v64,
+                  "coarse_rel_l2_vs_fp64": err(u[:fp64_batch].cpu().numpy()),
+                  "train_samples": n_train, "build_s": t_build, "rank_min": int(min(ranks)),
+                  "rank_max": int(max(ranks)), "rank_mean": float(sum(ranks) / len(ranks)),
+                  "pod_upscale_ms": ms_up, "gemm_tensor_tflops_whole_call": gemm_flops / (ms_up / 1e3) / 1e12,
+                  "refinement": "none (FP64 refinement is offered for H/h <= 8)"}
+    api.stomsfem_pod_destroy(h)
+    out["note"] = ("surrogate and random interpolation: a cell of this workload sees more than 16 local "
+                   "variables (their limit), so they are not run here")
+    return out
+
+
 def bench_pod_affine(api, dev, stream, samples=None):
     """Affine reduced basis (Sec. 3.2.2, Eqs. RBaffine, localAF) on the 64^2 /
     8^2 grid with the affine field: basis from 200 training samples, affine
@@ -1119,6 +1228,7 @@ def main():
         extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
         extra["two_level_mc"] = bench_two_level(api, dev, stream)
         extra["two_level_mc_1024"] = bench_two_level_1024(api, dev, stream, ov)
+        extra["contrast_2048"] = bench_contrast(api, dev, stream)
         extra["mixed_bc"] = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)
         extra["oscillatory_bc"] = dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form], stream))
         # kernels of each form's own timed calls (outside the step's timed region)

@@ -552,9 +552,15 @@ typedef struct stomsfem_pod stomsfem_pod; /* opaque, owned by the library */
  * (footnote of Eq. KLphi); modes kept while sqrt(lambda_q/lambda_1) >= tol,
  * at most max_rank; or, if ranks_in (host [nc*nc]) is not NULL, exactly
  * ranks_in[cell] modes.  ranks_out (host [nc*nc], may be NULL) receives the
- * ranks.  Limits: 2 <= rho <= 8, 1 <= max_rank <= 27.  Allocates the
- * handle's device memory and synchronises `stream` before returning.
- * Errors: EINVAL, ENOTSPD (training-mean energy matrix), ECUDA. */
+ * ranks.  Limits: 2 <= rho <= 32, 1 <= max_rank <= 27.  For rho <= 8 the
+ * KL eigenproblem is the interior-node covariance's ((rho-1)^2 wide); for
+ * 8 < rho <= 32 it is solved in snapshot space (the 4 S_train x 4 S_train
+ * matrix X^T Abar X / (4 S_train) of the centred snapshots X, whose
+ * nonzero eigenvalues are the covariance's, modes X v / sqrt(4 S_train
+ * lambda)): S_train <= 16 there, and the eigenvalues past 4 S_train read 0.
+ * Allocates the handle's device memory and synchronises `stream` before
+ * returning.  Errors: EINVAL, ENOTSPD (training-mean energy matrix, rho <=
+ * 8), ECUDA. */
 int stomsfem_pod_build(const stomsfem_grid* grid, const double* phi_snap, const double* a_train,
                        int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
                        stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream);
@@ -601,19 +607,23 @@ int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t buf_bytes,
  * truncated or its dimensions are inconsistent.  Synchronous. */
 int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfem_pod** out);
 
-/* Scratch of stomsfem_pod_upscale for S samples (BF16 copy of a by cell and
- * the FP32 reduced matrices). */
+/* Scratch of stomsfem_pod_upscale for S samples (BF16 copy of a by cell,
+ * [nc*nc][S rounded up to 128][rho^2 rounded up to 64], and the FP32
+ * reduced matrices [nc*nc][S rounded up to 128][packed pairs rounded up to
+ * 16]; about 4 MB per sample at H/h = 32 on a 64 x 64 coarse grid). */
 int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* bytes);
 
 /* Online stage (Alg. 4) for S samples a (device [S][nf][nf] float64):
  * G = W^T A(omega) W for the extended basis W = [phibar, V] as one
- * tensor-core GEMM per cell (BF16 operands, FP32 accumulation), the r x r
+ * tensor-core GEMM per cell (BF16 operands, FP32 accumulation; K = the
+ * cell's rho^2 elements in steps of 64), the r x r
  * Galerkin system (V^T A V) c_l = -V^T A phibar_l in FP32, then
  * refine_iters FP64 refinement steps whose residual is formed with the fine
  * 9-point stencil of A(omega) (0 = none: K_e and b_e from the FP32 reduced
  * quantities).  Outputs as in stomsfem_upscale (Ke [S][nc*nc][10], be
  * [S][nc*nc][4], unit_status [S][nc*nc] or NULL: 0, ENOTSPD, ETIMEOUT).
- * Errors: EINVAL, ENOMEM (workspace), ECUDA. */
+ * The refinement needs rho <= 8.  Errors: EINVAL, ENOMEM (workspace),
+ * ECUDA. */
 int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t refine_iters,
                          double* Ke, double* be, int32_t* unit_status, void* workspace,
                          size_t workspace_bytes, stomsfem_stream_t stream);
@@ -627,8 +637,8 @@ int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t 
  *   W^T A(xi) W = gain G_0 + scale sum_k xi_k G_k,
  *   G_0 = sum_e W_e^T K_ref W_e,  G_k = sum_e psi_k(x_e) W_e^T K_ref W_e,
  * computed here once per cell in FP64 (stored FP32).  grid must be the
- * handle's; EINVAL for another field kind or more than 16 local
- * parameters.  Allocates device memory, synchronises `stream`.  The parts
+ * handle's and rho <= 8; EINVAL for another field kind or more than 16
+ * local parameters.  Allocates device memory, synchronises `stream`.  The parts
  * are not part of stomsfem_pod_save; call again after a load. */
 int stomsfem_pod_set_affine(stomsfem_pod* pod, const stomsfem_grid* grid, const stomsfem_field* field,
                             double tau, stomsfem_stream_t stream);

@@ -30,10 +30,12 @@
 
 namespace stomsfem {
 
-constexpr int kPodMaxRho = 8;      // elements per cell side (64 elements = one 128-byte K row)
-constexpr int kPodMaxN = 49;       // interior nodes, (rho - 1)^2
+constexpr int kPodMaxRhoSmall = 8;  // the covariance eigensolver, refinement, affine and per-l bases
+constexpr int kPodMaxRho = 32;      // elements per cell side (1024 elements: 16 K steps of 64)
+constexpr int kPodMaxN = 49;        // interior nodes of a small cell, (rho - 1)^2
+constexpr int kPodSnapMax = 64;     // large cells: snapshot columns (4 x training samples)
 constexpr int kPodMaxRank = 27;    // (4 + r)(5 + r)/2 <= 496 packed entries fit 512 TMEM columns
-constexpr int kPodK = 64;          // GEMM K (elements per cell, zero padded)
+constexpr int kPodK = 64;          // elements per GEMM K step (one 128-byte BF16 row)
 constexpr int kPodTileM = 128;
 constexpr int kPodAffParts = 17;   // affine parts: the constant one and up to 16 local parameters
 
@@ -52,7 +54,10 @@ struct PodDims {
   double f;
   int per_l;  // 1: one basis per basis function l = 1..3 (columns 4 + l * rcl ..), else one shared basis
   int rcl;    // per-l: the column block of each basis (its rank cap)
+  int Kp;     // GEMM K: the cell's elements rounded up to kPodK
 };
+
+__host__ __device__ inline int pod_kp(int ne) { return (ne + kPodK - 1) / kPodK * kPodK; }
 
 // Number of reduced unknowns a solve lane set spans: r (shared basis) or
 // 3 blocks of rcl (per-l bases).
@@ -138,6 +143,76 @@ __global__ void pod_w_init_kernel(PodDims d, const double* __restrict__ phibar, 
   for (int idx = threadIdx.x; idx < d.N2 * d.P0; idx += blockDim.x) {
     const int node = idx / d.P0, col = idx % d.P0;
     Wc[idx] = col < 4 ? phibar[(size_t)cell * 4 * d.N2 + col * d.N2 + node] : 0.0;
+  }
+}
+
+// Parallel cyclic Jacobi on the symmetric ne2 x ne2 matrix B (ne2 even,
+// row stride ld, shared memory), eigenvectors accumulated into the columns
+// of Z (initialised here to the identity): round-robin pairs (position 0
+// fixed, the others rotating), at most 40 sweeps, stopping when the
+// off-diagonal mass falls below 1e-30 of the diagonal's.  Every thread of
+// the CTA takes part; cs and pairs hold ne2 / 2 entries, offn one.
+__device__ void pod_jacobi(double* B, double* Z, int ld, int ne2, double (*cs)[2], int (*pairs)[2],
+                           double* offn) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < ne2 * ne2; idx += nt) {
+    const int i = idx / ne2, j = idx % ne2;
+    Z[i * ld + j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = ne2 / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) {
+      double off = 0.0, dia = 0.0;
+      for (int i = 0; i < ne2; ++i)
+        for (int j = 0; j < ne2; ++j) (i == j ? dia : off) += B[i * ld + j] * B[i * ld + j];
+      *offn = (off <= 1e-30 * dia) ? -1.0 : off;
+    }
+    __syncthreads();
+    if (*offn < 0.0) break;
+    for (int rnd = 0; rnd < ne2 - 1; ++rnd) {
+      for (int k = tid; k < np; k += nt) {
+        int a = (k == 0) ? 0 : 1 + (k - 1 + rnd) % (ne2 - 1);
+        int b = 1 + (ne2 - 2 - k + rnd) % (ne2 - 1);
+        if (a > b) { const int t = a; a = b; b = t; }
+        pairs[k][0] = a;
+        pairs[k][1] = b;
+        const double app = B[a * ld + a], aqq = B[b * ld + b], apq = B[a * ld + b];
+        double c = 1.0, sn = 0.0;
+        if (fabs(apq) > 1e-300) {
+          const double th = (aqq - app) / (2.0 * apq);
+          const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          sn = t * c;
+        }
+        cs[k][0] = c;
+        cs[k][1] = sn;
+      }
+      __syncthreads();
+      // rows: B[a,:], B[b,:]
+      for (int idx = tid; idx < np * ne2; idx += nt) {
+        const int k = idx / ne2, j = idx % ne2;
+        const int a = pairs[k][0], b = pairs[k][1];
+        const double c = cs[k][0], sn = cs[k][1];
+        const double x = B[a * ld + j], y = B[b * ld + j];
+        B[a * ld + j] = c * x - sn * y;
+        B[b * ld + j] = sn * x + c * y;
+      }
+      __syncthreads();
+      // columns: B[:,a], B[:,b] and the vectors Z[:,a], Z[:,b]
+      for (int idx = tid; idx < np * ne2; idx += nt) {
+        const int k = idx / ne2, i = idx % ne2;
+        const int a = pairs[k][0], b = pairs[k][1];
+        const double c = cs[k][0], sn = cs[k][1];
+        const double x = B[i * ld + a], y = B[i * ld + b];
+        B[i * ld + a] = c * x - sn * y;
+        B[i * ld + b] = sn * x + c * y;
+        const double zx = Z[i * ld + a], zy = Z[i * ld + b];
+        Z[i * ld + a] = c * zx - sn * zy;
+        Z[i * ld + b] = sn * zx + c * zy;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -227,63 +302,7 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
   }
   __syncthreads();
   // --- parallel cyclic Jacobi with round-robin pairs; Z accumulates vectors
-  for (int idx = tid; idx < ne2 * ne2; idx += nt) Z[idx / ne2][idx % ne2] = (idx / ne2 == idx % ne2) ? 1.0 : 0.0;
-  __syncthreads();
-  const int np = ne2 / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) {
-      double off = 0.0, dia = 0.0;
-      for (int i = 0; i < ne2; ++i)
-        for (int j = 0; j < ne2; ++j) (i == j ? dia : off) += B[i][j] * B[i][j];
-      offn = (off <= 1e-30 * dia) ? -1.0 : off;
-    }
-    __syncthreads();
-    if (offn < 0.0) break;
-    for (int rnd = 0; rnd < ne2 - 1; ++rnd) {
-      // round-robin: position 0 fixed, others rotate
-      for (int k = tid; k < np; k += nt) {
-        int a = (k == 0) ? 0 : 1 + (k - 1 + rnd) % (ne2 - 1);
-        int b = 1 + (ne2 - 2 - k + rnd) % (ne2 - 1);
-        if (a > b) { const int t = a; a = b; b = t; }
-        pairs[k][0] = a;
-        pairs[k][1] = b;
-        const double app = B[a][a], aqq = B[b][b], apq = B[a][b];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300) {
-          const double th = (aqq - app) / (2.0 * apq);
-          const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
-        }
-        cs[k][0] = c;
-        cs[k][1] = s;
-      }
-      __syncthreads();
-      // rows: B[a,:], B[b,:]
-      for (int idx = tid; idx < np * ne2; idx += nt) {
-        const int k = idx / ne2, j = idx % ne2;
-        const int a = pairs[k][0], b = pairs[k][1];
-        const double c = cs[k][0], s = cs[k][1];
-        const double x = B[a][j], y = B[b][j];
-        B[a][j] = c * x - s * y;
-        B[b][j] = s * x + c * y;
-      }
-      __syncthreads();
-      // columns: B[:,a], B[:,b] and the vectors Z[:,a], Z[:,b]
-      for (int idx = tid; idx < np * ne2; idx += nt) {
-        const int k = idx / ne2, i = idx % ne2;
-        const int a = pairs[k][0], b = pairs[k][1];
-        const double c = cs[k][0], s = cs[k][1];
-        const double x = B[i][a], y = B[i][b];
-        B[i][a] = c * x - s * y;
-        B[i][b] = s * x + c * y;
-        const double zx = Z[i][a], zy = Z[i][b];
-        Z[i][a] = c * zx - s * zy;
-        Z[i][b] = s * zx + c * zy;
-      }
-      __syncthreads();
-    }
-  }
+  pod_jacobi(&B[0][0], &Z[0][0], kPodMaxN + 1, ne2, cs, pairs, &offn);
   // --- order eigenvalues (descending) among the n real ones
   for (int i = tid; i < n; i += nt) {
     int rank = 0;
@@ -330,15 +349,205 @@ __global__ void pod_eig_kernel(PodDims d, const double* __restrict__ cov,
   }
 }
 
-// T[cell][j][e] (BF16, K-major rows of kPodK) and the load terms
+// ---- large cells (H/h > 8): the KL eigenproblem in snapshot space.
+// With X the m = 4 Ns centred interior snapshots (columns t * 4 + l) and
+// Abar the training-mean energy matrix, the covariance C = X X^T / m and
+// the snapshot matrix M = X^T Abar X / m have the same nonzero eigenvalues
+// in the energy inner product (B = R^T C R and M = Y^T Y with Y = R^T X /
+// sqrt(m), Abar = R R^T), and M v = lambda v gives the Abar-orthonormal mode
+// zeta = X v / sqrt(m lambda) = R^-T (Y v / sqrt(lambda)): the m x m problem
+// replaces the n x n one (n = 961 at H/h = 32).
+
+// X[cell][i][j] and Y = Abar X (the training-mean 9-point stencil applied to
+// the centred snapshots, zero on the cell boundary), FP64.
+__global__ void pod_snap_xy_kernel(PodDims d, const double* __restrict__ phi, int Ns,
+                                   const double* __restrict__ phibar, const double* __restrict__ abar,
+                                   double* __restrict__ X, double* __restrict__ Y) {
+  const int cell = blockIdx.x;
+  const int rho = d.rho, NN = rho + 1, m = 4 * Ns;
+  const double* pb = phibar + (size_t)cell * 4 * d.N2;
+  const double* ab = abar + (size_t)cell * d.ne;
+  auto xc = [&](int t, int l, int ix, int iy) -> double {  // centred value, 0 on the boundary
+    if (ix <= 0 || iy <= 0 || ix >= rho || iy >= rho) return 0.0;
+    const int node = iy * NN + ix;
+    return phi[((size_t)t * d.ncell + cell) * 4 * d.N2 + (size_t)l * d.N2 + node] - pb[(size_t)l * d.N2 + node];
+  };
+  for (int idx = threadIdx.x; idx < d.n * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m, t = j >> 2, l = j & 3;
+    const int ix = i % (rho - 1) + 1, iy = i / (rho - 1) + 1;
+    double y = 0.0;
+    // the four elements around the node; r = the node's corner in each
+    for (int ey = iy - 1; ey <= iy; ++ey)
+      for (int ex = ix - 1; ex <= ix; ++ex) {
+        const int cx[4] = {ex, ex + 1, ex + 1, ex}, cy[4] = {ey, ey, ey + 1, ey + 1};
+        const int r = (ix == ex ? (iy == ey ? 0 : 3) : (iy == ey ? 1 : 2));
+        double t4 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) t4 += kKref[r][c] * xc(t, l, cx[c], cy[c]);
+        y += ab[ey * rho + ex] * t4;
+      }
+    X[((size_t)cell * d.n + i) * m + j] = xc(t, l, ix, iy);
+    Y[((size_t)cell * d.n + i) * m + j] = y;
+  }
+}
+
+// One CTA per cell: M = X^T Y / m (upper triangle, mirrored: Abar is
+// symmetric, so M is up to rounding) in shared memory, its
+// eigenpairs (pod_jacobi), rank, eigenvalues (lam [cell][n], descending,
+// zero past m), and W = [phibar_1..4, zeta_1..r, 0 ...].
+__global__ void pod_snap_eig_kernel(PodDims d, const double* __restrict__ X, const double* __restrict__ Y, int Ns,
+                                    const double* __restrict__ phibar, double tol, int max_rank,
+                                    const int32_t* __restrict__ ranks_in, double* __restrict__ W,
+                                    double* __restrict__ lam_out, int32_t* __restrict__ ranks_out) {
+  constexpr int LD = kPodSnapMax + 1;
+  extern __shared__ double snap_smem[];
+  double* B = snap_smem;       // [m][LD]
+  double* Z = B + kPodSnapMax * LD;
+  __shared__ double cs[kPodSnapMax / 2][2];
+  __shared__ int pairs[kPodSnapMax / 2][2];
+  __shared__ int order[kPodSnapMax];
+  __shared__ double offn, s_scale[kPodSnapMax];
+  __shared__ int s_rank;
+  const int cell = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int m = 4 * Ns, n = d.n;
+  const double* Xc = X + (size_t)cell * n * m;
+  const double* Yc = Y + (size_t)cell * n * m;
+  for (int idx = tid; idx < m * m; idx += nt) {
+    const int j = idx / m, k = idx % m;
+    if (k < j) continue;
+    double sxy = 0.0;
+    for (int i = 0; i < n; ++i) sxy += Xc[(size_t)i * m + j] * Yc[(size_t)i * m + k];
+    const double v = sxy / m;
+    B[j * LD + k] = v;
+    B[k * LD + j] = v;
+  }
+  __syncthreads();
+  pod_jacobi(B, Z, LD, m, cs, pairs, &offn);
+  for (int i = tid; i < m; i += nt) {
+    int rank = 0;
+    for (int j = 0; j < m; ++j)
+      if (B[j * LD + j] > B[i * LD + i] || (B[j * LD + j] == B[i * LD + i] && j < i)) ++rank;
+    order[rank] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r;
+    if (ranks_in) {
+      r = ranks_in[cell];
+    } else {
+      const double l1 = B[order[0] * LD + order[0]] > 0 ? B[order[0] * LD + order[0]] : 1.0;
+      r = 0;
+      while (r < m && sqrt(fmax(B[order[r] * LD + order[r]], 0.0) / l1) >= tol) ++r;
+    }
+    if (r > max_rank) r = max_rank;
+    if (r > m) r = m;
+    if (r < 1) r = 1;
+    s_rank = r;
+    ranks_out[cell] = r;
+  }
+  for (int i = tid; i < n; i += nt) lam_out[(size_t)cell * n + i] = i < m ? B[order[i] * LD + order[i]] : 0.0;
+  __syncthreads();
+  const int r = s_rank;
+  // 1 / sqrt(m lambda) per kept mode (a non-positive eigenvalue, only
+  // reachable through pinned ranks, gives a zero column)
+  for (int q = tid; q < r; q += nt) {
+    const double lq = B[order[q] * LD + order[q]];
+    s_scale[q] = lq > 0.0 ? 1.0 / sqrt((double)m * lq) : 0.0;
+  }
+  __syncthreads();
+  double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  const int rho = d.rho, NN = rho + 1;
+  for (int idx = tid; idx < d.N2 * d.P0; idx += nt) {
+    const int node = idx / d.P0, col = idx % d.P0;
+    double v = 0.0;
+    if (col < 4) {
+      v = phibar[(size_t)cell * 4 * d.N2 + (size_t)col * d.N2 + node];
+    } else if (col - 4 < r) {
+      const int ix = node % NN, iy = node / NN;
+      if (ix > 0 && iy > 0 && ix < rho && iy < rho) {
+        const int i = (iy - 1) * (rho - 1) + (ix - 1), src = order[col - 4];
+        for (int j = 0; j < m; ++j) v += Xc[(size_t)i * m + j] * Z[j * LD + src];
+        v *= s_scale[col - 4];
+      }
+    }
+    Wc[idx] = v;
+  }
+}
+
+// Large cells: T[cell][j][e] = Wfull_e,alpha^T K_ref Wfull_e,beta (packed pair
+// j = (alpha, beta)) in BF16, from FP32 products (the BF16 rounding of T is
+// far above their error), 64 elements at a time: the corner values w and
+// K_ref w of the block's elements staged in shared memory, each thread
+// writing consecutive elements of one pair (coalesced rows).  The load
+// terms wl as in pod_tensor_kernel (FP64).
+__global__ void pod_tensor_large_kernel(PodDims d, const double* __restrict__ W, __nv_bfloat16* __restrict__ T,
+                                        double* __restrict__ wl) {
+  extern __shared__ float tl_smem[];
+  float* w = tl_smem;                       // [64][4][P0]
+  float* kw = tl_smem + kPodK * 4 * d.P0;   // [64][4][P0]
+  __shared__ int s_a[512], s_b[512];
+  const int cell = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const double* Wc = W + (size_t)cell * d.N2 * d.P0;
+  const int rho = d.rho, P0 = d.P0;
+  for (int j = tid; j < d.P; j += nt) {
+    int a = 0, rem = j;
+    while (rem >= P0 - a) { rem -= P0 - a; ++a; }
+    s_a[j] = a;
+    s_b[j] = a + rem;
+  }
+  for (int e0 = 0; e0 < d.Kp; e0 += kPodK) {
+    __syncthreads();
+    for (int idx = tid; idx < kPodK * P0; idx += nt) {
+      const int el = idx / P0, al = idx % P0, e = e0 + el;
+      float c4[4] = {0.f, 0.f, 0.f, 0.f};
+      if (e < d.ne) {
+        const int ex = e % rho, ey = e / rho;
+        const int nodes[4] = {ey * (rho + 1) + ex, ey * (rho + 1) + ex + 1, (ey + 1) * (rho + 1) + ex + 1,
+                              (ey + 1) * (rho + 1) + ex};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) c4[r] = (float)Wc[(size_t)nodes[r] * P0 + al];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float k = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) k = fmaf((float)kKref[r][c], c4[c], k);
+        w[(el * 4 + r) * P0 + al] = c4[r];
+        kw[(el * 4 + r) * P0 + al] = k;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < d.Ppad * kPodK; idx += nt) {
+      const int j = idx / kPodK, el = idx % kPodK;
+      float v = 0.f;
+      if (j < d.P) {
+        const int a = s_a[j], b = s_b[j];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v = fmaf(w[(el * 4 + r) * P0 + a], kw[(el * 4 + r) * P0 + b], v);
+      }
+      T[((size_t)cell * d.Ppad + j) * d.Kp + e0 + el] = __float2bfloat16_rn(v);
+    }
+  }
+  const double h = 1.0 / d.nf;
+  for (int al = tid; al < P0; al += nt) {
+    double s = 0.0;
+    for (int ey = 0; ey < rho; ++ey)
+      for (int ex = 0; ex < rho; ++ex)
+        s += Wc[(size_t)(ey * (rho + 1) + ex) * P0 + al] + Wc[(size_t)(ey * (rho + 1) + ex + 1) * P0 + al] +
+             Wc[(size_t)((ey + 1) * (rho + 1) + ex + 1) * P0 + al] + Wc[(size_t)((ey + 1) * (rho + 1) + ex) * P0 + al];
+    wl[(size_t)cell * P0 + al] = d.f * h * h / 4.0 * s;
+  }
+}
+
+// T[cell][j][e] (BF16, K-major rows of Kp = 64 elements: small cells) and the load terms
 // wl[cell][alpha] = f int Wfull_alpha.
 __global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_bfloat16* __restrict__ T,
                                   double* __restrict__ wl) {
   const int cell = blockIdx.x;
   const double* Wc = W + (size_t)cell * d.N2 * d.P0;
   const int rho = d.rho;
-  for (int idx = threadIdx.x; idx < d.Ppad * kPodK; idx += blockDim.x) {
-    const int j = idx / kPodK, e = idx % kPodK;
+  for (int idx = threadIdx.x; idx < d.Ppad * d.Kp; idx += blockDim.x) {
+    const int j = idx / d.Kp, e = idx % d.Kp;
     double v = 0.0;
     if (j < d.P && e < d.ne) {
       // invert the packed index
@@ -355,7 +564,7 @@ __global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_
         for (int c = 0; c < 4; ++c) v += wa * kKref[r][c] * Wc[(size_t)nodes[c] * d.P0 + b];
       }
     }
-    T[((size_t)cell * d.Ppad + j) * kPodK + e] = __float2bfloat16_rn((float)v);
+    T[((size_t)cell * d.Ppad + j) * d.Kp + e] = __float2bfloat16_rn((float)v);
   }
   const double h = 1.0 / d.nf;
   for (int al = threadIdx.x; al < d.P0; al += blockDim.x) {
@@ -411,14 +620,14 @@ __global__ void pod_affine_parts_kernel(PodDims d, const double* __restrict__ W,
 
 // ------------------------------------------------------------------ online
 
-// a [S][nf][nf] -> Ab [cell][Spad][kPodK] BF16 (zero padded rows and columns)
+// a [S][nf][nf] -> Ab [cell][Spad][Kp] BF16 (zero padded rows and columns)
 __global__ void pod_gather_kernel(PodDims d, const double* __restrict__ a, int S, int Spad,
                                   __nv_bfloat16* __restrict__ Ab) {
-  const long long total = (long long)d.ncell * Spad * kPodK;
+  const long long total = (long long)d.ncell * Spad * d.Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int e = (int)(idx % kPodK);
-    const long long t = idx / kPodK;
+    const int e = (int)(idx % d.Kp);
+    const long long t = idx / d.Kp;
     const int s = (int)(t % Spad), cell = (int)(t / Spad);
     float v = 0.f;
     if (s < S && e < d.ne) {
@@ -432,8 +641,11 @@ __global__ void pod_gather_kernel(PodDims d, const double* __restrict__ a, int S
 constexpr uint32_t kWaitLimit = 1u << 24;  // about 2 s
 
 // G[cell][s][j] = sum_e Ab[cell][s][e] T[cell][j][e]: one CTA per (128-sample
-// tile, cell); both operands staged once into 128-byte-swizzled shared
-// memory, 4 K-steps of 16 per N-chunk of <= 256, accumulator in TMEM.
+// tile, cell); the K dimension (the cell's elements, Kp of them) in steps of
+// 64: both operands' step staged into 128-byte-swizzled shared memory, 4
+// MMAs of K = 16 per N-chunk of <= 256 into one TMEM accumulator, and the
+// step's completion awaited (bounded) on an mbarrier before the next step
+// overwrites the buffers.
 __global__ void __launch_bounds__(128, 1)
 pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
                 const __nv_bfloat16* __restrict__ T, float* __restrict__ G, int32_t* err) {
@@ -444,48 +656,59 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
   unsigned char* sB = smem + kPodTileM * 128;     // Ppad rows x 128 B
   __shared__ uint64_t mbar;
   __shared__ uint32_t taddr_s;
+  __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cell = blockIdx.y;
   const int s0 = blockIdx.x * kPodTileM;
+  const int nk = d.Kp / kPodK;
+  const int rowv = d.Kp / 8;  // 16-byte chunks per operand row
   uint32_t ncols = 32;
   while ((int)ncols < d.Ppad) ncols <<= 1;
   if (warp == 0) tc::tmem_alloc(&taddr_s, ncols);
   if (tid == 0) tc::mbar_init(&mbar, 1);
-  // stage operands (16-byte chunks into the swizzled layout)
-  const uint4* gA = reinterpret_cast<const uint4*>(Ab + ((size_t)cell * Spad + s0) * kPodK);
-  for (int c = tid; c < kPodTileM * 8; c += 128) {
-    const int row = c >> 3, ch = c & 7;
-    *reinterpret_cast<uint4*>(sA + tc::sw128_offset(row, ch * 8)) = gA[c];
-  }
-  const uint4* gB = reinterpret_cast<const uint4*>(T + (size_t)cell * d.Ppad * kPodK);
-  for (int c = tid; c < d.Ppad * 8; c += 128) {
-    const int row = c >> 3, ch = c & 7;
-    *reinterpret_cast<uint4*>(sB + tc::sw128_offset(row, ch * 8)) = gB[c];
-  }
-  tc::fence_proxy_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = taddr_s;
-  if (tid == 0) {
-    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-    for (int nb = 0; nb < d.Ppad; nb += 256) {
-      const int nsz = min(256, d.Ppad - nb);
-      const uint32_t idesc = tc::idesc_bf16_f32(kPodTileM, nsz);
-#pragma unroll
-      for (int kk = 0; kk < kPodK / 16; ++kk) {
-        const uint64_t ad = tc::sdesc_sw128(a0 + kk * 32);
-        const uint64_t bd = tc::sdesc_sw128(b0 + nb * 128 + kk * 32);
-        tc::mma_bf16(taddr + nb, ad, bd, idesc, kk > 0 ? 1u : 0u);
-      }
+  const uint4* gA = reinterpret_cast<const uint4*>(Ab + ((size_t)cell * Spad + s0) * d.Kp);
+  const uint4* gB = reinterpret_cast<const uint4*>(T + (size_t)cell * d.Ppad * d.Kp);
+  bool ok = true;
+  uint32_t taddr = 0;
+  for (int kc = 0; kc < nk; ++kc) {
+    // stage K step kc (16-byte chunks into the swizzled layout)
+    for (int c = tid; c < kPodTileM * 8; c += 128) {
+      const int row = c >> 3, ch = c & 7;
+      *reinterpret_cast<uint4*>(sA + tc::sw128_offset(row, ch * 8)) = gA[(size_t)row * rowv + kc * 8 + ch];
     }
-    tc::mma_commit(&mbar);
+    for (int c = tid; c < d.Ppad * 8; c += 128) {
+      const int row = c >> 3, ch = c & 7;
+      *reinterpret_cast<uint4*>(sB + tc::sw128_offset(row, ch * 8)) = gB[(size_t)row * rowv + kc * 8 + ch];
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    taddr = taddr_s;
+    if (tid == 0) {
+      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+      for (int nb = 0; nb < d.Ppad; nb += 256) {
+        const int nsz = min(256, d.Ppad - nb);
+        const uint32_t idesc = tc::idesc_bf16_f32(kPodTileM, nsz);
+#pragma unroll
+        for (int kk = 0; kk < kPodK / 16; ++kk) {
+          const uint64_t ad = tc::sdesc_sw128(a0 + kk * 32);
+          const uint64_t bd = tc::sdesc_sw128(b0 + nb * 128 + kk * 32);
+          tc::mma_bf16(taddr + nb, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&mbar);
+      s_ok = tc::mbar_wait_bounded(&mbar, kc & 1, kWaitLimit) ? 1 : 0;
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!s_ok) {
+      ok = false;
+      break;
+    }
   }
-  __syncwarp();
-  const bool ok = tc::mbar_wait_bounded(&mbar, 0, kWaitLimit);
-  tc::fence_after_sync();
   if (!ok) {
-    if (lane == 0) atomicOr(err, 2);
+    if (tid == 0) atomicOr(err, 2);
   } else {
     float* Grow = G + ((size_t)cell * Spad + s0 + warp * 32 + lane) * d.Ppad;
     for (int col = 0; col < d.Ppad; col += 16) {
@@ -498,7 +721,7 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+  if (warp == 0) tc::tmem_dealloc(taddr_s, ncols);
 }
 
 // ---- warp r x r Cholesky with 4 right-hand sides (lane q owns row q)
@@ -621,7 +844,7 @@ struct PodSolveArgs {
 };
 
 constexpr int kPodSolveWarps = 4;
-constexpr int kPodN2Max = (kPodMaxRho + 1) * (kPodMaxRho + 1);
+constexpr int kPodN2Max = (kPodMaxRhoSmall + 1) * (kPodMaxRhoSmall + 1);  // refinement: small cells only
 
 // REFINE: the FP64 stencil refinement of c (refine_iters > 0) is compiled
 // into its own kernel, so the unrefined launch carries only its own code;
@@ -930,7 +1153,7 @@ struct stomsfem_pod {
   double* W = nullptr;          // [cell][N2][P0]
   double* wl = nullptr;         // [cell][P0]
   double* lam = nullptr;        // [cell][n]
-  __nv_bfloat16* T = nullptr;   // [cell][Ppad][kPodK]
+  __nv_bfloat16* T = nullptr;   // [cell][Ppad][Kp]
   int32_t* ranks = nullptr;     // [cell]
   int32_t* err = nullptr;       // [1] device error word
 };
@@ -961,6 +1184,12 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
   if (rho < 2 || rho > kPodMaxRho)
     return set_error(STOMSFEM_EINVAL, "POD needs 2 <= H/h <= %d (got %d)", kPodMaxRho, rho);
   if (S_train < 1 || !phi_snap || !a_train) return set_error(STOMSFEM_EINVAL, "no training data");
+  // cells above H/h = 8: the snapshot-space eigenproblem (one shared basis)
+  const bool large = rho > kPodMaxRhoSmall;
+  if (large && per_l) return set_error(STOMSFEM_EINVAL, "per-l bases need H/h <= %d", kPodMaxRhoSmall);
+  if (large && 4 * S_train > kPodSnapMax)
+    return set_error(STOMSFEM_EINVAL, "H/h > %d: at most %d training samples (got %d)", kPodMaxRhoSmall,
+                     kPodSnapMax / 4, S_train);
   const int rank_cap = per_l ? kPodMaxRank / 3 : kPodMaxRank;
   if (max_rank < 1 || max_rank > rank_cap)
     return set_error(STOMSFEM_EINVAL, "max_rank must be in [1, %d]", rank_cap);
@@ -976,6 +1205,7 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
   d.ne = rho * rho;
   d.ncell = grid->nc * grid->nc;
   d.f = grid->f;
+  d.Kp = pod_kp(d.ne);
   const int rcap = max_rank < d.n ? max_rank : d.n;
   const int nslot = per_l ? 3 : 1;  // eigenproblems per cell
   d.per_l = per_l;
@@ -1002,29 +1232,44 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
   TRY(cudaMalloc(&p->W, sizeof(double) * d.ncell * d.N2 * d.P0));
   TRY(cudaMalloc(&p->wl, sizeof(double) * d.ncell * d.P0));
   TRY(cudaMalloc(&p->lam, sizeof(double) * d.ncell * nslot * d.n));
-  TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * kPodK));
+  TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * d.Kp));
   TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell * nslot));
   TRY(cudaMalloc(&p->err, sizeof(int32_t)));
   TRY(cudaMalloc(&phibar, sizeof(double) * d.ncell * 4 * d.N2));
   TRY(cudaMalloc(&abar, sizeof(double) * d.ncell * d.ne));
-  TRY(cudaMalloc(&cov, sizeof(double) * d.ncell * nslot * d.n * d.n));
+  // small cells: the covariances; large cells: the snapshots X and Abar X
+  TRY(cudaMalloc(&cov, large ? sizeof(double) * 2 * d.ncell * d.n * 4 * S_train
+                             : sizeof(double) * d.ncell * nslot * d.n * d.n));
   TRY(cudaMemsetAsync(p->err, 0, sizeof(int32_t), st));
   if (ranks_in) {
     TRY(cudaMalloc(&rin_d, sizeof(int32_t) * d.ncell * nslot));
     TRY(cudaMemcpyAsync(rin_d, ranks_in, sizeof(int32_t) * d.ncell * nslot, cudaMemcpyHostToDevice, st));
   }
   pod_mean_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, a_train, S_train, phibar, abar);
-  if (per_l) {
+  if (large) {
+    double* X = cov;
+    double* Y = cov + (size_t)d.ncell * d.n * 4 * S_train;
+    pod_snap_xy_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, S_train, phibar, abar, X, Y);
+    const size_t snap_smem = sizeof(double) * 2 * kPodSnapMax * (kPodSnapMax + 1);
+    TRY(cudaFuncSetAttribute(pod_snap_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)snap_smem));
+    pod_snap_eig_kernel<<<d.ncell, 256, snap_smem, st>>>(d, X, Y, S_train, phibar, tol, rcap, rin_d, p->W, p->lam,
+                                                         p->ranks);
+    const size_t tl_smem = sizeof(float) * 2 * kPodK * 4 * d.P0;
+    TRY(cudaFuncSetAttribute(pod_tensor_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl_smem));
+    pod_tensor_large_kernel<<<d.ncell, 256, tl_smem, st>>>(d, p->W, p->T, p->wl);
+  } else if (per_l) {
     pod_cov_per_l_kernel<<<dim3(d.ncell, 3), 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
     pod_w_init_kernel<<<d.ncell, 256, 0, st>>>(d, phibar, p->W);
   } else {
     pod_cov_kernel<<<d.ncell, 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
   }
-  const size_t eig_smem = sizeof(double) * 3 * (kPodMaxN + 1) * (kPodMaxN + 1);
-  TRY(cudaFuncSetAttribute(pod_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem));
-  pod_eig_kernel<<<dim3(d.ncell, nslot), 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W, p->lam,
-                                                               p->ranks, p->err);
-  pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->wl);
+  if (!large) {
+    const size_t eig_smem = sizeof(double) * 3 * (kPodMaxN + 1) * (kPodMaxN + 1);
+    TRY(cudaFuncSetAttribute(pod_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem));
+    pod_eig_kernel<<<dim3(d.ncell, nslot), 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W,
+                                                                 p->lam, p->ranks, p->err);
+    pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->wl);
+  }
   TRY(cudaGetLastError());
   int32_t herr = 0;
   TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1078,7 +1323,7 @@ extern "C" int stomsfem_pod_save(const stomsfem_pod* pod, void* host_buf, size_t
   const int nslot = d.per_l ? 3 : 1;
   const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0,
                nlam = (size_t)d.ncell * nslot * d.n;
-  const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
+  const size_t nT = (size_t)d.ncell * d.Ppad * d.Kp;
   std::vector<double> W, wl, lam;
   std::vector<__nv_bfloat16> T;
   std::vector<int32_t> rk;
@@ -1140,9 +1385,11 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   const int rcap = dims[10];
   d.per_l = per_l;
   d.rcl = per_l ? rcap : 0;
+  d.Kp = pod_kp(d.ne);
   // the stored sizes must be the ones the build derives from the grid
   const bool consistent = r.ok && d.nc > 0 && d.nf % d.nc == 0 && d.rho == d.nf / d.nc && d.rho >= 2 &&
-                          d.rho <= kPodMaxRho && d.N2 == (d.rho + 1) * (d.rho + 1) &&
+                          d.rho <= kPodMaxRho && (!per_l || d.rho <= kPodMaxRhoSmall) &&
+                          d.N2 == (d.rho + 1) * (d.rho + 1) &&
                           d.n == (d.rho - 1) * (d.rho - 1) && d.ne == d.rho * d.rho && d.ncell == d.nc * d.nc &&
                           rcap >= 1 && rcap <= d.n && rcap * nslot <= kPodMaxRank && d.P0 == 4 + nslot * rcap &&
                           d.P == d.P0 * (d.P0 + 1) / 2 &&
@@ -1150,7 +1397,7 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
   if (!consistent) return set_error(STOMSFEM_EINVAL, "inconsistent POD checkpoint header");
   const size_t nW = (size_t)d.ncell * d.N2 * d.P0, nwl = (size_t)d.ncell * d.P0,
                nlam = (size_t)d.ncell * nslot * d.n;
-  const size_t nT = (size_t)d.ncell * d.Ppad * kPodK;
+  const size_t nT = (size_t)d.ncell * d.Ppad * d.Kp;
   const size_t need = r.pos + sizeof(double) * (nW + nwl + nlam) + sizeof(__nv_bfloat16) * nT +
                       sizeof(int32_t) * d.ncell * nslot;
   if (buf_bytes < need) return set_error(STOMSFEM_EINVAL, "truncated POD checkpoint (%zu < %zu)", buf_bytes, need);
@@ -1194,7 +1441,7 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
 
 static size_t pod_ws_layout(const PodDims& d, int S, size_t* off_G) {
   const int Spad = (S + kPodTileM - 1) / kPodTileM * kPodTileM;
-  const size_t ab = ((size_t)d.ncell * Spad * kPodK * 2 + 1023) & ~size_t(1023);
+  const size_t ab = ((size_t)d.ncell * Spad * d.Kp * 2 + 1023) & ~size_t(1023);
   *off_G = ab;
   return ab + (size_t)d.ncell * Spad * d.Ppad * 4;
 }
@@ -1212,9 +1459,11 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
                                     stomsfem_stream_t stream) {
   if (!pod) return set_error(STOMSFEM_EINVAL, "pod is NULL");
   if (S < 0 || refine_iters < 0 || refine_iters > 16) return set_error(STOMSFEM_EINVAL, "bad S / refine_iters");
+  const PodDims& d = pod->d;
+  if (refine_iters > 0 && d.rho > kPodMaxRhoSmall)
+    return set_error(STOMSFEM_EINVAL, "the FP64 refinement needs H/h <= %d", kPodMaxRhoSmall);
   if (S == 0) return STOMSFEM_OK;
   if (!a || !Ke || !be || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
-  const PodDims& d = pod->d;
   size_t og;
   const size_t need = pod_ws_layout(d, S, &og);
   if (workspace_bytes < need) return set_error(STOMSFEM_ENOMEM, "POD workspace %zu < %zu", workspace_bytes, need);
@@ -1268,6 +1517,7 @@ extern "C" int stomsfem_pod_set_affine(stomsfem_pod* pod, const stomsfem_grid* g
   if (!pod || !grid || !field) return set_error(STOMSFEM_EINVAL, "NULL argument");
   const PodDims& d = pod->d;
   if (grid->nf != d.nf || grid->nc != d.nc) return set_error(STOMSFEM_EINVAL, "grid does not match the POD handle");
+  if (d.rho > kPodMaxRhoSmall) return set_error(STOMSFEM_EINVAL, "the affine parts need H/h <= %d", kPodMaxRhoSmall);
   if (field->kind != STOMSFEM_FIELD_AFFINE)
     return set_error(STOMSFEM_EINVAL, "the affine reduced basis needs an affine field (kind %d)", STOMSFEM_FIELD_AFFINE);
   if (!(field->width > 0.0) || field->nbx <= 0 || field->nby <= 0) return set_error(STOMSFEM_EINVAL, "bad field");

@@ -1,0 +1,130 @@
+"""Reduced-basis (POD) path at H/h = 32 on the GPU vs the FP64 POD oracle.
+
+At H/h = 32 the GPU solves the KL eigenproblem in snapshot space (the
+4 S_train-wide matrix of the centred snapshots in the energy inner
+product) and the oracle in node space (the covariance of the 961 interior
+nodes, numpy eigh): the two share the nonzero spectrum and, for the ranks
+pinned to the oracle's, the reduced subspace.  Online: the tensor-core GEMM
+runs K = 1024 in 16 steps; K_e and b_e without refinement (BF16 reduced
+matrices) against the oracle's reduced-basis results; the FP64 refinement
+is refused at this size; a checkpoint round trip is bit-identical.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1607_00693_gb300 import api
+from paper_1607_00693_gb300 import workloads as W
+
+DEV = "cuda:0"
+NF, NC, NS = 64, 2, 12
+
+
+def _field():
+    return dict(W.workload("upscale_1024")["field"], nbx=4, nby=4, width=0.125)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import oracle
+    from oracle import pod
+    from paper_1607_00693_gb300.build import build_library
+    oracle.build()
+    build_library()
+    fld = _field()
+    xi = W.draw_xi(fld, NS, 41)
+    a_tr = oracle.sample_coef(NF, fld, xi)
+    _, _, phi_o = oracle.upscale(NF, NC, 1.0, a_tr, want_phi=True)
+    models = pod.build(NF, NC, phi_o, a_tr, tol=1e-6, max_rank=27)
+    ranks = [m["rank"] for m in models]
+    g = api.grid(NF, NC, 1.0)
+    a_t = torch.from_numpy(a_tr).to(DEV)
+    rho = NF // NC
+    Ke = torch.empty((NS, NC * NC, 10), dtype=torch.float64, device=DEV)
+    be = torch.empty((NS, NC * NC, 4), dtype=torch.float64, device=DEV)
+    phi = torch.empty((NS, NC * NC, 4, (rho + 1) ** 2), dtype=torch.float64, device=DEV)
+    api.stomsfem_upscale(g, a_t, Ke, be, phi=phi)
+    h, rk = api.stomsfem_pod_build(g, phi, a_t, ranks=ranks)
+    hfree, rk_free = api.stomsfem_pod_build(g, phi, a_t, tol=1e-6, max_rank=27)
+    a_te = oracle.sample_coef(NF, fld, W.draw_xi(fld, 9, 42))
+    yield dict(oracle=oracle, pod=pod, g=g, models=models, ranks=ranks, h=h, rk=rk, rk_free=rk_free,
+               hfree=hfree, a_te=a_te, phi=phi, a_t=a_t)
+    api.stomsfem_pod_destroy(h)
+    api.stomsfem_pod_destroy(hfree)
+
+
+def _gpu(setup, refine=0, handle=None):
+    g = setup["g"]
+    a = torch.from_numpy(setup["a_te"]).to(DEV)
+    S = a.shape[0]
+    Ke = torch.empty((S, NC * NC, 10), dtype=torch.float64, device=DEV)
+    be = torch.empty((S, NC * NC, 4), dtype=torch.float64, device=DEV)
+    st = torch.full((S, NC * NC), 9, dtype=torch.int32, device=DEV)
+    api.stomsfem_pod_upscale(handle or setup["h"], g, a, Ke, be, refine_iters=refine, unit_status=st)
+    torch.cuda.synchronize()
+    return Ke.cpu().numpy(), be.cpu().numpy(), st.cpu().numpy()
+
+
+def _rel(x, y):
+    return float(np.max(np.linalg.norm(x - y, axis=-1) / np.linalg.norm(y, axis=-1)))
+
+
+def test_large_ranks_and_spectrum(setup):
+    assert setup["rk"] == setup["ranks"]
+    assert max(abs(a - b) for a, b in zip(setup["rk_free"], setup["ranks"])) <= 1
+    lam = api.stomsfem_pod_eigenvalues(setup["h"], setup["g"])
+    m = 4 * NS
+    for cell in range(NC * NC):
+        lo = setup["models"][cell]["lam"]
+        keep = lo / lo[0] > 1e-6
+        np.testing.assert_allclose(lam[cell][:m][keep[:m]], lo[:m][keep[:m]], rtol=1e-6)
+        # the covariance has rank <= 4 S_train: the GPU's eigenvalues past it are 0
+        assert np.all(lam[cell][m:] == 0.0)
+        assert np.all(lo[m:] <= 1e-10 * lo[0])
+
+
+def test_large_unrefined_matches_oracle(setup):
+    Ko, bo = setup["pod"].upscale(setup["models"], NF, NC, 1.0, setup["a_te"])
+    Kg, bg, st = _gpu(setup)
+    assert np.all(st == 0)
+    eK, eb = _rel(Kg, Ko), _rel(bg, bo)
+    Kp, _ = setup["oracle"].upscale(NF, NC, 1.0, setup["a_te"])
+    print("H/h = 32 POD: K_e rel %.3e, b_e rel %.3e vs the oracle's reduced basis; oracle POD vs plain %.3e"
+          % (eK, eb, _rel(Ko, Kp)))
+    assert eK <= 1e-2
+    assert eb <= 1e-2
+    K = Kg.reshape(-1, 10)
+    rows = K[:, 0] + K[:, 1] + K[:, 2] + K[:, 3]
+    assert np.max(np.abs(rows)) <= 1e-4 * np.max(np.abs(K))   # FP32 reduced quantities
+
+
+def test_large_refinement_refused(setup):
+    with pytest.raises(Exception):
+        _gpu(setup, refine=1)
+
+
+def test_large_checkpoint_roundtrip(setup):
+    data = api.stomsfem_pod_save(setup["h"])
+    h2 = api.stomsfem_pod_load(data)
+    try:
+        K1, b1, _ = _gpu(setup)
+        K2, b2, _ = _gpu(setup, handle=h2)
+        np.testing.assert_array_equal(K1, K2)
+        np.testing.assert_array_equal(b1, b2)
+    finally:
+        api.stomsfem_pod_destroy(h2)
+
+
+def test_large_build_limits(setup):
+    g = setup["g"]
+    phi = setup["phi"]
+    a_t = setup["a_t"]
+    with pytest.raises(Exception):   # per-l bases: small cells only
+        api.stomsfem_pod_build_per_l(g, phi, a_t, tol=1e-6, max_rank_per_l=9)
+    big_phi = phi.repeat(2, 1, 1, 1)   # 24 training samples: above the snapshot limit of 16
+    big_a = a_t.repeat(2, 1, 1)
+    with pytest.raises(Exception):
+        api.stomsfem_pod_build(g, big_phi, big_a, tol=1e-6, max_rank=27)
