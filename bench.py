@@ -35,17 +35,16 @@ from paper_1607_00693_gb300 import workloads as W  # noqa: E402
 FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
 
 # Measured DRAM traffic per unit of the upscale kernel (ncu, 32 samples of
-# the H/h = 32 workload), by library version and form.  The counters were
-# taken on 0.6; 0.7 adds calls (mixed boundary data, oscillatory cell data)
-# and leaves the upscale kernels these figures describe as they were (same
-# source path, same registers and spills for every instantiation).
-_UPSCALE_TRAFFIC = {
-    # FP32: the forward-only and the back-substitution launches of one call
-    "fp32": (0.051981e9 + 0.000175e9 + 7.110618e9 + 6.763874e9) / 32768,
-    "fp64": (1.827271e9 + 1.937667e9) / 4096,
-}
-DRAM_BYTES_PER_UNIT = {(v, f): b for v in ("stomsfem-gb300 0.6 (sm_103a)", "stomsfem-gb300 0.7 (sm_103a)")
-                       for f, b in _UPSCALE_TRAFFIC.items()}
+# the H/h = 32 workload, the forward-only and the back-substitution launches
+# of one FP32 call), by library version and form: 0.6 and 0.7 share one
+# kernel (counters taken on 0.6); 0.8 changed the factorisation window's
+# layout (counters retaken on 0.8; FP64 not retaken).
+_TRAFFIC_06 = {"fp32": (0.051981e9 + 0.000175e9 + 7.110618e9 + 6.763874e9) / 32768,
+               "fp64": (1.827271e9 + 1.937667e9) / 4096}
+_TRAFFIC_08 = {"fp32": (0.051976e9 + 0.000239e9 + 7.124753e9 + 6.771178e9) / 32768}
+DRAM_BYTES_PER_UNIT = {("stomsfem-gb300 %s (sm_103a)" % v, f): b
+                       for v, t in (("0.6", _TRAFFIC_06), ("0.7", _TRAFFIC_06), ("0.8", _TRAFFIC_08))
+                       for f, b in t.items()}
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
 
@@ -325,12 +324,23 @@ def bench_pod(api, dev, stream, samples=None):
                                                          be[:256].contiguous(), Kp[:256].contiguous(),
                                                          bp[:256].contiguous(), dev),
                     "tensor_tflops_lower_bound": gemm_flops / (ms / 1e3) / 1e12}
+    # the same unrefined call with one BF16 product per K step instead of the
+    # default BF16 pairs (three products)
+    api.stomsfem_pod_set_gemm_split(h, 0)
+    ms = _timed_call(stream, lambda: api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=0,
+                                                              workspace=wsp, stream=stream))
+    api.stomsfem_pod_set_gemm_split(h, 1)
+    res["refined0_one_bf16_pass"] = {
+        "units_per_s": S * nc * nc / (ms / 1e3), "ms": ms,
+        "Ke_rel_vs_plain": float(((Ke - Kp).norm(dim=2) / Kp.norm(dim=2)).max().item()),
+        "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:256].contiguous(), be[:256].contiguous(),
+                                             Kp[:256].contiguous(), bp[:256].contiguous(), dev)}
     api.stomsfem_pod_destroy(h)
     peaks = _peaks()
     res["roofline_note"] = ("GEMM flops of the whole call / whole-call time vs bf16 %.0f TFLOP/s "
                             "(measured burst): launch- and FP64-epilogue-bound at this size"
                             % peaks.get("bf16_tflops", 1900.0))
-    return res, 4 + 2 * 3 * 4
+    return res, 4 + 3 * 3 * 4
 
 
 def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
@@ -401,6 +411,7 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
     Ke = torch.empty((batch, ncell, 10), dtype=torch.float64, device=dev)
     be = torch.empty((batch, ncell, 4), dtype=torch.float64, device=dev)
     u = torch.empty((batch, nn), dtype=torch.float64, device=dev)
+    pst = torch.zeros((batch, ncell), dtype=torch.int32, device=dev)
     wsp = torch.empty(api.stomsfem_pod_workspace_size(h, batch), dtype=torch.uint8, device=dev)
     wsc = torch.empty(api.stomsfem_coarse_workspace_size(g, batch), dtype=torch.uint8, device=dev)
     evs = []
@@ -409,7 +420,7 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
         api.stomsfem_sample_coef(g, fld, xi, a, stream=stream)
         if ev is not None:
             ev[0].record(stream)
-        api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=0, workspace=wsp, stream=stream)
+        api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=0, unit_status=pst, workspace=wsp, stream=stream)
         if ev is not None:
             ev[1].record(stream)
         api.stomsfem_coarse_solve(g, Ke, be, u, workspace=wsc, stream=stream)
@@ -435,6 +446,7 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
                   "train_samples": n_train, "build_s": t_build, "rank_min": int(min(ranks)),
                   "rank_max": int(max(ranks)), "rank_mean": float(sum(ranks) / len(ranks)),
                   "pod_upscale_ms": ms_up, "gemm_tensor_tflops_whole_call": gemm_flops / (ms_up / 1e3) / 1e12,
+                  "failed_units": int((pst != 0).sum().item()),
                   "refinement": "none (FP64 refinement is offered for H/h <= 8)"}
     api.stomsfem_pod_destroy(h)
     out["note"] = ("surrogate and random interpolation: a cell of this workload sees more than 16 local "

@@ -616,7 +616,10 @@ int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* byte
 /* Online stage (Alg. 4) for S samples a (device [S][nf][nf] float64):
  * G = W^T A(omega) W for the extended basis W = [phibar, V] as one
  * tensor-core GEMM per cell (BF16 operands, FP32 accumulation; K = the
- * cell's rho^2 elements in steps of 64), the r x r
+ * cell's rho^2 elements in steps of 64; by default each operand carried as
+ * a BF16 pair, value and BF16 of the remainder, and three products
+ * summed, about 16 significant bits in G: see stomsfem_pod_set_gemm_split),
+ * the r x r
  * Galerkin system (V^T A V) c_l = -V^T A phibar_l in FP32, then
  * refine_iters FP64 refinement steps whose residual is formed with the fine
  * 9-point stencil of A(omega) (0 = none: K_e and b_e from the FP32 reduced
@@ -627,6 +630,15 @@ int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* byte
 int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t S, int32_t refine_iters,
                          double* Ke, double* be, int32_t* unit_status, void* workspace,
                          size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* The online GEMM's operand precision (no paper counterpart): split = 1
+ * (the default) both operands as BF16 (hi, lo) pairs and three tensor-core
+ * products per K step (hi hi + hi lo + lo hi); split = 0 one BF16 product
+ * (8 significant bits in G: enough where the reduced matrices are well
+ * conditioned, e.g. the H/h = 8 workloads; at contrast 10^4 and H/h = 32
+ * the reduced Cholesky then meets non-positive pivots).  EINVAL for a NULL
+ * handle or another value. */
+int stomsfem_pod_set_gemm_split(stomsfem_pod* pod, int32_t split);
 
 /* Affine structure of the coefficient (Sec. 3.2.2, Eqs. RBaffine and
  * localAF) for an affine field (field->kind == STOMSFEM_FIELD_AFFINE,

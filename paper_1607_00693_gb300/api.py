@@ -208,6 +208,10 @@ def stomsfem_pod_eigenvalues(h, g: Grid, per_l=False):
     return lam
 
 
+def stomsfem_pod_set_gemm_split(h, split=1):
+    L.check(L.lib().stomsfem_pod_set_gemm_split(h, int(split)))
+
+
 def stomsfem_pod_workspace_size(h, S):
     b = ctypes.c_size_t()
     L.check(L.lib().stomsfem_pod_workspace_size(h, int(S), ctypes.byref(b)))

@@ -481,7 +481,7 @@ __global__ void pod_snap_eig_kernel(PodDims d, const double* __restrict__ X, con
 // writing consecutive elements of one pair (coalesced rows).  The load
 // terms wl as in pod_tensor_kernel (FP64).
 __global__ void pod_tensor_large_kernel(PodDims d, const double* __restrict__ W, __nv_bfloat16* __restrict__ T,
-                                        double* __restrict__ wl) {
+                                        __nv_bfloat16* __restrict__ Tlo, double* __restrict__ wl) {
   extern __shared__ float tl_smem[];
   float* w = tl_smem;                       // [64][4][P0]
   float* kw = tl_smem + kPodK * 4 * d.P0;   // [64][4][P0]
@@ -525,7 +525,9 @@ __global__ void pod_tensor_large_kernel(PodDims d, const double* __restrict__ W,
 #pragma unroll
         for (int r = 0; r < 4; ++r) v = fmaf(w[(el * 4 + r) * P0 + a], kw[(el * 4 + r) * P0 + b], v);
       }
-      T[((size_t)cell * d.Ppad + j) * d.Kp + e0 + el] = __float2bfloat16_rn(v);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      T[((size_t)cell * d.Ppad + j) * d.Kp + e0 + el] = hi;
+      Tlo[((size_t)cell * d.Ppad + j) * d.Kp + e0 + el] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
   }
   const double h = 1.0 / d.nf;
@@ -542,7 +544,7 @@ __global__ void pod_tensor_large_kernel(PodDims d, const double* __restrict__ W,
 // T[cell][j][e] (BF16, K-major rows of Kp = 64 elements: small cells) and the load terms
 // wl[cell][alpha] = f int Wfull_alpha.
 __global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_bfloat16* __restrict__ T,
-                                  double* __restrict__ wl) {
+                                  __nv_bfloat16* __restrict__ Tlo, double* __restrict__ wl) {
   const int cell = blockIdx.x;
   const double* Wc = W + (size_t)cell * d.N2 * d.P0;
   const int rho = d.rho;
@@ -564,7 +566,9 @@ __global__ void pod_tensor_kernel(PodDims d, const double* __restrict__ W, __nv_
         for (int c = 0; c < 4; ++c) v += wa * kKref[r][c] * Wc[(size_t)nodes[c] * d.P0 + b];
       }
     }
-    T[((size_t)cell * d.Ppad + j) * d.Kp + e] = __float2bfloat16_rn((float)v);
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+    T[((size_t)cell * d.Ppad + j) * d.Kp + e] = hi;
+    Tlo[((size_t)cell * d.Ppad + j) * d.Kp + e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
   }
   const double h = 1.0 / d.nf;
   for (int al = threadIdx.x; al < d.P0; al += blockDim.x) {
@@ -620,9 +624,10 @@ __global__ void pod_affine_parts_kernel(PodDims d, const double* __restrict__ W,
 
 // ------------------------------------------------------------------ online
 
-// a [S][nf][nf] -> Ab [cell][Spad][Kp] BF16 (zero padded rows and columns)
+// a [S][nf][nf] -> Ab [cell][Spad][Kp] BF16 and its remainder Ablo = BF16(a -
+// Ab) (zero padded rows and columns)
 __global__ void pod_gather_kernel(PodDims d, const double* __restrict__ a, int S, int Spad,
-                                  __nv_bfloat16* __restrict__ Ab) {
+                                  __nv_bfloat16* __restrict__ Ab, __nv_bfloat16* __restrict__ Ablo) {
   const long long total = (long long)d.ncell * Spad * d.Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -634,7 +639,9 @@ __global__ void pod_gather_kernel(PodDims d, const double* __restrict__ a, int S
       const int cx = cell % d.nc, cy = cell / d.nc, ex = e % d.rho, ey = e / d.rho;
       v = (float)a[((size_t)s * d.nf + cy * d.rho + ey) * d.nf + cx * d.rho + ex];
     }
-    Ab[idx] = __float2bfloat16_rn(v);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    Ab[idx] = hi;
+    Ablo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
@@ -642,18 +649,23 @@ constexpr uint32_t kWaitLimit = 1u << 24;  // about 2 s
 
 // G[cell][s][j] = sum_e Ab[cell][s][e] T[cell][j][e]: one CTA per (128-sample
 // tile, cell); the K dimension (the cell's elements, Kp of them) in steps of
-// 64: both operands' step staged into 128-byte-swizzled shared memory, 4
+// 64: the operands' step staged into 128-byte-swizzled shared memory, 4
 // MMAs of K = 16 per N-chunk of <= 256 into one TMEM accumulator, and the
 // step's completion awaited (bounded) on an mbarrier before the next step
-// overwrites the buffers.
+// overwrites the buffers.  split: both operands as BF16 pairs (hi, lo =
+// BF16 of the remainder) and three products per step, Ab T + Ab Tlo + Ablo
+// T (the dropped Ablo Tlo is below 2^-16 relative), so G carries about
+// 16 bits instead of BF16's 8; one product otherwise.
 __global__ void __launch_bounds__(128, 1)
-pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
-                const __nv_bfloat16* __restrict__ T, float* __restrict__ G, int32_t* err) {
+pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab, const __nv_bfloat16* __restrict__ Ablo,
+                const __nv_bfloat16* __restrict__ T, const __nv_bfloat16* __restrict__ Tlo, int split,
+                float* __restrict__ G, int32_t* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sA = smem;                       // 128 rows x 128 B
-  unsigned char* sB = smem + kPodTileM * 128;     // Ppad rows x 128 B
+  // sA[0..1]: 128 rows x 128 B each; sB[0..1]: Ppad rows x 128 B each
+  unsigned char* sA[2] = {smem, smem + kPodTileM * 128};
+  unsigned char* sB[2] = {smem + 2 * kPodTileM * 128, smem + 2 * kPodTileM * 128 + (size_t)d.Ppad * 128};
   __shared__ uint64_t mbar;
   __shared__ uint32_t taddr_s;
   __shared__ int s_ok;
@@ -662,23 +674,30 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
   const int s0 = blockIdx.x * kPodTileM;
   const int nk = d.Kp / kPodK;
   const int rowv = d.Kp / 8;  // 16-byte chunks per operand row
+  const int nparts = split ? 2 : 1;
   uint32_t ncols = 32;
   while ((int)ncols < d.Ppad) ncols <<= 1;
   if (warp == 0) tc::tmem_alloc(&taddr_s, ncols);
   if (tid == 0) tc::mbar_init(&mbar, 1);
-  const uint4* gA = reinterpret_cast<const uint4*>(Ab + ((size_t)cell * Spad + s0) * d.Kp);
-  const uint4* gB = reinterpret_cast<const uint4*>(T + (size_t)cell * d.Ppad * d.Kp);
+  const uint4* gA[2] = {reinterpret_cast<const uint4*>(Ab + ((size_t)cell * Spad + s0) * d.Kp),
+                        reinterpret_cast<const uint4*>(Ablo + ((size_t)cell * Spad + s0) * d.Kp)};
+  const uint4* gB[2] = {reinterpret_cast<const uint4*>(T + (size_t)cell * d.Ppad * d.Kp),
+                        reinterpret_cast<const uint4*>(Tlo + (size_t)cell * d.Ppad * d.Kp)};
   bool ok = true;
   uint32_t taddr = 0;
   for (int kc = 0; kc < nk; ++kc) {
     // stage K step kc (16-byte chunks into the swizzled layout)
-    for (int c = tid; c < kPodTileM * 8; c += 128) {
-      const int row = c >> 3, ch = c & 7;
-      *reinterpret_cast<uint4*>(sA + tc::sw128_offset(row, ch * 8)) = gA[(size_t)row * rowv + kc * 8 + ch];
-    }
-    for (int c = tid; c < d.Ppad * 8; c += 128) {
-      const int row = c >> 3, ch = c & 7;
-      *reinterpret_cast<uint4*>(sB + tc::sw128_offset(row, ch * 8)) = gB[(size_t)row * rowv + kc * 8 + ch];
+    for (int part = 0; part < nparts; ++part) {
+      for (int c = tid; c < kPodTileM * 8; c += 128) {
+        const int row = c >> 3, ch = c & 7;
+        *reinterpret_cast<uint4*>(sA[part] + tc::sw128_offset(row, ch * 8)) =
+            gA[part][(size_t)row * rowv + kc * 8 + ch];
+      }
+      for (int c = tid; c < d.Ppad * 8; c += 128) {
+        const int row = c >> 3, ch = c & 7;
+        *reinterpret_cast<uint4*>(sB[part] + tc::sw128_offset(row, ch * 8)) =
+            gB[part][(size_t)row * rowv + kc * 8 + ch];
+      }
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -686,15 +705,20 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab,
     tc::fence_after_sync();
     taddr = taddr_s;
     if (tid == 0) {
-      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-      for (int nb = 0; nb < d.Ppad; nb += 256) {
-        const int nsz = min(256, d.Ppad - nb);
-        const uint32_t idesc = tc::idesc_bf16_f32(kPodTileM, nsz);
+      // products (A part, B part): (0, 0), then with split (0, 1) and (1, 0)
+      const int nprod = split ? 3 : 1;
+      for (int pr = 0; pr < nprod; ++pr) {
+        const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+        const uint32_t a0 = tc::smem_u32(sA[pa]), b0 = tc::smem_u32(sB[pb]);
+        for (int nb = 0; nb < d.Ppad; nb += 256) {
+          const int nsz = min(256, d.Ppad - nb);
+          const uint32_t idesc = tc::idesc_bf16_f32(kPodTileM, nsz);
 #pragma unroll
-        for (int kk = 0; kk < kPodK / 16; ++kk) {
-          const uint64_t ad = tc::sdesc_sw128(a0 + kk * 32);
-          const uint64_t bd = tc::sdesc_sw128(b0 + nb * 128 + kk * 32);
-          tc::mma_bf16(taddr + nb, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kPodK / 16; ++kk) {
+            const uint64_t ad = tc::sdesc_sw128(a0 + kk * 32);
+            const uint64_t bd = tc::sdesc_sw128(b0 + nb * 128 + kk * 32);
+            tc::mma_bf16(taddr + nb, ad, bd, idesc, (kc > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+          }
         }
       }
       tc::mma_commit(&mbar);
@@ -1154,6 +1178,8 @@ struct stomsfem_pod {
   double* wl = nullptr;         // [cell][P0]
   double* lam = nullptr;        // [cell][n]
   __nv_bfloat16* T = nullptr;   // [cell][Ppad][Kp]
+  __nv_bfloat16* Tlo = nullptr; // [cell][Ppad][Kp]: BF16 of T's remainder
+  int split = 1;                // online GEMM with the BF16 remainders (three products)
   int32_t* ranks = nullptr;     // [cell]
   int32_t* err = nullptr;       // [1] device error word
 };
@@ -1167,6 +1193,7 @@ static void pod_free(stomsfem_pod* p) {
   cudaFree(p->wl);
   cudaFree(p->lam);
   cudaFree(p->T);
+  cudaFree(p->Tlo);
   cudaFree(p->ranks);
   cudaFree(p->err);
   delete p;
@@ -1233,6 +1260,7 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
   TRY(cudaMalloc(&p->wl, sizeof(double) * d.ncell * d.P0));
   TRY(cudaMalloc(&p->lam, sizeof(double) * d.ncell * nslot * d.n));
   TRY(cudaMalloc(&p->T, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * d.Kp));
+  TRY(cudaMalloc(&p->Tlo, sizeof(__nv_bfloat16) * d.ncell * d.Ppad * d.Kp));
   TRY(cudaMalloc(&p->ranks, sizeof(int32_t) * d.ncell * nslot));
   TRY(cudaMalloc(&p->err, sizeof(int32_t)));
   TRY(cudaMalloc(&phibar, sizeof(double) * d.ncell * 4 * d.N2));
@@ -1256,7 +1284,7 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
                                                          p->ranks);
     const size_t tl_smem = sizeof(float) * 2 * kPodK * 4 * d.P0;
     TRY(cudaFuncSetAttribute(pod_tensor_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl_smem));
-    pod_tensor_large_kernel<<<d.ncell, 256, tl_smem, st>>>(d, p->W, p->T, p->wl);
+    pod_tensor_large_kernel<<<d.ncell, 256, tl_smem, st>>>(d, p->W, p->T, p->Tlo, p->wl);
   } else if (per_l) {
     pod_cov_per_l_kernel<<<dim3(d.ncell, 3), 256, 0, st>>>(d, phi_snap, S_train, phibar, cov);
     pod_w_init_kernel<<<d.ncell, 256, 0, st>>>(d, phibar, p->W);
@@ -1268,7 +1296,7 @@ static int pod_build_impl(const stomsfem_grid* grid, const double* phi_snap, con
     TRY(cudaFuncSetAttribute(pod_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig_smem));
     pod_eig_kernel<<<dim3(d.ncell, nslot), 256, eig_smem, st>>>(d, cov, phibar, abar, tol, rcap, rin_d, p->W,
                                                                  p->lam, p->ranks, p->err);
-    pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->wl);
+    pod_tensor_kernel<<<d.ncell, 256, 0, st>>>(d, p->W, p->T, p->Tlo, p->wl);
   }
   TRY(cudaGetLastError());
   int32_t herr = 0;
@@ -1434,22 +1462,37 @@ extern "C" int stomsfem_pod_load(const void* host_buf, size_t buf_bytes, stomsfe
     }
   TRY(cudaMemcpy(p->ranks, rk.data(), sizeof(int32_t) * d.ncell * nslot, cudaMemcpyHostToDevice));
   TRY(cudaMemset(p->err, 0, sizeof(int32_t)));
+  // T's BF16 remainders are not stored: the build's kernel recomputes them
+  // (and the same T and wl) from W
+  TRY(cudaMalloc(&p->Tlo, sizeof(__nv_bfloat16) * nT));
+  if (d.rho > kPodMaxRhoSmall) {
+    const size_t tl_smem = sizeof(float) * 2 * kPodK * 4 * d.P0;
+    TRY(cudaFuncSetAttribute(pod_tensor_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tl_smem));
+    pod_tensor_large_kernel<<<d.ncell, 256, tl_smem>>>(d, p->W, p->T, p->Tlo, p->wl);
+  } else {
+    pod_tensor_kernel<<<d.ncell, 256>>>(d, p->W, p->T, p->Tlo, p->wl);
+  }
+  TRY(cudaGetLastError());
+  TRY(cudaDeviceSynchronize());
 #undef TRY
   *out = p;
   return STOMSFEM_OK;
 }
 
-static size_t pod_ws_layout(const PodDims& d, int S, size_t* off_G) {
+// Workspace: Ab, Ablo ([cell][Spad][Kp] BF16 each), then G [cell][Spad][Ppad]
+// FP32.
+static size_t pod_ws_layout(const PodDims& d, int S, size_t* off_lo, size_t* off_G) {
   const int Spad = (S + kPodTileM - 1) / kPodTileM * kPodTileM;
   const size_t ab = ((size_t)d.ncell * Spad * d.Kp * 2 + 1023) & ~size_t(1023);
-  *off_G = ab;
-  return ab + (size_t)d.ncell * Spad * d.Ppad * 4;
+  *off_lo = ab;
+  *off_G = 2 * ab;
+  return 2 * ab + (size_t)d.ncell * Spad * d.Ppad * 4;
 }
 
 extern "C" int stomsfem_pod_workspace_size(const stomsfem_pod* pod, int32_t S, size_t* bytes) {
   if (!pod || S < 0 || !bytes) return set_error(STOMSFEM_EINVAL, "bad arguments");
-  size_t og;
-  *bytes = pod_ws_layout(pod->d, S, &og);
+  size_t ol, og;
+  *bytes = pod_ws_layout(pod->d, S, &ol, &og);
   return STOMSFEM_OK;
 }
 
@@ -1464,22 +1507,24 @@ extern "C" int stomsfem_pod_upscale(stomsfem_pod* pod, const double* a, int32_t 
     return set_error(STOMSFEM_EINVAL, "the FP64 refinement needs H/h <= %d", kPodMaxRhoSmall);
   if (S == 0) return STOMSFEM_OK;
   if (!a || !Ke || !be || !workspace) return set_error(STOMSFEM_EINVAL, "NULL device pointer");
-  size_t og;
-  const size_t need = pod_ws_layout(d, S, &og);
+  size_t ol, og;
+  const size_t need = pod_ws_layout(d, S, &ol, &og);
   if (workspace_bytes < need) return set_error(STOMSFEM_ENOMEM, "POD workspace %zu < %zu", workspace_bytes, need);
   const int Spad = (S + kPodTileM - 1) / kPodTileM * kPodTileM;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   auto* Ab = reinterpret_cast<__nv_bfloat16*>(workspace);
+  auto* Ablo = reinterpret_cast<__nv_bfloat16*>(static_cast<unsigned char*>(workspace) + ol);
   float* G = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + og);
   const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
-  pod_gather_kernel<<<sms * 8, 256, 0, st>>>(d, a, S, Spad, Ab);
+  pod_gather_kernel<<<sms * 8, 256, 0, st>>>(d, a, S, Spad, Ab, Ablo);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
-  const size_t smem = 1024 + (size_t)kPodTileM * 128 + (size_t)d.Ppad * 128;
+  const int parts = pod->split ? 2 : 1;
+  const size_t smem = 1024 + parts * ((size_t)kPodTileM * 128 + (size_t)d.Ppad * 128);
   const size_t smem_req = smem < 120 * 1024 ? 120 * 1024 : smem;  // one CTA per SM (TMEM)
   STOMSFEM_TRY_CUDA(cudaFuncSetAttribute(pod_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_req));
   dim3 grd(Spad / kPodTileM, d.ncell);
-  pod_gemm_kernel<<<grd, 128, smem_req, st>>>(d, Spad, Ab, pod->T, G, pod->err);
+  pod_gemm_kernel<<<grd, 128, smem_req, st>>>(d, Spad, Ab, Ablo, pod->T, pod->Tlo, pod->split, G, pod->err);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   PodSolveArgs A;
   A.d = d;
@@ -1628,4 +1673,10 @@ extern "C" int stomsfem_build_pod(const stomsfem_grid* grid, const double* phi_s
                                   int32_t S_train, double tol, int32_t max_rank, const int32_t* ranks_in,
                                   stomsfem_pod** out, int32_t* ranks_out, stomsfem_stream_t stream) {
   return stomsfem_pod_build(grid, phi_snap, a_train, S_train, tol, max_rank, ranks_in, out, ranks_out, stream);
+}
+
+extern "C" int stomsfem_pod_set_gemm_split(stomsfem_pod* pod, int32_t split) {
+  if (!pod || split < 0 || split > 1) return set_error(STOMSFEM_EINVAL, "pod NULL or split not 0 / 1");
+  pod->split = split;
+  return STOMSFEM_OK;
 }

@@ -6,7 +6,8 @@ product) and the oracle in node space (the covariance of the 961 interior
 nodes, numpy eigh): the two share the nonzero spectrum and, for the ranks
 pinned to the oracle's, the reduced subspace.  Online: the tensor-core GEMM
 runs K = 1024 in 16 steps; K_e and b_e without refinement (BF16 reduced
-matrices) against the oracle's reduced-basis results; the FP64 refinement
+pairs by default, one BF16 pass on request) against the oracle's
+reduced-basis results; the FP64 refinement
 is refused at this size; a checkpoint round trip is bit-identical.
 """
 import numpy as np
@@ -92,10 +93,16 @@ def test_large_unrefined_matches_oracle(setup):
     assert np.all(st == 0)
     eK, eb = _rel(Kg, Ko), _rel(bg, bo)
     Kp, _ = setup["oracle"].upscale(NF, NC, 1.0, setup["a_te"])
-    print("H/h = 32 POD: K_e rel %.3e, b_e rel %.3e vs the oracle's reduced basis; oracle POD vs plain %.3e"
-          % (eK, eb, _rel(Ko, Kp)))
-    assert eK <= 1e-2
-    assert eb <= 1e-2
+    api.stomsfem_pod_set_gemm_split(setup["h"], 0)
+    try:
+        K1, _, _ = _gpu(setup)
+    finally:
+        api.stomsfem_pod_set_gemm_split(setup["h"], 1)
+    print("H/h = 32 POD: K_e rel %.3e (one BF16 pass %.3e), b_e rel %.3e vs the oracle's reduced basis; "
+          "oracle POD vs plain %.3e" % (eK, _rel(K1, Ko), eb, _rel(Ko, Kp)))
+    assert eK <= 1e-4
+    assert eb <= 1e-4
+    assert _rel(K1, Ko) <= 5e-3
     K = Kg.reshape(-1, 10)
     rows = K[:, 0] + K[:, 1] + K[:, 2] + K[:, 3]
     assert np.max(np.abs(rows)) <= 1e-4 * np.max(np.abs(K))   # FP32 reduced quantities
