@@ -343,7 +343,7 @@ def bench_pod(api, dev, stream, samples=None):
     return res, 4 + 3 * 3 * 4
 
 
-def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=8):
+def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
     """The high-contrast comparison (contrast_2048: 2048^2 fine, 64^2 coarse,
     H/h = 32, contrast 10^4, xi ~ N(0,1), no oversampling): plain FP64, the
     FP32 form, FP32 + one refinement sweep (tuned plans, one graph per
@@ -991,6 +991,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-forms", action="store_true",
                     help="skip the reduced-basis, surrogate and interpolation measurements")
+    ap.add_argument("--contrast-batch", type=int, default=128, help="samples per step of the contrast_2048 arms")
+    ap.add_argument("--contrast-train", type=int, default=24, help="POD training samples on contrast_2048 (<= 24)")
+    ap.add_argument("--sections", default="",
+                    help="comma-separated subset of the extra sections (engines, petrov_galerkin, pod, surrogate, "
+                         "ri, pod_affine, two_level_mc, two_level_mc_1024, contrast_2048, mixed_bc, "
+                         "oscillatory_bc); default all")
     ap.add_argument("--pod-samples", type=int, default=None, help="online POD samples (default 10^4)")
     ap.add_argument("--sg-samples", type=int, default=None, help="surrogate inference samples (default 10^5)")
     ap.add_argument("--sg-steps", type=int, default=3000, help="surrogate training steps")
@@ -1231,20 +1237,36 @@ def main():
 
     extra = {}
     if not args.no_extra_forms:
-        extra["engines"] = bench_engines(api, g, fld, ov_t, mo, min(B, 256), nn, stream, dev, xs_for, u64, Bc)
-        extra["petrov_galerkin"] = bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for,
-                                            args.pg_batch, Bc, u64)
-        extra["pod"], n1 = bench_pod(api, dev, stream, args.pod_samples)
-        extra["surrogate"], n2 = bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)
-        extra["ri"], n3 = bench_ri(api, dev, stream, args.ri_samples)
-        extra["pod_affine"], n4 = bench_pod_affine(api, dev, stream, args.pod_samples)
-        extra["two_level_mc"] = bench_two_level(api, dev, stream)
-        extra["two_level_mc_1024"] = bench_two_level_1024(api, dev, stream, ov)
-        extra["contrast_2048"] = bench_contrast(api, dev, stream)
-        extra["mixed_bc"] = bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)
-        extra["oscillatory_bc"] = dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form], stream))
+        # the other forms and paths, each outside the headline's timed region
+        # (--sections picks a subset by name)
+        want = set(args.sections.split(",")) if args.sections else None
+        counts = {}
+        sections = [
+            ("engines", lambda: bench_engines(api, g, fld, ov_t, mo, min(B, 256), nn, stream, dev, xs_for, u64,
+                                              Bc)),
+            ("petrov_galerkin", lambda: bench_pg(api, g, fld, ov_t, mo, nf, ncell, nn, stream, dev, xs_for,
+                                                 args.pg_batch, Bc, u64)),
+            ("pod", lambda: bench_pod(api, dev, stream, args.pod_samples)),
+            ("surrogate", lambda: bench_surrogate(api, dev, stream, args.sg_samples, args.sg_steps)),
+            ("ri", lambda: bench_ri(api, dev, stream, args.ri_samples)),
+            ("pod_affine", lambda: bench_pod_affine(api, dev, stream, args.pod_samples)),
+            ("two_level_mc", lambda: bench_two_level(api, dev, stream)),
+            ("two_level_mc_1024", lambda: bench_two_level_1024(api, dev, stream, ov)),
+            ("contrast_2048", lambda: bench_contrast(api, dev, stream, batch=args.contrast_batch,
+                                                     n_train=args.contrast_train)),
+            ("mixed_bc", lambda: bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)),
+            ("oscillatory_bc", lambda: dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form],
+                                                                           stream))),
+        ]
+        for name, fn in sections:
+            if want is not None and name not in want:
+                continue
+            r = fn()
+            if name in ("pod", "surrogate", "ri", "pod_affine"):
+                r, counts[name] = r
+            extra[name] = r
         # kernels of each form's own timed calls (outside the step's timed region)
-        for k, n in (("pod", n1), ("surrogate", n2), ("ri", n3), ("pod_affine", n4)):
+        for k, n in counts.items():
             extra[k]["gpu_launches_timed_calls"] = n
 
     cpu = None

@@ -557,7 +557,7 @@ typedef struct stomsfem_pod stomsfem_pod; /* opaque, owned by the library */
  * 8 < rho <= 32 it is solved in snapshot space (the 4 S_train x 4 S_train
  * matrix X^T Abar X / (4 S_train) of the centred snapshots X, whose
  * nonzero eigenvalues are the covariance's, modes X v / sqrt(4 S_train
- * lambda)): S_train <= 16 there, and the eigenvalues past 4 S_train read 0.
+ * lambda)): S_train <= 24 there, and the eigenvalues past 4 S_train read 0.
  * Allocates the handle's device memory and synchronises `stream` before
  * returning.  Errors: EINVAL, ENOTSPD (training-mean energy matrix, rho <=
  * 8), ECUDA. */

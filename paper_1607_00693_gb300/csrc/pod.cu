@@ -33,7 +33,7 @@ namespace stomsfem {
 constexpr int kPodMaxRhoSmall = 8;  // the covariance eigensolver, refinement, affine and per-l bases
 constexpr int kPodMaxRho = 32;      // elements per cell side (1024 elements: 16 K steps of 64)
 constexpr int kPodMaxN = 49;        // interior nodes of a small cell, (rho - 1)^2
-constexpr int kPodSnapMax = 64;     // large cells: snapshot columns (4 x training samples)
+constexpr int kPodSnapMax = 96;     // large cells: snapshot columns (4 x training samples)
 constexpr int kPodMaxRank = 27;    // (4 + r)(5 + r)/2 <= 496 packed entries fit 512 TMEM columns
 constexpr int kPodK = 64;          // elements per GEMM K step (one 128-byte BF16 row)
 constexpr int kPodTileM = 128;

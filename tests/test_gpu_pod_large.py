@@ -131,7 +131,7 @@ def test_large_build_limits(setup):
     a_t = setup["a_t"]
     with pytest.raises(Exception):   # per-l bases: small cells only
         api.stomsfem_pod_build_per_l(g, phi, a_t, tol=1e-6, max_rank_per_l=9)
-    big_phi = phi.repeat(2, 1, 1, 1)   # 24 training samples: above the snapshot limit of 16
-    big_a = a_t.repeat(2, 1, 1)
+    big_phi = phi.repeat(3, 1, 1, 1)   # 36 training samples: above the snapshot limit of 24
+    big_a = a_t.repeat(3, 1, 1)
     with pytest.raises(Exception):
         api.stomsfem_pod_build(g, big_phi, big_a, tol=1e-6, max_rank=27)
