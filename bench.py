@@ -417,7 +417,9 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
     evs = []
 
     def pod_step(ev=None):
-        api.stomsfem_sample_coef(g, fld, xi, a, stream=stream)
+        # the coefficient in FP32 arithmetic, as the FP32 form samples it (the
+        # GEMM takes it as BF16 pairs, 16 bits)
+        api.stomsfem_sample_coef_precision(g, fld, xi, a, precision=api.FP32, stream=stream)
         if ev is not None:
             ev[0].record(stream)
         api.stomsfem_pod_upscale(h, g, a, Ke, be, refine_iters=0, unit_status=pst, workspace=wsp, stream=stream)

@@ -686,19 +686,19 @@ pod_gemm_kernel(PodDims d, int Spad, const __nv_bfloat16* __restrict__ Ab, const
   bool ok = true;
   uint32_t taddr = 0;
   for (int kc = 0; kc < nk; ++kc) {
-    // stage K step kc (16-byte chunks into the swizzled layout)
+    // stage K step kc: 16-byte asynchronous copies into the swizzled layout
+    // (every thread's copies in flight at once), then wait for them
     for (int part = 0; part < nparts; ++part) {
       for (int c = tid; c < kPodTileM * 8; c += 128) {
         const int row = c >> 3, ch = c & 7;
-        *reinterpret_cast<uint4*>(sA[part] + tc::sw128_offset(row, ch * 8)) =
-            gA[part][(size_t)row * rowv + kc * 8 + ch];
+        tc::cp_async16(sA[part] + tc::sw128_offset(row, ch * 8), gA[part] + (size_t)row * rowv + kc * 8 + ch);
       }
       for (int c = tid; c < d.Ppad * 8; c += 128) {
         const int row = c >> 3, ch = c & 7;
-        *reinterpret_cast<uint4*>(sB[part] + tc::sw128_offset(row, ch * 8)) =
-            gB[part][(size_t)row * rowv + kc * 8 + ch];
+        tc::cp_async16(sB[part] + tc::sw128_offset(row, ch * 8), gB[part] + (size_t)row * rowv + kc * 8 + ch);
       }
     }
+    tc::cp_async_wait_all();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
