@@ -765,13 +765,29 @@ int stomsfem_surrogate_workspace_size(const stomsfem_surrogate* sg, int32_t S, s
  * y-linear corner vectors v, v^T K v outside [ahar (1 - delta),
  * abar (1 + delta)] (harmonic and arithmetic cell means of a: the energy
  * bounds of the cell problem with affine data); K not positive definite
- * on the complement of the constants.  Flagged units (fell_back device
- * [S][nc*nc] uint8 set to 1) are recomputed by the plain FP64 upscaler in
+ * on the complement of the constants.  With an ensemble partner
+ * (stomsfem_surrogate_set_partner), also: the partner network's K_e on the
+ * same inputs differs from this one's by more than tol relative.  Flagged
+ * units (fell_back device [S][nc*nc] uint8: 1 by the rules above, 2 by the
+ * ensemble test, 0 accepted) are recomputed by the plain FP64 upscaler in
  * the same call.  Outputs Ke [S][nc*nc][10], be [S][nc*nc][4] (device).
  * A device-side wait that ran out flags every unit (all fall back). */
 int stomsfem_surrogate_infer(stomsfem_surrogate* sg, const double* xi, const double* a, int32_t S,
                              double delta, double* Ke, double* be, uint8_t* fell_back,
                              void* workspace, size_t workspace_bytes, stomsfem_stream_t stream);
+
+/* Ensemble indicator (the a-posteriori detection of Sec. 3.2 read as the
+ * disagreement of two independently trained networks; no paper formula):
+ * stomsfem_surrogate_infer on sg also runs `partner` (a second surrogate of
+ * the same grid, local variables and families, trained from other initial
+ * weights; not owned, it must outlive its use) and sends to the fallback
+ * every unit the rules accepted whose two K_e differ by more than tol
+ * (||K1 - K2|| > tol ||K1||, Euclidean norm over the 10 packed entries).
+ * partner NULL removes it.  Changes the workspace size
+ * (stomsfem_surrogate_workspace_size: query again).  Not part of
+ * stomsfem_surrogate_save.  EINVAL: sg NULL, partner == sg, tol < 0, or a
+ * partner of other families. */
+int stomsfem_surrogate_set_partner(stomsfem_surrogate* sg, const stomsfem_surrogate* partner, double tol);
 
 /* ---------------------------------------------------------------------
  * Random interpolation of the local upscaled quantities (Sec. 3.1,

@@ -15,7 +15,8 @@
   margin, the out-of-range recompute of the remark closing Sec. 3.1.1), an
   energy of the x- or y-linear corner vector outside the cell's harmonic /
   arithmetic mean bounds, or a matrix that is not positive definite once
-  the constants are factored out (the a-posteriori checks of Sec. 3.2).
+  the constants are factored out (the a-posteriori checks of Sec. 3.2);
+  ``ensemble_disagrees`` the optional test of two networks' disagreement.
 * ``minibatch_rows`` -- the training rows of one Adam step: SplitMix64
   (Steele, Lea and Flood, OOPSLA 2014, in Vigna's 64-bit form) of the seed,
   the family, the step and the row slot, reduced modulo the family's rows;
@@ -207,6 +208,16 @@ def energy_values(Kp):
 
 def flagged(x, box, margin, Kp, abar, ahar, delta):
     return any(indicator(x, box, margin, Kp, abar, ahar, delta).values())
+
+
+def ensemble_disagrees(Kp1, Kp2, tol):
+    """The ensemble test of two independently trained networks on the same
+    unit: their packed predictions differ by more than tol relative to the
+    first, ||Kp1 - Kp2|| > tol ||Kp1|| (Euclidean norm over the 10 packed
+    entries)."""
+    Kp1 = np.asarray(Kp1, dtype=np.float64)
+    Kp2 = np.asarray(Kp2, dtype=np.float64)
+    return bool(np.linalg.norm(Kp1 - Kp2) > tol * np.linalg.norm(Kp1))
 
 
 # ---------------------------------------------------------------- training loop

@@ -109,6 +109,7 @@ _SIG = {
     "stomsfem_plan_upscale_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
     "stomsfem_mc_merge": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _P, _P]),
     "stomsfem_pod_set_gemm_split": (ctypes.c_int, [_P, _I]),
+    "stomsfem_surrogate_set_partner": (ctypes.c_int, [_P, _P, ctypes.c_double]),
     "stomsfem_upscale_engine": (ctypes.c_int, [ctypes.POINTER(Grid), _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P,
                                                _P, _P, _SZ, _P]),
     "stomsfem_local_kl_build": (ctypes.c_int, [ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Field),

@@ -208,6 +208,11 @@ def stomsfem_pod_eigenvalues(h, g: Grid, per_l=False):
     return lam
 
 
+def stomsfem_surrogate_set_partner(h, partner, tol):
+    """partner None removes the ensemble partner."""
+    L.check(L.lib().stomsfem_surrogate_set_partner(h, partner, float(tol)))
+
+
 def stomsfem_pod_set_gemm_split(h, split=1):
     L.check(L.lib().stomsfem_pod_set_gemm_split(h, int(split)))
 

@@ -777,6 +777,25 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(Infer
 }
 
 // Units whose indicator fired (or every unit after a device-side failure).
+// Ensemble indicator: a unit the rules accepted falls back (flag 2) when the
+// two networks' K_e differ by more than tol relative (Euclidean norm over the
+// 10 packed entries, FP64 from the stored outputs).
+__global__ void surrogate_ensemble_kernel(long long units, const double* __restrict__ K1, const double* __restrict__ K2,
+                                          double tol, uint8_t* __restrict__ flag) {
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    if (flag[u]) continue;
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const double x = K1[u * 10 + q], y = K2[u * 10 + q];
+      num += (x - y) * (x - y);
+      den += x * x;
+    }
+    if (!(num <= tol * tol * den)) flag[u] = 2;
+  }
+}
+
 __global__ void surrogate_compact_kernel(long long units, uint8_t* __restrict__ flag, const int32_t* __restrict__ err,
                                          int32_t* __restrict__ list, int32_t* __restrict__ count) {
   const bool all = err[0] != 0;
@@ -800,6 +819,10 @@ struct stomsfem_surrogate {
   int *var_ids_d = nullptr, *cell_fam_d = nullptr, *cell_pos_d = nullptr, *fam_ncell_d = nullptr;
   float *W = nullptr, *m = nullptr, *v = nullptr, *box = nullptr;
   int step = 0;
+  // ensemble indicator: a second network on the same families (not owned)
+  // and the relative K_e disagreement above which a unit falls back
+  const stomsfem_surrogate* partner = nullptr;
+  double ens_tol = 0.0;
 };
 
 static void sg_free(stomsfem_surrogate* h) {
@@ -1190,6 +1213,7 @@ namespace {
 
 struct InferLayout {
   size_t X, uor, Xf, abar, ahar, Wb, tfam, list, count, err, fb, total;
+  size_t Wb2 = 0, K2 = 0, b2 = 0, f2 = 0;  // the ensemble partner's pass
   long long rows_pad, units;
   int ntiles;
 };
@@ -1225,6 +1249,12 @@ InferLayout infer_layout(const stomsfem_surrogate* h, int S, std::vector<int>* r
   L.list = o; o += al(L.units * 4);
   L.count = o; o += 1024;
   L.err = o;  o += 1024;
+  if (h->partner) {
+    L.Wb2 = o; o += al((size_t)h->nfam * kWbSize * 2);
+    L.K2 = o;  o += al(L.units * 10 * 8);
+    L.b2 = o;  o += al(L.units * 4 * 8);
+    L.f2 = o;  o += al(L.units);
+  }
   L.fb = o;
   o += upscale_slot_bytes_fp64(&h->grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 8;
   L.total = o;
@@ -1303,7 +1333,43 @@ extern "C" int stomsfem_surrogate_infer(stomsfem_surrogate* h, const double* xi,
   STOMSFEM_TRY_CUDA(cudaMemcpyToSymbolAsync(kZeroRowSumProj, proj, sizeof(proj), 0, cudaMemcpyHostToDevice, st));
   surrogate_infer_kernel<<<L.ntiles, kInferThreads, smem, st>>>(A);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
+  if (h->partner) {
+    // the partner network on the same inputs (its own outputs and flags in
+    // scratch), then the disagreement test on the units the rules accepted
+    const stomsfem_surrogate* p2 = h->partner;
+    auto* Wb2 = reinterpret_cast<__nv_bfloat16*>(ws + L.Wb2);
+    surrogate_pack_kernel<<<sms * 2, 256, 0, st>>>(p2->nfam, p2->W, Wb2);
+    InferArgs A2 = A;
+    A2.Wb = Wb2;
+    A2.W = p2->W;
+    A2.box = p2->box;
+    A2.Ke = reinterpret_cast<double*>(ws + L.K2);
+    A2.be = reinterpret_cast<double*>(ws + L.b2);
+    A2.flag = ws + L.f2;
+    surrogate_infer_kernel<<<L.ntiles, kInferThreads, smem, st>>>(A2);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+    surrogate_ensemble_kernel<<<sms * 4, 256, 0, st>>>(L.units, Ke, A2.Ke, h->ens_tol, fell_back);
+    STOMSFEM_TRY_CUDA(cudaGetLastError());
+  }
   surrogate_compact_kernel<<<sms * 4, 256, 0, st>>>(L.units, fell_back, err, list, count);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
   return upscale_list_fp64(&h->grid, a, S, list, count, Ke, be, ws + L.fb, L.total - L.fb, st);
+}
+
+extern "C" int stomsfem_surrogate_set_partner(stomsfem_surrogate* h, const stomsfem_surrogate* partner, double tol) {
+  if (!h) return set_error(STOMSFEM_EINVAL, "surrogate is NULL");
+  if (!partner) {
+    h->partner = nullptr;
+    h->ens_tol = 0.0;
+    return STOMSFEM_OK;
+  }
+  if (partner == h) return set_error(STOMSFEM_EINVAL, "a surrogate cannot be its own partner");
+  if (!(tol >= 0.0)) return set_error(STOMSFEM_EINVAL, "tol must be >= 0");
+  const bool same = partner->grid.nf == h->grid.nf && partner->grid.nc == h->grid.nc &&
+                    partner->nfam == h->nfam && partner->fam_cell == h->fam_cell &&
+                    partner->k_cell == h->k_cell && partner->var_ids == h->var_ids;
+  if (!same) return set_error(STOMSFEM_EINVAL, "the partner must have the same grid, local variables and families");
+  h->partner = partner;
+  h->ens_tol = tol;
+  return STOMSFEM_OK;
 }

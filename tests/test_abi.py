@@ -144,6 +144,7 @@ def test_host_validation_of_the_further_forms(lib):
     fld = L.Field(2, 4, 4, 0.1, 1.0, 0.0, 2.0)
     assert lib.stomsfem_pod_set_affine(None, ctypes.byref(g), ctypes.byref(fld), 1e-6, None) == L.EINVAL
     assert lib.stomsfem_pod_set_gemm_split(None, 1) == L.EINVAL
+    assert lib.stomsfem_surrogate_set_partner(None, None, 0.1) == L.EINVAL
     assert lib.stomsfem_pod_upscale_affine(None, v, None, 1, 0, v, v, None, None) == L.EINVAL
     # plans
     h = ctypes.c_void_p()

@@ -127,3 +127,91 @@ def test_indicator_flags_match_oracle(orc):
     # every bound has units that trip it alone, and units pass every test
     for key, n in counts.items():
         assert n >= 20, (key, counts)
+
+
+def _bias_only_handle(g, fld, nfam, ys, box_of_fam):
+    """A surrogate whose network outputs exactly ys[f] for family f (zero
+    last-layer weights, the outputs in the bias), with a given input box."""
+    weights = api.xavier_weights(nfam, 3)
+    o_w4, o_b4 = 2 * (128 * 128 + 128) + 128 * 16 + 128, 2 * (128 * 128 + 128) + 128 * 16 + 128 + 16 * 128
+    weights[:, o_w4:o_b4] = 0.0
+    weights[:, o_b4:o_b4 + 16] = ys.astype(np.float32)
+    h, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, weights)
+    data = bytearray(api.stomsfem_surrogate_save(h))
+    api.stomsfem_surrogate_destroy(h)
+    nb = box_of_fam.size * 4
+    data[-nb:] = box_of_fam.astype(np.float32).tobytes()
+    h, _ = api.stomsfem_surrogate_load(bytes(data))
+    return h
+
+
+def test_ensemble_flags_and_fallback(orc):
+    """Two networks with known outputs: the first K = abar K_ref on every
+    unit (accepted by every rule), the partner K = abar (1 + eps_f) K_ref
+    with eps_f spread over [0, 0.1] by family, so that the two differ by
+    exactly eps_f relative.  With tol = 0.05 the flags are 2 on the
+    families the oracle's rule (ensemble_disagrees) flags and 0 elsewhere;
+    the flagged units hold the plain FP64 upscaler's K_e, the others
+    abar K_ref; without the partner nothing falls back; a partner of other
+    families is refused."""
+    from oracle import surrogate as S
+    w = W.workload("surrogate_64")
+    nf, nc = w["nf"], w["nc"]
+    rho = nf // nc
+    g = api.grid(nf, nc, w["f"])
+    fld = api.field_from_dict(w["field"])
+    k, ids, fam, nfam = S.local_vars(nf, nc, w["field"], 1e-6)
+    kref = S.KREF_PACKED
+    box = np.zeros((nfam, 16, 2))
+    box[:, :, 0], box[:, :, 1] = -2.0, 2.0
+    eps = np.linspace(0.0, 0.1, nfam)
+    eps[np.abs(eps - 0.05) < 2e-3] += 5e-3       # keep every family clear of the threshold
+    y1 = np.zeros((nfam, 16))
+    y2 = np.zeros((nfam, 16))
+    y2[:, :10] = eps[:, None] * kref[None, :]
+    h1 = _bias_only_handle(g, fld, nfam, y1, box)
+    h2 = _bias_only_handle(g, fld, nfam, y2, box)
+    hx, _ = api.stomsfem_surrogate_create(g, fld, 1e-2, api.xavier_weights(
+        len(set(S.local_vars(nf, nc, w["field"], 1e-2)[2])), 4))
+    try:
+        with pytest.raises(Exception):
+            api.stomsfem_surrogate_set_partner(h1, hx, 0.05)   # other families (tau 1e-2)
+        with pytest.raises(Exception):
+            api.stomsfem_surrogate_set_partner(h1, h1, 0.05)
+        S_ = 40
+        xi = W.draw_xi(w["field"], S_, 33)
+        a = orc.sample_coef(nf, w["field"], xi)
+        xt = torch.from_numpy(xi).to(DEV)
+        at = torch.from_numpy(a).to(DEV)
+        Ke = torch.empty((S_, nc * nc, 10), dtype=torch.float64, device=DEV)
+        be = torch.empty((S_, nc * nc, 4), dtype=torch.float64, device=DEV)
+        fb = torch.empty((S_, nc * nc), dtype=torch.uint8, device=DEV)
+        api.stomsfem_surrogate_infer(h1, g, xt, at, Ke, be, fb, delta=DELTA)
+        torch.cuda.synchronize()
+        assert int(fb.sum().item()) == 0                        # no partner: every unit accepted
+        api.stomsfem_surrogate_set_partner(h1, h2, 0.05)
+        api.stomsfem_surrogate_infer(h1, g, xt, at, Ke, be, fb, delta=DELTA)
+        torch.cuda.synchronize()
+        flags, Kg = fb.cpu().numpy(), Ke.cpu().numpy()
+        api.stomsfem_surrogate_set_partner(h1, None, 0.0)
+        api.stomsfem_surrogate_infer(h1, g, xt, at, Ke, be, fb, delta=DELTA)
+        torch.cuda.synchronize()
+        assert int(fb.sum().item()) == 0                        # partner removed
+    finally:
+        for h in (h1, h2, hx):
+            api.stomsfem_surrogate_destroy(h)
+    Kplain, _ = orc.upscale(nf, nc, w["f"], a)
+    n2 = 0
+    for s in range(S_):
+        for c in range(nc * nc):
+            blk = a[s, (c // nc) * rho:(c // nc + 1) * rho, (c % nc) * rho:(c % nc + 1) * rho]
+            abar = blk.mean()
+            K1, K2 = abar * kref, abar * (1 + eps[fam[c]]) * kref
+            want = S.ensemble_disagrees(K1, K2, 0.05)
+            assert flags[s, c] == (2 if want else 0), (s, c, eps[fam[c]])
+            if want:
+                n2 += 1
+                np.testing.assert_allclose(Kg[s, c], Kplain[s, c], rtol=1e-11, atol=1e-13)
+            else:
+                np.testing.assert_allclose(Kg[s, c], K1, rtol=1e-6)
+    assert 0.2 * S_ * nc * nc < n2 < 0.8 * S_ * nc * nc

@@ -187,3 +187,18 @@ def test_train_reduces_loss():
     T = np.tanh(X[:, :16] @ rng.standard_normal((16, 16)) * 0.3)
     _, _, _, loss = S.train(w0, X, T, 60, lr=3e-3, lr_min=1e-4, seed=1)
     assert loss[-10:].mean() < 0.5 * loss[:3].mean()
+
+
+def test_ensemble_disagreement_rule():
+    """Identical predictions never disagree; a scaled copy (1 + eps) K
+    disagrees exactly when |eps| > tol; the norm is the first network's
+    (K2 = 2 K1 differs by ||K1||: flagged at tol 0.9 from K1's side, not
+    from K2's, where the difference is half of ||K2||)."""
+    from oracle import surrogate as S
+    K1 = S.KREF_PACKED * 1.7
+    for tol in (0.0, 0.01, 0.5):
+        assert not S.ensemble_disagrees(K1, K1.copy(), tol)
+    for eps, tol, want in ((0.049, 0.05, False), (0.051, 0.05, True), (-0.051, 0.05, True), (0.2, 0.25, False)):
+        assert S.ensemble_disagrees(K1, (1 + eps) * K1, tol) == want, (eps, tol)
+    assert S.ensemble_disagrees(K1, 2 * K1, 0.9)
+    assert not S.ensemble_disagrees(2 * K1, K1, 0.9)
