@@ -683,8 +683,23 @@ def bench_surrogate(api, dev, stream, samples=None, steps=3000):
                                                 Kp[:2000].contiguous(), bp[:2000].contiguous(), dev),
            "tensor_tflops_whole_call": flops / (ms_inf / 1e3) / 1e12,
            "tensor_peak_tflops": _peaks().get("bf16_tflops", 1900.0)}
+    # the ensemble indicator: a second network from other initial weights
+    # and minibatch draws, its disagreement above 2 % sending units back
+    h2, _ = api.stomsfem_surrogate_create(g, fld, 1e-6, api.xavier_weights(nfam, 1))
+    api.stomsfem_surrogate_train(h2, xtr, atr, Ktr, btr, steps=steps, lr=2e-3, lr_min=2e-5,
+                                 seed=w["train_seed"] + 1)
+    api.stomsfem_surrogate_set_partner(h, h2, 0.02)
+    wss2 = torch.empty(api.stomsfem_surrogate_workspace_size(h, S), dtype=torch.uint8, device=dev)
+    ms_ens = _timed_call(stream, lambda: api.stomsfem_surrogate_infer(h, g, xi, a, Ke, be, fb, workspace=wss2,
+                                                                      stream=stream))
+    res["ensemble"] = {"tol": 0.02, "units_per_s": units / (ms_ens / 1e3), "speedup_vs_fp64": ms_plain / ms_ens,
+                       "fallback_rate": float((fb != 0).double().mean().item()),
+                       "ensemble_fallback_rate": float((fb == 2).double().mean().item()),
+                       "coarse_rel_l2_vs_fp64": _coarse_err(api, g, Ke[:2000].contiguous(), be[:2000].contiguous(),
+                                                            Kp[:2000].contiguous(), bp[:2000].contiguous(), dev)}
     api.stomsfem_surrogate_destroy(h)
-    return res, 6 * 4 + 8
+    api.stomsfem_surrogate_destroy(h2)
+    return res, 6 * 4 + 8 + 9 * 4
 
 
 def bench_ri(api, dev, stream, samples=None):
@@ -1162,12 +1177,12 @@ def main():
             torch.cuda.synchronize()
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record(stream)
-            for i in range(steps):
-                a.step(xs_for(warmup + i, Bs))
+            ups = [a.step(xs_for(warmup + i, Bs)) for i in range(steps)]
             t1.record(stream)
             stream.synchronize()
             a.step(xs_for(0, Bs))
             stream.synchronize()
+        a.up_ms = sum(ups) / len(ups)
         return max_over_ranks(t0.elapsed_time(t1), dev), a
 
     # the plain FP64 arm (same path, FP64 throughout, its own tuned plan),
@@ -1177,6 +1192,11 @@ def main():
     value64 = args.fp64_batch * ncell * ws * steps_s / (ms64 / 1e3)
     plan64 = arm64.info()
     u64 = arm64.u[:Bc].cpu().numpy()
+    # the FP64 upscaling's own roofline (FP64 FMA pipe, measured here)
+    peak64, _ = alu_peak_tflops("fp64", api)
+    ach64 = unit_flops(nf, nc, ov, "fp64") * args.fp64_batch / (arm64.up_ms / 1e3) / 1e12
+    roof64 = {"achieved": ach64, "peak": peak64, "unit": "TFLOP/s", "frac": ach64 / peak64,
+              "upscale_ms": arm64.up_ms, "peak_note": "measured in this run: FMA-chain probe, FP64"}
     arm64.close()
     # coarse-solution error of the chosen form vs the FP64 path on the same samples
     err = float(np.max(np.linalg.norm(uf - u64, axis=1) / np.linalg.norm(u64, axis=1)))
@@ -1189,10 +1209,11 @@ def main():
         v = args.fp32r_batch * ncell * ws * steps_s / (ms32r / 1e3)
         e = float(np.max(np.linalg.norm(arm32r.u[:Br].cpu().numpy() - u64[:Br], axis=1) /
                          np.linalg.norm(u64[:Br], axis=1)))
-        fp32r[sweeps] = (v, e, arm32r.info())
+        fp32r[sweeps] = (v, e, arm32r.info(),
+                         unit_flops(nf, nc, ov, "fp32r", refine=sweeps) * args.fp32r_batch / (arm32r.up_ms / 1e3) / 1e12)
         arm32r.close()
     sweeps_chosen = 1 if fp32r[1][1] <= 1e-10 else 2
-    value32r, err32r, plan32r = fp32r[sweeps_chosen]
+    value32r, err32r, plan32r, ach32r = fp32r[sweeps_chosen]
 
     e2e = None
     if not args.no_e2e:
@@ -1304,13 +1325,19 @@ def main():
                       "fp32r_coarse_rel_l2_vs_fp64": err32r, "fp32r_sweeps": sweeps_chosen,
                       "fp32r_by_sweeps": {str(k): {"units_per_s": v[0], "coarse_rel_l2_vs_fp64": v[1]}
                                           for k, v in fp32r.items()},
-                      "plans": {"fp64": plan64, "fp32r": plan32r}},
+                      "plans": {"fp64": plan64, "fp32r": plan32r},
+                      "fp64_roofline": roof64,
+                      "fp32r_achieved_tflops": ach32r,
+                      "fp32r_frac_of_fp32_peak": ach32r / peak},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "traffic_note": traffic_note,
                          "kernel": "upscale_kernel (%s)" % form,
                          "peak_note": peak_note},
             "e2e": e2e,
+            # the upscaling alone (coefficient resident in HBM): the plan's
+            # events around its launches in every timed step
+            "upscale_only": {"units_per_s": units_step * ws / (up_avg / 1e3), "ms_per_step": up_avg},
             # per step: sampling, upscaling (FP32 form with oversampling: a
             # cell-list kernel and two upscale launches), coarse solve, moments, count
             "gpu_launches": launches * args.steps,
