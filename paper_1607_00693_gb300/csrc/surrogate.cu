@@ -631,12 +631,13 @@ constexpr int kInferThreads = 128 * kInferSplit;
 
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int rows, int kblocks,
                                            int ld, int tid) {
-  // src rows of ld BF16 (ld = 64 * kblocks) -> kblocks swizzled [rows][64] blocks
+  // src rows of ld BF16 (ld = 64 * kblocks) -> kblocks swizzled [rows][64]
+  // blocks, by 16-byte asynchronous copies (the caller waits for them)
   const int chunks = rows * kblocks * 8;
   for (int c = tid; c < chunks; c += kInferThreads) {
     const int row = c / (kblocks * 8), rem = c % (kblocks * 8), kb = rem / 8, ch = rem % 8;
-    const uint4 v = reinterpret_cast<const uint4*>(src + (size_t)row * ld + kb * 64)[ch];
-    *reinterpret_cast<uint4*>(dst + (size_t)kb * rows * 128 + tc::sw128_offset(row, ch * 8)) = v;
+    tc::cp_async16(dst + (size_t)kb * rows * 128 + tc::sw128_offset(row, ch * 8),
+                   reinterpret_cast<const uint4*>(src + (size_t)row * ld + kb * 64) + ch);
   }
 }
 
@@ -669,6 +670,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) surrogate_infer_kernel(Infer
   stage_rows(sW2, Wb + kWb2, kHid, 2, kHid, tid);
   stage_rows(sW3, Wb + kWb3, kHid, 2, kHid, tid);
   stage_rows(sW4, Wb + kWb4, kOut, 2, kHid, tid);
+  tc::cp_async_wait_all();
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
