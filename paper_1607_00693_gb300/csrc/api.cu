@@ -30,5 +30,5 @@ int device_sm_count() {
 
 }  // namespace stomsfem
 
-extern "C" const char* stomsfem_version(void) { return "stomsfem-gb300 0.8 (sm_103a)"; }
+extern "C" const char* stomsfem_version(void) { return "stomsfem-gb300 0.9 (sm_103a)"; }
 extern "C" const char* stomsfem_last_error(void) { return stomsfem::g_err; }

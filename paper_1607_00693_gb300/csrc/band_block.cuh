@@ -403,13 +403,15 @@ __device__ __forceinline__ void panel_pair(T (&pr)[RPL][NB], T (&rh)[RPL][NR], T
 // Factorise (and forward-substitute NR rhs).  Lg: blocks of (NB+bmax) x NB;
 // yg[k*NR + c] receives the forward solution.  Returns -1 or the first
 // failing pivot index (the factorisation runs to the end either way).
+// store_from: the factor blocks wholly below this row are not stored (a
+// back substitution that stops there never reads them).
 // FWD_ONLY (NR = 4): neither the factor nor y is stored; each lane adds,
 // over the rows it finishes, y0 y0, y0 y1, y0 y2, y1 y1, y1 y2, y2 y2 and
 // y3 y0, y3 y1, y3 y2 into yy[0..8] (FP64), for the caller to sum over the
 // group.
 template <int G, typename T, int NR, int RPL, class Gen, typename TS, bool FWD_ONLY = false>
 __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<T>& s, T* __restrict__ Lg,
-                          TS* __restrict__ yg, int gl, double* yy = nullptr) {
+                          TS* __restrict__ yg, int gl, double* yy = nullptr, int store_from = 0) {
   constexpr int NB = G / 2;
   const int LBS = (NB + bmax) * NB;
   const int RW = s.RW;
@@ -486,6 +488,7 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
     // the transposed trailing panel: 16-byte aligned inside the retired
     // rows' span [kWndOff + kslot PW, kWndOff + (kslot + NB) PW)
     T* pt = s.wnd + kslot * s.PW + 4;
+    const bool store_blk = K + NB > store_from;
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -493,6 +496,8 @@ __device__ int blk_factor(const Gen& gen, int n, int b, int bmax, const BlkSmem<
       if (i < np) {
         T* dst = Lb + i * NB;
         if constexpr (FWD_ONLY) {
+          (void)dst;
+        } else if (!store_blk) {
           (void)dst;
         } else if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -617,22 +622,24 @@ __device__ __forceinline__ void blk_stage(const T* __restrict__ Lg, int kb, int 
 
 // Back substitution L^T x = y, in place on xg ([n][NR], y in, x out).
 // Factor blocks of NB columns (NB <= G; G / NB lane groups share the rows
-// below each block).
+// below each block).  stop_from: the substitution ends with the block that
+// holds this row (the rows below it keep y).
 template <int G, typename T, int NR, typename TS, int NB = G / 2>
 __device__ void blk_backward(int n, int b, int bmax, const BlkSmem<T>& s, const T* __restrict__ Lg,
-                             TS* __restrict__ xg, int gl) {
+                             TS* __restrict__ xg, int gl, int stop_from = 0) {
   static_assert(G % NB == 0 && NB % 2 == 0, "lane groups of whole blocks");
   const int nbk = (n + NB - 1) / NB;
+  const int kb_stop = min(stop_from / NB, nbk - 1);
   const int RW = s.RW;
   const int stg = (NB + bmax) * NB;
   T* xr = s.rhs;  // ring of solution rows
   blk_stage<G, T, NB>(Lg, nbk - 1, n, b, bmax, s.tb + ((nbk - 1) & 1) * stg, gl);
   int kslot = ((nbk - 1) * NB) % RW;  // slot of row K
-  for (int kb = nbk - 1; kb >= 0; --kb, kslot = kslot >= NB ? kslot - NB : kslot - NB + RW) {
+  for (int kb = nbk - 1; kb >= kb_stop; --kb, kslot = kslot >= NB ? kslot - NB : kslot - NB + RW) {
     const int K = kb * NB;
     const int nb = min(NB, n - K);
     const int np = min(nb + b, n - K);
-    if (kb > 0) {
+    if (kb > kb_stop) {
       blk_stage<G, T, NB>(Lg, kb - 1, n, b, bmax, s.tb + ((kb - 1) & 1) * stg, gl);
       cp_async_wait<1>();
     } else {

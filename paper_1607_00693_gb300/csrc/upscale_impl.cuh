@@ -620,11 +620,15 @@ upscale_kernel(UpscaleArgs A) {
           fail = blk_factor<G, TK, 4, RPL, Gen, TS, true>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, yy);
       }
     } else if (g.n > 0) {
+      // without refinement only psi on the cell's nodes is read: the rows
+      // below the cell's first node row (the bottom oversampling layer) need
+      // neither stored factor blocks nor back substitution
+      const int need_from = A.refine == 0 ? max(0, g.cy0 - 1) * g.mx : 0;
       if constexpr (TC > 0)
         fail = tc_factor<3, false, Gen, TS, TC>(pg, g.n, g.b, A.bmax, tsm, reinterpret_cast<float*>(Lg), psi0, gl);
       else
-        fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl);
-      blk_backward<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl);
+        fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, nullptr, need_from);
+      blk_backward<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl, need_from);
       // FP64 iterative refinement with the factor: corr = residual, solve, add
       for (int it = 0; it < A.refine; ++it) {
         __syncwarp();
