@@ -38,12 +38,15 @@ FORMS = {"fp64": 0, "fp32r": 1, "fp32": 2}
 # the H/h = 32 workload, the forward-only and the back-substitution launches
 # of one FP32 call), by library version and form: 0.6 and 0.7 share one
 # kernel (counters taken on 0.6); 0.8 changed the factorisation window's
-# layout (counters retaken on 0.8; FP64 not retaken).
+# layout and 0.9 the back substitution's end row (counters retaken on each;
+# FP64 not retaken).
 _TRAFFIC_06 = {"fp32": (0.051981e9 + 0.000175e9 + 7.110618e9 + 6.763874e9) / 32768,
                "fp64": (1.827271e9 + 1.937667e9) / 4096}
 _TRAFFIC_08 = {"fp32": (0.051976e9 + 0.000239e9 + 7.124753e9 + 6.771178e9) / 32768}
+_TRAFFIC_09 = {"fp32": (0.051979e9 + 0.000154e9 + 6.837680e9 + 6.506667e9) / 32768}
 DRAM_BYTES_PER_UNIT = {("stomsfem-gb300 %s (sm_103a)" % v, f): b
-                       for v, t in (("0.6", _TRAFFIC_06), ("0.7", _TRAFFIC_06), ("0.8", _TRAFFIC_08))
+                       for v, t in (("0.6", _TRAFFIC_06), ("0.7", _TRAFFIC_06), ("0.8", _TRAFFIC_08),
+                                    ("0.9", _TRAFFIC_09))
                        for f, b in t.items()}
 DTYPE = {"fp64": "f64", "fp32r": "f32 factor + f64 refinement", "fp32": "f32"}
 
