@@ -85,7 +85,10 @@ def test_host_validation_without_gpu(lib):
 def test_host_validation_of_the_further_forms(lib):
     """Petrov-Galerkin, mixed boundary data, two-level Monte Carlo, affine
     reduced basis and plan calls reject bad arguments on the host, before
-    any device work."""
+    any device work.  Placeholder pointers are passed, so the test runs only
+    where no GPU is visible (a regression there cannot reach a device)."""
+    if _gpu_visible():
+        pytest.skip("placeholder device pointers: host-only check")
     g = L.Grid(64, 8, 1.0)
     v = ctypes.c_void_p(16)
     # Petrov-Galerkin: bad precision; coarse band limit and NULL pointers
