@@ -821,4 +821,22 @@ __device__ void blk_forward_stored(int n, int b, int bmax, const BlkSmem<T>& s, 
   }
 }
 
+// Out-of-line copies of the substitutions, for a kernel that runs them
+// several times (the factor-and-refine form: its first back substitution
+// and each refinement sweep's forward and backward solves share one copy
+// each instead of three inlined passes, whose code outgrew the instruction
+// cache).
+template <int G, typename T, int NR, typename TS, int NB = G / 2>
+__device__ __noinline__ void blk_backward_outlined(int n, int b, int bmax, const BlkSmem<T> s,
+                                                   const T* __restrict__ Lg, TS* __restrict__ xg, int gl,
+                                                   int stop_from) {
+  blk_backward<G, T, NR, TS, NB>(n, b, bmax, s, Lg, xg, gl, stop_from);
+}
+template <int G, typename T, int NR, int RPL, int NB = G / 2>
+__device__ __noinline__ void blk_forward_stored_outlined(int n, int b, int bmax, const BlkSmem<T> s,
+                                                         const T* __restrict__ Lg, double* __restrict__ rg,
+                                                         int gl) {
+  blk_forward_stored<G, T, NR, RPL, NB>(n, b, bmax, s, Lg, rg, gl);
+}
+
 }  // namespace stomsfem

@@ -628,7 +628,13 @@ upscale_kernel(UpscaleArgs A) {
         fail = tc_factor<3, false, Gen, TS, TC>(pg, g.n, g.b, A.bmax, tsm, reinterpret_cast<float*>(Lg), psi0, gl);
       else
         fail = blk_factor<G, TK, 3, RPL>(pg, g.n, g.b, A.bmax, sm, Lg, psi0, gl, nullptr, need_from);
-      blk_backward<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl, need_from);
+      // the factor-and-refine form (FP32 factor, FP64 solutions) calls the
+      // substitutions out of line: one copy of each for all its passes
+      constexpr bool outlined = sizeof(TK) == 4 && std::is_same<TA, double>::value;
+      if constexpr (outlined)
+        blk_backward_outlined<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl, need_from);
+      else
+        blk_backward<G, TK, 3, TS, NB>(g.n, g.b, A.bmax, sm, Lg, psi0, gl, need_from);
       // FP64 iterative refinement with the factor: corr = residual, solve, add
       for (int it = 0; it < A.refine; ++it) {
         __syncwarp();
@@ -644,8 +650,13 @@ upscale_kernel(UpscaleArgs A) {
           }
         }
         __syncwarp();
-        blk_forward_stored<G, TK, 3, RPL, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
-        blk_backward<G, TK, 3, double, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        if constexpr (outlined) {
+          blk_forward_stored_outlined<G, TK, 3, RPL, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+          blk_backward_outlined<G, TK, 3, double, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl, 0);
+        } else {
+          blk_forward_stored<G, TK, 3, RPL, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+          blk_backward<G, TK, 3, double, NB>(g.n, g.b, A.bmax, sm, Lg, corr, gl);
+        }
         __syncwarp();
         for (int k = gl; k < g.n * 3; k += G) psi0[k] += (TS)corr[k];
       }
