@@ -346,13 +346,16 @@ def bench_pod(api, dev, stream, samples=None):
     return res, 4 + 3 * 3 * 4
 
 
-def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
+def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24, n_sur_train=1024, sur_steps=20000):
     """The high-contrast comparison (contrast_2048: 2048^2 fine, 64^2 coarse,
     H/h = 32, contrast 10^4, xi ~ N(0,1), no oversampling): plain FP64, the
     FP32 form, FP32 + one refinement sweep (tuned plans, one graph per
     step) and the POD form (offline basis from n_train training samples in
     snapshot space; online BF16 tensor-core W^T A W with K = 1024 per cell
-    and the FP32 reduced solves, no refinement) on the same GPU, each a
+    and the FP32 reduced solves, no refinement) and the learned surrogate
+    (per-family networks on the local variables at tau = 1e-3, at most 15
+    per cell here; trained on n_sur_train samples from the plain FP32
+    upscaler; alone and with the ensemble indicator) on the same GPU, each a
     whole step (sampling, upscaling, coarse solve), with the coarse error
     against plain FP64 on the first fp64_batch samples.  CUDA events, one
     warm-up step and two timed steps per arm."""
@@ -417,7 +420,6 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
     pst = torch.zeros((batch, ncell), dtype=torch.int32, device=dev)
     wsp = torch.empty(api.stomsfem_pod_workspace_size(h, batch), dtype=torch.uint8, device=dev)
     wsc = torch.empty(api.stomsfem_coarse_workspace_size(g, batch), dtype=torch.uint8, device=dev)
-    evs = []
 
     def pod_step(ev=None):
         # the coefficient in FP32 arithmetic, as the FP32 form samples it (the
@@ -430,19 +432,24 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
             ev[1].record(stream)
         api.stomsfem_coarse_solve(g, Ke, be, u, workspace=wsc, stream=stream)
 
-    with torch.cuda.stream(stream):
-        pod_step()
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(2):
-            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            evs.append(ev)
-            pod_step(ev)
-        e1.record(stream)
-        stream.synchronize()
-    ms = e0.elapsed_time(e1) / 2
-    ms_up = sum(a_.elapsed_time(b_) for a_, b_ in evs) / len(evs)
+    def two_steps(step):
+        """(ms per whole step, ms of its upscaling call): one warm-up step,
+        then two timed ones."""
+        evs = []
+        with torch.cuda.stream(stream):
+            step()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                evs.append(ev)
+                step(ev)
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / 2, sum(a_.elapsed_time(b_) for a_, b_ in evs) / len(evs)
+
+    ms, ms_up = two_steps(pod_step)
     P0 = 4 + int(max(ranks))
     Ppad = (P0 * (P0 + 1) // 2 + 15) // 16 * 16
     gemm_flops = 2.0 * batch * ncell * (rho * rho) * Ppad
@@ -454,8 +461,66 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24):
                   "failed_units": int((pst != 0).sum().item()),
                   "refinement": "none (FP64 refinement is offered for H/h <= 8)"}
     api.stomsfem_pod_destroy(h)
-    out["note"] = ("surrogate and random interpolation: a cell of this workload sees more than 16 local "
-                   "variables (their limit), so they are not run here")
+    del pst, wsp
+    # learned surrogate: two networks per family (the second for the
+    # ensemble indicator), trained on FP32 plain-upscaler pairs
+    tau = 1e-3
+    kv, _, _, nfam = api.stomsfem_local_vars(g, fld, tau)
+    xs = torch.from_numpy(W.draw_xi(w["field"], n_sur_train, w["seed"] + 2000, w["dist"])).to(dev)
+    As = torch.empty((n_sur_train, nf, nf), dtype=torch.float64, device=dev)
+    api.stomsfem_sample_coef(g, fld, xs, As)
+    Ks = torch.empty((n_sur_train, ncell, 10), dtype=torch.float64, device=dev)
+    bs = torch.empty((n_sur_train, ncell, 4), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.stomsfem_upscale(g, As, Ks, bs, precision=api.FP32)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    hs, losses = [], []
+    t0 = time.perf_counter()
+    for rep in range(2):
+        hh, _ = api.stomsfem_surrogate_create(g, fld, tau, api.xavier_weights(nfam, rep))
+        losses.append(api.stomsfem_surrogate_train(hh, xs, As, Ks, bs, steps=sur_steps, lr=2e-3, lr_min=2e-5,
+                                                   seed=w["seed"] + 7 + rep))
+        hs.append(hh)
+    t_train = (time.perf_counter() - t0) / 2
+    del xs, As, Ks, bs
+    fb = torch.empty((batch, ncell), dtype=torch.uint8, device=dev)
+
+    def sur_arm(ws):
+        def step(ev=None):
+            # FP64 coefficient: the indicator's cell means and the fallback
+            # upscaler read it
+            api.stomsfem_sample_coef(g, fld, xi, a, stream=stream)
+            if ev is not None:
+                ev[0].record(stream)
+            api.stomsfem_surrogate_infer(hs[0], g, xi, a, Ke, be, fb, workspace=ws, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+            api.stomsfem_coarse_solve(g, Ke, be, u, workspace=wsc, stream=stream)
+
+        ms_, ms_inf = two_steps(step)
+        v = batch * ncell / (ms_ / 1e3)
+        return {"units_per_s": v, "speedup_vs_fp64": v / v64, "coarse_rel_l2_vs_fp64": err(u[:fp64_batch].cpu().numpy()),
+                "infer_ms": ms_inf, "fallback_rate": float((fb != 0).double().mean().item()),
+                "ensemble_fallback_rate": float((fb == 2).double().mean().item())}
+
+    sur = {"tau": tau, "k_min": int(kv.min()), "k_max": int(kv.max()), "families": nfam,
+           "train_samples": n_sur_train, "train_pairs": n_sur_train * ncell, "train_steps": sur_steps,
+           "pairs_s": t_pairs, "train_s_per_network": t_train,
+           "train_loss_last": float(losses[0][-50:].mean()),
+           "single": sur_arm(torch.empty(api.stomsfem_surrogate_workspace_size(hs[0], batch), dtype=torch.uint8,
+                                         device=dev))}
+    ens_tol = 0.005
+    api.stomsfem_surrogate_set_partner(hs[0], hs[1], ens_tol)
+    sur["ensemble"] = dict(tol=ens_tol, **sur_arm(torch.empty(api.stomsfem_surrogate_workspace_size(hs[0], batch),
+                                                              dtype=torch.uint8, device=dev)))
+    for hh in hs:
+        api.stomsfem_surrogate_destroy(hh)
+    out["surrogate"] = sur
+    out["note"] = ("random interpolation is not run here: its degree rule's sparse grids exceed the 2048 points "
+                   "per family that the online kernel holds (46,656 for one family at eps = 1e-3, 3,888 at "
+                   "eps = 0.1)")
     return out
 
 
@@ -1013,6 +1078,9 @@ def main():
                     help="skip the reduced-basis, surrogate and interpolation measurements")
     ap.add_argument("--contrast-batch", type=int, default=128, help="samples per step of the contrast_2048 arms")
     ap.add_argument("--contrast-train", type=int, default=24, help="POD training samples on contrast_2048 (<= 24)")
+    ap.add_argument("--contrast-sur-train", type=int, default=1024,
+                    help="surrogate training samples on contrast_2048")
+    ap.add_argument("--contrast-sur-steps", type=int, default=20000, help="surrogate training steps on contrast_2048")
     ap.add_argument("--sections", default="",
                     help="comma-separated subset of the extra sections (engines, petrov_galerkin, pod, surrogate, "
                          "ri, pod_affine, two_level_mc, two_level_mc_1024, contrast_2048, mixed_bc, "
@@ -1279,7 +1347,9 @@ def main():
             ("two_level_mc", lambda: bench_two_level(api, dev, stream)),
             ("two_level_mc_1024", lambda: bench_two_level_1024(api, dev, stream, ov)),
             ("contrast_2048", lambda: bench_contrast(api, dev, stream, batch=args.contrast_batch,
-                                                     n_train=args.contrast_train)),
+                                                     n_train=args.contrast_train,
+                                                     n_sur_train=args.contrast_sur_train,
+                                                     sur_steps=args.contrast_sur_steps)),
             ("mixed_bc", lambda: bench_mixed_bc(api, g, nn, stream, dev, bf["Ke"], bf["be"], 0)),
             ("oscillatory_bc", lambda: dict(form=form, **bench_oscillatory(api, g, bf, ov_t, mo, FORMS[form],
                                                                            stream))),
