@@ -18,6 +18,9 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
                       const int32_t* unit_count, double* Ke, double* be, void* workspace,
                       size_t workspace_bytes, cudaStream_t st);
 size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid);
+// Workspace of upscale_list_fp64 that keeps every SM at its resident units
+// (16 slots per SM: four blocks of two warps, two units per warp).
+size_t upscale_list_workspace_fp64(const stomsfem_grid* grid);
 // Scratch slots (units in flight) of one block of the upscaling launch for a
 // grid, oversampling limit and precision with the default engine: the least
 // workspace stomsfem_upscale accepts, in slots (8 in the FP32 forms, two

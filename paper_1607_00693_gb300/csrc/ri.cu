@@ -587,7 +587,7 @@ extern "C" int stomsfem_ri_build(const stomsfem_grid* grid, const stomsfem_field
   const size_t per_pt = (size_t)nf * nf * 8 + (size_t)ncell * 112 + (size_t)K * 8 + 4;
   long long chunk = (256ll << 20) / (long long)per_pt;
   chunk = std::max(1ll, std::min(chunk, std::min(4096ll, P.npoints)));
-  const size_t fb_bytes = upscale_slot_bytes_fp64(grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 8;
+  const size_t fb_bytes = upscale_list_workspace_fp64(grid);
   TRY(cudaMalloc(&xi_c, sizeof(double) * chunk * K));
   TRY(cudaMalloc(&a_c, sizeof(double) * chunk * nf * nf));
   TRY(cudaMalloc(&Ke_c, sizeof(double) * chunk * ncell * 10));
@@ -652,7 +652,7 @@ extern "C" int stomsfem_ri_values(const stomsfem_ri* ri, double* V_host, int64_t
 }
 
 static size_t ri_fb_bytes(const stomsfem_ri* ri) {
-  return upscale_slot_bytes_fp64(&ri->grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 8;
+  return upscale_list_workspace_fp64(&ri->grid);
 }
 
 extern "C" int stomsfem_ri_workspace_size(const stomsfem_ri* ri, int32_t S, size_t* bytes) {

@@ -1258,7 +1258,7 @@ InferLayout infer_layout(const stomsfem_surrogate* h, int S, std::vector<int>* r
     L.f2 = o;  o += al(L.units);
   }
   L.fb = o;
-  o += upscale_slot_bytes_fp64(&h->grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 8;
+  o += upscale_list_workspace_fp64(&h->grid);
   L.total = o;
   return L;
 }

@@ -76,8 +76,11 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   if (bmax > kMaxBand) return set_error(STOMSFEM_EINVAL, "bandwidth %d > %d", bmax, kMaxBand);
   size_t sb, lb;
   slot_layout(nmax, bmax, STOMSFEM_FP64, &sb, &lb);
+  // two units per warp, as the plain FP64 upscaler (the list's cells have no
+  // oversampling: one patch shape)
+  constexpr int kSlotsPerBlock = upscale_warps(true, 16) * 2;
   const long long slots = (long long)(workspace_bytes / sb);
-  if (slots < kUpscaleWarps) return set_error(STOMSFEM_ENOMEM, "fallback workspace too small");
+  if (slots < kSlotsPerBlock) return set_error(STOMSFEM_ENOMEM, "fallback workspace too small");
   UpscaleArgs A;
   A.a = a;
   A.oversample = nullptr;
@@ -106,7 +109,7 @@ int upscale_list_fp64(const stomsfem_grid* grid, const double* a, int32_t S, con
   A.cell_count = nullptr;
   A.blocks_per_sm_cap = 0;
   A.order = 0;
-  return launch_rpl<double, double, 32>(A, slots / kUpscaleWarps, st);
+  return launch_rpl<double, double, 16>(A, slots / kSlotsPerBlock, st);
 }
 
 int upscale_slots_per_block(const stomsfem_grid* grid, int32_t max_oversample, int precision) {
@@ -134,6 +137,10 @@ size_t upscale_slot_bytes_fp64(const stomsfem_grid* grid) {
   size_t sb, lb;
   slot_layout(nmax, bmax, STOMSFEM_FP64, &sb, &lb);
   return sb;
+}
+
+size_t upscale_list_workspace_fp64(const stomsfem_grid* grid) {
+  return upscale_slot_bytes_fp64(grid) * (size_t)(device_sm_count() > 0 ? device_sm_count() : 152) * 16;
 }
 
 // stomsfem_upscale with launch choices (the plan's autotuner).

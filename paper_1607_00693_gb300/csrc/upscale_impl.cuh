@@ -31,7 +31,6 @@ namespace stomsfem {
 // Warps per block: 4, except 2 for two FP64 units per warp (whose 36 KB of
 // shared memory per warp then fit three blocks on an SM).
 __host__ __device__ constexpr int upscale_warps(bool fp64, int G) { return fp64 && G == 16 ? 2 : 4; }
-constexpr int kUpscaleWarps = 4;  // list mode (one FP64 unit per warp)
 constexpr int kMaxBand = 64;       // half bandwidth limit (mx + 1)
 
 struct UnitGeom {
@@ -540,9 +539,13 @@ upscale_kernel(UpscaleArgs A) {
 
   // cells of this launch (MODE 1, 2: a device list, or all cells when none)
   const int nlc = A.cell_list ? A.cell_count[0] : ncell;
-  // work items: (sample, cell) for G = 32, (pair of samples, cell) for G = 16
+  // work items: (sample, cell) for G = 32, (pair of samples, cell) for G = 16;
+  // with a unit list, one entry (G = 32) or two consecutive entries (G = 16:
+  // the list holds cells without oversampling only, all of one patch shape,
+  // so the two halves of a warp run in lockstep)
   const long long npair = G == 32 ? (long long)A.S : (long long)((A.S + 1) / 2);
-  const long long nwork = A.unit_list ? (long long)A.unit_count[0] : npair * nlc;
+  const long long nlist = A.unit_list ? (long long)A.unit_count[0] : 0;
+  const long long nwork = A.unit_list ? (G == 32 ? nlist : (nlist + 1) / 2) : npair * nlc;
   for (long long w = gw; w < nwork; w += nw) {
     long long u;
     bool dup = false;  // this half mirrors the other half's unit
@@ -551,6 +554,13 @@ upscale_kernel(UpscaleArgs A) {
     const int cell_w = A.cell_list ? A.cell_list[ci] : ci;
     if (G == 32) {
       u = A.unit_list ? (long long)A.unit_list[w] : pw * ncell + cell_w;
+    } else if (A.unit_list) {
+      long long li = 2 * w + grp;
+      if (li >= nlist) {
+        li = nlist - 1;
+        dup = true;
+      }
+      u = (long long)A.unit_list[li];
     } else {
       int sp = 2 * (int)pw + grp;
       if (sp >= A.S) {
