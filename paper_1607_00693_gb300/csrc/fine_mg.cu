@@ -55,15 +55,18 @@ __global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, fl
     if (interior(i, j, nf)) {
       const double aSW = as[(size_t)(j - 1) * nf + i - 1], aSE = as[(size_t)(j - 1) * nf + i];
       const double aNE = as[(size_t)j * nf + i], aNW = as[(size_t)j * nf + i - 1];
-      c[4] = (float)((4.0 / 6.0) * (aSW + aSE + aNE + aNW));
-      c[3] = (float)(-(aSW + aNW) / 6.0);  // west
-      c[5] = (float)(-(aSE + aNE) / 6.0);  // east
-      c[1] = (float)(-(aSW + aSE) / 6.0);  // south
-      c[7] = (float)(-(aNW + aNE) / 6.0);  // north
-      c[0] = (float)(-aSW / 3.0);
-      c[2] = (float)(-aSE / 3.0);
-      c[8] = (float)(-aNE / 3.0);
-      c[6] = (float)(-aNW / 3.0);
+      // products with 1/6 and 1/3, not quotients: an FP64 division is a
+      // long instruction sequence on the FP64 pipe
+      constexpr double k6 = 1.0 / 6.0, k3 = 1.0 / 3.0;
+      c[4] = (float)((4.0 * k6) * (aSW + aSE + aNE + aNW));
+      c[3] = (float)(-(aSW + aNW) * k6);  // west
+      c[5] = (float)(-(aSE + aNE) * k6);  // east
+      c[1] = (float)(-(aSW + aSE) * k6);  // south
+      c[7] = (float)(-(aNW + aNE) * k6);  // north
+      c[0] = (float)(-aSW * k3);
+      c[2] = (float)(-aSE * k3);
+      c[8] = (float)(-aNE * k3);
+      c[6] = (float)(-aNW * k3);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) ss[(size_t)k * N + v] = c[k];
@@ -144,6 +147,43 @@ __global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const fl
   }
 }
 
+// The coarsest grid (nf <= 16: at most 289 nodes): all kMgCoarseSweeps
+// damped Jacobi sweeps from zero in one launch, one CTA per sample, the
+// iterates in shared memory; each sweep is mgf_jacobi_kernel's arithmetic.
+constexpr int kMgCoarseMaxNodes = 289;
+constexpr int kMgCoarseThreads = 320;
+
+__global__ void __launch_bounds__(kMgCoarseThreads) mgf_coarse_kernel(int nf, const float* __restrict__ st,
+                                                                      const float* __restrict__ f,
+                                                                      float* __restrict__ u) {
+  __shared__ float buf[2][kMgCoarseMaxNodes];
+  const int s = blockIdx.x;
+  const int W = nf + 1, N = W * W;
+  const int v = threadIdx.x;
+  const bool in = v < N && interior(v % W, v / W, nf);
+  float c[9], fv = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c[k] = in ? st[((size_t)s * 9 + k) * N + v] : 0.f;
+  if (in) fv = f[(size_t)s * N + v];
+  float o = in ? 0.f + kMgOmega * (fv - 0.f) / c[4] : 0.f;  // the first sweep, from zero
+  if (v < N) buf[0][v] = o;
+  __syncthreads();
+  for (int k = 1; k < kMgCoarseSweeps; ++k) {
+    const float* ui = buf[(k - 1) & 1];
+    if (in) {
+      float t = 0.f;
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+        for (int di = -1; di <= 1; ++di) t = fmaf(c[(dj + 1) * 3 + di + 1], ui[v + dj * W + di], t);
+      o = ui[v] + kMgOmega * (fv - t) / c[4];
+    }
+    if (v < N) buf[k & 1][v] = o;
+    __syncthreads();
+  }
+  if (v < N) u[(size_t)s * N + v] = o;
+}
+
 // r = f - A u at the interior nodes (0 elsewhere).
 __global__ void mgf_residual_kernel(int nf, const float* __restrict__ st, const float* __restrict__ f,
                                     const float* __restrict__ u, float* __restrict__ r) {
@@ -221,9 +261,12 @@ __global__ void __launch_bounds__(kMgThreads) cg_matvec_kernel(int nf, const dou
       const double aSW = as[(size_t)(j - 1) * nf + i - 1], aSE = as[(size_t)(j - 1) * nf + i];
       const double aNE = as[(size_t)j * nf + i], aNW = as[(size_t)j * nf + i - 1];
       const double* q = ps + v;
-      t = (4.0 / 6.0) * (aSW + aSE + aNE + aNW) * q[0] - ((aSW + aNW) * q[-1] + (aSE + aNE) * q[1] +
-                                                          (aSW + aSE) * q[-W] + (aNW + aNE) * q[W]) / 6.0 -
-          (aSW * q[-W - 1] + aSE * q[-W + 1] + aNE * q[W + 1] + aNW * q[W - 1]) / 3.0;
+      // (1/6) (4 sum(a) q_c - edge terms - 2 diagonal terms): one product
+      // with 1/6 in place of FP64 divisions
+      t = (4.0 * (aSW + aSE + aNE + aNW) * q[0] -
+           ((aSW + aNW) * q[-1] + (aSE + aNE) * q[1] + (aSW + aSE) * q[-W] + (aNW + aNE) * q[W]) -
+           2.0 * (aSW * q[-W - 1] + aSE * q[-W + 1] + aNE * q[W + 1] + aNW * q[W - 1])) *
+          (1.0 / 6.0);
       acc += q[0] * t;
     }
     Ap[(size_t)s * N + v] = t;
@@ -364,12 +407,8 @@ int vcycle(MgLevel* lv, int L, int l, int S, cudaStream_t st) {
   MgLevel& c = lv[l];
   const dim3 g = grid2(c.N, S);
   if (l == L - 1) {
-    mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u2, c.u, 1);
-    for (int k = 1; k < kMgCoarseSweeps; ++k) {
-      mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, (k & 1) ? c.u : c.u2, (k & 1) ? c.u2 : c.u, 0);
-    }
-    if (kMgCoarseSweeps % 2 == 0)
-      STOMSFEM_TRY_CUDA(cudaMemcpyAsync(c.u, c.u2, sizeof(float) * (size_t)c.N * S, cudaMemcpyDeviceToDevice, st));
+    if (c.N > kMgCoarseMaxNodes) return set_error(STOMSFEM_EINVAL, "coarsest grid of %d nodes", c.N);
+    mgf_coarse_kernel<<<S, kMgCoarseThreads, 0, st>>>(c.nf, c.st, c.f, c.u);
     return check_cuda(cudaGetLastError(), "coarse sweeps");
   }
   // pre-smoothing from zero
