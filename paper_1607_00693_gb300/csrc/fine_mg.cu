@@ -14,8 +14,9 @@
 // sample in FP32, structure of arrays over the full (nf_l+1)^2 node grid
 // (boundary nodes carry zero stencils and stay zero).
 //
-// CG: x, r, p, Ap in FP64; the matrix-vector product forms the fine 9-point
-// stencil from a in FP64 (nothing of the FP64 operator is stored); the
+// CG: x, r, p, Ap in FP64; the matrix-vector product applies the fine
+// 9-point stencil in FP64, formed from a once per solve and stored in
+// symmetric form (five entries per node, nine FMAs per product); the
 // per-sample dot products are block sums with one atomic per block; the
 // step lengths are computed on the device.  The host checks convergence
 // (max over samples of |r| / |f|) every few iterations.
@@ -43,21 +44,34 @@ struct MgLevel {
 
 __device__ __forceinline__ bool interior(int i, int j, int nf) { return i > 0 && j > 0 && i < nf && j < nf; }
 
-// Level-0 stencil from a: st[k][node], k = (dj + 1) * 3 + (di + 1).
-__global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, float* __restrict__ st) {
+// Level-0 stencil from a: st[k][node], k = (dj + 1) * 3 + (di + 1), FP32
+// for the preconditioner; and the FP64 operator of the CG in symmetric form,
+// st64[k][node] for k = centre, east, north, north-east, north-west (the
+// west, south, south-west and south-east entries of a node are the east,
+// north, north-east and north-west entries of its neighbours there; zero
+// at the boundary nodes, whose values are zero in every CG vector).
+__global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, float* __restrict__ st,
+                                        double* __restrict__ st64) {
   const int s = blockIdx.y;
   const int N = (nf + 1) * (nf + 1);
   const double* as = a + (size_t)s * nf * nf;
   float* ss = st + (size_t)s * 9 * N;
+  double* s64 = st64 + (size_t)s * 5 * N;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     const int i = v % (nf + 1), j = v / (nf + 1);
     float c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double d[5] = {0, 0, 0, 0, 0};
     if (interior(i, j, nf)) {
       const double aSW = as[(size_t)(j - 1) * nf + i - 1], aSE = as[(size_t)(j - 1) * nf + i];
       const double aNE = as[(size_t)j * nf + i], aNW = as[(size_t)j * nf + i - 1];
       // products with 1/6 and 1/3, not quotients: an FP64 division is a
       // long instruction sequence on the FP64 pipe
       constexpr double k6 = 1.0 / 6.0, k3 = 1.0 / 3.0;
+      d[0] = (4.0 * k6) * (aSW + aSE + aNE + aNW);
+      d[1] = -(aSE + aNE) * k6;
+      d[2] = -(aNW + aNE) * k6;
+      d[3] = -aNE * k3;
+      d[4] = -aNW * k3;
       c[4] = (float)((4.0 * k6) * (aSW + aSE + aNE + aNW));
       c[3] = (float)(-(aSW + aNW) * k6);  // west
       c[5] = (float)(-(aSE + aNE) * k6);  // east
@@ -70,6 +84,8 @@ __global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, fl
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) ss[(size_t)k * N + v] = c[k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s64[(size_t)k * N + v] = d[k];
   }
 }
 
@@ -245,28 +261,30 @@ __device__ __forceinline__ void block_sum_to(double v, double* acc) {
   __syncthreads();
 }
 
-// Ap = A p (FP64 stencil from a), and pAp[s] += p . Ap.
-__global__ void __launch_bounds__(kMgThreads) cg_matvec_kernel(int nf, const double* __restrict__ a,
+// Ap = A p (the stored FP64 stencil in symmetric form), and pAp[s] += p . Ap.
+__global__ void __launch_bounds__(kMgThreads) cg_matvec_kernel(int nf, const double* __restrict__ st64,
                                                                const double* __restrict__ p, double* __restrict__ Ap,
                                                                double* __restrict__ pAp) {
   const int s = blockIdx.y;
   const int W = nf + 1, N = W * W;
-  const double* as = a + (size_t)s * nf * nf;
+  const double* C = st64 + (size_t)s * 5 * N;
+  const double *E = C + N, *Nn = C + 2 * (size_t)N, *NE = C + 3 * (size_t)N, *NW = C + 4 * (size_t)N;
   const double* ps = p + (size_t)s * N;
   double acc = 0.0;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     const int i = v % W, j = v / W;
     double t = 0.0;
     if (interior(i, j, nf)) {
-      const double aSW = as[(size_t)(j - 1) * nf + i - 1], aSE = as[(size_t)(j - 1) * nf + i];
-      const double aNE = as[(size_t)j * nf + i], aNW = as[(size_t)j * nf + i - 1];
       const double* q = ps + v;
-      // (1/6) (4 sum(a) q_c - edge terms - 2 diagonal terms): one product
-      // with 1/6 in place of FP64 divisions
-      t = (4.0 * (aSW + aSE + aNE + aNW) * q[0] -
-           ((aSW + aNW) * q[-1] + (aSE + aNE) * q[1] + (aSW + aSE) * q[-W] + (aNW + aNE) * q[W]) -
-           2.0 * (aSW * q[-W - 1] + aSE * q[-W + 1] + aNE * q[W + 1] + aNW * q[W - 1])) *
-          (1.0 / 6.0);
+      t = C[v] * q[0];
+      t = fma(E[v], q[1], t);
+      t = fma(E[v - 1], q[-1], t);
+      t = fma(Nn[v], q[W], t);
+      t = fma(Nn[v - W], q[-W], t);
+      t = fma(NE[v], q[W + 1], t);
+      t = fma(NE[v - W - 1], q[-W - 1], t);
+      t = fma(NW[v], q[W - 1], t);
+      t = fma(NW[v - W + 1], q[-W + 1], t);
       acc += q[0] * t;
     }
     Ap[(size_t)s * N + v] = t;
@@ -383,9 +401,9 @@ size_t mg_layout(int nf, int S, MgLevel* lv, int* L, unsigned char* base, double
     o += al256(sizeof(float) * N * S);
   }
   const size_t N0 = (size_t)(nf + 1) * (nf + 1);
-  for (int k = 0; k < 3; ++k) {  // r, p, Ap (x is the caller's u)
+  for (int k = 0; k < 4; ++k) {  // r, p, Ap (x is the caller's u), then the FP64 stencil [S][5][N0]
     vec[k] = reinterpret_cast<double*>(base + o);
-    o += al256(sizeof(double) * N0 * S);
+    o += al256(sizeof(double) * N0 * S * (k == 3 ? 5 : 1));
   }
   *scal = reinterpret_cast<double*>(base + o);  // alpha, pAp, rz, rz_old, rr, bb [S] doubles, done [S] int
   o += al256(sizeof(double) * 6 * S + sizeof(int32_t) * S);
@@ -432,7 +450,7 @@ namespace stomsfem {
 size_t fine_mg_workspace_bytes(int nf, int S) {
   MgLevel lv[kMgMaxLevels];
   int L;
-  double* vec[3];
+  double* vec[4];
   double* scal;
   return mg_layout(nf, S, lv, &L, nullptr, vec, &scal);
 }
@@ -450,19 +468,19 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
                   double rtol, int max_iters, cudaStream_t st, double* res, int* iters) {
   MgLevel lv[kMgMaxLevels];
   int L;
-  double* vec[3];
+  double* vec[4];
   double* scal;
   const size_t need = mg_layout(nf, S, lv, &L, static_cast<unsigned char*>(workspace), vec, &scal);
   if (workspace_bytes < need)
     return set_error(STOMSFEM_ENOMEM, "fine FEM workspace %zu < %zu bytes", workspace_bytes, need);
-  double *r = vec[0], *p = vec[1], *Ap = vec[2];
+  double *r = vec[0], *p = vec[1], *Ap = vec[2], *st64 = vec[3];
   double *alpha = scal, *pAp = scal + S, *rz = scal + 2 * S, *rz_old = scal + 3 * S, *rr = scal + 4 * S,
          *bb = scal + 5 * S;
   int32_t* done = reinterpret_cast<int32_t*>(scal + 6 * S);
   const int N0 = lv[0].N;
   const dim3 g0 = grid2(N0, S);
   // multigrid set-up: stencils of every level
-  mgf_fine_stencil_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, lv[0].st);
+  mgf_fine_stencil_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, lv[0].st, st64);
   for (int l = 0; l + 1 < L; ++l)
     mgf_rap_kernel<<<grid2(lv[l + 1].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l + 1].st);
   STOMSFEM_TRY_CUDA(cudaGetLastError());
@@ -484,7 +502,7 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
   for (it = 1; it <= max_iters; ++it) {
     STOMSFEM_TRY_CUDA(cudaMemsetAsync(pAp, 0, sizeof(double) * S, st));
     STOMSFEM_TRY_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * S, st));
-    cg_matvec_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, p, Ap, pAp);
+    cg_matvec_kernel<<<g0, kMgThreads, 0, st>>>(nf, st64, p, Ap, pAp);
     cg_alpha_kernel<<<(S + 127) / 128, 128, 0, st>>>(S, rz, pAp, done, alpha);
     cg_update_kernel<<<g0, kMgThreads, 0, st>>>(nf, alpha, p, Ap, u, r, lv[0].f, rr);
     STOMSFEM_TRY_CUDA(cudaGetLastError());
