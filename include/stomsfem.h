@@ -412,7 +412,7 @@ int stomsfem_local_kl_project(const stomsfem_local_kl* kl, const double* kappa, 
 
 /* Scratch needed by stomsfem_fine_fem for S samples (nf <= 64: the banded
  * factors of the warps in flight; larger nf: the multigrid hierarchy, the
- * CG vectors and the FP64 operator of all S samples, about 135 bytes per
+ * CG vectors and the FP64 operator of all S samples, about 112 bytes per
  * fine node and sample).  EINVAL for an nf above 64 that does not halve down to 16 or
  * less. */
 int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);

@@ -11,8 +11,11 @@
 // and after the coarse correction: a symmetric V-cycle, so the
 // preconditioner is symmetric positive definite and plain CG applies), and
 // 60 Jacobi sweeps on the coarsest grid.  Stencils are stored per level and
-// sample in FP32, structure of arrays over the full (nf_l+1)^2 node grid
-// (boundary nodes carry zero stencils and stay zero).
+// sample in FP32, structure of arrays over the full (nf_l+1)^2 node grid,
+// in symmetric form: five couplings per node (centre, east, north,
+// north-east, north-west), the other four read from the neighbours, so
+// every level's operator is exactly symmetric (boundary nodes carry zero
+// stencils and stay zero).
 //
 // CG: x, r, p, Ap in FP64; the matrix-vector product applies the fine
 // 9-point stencil in FP64, formed from a once per solve and stored in
@@ -35,7 +38,7 @@ constexpr int kMgThreads = 256;
 struct MgLevel {
   int nf;          // elements per side
   int N;           // (nf + 1)^2 nodes
-  float* st;       // [S][9][N]
+  float* st;       // [S][5][N]: centre, east, north, north-east, north-west
   float* u;        // [S][N]
   float* u2;       // [S][N] (Jacobi ping-pong)
   float* f;        // [S][N]
@@ -44,8 +47,29 @@ struct MgLevel {
 
 __device__ __forceinline__ bool interior(int i, int j, int nf) { return i > 0 && j > 0 && i < nf && j < nf; }
 
-// Level-0 stencil from a: st[k][node], k = (dj + 1) * 3 + (di + 1), FP32
-// for the preconditioner; and the FP64 operator of the CG in symmetric form,
+// Stencils of every level in symmetric form: st[m][node] for m = 0..4 the
+// centre, east, north, north-east and north-west couplings of the node; the
+// west, south, south-west and south-east couplings are the east, north,
+// north-east and north-west ones of the neighbour there (zero at the
+// boundary nodes, whose values stay zero in every multigrid vector).
+// Entry k = (dj + 1) * 3 + (di + 1) of the 9-point stencil of node v:
+__device__ __forceinline__ int st_arr(int k) {  // array m holding entry k
+  return k == 4 ? 0 : (k == 5 || k == 3) ? 1 : (k == 7 || k == 1) ? 2 : (k == 8 || k == 0) ? 3 : 4;
+}
+__device__ __forceinline__ long st_node(int k, long v, int W) {  // node whose array holds it
+  const int di = k % 3 - 1, dj = k / 3 - 1;
+  return (dj < 0 || (dj == 0 && di < 0)) ? v + dj * W + di : v;
+}
+template <int K>
+__device__ __forceinline__ float st9(const float* __restrict__ st, size_t N, long v, int W) {
+  constexpr int di = K % 3 - 1, dj = K / 3 - 1;
+  constexpr int m = K == 4 ? 0 : (K == 5 || K == 3) ? 1 : (K == 7 || K == 1) ? 2 : (K == 8 || K == 0) ? 3 : 4;
+  constexpr bool own = !(dj < 0 || (dj == 0 && di < 0));
+  return st[(size_t)m * N + (own ? v : v + dj * W + di)];
+}
+
+// Level-0 stencil from a, FP32 for the preconditioner (symmetric form
+// above); and the FP64 operator of the CG in symmetric form,
 // st64[k][node] for k = centre, east, north, north-east, north-west (the
 // west, south, south-west and south-east entries of a node are the east,
 // north, north-east and north-west entries of its neighbours there; zero
@@ -55,7 +79,7 @@ __global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, fl
   const int s = blockIdx.y;
   const int N = (nf + 1) * (nf + 1);
   const double* as = a + (size_t)s * nf * nf;
-  float* ss = st + (size_t)s * 9 * N;
+  float* ss = st + (size_t)s * 5 * N;
   double* s64 = st64 + (size_t)s * 5 * N;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     const int i = v % (nf + 1), j = v / (nf + 1);
@@ -82,8 +106,11 @@ __global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, fl
       c[8] = (float)(-aNE * k3);
       c[6] = (float)(-aNW * k3);
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) ss[(size_t)k * N + v] = c[k];
+    ss[v] = c[4];
+    ss[(size_t)N + v] = c[5];
+    ss[(size_t)2 * N + v] = c[7];
+    ss[(size_t)3 * N + v] = c[8];
+    ss[(size_t)4 * N + v] = c[6];
 #pragma unroll
     for (int k = 0; k < 5; ++k) s64[(size_t)k * N + v] = d[k];
   }
@@ -100,8 +127,8 @@ __global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, float* __
   const int s = blockIdx.y;
   const int nfc = nff / 2;
   const int Nf = (nff + 1) * (nff + 1), Nc = (nfc + 1) * (nfc + 1);
-  const float* sf = stf + (size_t)s * 9 * Nf;
-  float* sc = stc + (size_t)s * 9 * Nc;
+  const float* sf = stf + (size_t)s * 5 * Nf;
+  float* sc = stc + (size_t)s * 5 * Nc;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nc; v += gridDim.x * blockDim.x) {
     const int I = v % (nfc + 1), J = v / (nfc + 1);
     float out[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -113,7 +140,8 @@ __global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, float* __
           const int fv = fy * (nff + 1) + fx;
           for (int ej = -1; ej <= 1; ++ej)
             for (int ei = -1; ei <= 1; ++ei) {
-              const float afv = sf[(size_t)((ej + 1) * 3 + ei + 1) * Nf + fv];
+              const int k = (ej + 1) * 3 + ei + 1;
+              const float afv = sf[(size_t)st_arr(k) * Nf + st_node(k, fv, nff + 1)];
               if (afv == 0.f) continue;
               const int gx = fx + ei, gy = fy + ej;  // neighbour fine node
               // coarse nodes (I + cI, J + cJ) whose hats cover (gx, gy)
@@ -127,18 +155,27 @@ __global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, float* __
             }
         }
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sc[(size_t)k * Nc + v] = out[k];
+    sc[v] = out[4];
+    sc[(size_t)Nc + v] = out[5];
+    sc[(size_t)2 * Nc + v] = out[7];
+    sc[(size_t)3 * Nc + v] = out[8];
+    sc[(size_t)4 * Nc + v] = out[6];
   }
 }
 
-__device__ __forceinline__ float apply9(const float* __restrict__ st, size_t N, size_t v, const float* __restrict__ u,
+// (A u)_v at an interior node from the symmetric stencil form.
+__device__ __forceinline__ float apply9(const float* __restrict__ st, size_t N, long v, const float* __restrict__ u,
                                         int W) {
   float t = 0.f;
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) t = fmaf(st[(size_t)((dj + 1) * 3 + di + 1) * N + v], u[v + dj * W + di], t);
+  t = fmaf(st9<0>(st, N, v, W), u[v - W - 1], t);
+  t = fmaf(st9<1>(st, N, v, W), u[v - W], t);
+  t = fmaf(st9<2>(st, N, v, W), u[v - W + 1], t);
+  t = fmaf(st9<3>(st, N, v, W), u[v - 1], t);
+  t = fmaf(st9<4>(st, N, v, W), u[v], t);
+  t = fmaf(st9<5>(st, N, v, W), u[v + 1], t);
+  t = fmaf(st9<6>(st, N, v, W), u[v + W - 1], t);
+  t = fmaf(st9<7>(st, N, v, W), u[v + W], t);
+  t = fmaf(st9<8>(st, N, v, W), u[v + W + 1], t);
   return t;
 }
 
@@ -147,7 +184,7 @@ __global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const fl
                                   const float* __restrict__ ui, float* __restrict__ uo, int zero_in) {
   const int s = blockIdx.y;
   const int W = nf + 1, N = W * W;
-  const float* ss = st + (size_t)s * 9 * N;
+  const float* ss = st + (size_t)s * 5 * N;
   const float* fs = f + (size_t)s * N;
   const float* us = ui + (size_t)s * N;
   float* os = uo + (size_t)s * N;
@@ -155,7 +192,7 @@ __global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const fl
     const int i = v % W, j = v / W;
     float o = 0.f;
     if (interior(i, j, nf)) {
-      const float d = ss[(size_t)4 * N + v];
+      const float d = ss[v];
       const float au = zero_in ? 0.f : apply9(ss, N, v, us, W);
       o = (zero_in ? 0.f : us[v]) + kMgOmega * (fs[v] - au) / d;
     }
@@ -178,8 +215,9 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mgf_coarse_kernel(int nf, co
   const int v = threadIdx.x;
   const bool in = v < N && interior(v % W, v / W, nf);
   float c[9], fv = 0.f;
+  const float* ss = st + (size_t)s * 5 * N;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) c[k] = in ? st[((size_t)s * 9 + k) * N + v] : 0.f;
+  for (int k = 0; k < 9; ++k) c[k] = in ? ss[(size_t)st_arr(k) * N + st_node(k, v, W)] : 0.f;
   if (in) fv = f[(size_t)s * N + v];
   float o = in ? 0.f + kMgOmega * (fv - 0.f) / c[4] : 0.f;  // the first sweep, from zero
   if (v < N) buf[0][v] = o;
@@ -205,7 +243,7 @@ __global__ void mgf_residual_kernel(int nf, const float* __restrict__ st, const 
                                     const float* __restrict__ u, float* __restrict__ r) {
   const int s = blockIdx.y;
   const int W = nf + 1, N = W * W;
-  const float* ss = st + (size_t)s * 9 * N;
+  const float* ss = st + (size_t)s * 5 * N;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     const int i = v % W, j = v / W;
     r[(size_t)s * N + v] = interior(i, j, nf) ? f[(size_t)s * N + v] - apply9(ss, N, v, u + (size_t)s * N, W) : 0.f;
@@ -390,7 +428,7 @@ size_t mg_layout(int nf, int S, MgLevel* lv, int* L, unsigned char* base, double
     lv[l].nf = nfs[l];
     lv[l].N = (int)N;
     lv[l].st = reinterpret_cast<float*>(base + o);
-    o += al256(sizeof(float) * 9 * N * S);
+    o += al256(sizeof(float) * 5 * N * S);
     lv[l].u = reinterpret_cast<float*>(base + o);
     o += al256(sizeof(float) * N * S);
     lv[l].u2 = reinterpret_cast<float*>(base + o);
