@@ -7,7 +7,7 @@
 // Multigrid: levels nf_0 = nf, nf_{l+1} = nf_l / 2 down to nf_L <= 16;
 // bilinear prolongation P (coarse node (I, J) at fine node (2I, 2J)),
 // restriction P^T, Galerkin coarse operators A_{l+1} = P^T A_l P (9-point
-// stencils again), damped Jacobi smoothing (omega = 0.6, two sweeps before
+// stencils again), damped Jacobi smoothing (omega = 0.8, two sweeps before
 // and after the coarse correction: a symmetric V-cycle, so the
 // preconditioner is symmetric positive definite and plain CG applies), and
 // 60 Jacobi sweeps on the coarsest grid.  Stencils are stored per level and
@@ -31,7 +31,7 @@
 namespace stomsfem {
 
 constexpr int kMgMaxLevels = 12;
-constexpr float kMgOmega = 0.6f;
+constexpr float kMgOmega = 0.8f;
 constexpr int kMgCoarseSweeps = 60;
 constexpr int kMgThreads = 256;
 
@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(kMgThreads) cg_rz_kernel(int nf, const double*
   block_sum_to(acc, rz + s);
 }
 
-// p = z + beta p, beta = rz_new / rz_old (p = z on the first step).
+// p = z + beta p, beta = rz_new / rz_old (p = z on the first step, where p
+// is not read: the workspace holds whatever it held before).
 __global__ void cg_direction_kernel(int nf, const float* __restrict__ z, const double* __restrict__ rz_new,
                                     const double* __restrict__ rz_old, const int32_t* done, int first,
                                     double* __restrict__ p) {
@@ -377,7 +378,7 @@ __global__ void cg_direction_kernel(int nf, const float* __restrict__ z, const d
   const double beta = (first || done[s] || !(rz_old[s] != 0.0)) ? 0.0 : rz_new[s] / rz_old[s];
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     const size_t q = (size_t)s * N + v;
-    p[q] = done[s] ? 0.0 : (double)z[q] + beta * p[q];
+    p[q] = done[s] ? 0.0 : first ? (double)z[q] : (double)z[q] + beta * p[q];
   }
 }
 
@@ -548,13 +549,16 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
       STOMSFEM_TRY_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
       STOMSFEM_TRY_CUDA(cudaStreamSynchronize(st));
       worst = 0.0;
-      bool all = true;
+      bool all = true, finite = true;
       for (int s = 0; s < S; ++s) {
         const double rel = hb[s] > 0.0 ? std::sqrt(hr[s] / hb[s]) : 0.0;
+        if (!std::isfinite(rel)) finite = false;
         if (rel <= rtol) hd[s] = 1;
         if (!hd[s]) all = false;
         worst = std::max(worst, rel);
       }
+      if (!finite)
+        return set_error(STOMSFEM_ENOTSPD, "fine FEM CG: non-finite residual after %d iterations", it);
       if (all) break;
       STOMSFEM_TRY_CUDA(cudaMemcpyAsync(done, hd.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
     }
@@ -568,8 +572,8 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
   }
   if (res) *res = worst;
   if (iters) *iters = it > max_iters ? max_iters : it;
-  if (worst > rtol) return set_error(STOMSFEM_ENOTSPD, "fine FEM CG: relative residual %.3e after %d iterations",
-                                     worst, max_iters);
+  if (!(worst <= rtol))
+    return set_error(STOMSFEM_ENOTSPD, "fine FEM CG: relative residual %.3e after %d iterations", worst, max_iters);
   return STOMSFEM_OK;
 }
 
