@@ -426,7 +426,8 @@ int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_
  *    samples at once, preconditioned by one multigrid V-cycle in FP32
  *    (bilinear prolongation, Galerkin coarse operators, damped Jacobi
  *    smoothing), until every sample's recursively updated CG residual is
- *    at most 1e-13 of its load (at most 400 iterations, else ENOTSPD);
+ *    at most 1e-13 of its load (at most 400 iterations, else ENOTSPD;
+ *    ENOTSPD too as soon as a residual is not finite);
  *    the true residual b - A u then sits at the FP64 rounding floor
  *    (about eps || |A| |u| ||, e.g. 2e-11 of the load on a 1024^2
  *    lognormal medium); synchronises `stream` (convergence is checked on
