@@ -7,7 +7,8 @@ solve is out of reach, against the definition: the residual of the Q1
 system assembled element by element here (numpy) at the FP64 rounding
 floor, |b - A u| <= 1e-12 |b| + 4 eps || |A| |u| || (the componentwise
 floor is 5e-11 |b| on this medium: a sparse direct solve in FP64 reaches
-3.3e-11 |b| there)."""
+3.3e-11 |b| there); the same bound on the 2048^2 channel medium of
+contrast 10^4."""
 import numpy as np
 import pytest
 
@@ -91,4 +92,26 @@ def test_fine_mg_residual_1024(orc):
         res = (b - _apply_q1(a[s], u[s]).reshape(nf + 1, nf + 1))[1:-1, 1:-1]
         floor = _apply_q1(a[s], np.abs(u[s]), np.abs(KREF)).reshape(nf + 1, nf + 1)[1:-1, 1:-1]
         bound = 1e-12 * np.linalg.norm(b[1:-1, 1:-1]) + 4 * np.finfo(np.float64).eps * np.linalg.norm(floor)
+        assert np.linalg.norm(res) <= bound, (np.linalg.norm(res), bound)
+
+
+def test_fine_mg_residual_2048_contrast(orc):
+    """The 2048^2 channel medium of contrast 10^4 (the high-contrast
+    workload's grid and field), two samples: the true residual at the same
+    rounding-floor bound."""
+    nf = 2048
+    fld = W.workload("contrast_2048")["field"]
+    a = orc.sample_coef(nf, fld, W.draw_xi(fld, 2, 17, "normal"))
+    assert a.max() / a.min() > 5e3
+    g = api.grid(nf, 64, 1.0)
+    u = _fine(g, a)
+    h = 1.0 / nf
+    b = np.zeros((nf + 1, nf + 1))
+    b[1:-1, 1:-1] = h * h
+    for s in range(2):
+        assert np.all(np.isfinite(u[s]))
+        res = (b - _apply_q1(a[s], u[s]).reshape(nf + 1, nf + 1))[1:-1, 1:-1]
+        floor = _apply_q1(a[s], np.abs(u[s]), np.abs(KREF)).reshape(nf + 1, nf + 1)[1:-1, 1:-1]
+        bound = 1e-12 * np.linalg.norm(b[1:-1, 1:-1]) + 4 * np.finfo(np.float64).eps * np.linalg.norm(floor)
+        print("2048 contrast residual %.3e bound %.3e" % (np.linalg.norm(res), bound))
         assert np.linalg.norm(res) <= bound, (np.linalg.norm(res), bound)
