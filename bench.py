@@ -518,7 +518,7 @@ def bench_contrast(api, dev, stream, batch=128, fp64_batch=8, n_train=24, n_sur_
     for hh in hs:
         api.stomsfem_surrogate_destroy(hh)
     out["surrogate"] = sur
-    out["note"] = ("random interpolation is not run here: its degree rule's sparse grids exceed the 2048 points "
+    out["note"] = ("random interpolation is not run here: its degree rule's tensor grids exceed the 2048 points "
                    "per family that the online kernel holds (46,656 for one family at eps = 1e-3, 3,888 at "
                    "eps = 0.1)")
     return out
