@@ -632,20 +632,21 @@ def bench_two_level(api, dev, stream, n0=10000, n1=256):
             "two_level_vs_plain_mean_rel": diff}
 
 
-def bench_two_level_1024(api, dev, stream, ov, n0=512, n1=16):
-    """Two-level Monte Carlo (Eq. MCmean2level) on the H/h = 32 workload's
-    1024^2 / 32^2 grids: level 0, n0 samples through the FP32 upscaler (with
-    its oversampling) and the coarse solve; level 1, n1 independent samples
+def bench_two_level_1024(api, dev, stream, ov, n0=512, n1=16, workload="upscale_1024"):
+    """Two-level Monte Carlo (Eq. MCmean2level) on an H/h = 32 workload's
+    grids (upscale_1024: 1024^2 / 32^2 with its oversampling; contrast_2048:
+    2048^2 / 64^2, contrast 10^4, none): level 0, n0 samples through the
+    FP32 upscaler and the coarse solve; level 1, n1 independent samples
     with the fine Q1 FEM (multigrid-preconditioned CG on the GPU) and their
     coarse solutions; against plain Monte Carlo with the same n1 fine solves."""
     import torch
-    w = W.workload("upscale_1024")
+    w = W.workload(workload)
     nf, nc = w["nf"], w["nc"]
     g = api.grid(nf, nc, w["f"])
     fld = api.field_from_dict(w["field"])
     nn = (nc + 1) ** 2
-    ov_t = torch.from_numpy(ov).to(dev)
-    mo = int(ov.max())
+    ov_t = torch.from_numpy(ov).to(dev) if ov is not None else None
+    mo = int(ov.max()) if ov is not None else 0
 
     def mom():
         return [torch.zeros(nn, dtype=torch.float64, device=dev), torch.zeros(nn, dtype=torch.float64, device=dev),
@@ -666,8 +667,8 @@ def bench_two_level_1024(api, dev, stream, ov, n0=512, n1=16):
         api.stomsfem_coarse_solve(g, Ke, be, u, *m, stream=stream)
         return u
 
-    x0 = torch.from_numpy(W.draw_xi(w["field"], n0, 601)).to(dev)
-    x1 = torch.from_numpy(W.draw_xi(w["field"], n1, 602)).to(dev)
+    x0 = torch.from_numpy(W.draw_xi(w["field"], n0, 601, w["dist"])).to(dev)
+    x1 = torch.from_numpy(W.draw_xi(w["field"], n1, 602, w["dist"])).to(dev)
     a1 = torch.empty((n1, nf, nf), dtype=torch.float64, device=dev)
     uh = torch.empty((n1, (nf + 1) ** 2), dtype=torch.float64, device=dev)
     wsf = torch.empty(api.stomsfem_fine_fem_workspace_size(g, n1), dtype=torch.uint8, device=dev)
@@ -693,7 +694,7 @@ def bench_two_level_1024(api, dev, stream, ov, n0=512, n1=16):
     sd2 = float(((m0[1] / n0 / n0) + (m1[1] / n1 / n1)).mean().sqrt().item())
     sdp = float((mp[1] / n1 / n1).mean().sqrt().item())
     fine_ms = e[2].elapsed_time(e[3])
-    return {"workload": "upscale_1024 grids (1024^2 fine, 32^2 coarse), level 0 by the FP32 upscaler",
+    return {"workload": "%s grids (%d^2 fine, %d^2 coarse), level 0 by the FP32 upscaler" % (workload, nf, nc),
             "n0_coarse": n0, "n1_fine": n1, "level0_ms": e[0].elapsed_time(e[1]),
             "fine_fem_ms": fine_ms, "fine_fem_samples_per_s": n1 / (fine_ms / 1e3),
             "fine_fem_method": "CG (FP64) with a multigrid V-cycle (FP32) preconditioner",
@@ -1083,7 +1084,7 @@ def main():
     ap.add_argument("--contrast-sur-steps", type=int, default=20000, help="surrogate training steps on contrast_2048")
     ap.add_argument("--sections", default="",
                     help="comma-separated subset of the extra sections (engines, petrov_galerkin, pod, surrogate, "
-                         "ri, pod_affine, two_level_mc, two_level_mc_1024, contrast_2048, mixed_bc, "
+                         "ri, pod_affine, two_level_mc, two_level_mc_1024, two_level_mc_2048, contrast_2048, mixed_bc, "
                          "oscillatory_bc); default all")
     ap.add_argument("--pod-samples", type=int, default=None, help="online POD samples (default 10^4)")
     ap.add_argument("--sg-samples", type=int, default=None, help="surrogate inference samples (default 10^5)")
@@ -1346,6 +1347,8 @@ def main():
             ("pod_affine", lambda: bench_pod_affine(api, dev, stream, args.pod_samples)),
             ("two_level_mc", lambda: bench_two_level(api, dev, stream)),
             ("two_level_mc_1024", lambda: bench_two_level_1024(api, dev, stream, ov)),
+            ("two_level_mc_2048", lambda: bench_two_level_1024(api, dev, stream, None, n0=128, n1=8,
+                                                               workload="contrast_2048")),
             ("contrast_2048", lambda: bench_contrast(api, dev, stream, batch=args.contrast_batch,
                                                      n_train=args.contrast_train,
                                                      n_sur_train=args.contrast_sur_train,
