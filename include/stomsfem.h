@@ -412,7 +412,7 @@ int stomsfem_local_kl_project(const stomsfem_local_kl* kl, const double* kappa, 
 
 /* Scratch needed by stomsfem_fine_fem for S samples (nf <= 64: the banded
  * factors of the warps in flight; larger nf: the multigrid hierarchy, the
- * CG vectors and the FP64 operator of all S samples, about 112 bytes per
+ * CG vectors and the FP64 operator of all S samples, about 139 bytes per
  * fine node and sample).  EINVAL for an nf above 64 that does not halve down to 16 or
  * less. */
 int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_t* bytes);
@@ -424,7 +424,9 @@ int stomsfem_fine_fem_workspace_size(const stomsfem_grid* grid, int32_t S, size_
  *    definite); stream-ordered.
  *  - nf > 64 (nf = c 2^k, c <= 16): conjugate gradients in FP64 on all S
  *    samples at once, preconditioned by one multigrid V-cycle in FP32
- *    (bilinear prolongation, Galerkin coarse operators, damped Jacobi
+ *    (bilinear prolongation, or operator-dependent prolongation when the
+ *    batch's coefficient contrast max a / min a exceeds 1e3; Galerkin
+ *    coarse operators, damped Jacobi
  *    smoothing), until every sample's recursively updated CG residual is
  *    at most 1e-13 of its load (at most 400 iterations, else ENOTSPD;
  *    ENOTSPD too as soon as a residual is not finite);

@@ -5,8 +5,10 @@
 // FP64 preconditioned with one geometric multigrid V-cycle in FP32.
 //
 // Multigrid: levels nf_0 = nf, nf_{l+1} = nf_l / 2 down to nf_L <= 16;
-// bilinear prolongation P (coarse node (I, J) at fine node (2I, 2J)),
-// restriction P^T, Galerkin coarse operators A_{l+1} = P^T A_l P (9-point
+// operator-dependent prolongation P (coarse node (I, J) at fine node
+// (2I, 2J); the other fine nodes' weights from the fine stencil, see
+// mgf_interp_kernel), restriction P^T, Galerkin coarse operators
+// A_{l+1} = P^T A_l P (9-point
 // stencils again), damped Jacobi smoothing (omega = 0.8, two sweeps before
 // and after the coarse correction: a symmetric V-cycle, so the
 // preconditioner is symmetric positive definite and plain CG applies), and
@@ -24,6 +26,7 @@
 // step lengths are computed on the device.  The host checks convergence
 // (max over samples of |r| / |f|) every few iterations.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -34,6 +37,12 @@ constexpr int kMgMaxLevels = 12;
 constexpr float kMgOmega = 0.8f;
 constexpr int kMgCoarseSweeps = 60;
 constexpr int kMgThreads = 256;
+// Coefficient contrast (max a / min a over the batch) above which the
+// transfers between levels use the operator-dependent prolongation; below
+// it the bilinear one, which converges as fast there (the same 12 CG
+// iterations on the lognormal 1024^2 medium of contrast 100) and moves
+// fewer bytes per cycle.
+constexpr double kMgOdContrast = 1e3;
 
 struct MgLevel {
   int nf;          // elements per side
@@ -43,6 +52,8 @@ struct MgLevel {
   float* u2;       // [S][N] (Jacobi ping-pong)
   float* f;        // [S][N]
   float* r;        // [S][N]
+  float* P;        // [S][4][N]: prolongation weights from the next coarser level (per node type)
+  float* dv;       // [S][N]: Jacobi divisor (see mgf_divisor_kernel)
 };
 
 __device__ __forceinline__ bool interior(int i, int j, int nf) { return i > 0 && j > 0 && i < nf && j < nf; }
@@ -116,18 +127,121 @@ __global__ void mgf_fine_stencil_kernel(int nf, const double* __restrict__ a, fl
   }
 }
 
-// Bilinear prolongation weight of coarse node c at fine coordinate x (1D).
-__device__ __forceinline__ float hat(int x, int c2) {
-  const int d = abs(x - c2);
-  return d == 0 ? 1.f : (d == 1 ? 0.5f : 0.f);
+// The 9-point stencil of interior node v (entries k = (dj + 1) * 3 + di + 1).
+__device__ __forceinline__ void stencil9(const float* __restrict__ st, size_t N, long v, int W, float a[9]) {
+  a[0] = st9<0>(st, N, v, W);
+  a[1] = st9<1>(st, N, v, W);
+  a[2] = st9<2>(st, N, v, W);
+  a[3] = st9<3>(st, N, v, W);
+  a[4] = st9<4>(st, N, v, W);
+  a[5] = st9<5>(st, N, v, W);
+  a[6] = st9<6>(st, N, v, W);
+  a[7] = st9<7>(st, N, v, W);
+  a[8] = st9<8>(st, N, v, W);
+}
+
+// The Jacobi divisor of a node from its nine entries (mgf_divisor_kernel).
+__device__ __forceinline__ float jacobi_divisor(const float a[9]) {
+  const float l1 = fabsf(a[0]) + fabsf(a[1]) + fabsf(a[2]) + fabsf(a[3]) + fabsf(a[5]) + fabsf(a[6]) +
+                   fabsf(a[7]) + fabsf(a[8]);
+  return fmaxf(a[4], 0.5f * (a[4] + l1));
+}
+
+// Operator-dependent prolongation (the black-box interpolation of Dendy,
+// J. Comput. Phys. 48, 1982, for 9-point stencils): a fine node between
+// two coarse nodes of a row takes weights from its stencil collapsed onto
+// that row (columns summed: w_W = -a_W / a_C, w_E = -a_E / a_C), one between
+// two coarse nodes of a column from the stencil collapsed onto the column;
+// a cell-centre node solves its own equation with its four edge neighbours
+// interpolated so.  Where the stencil sums to zero the weights sum to one;
+// next to the Dirichlet boundary the couplings to boundary nodes (zero in
+// the symmetric form) drop out.  Across jumps of the coefficient the
+// weights follow the operator, which keeps the coarse-grid correction
+// effective where bilinear interpolation is not.
+// (A collapsed centre that is not positive, which a coarse Galerkin
+// operator can in principle give, takes the bilinear weights instead.)
+__device__ __forceinline__ void interp_row(const float a[9], float& wW, float& wE) {
+  const float c = a[1] + a[4] + a[7];
+  wW = c > 0.f ? -(a[0] + a[3] + a[6]) / c : 0.5f;
+  wE = c > 0.f ? -(a[2] + a[5] + a[8]) / c : 0.5f;
+}
+__device__ __forceinline__ void interp_col(const float a[9], float& wS, float& wN) {
+  const float c = a[3] + a[4] + a[5];
+  wS = c > 0.f ? -(a[0] + a[1] + a[2]) / c : 0.5f;
+  wN = c > 0.f ? -(a[6] + a[7] + a[8]) / c : 0.5f;
+}
+
+// Weights P[m][node] of every fine node: between coarse nodes of a row
+// (x odd, y even) m = 0, 1 for the west and east ones; of a column (x even,
+// y odd) m = 0, 1 for the south and north ones; a cell centre (both odd)
+// m = 0..3 for its south-west, south-east, north-east and north-west
+// corners; zero elsewhere (coarse-grid nodes take their coarse value).
+__global__ void mgf_interp_kernel(int nff, const float* __restrict__ stf, float* __restrict__ P) {
+  const int s = blockIdx.y;
+  const int W = nff + 1;
+  const size_t N = (size_t)W * W;
+  const float* sf = stf + (size_t)s * 5 * N;
+  float* ps = P + (size_t)s * 4 * N;
+  for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < (long)N; v += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(v % W), y = (int)(v / W);
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    if (interior(x, y, nff) && ((x | y) & 1)) {
+      float a[9];
+      stencil9(sf, N, v, W, a);
+      if ((x & 1) && !(y & 1)) {
+        interp_row(a, w[0], w[1]);
+      } else if (!(x & 1) && (y & 1)) {
+        interp_col(a, w[0], w[1]);
+      } else {
+        // edge neighbours: south and north between coarse nodes of a row,
+        // west and east between coarse nodes of a column
+        float sW = 0.f, sE = 0.f, nW = 0.f, nE = 0.f, wS = 0.f, wN = 0.f, eS = 0.f, eN = 0.f, b[9];
+        if (y - 1 > 0) { stencil9(sf, N, v - W, W, b); interp_row(b, sW, sE); }
+        if (y + 1 < nff) { stencil9(sf, N, v + W, W, b); interp_row(b, nW, nE); }
+        if (x - 1 > 0) { stencil9(sf, N, v - 1, W, b); interp_col(b, wS, wN); }
+        if (x + 1 < nff) { stencil9(sf, N, v + 1, W, b); interp_col(b, eS, eN); }
+        const float c = a[4];
+        if (c > 0.f) {
+          w[0] = -(a[0] + a[1] * sW + a[3] * wS) / c;  // south-west corner
+          w[1] = -(a[2] + a[1] * sE + a[5] * eS) / c;  // south-east
+          w[2] = -(a[8] + a[7] * nE + a[5] * eN) / c;  // north-east
+          w[3] = -(a[6] + a[7] * nW + a[3] * wN) / c;  // north-west
+        } else {
+          w[0] = w[1] = w[2] = w[3] = 0.25f;
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ps[(size_t)m * N + v] = w[m];
+  }
+}
+
+// Weight of fine node (gx, gy) in the prolongation of coarse node (I, J):
+// the stored operator-dependent weights (OD), else bilinear (1, 1/2, 1/4).
+template <bool OD>
+__device__ __forceinline__ float pweight(const float* __restrict__ ps, size_t N, int W, int gx, int gy, int I, int J) {
+  const int dx = gx - 2 * I, dy = gy - 2 * J;
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1) return 0.f;
+  if constexpr (!OD) return (dx == 0 ? 1.f : 0.5f) * (dy == 0 ? 1.f : 0.5f);
+  const size_t g = (size_t)gy * W + gx;
+  const bool ox = gx & 1, oy = gy & 1;
+  if (!ox && !oy) return (dx == 0 && dy == 0) ? 1.f : 0.f;
+  if (ox && !oy) return dy != 0 ? 0.f : ps[(dx > 0 ? 0 : 1) * N + g];
+  if (!ox && oy) return dx != 0 ? 0.f : ps[(dy > 0 ? 0 : 1) * N + g];
+  const int m = dy > 0 ? (dx > 0 ? 0 : 1) : (dx < 0 ? 2 : 3);
+  return ps[(size_t)m * N + g];
 }
 
 // Galerkin coarse stencils A_c = P^T A_f P at the interior coarse nodes.
-__global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, float* __restrict__ stc) {
+template <bool OD>
+__global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, const float* __restrict__ P,
+                               float* __restrict__ stc) {
   const int s = blockIdx.y;
   const int nfc = nff / 2;
-  const int Nf = (nff + 1) * (nff + 1), Nc = (nfc + 1) * (nfc + 1);
+  const int Wf = nff + 1;
+  const int Nf = Wf * Wf, Nc = (nfc + 1) * (nfc + 1);
   const float* sf = stf + (size_t)s * 5 * Nf;
+  const float* ps = P + (size_t)s * 4 * Nf;
   float* sc = stc + (size_t)s * 5 * Nc;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nc; v += gridDim.x * blockDim.x) {
     const int I = v % (nfc + 1), J = v / (nfc + 1);
@@ -136,22 +250,51 @@ __global__ void mgf_rap_kernel(int nff, const float* __restrict__ stf, float* __
       for (int dj = -1; dj <= 1; ++dj)
         for (int di = -1; di <= 1; ++di) {
           const int fx = 2 * I + di, fy = 2 * J + dj;  // fine node in the support of coarse (I, J)
-          const float wf = hat(fx, 2 * I) * hat(fy, 2 * J);
-          const int fv = fy * (nff + 1) + fx;
+          const float wf = pweight<OD>(ps, Nf, Wf, fx, fy, I, J);
+          if (wf == 0.f) continue;
+          const int fv = fy * Wf + fx;
           for (int ej = -1; ej <= 1; ++ej)
             for (int ei = -1; ei <= 1; ++ei) {
               const int k = (ej + 1) * 3 + ei + 1;
-              const float afv = sf[(size_t)st_arr(k) * Nf + st_node(k, fv, nff + 1)];
+              const float afv = sf[(size_t)st_arr(k) * Nf + st_node(k, fv, Wf)];
               if (afv == 0.f) continue;
               const int gx = fx + ei, gy = fy + ej;  // neighbour fine node
-              // coarse nodes (I + cI, J + cJ) whose hats cover (gx, gy)
-              for (int cJ = -1; cJ <= 1; ++cJ)
-                for (int cI = -1; cI <= 1; ++cI) {
-                  const int Ic = I + cI, Jc = J + cJ;
-                  if (!interior(Ic, Jc, nfc)) continue;
-                  const float pg = hat(gx, 2 * Ic) * hat(gy, 2 * Jc);
-                  if (pg != 0.f) out[(cJ + 1) * 3 + cI + 1] += wf * afv * pg;
-                }
+              if constexpr (!OD) {
+                // coarse nodes (I + cI, J + cJ) whose hats cover (gx, gy)
+                for (int cJ = -1; cJ <= 1; ++cJ)
+                  for (int cI = -1; cI <= 1; ++cI) {
+                    const int Ic = I + cI, Jc = J + cJ;
+                    if (!interior(Ic, Jc, nfc)) continue;
+                    const float pg = pweight<false>(ps, Nf, Wf, gx, gy, Ic, Jc);
+                    if (pg != 0.f) out[(cJ + 1) * 3 + cI + 1] += wf * afv * pg;
+                  }
+                continue;
+              }
+              // the coarse nodes whose prolongation covers (gx, gy): one,
+              // two or four by the node's type, with their weights
+              int pI[4], pJ[4], np = 0;
+              float pw[4];
+              const size_t gv = (size_t)gy * Wf + gx;
+              const int I0 = gx >> 1, J0 = gy >> 1;
+              if (!(gx & 1) && !(gy & 1)) {
+                pI[0] = I0; pJ[0] = J0; pw[0] = 1.f; np = 1;
+              } else if (!(gy & 1)) {
+                pI[0] = I0; pJ[0] = J0; pw[0] = ps[gv];
+                pI[1] = I0 + 1; pJ[1] = J0; pw[1] = ps[(size_t)Nf + gv]; np = 2;
+              } else if (!(gx & 1)) {
+                pI[0] = I0; pJ[0] = J0; pw[0] = ps[gv];
+                pI[1] = I0; pJ[1] = J0 + 1; pw[1] = ps[(size_t)Nf + gv]; np = 2;
+              } else {
+                pI[0] = I0; pJ[0] = J0; pw[0] = ps[gv];
+                pI[1] = I0 + 1; pJ[1] = J0; pw[1] = ps[(size_t)Nf + gv];
+                pI[2] = I0 + 1; pJ[2] = J0 + 1; pw[2] = ps[(size_t)2 * Nf + gv];
+                pI[3] = I0; pJ[3] = J0 + 1; pw[3] = ps[(size_t)3 * Nf + gv]; np = 4;
+              }
+              for (int q = 0; q < np; ++q) {
+                const int cI = pI[q] - I, cJ = pJ[q] - J;
+                if (cI < -1 || cI > 1 || cJ < -1 || cJ > 1 || !interior(pI[q], pJ[q], nfc) || pw[q] == 0.f) continue;
+                out[(cJ + 1) * 3 + cI + 1] += wf * afv * pw[q];
+              }
             }
         }
     }
@@ -179,9 +322,38 @@ __device__ __forceinline__ float apply9(const float* __restrict__ st, size_t N, 
   return t;
 }
 
-// One damped Jacobi sweep: uo = ui + omega (f - A ui) / diag (zero_in: ui = 0).
-__global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const float* __restrict__ f,
-                                  const float* __restrict__ ui, float* __restrict__ uo, int zero_in) {
+// Jacobi divisor of each interior node: its diagonal entry, or half the
+// sum of the diagonal and the off-diagonal magnitudes where those exceed
+// the diagonal.  With omega = 0.8 the damped sweep then converges on every
+// level with a symmetric positive definite operator (the l1-Jacobi bound:
+// the divisors are at least (a_ii + sum |a_ij|) / 1.6), so the V-cycle stays
+// symmetric positive definite whatever the Galerkin coarse operators look
+// like; on the fine level, an M-matrix, it is the diagonal itself.
+__global__ void mgf_divisor_kernel(int nf, const float* __restrict__ st, float* __restrict__ dv) {
+  const int s = blockIdx.y;
+  const int W = nf + 1;
+  const size_t N = (size_t)W * W;
+  const float* ss = st + (size_t)s * 5 * N;
+  for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < (long)N; v += (long)gridDim.x * blockDim.x) {
+    float d = 1.f;
+    if (interior((int)(v % W), (int)(v / W), nf)) {
+      float a[9];
+      stencil9(ss, N, v, W, a);
+      d = jacobi_divisor(a);
+    }
+    dv[(size_t)s * N + v] = d;
+  }
+}
+
+// One damped Jacobi sweep: uo = ui + omega (f - A ui) / divisor (zero_in: ui = 0).
+// OD (operator-dependent transfers, whose coarse operators need not be
+// diagonally dominant): the divisor of mgf_divisor_kernel, read in the
+// sweep from zero and formed from the loaded entries in the others; with
+// the bilinear transfers the diagonal entry, as the M-matrix levels allow.
+template <bool OD>
+__global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const float* __restrict__ dv,
+                                  const float* __restrict__ f, const float* __restrict__ ui, float* __restrict__ uo,
+                                  int zero_in) {
   const int s = blockIdx.y;
   const int W = nf + 1, N = W * W;
   const float* ss = st + (size_t)s * 5 * N;
@@ -192,9 +364,23 @@ __global__ void mgf_jacobi_kernel(int nf, const float* __restrict__ st, const fl
     const int i = v % W, j = v / W;
     float o = 0.f;
     if (interior(i, j, nf)) {
-      const float d = ss[v];
-      const float au = zero_in ? 0.f : apply9(ss, N, v, us, W);
-      o = (zero_in ? 0.f : us[v]) + kMgOmega * (fs[v] - au) / d;
+      if (zero_in) {
+        o = 0.f + kMgOmega * (fs[v] - 0.f) / (OD ? dv[(size_t)s * N + v] : ss[v]);
+      } else {
+        float a[9];
+        stencil9(ss, N, v, W, a);
+        float t = 0.f;
+        t = fmaf(a[0], us[v - W - 1], t);
+        t = fmaf(a[1], us[v - W], t);
+        t = fmaf(a[2], us[v - W + 1], t);
+        t = fmaf(a[3], us[v - 1], t);
+        t = fmaf(a[4], us[v], t);
+        t = fmaf(a[5], us[v + 1], t);
+        t = fmaf(a[6], us[v + W - 1], t);
+        t = fmaf(a[7], us[v + W], t);
+        t = fmaf(a[8], us[v + W + 1], t);
+        o = us[v] + kMgOmega * (fs[v] - t) / (OD ? jacobi_divisor(a) : a[4]);
+      }
     }
     os[v] = o;
   }
@@ -207,6 +393,7 @@ constexpr int kMgCoarseMaxNodes = 289;
 constexpr int kMgCoarseThreads = 320;
 
 __global__ void __launch_bounds__(kMgCoarseThreads) mgf_coarse_kernel(int nf, const float* __restrict__ st,
+                                                                      const float* __restrict__ dv,
                                                                       const float* __restrict__ f,
                                                                       float* __restrict__ u) {
   __shared__ float buf[2][kMgCoarseMaxNodes];
@@ -219,7 +406,8 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mgf_coarse_kernel(int nf, co
 #pragma unroll
   for (int k = 0; k < 9; ++k) c[k] = in ? ss[(size_t)st_arr(k) * N + st_node(k, v, W)] : 0.f;
   if (in) fv = f[(size_t)s * N + v];
-  float o = in ? 0.f + kMgOmega * (fv - 0.f) / c[4] : 0.f;  // the first sweep, from zero
+  const float dd = in ? dv[(size_t)s * N + v] : 1.f;
+  float o = in ? 0.f + kMgOmega * (fv - 0.f) / dd : 0.f;  // the first sweep, from zero
   if (v < N) buf[0][v] = o;
   __syncthreads();
   for (int k = 1; k < kMgCoarseSweeps; ++k) {
@@ -230,7 +418,7 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mgf_coarse_kernel(int nf, co
       for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
         for (int di = -1; di <= 1; ++di) t = fmaf(c[(dj + 1) * 3 + di + 1], ui[v + dj * W + di], t);
-      o = ui[v] + kMgOmega * (fv - t) / c[4];
+      o = ui[v] + kMgOmega * (fv - t) / dd;
     }
     if (v < N) buf[k & 1][v] = o;
     __syncthreads();
@@ -251,34 +439,86 @@ __global__ void mgf_residual_kernel(int nf, const float* __restrict__ st, const 
 }
 
 // f_c = P^T r_f at the interior coarse nodes.
-__global__ void mgf_restrict_kernel(int nff, const float* __restrict__ rf, float* __restrict__ fc) {
+template <bool OD>
+__global__ void mgf_restrict_kernel(int nff, const float* __restrict__ P, const float* __restrict__ rf,
+                                    float* __restrict__ fc) {
   const int s = blockIdx.y;
   const int nfc = nff / 2, Wf = nff + 1, Wc = nfc + 1;
   const int Nf = Wf * Wf, Nc = Wc * Wc;
+  const float* ps = P + (size_t)s * 4 * Nf;
+  const float* r = rf + (size_t)s * Nf;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nc; v += gridDim.x * blockDim.x) {
     const int I = v % Wc, J = v / Wc;
     float t = 0.f;
     if (interior(I, J, nfc)) {
-      const float* r = rf + (size_t)s * Nf + (size_t)(2 * J) * Wf + 2 * I;
-      t = r[0] + 0.5f * (r[-1] + r[1] + r[-Wf] + r[Wf]) + 0.25f * (r[-Wf - 1] + r[-Wf + 1] + r[Wf - 1] + r[Wf + 1]);
+      if constexpr (OD) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int gx = 2 * I + dx, gy = 2 * J + dy;
+            t = fmaf(pweight<true>(ps, Nf, Wf, gx, gy, I, J), r[(size_t)gy * Wf + gx], t);
+          }
+      } else {
+        const float* q = r + (size_t)(2 * J) * Wf + 2 * I;
+        t = q[0] + 0.5f * (q[-1] + q[1] + q[-Wf] + q[Wf]) + 0.25f * (q[-Wf - 1] + q[-Wf + 1] + q[Wf - 1] + q[Wf + 1]);
+      }
     }
     fc[(size_t)s * Nc + v] = t;
   }
 }
 
 // u_f += P u_c at the interior fine nodes.
-__global__ void mgf_prolong_kernel(int nff, const float* __restrict__ uc, float* __restrict__ uf) {
+template <bool OD>
+__global__ void mgf_prolong_kernel(int nff, const float* __restrict__ P, const float* __restrict__ uc,
+                                   float* __restrict__ uf) {
   const int s = blockIdx.y;
   const int nfc = nff / 2, Wf = nff + 1, Wc = nfc + 1;
   const int Nf = Wf * Wf, Nc = Wc * Wc;
+  const float* ps = P + (size_t)s * 4 * Nf;
   const float* u = uc + (size_t)s * Nc;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nf; v += gridDim.x * blockDim.x) {
     const int x = v % Wf, y = v / Wf;
     if (!interior(x, y, nff)) continue;
-    const int I0 = x / 2, J0 = y / 2;
-    const int I1 = (x & 1) ? I0 + 1 : I0, J1 = (y & 1) ? J0 + 1 : J0;
-    const float t = 0.25f * (u[J0 * Wc + I0] + u[J0 * Wc + I1] + u[J1 * Wc + I0] + u[J1 * Wc + I1]);
+    const int I0 = x >> 1, J0 = y >> 1;
+    float t;
+    if constexpr (!OD) {
+      const int I1 = (x & 1) ? I0 + 1 : I0, J1 = (y & 1) ? J0 + 1 : J0;
+      t = 0.25f * (u[J0 * Wc + I0] + u[J0 * Wc + I1] + u[J1 * Wc + I0] + u[J1 * Wc + I1]);
+    } else if (!(x & 1) && !(y & 1)) {
+      t = u[J0 * Wc + I0];
+    } else if (!(y & 1)) {  // between coarse nodes I0, I0 + 1 of row J0
+      t = ps[v] * u[J0 * Wc + I0] + ps[(size_t)Nf + v] * u[J0 * Wc + I0 + 1];
+    } else if (!(x & 1)) {  // between coarse nodes J0, J0 + 1 of column I0
+      t = ps[v] * u[J0 * Wc + I0] + ps[(size_t)Nf + v] * u[(J0 + 1) * Wc + I0];
+    } else {  // cell centre: corners SW, SE, NE, NW
+      t = ps[v] * u[J0 * Wc + I0] + ps[(size_t)Nf + v] * u[J0 * Wc + I0 + 1] +
+          ps[(size_t)2 * Nf + v] * u[(J0 + 1) * Wc + I0 + 1] + ps[(size_t)3 * Nf + v] * u[(J0 + 1) * Wc + I0];
+    }
     uf[(size_t)s * Nf + v] += t;
+  }
+}
+
+// mm[0] = bit pattern of max a, mm[1] = that of max 1/a over the positive
+// entries of a (the patterns of positive doubles order like their values;
+// both start at zero).
+__global__ void mgf_range_kernel(long long n, const double* __restrict__ a, unsigned long long* __restrict__ mm) {
+  unsigned long long hi = 0, lo = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    if (v > 0.0) {
+      hi = max(hi, (unsigned long long)__double_as_longlong(v));
+      lo = max(lo, (unsigned long long)__double_as_longlong(1.0 / v));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(mm, hi);
+    atomicMax(mm + 1, lo);
   }
 }
 
@@ -418,6 +658,8 @@ int mg_levels(int nf, int* nfs) {
 }
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+size_t range_offset(int S) { return (sizeof(double) * 6 * S + sizeof(int32_t) * S + 7) & ~size_t(7); }
+size_t scal_bytes(int S) { return range_offset(S) + 2 * sizeof(unsigned long long); }
 
 // Workspace layout of a batch of S samples.
 size_t mg_layout(int nf, int S, MgLevel* lv, int* L, unsigned char* base, double** vec, double** scal) {
@@ -438,14 +680,19 @@ size_t mg_layout(int nf, int S, MgLevel* lv, int* L, unsigned char* base, double
     o += al256(sizeof(float) * N * S);
     lv[l].r = reinterpret_cast<float*>(base + o);
     o += al256(sizeof(float) * N * S);
+    lv[l].P = reinterpret_cast<float*>(base + o);  // unused on the coarsest level
+    o += l + 1 < *L ? al256(sizeof(float) * 4 * N * S) : 0;
+    lv[l].dv = reinterpret_cast<float*>(base + o);
+    o += al256(sizeof(float) * N * S);
   }
   const size_t N0 = (size_t)(nf + 1) * (nf + 1);
   for (int k = 0; k < 4; ++k) {  // r, p, Ap (x is the caller's u), then the FP64 stencil [S][5][N0]
     vec[k] = reinterpret_cast<double*>(base + o);
     o += al256(sizeof(double) * N0 * S * (k == 3 ? 5 : 1));
   }
-  *scal = reinterpret_cast<double*>(base + o);  // alpha, pAp, rz, rz_old, rr, bb [S] doubles, done [S] int
-  o += al256(sizeof(double) * 6 * S + sizeof(int32_t) * S);
+  *scal = reinterpret_cast<double*>(base + o);  // alpha, pAp, rz, rz_old, rr, bb [S] doubles, done [S] int,
+                                                // then the coefficient range (2 x 8 bytes, 8-aligned)
+  o += al256(scal_bytes(S));
   return o;
 }
 
@@ -460,25 +707,26 @@ dim3 grid2(int N, int S) {
 
 // z = V-cycle(r) on level l (f of level l holds the right-hand side; the
 // result in u of level l).
+template <bool OD>
 int vcycle(MgLevel* lv, int L, int l, int S, cudaStream_t st) {
   MgLevel& c = lv[l];
   const dim3 g = grid2(c.N, S);
   if (l == L - 1) {
     if (c.N > kMgCoarseMaxNodes) return set_error(STOMSFEM_EINVAL, "coarsest grid of %d nodes", c.N);
-    mgf_coarse_kernel<<<S, kMgCoarseThreads, 0, st>>>(c.nf, c.st, c.f, c.u);
+    mgf_coarse_kernel<<<S, kMgCoarseThreads, 0, st>>>(c.nf, c.st, c.dv, c.f, c.u);
     return check_cuda(cudaGetLastError(), "coarse sweeps");
   }
   // pre-smoothing from zero
-  mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u, c.u2, 1);
-  mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u2, c.u, 0);
+  mgf_jacobi_kernel<OD><<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.dv, c.f, c.u, c.u2, 1);
+  mgf_jacobi_kernel<OD><<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.dv, c.f, c.u2, c.u, 0);
   mgf_residual_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u, c.r);
   MgLevel& n = lv[l + 1];
-  mgf_restrict_kernel<<<grid2(n.N, S), kMgThreads, 0, st>>>(c.nf, c.r, n.f);
-  int rc = vcycle(lv, L, l + 1, S, st);
+  mgf_restrict_kernel<OD><<<grid2(n.N, S), kMgThreads, 0, st>>>(c.nf, c.P, c.r, n.f);
+  int rc = vcycle<OD>(lv, L, l + 1, S, st);
   if (rc) return rc;
-  mgf_prolong_kernel<<<g, kMgThreads, 0, st>>>(c.nf, n.u, c.u);
-  mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u, c.u2, 0);
-  mgf_jacobi_kernel<<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.f, c.u2, c.u, 0);
+  mgf_prolong_kernel<OD><<<g, kMgThreads, 0, st>>>(c.nf, c.P, n.u, c.u);
+  mgf_jacobi_kernel<OD><<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.dv, c.f, c.u, c.u2, 0);
+  mgf_jacobi_kernel<OD><<<g, kMgThreads, 0, st>>>(c.nf, c.st, c.dv, c.f, c.u2, c.u, 0);
   return check_cuda(cudaGetLastError(), "v-cycle");
 }
 
@@ -518,20 +766,41 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
   int32_t* done = reinterpret_cast<int32_t*>(scal + 6 * S);
   const int N0 = lv[0].N;
   const dim3 g0 = grid2(N0, S);
-  // multigrid set-up: stencils of every level
-  mgf_fine_stencil_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, lv[0].st, st64);
-  for (int l = 0; l + 1 < L; ++l)
-    mgf_rap_kernel<<<grid2(lv[l + 1].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l + 1].st);
-  STOMSFEM_TRY_CUDA(cudaGetLastError());
-  STOMSFEM_TRY_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 6 * S + sizeof(int32_t) * S, st));
+  unsigned long long* range = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(scal) +
+                                                                   range_offset(S));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(scal, 0, scal_bytes(S), st));
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
+  mgf_range_kernel<<<sms * 4, kMgThreads, 0, st>>>((long long)S * nf * nf, a, range);
   const double h = 1.0 / nf;
   cg_init_kernel<<<g0, kMgThreads, 0, st>>>(nf, f * h * h, u, r, lv[0].f, bb);
   std::vector<double> hb(S), hr(S);
   std::vector<int32_t> hd(S, 0);
+  unsigned long long hrange[2] = {0, 0};
   STOMSFEM_TRY_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  STOMSFEM_TRY_CUDA(cudaMemcpyAsync(hrange, range, sizeof(hrange), cudaMemcpyDeviceToHost, st));
   STOMSFEM_TRY_CUDA(cudaStreamSynchronize(st));
+  double amax, ainv;
+  std::memcpy(&amax, &hrange[0], sizeof(double));
+  std::memcpy(&ainv, &hrange[1], sizeof(double));
+  const bool od = amax * ainv > kMgOdContrast;
+  // multigrid set-up: stencils of every level
+  mgf_fine_stencil_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, lv[0].st, st64);
+  for (int l = 0; l + 1 < L; ++l) {
+    if (od) {
+      mgf_interp_kernel<<<grid2(lv[l].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l].P);
+      mgf_rap_kernel<true><<<grid2(lv[l + 1].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l].P,
+                                                                          lv[l + 1].st);
+    } else {
+      mgf_rap_kernel<false><<<grid2(lv[l + 1].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l].P,
+                                                                           lv[l + 1].st);
+    }
+  }
+  for (int l = 0; l < L; ++l)
+    mgf_divisor_kernel<<<grid2(lv[l].N, S), kMgThreads, 0, st>>>(lv[l].nf, lv[l].st, lv[l].dv);
+  STOMSFEM_TRY_CUDA(cudaGetLastError());
+  auto cycle = [&]() { return od ? vcycle<true>(lv, L, 0, S, st) : vcycle<false>(lv, L, 0, S, st); };
   // z = M r, rz = r . z, p = z
-  int rc = vcycle(lv, L, 0, S, st);
+  int rc = cycle();
   if (rc) return rc;
   cg_rz_kernel<<<g0, kMgThreads, 0, st>>>(nf, r, lv[0].u, rz);
   cg_direction_kernel<<<g0, kMgThreads, 0, st>>>(nf, lv[0].u, rz, rz_old, done, 1, p);
@@ -562,7 +831,7 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
       if (all) break;
       STOMSFEM_TRY_CUDA(cudaMemcpyAsync(done, hd.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
     }
-    rc = vcycle(lv, L, 0, S, st);
+    rc = cycle();
     if (rc) return rc;
     STOMSFEM_TRY_CUDA(cudaMemcpyAsync(rz_old, rz, sizeof(double) * S, cudaMemcpyDeviceToDevice, st));
     STOMSFEM_TRY_CUDA(cudaMemsetAsync(rz, 0, sizeof(double) * S, st));
