@@ -499,26 +499,28 @@ __global__ void mgf_prolong_kernel(int nff, const float* __restrict__ P, const f
   }
 }
 
-// mm[0] = bit pattern of max a, mm[1] = that of max 1/a over the positive
+// mm[0] = bit pattern of max a, mm[1] = that of min a over the positive
 // entries of a (the patterns of positive doubles order like their values;
-// both start at zero).
+// mm[0] starts at zero, mm[1] at the pattern 0x7F7F7F7F7F7F7F7F, a positive
+// double of about 1.4e306).
 __global__ void mgf_range_kernel(long long n, const double* __restrict__ a, unsigned long long* __restrict__ mm) {
-  unsigned long long hi = 0, lo = 0;
+  unsigned long long hi = 0, lo = 0x7F7F7F7F7F7F7F7Full;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = a[i];
     if (v > 0.0) {
-      hi = max(hi, (unsigned long long)__double_as_longlong(v));
-      lo = max(lo, (unsigned long long)__double_as_longlong(1.0 / v));
+      const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+      hi = max(hi, b);
+      lo = min(lo, b);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomicMax(mm, hi);
-    atomicMax(mm + 1, lo);
+    atomicMin(mm + 1, lo);
   }
 }
 
@@ -769,6 +771,7 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
   unsigned long long* range = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(scal) +
                                                                    range_offset(S));
   STOMSFEM_TRY_CUDA(cudaMemsetAsync(scal, 0, scal_bytes(S), st));
+  STOMSFEM_TRY_CUDA(cudaMemsetAsync(range + 1, 0x7F, sizeof(unsigned long long), st));
   const int sms = device_sm_count() > 0 ? device_sm_count() : 152;
   mgf_range_kernel<<<sms * 4, kMgThreads, 0, st>>>((long long)S * nf * nf, a, range);
   const double h = 1.0 / nf;
@@ -779,10 +782,10 @@ int fine_mg_solve(int nf, double f, const double* a, int S, double* u, void* wor
   STOMSFEM_TRY_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
   STOMSFEM_TRY_CUDA(cudaMemcpyAsync(hrange, range, sizeof(hrange), cudaMemcpyDeviceToHost, st));
   STOMSFEM_TRY_CUDA(cudaStreamSynchronize(st));
-  double amax, ainv;
+  double amax, amin;
   std::memcpy(&amax, &hrange[0], sizeof(double));
-  std::memcpy(&ainv, &hrange[1], sizeof(double));
-  const bool od = amax * ainv > kMgOdContrast;
+  std::memcpy(&amin, &hrange[1], sizeof(double));
+  const bool od = amax > kMgOdContrast * amin;
   // multigrid set-up: stencils of every level
   mgf_fine_stencil_kernel<<<g0, kMgThreads, 0, st>>>(nf, a, lv[0].st, st64);
   for (int l = 0; l + 1 < L; ++l) {
