@@ -5,10 +5,10 @@
 // FP64 preconditioned with one geometric multigrid V-cycle in FP32.
 //
 // Multigrid: levels nf_0 = nf, nf_{l+1} = nf_l / 2 down to nf_L <= 16;
-// operator-dependent prolongation P (coarse node (I, J) at fine node
-// (2I, 2J); the other fine nodes' weights from the fine stencil, see
-// mgf_interp_kernel), restriction P^T, Galerkin coarse operators
-// A_{l+1} = P^T A_l P (9-point
+// prolongation P (coarse node (I, J) at fine node (2I, 2J)) bilinear, or,
+// when the batch's coefficient contrast exceeds kMgOdContrast, with the
+// other fine nodes' weights from the fine stencil (mgf_interp_kernel);
+// restriction P^T, Galerkin coarse operators A_{l+1} = P^T A_l P (9-point
 // stencils again), damped Jacobi smoothing (omega = 0.8, two sweeps before
 // and after the coarse correction: a symmetric V-cycle, so the
 // preconditioner is symmetric positive definite and plain CG applies), and
