@@ -54,10 +54,20 @@ def _coef(name, S, seed, nf=None, nc=None):
     api.stomsfem_sample_coef(g, fld, xi, a)
     return w, g, fld, xi, a
 
-@pytest.mark.parametrize("nf,S", [(64, 3), (128, 2)])
-def test_fine_fem(nf, S):
-    """The direct path (nf <= 64) and the multigrid CG (above)."""
-    _, g, _, _, a = _coef("upscale_1024", S, 3, nf=nf, nc=4)
+@pytest.mark.parametrize("nf,S,channels", [(64, 3, False), (128, 2, False), (128, 2, True)])
+def test_fine_fem(nf, S, channels):
+    """The direct path (nf <= 64) and the multigrid CG (above) with bilinear
+    transfers (a lognormal medium) and with operator-dependent ones (a
+    channel medium of contrast 10^4)."""
+    if channels:
+        fd = dict(W.workload("contrast_2048")["field"], nbx=16, nby=16, width=1.5 / 16)
+        g = api.grid(nf, 4, 1.0)
+        xi = torch.from_numpy(W.draw_xi(fd, S, 3, "normal")).to(DEV)
+        a = torch.empty((S, nf, nf), dtype=torch.float64, device=DEV)
+        api.stomsfem_sample_coef(g, api.field_from_dict(fd), xi, a)
+        assert float(a.max() / a.min()) > 1e3
+    else:
+        _, g, _, _, a = _coef("upscale_1024", S, 3, nf=nf, nc=4)
     u = torch.empty((S, (nf + 1) ** 2), dtype=torch.float64, device=DEV)
 
     def run(ws):
